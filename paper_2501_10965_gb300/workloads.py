@@ -1,0 +1,122 @@
+"""Seeded synthetic workloads shaped like the paper's cases.
+
+This module only states inputs: geometry, gas constants, wall states, initial
+state, time step and seed, as plain numbers.  It holds none of the method's
+arithmetic, so that both the CUDA library and the independent CPU oracle can be
+driven from the same description.
+
+Units follow Sec. 2 of the paper: lengths in L0, density in rho0, temperature
+in T0 and speed in sqrt(R T0).  For the N2-like gas, R = k/m with
+m = 4.65e-26 kg (Sec. 4), so sqrt(R * 273 K) = 284.7 m/s.
+
+The time step follows the rule dt = CFL * dx_min / sqrt(T_max): a particle at
+the thermal speed crosses at most a fraction CFL of a cell per step; every
+workload below also keeps dt under the mean collision time, as Sec. 4 asks.
+"""
+from __future__ import annotations
+
+import copy
+import math
+
+K_BOLTZMANN = 1.380649e-23
+N2_MASS = 4.65e-26            # kg, Sec. 4
+T_REF_K = 273.0               # K, reference temperature of the 1D and cavity cases
+R_N2 = K_BOLTZMANN / N2_MASS  # J/(kg K)
+SPEED_REF = math.sqrt(R_N2 * T_REF_K)  # m/s
+
+
+def _wall(kind="diffuse", T=1.0, u=(0.0, 0.0, 0.0)):
+    return {"kind": kind, "T": float(T), "u": tuple(float(v) for v in u)}
+
+
+def base_config(**kw) -> dict:
+    """Defaults: N2-like gas (omega 0.74, alpha 1, d_r 2, Z_rot 5), unit box."""
+    cfg = {
+        "dim": 1, "nx": 100, "ny": 1, "ppc": 100,
+        "lx": 1.0, "ly": 1.0,
+        "kn": 0.1, "omega": 0.74, "alpha": 1.0, "z_rot": 5.0, "d_r": 2.0,
+        # heat-flux relaxation matrix A (A_tt, A_tr, A_rt, A_rr); the paper
+        # prints no values, these give kappa_t = 15/4 mu, kappa_r = 1.32 mu
+        "a_matrix": (2.0 / 3.0, 0.0, 0.0, 1.0 / 1.32),
+        "dt": 1e-3,
+        "walls": [_wall(), _wall(), _wall(), _wall()],
+        "init_rho": 1.0, "init_tt": 1.0, "init_tr": 1.0, "init_u": (0.0, 0.0, 0.0),
+        "collisions": True,
+        "precision": "fp64",
+        "seed": 0,
+        "capacity": 0,
+        "n_s": 100, "n_m": 2000,
+        "kn_ref": 0.01,
+        "synth_tol": 1e-5,
+        "bin_slack": 2.0,
+    }
+    cfg.update(kw)
+    return cfg
+
+
+def fourier_1d(**kw) -> dict:
+    """1D planar Fourier heat transfer: 100 cells x 100 particles, walls at
+    273 K and 373 K, uniform initial Maxwellian at 323 K, Kn 0.1, FP64,
+    Philox seed 0 (4000 steps in the full run)."""
+    t_hot = 373.0 / T_REF_K
+    t0 = 323.0 / T_REF_K
+    dx = 1.0 / 100
+    cfg = base_config(dim=1, nx=100, ppc=100, kn=0.1, z_rot=5.0,
+                      walls=[_wall(T=1.0), _wall(T=t_hot), _wall(), _wall()],
+                      init_tt=t0, init_tr=t0, precision="fp64", seed=0,
+                      dt=0.3 * dx / math.sqrt(t_hot), n_s=100)
+    cfg.update(kw)
+    return cfg
+
+
+def couette_1d(kn: float = 0.1, **kw) -> dict:
+    """1D Couette flow: 200 cells x 200 particles, walls moving at -/+100 m/s
+    (tangential, y) at 273 K; DIG every 50 steps; FP32 particles."""
+    uw = 100.0 / SPEED_REF
+    dx = 1.0 / 200
+    cfg = base_config(dim=1, nx=200, ppc=200, kn=kn, z_rot=5.0,
+                      walls=[_wall(T=1.0, u=(0.0, -uw, 0.0)), _wall(T=1.0, u=(0.0, uw, 0.0)),
+                             _wall(), _wall()],
+                      precision="fp32", dt=0.3 * dx, n_s=50)
+    cfg.update(kw)
+    return cfg
+
+
+def cavity_2d(nx: int = 100, ny: int = 100, ppc: int = 50, kn: float = 0.01,
+              lid_mps: float = 50.0, lx: float = 1.0, ly: float = 1.0, **kw) -> dict:
+    """2D lid-driven cavity: diffuse walls at 273 K, the top wall (y = ly)
+    slides along +x.  Defaults: 100 x 100 cells, 50 particles per cell,
+    Kn 0.01, lid 50 m/s, Kn_ref 0.05, FP32."""
+    ulid = lid_mps / SPEED_REF
+    dxm = min(lx / nx, ly / ny)
+    cfg = base_config(dim=2, nx=nx, ny=ny, ppc=ppc, lx=lx, ly=ly, kn=kn, z_rot=5.0,
+                      walls=[_wall(), _wall(), _wall(), _wall(u=(ulid, 0.0, 0.0))],
+                      precision="fp32", dt=0.3 * dxm, kn_ref=0.05, n_s=100)
+    cfg.update(kw)
+    return cfg
+
+
+def cavity_2d_20m(**kw) -> dict:
+    """Throughput workload at the cylinder case's scale (400 x 300 cells,
+    ~167 particles per cell, 20.0 M particles, Kn 0.01, FP32): a 4:3 cavity
+    with square cells and a 50 m/s lid."""
+    cfg = cavity_2d(nx=400, ny=300, ppc=167, kn=0.01, lx=4.0 / 3.0, ly=1.0)
+    cfg.update(kw)
+    return cfg
+
+
+def homogeneous_box(ncells: int = 100, ppc: int = 100, kn: float = 0.1, tt: float = 1.0,
+                    tr: float = 1.0, dt: float = 2e-3, **kw) -> dict:
+    """Spatially homogeneous gas: a 1D box with specular walls, so no wall
+    changes the state and every cell is an independent sample."""
+    cfg = base_config(dim=1, nx=ncells, ppc=ppc, kn=kn,
+                      walls=[_wall("specular"), _wall("specular"), _wall(), _wall()],
+                      init_tt=tt, init_tr=tr, dt=dt, precision="fp64")
+    cfg.update(kw)
+    return cfg
+
+
+def with_overrides(cfg: dict, **kw) -> dict:
+    out = copy.deepcopy(cfg)
+    out.update(kw)
+    return out
