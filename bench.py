@@ -1,0 +1,299 @@
+"""Throughput benchmark of the DSMC hot path on one GB300.
+
+A step is one DSMC time step of the whole particle path (free flight with
+diffuse walls, cell indexing and bin sort, NTC/VHS/Borgnakke-Larsen
+collisions, cell sampling) over the workload's full particle state, which
+stays resident in HBM.  The default workload is a 2D lid-driven cavity at the
+scale of the paper's cylinder case: 400 x 300 cells, 167 particles per cell
+(20.0 M particles), Kn 0.01, FP32 particles with FP64 moment accumulators.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead, on a
+bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+ALGO_BYTES_PER_PARTICLE_STEP = {("fp32", 2): 48, ("fp32", 1): 40, ("fp64", 2): 96, ("fp64", 1): 80}
+METRIC = "particle-steps/s"
+
+
+def workload(name: str) -> dict:
+    from paper_2501_10965_gb300 import workloads as W
+    if name == "cavity2d_20m":
+        return W.cavity_2d_20m()
+    if name == "cavity2d_500k":
+        return W.cavity_2d()
+    if name == "couette1d_40k":
+        return W.couette_1d(kn=0.01)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = sorted(v for v in (num(r[1]) for r in rows) if v is not None)
+        smax = max((v for v in (num(r[2]) for r in rows) if v is not None), default=None)
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        load = [v for v in sm if smax is None or v > 0.3 * smax] or sm
+        return {"sm_mhz": load[len(load) // 2] if load else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _events_time(fn, stream) -> float:
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def cpu_baseline(cfg: dict, budget_s: float = 12.0) -> dict:
+    """The oracle, as it stands, on a bounded sample of the workload: the same
+    gas, Kn, particles per cell and time step on a smaller box of cells."""
+    import oracle
+    sub = dict(cfg)
+    sub["precision"] = "fp64"
+    if int(cfg["dim"]) == 2:
+        sub["nx"], sub["ny"] = 40, 30
+        sub["lx"] = float(cfg["lx"]) * 40 / int(cfg["nx"])
+        sub["ly"] = float(cfg["ly"]) * 30 / int(cfg["ny"])
+    sim = oracle.OracleSim(sub)
+    n = sim.n
+    sim.step(2, sample=True)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        sim.step(5, sample=True)
+        steps += 5
+    dt = time.perf_counter() - t0
+    cells = int(sub["nx"]) * (int(sub.get("ny", 1)) if int(sub["dim"]) == 2 else 1)
+    return {"value": n * steps / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{cells} cells x {sub['ppc']} particles ({n} particles), {steps} steps, {dt:.1f} s, "
+                      f"FP64 single-threaded C oracle, same gas/Kn/ppc/dt as the workload"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cfg = workload(args.workload)
+    per_step = []
+    for _ in range(args.warmup):
+        cpu_baseline(cfg, budget_s=1.0)
+    tot = 0.0
+    for _ in range(args.steps):
+        r = cpu_baseline(cfg, budget_s=max(2.0, 30.0 / max(args.steps, 1)))
+        per_step.append(r["value"])
+        tot += r["value"]
+    v = tot / len(per_step)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": r["sample"]},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": r["sample"]},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_10965_gb300 import dsmc
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = workload(args.workload)
+    # independent replicas: every rank runs its own seeded copy of the workload
+    cfg["seed"] = int(cfg.get("seed", 0)) + 1000 * rank
+    prec = cfg["precision"]
+    dim = int(cfg["dim"])
+    stream = torch.cuda.current_stream(dev)
+    sim = dsmc.Dsmc(cfg, device=dev, stream=stream)
+    n = sim.num_particles()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (untimed)
+    sim.dsmc_step(max(args.warmup, 3), sample=True)
+    reb0 = sim.stats()["n_rebuild"]
+    barrier()
+    with ClockSampler(local) as clk:
+        barrier()
+        t = _events_time(lambda: sim.dsmc_step(args.steps, sample=True), stream)
+        barrier()
+    clocks = clk.summary()
+    reb1 = sim.stats()["n_rebuild"]
+    if world > 1:
+        tt = torch.tensor([t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    value = n * args.steps * world / t
+
+    # average duration of one fused step kernel: difference of two runs with
+    # different step counts on the launching stream (the constant parts --
+    # the first move-only and last collide-only launch and the bin check --
+    # cancel)
+    k1, k2 = 4, 4 + max(8, args.steps // 2)
+    t1 = min(_events_time(lambda: sim.dsmc_step(k1, sample=True), stream) for _ in range(2))
+    t2 = min(_events_time(lambda: sim.dsmc_step(k2, sample=True), stream) for _ in range(2))
+    per_launch = (t2 - t1) / (k2 - k1)
+    algo = ALGO_BYTES_PER_PARTICLE_STEP[(prec, dim)] * n
+    peaks = measured_peaks()
+    achieved = algo / per_launch / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": args.traffic,
+                "kernel": "k_fused (collide + sample + move + bin append, one launch per step)",
+                "algorithmic_bytes_per_launch": algo, "launch_ms": per_launch * 1e3,
+                "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
+
+    # end to end through the C ABI with host buffers: upload the particle
+    # state from pinned host memory, K steps, download the sampled fields
+    p = sim.get_particles()
+    host = {k: v.to("cpu").pin_memory() for k, v in p.items() if k != "cell"}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    fields_host = torch.empty((sim.ncells, dsmc.NFIELDS), dtype=torch.float64).pin_memory()
+    d2h = fields_host.numel() * fields_host.element_size()
+
+    def e2e():
+        dev_p = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+        sim.set_particles(dev_p)
+        sim.dsmc_sample(reset=True)
+        sim.dsmc_step(args.steps, sample=True)
+        f = sim.dsmc_sample(reset=True)
+        fields_host.copy_(f, non_blocking=True)
+    barrier()
+    te = _events_time(e2e, stream)
+    e2e_value = n * args.steps * world / te
+
+    gpu_launches = (args.steps + 1) + 5 * (reb1 - reb0)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "cells": sim.ncells, "particles": n,
+                           "particles_per_cell": cfg["ppc"], "kn": cfg["kn"], "dt": cfg["dt"],
+                           "precision": prec + " particles, fp64 compensated moments",
+                           "l2": "inputs larger than L2 (particle state %.2f GB)" % (n * 24 / 1e9),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "clocks": clocks, "gpu_launches": gpu_launches,
+                "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d / args.steps,
+                        "d2h_bytes_per_step": d2h / args.steps},
+                "cpu_baseline": cpu,
+                "stats": sim.stats()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="cavity2d_20m")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per fused launch from an ncu capture of the current kernel")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

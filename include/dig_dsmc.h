@@ -1,0 +1,217 @@
+/*
+ * dig_dsmc.h -- C ABI of the GB300 (sm_103a) DSMC / DIG hot-path library.
+ *
+ * The library runs the data-parallel hot path of the DIG method of
+ * "Multiscale simulation of rarefied polyatomic gas flow via DIG method"
+ * (arXiv 2501.10965): the DSMC time step of a polyatomic gas with continuous
+ * rotational energy (Sec. 2.2), the cell sampling of Eq. (DSMC_macroscopic),
+ * the higher-order terms of Eq. (hot_constitutive) with the adaptive Kn_GLL
+ * mask of Sec. 3.1, the steady synthetic equations of Eq. (macroscopic_equation)
+ * (Sec. 3 step 3) and the particle modification of Sec. 3.2.
+ *
+ * Conventions for every entry point:
+ *  - Plain C types only.  "dev" pointers are CUDA device pointers on the
+ *    device that was current when dsmc_init ran; "host" pointers are CPU
+ *    memory.  Arrays are dense, row-major, FP64 unless stated.
+ *  - The caller owns every buffer it passes, including the workspace given to
+ *    dsmc_init; the library never frees caller memory and allocates no device
+ *    memory of its own.  The library owns only the opaque handle (host memory).
+ *  - Work is queued on the CUDA stream given to dsmc_init.  Calls that return
+ *    host values (counts, iterations, statistics) synchronise that stream.
+ *  - Return value: DSMC_OK (0) or a negative DSMC_ERR_* code; no exception or
+ *    longjmp crosses the ABI.  dsmc_last_error() describes the last failure
+ *    on a handle.  On DSMC_ERR_ARG, DSMC_ERR_CAPACITY and DSMC_ERR_NUMERIC the
+ *    simulation state is left unchanged unless stated otherwise.
+ *  - A handle must not be used from two host threads at once.
+ *
+ * Units (Sec. 2): lengths in L0, density in rho0, temperature in T0, speed in
+ * sqrt(R T0); a particle has unit mass; I_r is the rotational energy of one
+ * molecule per unit mass in units of R T0, so <I_r> = (d_r/2) T_r.
+ */
+#ifndef DIG_DSMC_H
+#define DIG_DSMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DSMC_ABI_VERSION 1
+
+#define DSMC_OK 0
+#define DSMC_ERR_ARG (-1)           /* invalid argument or configuration */
+#define DSMC_ERR_CAPACITY (-2)      /* particle count would exceed the workspace */
+#define DSMC_ERR_NUMERIC (-3)       /* non-finite or non-positive rho / T input */
+#define DSMC_ERR_NOT_CONVERGED (-4) /* synth_solve hit n_m iterations; outputs written */
+#define DSMC_ERR_TIMEOUT (-5)       /* a bounded device wait gave up */
+#define DSMC_ERR_CUDA (-6)          /* a CUDA runtime call failed */
+
+#define DSMC_PREC_FP64_DET 0 /* FP64 particles, oracle-identical event order */
+#define DSMC_PREC_FP32 1     /* FP32 particles in padded cell bins, FP64 moments */
+
+#define DSMC_WALL_DIFFUSE 0  /* full accommodation at wall_t, wall_u (Sec. 4) */
+#define DSMC_WALL_SPECULAR 1 /* mirror reflection */
+
+#define DSMC_NFIELDS 18 /* rho, u(3), T_t, T_r, sigma(xx yy zz xy xz yz), q_t(3), q_r(3) */
+#define DSMC_NHOT 12    /* HoT of sigma (6), q_t (3), q_r (3) */
+#define DSMC_NTARGET 6  /* rho, u(3), T_t, T_r */
+#define DSMC_NMOM 17    /* raw sums per cell, see dsmc_get_accumulators */
+
+/* Simulation description.  Walls: 0 at x = 0, 1 at x = lx, 2 at y = 0,
+ * 3 at y = ly (2D only).  A 1D slab has walls 0 and 1 only and ignores ny, ly. */
+typedef struct dsmc_config {
+  int32_t version;   /* DSMC_ABI_VERSION */
+  int32_t dim;       /* 1 or 2 */
+  int32_t nx, ny;    /* uniform Cartesian cells */
+  int32_t ppc;       /* initial particles per cell */
+  int32_t precision; /* DSMC_PREC_* */
+  double lx, ly;     /* domain lengths */
+  double kn;         /* global Knudsen number, Sec. 2: mu_ref = Kn sqrt(2/pi) */
+  double omega;      /* VHS viscosity index (Sec. 4: 0.74) */
+  double alpha;      /* VSS scattering parameter; only 1 (VHS) is supported */
+  double z_rot;      /* rotational collision number Z, Eq. (P_inelastic) */
+  double d_r;        /* rotational degrees of freedom; only 2 is supported */
+  double a_matrix[4]; /* A_tt, A_tr, A_rt, A_rr of Eq. (heat_flux_relaxation) */
+  double dt;          /* time step */
+  int32_t wall_kind[4];
+  double wall_t[4];
+  double wall_u[4][3]; /* wall velocity; its normal component must be 0 */
+  double init_rho, init_tt, init_tr; /* initial uniform equilibrium state */
+  double init_u[3];
+  int32_t collisions; /* 1: collide (normal); 0: collisionless gas */
+  int32_t n_s;        /* DSMC steps per DIG iteration (informational) */
+  int32_t n_m;        /* maximum synth_solve iterations (Sec. 3 step 3) */
+  int32_t pad0;
+  double kn_ref;      /* Kn_GLL threshold of Sec. 3.1 */
+  double synth_tol;   /* synth_solve stops when the relative change is below this */
+  uint64_t seed;      /* Philox4x32-10 key */
+  int64_t capacity;   /* maximum particles; 0 = chosen from ppc and bin_slack */
+  double bin_slack;   /* FP32 layout: a cell's bin holds slack x its count (+32) */
+} dsmc_config;
+
+typedef struct dsmc_handle dsmc_handle;
+
+/* Workspace bytes dsmc_init needs for cfg (device memory, 256-byte aligned,
+ * any contents).  Returns DSMC_ERR_ARG for an unsupported configuration. */
+int dsmc_workspace_size(const dsmc_config *cfg, size_t *bytes);
+
+/* Create a simulation in the caller's workspace (dev, >= dsmc_workspace_size
+ * bytes) on stream (a cudaStream_t, or NULL for the legacy default stream) and
+ * fill it with the uniform equilibrium state of cfg: in every cell, ppc
+ * particles uniform in the cell with Maxwellian velocities at (init_u,
+ * init_tt) and exponential rotational energies of mean init_tr (d_r = 2)
+ * (Sec. 3 step 1: particles initialised from an equilibrium distribution).
+ * The workspace must stay allocated until dsmc_destroy. */
+int dsmc_init(const dsmc_config *cfg, void *dev_workspace, size_t bytes, void *stream,
+              dsmc_handle **out);
+
+/* Release the handle (host memory only; the workspace stays the caller's). */
+int dsmc_destroy(dsmc_handle *h);
+
+/* Text of the last error on h (never NULL). */
+const char *dsmc_last_error(const dsmc_handle *h);
+
+/* Advance nsteps DSMC time steps (Sec. 2.2), each in the order: free flight
+ * with wall interaction, cell indexing and sort, No-Time-Counter collisions
+ * with VHS cross-section and Borgnakke-Larsen exchange (Eq. P_inelastic),
+ * and, if sample != 0, accumulation of the cell sums behind
+ * Eq. (DSMC_macroscopic).  Asynchronous, except that the FP32 layout reads
+ * one word back at the end to decide whether its cell bins must be rebuilt. */
+int dsmc_step(dsmc_handle *h, int nsteps, int sample);
+
+/* Time-averaged cell fields of Eq. (DSMC_macroscopic) from the sums
+ * accumulated since the last reset: dev_fields is ncells x DSMC_NFIELDS.
+ * Central moments are taken about the time-averaged velocity; T_r =
+ * 2 sum(I_r)/(d_r N); empty cells give zeros.  reset != 0 clears the sums
+ * afterwards. */
+int dsmc_sample(dsmc_handle *h, double *dev_fields, int reset);
+
+/* Higher-order terms, Eq. (hot_constitutive): dev_hot (ncells x DSMC_NHOT) =
+ * sampled stress and heat fluxes minus the NSF relations of
+ * Eq. (ns_constitutive) evaluated with the sampled fields (kappa from
+ * Eq. (kappa_A)); dev_kngll (ncells) = Kn_GLL of Sec. 3.1; dev_mask (ncells,
+ * uint8) = 1 where Kn_GLL >= kn_ref.  HoT is set to 0 where mask = 0.
+ * Any of dev_kngll / dev_mask may be NULL. */
+int dsmc_hot(dsmc_handle *h, const double *dev_fields, double *dev_hot, double *dev_kngll,
+             uint8_t *dev_mask);
+
+/* Steady synthetic equations (Eq. macroscopic_equation with the
+ * constitutive relations of Eq. full_constitutive), Sec. 3 step 3, for the 1D
+ * slab: u_x = 0; the first and last cell keep the sampled u_y, u_z, T_t, T_r
+ * (Dirichlet); total mass equals the sampled mass.  Newton iterations from
+ * dev_fields until the largest relative update is below synth_tol or n_m
+ * iterations.  dev_out is ncells x DSMC_NTARGET.  host_iters / host_resid
+ * (may be NULL) receive the iteration count and the final max |residual|.
+ * Returns DSMC_ERR_NOT_CONVERGED (outputs written) when n_m is reached, and
+ * DSMC_ERR_NUMERIC if the solution leaves rho > 0, T > 0. */
+int synth_solve(dsmc_handle *h, const double *dev_fields, const double *dev_hot, double *dev_out,
+                int *host_iters, double *host_resid);
+
+/* Particle modification of Sec. 3.2 to the target dev_target (ncells x
+ * DSMC_NTARGET = rho, u, T_t, T_r): (i) N_new = Iround(rho V / F); (ii) remove
+ * uniformly chosen particles, or add copies of uniformly chosen existing ones
+ * placed uniformly in the cell (an empty cell draws from the target
+ * Maxwellian); (iii) sample u*, T_t*, T_r* of the result; (iv) v <- a v + b,
+ * I_r <- c I_r with a = sqrt(T_t/T_t*), b = u - a u*, c = T_r/T_r*.
+ * DSMC_ERR_NUMERIC (nothing changed) if a target is non-finite, rho < 0 or a
+ * temperature <= 0; DSMC_ERR_CAPACITY (nothing changed) if the new total does
+ * not fit. */
+int dig_correct(dsmc_handle *h, const double *dev_target);
+
+/* ---- state access (tests, checkpoints, diagnostics) ---------------------- */
+
+/* Number of particles (synchronises). */
+int dsmc_num_particles(dsmc_handle *h, int64_t *host_n);
+
+/* Copy the particles out, cell by cell (cell index order; within a cell the
+ * current storage order), converted to FP64: six dev arrays of length
+ * capacity_out (x, y, vx, vy, vz, I_r; y = 0 in 1D) and dev_cell (int32).
+ * host_n receives the count; DSMC_ERR_CAPACITY if capacity_out is too small. */
+int dsmc_get_particles(dsmc_handle *h, double *dev_x, double *dev_y, double *dev_vx, double *dev_vy,
+                       double *dev_vz, double *dev_ir, int32_t *dev_cell, int64_t capacity_out,
+                       int64_t *host_n);
+
+/* Replace the particles by n given ones (dev FP64 arrays; y ignored in 1D);
+ * they are binned by position keeping their given order within a cell. */
+int dsmc_set_particles(dsmc_handle *h, int64_t n, const double *dev_x, const double *dev_y,
+                       const double *dev_vx, const double *dev_vy, const double *dev_vz,
+                       const double *dev_ir);
+
+/* Raw per-cell sums (dev, ncells x DSMC_NMOM): N, sum v_i (3), sum v_i v_j
+ * (xx yy zz xy xz yz), sum v_i |v|^2 (3), sum I_r, sum I_r v_i (3), over the
+ * sampled steps since the last reset; host_nsamples receives their number. */
+int dsmc_get_accumulators(dsmc_handle *h, double *dev_out, int64_t *host_nsamples);
+
+/* Per-cell (sigma g)_max (dev, ncells), read or overwritten. */
+int dsmc_get_sgmax(dsmc_handle *h, double *dev_out);
+int dsmc_set_sgmax(dsmc_handle *h, const double *dev_in);
+
+/* Step counter (keys the random streams of the DSMC step) and DIG iteration
+ * counter (keys those of dig_correct). */
+int dsmc_get_counters(dsmc_handle *h, uint32_t *host_step, uint32_t *host_dig_iter);
+int dsmc_set_counters(dsmc_handle *h, uint32_t step, uint32_t dig_iter);
+
+/* Event counters since dsmc_init (host, 8 entries): candidate pairs, accepted
+ * collisions, accepted pairs with sigma g > (sigma g)_max, Borgnakke-Larsen
+ * events, wall hits, flights cut after 8 wall hits, particles that did not fit
+ * their cell bin (FP32 layout, kept in an overflow list until the next
+ * rebuild), bin rebuilds. */
+int dsmc_get_stats(dsmc_handle *h, int64_t *host_out8);
+
+/* Wall tallies since dsmc_init (host, 4 walls x 5): hits, momentum (3) and
+ * energy (translational + rotational) delivered to the wall, per unit mass
+ * of a simulated particle (multiply by F = rho V / N for physical units). */
+int dsmc_get_wall_tally(dsmc_handle *h, double *host_out20);
+
+/* Derived constants (host, 8 entries): dx, dy, cell volume V, particle weight
+ * F, mu_ref, K (nu = K p / mu), C_sigma (sigma g = C_sigma g^(2-2 omega)),
+ * P_inelastic. */
+int dsmc_get_constants(dsmc_handle *h, double *host_out8);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIG_DSMC_H */

@@ -178,7 +178,9 @@ static void or_constants_compute(or_state *S) {
   S->dx = c->lx / (double)c->nx;
   S->dy = (c->dim == 2) ? c->ly / (double)c->ny : 1.0;
   S->vcell = S->dx * S->dy;
-  S->fnum = c->init_rho * S->vcell / (double)c->ppc;
+  /* particle weight F = rho V / N_p (Eq. DSMC_macroscopic); a state created
+   * empty is weighted as if it had one particle per cell */
+  S->fnum = c->init_rho * S->vcell / (double)(c->ppc > 0 ? c->ppc : 1);
   S->mu_ref = c->kn * sqrt(2.0 / M_PI);
   S->k_visc = 5.0 * (a + 1.0) * (a + 2.0) / (a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w));
   S->c_sigma = S->k_visc /

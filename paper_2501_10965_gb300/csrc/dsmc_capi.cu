@@ -1,0 +1,590 @@
+// dsmc_capi.cu -- the extern "C" entry points declared in include/dig_dsmc.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dig_dsmc.h"
+#include "dsmc_internal.h"
+
+using namespace dsmc;
+
+struct dsmc_handle {
+  dsmc_config cfg;
+  int ncells = 0;
+  int det = 1;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  Params<double> pd{};
+  Params<float> pf{};
+  CellParams cp{};
+  State<double> sd{};
+  State<float> sf{};
+  int cur = 0, lay = 0;
+  uint32_t step = 0, dig_iter = 0;
+  int64_t nsamples = 0;
+  int64_t rebuilds = 0;
+  double* synth_work = nullptr;
+  double* synth_info = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int set_err(dsmc_handle* h, int code, const char* fmt, ...) {
+  if (h) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    h->err = buf;
+  }
+  return code;
+}
+
+int check_cuda(dsmc_handle* h, const char* where) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_err(h, DSMC_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+  return DSMC_OK;
+}
+
+int sync_check(dsmc_handle* h, const char* where) {
+  const cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return set_err(h, DSMC_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+  return check_cuda(h, where);
+}
+
+int32_t host_bin_cap(int32_t count, double slack) {
+  const int32_t c = (int32_t)std::ceil(slack * (double)count) + 32;
+  return (c + 7) & ~7;
+}
+
+int validate(const dsmc_config* c, char* why, size_t n) {
+  if (!c) return snprintf(why, n, "null config"), DSMC_ERR_ARG;
+  if (c->version != DSMC_ABI_VERSION) return snprintf(why, n, "config version %d != %d", c->version, DSMC_ABI_VERSION), DSMC_ERR_ARG;
+  if (c->dim != 1 && c->dim != 2) return snprintf(why, n, "dim must be 1 or 2"), DSMC_ERR_ARG;
+  if (c->nx <= 0 || (c->dim == 2 && c->ny <= 0)) return snprintf(why, n, "cell counts must be positive"), DSMC_ERR_ARG;
+  if (c->ppc < 0) return snprintf(why, n, "ppc must be >= 0"), DSMC_ERR_ARG;
+  if (!(c->lx > 0) || (c->dim == 2 && !(c->ly > 0))) return snprintf(why, n, "domain lengths must be positive"), DSMC_ERR_ARG;
+  if (!(c->kn > 0) || !(c->dt > 0) || !(c->z_rot > 0)) return snprintf(why, n, "kn, dt, z_rot must be positive"), DSMC_ERR_ARG;
+  if (!(c->omega > 0.5 && c->omega <= 1.0)) return snprintf(why, n, "omega must lie in (0.5, 1]"), DSMC_ERR_ARG;
+  if (c->alpha != 1.0) return snprintf(why, n, "only alpha = 1 (VHS scattering) is supported"), DSMC_ERR_ARG;
+  if (c->d_r != 2.0) return snprintf(why, n, "only d_r = 2 is supported"), DSMC_ERR_ARG;
+  if (c->precision != DSMC_PREC_FP64_DET && c->precision != DSMC_PREC_FP32) return snprintf(why, n, "bad precision"), DSMC_ERR_ARG;
+  if (!(c->init_rho > 0) || !(c->init_tt > 0) || !(c->init_tr > 0)) return snprintf(why, n, "initial rho, T must be positive"), DSMC_ERR_ARG;
+  const int nw = 2 * c->dim;
+  for (int w = 0; w < nw; ++w) {
+    if (c->wall_kind[w] != DSMC_WALL_DIFFUSE && c->wall_kind[w] != DSMC_WALL_SPECULAR) return snprintf(why, n, "bad wall kind"), DSMC_ERR_ARG;
+    if (c->wall_kind[w] == DSMC_WALL_DIFFUSE && !(c->wall_t[w] > 0)) return snprintf(why, n, "wall temperature must be positive"), DSMC_ERR_ARG;
+    const int axis = w < 2 ? 0 : 1;
+    if (c->wall_u[w][axis] != 0.0) return snprintf(why, n, "wall %d moves along its normal", w), DSMC_ERR_ARG;
+  }
+  const long long ncells = (long long)c->nx * (c->dim == 2 ? c->ny : 1);
+  if (ncells > (1LL << 26)) return snprintf(why, n, "too many cells"), DSMC_ERR_ARG;
+  if (ncells * (long long)c->ppc > (1LL << 30)) return snprintf(why, n, "too many particles"), DSMC_ERR_ARG;
+  if (c->precision == DSMC_PREC_FP32 && !(c->bin_slack >= 1.0)) return snprintf(why, n, "bin_slack must be >= 1"), DSMC_ERR_ARG;
+  return DSMC_OK;
+}
+
+struct Plan {
+  int ncells, det, tile, ovf_cap;
+  int64_t capacity;
+  size_t bytes;
+};
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <typename P>
+  P* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    P* p = base ? reinterpret_cast<P*>(base + off) : nullptr;
+    off += sizeof(P) * (count ? count : 1);
+    return p;
+  }
+};
+
+template <typename T>
+void carve_state(Carver& cv, const Plan& pl, State<T>& s) {
+  const size_t cap = (size_t)pl.capacity, nc = (size_t)pl.ncells;
+  for (int b = 0; b < 2; ++b) {
+    s.buf[b].x = cv.take<T>(cap);
+    s.buf[b].y = cv.take<T>(cap);
+    s.buf[b].vx = cv.take<T>(cap);
+    s.buf[b].vy = cv.take<T>(cap);
+    s.buf[b].vz = cv.take<T>(cap);
+    s.buf[b].ir = cv.take<T>(cap);
+    s.start[b] = cv.take<int32_t>(nc + 1);
+    s.count[b] = cv.take<int32_t>(nc);
+  }
+  s.cellof = cv.take<int32_t>(cap);
+  s.key = cv.take<int32_t>(cap);
+  s.dest = cv.take<int32_t>(cap);
+  s.scratch_i = cv.take<int32_t>(cap);
+  s.owner = cv.take<uint32_t>(cap);
+  s.nt = cv.take<int32_t>(nc + 1);
+  s.tmp_start = cv.take<int32_t>(nc + 1);
+  s.tmp2 = cv.take<int32_t>(nc + 1);
+  s.sgmax = cv.take<T>(nc);
+  s.acc = cv.take<double>(nc * NMOM);
+  s.comp = cv.take<double>(nc * NMOM);
+  s.tally = cv.take<double>(20);
+  s.stats = cv.take<unsigned long long>(ST_NSLOTS);
+  s.flags = cv.take<int32_t>(16);
+  for (int b = 0; b < 2; ++b) {
+    const size_t oc = pl.det ? 1 : (size_t)pl.ovf_cap;
+    s.ovf[b].x = reinterpret_cast<float*>(cv.take<float>(oc));
+    s.ovf[b].y = cv.take<float>(oc);
+    s.ovf[b].vx = cv.take<float>(oc);
+    s.ovf[b].vy = cv.take<float>(oc);
+    s.ovf[b].vz = cv.take<float>(oc);
+    s.ovf[b].ir = cv.take<float>(oc);
+    s.ovf[b].dest = cv.take<int32_t>(oc);
+    s.ovf[b].count = cv.take<int32_t>(1);
+  }
+  s.capacity = pl.capacity;
+  s.ovf_cap = pl.ovf_cap;
+  s.tile = pl.tile;
+}
+
+Plan make_plan(const dsmc_config* c, char* base, dsmc_handle* h) {
+  Plan pl{};
+  pl.ncells = c->nx * (c->dim == 2 ? c->ny : 1);
+  pl.det = c->precision == DSMC_PREC_FP64_DET;
+  const int64_t n0 = (int64_t)pl.ncells * c->ppc;
+  if (pl.det) {
+    pl.capacity = c->capacity > 0 ? c->capacity : 2 * n0 + 64;
+  } else {
+    const int64_t bins = (int64_t)pl.ncells * host_bin_cap(c->ppc, c->bin_slack);
+    pl.capacity = c->capacity > 0 ? c->capacity : bins + bins / 4 + 1024;
+  }
+  int tile = 2 * c->ppc;
+  if (tile < 64) tile = 64;
+  tile = (tile + 31) & ~31;
+  const int tmax = pl.det ? 256 : 512;
+  if (tile > tmax) tile = tmax;
+  pl.tile = tile;
+  pl.ovf_cap = pl.det ? 1 : (int)(pl.capacity / 16 + 1024);
+  Carver cv{base};
+  if (pl.det) {
+    State<double> s{};
+    carve_state(cv, pl, s);
+    if (h) h->sd = s;
+  } else {
+    State<float> s{};
+    carve_state(cv, pl, s);
+    if (h) h->sf = s;
+  }
+  double* sw = cv.take<double>(c->dim == 1 ? synth1d_work_doubles(pl.ncells) : 1);
+  double* si = cv.take<double>(8);
+  if (h) {
+    h->synth_work = sw;
+    h->synth_info = si;
+  }
+  pl.bytes = cv.off + 256;
+  return pl;
+}
+
+template <typename T>
+void fill_params(const dsmc_config* c, Params<T>& p, CellParams& cp) {
+  const double w = c->omega, a = c->alpha;
+  const int ny = (c->dim == 2) ? c->ny : 1;
+  const double lx = c->lx, ly = (c->dim == 2) ? c->ly : 1.0;
+  const double dx = lx / (double)c->nx;
+  const double dy = (c->dim == 2) ? ly / (double)ny : 1.0;
+  const double vcell = dx * dy;
+  const double fnum = c->init_rho * vcell / (double)(c->ppc > 0 ? c->ppc : 1);
+  const double mu_ref = c->kn * std::sqrt(2.0 / M_PI);
+  const double kv = 5.0 * (a + 1.0) * (a + 2.0) / (a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w));
+  const double c_sigma = kv / (mu_ref * std::pow(4.0, 1.0 - w) * (2.0 / std::sqrt(M_PI)) * std::tgamma(2.5 - w));
+  const double p_inel = a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (a + 1.0) * (a + 2.0) * c->z_rot);
+  p.dim = c->dim;
+  p.nx = c->nx;
+  p.ny = ny;
+  p.ncells = c->nx * ny;
+  p.lx = (T)lx;
+  p.ly = (T)ly;
+  p.dx = (T)dx;
+  p.dy = (T)dy;
+  p.sx = (T)((double)c->nx / lx);
+  p.sy = (T)((double)ny / ly);
+  p.vcell = (T)vcell;
+  p.fnum = (T)fnum;
+  p.dt = (T)c->dt;
+  p.c_sigma = (T)c_sigma;
+  p.p_inel = (T)p_inel;
+  p.vhs_e = (T)(2.0 - 2.0 * w);
+  p.bl_exp = (T)(1.0 / (2.5 - w));
+  p.collisions = c->collisions ? 1 : 0;
+  for (int k = 0; k < 4; ++k) {
+    p.wall_kind[k] = c->wall_kind[k];
+    p.wall_t[k] = (T)c->wall_t[k];
+    for (int q = 0; q < 3; ++q) p.wall_u[k][q] = (T)c->wall_u[k][q];
+  }
+  p.k0 = (uint32_t)(c->seed & 0xffffffffu);
+  p.k1 = (uint32_t)(c->seed >> 32);
+  // FP64 cell parameters
+  cp.dim = c->dim;
+  cp.nx = c->nx;
+  cp.ny = ny;
+  cp.ncells = c->nx * ny;
+  cp.lx = lx;
+  cp.ly = ly;
+  cp.dx = dx;
+  cp.dy = dy;
+  cp.vcell = vcell;
+  cp.fnum = fnum;
+  cp.d_r = c->d_r;
+  cp.omega = w;
+  cp.mu_ref = mu_ref;
+  cp.z_rot = c->z_rot;
+  // Eq. (kappa_A): (kappa_t, kappa_r) = (mu/2) A^-1 (5, d_r)
+  const double* A = c->a_matrix;
+  const double det = A[0] * A[3] - A[1] * A[2];
+  cp.kappa_t = 0.5 * (A[3] * 5.0 - A[1] * c->d_r) / det;
+  cp.kappa_r = 0.5 * (-A[2] * 5.0 + A[0] * c->d_r) / det;
+  cp.kn_ref = c->kn_ref;
+  cp.k0 = p.k0;
+  cp.k1 = p.k1;
+}
+
+double sgmax0(const dsmc_config* c, double c_sigma) {
+  double tref = c->init_tt;
+  double uref = std::sqrt(c->init_u[0] * c->init_u[0] + c->init_u[1] * c->init_u[1] + c->init_u[2] * c->init_u[2]);
+  double umax = 0.0;
+  for (int w = 0; w < 2 * c->dim; ++w) {
+    if (c->wall_kind[w] == 0 && c->wall_t[w] > tref) tref = c->wall_t[w];
+    const double uw = std::sqrt(c->wall_u[w][0] * c->wall_u[w][0] + c->wall_u[w][1] * c->wall_u[w][1] +
+                                c->wall_u[w][2] * c->wall_u[w][2]);
+    if (uw > umax) umax = uw;
+  }
+  uref += umax;
+  return c_sigma * std::pow(4.0 * std::sqrt(tref) + uref, 2.0 - 2.0 * c->omega);
+}
+
+template <typename T>
+__global__ void k_fill(T* a, int n, T v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
+}
+
+template <typename T>
+int init_state(dsmc_handle* h, State<T>& s, Params<T>& p) {
+  const dsmc_config* c = &h->cfg;
+  cudaStream_t st = h->stream;
+  const int nc = h->ncells;
+  cudaMemsetAsync(s.stats, 0, sizeof(unsigned long long) * ST_NSLOTS, st);
+  cudaMemsetAsync(s.tally, 0, sizeof(double) * 20, st);
+  cudaMemsetAsync(s.flags, 0, sizeof(int32_t) * 16, st);
+  cudaMemsetAsync(s.acc, 0, sizeof(double) * nc * NMOM, st);
+  cudaMemsetAsync(s.comp, 0, sizeof(double) * nc * NMOM, st);
+  for (int b = 0; b < 2; ++b) {
+    cudaMemsetAsync(s.count[b], 0, sizeof(int32_t) * nc, st);
+    cudaMemsetAsync(s.ovf[b].count, 0, sizeof(int32_t), st);
+  }
+  cudaMemsetAsync(s.buf[0].y, 0, sizeof(T) * (size_t)s.capacity, st);
+  cudaMemsetAsync(s.buf[1].y, 0, sizeof(T) * (size_t)s.capacity, st);
+  double csd;
+  {
+    Params<double> pd;
+    CellParams cpd;
+    fill_params<double>(c, pd, cpd);
+    csd = (double)pd.c_sigma;
+  }
+  k_fill<T><<<(nc + 255) / 256, 256, 0, st>>>(s.sgmax, nc, (T)sgmax0(c, csd));
+  // layout: compact (det) or padded bins of equal capacity (FP32)
+  const int32_t cap0 = h->det ? c->ppc : host_bin_cap(c->ppc, c->bin_slack);
+  if ((int64_t)cap0 * nc > s.capacity) return set_err(h, DSMC_ERR_CAPACITY, "initial bins need %lld slots, capacity %lld", (long long)cap0 * nc, (long long)s.capacity);
+  h->cur = 0;
+  h->lay = 0;
+  Ops<T>::init(p, s, 0, 0, c->ppc, cap0, c->init_tt, c->init_tr, c->init_u, st);
+  s.nparticles = nc * c->ppc;
+  s.slack = c->bin_slack;
+  return check_cuda(h, "dsmc_init");
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int dsmc_workspace_size(const dsmc_config* cfg, size_t* bytes) {
+  char why[256];
+  if (!bytes) return DSMC_ERR_ARG;
+  const int rc = validate(cfg, why, sizeof why);
+  if (rc) return rc;
+  *bytes = make_plan(cfg, nullptr, nullptr).bytes;
+  return DSMC_OK;
+}
+
+int dsmc_init(const dsmc_config* cfg, void* dev_workspace, size_t bytes, void* stream, dsmc_handle** out) {
+  if (!out) return DSMC_ERR_ARG;
+  *out = nullptr;
+  char why[256];
+  const int rc = validate(cfg, why, sizeof why);
+  if (rc) return rc;
+  const Plan pl = make_plan(cfg, nullptr, nullptr);
+  if (!dev_workspace || bytes < pl.bytes) return DSMC_ERR_ARG;
+  dsmc_handle* h = new (std::nothrow) dsmc_handle();
+  if (!h) return DSMC_ERR_ARG;
+  h->cfg = *cfg;
+  if (h->cfg.dim == 1) {
+    h->cfg.ny = 1;
+    h->cfg.ly = 1.0;
+  }
+  h->ncells = pl.ncells;
+  h->det = pl.det;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->ws = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(dev_workspace) + 255) & ~(uintptr_t)255);
+  h->ws_bytes = bytes;
+  make_plan(&h->cfg, h->ws, h);
+  fill_params<double>(&h->cfg, h->pd, h->cp);
+  fill_params<float>(&h->cfg, h->pf, h->cp);
+  int r;
+  if (h->det) {
+    Ops<double>::configure(pl.tile);
+    r = init_state<double>(h, h->sd, h->pd);
+  } else {
+    Ops<float>::configure(pl.tile);
+    r = init_state<float>(h, h->sf, h->pf);
+  }
+  if (r) {
+    const int code = r;
+    delete h;
+    return code;
+  }
+  *out = h;
+  return DSMC_OK;
+}
+
+int dsmc_destroy(dsmc_handle* h) {
+  delete h;
+  return DSMC_OK;
+}
+
+const char* dsmc_last_error(const dsmc_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+int dsmc_step(dsmc_handle* h, int nsteps, int sample) {
+  if (!h || nsteps < 0) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (nsteps == 0) return DSMC_OK;
+  if (h->det) {
+    for (int k = 0; k < nsteps; ++k) {
+      Ops<double>::step_det(h->pd, h->sd, h->cur, h->lay, h->step, sample, h->stream);
+      h->step += 1;
+      if (sample) h->nsamples += 1;
+    }
+    return check_cuda(h, "dsmc_step");
+  }
+  Ops<float>::step_bins(h->pf, h->sf, h->cur, h->lay, h->step, nsteps, sample, h->stream);
+  h->step += (uint32_t)nsteps;
+  if (sample) h->nsamples += nsteps;
+  int r = check_cuda(h, "dsmc_step");
+  if (r) return r;
+  // rebuild the bins if a particle overflowed or a bin came near its capacity
+  int32_t ovf = 0;
+  unsigned long long nearfull = 0;
+  cudaMemcpyAsync(&ovf, h->sf.ovf[h->cur].count, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(&nearfull, h->sf.stats + ST_NEARFULL, sizeof(nearfull), cudaMemcpyDeviceToHost, h->stream);
+  r = sync_check(h, "dsmc_step (bin check)");
+  if (r) return r;
+  if (ovf > 0 || nearfull > 0) {
+    Ops<float>::rebin(h->pf, h->sf, h->cur, h->lay, 1, h->sf.slack, h->stream);
+    cudaMemsetAsync(h->sf.stats + ST_NEARFULL, 0, sizeof(unsigned long long), h->stream);
+    int32_t fl[4] = {0, 0, 0, 0};
+    cudaMemcpyAsync(fl, h->sf.flags, sizeof fl, cudaMemcpyDeviceToHost, h->stream);
+    r = sync_check(h, "dsmc_step (rebin)");
+    if (r) return r;
+    h->rebuilds += 1;
+    if (fl[2]) return set_err(h, DSMC_ERR_CAPACITY, "cell bins do not fit the capacity");
+  }
+  return DSMC_OK;
+}
+
+int dsmc_sample(dsmc_handle* h, double* dev_fields, int reset) {
+  if (!h || !dev_fields) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  const double* acc = h->det ? h->sd.acc : h->sf.acc;
+  double* comp = h->det ? h->sd.comp : h->sf.comp;
+  launch_fields(h->cp, acc, comp, h->nsamples, dev_fields, h->stream);
+  if (reset) {
+    cudaMemsetAsync(const_cast<double*>(acc), 0, sizeof(double) * h->ncells * NMOM, h->stream);
+    cudaMemsetAsync(comp, 0, sizeof(double) * h->ncells * NMOM, h->stream);
+    h->nsamples = 0;
+  }
+  return check_cuda(h, "dsmc_sample");
+}
+
+int dsmc_hot(dsmc_handle* h, const double* dev_fields, double* dev_hot, double* dev_kngll, uint8_t* dev_mask) {
+  if (!h || !dev_fields || !dev_hot) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  launch_hot(h->cp, dev_fields, dev_hot, dev_kngll, dev_mask, h->stream);
+  return check_cuda(h, "dsmc_hot");
+}
+
+int synth_solve(dsmc_handle* h, const double* dev_fields, const double* dev_hot, double* dev_out, int* host_iters,
+                double* host_resid) {
+  if (!h || !dev_fields || !dev_hot || !dev_out) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (h->cfg.dim != 1) return set_err(h, DSMC_ERR_ARG, "synth_solve: only the 1D slab is implemented");
+  if (h->ncells < 3) return set_err(h, DSMC_ERR_ARG, "synth_solve needs at least 3 cells");
+  const int n_m = h->cfg.n_m > 0 ? h->cfg.n_m : 2000;
+  const double tol = h->cfg.synth_tol > 0 ? h->cfg.synth_tol : 1e-5;
+  launch_synth1d(h->cp, dev_fields, dev_hot, dev_out, h->synth_work, n_m, tol, h->synth_info, h->stream);
+  double info[3] = {0, 0, 0};
+  cudaMemcpyAsync(info, h->synth_info, sizeof info, cudaMemcpyDeviceToHost, h->stream);
+  const int r = sync_check(h, "synth_solve");
+  if (r) return r;
+  if (host_iters) *host_iters = (int)info[0];
+  if (host_resid) *host_resid = info[1];
+  if (info[2] == 2.0) return set_err(h, DSMC_ERR_NUMERIC, "synth_solve: no update keeps rho, T positive");
+  if (info[2] == 1.0) return set_err(h, DSMC_ERR_NOT_CONVERGED, "synth_solve: %d iterations without convergence", n_m);
+  return DSMC_OK;
+}
+
+int dig_correct(dsmc_handle* h, const double* dev_target) {
+  if (!h || !dev_target) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  int32_t fl[4] = {0, 0, 0, 0};
+  if (h->det) Ops<double>::dig_counts(h->cp, h->sd, h->lay, dev_target, h->dig_iter, 1, h->stream);
+  else Ops<float>::dig_counts(h->cp, h->sf, h->lay, dev_target, h->dig_iter, 0, h->stream);
+  int32_t* flags = h->det ? h->sd.flags : h->sf.flags;
+  cudaMemcpyAsync(fl, flags, sizeof fl, cudaMemcpyDeviceToHost, h->stream);
+  int r = sync_check(h, "dig_correct (counts)");
+  if (r) return r;
+  if (fl[0] & 1) return set_err(h, DSMC_ERR_NUMERIC, "dig_correct: non-finite or non-positive target");
+  if (fl[0] & 6) return set_err(h, DSMC_ERR_CAPACITY, "dig_correct: new particle count does not fit");
+  if (h->det) {
+    Ops<double>::dig_apply(h->cp, h->sd, h->cur, h->lay, dev_target, h->dig_iter, 1, h->stream);
+    h->sd.nparticles = fl[1];
+  } else {
+    Ops<float>::dig_apply(h->cp, h->sf, h->cur, h->lay, dev_target, h->dig_iter, 0, h->stream);
+    h->sf.nparticles = fl[3];
+  }
+  h->dig_iter += 1;
+  return check_cuda(h, "dig_correct");
+}
+
+int dsmc_num_particles(dsmc_handle* h, int64_t* host_n) {
+  if (!h || !host_n) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  int32_t* cnt = h->det ? h->sd.count[h->lay] : h->sf.count[h->cur];
+  int32_t* tmp = h->det ? h->sd.tmp_start : h->sf.tmp_start;
+  if (h->det) Ops<double>::total_count(h->sd, cnt, h->ncells, h->stream);
+  else Ops<float>::total_count(h->sf, cnt, h->ncells, h->stream);
+  int32_t tot = 0, ov = 0;
+  cudaMemcpyAsync(&tot, tmp + h->ncells, sizeof tot, cudaMemcpyDeviceToHost, h->stream);
+  if (!h->det) cudaMemcpyAsync(&ov, h->sf.ovf[h->cur].count, sizeof ov, cudaMemcpyDeviceToHost, h->stream);
+  const int r = sync_check(h, "dsmc_num_particles");
+  if (r) return r;
+  *host_n = (int64_t)tot + (ov < h->sf.ovf_cap || h->det ? ov : h->sf.ovf_cap);
+  return DSMC_OK;
+}
+
+int dsmc_get_particles(dsmc_handle* h, double* x, double* y, double* vx, double* vy, double* vz, double* ir,
+                       int32_t* cell, int64_t capacity_out, int64_t* host_n) {
+  if (!h || !x || !y || !vx || !vy || !vz || !ir || !cell) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  int64_t n = 0;
+  int r = dsmc_num_particles(h, &n);
+  if (r) return r;
+  if (host_n) *host_n = n;
+  if (n > capacity_out) return set_err(h, DSMC_ERR_CAPACITY, "output holds %lld, need %lld", (long long)capacity_out, (long long)n);
+  if (h->det) Ops<double>::export_particles(h->pd, h->sd, h->cur, h->lay, x, y, vx, vy, vz, ir, cell, h->stream);
+  else Ops<float>::export_particles(h->pf, h->sf, h->cur, h->lay, x, y, vx, vy, vz, ir, cell, h->stream);
+  return check_cuda(h, "dsmc_get_particles");
+}
+
+int dsmc_set_particles(dsmc_handle* h, int64_t n, const double* x, const double* y, const double* vx,
+                       const double* vy, const double* vz, const double* ir) {
+  if (!h || n < 0 || (n > 0 && (!x || !vx || !vy || !vz || !ir || (h->cfg.dim == 2 && !y))))
+    return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  const int64_t cap = h->det ? h->sd.capacity : h->sf.capacity;
+  if (n > cap) return set_err(h, DSMC_ERR_CAPACITY, "%lld particles exceed capacity %lld", (long long)n, (long long)cap);
+  int32_t* flags = h->det ? h->sd.flags : h->sf.flags;
+  cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, h->stream);
+  if (h->det) Ops<double>::import_particles(h->pd, h->sd, h->cur, h->lay, n, x, y, vx, vy, vz, ir, 1, h->stream);
+  else Ops<float>::import_particles(h->pf, h->sf, h->cur, h->lay, n, x, y, vx, vy, vz, ir, 0, h->stream);
+  int32_t fl[4] = {0, 0, 0, 0};
+  cudaMemcpyAsync(fl, flags, sizeof fl, cudaMemcpyDeviceToHost, h->stream);
+  const int r = sync_check(h, "dsmc_set_particles");
+  if (r) return r;
+  if (fl[2]) return set_err(h, DSMC_ERR_CAPACITY, "cell bins do not fit the capacity");
+  return DSMC_OK;
+}
+
+int dsmc_get_accumulators(dsmc_handle* h, double* dev_out, int64_t* host_nsamples) {
+  if (!h || !dev_out) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (h->det) launch_acc_sum(h->ncells, h->sd.acc, h->sd.comp, dev_out, h->stream);
+  else launch_acc_sum(h->ncells, h->sf.acc, h->sf.comp, dev_out, h->stream);
+  if (host_nsamples) *host_nsamples = h->nsamples;
+  return check_cuda(h, "dsmc_get_accumulators");
+}
+
+int dsmc_get_sgmax(dsmc_handle* h, double* dev_out) {
+  if (!h || !dev_out) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (h->det) Ops<double>::sgmax_io(h->sd, h->ncells, dev_out, nullptr, h->stream);
+  else Ops<float>::sgmax_io(h->sf, h->ncells, dev_out, nullptr, h->stream);
+  return check_cuda(h, "dsmc_get_sgmax");
+}
+
+int dsmc_set_sgmax(dsmc_handle* h, const double* dev_in) {
+  if (!h || !dev_in) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (h->det) Ops<double>::sgmax_io(h->sd, h->ncells, nullptr, dev_in, h->stream);
+  else Ops<float>::sgmax_io(h->sf, h->ncells, nullptr, dev_in, h->stream);
+  return check_cuda(h, "dsmc_set_sgmax");
+}
+
+int dsmc_get_counters(dsmc_handle* h, uint32_t* host_step, uint32_t* host_dig_iter) {
+  if (!h) return DSMC_ERR_ARG;
+  if (host_step) *host_step = h->step;
+  if (host_dig_iter) *host_dig_iter = h->dig_iter;
+  return DSMC_OK;
+}
+
+int dsmc_set_counters(dsmc_handle* h, uint32_t step, uint32_t dig_iter) {
+  if (!h) return DSMC_ERR_ARG;
+  h->step = step;
+  h->dig_iter = dig_iter;
+  return DSMC_OK;
+}
+
+int dsmc_get_stats(dsmc_handle* h, int64_t* out8) {
+  if (!h || !out8) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  unsigned long long s[ST_NSLOTS];
+  cudaMemcpyAsync(s, h->det ? h->sd.stats : h->sf.stats, sizeof s, cudaMemcpyDeviceToHost, h->stream);
+  const int r = sync_check(h, "dsmc_get_stats");
+  if (r) return r;
+  out8[0] = (int64_t)s[ST_CAND];
+  out8[1] = (int64_t)s[ST_COLL];
+  out8[2] = (int64_t)s[ST_CLIP];
+  out8[3] = (int64_t)s[ST_INEL];
+  out8[4] = (int64_t)s[ST_HITS];
+  out8[5] = (int64_t)s[ST_MAXHIT];
+  out8[6] = (int64_t)s[ST_OVF];
+  out8[7] = h->rebuilds;
+  return DSMC_OK;
+}
+
+int dsmc_get_wall_tally(dsmc_handle* h, double* out20) {
+  if (!h || !out20) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  cudaMemcpyAsync(out20, h->det ? h->sd.tally : h->sf.tally, sizeof(double) * 20, cudaMemcpyDeviceToHost, h->stream);
+  return sync_check(h, "dsmc_get_wall_tally");
+}
+
+int dsmc_get_constants(dsmc_handle* h, double* out8) {
+  if (!h || !out8) return DSMC_ERR_ARG;
+  Params<double> p;
+  CellParams cp;
+  fill_params<double>(&h->cfg, p, cp);
+  const double w = h->cfg.omega, a = h->cfg.alpha;
+  out8[0] = cp.dx;
+  out8[1] = cp.dy;
+  out8[2] = cp.vcell;
+  out8[3] = cp.fnum;
+  out8[4] = cp.mu_ref;
+  out8[5] = 5.0 * (a + 1.0) * (a + 2.0) / (a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w));
+  out8[6] = p.c_sigma;
+  out8[7] = p.p_inel;
+  return DSMC_OK;
+}
+
+}  // extern "C"

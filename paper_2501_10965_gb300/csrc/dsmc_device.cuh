@@ -1,0 +1,495 @@
+// dsmc_device.cuh -- device building blocks of the DSMC step (sm_103a).
+//
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
+// the 64-bit seed, counter = (c0, c1, c2, tag << 24 | block).  A stream is a
+// (tag, c0, c1, c2) tuple; its uniform number j lives in block j / P, where
+// P = 2 in FP64 (two words per uniform: the top 52 bits of (w_hi, w_lo),
+// u = (m + 1/2) 2^-52) and P = 4 in FP32 (u = (w >> 9 + 1/2) 2^-23).  Both
+// lie strictly inside (0, 1).  Streams used by the step:
+//   TAG_INIT  (k, cell, 0)      initial particle k of a cell
+//   TAG_WALL  (k, cell, step)   wall hits of the k-th particle of a cell
+//   TAG_NTC   (0, cell, step)   Iround of the candidate-pair count
+//   TAG_COLL  (m, cell, step)   candidate pair m of a cell
+//   TAG_DIG_* (q, cell, iter)   particle modification, always FP64 layout
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dsmc {
+
+constexpr uint32_t TAG_INIT = 1u, TAG_WALL = 2u, TAG_NTC = 3u, TAG_COLL = 4u;
+constexpr uint32_t TAG_DIG_N = 5u, TAG_DIG_SEL = 6u, TAG_DIG_POS = 7u;
+constexpr int MAX_HITS = 8;
+constexpr int NMOM = 17;
+constexpr uint32_t OWNER_FREE = 0xFFFFFFFFu;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr double PI_D = 3.141592653589793;
+
+// Simulation constants in the particle precision T.
+template <typename T>
+struct Params {
+  int dim, nx, ny, ncells;
+  T lx, ly, dx, dy, sx, sy;  // sx = nx / lx, sy = ny / ly
+  T vcell, fnum, dt;
+  T c_sigma, p_inel, vhs_e, bl_exp;  // vhs_e = 2 - 2 omega, bl_exp = 1/(5/2 - omega)
+  int collisions;
+  int wall_kind[4];
+  T wall_t[4];
+  T wall_u[4][3];
+  uint32_t k0, k1;
+};
+
+// Per-step device counters (unsigned long long so they can be added atomically).
+enum StatSlot {
+  ST_CAND = 0, ST_COLL = 1, ST_CLIP = 2, ST_INEL = 3, ST_HITS = 4, ST_MAXHIT = 5, ST_OVF = 6,
+  ST_REBIN = 7, ST_NEARFULL = 8, ST_NSLOTS = 16
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ double u01_from_words(uint32_t hi, uint32_t lo) {
+  const unsigned long long m = ((unsigned long long)hi << 20) | (unsigned long long)(lo >> 12);
+  return ((double)m + 0.5) * 0x1p-52;
+}
+
+__device__ __forceinline__ float u01_from_word(uint32_t w) {
+  return ((float)(w >> 9) + 0.5f) * 0x1p-23f;
+}
+
+template <typename T>
+struct Stream;
+
+template <>
+struct Stream<double> {
+  uint32_t c0, c1, c2, tag, k0, k1;
+  int blk;
+  uint4 w;
+  __device__ Stream(uint32_t tag_, uint32_t c0_, uint32_t c1_, uint32_t c2_, uint32_t k0_, uint32_t k1_)
+      : c0(c0_), c1(c1_), c2(c2_), tag(tag_ << 24), k0(k0_), k1(k1_), blk(-1) {}
+  __device__ __forceinline__ double u(uint32_t j) {
+    const uint32_t b = j >> 1;
+    if ((int)b != blk) {
+      w = philox4x32_10(c0, c1, c2, tag | b, k0, k1);
+      blk = (int)b;
+    }
+    return (j & 1u) ? u01_from_words(w.z, w.w) : u01_from_words(w.x, w.y);
+  }
+};
+
+template <>
+struct Stream<float> {
+  uint32_t c0, c1, c2, tag, k0, k1;
+  int blk;
+  uint4 w;
+  __device__ Stream(uint32_t tag_, uint32_t c0_, uint32_t c1_, uint32_t c2_, uint32_t k0_, uint32_t k1_)
+      : c0(c0_), c1(c1_), c2(c2_), tag(tag_ << 24), k0(k0_), k1(k1_), blk(-1) {}
+  __device__ __forceinline__ float u(uint32_t j) {
+    const uint32_t b = j >> 2;
+    if ((int)b != blk) {
+      w = philox4x32_10(c0, c1, c2, tag | b, k0, k1);
+      blk = (int)b;
+    }
+    const uint32_t s = j & 3u;
+    const uint32_t word = s == 0 ? w.x : (s == 1 ? w.y : (s == 2 ? w.z : w.w));
+    return u01_from_word(word);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Precision-dispatched math.  FP64 calls the CUDA double functions (the
+// oracle calls the C library ones; both are within a few ulp).  FP32 uses the
+// hardware approximations where the error is far below the statistical noise.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_log(float x) { return __logf(x); }
+__device__ __forceinline__ double m_pow(double x, double e) { return pow(x, e); }
+__device__ __forceinline__ float m_pow(float x, float e) {
+  // x >= 0; exp2(e log2 x) with log2(0) = -inf giving 0 for e > 0
+  return exp2f(e * __log2f(x));
+}
+__device__ __forceinline__ void m_sincos_2pi(double u, double* s, double* c) {
+  const double th = 2.0 * PI_D * u;
+  *c = cos(th);
+  *s = sin(th);
+}
+__device__ __forceinline__ void m_sincos_2pi(float u, float* s, float* c) {
+  sincospif(2.0f * u, s, c);
+}
+__device__ __forceinline__ double m_floor(double x) { return floor(x); }
+__device__ __forceinline__ float m_floor(float x) { return floorf(x); }
+
+template <typename T>
+__device__ __forceinline__ void box_muller(T ua, T ub, T* n1, T* n2) {
+  const T r = m_sqrt(T(-2) * m_log(ua));
+  T s, c;
+  m_sincos_2pi(ub, &s, &c);
+  *n1 = r * c;
+  *n2 = r * s;
+}
+
+// Iround of Sec. 3.2 step i: floor(x) + 1 with probability x - floor(x).
+template <typename T>
+__device__ __forceinline__ long long iround(T x, T u) {
+  const T f = m_floor(x);
+  return (long long)f + ((u < x - f) ? 1 : 0);
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ int cell_of(const Params<T>& p, T x, T y) {
+  int ix = (int)(x * p.sx);
+  ix = ix < 0 ? 0 : (ix > p.nx - 1 ? p.nx - 1 : ix);
+  if (DIM == 1) return ix;
+  int iy = (int)(y * p.sy);
+  iy = iy < 0 ? 0 : (iy > p.ny - 1 ? p.ny - 1 : iy);
+  return iy * p.nx + ix;
+}
+
+// ---------------------------------------------------------------------------
+// Stage (a): free flight with wall interaction (Sec. 2.2; fully diffuse
+// walls of Sec. 4).  A diffuse wall re-emits with normal speed
+// sqrt(-2 T_w ln u) (flux-weighted half-range Maxwellian), Maxwellian
+// tangential components about the wall velocity and a rotational energy drawn
+// at T_w; the particle then flies the rest of the step; at most MAX_HITS hits.
+// tally[w*5 + q]: hits, momentum (3) and energy delivered to wall w.
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__device__ void fly(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& ir, uint32_t idx,
+                    uint32_t cell, uint32_t step, T* tally, unsigned long long* hits_out,
+                    unsigned long long* maxhit_out) {
+  T t = p.dt;
+  int hits = 0;
+  Stream<T> st(TAG_WALL, idx, cell, step, p.k0, p.k1);
+  for (;;) {
+    const T xn = x + vx * t;
+    const T yn = (DIM == 2) ? y + vy * t : y;
+    T tx = T(0), ty = T(0);
+    int wx = -1, wy = -1;
+    if (xn < T(0)) {
+      tx = -x / vx;
+      wx = 0;
+    } else if (xn > p.lx) {
+      tx = (p.lx - x) / vx;
+      wx = 1;
+    }
+    if (DIM == 2) {
+      if (yn < T(0)) {
+        ty = -y / vy;
+        wy = 2;
+      } else if (yn > p.ly) {
+        ty = (p.ly - y) / vy;
+        wy = 3;
+      }
+    }
+    if (wx < 0 && wy < 0) {
+      x = xn;
+      y = yn;
+      break;
+    }
+    int w;
+    T tw;
+    if (wy < 0 || (wx >= 0 && tx <= ty)) {
+      w = wx;
+      tw = tx;
+    } else {
+      w = wy;
+      tw = ty;
+    }
+    if (w < 2) {
+      x = (w == 0) ? T(0) : p.lx;
+      if (DIM == 2) {
+        y = y + vy * tw;
+        if (y < T(0)) y = T(0);
+        if (y > p.ly) y = p.ly;
+      }
+    } else {
+      y = (w == 2) ? T(0) : p.ly;
+      x = x + vx * tw;
+      if (x < T(0)) x = T(0);
+      if (x > p.lx) x = p.lx;
+    }
+    if (hits == MAX_HITS) {
+      atomicAdd(maxhit_out, 1ull);
+      break;
+    }
+    t = t - tw;
+    if (t < T(0)) t = T(0);
+    // re-emission
+    const T vix = vx, viy = vy, viz = vz, iri = ir;
+    const int axis = (w < 2) ? 0 : 1;
+    const T sgn = (w % 2 == 0) ? T(1) : T(-1);
+    if (p.wall_kind[w] == 1) {
+      if (axis == 0) vx = -vx;
+      else vy = -vy;
+    } else {
+      const T Tw = p.wall_t[w];
+      const T ua = st.u(4 * hits + 0), ub = st.u(4 * hits + 1);
+      const T uc = st.u(4 * hits + 2), ud = st.u(4 * hits + 3);
+      const T vn = m_sqrt(T(-2) * Tw * m_log(ua));
+      T n1, n2;
+      box_muller(ub, uc, &n1, &n2);
+      const T sT = m_sqrt(Tw);
+      if (axis == 0) {
+        vx = sgn * vn;
+        vy = p.wall_u[w][1] + sT * n1;
+        vz = p.wall_u[w][2] + sT * n2;
+      } else {
+        vx = p.wall_u[w][0] + sT * n1;
+        vy = sgn * vn;
+        vz = p.wall_u[w][2] + sT * n2;
+      }
+      ir = -Tw * m_log(ud);
+    }
+    T* tl = tally + 5 * w;
+    atomicAdd(tl + 0, T(1));
+    atomicAdd(tl + 1, vix - vx);
+    atomicAdd(tl + 2, viy - vy);
+    atomicAdd(tl + 3, viz - vz);
+    atomicAdd(tl + 4, (T(0.5) * (vix * vix + viy * viy + viz * viz) + iri) -
+                          (T(0.5) * (vx * vx + vy * vy + vz * vz) + ir));
+    hits += 1;
+  }
+  if (hits) atomicAdd(hits_out, (unsigned long long)hits);
+}
+
+// ---------------------------------------------------------------------------
+// Stage (c): NTC / VHS / Borgnakke-Larsen for one cell, one warp.
+//
+// The candidate pairs m = 0 .. M-1 are those of the sequential algorithm
+// (Sec. 2.2): pick i, then j != i, accept with sigma g / (sigma g)_max, then
+// Borgnakke-Larsen for i and for j (each with probability P_inelastic, Bird's
+// particle selection permitting double relaxation) and isotropic scattering.
+// (sigma g)_max is frozen during the step, so the only coupling between
+// candidates is through shared particles.  The warp keeps a window of the
+// (up to) 32 earliest unprocessed candidates; a candidate runs once no
+// earlier unprocessed candidate uses either of its particles (it owns both:
+// owner[] holds the smallest claiming index).  Candidates that run together
+// touch disjoint particles, and every candidate sees exactly the particle
+// state the sequential loop would give it, so the result is the sequential
+// one, pair for pair.
+// ---------------------------------------------------------------------------
+struct CollCount {
+  unsigned cand, coll, clip, inel;
+};
+
+template <typename T>
+struct PairDraw;
+
+template <>
+struct PairDraw<float> {
+  // FP32: block 0 = (u0, u1, u2, u3), block 1 = (u4..u7), block 2 = (u8, ...)
+  __device__ static void first(Stream<float>& st, float& u0, float& u1, float& u2, float& u3) {
+    u0 = st.u(0);
+    u1 = st.u(1);
+    u2 = st.u(2);
+    u3 = st.u(3);
+  }
+};
+
+template <>
+struct PairDraw<double> {
+  __device__ static void first(Stream<double>& st, double& u0, double& u1, double& u2, double& u3) {
+    u0 = st.u(0);
+    u1 = st.u(1);
+    u2 = st.u(2);
+    u3 = st.u(3);
+  }
+};
+
+template <typename T>
+__device__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restrict__ vy,
+                             T* __restrict__ vz, T* __restrict__ ir, int n, uint32_t cell,
+                             uint32_t step, T* sgmax_ptr, uint32_t* owner, CollCount& cc) {
+  const int lane = threadIdx.x & 31;
+  if (!p.collisions || n < 2) return;
+  const T sgmax = *sgmax_ptr;
+  const T xm = T(0.5) * T(n) * T(n - 1) * p.fnum * sgmax * p.dt / p.vcell;
+  Stream<T> sn(TAG_NTC, 0u, cell, step, p.k0, p.k1);
+  const long long Mll = iround(xm, sn.u(0));
+  const uint32_t M = (uint32_t)(Mll < 0 ? 0 : Mll);
+  if (M == 0) return;
+  for (int q = lane; q < n; q += 32) owner[q] = OWNER_FREE;
+  __syncwarp();
+  T obs = T(0);
+  uint32_t next = 0;
+  bool has = false;
+  uint32_t k = 0;
+  int pi = 0, pj = 0;
+  T uacc = T(0), uinel = T(0);
+  const T fn = T(n), fn1 = T(n - 1);
+  for (;;) {
+    const int np = __popc(__ballot_sync(FULL, has));
+    if (!has) {
+      const uint32_t kk = next + (uint32_t)(lane - np);
+      if (kk < M) {
+        Stream<T> st(TAG_COLL, kk, cell, step, p.k0, p.k1);
+        T u0, u1;
+        PairDraw<T>::first(st, u0, u1, uacc, uinel);
+        int i = (int)(u0 * fn);
+        if (i > n - 1) i = n - 1;
+        int j = (int)(u1 * fn1);
+        if (j > n - 2) j = n - 2;
+        if (j >= i) j += 1;
+        pi = i;
+        pj = j;
+        k = kk;
+        has = true;
+      }
+    }
+    {
+      const uint32_t room = (uint32_t)(32 - np);
+      next = (M - next > room) ? next + room : M;
+    }
+    if (__ballot_sync(FULL, has) == 0u) break;
+    if (has) {
+      atomicMin(&owner[pi], k);
+      atomicMin(&owner[pj], k);
+    }
+    __syncwarp();
+    const bool ready = has && owner[pi] == k && owner[pj] == k;
+    __syncwarp();
+    if (has) {
+      owner[pi] = OWNER_FREE;
+      owner[pj] = OWNER_FREE;
+    }
+    __syncwarp();
+    if (ready) {
+      const T gx = vx[pi] - vx[pj];
+      const T gy = vy[pi] - vy[pj];
+      const T gz = vz[pi] - vz[pj];
+      const T g2 = gx * gx + gy * gy + gz * gz;
+      const T g = m_sqrt(g2);
+      const T sg = p.c_sigma * m_pow(g, p.vhs_e);
+      if (sg > obs) obs = sg;
+      cc.cand += 1;
+      if (uacc * sgmax < sg) {
+        cc.coll += 1;
+        if (sg > sgmax) cc.clip += 1;
+        Stream<T> st(TAG_COLL, k, cell, step, p.k0, p.k1);
+        T et = T(0.25) * g2;
+        if (uinel < p.p_inel) {
+          const T ec = et + ir[pi];
+          ir[pi] = ec * (T(1) - m_pow(st.u(4), p.bl_exp));
+          et = ec - ir[pi];
+          cc.inel += 1;
+        }
+        if (st.u(5) < p.p_inel) {
+          const T ec = et + ir[pj];
+          ir[pj] = ec * (T(1) - m_pow(st.u(6), p.bl_exp));
+          et = ec - ir[pj];
+          cc.inel += 1;
+        }
+        const T gn = T(2) * m_sqrt(et);
+        const T cth = T(2) * st.u(7) - T(1);
+        const T sth = m_sqrt(T(1) - cth * cth);
+        T sph, cph;
+        m_sincos_2pi(st.u(8), &sph, &cph);
+        const T hx = T(0.5) * gn * cth;
+        const T hy = T(0.5) * gn * sth * cph;
+        const T hz = T(0.5) * gn * sth * sph;
+        const T cx = T(0.5) * (vx[pi] + vx[pj]);
+        const T cy = T(0.5) * (vy[pi] + vy[pj]);
+        const T cz = T(0.5) * (vz[pi] + vz[pj]);
+        vx[pi] = cx + hx;
+        vy[pi] = cy + hy;
+        vz[pi] = cz + hz;
+        vx[pj] = cx - hx;
+        vy[pj] = cy - hy;
+        vz[pj] = cz - hz;
+      }
+    }
+    __syncwarp();
+    const unsigned rem = __ballot_sync(FULL, has && !ready);
+    const int nr = __popc(rem);
+    const int src = (lane < nr) ? (int)__fns(rem, 0u, lane + 1) : lane;
+    k = __shfl_sync(FULL, k, src);
+    pi = __shfl_sync(FULL, pi, src);
+    pj = __shfl_sync(FULL, pj, src);
+    uacc = __shfl_sync(FULL, uacc, src);
+    uinel = __shfl_sync(FULL, uinel, src);
+    has = lane < nr;
+  }
+  // (sigma g)_max takes the largest sigma g seen in the step
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T other = __shfl_xor_sync(FULL, obs, o);
+    obs = other > obs ? other : obs;
+  }
+  __syncwarp();
+  if (lane == 0 && obs > sgmax) *sgmax_ptr = obs;
+}
+
+// ---------------------------------------------------------------------------
+// Stage (d): raw sums of one cell for Eq. (DSMC_macroscopic), added to
+// Neumaier-compensated FP64 accumulators (acc, comp: 17 per cell).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void sample_cell(const T* __restrict__ vx, const T* __restrict__ vy,
+                            const T* __restrict__ vz, const T* __restrict__ ir, int n,
+                            double* __restrict__ acc, double* __restrict__ comp) {
+  const int lane = threadIdx.x & 31;
+  T s[NMOM];
+#pragma unroll
+  for (int q = 0; q < NMOM; ++q) s[q] = T(0);
+  for (int q = lane; q < n; q += 32) {
+    const T a = vx[q], b = vy[q], c = vz[q], e = ir[q];
+    const T v2 = a * a + b * b + c * c;
+    s[0] += T(1);
+    s[1] += a;
+    s[2] += b;
+    s[3] += c;
+    s[4] += a * a;
+    s[5] += b * b;
+    s[6] += c * c;
+    s[7] += a * b;
+    s[8] += a * c;
+    s[9] += b * c;
+    s[10] += a * v2;
+    s[11] += b * v2;
+    s[12] += c * v2;
+    s[13] += e;
+    s[14] += e * a;
+    s[15] += e * b;
+    s[16] += e * c;
+  }
+#pragma unroll
+  for (int q = 0; q < NMOM; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(FULL, s[q], o);
+  }
+  T mine = T(0);
+#pragma unroll
+  for (int q = 0; q < NMOM; ++q)
+    if (lane == q) mine = s[q];
+  if (lane < NMOM) {
+    const double v = (double)mine;
+    const double a = acc[lane];
+    const double t = a + v;
+    const double cmp = (fabs(a) >= fabs(v)) ? ((a - t) + v) : ((v - t) + a);
+    acc[lane] = t;
+    comp[lane] += cmp;
+  }
+}
+
+}  // namespace dsmc

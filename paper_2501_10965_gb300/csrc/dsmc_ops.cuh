@@ -1,0 +1,985 @@
+// dsmc_ops.cuh -- kernels of the DSMC step and of the particle modification,
+// templated on the particle precision T and the dimension DIM, and their
+// launch wrappers.  Included by one translation unit per precision.
+//
+// Two particle layouts:
+//  * FP64-deterministic: compact, cell-sorted arrays; each step runs
+//    move (one thread per particle) -> stable counting sort (one CTA) ->
+//    collide + sample (one warp per cell).  The event order equals the
+//    sequential definition, so results match a sequential implementation.
+//  * FP32: each cell owns a padded bin; one fused kernel per step runs, per
+//    cell (one warp): stage the cell in shared memory, collide, sample, move,
+//    and append each particle to its new cell's bin in the other buffer
+//    (warp-aggregated atomics).  Particles read once and written once per step.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dsmc_device.cuh"
+#include "dsmc_internal.h"
+
+namespace dsmc {
+
+constexpr int WPB = 8;  // warps per CTA for the per-cell kernels
+constexpr int CTA_SCAN = 1024;
+
+// ---------------------------------------------------------------------------
+// single-CTA exclusive scan: out[i] = sum_{k<i} value(k), out[n] = total
+// ---------------------------------------------------------------------------
+template <typename F>
+__device__ void cta_exclusive_scan(int n, F value, int32_t* out) {
+  __shared__ int32_t wsum[32];
+  __shared__ int32_t carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int32_t v = (i < n) ? value(i) : 0;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int32_t w = (lane < nw) ? wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(FULL, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    const int32_t excl = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - v;
+    if (i < n) out[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+  __syncthreads();
+}
+
+__device__ __forceinline__ int32_t bin_cap_of(int32_t count, double slack) {
+  const int32_t c = (int32_t)ceil(slack * (double)count) + 32;
+  return (c + 7) & ~7;
+}
+
+// ---------------------------------------------------------------------------
+// initial equilibrium state (Sec. 3 step 1)
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void k_init(Params<T> p, PBuf<T> b, const int32_t* __restrict__ start,
+                       int32_t* __restrict__ count, int32_t* __restrict__ cellof, int ppc, T tt,
+                       T tr, T u0x, T u0y, T u0z) {
+  const long long total = (long long)p.ncells * ppc;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < total;
+       s += (long long)gridDim.x * blockDim.x) {
+    const int cell = (int)(s / ppc), k = (int)(s % ppc);
+    const int ix = cell % p.nx, iy = cell / p.nx;
+    Stream<T> st(TAG_INIT, (uint32_t)k, (uint32_t)cell, 0u, p.k0, p.k1);
+    const T a0 = st.u(0), a1 = st.u(1);
+    T n1, n2, n3, n4;
+    box_muller(st.u(2), st.u(3), &n1, &n2);
+    box_muller(st.u(4), st.u(5), &n3, &n4);
+    const T stt = m_sqrt(tt);
+    const int slot = start[cell] + k;
+    b.x[slot] = ((T)ix + a0) * p.dx;
+    b.y[slot] = (DIM == 2) ? ((T)iy + a1) * p.dy : T(0);
+    b.vx[slot] = u0x + stt * n1;
+    b.vy[slot] = u0y + stt * n2;
+    b.vz[slot] = u0z + stt * n3;
+    b.ir[slot] = -tr * m_log(st.u(6));
+    if (cellof) cellof[slot] = cell;
+    if (k == 0) count[cell] = ppc;
+  }
+}
+
+static __global__ void k_layout_uniform(int ncells, int32_t cap, int32_t* start) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= ncells; c += gridDim.x * blockDim.x)
+    start[c] = c * cap;
+}
+
+// ---------------------------------------------------------------------------
+// FP64-deterministic layout: move, stable sort, collide + sample
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_move_det(Params<T> p, PBuf<T> b, const int32_t* __restrict__ cellof,
+                                                  const int32_t* __restrict__ start, int n,
+                                                  uint32_t step, int32_t* __restrict__ key,
+                                                  double* __restrict__ tally_g,
+                                                  unsigned long long* __restrict__ stats) {
+  __shared__ T s_tally[20];
+  if (threadIdx.x < 20) s_tally[threadIdx.x] = T(0);
+  __syncthreads();
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const int c = cellof[s];
+    T x = b.x[s], y = b.y[s], vx = b.vx[s], vy = b.vy[s], vz = b.vz[s], ir = b.ir[s];
+    fly<T, DIM>(p, x, y, vx, vy, vz, ir, (uint32_t)(s - start[c]), (uint32_t)c, step, s_tally,
+                stats + ST_HITS, stats + ST_MAXHIT);
+    b.x[s] = x;
+    b.y[s] = y;
+    b.vx[s] = vx;
+    b.vy[s] = vy;
+    b.vz[s] = vz;
+    b.ir[s] = ir;
+    key[s] = cell_of<T, DIM>(p, x, y);
+  }
+  __syncthreads();
+  if (threadIdx.x < 20 && s_tally[threadIdx.x] != T(0))
+    atomicAdd(tally_g + threadIdx.x, (double)s_tally[threadIdx.x]);
+}
+
+// Stable counting sort by key (one CTA of 1024 threads): histogram, scan,
+// then one warp assigns destinations 32 slots at a time in slot order (ties
+// keep their order), then every thread scatters.  Tin -> Tout conversion.
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(1024) k_sort_stable(const Tin* __restrict__ ix, const Tin* __restrict__ iy,
+                                                      const Tin* __restrict__ ivx, const Tin* __restrict__ ivy,
+                                                      const Tin* __restrict__ ivz, const Tin* __restrict__ iir,
+                                                      PBuf<Tout> o, const int32_t* __restrict__ key, int n,
+                                                      int ncells, int32_t* __restrict__ start_out,
+                                                      int32_t* __restrict__ count_out,
+                                                      int32_t* __restrict__ fill,
+                                                      int32_t* __restrict__ dest,
+                                                      int32_t* __restrict__ cellof_out) {
+  for (int c = threadIdx.x; c < ncells; c += blockDim.x) count_out[c] = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < n; s += blockDim.x) atomicAdd(&count_out[key[s]], 1);
+  __syncthreads();
+  cta_exclusive_scan(ncells, [&](int i) { return count_out[i]; }, start_out);
+  for (int c = threadIdx.x; c < ncells; c += blockDim.x) fill[c] = start_out[c];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int base = 0; base < n; base += 32) {
+      const int s = base + lane;
+      const int k = (s < n) ? key[s] : -1;
+      const unsigned peers = __match_any_sync(FULL, k);
+      const int leader = __ffs(peers) - 1;
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      int b = 0;
+      if (s < n && lane == leader) {
+        b = fill[k];
+        fill[k] = b + __popc(peers);
+      }
+      b = __shfl_sync(FULL, b, leader);
+      if (s < n) dest[s] = b + rank;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    const int d = dest[s];
+    o.x[d] = (Tout)ix[s];
+    o.y[d] = (Tout)iy[s];
+    o.vx[d] = (Tout)ivx[s];
+    o.vy[d] = (Tout)ivy[s];
+    o.vz[d] = (Tout)ivz[s];
+    o.ir[d] = (Tout)iir[s];
+    if (cellof_out) cellof_out[d] = key[s];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void flush_counts(const CollCount& cc, unsigned* s_cnt) {
+  unsigned a = cc.cand, b = cc.coll, c = cc.clip, d = cc.inel;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(FULL, a, o);
+    b += __shfl_xor_sync(FULL, b, o);
+    c += __shfl_xor_sync(FULL, c, o);
+    d += __shfl_xor_sync(FULL, d, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(s_cnt + 0, a);
+    atomicAdd(s_cnt + 1, b);
+    atomicAdd(s_cnt + 2, c);
+    atomicAdd(s_cnt + 3, d);
+  }
+}
+
+// One warp per cell: stage the cell's velocities and rotational energies in
+// shared memory (cells above `tile` particles work in global memory), run
+// NTC collisions and/or sampling, write back.  flags: 1 collide, 2 sample.
+template <typename T>
+__global__ void __launch_bounds__(WPB * 32) k_collide_sample(Params<T> p, PBuf<T> b,
+                                                             const int32_t* __restrict__ start,
+                                                             const int32_t* __restrict__ count,
+                                                             T* __restrict__ sgmax, double* __restrict__ acc,
+                                                             double* __restrict__ comp,
+                                                             uint32_t* __restrict__ owner_g,
+                                                             uint32_t step, int flags, int tile,
+                                                             unsigned long long* __restrict__ stats) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned s_cnt[4];
+  if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cell = blockIdx.x * WPB + warp;
+  if (cell < p.ncells) {
+    const int base = start[cell], n = count[cell];
+    T* tv = reinterpret_cast<T*>(smem) + (size_t)warp * tile * 4;
+    uint32_t* tow = reinterpret_cast<uint32_t*>(smem + (size_t)WPB * tile * 4 * sizeof(T)) + (size_t)warp * tile;
+    const bool staged = n <= tile;
+    T *vx, *vy, *vz, *ir;
+    uint32_t* own;
+    if (staged) {
+      vx = tv;
+      vy = tv + tile;
+      vz = tv + 2 * tile;
+      ir = tv + 3 * tile;
+      own = tow;
+      for (int q = lane; q < n; q += 32) {
+        vx[q] = b.vx[base + q];
+        vy[q] = b.vy[base + q];
+        vz[q] = b.vz[base + q];
+        ir[q] = b.ir[base + q];
+      }
+    } else {
+      vx = b.vx + base;
+      vy = b.vy + base;
+      vz = b.vz + base;
+      ir = b.ir + base;
+      own = owner_g + base;
+    }
+    __syncwarp();
+    if (flags & 1) {
+      CollCount cc{0, 0, 0, 0};
+      collide_cell<T>(p, vx, vy, vz, ir, n, (uint32_t)cell, step, sgmax + cell, own, cc);
+      flush_counts<T>(cc, s_cnt);
+      __syncwarp();
+    }
+    if (flags & 2) sample_cell<T>(vx, vy, vz, ir, n, acc + (size_t)cell * NMOM, comp + (size_t)cell * NMOM);
+    if (staged && (flags & 1)) {
+      for (int q = lane; q < n; q += 32) {
+        b.vx[base + q] = vx[q];
+        b.vy[base + q] = vy[q];
+        b.vz[base + q] = vz[q];
+        b.ir[base + q] = ir[q];
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && s_cnt[threadIdx.x]) atomicAdd(stats + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 padded-bin layout: the fused step
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void append_particle(const Params<float>& p, const PBuf<float>& o,
+                                                const int32_t* __restrict__ start,
+                                                int32_t* __restrict__ cnt_out, const Ovf& ovo,
+                                                int ovf_cap, bool active, int d, float x, float y,
+                                                float vx, float vy, float vz, float ir,
+                                                unsigned* s_misc) {
+  const int lane = threadIdx.x & 31;
+  const int key = active ? d : -1;
+  const unsigned peers = __match_any_sync(FULL, key);
+  const int leader = __ffs(peers) - 1;
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  int b = 0;
+  if (active && lane == leader) b = atomicAdd(&cnt_out[d], __popc(peers));
+  b = __shfl_sync(FULL, b, leader);
+  if (!active) return;
+  const int slot = b + rank;
+  const int s0 = start[d], cap = start[d + 1] - s0;
+  if (slot < cap) {
+    const int w = s0 + slot;
+    o.x[w] = x;
+    if (DIM == 2) o.y[w] = y;
+    o.vx[w] = vx;
+    o.vy[w] = vy;
+    o.vz[w] = vz;
+    o.ir[w] = ir;
+    if (slot >= cap - 8) atomicAdd(s_misc + 1, 1u);
+  } else {
+    const int q = atomicAdd(ovo.count, 1);
+    atomicAdd(s_misc + 0, 1u);
+    if (q < ovf_cap) {
+      ovo.x[q] = x;
+      ovo.y[q] = y;
+      ovo.vx[q] = vx;
+      ovo.vy[q] = vy;
+      ovo.vz[q] = vz;
+      ovo.ir[q] = ir;
+      ovo.dest[q] = d;
+    }
+  }
+}
+
+// flags: 1 collide (step_c), 2 sample, 4 move (step_m) into `out`.
+// Blocks [0, ncell_blocks) take WPB cells each; the remaining blocks move the
+// particles of the input overflow list.
+template <int DIM>
+__global__ void __launch_bounds__(WPB * 32) k_fused(Params<float> p, PBuf<float> in, PBuf<float> out,
+                                                    const int32_t* __restrict__ start,
+                                                    int32_t* __restrict__ cnt_in,
+                                                    int32_t* __restrict__ cnt_out,
+                                                    float* __restrict__ sgmax, double* __restrict__ acc,
+                                                    double* __restrict__ comp,
+                                                    uint32_t* __restrict__ owner_g, Ovf ovi, Ovf ovo,
+                                                    int ovf_cap, uint32_t step_c, uint32_t step_m,
+                                                    int flags, int tile, int ncell_blocks,
+                                                    double* __restrict__ tally_g,
+                                                    unsigned long long* __restrict__ stats) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned s_cnt[4];
+  __shared__ unsigned s_misc[2];
+  __shared__ float s_tally[20];
+  if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
+  if (threadIdx.x < 2) s_misc[threadIdx.x] = 0;
+  if (threadIdx.x < 20) s_tally[threadIdx.x] = 0.f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if ((int)blockIdx.x < ncell_blocks) {
+    const int cell = blockIdx.x * WPB + warp;
+    if (cell < p.ncells) {
+      const int base = start[cell], n = cnt_in[cell];
+      float* tv = reinterpret_cast<float*>(smem) + (size_t)warp * tile * 4;
+      uint32_t* tow = reinterpret_cast<uint32_t*>(smem + (size_t)WPB * tile * 16) + (size_t)warp * tile;
+      const bool staged = n <= tile;
+      float *vx, *vy, *vz, *ir;
+      uint32_t* own;
+      if (staged) {
+        vx = tv;
+        vy = tv + tile;
+        vz = tv + 2 * tile;
+        ir = tv + 3 * tile;
+        own = tow;
+        for (int q = lane; q < n; q += 32) {
+          vx[q] = in.vx[base + q];
+          vy[q] = in.vy[base + q];
+          vz[q] = in.vz[base + q];
+          ir[q] = in.ir[base + q];
+        }
+      } else {
+        vx = in.vx + base;
+        vy = in.vy + base;
+        vz = in.vz + base;
+        ir = in.ir + base;
+        own = owner_g + base;
+      }
+      __syncwarp();
+      if (flags & 1) {
+        CollCount cc{0, 0, 0, 0};
+        collide_cell<float>(p, vx, vy, vz, ir, n, (uint32_t)cell, step_c, sgmax + cell, own, cc);
+        flush_counts<float>(cc, s_cnt);
+        __syncwarp();
+      }
+      if (flags & 2) sample_cell<float>(vx, vy, vz, ir, n, acc + (size_t)cell * NMOM, comp + (size_t)cell * NMOM);
+      if (flags & 4) {
+        const int nr = (n + 31) & ~31;
+        for (int q = lane; q < nr; q += 32) {
+          const bool active = q < n;
+          float x = 0.f, y = 0.f, a = 0.f, bb = 0.f, c = 0.f, e = 0.f;
+          int d = 0;
+          if (active) {
+            x = in.x[base + q];
+            if (DIM == 2) y = in.y[base + q];
+            a = vx[q];
+            bb = vy[q];
+            c = vz[q];
+            e = ir[q];
+            fly<float, DIM>(p, x, y, a, bb, c, e, (uint32_t)q, (uint32_t)cell, step_m, s_tally,
+                            stats + ST_HITS, stats + ST_MAXHIT);
+            d = cell_of<float, DIM>(p, x, y);
+          }
+          append_particle<DIM>(p, out, start, cnt_out, ovo, ovf_cap, active, d, x, y, a, bb, c, e, s_misc);
+        }
+        __syncwarp();
+        if (lane == 0) cnt_in[cell] = 0;
+      } else if (staged && (flags & 1)) {
+        for (int q = lane; q < n; q += 32) {
+          in.vx[base + q] = vx[q];
+          in.vy[base + q] = vy[q];
+          in.vz[base + q] = vz[q];
+          in.ir[base + q] = ir[q];
+        }
+      }
+    }
+  } else if (flags & 4) {
+    // overflow list of the previous step: move and append (no collision)
+    const int nov = min(*ovi.count, ovf_cap);
+    const int gw = (blockIdx.x - ncell_blocks) * WPB + warp;
+    const int nwarps = (gridDim.x - ncell_blocks) * WPB;
+    for (int base = gw * 32; base < nov; base += nwarps * 32) {
+      const int q = base + lane;
+      const bool active = q < nov;
+      float x = 0.f, y = 0.f, a = 0.f, bb = 0.f, c = 0.f, e = 0.f;
+      int d = 0;
+      if (active) {
+        x = ovi.x[q];
+        y = ovi.y[q];
+        a = ovi.vx[q];
+        bb = ovi.vy[q];
+        c = ovi.vz[q];
+        e = ovi.ir[q];
+        fly<float, DIM>(p, x, y, a, bb, c, e, (uint32_t)q, (uint32_t)(p.ncells + 1), step_m, s_tally,
+                        stats + ST_HITS, stats + ST_MAXHIT);
+        d = cell_of<float, DIM>(p, x, y);
+      }
+      append_particle<DIM>(p, out, start, cnt_out, ovo, ovf_cap, active, d, x, y, a, bb, c, e, s_misc);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && s_cnt[threadIdx.x]) atomicAdd(stats + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
+  if (threadIdx.x == 4 && s_misc[0]) atomicAdd(stats + ST_OVF, (unsigned long long)s_misc[0]);
+  if (threadIdx.x == 5 && s_misc[1]) atomicAdd(stats + ST_NEARFULL, (unsigned long long)s_misc[1]);
+  if (threadIdx.x >= 32 && threadIdx.x < 52 && s_tally[threadIdx.x - 32] != 0.f)
+    atomicAdd(tally_g + (threadIdx.x - 32), (double)s_tally[threadIdx.x - 32]);
+}
+
+static __global__ void k_zero_i32(int32_t* a, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 layout rebuild: new bin capacities from the occupancies (+ overflow)
+// ---------------------------------------------------------------------------
+static __global__ void k_rebin_add_ovf(const Ovf ov, int ovf_cap, int32_t* __restrict__ tot) {
+  const int nov = min(*ov.count, ovf_cap);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nov; q += gridDim.x * blockDim.x)
+    atomicAdd(&tot[ov.dest[q]], 1);
+}
+
+// caps = bin_cap_of(tot, slack); halve the slack until the bins fit.
+static __global__ void __launch_bounds__(1024) k_caps_scan(const int32_t* __restrict__ tot, int ncells,
+                                                    double slack, long long capacity,
+                                                    int32_t* __restrict__ start_out,
+                                                    int32_t* __restrict__ flags) {
+  __shared__ double s_slack;
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    s_slack = slack;
+    s_ok = 0;
+  }
+  __syncthreads();
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    const double sl = s_slack;
+    cta_exclusive_scan(ncells, [&](int i) { return bin_cap_of(tot[i], sl); }, start_out);
+    if (threadIdx.x == 0) {
+      if ((long long)start_out[ncells] <= capacity) s_ok = 1;
+      else s_slack = 1.0 + 0.5 * (s_slack - 1.0);
+    }
+    __syncthreads();
+    if (s_ok) break;
+  }
+  if (threadIdx.x == 0 && !s_ok) flags[2] = 1;
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(WPB * 32) k_rebin_copy(PBuf<T> in, PBuf<T> out,
+                                                         const int32_t* __restrict__ start_in,
+                                                         const int32_t* __restrict__ cnt_in,
+                                                         const int32_t* __restrict__ start_out,
+                                                         int32_t* __restrict__ cnt_out, int ncells) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cell = blockIdx.x * WPB + warp;
+  if (cell >= ncells) return;
+  const int si = start_in[cell], so = start_out[cell], n = cnt_in[cell];
+  for (int q = lane; q < n; q += 32) {
+    out.x[so + q] = in.x[si + q];
+    if (DIM == 2) out.y[so + q] = in.y[si + q];
+    out.vx[so + q] = in.vx[si + q];
+    out.vy[so + q] = in.vy[si + q];
+    out.vz[so + q] = in.vz[si + q];
+    out.ir[so + q] = in.ir[si + q];
+  }
+  if (lane == 0) cnt_out[cell] = n;
+}
+
+template <int DIM>
+__global__ void k_rebin_ovf(const Ovf ov, int ovf_cap, PBuf<float> out, const int32_t* __restrict__ start_out,
+                            int32_t* __restrict__ cnt_out) {
+  const int nov = min(*ov.count, ovf_cap);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nov; q += gridDim.x * blockDim.x) {
+    const int d = ov.dest[q];
+    const int w = start_out[d] + atomicAdd(&cnt_out[d], 1);
+    out.x[w] = ov.x[q];
+    if (DIM == 2) out.y[w] = ov.y[q];
+    out.vx[w] = ov.vx[q];
+    out.vy[w] = ov.vy[q];
+    out.vz[w] = ov.vz[q];
+    out.ir[w] = ov.ir[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// export / import
+// ---------------------------------------------------------------------------
+static __global__ void __launch_bounds__(1024) k_scan_counts(const int32_t* __restrict__ cnt, int ncells,
+                                                      int32_t* __restrict__ out) {
+  cta_exclusive_scan(ncells, [&](int i) { return cnt[i]; }, out);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(WPB * 32) k_export(PBuf<T> b, const int32_t* __restrict__ start,
+                                                     const int32_t* __restrict__ cnt,
+                                                     const int32_t* __restrict__ ostart, int ncells,
+                                                     double* x, double* y, double* vx, double* vy,
+                                                     double* vz, double* ir, int32_t* cell_out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cell = blockIdx.x * WPB + warp;
+  if (cell >= ncells) return;
+  const int si = start[cell], so = ostart[cell], n = cnt[cell];
+  for (int q = lane; q < n; q += 32) {
+    x[so + q] = (double)b.x[si + q];
+    y[so + q] = (double)b.y[si + q];
+    vx[so + q] = (double)b.vx[si + q];
+    vy[so + q] = (double)b.vy[si + q];
+    vz[so + q] = (double)b.vz[si + q];
+    ir[so + q] = (double)b.ir[si + q];
+    cell_out[so + q] = cell;
+  }
+}
+
+template <typename T, int DIM>
+__global__ void k_keys_from_pos(Params<T> p, const double* __restrict__ x, const double* __restrict__ y,
+                                int n, int32_t* __restrict__ key) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+    key[s] = cell_of<T, DIM>(p, (T)x[s], (DIM == 2) ? (T)y[s] : T(0));
+}
+
+static __global__ void k_fill_zero_d(double* a, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3.2: particle modification
+// ---------------------------------------------------------------------------
+static __global__ void k_dig_counts(CellParams cp, const double* __restrict__ target, uint32_t iter,
+                             int det, double slack, int32_t* __restrict__ nt,
+                             int32_t* __restrict__ caps, int32_t* __restrict__ flags) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cp.ncells; c += gridDim.x * blockDim.x) {
+    const double* t = target + (size_t)c * 6;
+    bool bad = false;
+    for (int q = 0; q < 6; ++q)
+      if (!isfinite(t[q])) bad = true;
+    if (!(t[0] >= 0.0) || !(t[4] > 0.0) || !(t[5] > 0.0)) bad = true;
+    if (bad) {
+      atomicOr(flags, 1);
+      nt[c] = 0;
+      caps[c] = 0;
+      continue;
+    }
+    Stream<double> st(TAG_DIG_N, 0u, (uint32_t)c, iter, cp.k0, cp.k1);
+    const double xm = t[0] * cp.vcell / cp.fnum;
+    long long v = iround(xm, st.u(0));
+    if (v > 0x3fffffffLL) {
+      atomicOr(flags, 2);
+      v = 0;
+    }
+    nt[c] = (int32_t)v;
+    caps[c] = det ? (int32_t)v : bin_cap_of((int32_t)v, slack);
+  }
+}
+
+static __global__ void __launch_bounds__(1024) k_scan_caps(const int32_t* __restrict__ caps, int ncells,
+                                                    long long capacity, int32_t* __restrict__ start_out,
+                                                    int32_t* __restrict__ flags) {
+  cta_exclusive_scan(ncells, [&](int i) { return caps[i]; }, start_out);
+  if (threadIdx.x == 0) {
+    flags[1] = start_out[ncells];
+    if ((long long)start_out[ncells] > capacity) atomicOr(flags, 4);
+  }
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(WPB * 32) k_dig_apply(CellParams cp, PBuf<T> in, PBuf<T> out,
+                                                        const int32_t* __restrict__ start_in,
+                                                        const int32_t* __restrict__ cnt_in,
+                                                        const int32_t* __restrict__ start_out,
+                                                        int32_t* __restrict__ cnt_out,
+                                                        const int32_t* __restrict__ nt,
+                                                        const double* __restrict__ target, uint32_t iter,
+                                                        int32_t* __restrict__ idx_g,
+                                                        int32_t* __restrict__ cellof_out, int tile) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cell = blockIdx.x * WPB + warp;
+  if (cell >= cp.ncells) return;
+  const int s0 = start_in[cell], n = cnt_in[cell], d0 = start_out[cell], ntg = nt[cell];
+  const double* t = target + (size_t)cell * 6;
+  const int ix = cell % cp.nx, iy = cell / cp.nx;
+  int32_t* idx = (n <= tile) ? reinterpret_cast<int32_t*>(smem) + (size_t)warp * tile * 2 : idx_g + s0;
+  int32_t* rm = (n <= tile) ? reinterpret_cast<int32_t*>(smem) + (size_t)warp * tile * 2 + tile : nullptr;
+  // step ii
+  if (ntg <= n) {
+    const int k = n - ntg;
+    if (k > 0) {
+      for (int q = lane; q < n; q += 32) idx[q] = q;
+      __syncwarp();
+      if (lane == 0) {
+        for (int q = 0; q < k; ++q) {
+          Stream<double> st(TAG_DIG_SEL, (uint32_t)q, (uint32_t)cell, iter, cp.k0, cp.k1);
+          int r = q + (int)(st.u(0) * (double)(n - q));
+          if (r > n - 1) r = n - 1;
+          const int tmp = idx[q];
+          idx[q] = idx[r];
+          idx[r] = tmp;
+        }
+      }
+      __syncwarp();
+    }
+    // mark the removed slots: in shared memory when the cell fits, else by
+    // negating entries of idx (idx holds a permutation of 0..n-1)
+    if (rm) {
+      for (int q = lane; q < n; q += 32) rm[q] = 0;
+      __syncwarp();
+      for (int q = lane; q < k; q += 32) rm[idx[q]] = 1;
+    } else if (k > 0) {
+      // cell larger than the tile: idx lives in global scratch; mark removed
+      // slot r by setting bit 30 of idx[r] (entries are < 2^30)
+      for (int q = lane; q < k; q += 32) {
+        const int slot = idx[q] & 0x3fffffff;
+        atomicOr(&idx[slot], 0x40000000);
+      }
+    }
+    __syncwarp();
+    int kept_before = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int q = base + lane;
+      bool keep = false;
+      if (q < n) {
+        if (rm) keep = rm[q] == 0;
+        else keep = (k == 0) || ((idx[q] & 0x40000000) == 0);
+      }
+      const unsigned m = __ballot_sync(FULL, keep);
+      if (keep) {
+        const int w = d0 + kept_before + __popc(m & ((1u << lane) - 1u));
+        out.x[w] = in.x[s0 + q];
+        out.y[w] = in.y[s0 + q];
+        out.vx[w] = in.vx[s0 + q];
+        out.vy[w] = in.vy[s0 + q];
+        out.vz[w] = in.vz[s0 + q];
+        out.ir[w] = in.ir[s0 + q];
+      }
+      kept_before += __popc(m);
+    }
+  } else {
+    for (int q = lane; q < n; q += 32) {
+      out.x[d0 + q] = in.x[s0 + q];
+      out.y[d0 + q] = in.y[s0 + q];
+      out.vx[d0 + q] = in.vx[s0 + q];
+      out.vy[d0 + q] = in.vy[s0 + q];
+      out.vz[d0 + q] = in.vz[s0 + q];
+      out.ir[d0 + q] = in.ir[s0 + q];
+    }
+    for (int q = lane; q < ntg - n; q += 32) {
+      Stream<double> sp(TAG_DIG_POS, (uint32_t)q, (uint32_t)cell, iter, cp.k0, cp.k1);
+      const int w = d0 + n + q;
+      out.x[w] = (T)(((double)ix + sp.u(0)) * cp.dx);
+      out.y[w] = (T)((cp.dim == 2) ? ((double)iy + sp.u(1)) * cp.dy : 0.0);
+      if (n > 0) {
+        Stream<double> ss(TAG_DIG_SEL, (uint32_t)q, (uint32_t)cell, iter, cp.k0, cp.k1);
+        int src = (int)(ss.u(0) * (double)n);
+        if (src > n - 1) src = n - 1;
+        out.vx[w] = in.vx[s0 + src];
+        out.vy[w] = in.vy[s0 + src];
+        out.vz[w] = in.vz[s0 + src];
+        out.ir[w] = in.ir[s0 + src];
+      } else {
+        double n1, n2, n3, n4;
+        box_muller(sp.u(2), sp.u(3), &n1, &n2);
+        box_muller(sp.u(4), sp.u(5), &n3, &n4);
+        const double stt = sqrt(t[4]);
+        out.vx[w] = (T)(t[1] + stt * n1);
+        out.vy[w] = (T)(t[2] + stt * n2);
+        out.vz[w] = (T)(t[3] + stt * n3);
+        out.ir[w] = (T)(-t[5] * log(sp.u(6)));
+      }
+    }
+  }
+  __syncwarp();
+  // step iii: u*, T_t*, T_r* of the new population (FP64 sums)
+  const int np = ntg;
+  if (np > 0) {
+    double sx = 0, sy = 0, sz = 0, si = 0;
+    for (int q = lane; q < np; q += 32) {
+      sx += (double)out.vx[d0 + q];
+      sy += (double)out.vy[d0 + q];
+      sz += (double)out.vz[d0 + q];
+      si += (double)out.ir[d0 + q];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(FULL, sx, o);
+      sy += __shfl_xor_sync(FULL, sy, o);
+      sz += __shfl_xor_sync(FULL, sz, o);
+      si += __shfl_xor_sync(FULL, si, o);
+    }
+    const double ux = sx / (double)np, uy = sy / (double)np, uz = sz / (double)np;
+    double c2 = 0;
+    for (int q = lane; q < np; q += 32) {
+      const double cx = (double)out.vx[d0 + q] - ux, cy = (double)out.vy[d0 + q] - uy,
+                   cz = (double)out.vz[d0 + q] - uz;
+      c2 += cx * cx + cy * cy + cz * cz;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c2 += __shfl_xor_sync(FULL, c2, o);
+    const double tts = c2 / (3.0 * (double)np);
+    const double trs = 2.0 * si / (cp.d_r * (double)np);
+    // step iv
+    const double a = (np >= 2 && tts > 0.0) ? sqrt(t[4] / tts) : 1.0;
+    const double bx = t[1] - ux * a, by = t[2] - uy * a, bz = t[3] - uz * a;
+    const double cc = (trs > 0.0) ? t[5] / trs : 1.0;
+    for (int q = lane; q < np; q += 32) {
+      const int w = d0 + q;
+      out.vx[w] = (T)(a * (double)out.vx[w] + bx);
+      out.vy[w] = (T)(a * (double)out.vy[w] + by);
+      out.vz[w] = (T)(a * (double)out.vz[w] + bz);
+      out.ir[w] = (T)(cc * (double)out.ir[w]);
+      if (cellof_out) cellof_out[w] = cell;
+    }
+  }
+  if (lane == 0) cnt_out[cell] = ntg;
+}
+
+template <typename T>
+__global__ void k_sgmax_io(T* sg, int n, double* out, const double* in) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    if (out) out[c] = (double)sg[c];
+    if (in) sg[c] = (T)in[c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------
+inline int grid_for(long long n, int threads, int maxblocks = 152 * 16) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > maxblocks) b = maxblocks;
+  return (int)b;
+}
+
+template <typename T>
+void Ops<T>::init(const Params<T>& p, State<T>& s, int cur, int lay, int ppc, int cap0, double tt,
+                  double tr, const double* u3, cudaStream_t st) {
+  k_layout_uniform<<<grid_for(p.ncells + 1, 256), 256, 0, st>>>(p.ncells, (int32_t)cap0, s.start[lay]);
+  const long long total = (long long)p.ncells * ppc;
+  const int g = grid_for(total, 256);
+  if (p.dim == 1)
+    k_init<T, 1><<<g, 256, 0, st>>>(p, s.buf[cur], s.start[lay], s.count[lay], s.cellof, ppc, (T)tt, (T)tr,
+                                    (T)u3[0], (T)u3[1], (T)u3[2]);
+  else
+    k_init<T, 2><<<g, 256, 0, st>>>(p, s.buf[cur], s.start[lay], s.count[lay], s.cellof, ppc, (T)tt, (T)tr,
+                                    (T)u3[0], (T)u3[1], (T)u3[2]);
+  if (ppc == 0) k_zero_i32<<<grid_for(p.ncells, 256), 256, 0, st>>>(s.count[lay], p.ncells);
+  (void)cur;
+}
+
+template <typename T>
+static size_t tile_smem(int tile) {
+  return (size_t)WPB * tile * (4 * sizeof(T) + sizeof(uint32_t));
+}
+
+template <typename T>
+void Ops<T>::step_det(const Params<T>& p, State<T>& s, int& cur, int& lay, uint32_t step, int do_sample,
+                      cudaStream_t st) {
+  const int n = s.nparticles;
+  const int other = cur ^ 1, olay = lay ^ 1;
+  if (n > 0) {
+    if (p.dim == 1)
+      k_move_det<T, 1><<<grid_for(n, 256), 256, 0, st>>>(p, s.buf[cur], s.cellof, s.start[lay], n, step, s.key,
+                                                         s.tally, s.stats);
+    else
+      k_move_det<T, 2><<<grid_for(n, 256), 256, 0, st>>>(p, s.buf[cur], s.cellof, s.start[lay], n, step, s.key,
+                                                         s.tally, s.stats);
+  }
+  const PBuf<T>& a = s.buf[cur];
+  k_sort_stable<T, T><<<1, 1024, 0, st>>>(a.x, a.y, a.vx, a.vy, a.vz, a.ir, s.buf[other], s.key, n, p.ncells,
+                                          s.start[olay], s.count[olay], s.tmp2, s.dest, s.cellof);
+  cur = other;
+  lay = olay;
+  const int flags = 1 | (do_sample ? 2 : 0);
+  const int blocks = (p.ncells + WPB - 1) / WPB;
+  k_collide_sample<T><<<blocks, WPB * 32, tile_smem<T>(s.tile), st>>>(
+      p, s.buf[cur], s.start[lay], s.count[lay], s.sgmax, s.acc, s.comp, s.owner, step, flags, s.tile, s.stats);
+}
+
+template <typename T>
+void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint32_t step0, int nsteps,
+                       int do_sample, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (nsteps <= 0) return;
+    const int cblocks = (p.ncells + WPB - 1) / WPB;
+    const int oblocks = 4;
+    const size_t sm = tile_smem<T>(s.tile);
+    auto launch = [&](int flags, uint32_t sc, uint32_t sm_step) {
+      const int other = cur ^ 1;
+      if (p.dim == 1)
+        k_fused<1><<<cblocks + oblocks, WPB * 32, sm, st>>>(
+            p, s.buf[cur], s.buf[other], s.start[lay], s.count[cur], s.count[other], s.sgmax, s.acc, s.comp,
+            s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats);
+      else
+        k_fused<2><<<cblocks + oblocks, WPB * 32, sm, st>>>(
+            p, s.buf[cur], s.buf[other], s.start[lay], s.count[cur], s.count[other], s.sgmax, s.acc, s.comp,
+            s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats);
+      // the input overflow list has been consumed
+      cudaMemsetAsync(s.ovf[cur].count, 0, sizeof(int32_t), st);
+      cur = other;
+    };
+    // move of step0, then per step: collide (+sample) of step k and move of step k+1
+    launch(4, step0, step0);
+    for (int i = 0; i < nsteps; ++i) {
+      const bool last = (i == nsteps - 1);
+      const uint32_t sc = step0 + (uint32_t)i;
+      if (!last) {
+        launch(1 | (do_sample ? 2 : 0) | 4, sc, sc + 1);
+      } else {
+        k_collide_sample<T><<<cblocks, WPB * 32, sm, st>>>(p, s.buf[cur], s.start[lay], s.count[cur], s.sgmax,
+                                                          s.acc, s.comp, s.owner, sc, 1 | (do_sample ? 2 : 0),
+                                                          s.tile, s.stats);
+      }
+    }
+  } else {
+    (void)p; (void)s; (void)cur; (void)lay; (void)step0; (void)nsteps; (void)do_sample; (void)st;
+  }
+}
+
+template <typename T>
+void Ops<T>::rebin(const Params<T>& p, State<T>& s, int& cur, int& lay, int with_ovf, double slack,
+                   cudaStream_t st) {
+  // tot (tmp in s.nt) = occupancy (+ overflow destinations)
+  const int other = cur ^ 1, olay = lay ^ 1;
+  cudaMemcpyAsync(s.nt, s.count[cur], sizeof(int32_t) * p.ncells, cudaMemcpyDeviceToDevice, st);
+  if constexpr (sizeof(T) == 4) {
+    if (with_ovf) k_rebin_add_ovf<<<64, 256, 0, st>>>(s.ovf[cur], s.ovf_cap, s.nt);
+  }
+  k_caps_scan<<<1, 1024, 0, st>>>(s.nt, p.ncells, slack, (long long)s.capacity, s.start[olay], s.flags);
+  const int blocks = (p.ncells + WPB - 1) / WPB;
+  if (p.dim == 1)
+    k_rebin_copy<T, 1><<<blocks, WPB * 32, 0, st>>>(s.buf[cur], s.buf[other], s.start[lay], s.count[cur],
+                                                    s.start[olay], s.count[other], p.ncells);
+  else
+    k_rebin_copy<T, 2><<<blocks, WPB * 32, 0, st>>>(s.buf[cur], s.buf[other], s.start[lay], s.count[cur],
+                                                    s.start[olay], s.count[other], p.ncells);
+  if constexpr (sizeof(T) == 4) {
+    if (with_ovf) {
+      if (p.dim == 1)
+        k_rebin_ovf<1><<<64, 256, 0, st>>>(s.ovf[cur], s.ovf_cap, s.buf[other], s.start[olay], s.count[other]);
+      else
+        k_rebin_ovf<2><<<64, 256, 0, st>>>(s.ovf[cur], s.ovf_cap, s.buf[other], s.start[olay], s.count[other]);
+      cudaMemsetAsync(s.ovf[cur].count, 0, sizeof(int32_t), st);
+    }
+  }
+  // the old buffer's occupancies are cleared so that it can take appends
+  k_zero_i32<<<grid_for(p.ncells, 256), 256, 0, st>>>(s.count[cur], p.ncells);
+  cur = other;
+  lay = olay;
+}
+
+template <typename T>
+void Ops<T>::export_particles(const Params<T>& p, State<T>& s, int cur, int lay, double* x, double* y,
+                              double* vx, double* vy, double* vz, double* ir, int32_t* cell, cudaStream_t st) {
+  const int cntlay = (sizeof(T) == 4) ? cur : lay;
+  k_scan_counts<<<1, 1024, 0, st>>>(s.count[cntlay], p.ncells, s.tmp_start);
+  const int blocks = (p.ncells + WPB - 1) / WPB;
+  k_export<T><<<blocks, WPB * 32, 0, st>>>(s.buf[cur], s.start[lay], s.count[cntlay], s.tmp_start, p.ncells, x, y,
+                                          vx, vy, vz, ir, cell);
+}
+
+template <typename T>
+void Ops<T>::import_particles(const Params<T>& p, State<T>& s, int& cur, int& lay, int64_t n, const double* x,
+                              const double* y, const double* vx, const double* vy, const double* vz,
+                              const double* ir, int det, cudaStream_t st) {
+  const int other = cur ^ 1, olay = lay ^ 1;
+  if (n > 0) {
+    if (p.dim == 1)
+      k_keys_from_pos<T, 1><<<grid_for(n, 256), 256, 0, st>>>(p, x, y, (int)n, s.key);
+    else
+      k_keys_from_pos<T, 2><<<grid_for(n, 256), 256, 0, st>>>(p, x, y, (int)n, s.key);
+  }
+  const double* yy = (p.dim == 2) ? y : x;  // y is not read in 1D; pass any valid pointer
+  s.nparticles = (int)n;
+  if (det) {
+    // stable sort of the input into the other buffer: the compact layout
+    k_sort_stable<double, T><<<1, 1024, 0, st>>>(x, yy, vx, vy, vz, ir, s.buf[other], s.key, (int)n, p.ncells,
+                                                 s.start[olay], s.count[olay], s.tmp2, s.dest, s.cellof);
+    cur = other;
+    lay = olay;
+    if (p.dim == 1) cudaMemsetAsync(s.buf[cur].y, 0, sizeof(T) * (size_t)n, st);
+    return;
+  }
+  if constexpr (sizeof(T) == 4) {
+    // stable sort into the other buffer as a compact list (start tmp_start,
+    // counts nt), then copy into padded bins of buffer cur, layout lay
+    k_sort_stable<double, T><<<1, 1024, 0, st>>>(x, yy, vx, vy, vz, ir, s.buf[other], s.key, (int)n, p.ncells,
+                                                 s.tmp_start, s.nt, s.tmp2, s.dest, nullptr);
+    k_caps_scan<<<1, 1024, 0, st>>>(s.nt, p.ncells, s.slack, (long long)s.capacity, s.start[lay], s.flags);
+    const int blocks = (p.ncells + WPB - 1) / WPB;
+    if (p.dim == 1)
+      k_rebin_copy<T, 1><<<blocks, WPB * 32, 0, st>>>(s.buf[other], s.buf[cur], s.tmp_start, s.nt, s.start[lay],
+                                                      s.count[cur], p.ncells);
+    else
+      k_rebin_copy<T, 2><<<blocks, WPB * 32, 0, st>>>(s.buf[other], s.buf[cur], s.tmp_start, s.nt, s.start[lay],
+                                                      s.count[cur], p.ncells);
+    k_zero_i32<<<grid_for(p.ncells, 256), 256, 0, st>>>(s.count[other], p.ncells);
+    cudaMemsetAsync(s.ovf[0].count, 0, sizeof(int32_t), st);
+    cudaMemsetAsync(s.ovf[1].count, 0, sizeof(int32_t), st);
+  }
+}
+
+template <typename T>
+void Ops<T>::dig_counts(const CellParams& cp, State<T>& s, int lay, const double* target, uint32_t iter, int det,
+                        cudaStream_t st) {
+  cudaMemsetAsync(s.flags, 0, sizeof(int32_t) * 4, st);
+  // caps go to tmp_start (ncells), then scanned into the other layout's start
+  k_dig_counts<<<grid_for(cp.ncells, 256), 256, 0, st>>>(cp, target, iter, det, s.slack, s.nt, s.tmp_start,
+                                                         s.flags);
+  k_scan_caps<<<1, 1024, 0, st>>>(s.tmp_start, cp.ncells, (long long)s.capacity, s.start[lay ^ 1], s.flags);
+}
+
+template <typename T>
+void Ops<T>::dig_apply(const CellParams& cp, State<T>& s, int& cur, int& lay, const double* target,
+                       uint32_t iter, int det, cudaStream_t st) {
+  const int other = cur ^ 1, olay = lay ^ 1;
+  const int cin = det ? lay : cur;    // occupancy array of the current state
+  const int cout = det ? olay : other;
+  const int blocks = (cp.ncells + WPB - 1) / WPB;
+  const size_t sm = (size_t)WPB * s.tile * 2 * sizeof(int32_t);
+  if (cp.dim == 1)
+    k_dig_apply<T, 1><<<blocks, WPB * 32, sm, st>>>(cp, s.buf[cur], s.buf[other], s.start[lay], s.count[cin],
+                                                    s.start[olay], s.count[cout], s.nt, target, iter, s.scratch_i,
+                                                    det ? s.cellof : nullptr, s.tile);
+  else
+    k_dig_apply<T, 2><<<blocks, WPB * 32, sm, st>>>(cp, s.buf[cur], s.buf[other], s.start[lay], s.count[cin],
+                                                    s.start[olay], s.count[cout], s.nt, target, iter, s.scratch_i,
+                                                    det ? s.cellof : nullptr, s.tile);
+  if (!det) k_zero_i32<<<grid_for(cp.ncells, 256), 256, 0, st>>>(s.count[cur], cp.ncells);
+  cur = other;
+  lay = olay;
+}
+
+template <typename T>
+void Ops<T>::total_count(State<T>& s, const int32_t* cnt, int ncells, cudaStream_t st) {
+  k_scan_counts<<<1, 1024, 0, st>>>(cnt, ncells, s.tmp_start);
+}
+
+template <typename T>
+void Ops<T>::configure(int tile) {
+  const int sm = (int)tile_smem<T>(tile);
+  const int smd = WPB * tile * 2 * (int)sizeof(int32_t);
+  cudaFuncSetAttribute(k_collide_sample<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_dig_apply<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
+  cudaFuncSetAttribute(k_dig_apply<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
+  if constexpr (sizeof(T) == 4) {
+    cudaFuncSetAttribute(k_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  }
+}
+
+template <typename T>
+void Ops<T>::sgmax_io(State<T>& s, int ncells, double* out, const double* in, cudaStream_t st) {
+  k_sgmax_io<T><<<grid_for(ncells, 256), 256, 0, st>>>(s.sgmax, ncells, out, in);
+}
+
+}  // namespace dsmc

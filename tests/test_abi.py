@@ -1,0 +1,82 @@
+"""Host-side checks of the C ABI (no GPU needed): the shared library loads and
+exports every entry point include/dig_dsmc.h declares, the Python struct
+mirrors the C struct byte for byte, and configuration errors are reported."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2501_10965_gb300 import dsmc, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dig_dsmc.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = dsmc.load()
+    declared = _declared()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(L, name), name
+    assert sorted(dsmc.SYMBOLS) == declared
+    out = subprocess.run(["nm", "-D", "--defined-only", dsmc.library_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (\w+)$", out, flags=re.M))
+    assert set(declared) <= exported
+
+
+def test_config_struct_layout_matches_header():
+    fields = [f[0] for f in dsmc.DsmcConfig._fields_]
+    prog = "#include <stdio.h>\n#include <stddef.h>\n#include \"dig_dsmc.h\"\nint main(void){\n"
+    prog += 'printf("size %zu\\n", sizeof(dsmc_config));\n'
+    for f in fields:
+        prog += f'printf("{f} %zu\\n", offsetof(dsmc_config, {f}));\n'
+    prog += "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(prog)
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(l.split() for l in lines if l)
+    assert int(got["size"]) == ctypes.sizeof(dsmc.DsmcConfig)
+    for f in fields:
+        assert int(got[f]) == getattr(dsmc.DsmcConfig, f).offset, f
+
+
+def _ws(cfg):
+    L = dsmc.load()
+    c = dsmc.make_config(cfg)
+    n = ctypes.c_size_t()
+    return L.dsmc_workspace_size(ctypes.byref(c), ctypes.byref(n)), n.value
+
+
+def test_workspace_size_and_argument_errors():
+    rc, n = _ws(W.cavity_2d_20m())
+    assert rc == 0 and n > 2 * 6 * 4 * 20_040_000  # two FP32 particle buffers at least
+    rc, n64 = _ws(W.fourier_1d())
+    assert rc == 0 and n64 > 2 * 6 * 8 * 10000
+    assert _ws(W.fourier_1d(d_r=3.0))[0] == -1
+    assert _ws(W.fourier_1d(alpha=1.5))[0] == -1
+    assert _ws(W.fourier_1d(nx=0))[0] == -1
+    assert _ws(W.fourier_1d(dt=-1.0))[0] == -1
+    bad = W.fourier_1d()
+    bad["walls"][0] = {"kind": "diffuse", "T": 1.0, "u": (0.5, 0.0, 0.0)}  # moving along its normal
+    assert _ws(bad)[0] == -1
+    assert _ws(W.couette_1d(bin_slack=0.5))[0] == -1
+
+
+def test_init_without_workspace_is_rejected():
+    L = dsmc.load()
+    c = dsmc.make_config(W.fourier_1d())
+    h = ctypes.c_void_p()
+    assert L.dsmc_init(ctypes.byref(c), None, 0, None, ctypes.byref(h)) == -1
+    assert not h.value
