@@ -15,7 +15,8 @@
  *    memory.  Arrays are dense, row-major, FP64 unless stated.
  *  - The caller owns every buffer it passes, including the workspace given to
  *    dsmc_init; the library never frees caller memory and allocates no device
- *    memory of its own.  The library owns only the opaque handle (host memory).
+ *    memory at run time.  The library owns the opaque handle (host memory)
+ *    and one fixed device array used only by synth_solve_noalloc.
  *  - Work is queued on the CUDA stream given to dsmc_init.  Calls that return
  *    host values (counts, iterations, statistics) synchronise that stream.
  *  - Return value: DSMC_OK (0) or a negative DSMC_ERR_* code; no exception or
@@ -159,6 +160,40 @@ int synth_solve(dsmc_handle *h, const double *dev_fields, const double *dev_hot,
  * temperature <= 0; DSMC_ERR_CAPACITY (nothing changed) if the new total does
  * not fit. */
 int dig_correct(dsmc_handle *h, const double *dev_target);
+
+/* Largest slab synth_solve_noalloc accepts. */
+#define DSMC_SYNTH_NOALLOC_MAX_CELLS 2048
+
+/* synth_solve for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is a library convenience.  Callers such as a host code
+ * whose device memory is owned by another allocator, or code running where
+ * cudaMalloc is not allowed (for example during stream capture), cannot
+ * create a handle, because dsmc_init needs a workspace they would have to
+ * allocate.  This call needs no handle and no workspace: it reads the
+ * configuration from cfg (dim must be 1, nx >= 3) and solves the same
+ * discrete equations as synth_solve, from the same kind of inputs
+ * (dev_fields ncells x DSMC_NFIELDS, dev_hot ncells x DSMC_NHOT) into
+ * dev_out (ncells x DSMC_NTARGET), all caller-owned device arrays, on
+ * stream (a cudaStream_t or NULL).  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *  - Scratch: the solver's Newton scratch lives in one fixed device array in
+ *    the library (about 1.5 MB, enough for DSMC_SYNTH_NOALLOC_MAX_CELLS
+ *    cells); every GPU that loads the library holds it until the process
+ *    exits.  nx above DSMC_SYNTH_NOALLOC_MAX_CELLS returns DSMC_ERR_CAPACITY
+ *    and launches nothing.
+ *  - The first call on a device looks up the array's device address on the
+ *    current device (once per device); make that first call before any
+ *    stream capture on that device.
+ *  - Every call uses the same array, which keeps the last call's contents;
+ *    the solver writes each scratch word before it reads it.  Calls that
+ *    overlap on the GPU (other streams, other host threads) race on the
+ *    array and corrupt each other's results: serialise them.
+ *  - Synchronises stream; host_iters / host_resid (may be NULL) receive the
+ *    iteration count and the final max |residual|.  Returns DSMC_OK,
+ *    DSMC_ERR_NOT_CONVERGED (outputs written), DSMC_ERR_NUMERIC,
+ *    DSMC_ERR_ARG, DSMC_ERR_CAPACITY or DSMC_ERR_CUDA. */
+int synth_solve_noalloc(const dsmc_config *cfg, const double *dev_fields, const double *dev_hot,
+                        double *dev_out, void *stream, int *host_iters, double *host_resid);
 
 /* ---- state access (tests, checkpoints, diagnostics) ---------------------- */
 

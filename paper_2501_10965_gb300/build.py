@@ -22,6 +22,7 @@ UNITS = {
     "dsmc_ops_f32.cu": [],
     "dsmc_fields.cu": ["-fmad=false"],
     "dsmc_capi.cu": ["-fmad=false"],
+    "dsmc_noalloc.cu": ["-fmad=false"],
 }
 
 

@@ -27,7 +27,7 @@ SYMBOLS = ["dsmc_workspace_size", "dsmc_init", "dsmc_destroy", "dsmc_last_error"
            "dsmc_hot", "synth_solve", "dig_correct", "dsmc_num_particles", "dsmc_get_particles",
            "dsmc_set_particles", "dsmc_get_accumulators", "dsmc_get_sgmax", "dsmc_set_sgmax",
            "dsmc_get_counters", "dsmc_set_counters", "dsmc_get_stats", "dsmc_get_wall_tally",
-           "dsmc_get_constants"]
+           "dsmc_get_constants", "synth_solve_noalloc"]
 
 
 class DsmcConfig(ctypes.Structure):
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
         "dsmc_get_stats": ([H, P], ctypes.c_int),
         "dsmc_get_wall_tally": ([H, P], ctypes.c_int),
         "dsmc_get_constants": ([H, P], ctypes.c_int),
+        "synth_solve_noalloc": ([P, P, P, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -267,3 +268,20 @@ class Dsmc:
         out = (ctypes.c_double * 8)()
         self._check(load().dsmc_get_constants(self._h, out))
         return dict(zip(("dx", "dy", "vcell", "fnum", "mu_ref", "k_visc", "c_sigma", "p_inel"), list(out)))
+
+
+def synth_solve_noalloc(cfg: dict, fields: torch.Tensor, hot: torch.Tensor, out: torch.Tensor | None = None,
+                        stream: torch.cuda.Stream | None = None):
+    """The 1D synthetic solve without a handle or workspace (see the header):
+    for callers that cannot allocate device memory.  Returns (out, iterations,
+    max residual, status code)."""
+    L = load()
+    c = make_config(cfg)
+    if out is None:
+        out = torch.empty((int(cfg["nx"]), NTARGET), dtype=torch.float64, device=fields.device)
+    st = stream if stream is not None else torch.cuda.current_stream(fields.device)
+    it = ctypes.c_int()
+    res = ctypes.c_double()
+    rc = L.synth_solve_noalloc(ctypes.byref(c), _ptr(fields.contiguous()), _ptr(hot.contiguous()), _ptr(out),
+                               ctypes.c_void_p(st.cuda_stream), ctypes.byref(it), ctypes.byref(res))
+    return out, it.value, res.value, rc
