@@ -34,6 +34,8 @@ def workload(name: str) -> dict:
     from paper_2501_10965_gb300 import workloads as W
     if name == "cavity2d_20m":
         return W.cavity_2d_20m()
+    if name == "cavity2d_11m":
+        return W.cavity_2d(nx=300, ny=225, ppc=167, kn=0.01, lx=4.0 / 3.0, ly=1.0)
     if name == "cavity2d_500k":
         return W.cavity_2d()
     if name == "couette1d_40k":
@@ -177,6 +179,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """Initialise, run the warm-up steps and then --profile-steps steps of the
+    workload, nothing else (a short, fixed launch sequence for ncu)."""
+    import torch
+
+    from paper_2501_10965_gb300 import dsmc
+    cfg = workload(args.workload)
+    sim = dsmc.Dsmc(cfg)
+    sim.dsmc_step(args.warmup, sample=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.dsmc_step(args.profile_steps, sample=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    print(json.dumps({"profile_steps": args.profile_steps, "workload": args.workload,
+                      "particles": sim.num_particles(), "wall_s": dt, "stats": sim.stats()}), flush=True)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -288,8 +308,12 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per fused launch from an ncu capture of the current kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="only run warm-up + this many steps (for profiler captures)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_steps > 0:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -134,6 +134,8 @@ void carve_state(Carver& cv, const Plan& pl, State<T>& s) {
   s.sgmax = cv.take<T>(nc);
   s.acc = cv.take<double>(nc * NMOM);
   s.comp = cv.take<double>(nc * NMOM);
+  s.stg = pl.det ? nullptr : cv.take<float>(nc * NMOM);
+  s.stc = pl.det ? nullptr : cv.take<float>(nc * NMOM);
   s.tally = cv.take<double>(20);
   s.stats = cv.take<unsigned long long>(ST_NSLOTS);
   s.flags = cv.take<int32_t>(16);
@@ -164,9 +166,11 @@ Plan make_plan(const dsmc_config* c, char* base, dsmc_handle* h) {
     const int64_t bins = (int64_t)pl.ncells * host_bin_cap(c->ppc, c->bin_slack);
     pl.capacity = c->capacity > 0 ? c->capacity : bins + bins / 4 + 1024;
   }
-  int tile = 2 * c->ppc;
+  // particles staged per warp: room for density fluctuations above ppc;
+  // larger cells are processed in global memory
+  int tile = pl.det ? 2 * c->ppc : (5 * c->ppc) / 4 + 32;
   if (tile < 64) tile = 64;
-  tile = (tile + 31) & ~31;
+  tile = pl.det ? (tile + 31) & ~31 : (tile + 15) & ~15;  // FP32: 16-float multiple for bulk copies
   const int tmax = pl.det ? 256 : 512;
   if (tile > tmax) tile = tmax;
   pl.tile = tile;
@@ -283,6 +287,10 @@ int init_state(dsmc_handle* h, State<T>& s, Params<T>& p) {
   cudaMemsetAsync(s.flags, 0, sizeof(int32_t) * 16, st);
   cudaMemsetAsync(s.acc, 0, sizeof(double) * nc * NMOM, st);
   cudaMemsetAsync(s.comp, 0, sizeof(double) * nc * NMOM, st);
+  if (s.stg) {
+    cudaMemsetAsync(s.stg, 0, sizeof(float) * nc * NMOM, st);
+    cudaMemsetAsync(s.stc, 0, sizeof(float) * nc * NMOM, st);
+  }
   for (int b = 0; b < 2; ++b) {
     cudaMemsetAsync(s.count[b], 0, sizeof(int32_t) * nc, st);
     cudaMemsetAsync(s.ovf[b].count, 0, sizeof(int32_t), st);
@@ -386,12 +394,14 @@ int dsmc_step(dsmc_handle* h, int nsteps, int sample) {
   int r = check_cuda(h, "dsmc_step");
   if (r) return r;
   // rebuild the bins if a particle overflowed or a bin came near its capacity
-  int32_t ovf = 0;
+  int32_t ovf = 0, timeout = 0;
   unsigned long long nearfull = 0;
   cudaMemcpyAsync(&ovf, h->sf.ovf[h->cur].count, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
   cudaMemcpyAsync(&nearfull, h->sf.stats + ST_NEARFULL, sizeof(nearfull), cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(&timeout, h->sf.flags + 8, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
   r = sync_check(h, "dsmc_step (bin check)");
   if (r) return r;
+  if (timeout) return set_err(h, DSMC_ERR_TIMEOUT, "dsmc_step: a cell's bulk copy did not complete in time");
   if (ovf > 0 || nearfull > 0) {
     Ops<float>::rebin(h->pf, h->sf, h->cur, h->lay, 1, h->sf.slack, h->stream);
     cudaMemsetAsync(h->sf.stats + ST_NEARFULL, 0, sizeof(unsigned long long), h->stream);

@@ -115,6 +115,48 @@ struct Stream<float> {
   }
 };
 
+// Uniforms j0 .. j0+3 of a stream (j0 a multiple of 4): one Philox block in
+// FP32, two in FP64.
+__device__ __forceinline__ void draw4(uint32_t tag, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t j0,
+                                      uint32_t k0, uint32_t k1, float* u) {
+  const uint4 w = philox4x32_10(c0, c1, c2, (tag << 24) | (j0 >> 2), k0, k1);
+  u[0] = u01_from_word(w.x);
+  u[1] = u01_from_word(w.y);
+  u[2] = u01_from_word(w.z);
+  u[3] = u01_from_word(w.w);
+}
+
+__device__ __forceinline__ void draw4(uint32_t tag, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t j0,
+                                      uint32_t k0, uint32_t k1, double* u) {
+  const uint4 a = philox4x32_10(c0, c1, c2, (tag << 24) | (j0 >> 1), k0, k1);
+  const uint4 b = philox4x32_10(c0, c1, c2, (tag << 24) | ((j0 >> 1) + 1), k0, k1);
+  u[0] = u01_from_words(a.x, a.y);
+  u[1] = u01_from_words(a.z, a.w);
+  u[2] = u01_from_words(b.x, b.y);
+  u[3] = u01_from_words(b.z, b.w);
+}
+
+// Post-collision uniforms u4 .. u8 of candidate stream (m, cell, step).  FP64:
+// uniforms 4..8 of the stream (blocks 2, 3, 4).  FP32: one block gives
+// u4..u7 from the top 23 bits of its four words and u8 from 23 of the 36
+// unused low bits (9 of word 0, 9 of word 1, 5 of word 2).
+__device__ __forceinline__ void draw_post(uint32_t m, uint32_t cell, uint32_t step, uint32_t k0, uint32_t k1,
+                                          float* u) {
+  const uint4 w = philox4x32_10(m, cell, step, (4u << 24) | 1u, k0, k1);
+  u[0] = u01_from_word(w.x);
+  u[1] = u01_from_word(w.y);
+  u[2] = u01_from_word(w.z);
+  u[3] = u01_from_word(w.w);
+  const uint32_t m8 = ((w.x & 0x1FFu) << 14) | ((w.y & 0x1FFu) << 5) | (w.z & 0x1Fu);
+  u[4] = ((float)m8 + 0.5f) * 0x1p-23f;
+}
+
+__device__ __forceinline__ void draw_post(uint32_t m, uint32_t cell, uint32_t step, uint32_t k0, uint32_t k1,
+                                          double* u) {
+  Stream<double> st(4u, m, cell, step, k0, k1);
+  for (int j = 0; j < 5; ++j) u[j] = st.u(4 + j);
+}
+
 // ---------------------------------------------------------------------------
 // Precision-dispatched math.  FP64 calls the CUDA double functions (the
 // oracle calls the C library ones; both are within a few ulp).  FP32 uses the
@@ -167,6 +209,59 @@ __device__ __forceinline__ int cell_of(const Params<T>& p, T x, T y) {
 }
 
 // ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, cp.async.bulk) into shared memory, completed
+// on an mbarrier.  Addresses and sizes must be multiples of 16 bytes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// generic-proxy accesses to shared memory are ordered before later
+// async-proxy (bulk copy) accesses
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Wait for the phase with the given parity; gives up after `limit` polls
+// (each poll may suspend the thread for a while) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------------------
 // Stage (a): free flight with wall interaction (Sec. 2.2; fully diffuse
 // walls of Sec. 4).  A diffuse wall re-emits with normal speed
 // sqrt(-2 T_w ln u) (flux-weighted half-range Maxwellian), Maxwellian
@@ -174,13 +269,12 @@ __device__ __forceinline__ int cell_of(const Params<T>& p, T x, T y) {
 // at T_w; the particle then flies the rest of the step; at most MAX_HITS hits.
 // tally[w*5 + q]: hits, momentum (3) and energy delivered to wall w.
 // ---------------------------------------------------------------------------
-template <typename T, int DIM>
-__device__ void fly(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& ir, uint32_t idx,
-                    uint32_t cell, uint32_t step, T* tally, unsigned long long* hits_out,
-                    unsigned long long* maxhit_out) {
+template <typename T, int DIM, bool TALLY>
+__device__ void fly_walls(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& ir, uint32_t idx,
+                          uint32_t cell, uint32_t step, T* tally, unsigned long long* hits_out,
+                          unsigned long long* maxhit_out) {
   T t = p.dt;
   int hits = 0;
-  Stream<T> st(TAG_WALL, idx, cell, step, p.k0, p.k1);
   for (;;) {
     const T xn = x + vx * t;
     const T yn = (DIM == 2) ? y + vy * t : y;
@@ -230,7 +324,7 @@ __device__ void fly(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& ir, 
       if (x > p.lx) x = p.lx;
     }
     if (hits == MAX_HITS) {
-      atomicAdd(maxhit_out, 1ull);
+      if (TALLY) atomicAdd(maxhit_out, 1ull);
       break;
     }
     t = t - tw;
@@ -244,8 +338,9 @@ __device__ void fly(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& ir, 
       else vy = -vy;
     } else {
       const T Tw = p.wall_t[w];
-      const T ua = st.u(4 * hits + 0), ub = st.u(4 * hits + 1);
-      const T uc = st.u(4 * hits + 2), ud = st.u(4 * hits + 3);
+      T u4[4];
+      draw4(TAG_WALL, idx, cell, step, 4u * (uint32_t)hits, p.k0, p.k1, u4);
+      const T ua = u4[0], ub = u4[1], uc = u4[2], ud = u4[3];
       const T vn = m_sqrt(T(-2) * Tw * m_log(ua));
       T n1, n2;
       box_muller(ub, uc, &n1, &n2);
@@ -261,16 +356,43 @@ __device__ void fly(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& ir, 
       }
       ir = -Tw * m_log(ud);
     }
-    T* tl = tally + 5 * w;
-    atomicAdd(tl + 0, T(1));
-    atomicAdd(tl + 1, vix - vx);
-    atomicAdd(tl + 2, viy - vy);
-    atomicAdd(tl + 3, viz - vz);
-    atomicAdd(tl + 4, (T(0.5) * (vix * vix + viy * viy + viz * viz) + iri) -
-                          (T(0.5) * (vx * vx + vy * vy + vz * vz) + ir));
+    if (TALLY) {
+      T* tl = tally + 5 * w;
+      atomicAdd(tl + 0, T(1));
+      atomicAdd(tl + 1, vix - vx);
+      atomicAdd(tl + 2, viy - vy);
+      atomicAdd(tl + 3, viz - vz);
+      atomicAdd(tl + 4, (T(0.5) * (vix * vix + viy * viy + viz * viz) + iri) -
+                            (T(0.5) * (vx * vx + vy * vy + vz * vz) + ir));
+    }
     hits += 1;
   }
-  if (hits) atomicAdd(hits_out, (unsigned long long)hits);
+  if (TALLY && hits) atomicAdd(hits_out, (unsigned long long)hits);
+}
+
+// true if a free flight over dt stays inside the domain (no wall is reached)
+template <typename T, int DIM>
+__device__ __forceinline__ bool flight_stays_inside(const Params<T>& p, T x, T y, T vx, T vy, T* xn, T* yn) {
+  *xn = x + vx * p.dt;
+  *yn = (DIM == 2) ? y + vy * p.dt : y;
+  bool in = !(*xn < T(0)) && !(*xn > p.lx);
+  if (DIM == 2) in = in && !(*yn < T(0)) && !(*yn > p.ly);
+  return in;
+}
+
+// Full flight: the common straight flight inline, the wall loop only when a
+// wall is reached (the loop repeats the first straight step identically).
+template <typename T, int DIM, bool TALLY>
+__device__ __forceinline__ void fly(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& ir, uint32_t idx,
+                                    uint32_t cell, uint32_t step, T* tally, unsigned long long* hits_out,
+                                    unsigned long long* maxhit_out) {
+  T xn, yn;
+  if (flight_stays_inside<T, DIM>(p, x, y, vx, vy, &xn, &yn)) {
+    x = xn;
+    y = yn;
+    return;
+  }
+  fly_walls<T, DIM, TALLY>(p, x, y, vx, vy, vz, ir, idx, cell, step, tally, hits_out, maxhit_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -291,30 +413,6 @@ __device__ void fly(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& ir, 
 // ---------------------------------------------------------------------------
 struct CollCount {
   unsigned cand, coll, clip, inel;
-};
-
-template <typename T>
-struct PairDraw;
-
-template <>
-struct PairDraw<float> {
-  // FP32: block 0 = (u0, u1, u2, u3), block 1 = (u4..u7), block 2 = (u8, ...)
-  __device__ static void first(Stream<float>& st, float& u0, float& u1, float& u2, float& u3) {
-    u0 = st.u(0);
-    u1 = st.u(1);
-    u2 = st.u(2);
-    u3 = st.u(3);
-  }
-};
-
-template <>
-struct PairDraw<double> {
-  __device__ static void first(Stream<double>& st, double& u0, double& u1, double& u2, double& u3) {
-    u0 = st.u(0);
-    u1 = st.u(1);
-    u2 = st.u(2);
-    u3 = st.u(3);
-  }
 };
 
 template <typename T>
@@ -343,9 +441,11 @@ __device__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restri
     if (!has) {
       const uint32_t kk = next + (uint32_t)(lane - np);
       if (kk < M) {
-        Stream<T> st(TAG_COLL, kk, cell, step, p.k0, p.k1);
-        T u0, u1;
-        PairDraw<T>::first(st, u0, u1, uacc, uinel);
+        T u4[4];
+        draw4(TAG_COLL, kk, cell, step, 0u, p.k0, p.k1, u4);
+        const T u0 = u4[0], u1 = u4[1];
+        uacc = u4[2];
+        uinel = u4[3];
         int i = (int)(u0 * fn);
         if (i > n - 1) i = n - 1;
         int j = (int)(u1 * fn1);
@@ -386,25 +486,26 @@ __device__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restri
       if (uacc * sgmax < sg) {
         cc.coll += 1;
         if (sg > sgmax) cc.clip += 1;
-        Stream<T> st(TAG_COLL, k, cell, step, p.k0, p.k1);
+        T up[5];
+        draw_post(k, cell, step, p.k0, p.k1, up);
         T et = T(0.25) * g2;
         if (uinel < p.p_inel) {
           const T ec = et + ir[pi];
-          ir[pi] = ec * (T(1) - m_pow(st.u(4), p.bl_exp));
+          ir[pi] = ec * (T(1) - m_pow(up[0], p.bl_exp));
           et = ec - ir[pi];
           cc.inel += 1;
         }
-        if (st.u(5) < p.p_inel) {
+        if (up[1] < p.p_inel) {
           const T ec = et + ir[pj];
-          ir[pj] = ec * (T(1) - m_pow(st.u(6), p.bl_exp));
+          ir[pj] = ec * (T(1) - m_pow(up[2], p.bl_exp));
           et = ec - ir[pj];
           cc.inel += 1;
         }
         const T gn = T(2) * m_sqrt(et);
-        const T cth = T(2) * st.u(7) - T(1);
+        const T cth = T(2) * up[3] - T(1);
         const T sth = m_sqrt(T(1) - cth * cth);
         T sph, cph;
-        m_sincos_2pi(st.u(8), &sph, &cph);
+        m_sincos_2pi(up[4], &sph, &cph);
         const T hx = T(0.5) * gn * cth;
         const T hy = T(0.5) * gn * sth * cph;
         const T hz = T(0.5) * gn * sth * sph;
@@ -444,10 +545,19 @@ __device__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restri
 // Stage (d): raw sums of one cell for Eq. (DSMC_macroscopic), added to
 // Neumaier-compensated FP64 accumulators (acc, comp: 17 per cell).
 // ---------------------------------------------------------------------------
+//
+// FP32 particles: each step's sums go to Kahan-compensated FP32 staging
+// accumulators (stg, stc: 17 per cell; pre32 holds this lane's values loaded
+// earlier); when `flush` is set they are folded into the FP64 accumulators
+// and cleared.  FP64 particles add to the FP64 accumulators every step (pre
+// holds this lane's (acc, comp) loaded earlier, or is null).
 template <typename T>
 __device__ void sample_cell(const T* __restrict__ vx, const T* __restrict__ vy,
                             const T* __restrict__ vz, const T* __restrict__ ir, int n,
-                            double* __restrict__ acc, double* __restrict__ comp) {
+                            double* __restrict__ acc, double* __restrict__ comp,
+                            const double* pre = nullptr, float* __restrict__ stg = nullptr,
+                            float* __restrict__ stc = nullptr, const float* pre32 = nullptr,
+                            bool flush = true) {
   const int lane = threadIdx.x & 31;
   T s[NMOM];
 #pragma unroll
@@ -483,12 +593,30 @@ __device__ void sample_cell(const T* __restrict__ vx, const T* __restrict__ vy,
   for (int q = 0; q < NMOM; ++q)
     if (lane == q) mine = s[q];
   if (lane < NMOM) {
-    const double v = (double)mine;
-    const double a = acc[lane];
+    double v;
+    if (stg) {
+      // Kahan step into the FP32 staging pair
+      const float s0 = pre32[0], c0 = pre32[1];
+      const float yk = (float)mine - c0;
+      const float tk = s0 + yk;
+      const float ck = (tk - s0) - yk;
+      if (!flush) {
+        stg[lane] = tk;
+        stc[lane] = ck;
+        return;
+      }
+      stg[lane] = 0.f;
+      stc[lane] = 0.f;
+      v = (double)tk - (double)ck;
+    } else {
+      v = (double)mine;
+    }
+    const double a = pre ? pre[0] : acc[lane];
+    const double cprev = pre ? pre[1] : comp[lane];
     const double t = a + v;
     const double cmp = (fabs(a) >= fabs(v)) ? ((a - t) + v) : ((v - t) + a);
     acc[lane] = t;
-    comp[lane] += cmp;
+    comp[lane] = cprev + cmp;
   }
 }
 

@@ -53,6 +53,8 @@ struct State {
   T* sgmax;           // ncells
   double* acc;        // ncells x 17
   double* comp;       // ncells x 17
+  float* stg;         // FP32 layout: staged per-step sums (ncells x 17) ...
+  float* stc;         // ... and their Kahan compensations
   double* tally;      // 20
   unsigned long long* stats;  // ST_NSLOTS
   int32_t* flags;     // 16 device words: [0] error bits, [1] total, [2] over-capacity

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) k_move_det(Params<T> p, PBuf<T> b, const 
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     const int c = cellof[s];
     T x = b.x[s], y = b.y[s], vx = b.vx[s], vy = b.vy[s], vz = b.vz[s], ir = b.ir[s];
-    fly<T, DIM>(p, x, y, vx, vy, vz, ir, (uint32_t)(s - start[c]), (uint32_t)c, step, s_tally,
+    fly<T, DIM, true>(p, x, y, vx, vy, vz, ir, (uint32_t)(s - start[c]), (uint32_t)c, step, s_tally,
                 stats + ST_HITS, stats + ST_MAXHIT);
     b.x[s] = x;
     b.y[s] = y;
@@ -215,7 +215,9 @@ __global__ void __launch_bounds__(WPB * 32) k_collide_sample(Params<T> p, PBuf<T
                                                              double* __restrict__ comp,
                                                              uint32_t* __restrict__ owner_g,
                                                              uint32_t step, int flags, int tile,
-                                                             unsigned long long* __restrict__ stats) {
+                                                             unsigned long long* __restrict__ stats,
+                                                             float* __restrict__ stg = nullptr,
+                                                             float* __restrict__ stc = nullptr) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_cnt[4];
   if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
@@ -255,7 +257,20 @@ __global__ void __launch_bounds__(WPB * 32) k_collide_sample(Params<T> p, PBuf<T
       flush_counts<T>(cc, s_cnt);
       __syncwarp();
     }
-    if (flags & 2) sample_cell<T>(vx, vy, vz, ir, n, acc + (size_t)cell * NMOM, comp + (size_t)cell * NMOM);
+    if (flags & 2) {
+      if (stg) {
+        // FP32 staging accumulators: always folded here (last step of a call)
+        float pre32[2] = {0.f, 0.f};
+        if (lane < NMOM) {
+          pre32[0] = stg[(size_t)cell * NMOM + lane];
+          pre32[1] = stc[(size_t)cell * NMOM + lane];
+        }
+        sample_cell<T>(vx, vy, vz, ir, n, acc + (size_t)cell * NMOM, comp + (size_t)cell * NMOM, nullptr,
+                       stg + (size_t)cell * NMOM, stc + (size_t)cell * NMOM, pre32, true);
+      } else {
+        sample_cell<T>(vx, vy, vz, ir, n, acc + (size_t)cell * NMOM, comp + (size_t)cell * NMOM);
+      }
+    }
     if (staged && (flags & 1)) {
       for (int q = lane; q < n; q += 32) {
         b.vx[base + q] = vx[q];
@@ -314,101 +329,230 @@ __device__ __forceinline__ void append_particle(const Params<float>& p, const PB
   }
 }
 
-// flags: 1 collide (step_c), 2 sample, 4 move (step_m) into `out`.
-// Blocks [0, ncell_blocks) take WPB cells each; the remaining blocks move the
-// particles of the input overflow list.
+// Destination of a particle that left cell `cell` for cell `d`, as an index
+// into the 3 x 3 neighbourhood of `cell` (4 = stays), or 9 for a farther cell.
 template <int DIM>
-__global__ void __launch_bounds__(WPB * 32) k_fused(Params<float> p, PBuf<float> in, PBuf<float> out,
-                                                    const int32_t* __restrict__ start,
-                                                    int32_t* __restrict__ cnt_in,
-                                                    int32_t* __restrict__ cnt_out,
-                                                    float* __restrict__ sgmax, double* __restrict__ acc,
-                                                    double* __restrict__ comp,
-                                                    uint32_t* __restrict__ owner_g, Ovf ovi, Ovf ovo,
-                                                    int ovf_cap, uint32_t step_c, uint32_t step_m,
-                                                    int flags, int tile, int ncell_blocks,
-                                                    double* __restrict__ tally_g,
-                                                    unsigned long long* __restrict__ stats) {
+__device__ __forceinline__ int neighbour_code(const Params<float>& p, int ix, int iy, float x, float y) {
+  int jx = (int)(x * p.sx);
+  jx = jx < 0 ? 0 : (jx > p.nx - 1 ? p.nx - 1 : jx);
+  int jy = 0;
+  if (DIM == 2) {
+    jy = (int)(y * p.sy);
+    jy = jy < 0 ? 0 : (jy > p.ny - 1 ? p.ny - 1 : jy);
+  }
+  const int dx = jx - ix, dy = jy - iy;
+  if (dx < -1 || dx > 1 || dy < -1 || dy > 1) return 9;
+  return (dy + 1) * 3 + (dx + 1);
+}
+
+__device__ __forceinline__ int neighbour_cell(int nx, int cell, int code) {
+  return cell + (code / 3 - 1) * nx + (code % 3 - 1);
+}
+
+constexpr int FWPB = 4;                      // warps per CTA of the fused step
+constexpr uint32_t MBAR_POLL_LIMIT = 1u << 22;  // bounded wait for a cell's bulk copies
+
+// shared memory of the fused step: per warp, tile x (vx, vy, vz, I_r, x, y)
+// floats and tile x u32 (collision owners, then destination tags)
+inline size_t fused_smem_bytes(int tile) { return (size_t)FWPB * tile * 28; }
+
+// flags: 1 collide (step_c), 2 sample, 4 move (step_m) into `out`, 8 fold the
+// FP32 staging sums into the FP64 accumulators after sampling.
+// Blocks [0, ncell_blocks) take FWPB cells each, one warp per cell; the
+// remaining blocks move the particles of the input overflow list.
+//
+// Staging: one lane issues bulk asynchronous copies (TMA, cp.async.bulk) of
+// the cell's six arrays into shared memory, completed on the warp's mbarrier,
+// so a cell costs one memory round trip however many particles it holds.
+// Move and append: (M1) fly every particle to find its destination and its
+// rank among the cell's particles bound for the same neighbour (shared-memory
+// counters over the 3 x 3 neighbourhood); (M2) one global atomicAdd per
+// destination bin reserves the slots; (M3) fly again (the same counter-based
+// random stream, so the same result) and store.  Counters are flushed by the
+// last warp of the block to finish, so warps never wait for one another.
+template <int DIM>
+__global__ void __launch_bounds__(FWPB * 32, 8) k_fused(Params<float> p, PBuf<float> in, PBuf<float> out,
+                                                        const int32_t* __restrict__ start,
+                                                        int32_t* __restrict__ cnt_in,
+                                                        int32_t* __restrict__ cnt_out,
+                                                        float* __restrict__ sgmax, double* __restrict__ acc,
+                                                        double* __restrict__ comp,
+                                                        uint32_t* __restrict__ owner_g, Ovf ovi, Ovf ovo,
+                                                        int ovf_cap, uint32_t step_c, uint32_t step_m,
+                                                        int flags, int tile, int ncell_blocks,
+                                                        double* __restrict__ tally_g,
+                                                        unsigned long long* __restrict__ stats,
+                                                        int32_t* __restrict__ errflag, float* __restrict__ stg,
+                                                        float* __restrict__ stc) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_cnt[4];
   __shared__ unsigned s_misc[2];
   __shared__ float s_tally[20];
+  __shared__ unsigned s_done;
+  __shared__ int s_nb[FWPB][4][12];  // per warp: count, base, bin start, bin capacity
+  __shared__ __align__(8) uint64_t s_bar[FWPB];
   if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
   if (threadIdx.x < 2) s_misc[threadIdx.x] = 0;
   if (threadIdx.x < 20) s_tally[threadIdx.x] = 0.f;
+  if (threadIdx.x == 0) s_done = 0;
+  if (threadIdx.x < FWPB) mbar_init(&s_bar[threadIdx.x], 1);
+  mbar_fence_init();
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if ((int)blockIdx.x < ncell_blocks) {
-    const int cell = blockIdx.x * WPB + warp;
+    const int cell = blockIdx.x * FWPB + warp;
     if (cell < p.ncells) {
       const int base = start[cell], n = cnt_in[cell];
-      float* tv = reinterpret_cast<float*>(smem) + (size_t)warp * tile * 4;
-      uint32_t* tow = reinterpret_cast<uint32_t*>(smem + (size_t)WPB * tile * 16) + (size_t)warp * tile;
+      const bool flush = (flags & 8) != 0;
+      double pre[2] = {0.0, 0.0};
+      float pre32[2] = {0.f, 0.f};
+      if ((flags & 2) && lane < NMOM) {
+        pre32[0] = stg[(size_t)cell * NMOM + lane];
+        pre32[1] = stc[(size_t)cell * NMOM + lane];
+        if (flush) {
+          pre[0] = acc[(size_t)cell * NMOM + lane];
+          pre[1] = comp[(size_t)cell * NMOM + lane];
+        }
+      }
+      float* tvx = reinterpret_cast<float*>(smem + (size_t)warp * tile * 28);
+      uint32_t* tow = reinterpret_cast<uint32_t*>(tvx + 6 * tile);
       const bool staged = n <= tile;
-      float *vx, *vy, *vz, *ir;
-      uint32_t* own;
-      if (staged) {
-        vx = tv;
-        vy = tv + tile;
-        vz = tv + 2 * tile;
-        ir = tv + 3 * tile;
-        own = tow;
-        for (int q = lane; q < n; q += 32) {
-          vx[q] = in.vx[base + q];
-          vy[q] = in.vy[base + q];
-          vz[q] = in.vz[base + q];
-          ir[q] = in.ir[base + q];
+      bool ok = true;
+      if (staged && n > 0) {
+        if (lane == 0) {
+          const uint32_t bytes = (uint32_t)((n + 3) & ~3) * 4u;
+          const int narr = (DIM == 2) ? 6 : 5;
+          fence_proxy_async_smem();
+          mbar_arrive_expect_tx(&s_bar[warp], bytes * narr);
+          bulk_g2s(tvx, in.vx + base, bytes, &s_bar[warp]);
+          bulk_g2s(tvx + tile, in.vy + base, bytes, &s_bar[warp]);
+          bulk_g2s(tvx + 2 * tile, in.vz + base, bytes, &s_bar[warp]);
+          bulk_g2s(tvx + 3 * tile, in.ir + base, bytes, &s_bar[warp]);
+          bulk_g2s(tvx + 4 * tile, in.x + base, bytes, &s_bar[warp]);
+          if (DIM == 2) bulk_g2s(tvx + 5 * tile, in.y + base, bytes, &s_bar[warp]);
         }
-      } else {
-        vx = in.vx + base;
-        vy = in.vy + base;
-        vz = in.vz + base;
-        ir = in.ir + base;
-        own = owner_g + base;
+        ok = mbar_wait_bounded(&s_bar[warp], 0u, MBAR_POLL_LIMIT);
+        if (!ok && lane == 0) atomicOr(errflag, 1);
       }
-      __syncwarp();
-      if (flags & 1) {
-        CollCount cc{0, 0, 0, 0};
-        collide_cell<float>(p, vx, vy, vz, ir, n, (uint32_t)cell, step_c, sgmax + cell, own, cc);
-        flush_counts<float>(cc, s_cnt);
-        __syncwarp();
-      }
-      if (flags & 2) sample_cell<float>(vx, vy, vz, ir, n, acc + (size_t)cell * NMOM, comp + (size_t)cell * NMOM);
-      if (flags & 4) {
-        const int nr = (n + 31) & ~31;
-        for (int q = lane; q < nr; q += 32) {
-          const bool active = q < n;
-          float x = 0.f, y = 0.f, a = 0.f, bb = 0.f, c = 0.f, e = 0.f;
-          int d = 0;
-          if (active) {
-            x = in.x[base + q];
-            if (DIM == 2) y = in.y[base + q];
-            a = vx[q];
-            bb = vy[q];
-            c = vz[q];
-            e = ir[q];
-            fly<float, DIM>(p, x, y, a, bb, c, e, (uint32_t)q, (uint32_t)cell, step_m, s_tally,
-                            stats + ST_HITS, stats + ST_MAXHIT);
-            d = cell_of<float, DIM>(p, x, y);
+      ok = __all_sync(FULL, ok);
+      if (ok) {
+        float *vx, *vy, *vz, *ir;
+        const float *px, *py;
+        uint32_t* own;
+        if (staged) {
+          vx = tvx;
+          vy = tvx + tile;
+          vz = tvx + 2 * tile;
+          ir = tvx + 3 * tile;
+          px = tvx + 4 * tile;
+          py = tvx + 5 * tile;
+          own = tow;
+        } else {
+          vx = in.vx + base;
+          vy = in.vy + base;
+          vz = in.vz + base;
+          ir = in.ir + base;
+          px = in.x + base;
+          py = in.y + base;
+          own = owner_g + base;
+        }
+        if (flags & 1) {
+          CollCount cc{0, 0, 0, 0};
+          collide_cell<float>(p, vx, vy, vz, ir, n, (uint32_t)cell, step_c, sgmax + cell, own, cc);
+          flush_counts<float>(cc, s_cnt);
+          __syncwarp();
+        }
+        if (flags & 2)
+          sample_cell<float>(vx, vy, vz, ir, n, acc + (size_t)cell * NMOM, comp + (size_t)cell * NMOM, pre,
+                             stg + (size_t)cell * NMOM, stc + (size_t)cell * NMOM, pre32, flush);
+        if (flags & 4) {
+          int* nb_cnt = s_nb[warp][0];
+          int* nb_base = s_nb[warp][1];
+          int* nb_s0 = s_nb[warp][2];
+          int* nb_cap = s_nb[warp][3];
+          if (lane < 12) nb_cnt[lane] = 0;
+          __syncwarp();
+          // M1: destinations and ranks; a particle that reaches a wall is
+          // placed individually in M3 (code 9)
+          const int cix = cell % p.nx, ciy = cell / p.nx;
+          for (int q = lane; q < n; q += 32) {
+            float xn, yn;
+            int code = 9;
+            if (flight_stays_inside<float, DIM>(p, px[q], (DIM == 2) ? py[q] : 0.f, vx[q], vy[q], &xn, &yn))
+              code = neighbour_code<DIM>(p, cix, ciy, xn, yn);
+            const int r = atomicAdd(&nb_cnt[code], 1);
+            own[q] = ((uint32_t)code << 24) | (uint32_t)r;
           }
-          append_particle<DIM>(p, out, start, cnt_out, ovo, ovf_cap, active, d, x, y, a, bb, c, e, s_misc);
-        }
-        __syncwarp();
-        if (lane == 0) cnt_in[cell] = 0;
-      } else if (staged && (flags & 1)) {
-        for (int q = lane; q < n; q += 32) {
-          in.vx[base + q] = vx[q];
-          in.vy[base + q] = vy[q];
-          in.vz[base + q] = vz[q];
-          in.ir[base + q] = ir[q];
+          __syncwarp();
+          // M2: reserve the slots, one atomic per destination bin
+          if (lane < 9 && nb_cnt[lane] > 0) {
+            const int d = neighbour_cell(p.nx, cell, lane);
+            nb_base[lane] = atomicAdd(&cnt_out[d], nb_cnt[lane]);
+            const int s0 = start[d];
+            nb_s0[lane] = s0;
+            nb_cap[lane] = start[d + 1] - s0;
+          }
+          __syncwarp();
+          // M3: fly again (identical result) with wall tallies, and store
+          for (int q = lane; q < n; q += 32) {
+            float x = px[q], y = (DIM == 2) ? py[q] : 0.f;
+            float a = vx[q], b = vy[q], c = vz[q], e = ir[q];
+            fly<float, DIM, true>(p, x, y, a, b, c, e, (uint32_t)q, (uint32_t)cell, step_m, s_tally,
+                                  stats + ST_HITS, stats + ST_MAXHIT);
+            const uint32_t tag = own[q];
+            const int code = (int)(tag >> 24), r = (int)(tag & 0xFFFFFFu);
+            int d, slot, s0, cap;
+            if (code < 9) {
+              d = neighbour_cell(p.nx, cell, code);
+              slot = nb_base[code] + r;
+              s0 = nb_s0[code];
+              cap = nb_cap[code];
+            } else {
+              d = cell_of<float, DIM>(p, x, y);
+              slot = atomicAdd(&cnt_out[d], 1);
+              s0 = start[d];
+              cap = start[d + 1] - s0;
+            }
+            if (slot < cap) {
+              const int w = s0 + slot;
+              out.x[w] = x;
+              if (DIM == 2) out.y[w] = y;
+              out.vx[w] = a;
+              out.vy[w] = b;
+              out.vz[w] = c;
+              out.ir[w] = e;
+              if (slot >= cap - 8) atomicAdd(s_misc + 1, 1u);
+            } else {
+              const int qo = atomicAdd(ovo.count, 1);
+              atomicAdd(s_misc + 0, 1u);
+              if (qo < ovf_cap) {
+                ovo.x[qo] = x;
+                ovo.y[qo] = y;
+                ovo.vx[qo] = a;
+                ovo.vy[qo] = b;
+                ovo.vz[qo] = c;
+                ovo.ir[qo] = e;
+                ovo.dest[qo] = d;
+              }
+            }
+          }
+          __syncwarp();
+          if (lane == 0) cnt_in[cell] = 0;
+        } else if (staged && (flags & 1)) {
+          for (int q = lane; q < n; q += 32) {
+            in.vx[base + q] = vx[q];
+            in.vy[base + q] = vy[q];
+            in.vz[base + q] = vz[q];
+            in.ir[base + q] = ir[q];
+          }
         }
       }
     }
   } else if (flags & 4) {
     // overflow list of the previous step: move and append (no collision)
     const int nov = min(*ovi.count, ovf_cap);
-    const int gw = (blockIdx.x - ncell_blocks) * WPB + warp;
-    const int nwarps = (gridDim.x - ncell_blocks) * WPB;
+    const int gw = (blockIdx.x - ncell_blocks) * FWPB + warp;
+    const int nwarps = (gridDim.x - ncell_blocks) * FWPB;
     for (int base = gw * 32; base < nov; base += nwarps * 32) {
       const int q = base + lane;
       const bool active = q < nov;
@@ -421,19 +565,26 @@ __global__ void __launch_bounds__(WPB * 32) k_fused(Params<float> p, PBuf<float>
         bb = ovi.vy[q];
         c = ovi.vz[q];
         e = ovi.ir[q];
-        fly<float, DIM>(p, x, y, a, bb, c, e, (uint32_t)q, (uint32_t)(p.ncells + 1), step_m, s_tally,
-                        stats + ST_HITS, stats + ST_MAXHIT);
+        fly<float, DIM, true>(p, x, y, a, bb, c, e, (uint32_t)q, (uint32_t)(p.ncells + 1), step_m, s_tally,
+                              stats + ST_HITS, stats + ST_MAXHIT);
         d = cell_of<float, DIM>(p, x, y);
       }
       append_particle<DIM>(p, out, start, cnt_out, ovo, ovf_cap, active, d, x, y, a, bb, c, e, s_misc);
     }
   }
-  __syncthreads();
-  if (threadIdx.x < 4 && s_cnt[threadIdx.x]) atomicAdd(stats + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
-  if (threadIdx.x == 4 && s_misc[0]) atomicAdd(stats + ST_OVF, (unsigned long long)s_misc[0]);
-  if (threadIdx.x == 5 && s_misc[1]) atomicAdd(stats + ST_NEARFULL, (unsigned long long)s_misc[1]);
-  if (threadIdx.x >= 32 && threadIdx.x < 52 && s_tally[threadIdx.x - 32] != 0.f)
-    atomicAdd(tally_g + (threadIdx.x - 32), (double)s_tally[threadIdx.x - 32]);
+  // the last warp of the block to finish flushes the block's counters
+  __syncwarp();
+  __threadfence_block();
+  unsigned done = 0;
+  if (lane == 0) done = atomicAdd(&s_done, 1u);
+  done = __shfl_sync(FULL, done, 0);
+  if (done == FWPB - 1) {
+    __threadfence_block();
+    if (lane < 4 && s_cnt[lane]) atomicAdd(stats + lane, (unsigned long long)s_cnt[lane]);
+    if (lane == 4 && s_misc[0]) atomicAdd(stats + ST_OVF, (unsigned long long)s_misc[0]);
+    if (lane == 5 && s_misc[1]) atomicAdd(stats + ST_NEARFULL, (unsigned long long)s_misc[1]);
+    if (lane < 20 && s_tally[lane] != 0.f) atomicAdd(tally_g + lane, (double)s_tally[lane]);
+  }
 }
 
 static __global__ void k_zero_i32(int32_t* a, int n) {
@@ -810,34 +961,42 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
                        int do_sample, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
     if (nsteps <= 0) return;
-    const int cblocks = (p.ncells + WPB - 1) / WPB;
-    const int oblocks = 4;
+    const int cblocks = (p.ncells + FWPB - 1) / FWPB;
+    const int oblocks = 8;
     const size_t sm = tile_smem<T>(s.tile);
+    const size_t smf = fused_smem_bytes(s.tile);
     auto launch = [&](int flags, uint32_t sc, uint32_t sm_step) {
       const int other = cur ^ 1;
       if (p.dim == 1)
-        k_fused<1><<<cblocks + oblocks, WPB * 32, sm, st>>>(
+        k_fused<1><<<cblocks + oblocks, FWPB * 32, smf, st>>>(
             p, s.buf[cur], s.buf[other], s.start[lay], s.count[cur], s.count[other], s.sgmax, s.acc, s.comp,
-            s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats);
+            s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats,
+            s.flags + 8, s.stg, s.stc);
       else
-        k_fused<2><<<cblocks + oblocks, WPB * 32, sm, st>>>(
+        k_fused<2><<<cblocks + oblocks, FWPB * 32, smf, st>>>(
             p, s.buf[cur], s.buf[other], s.start[lay], s.count[cur], s.count[other], s.sgmax, s.acc, s.comp,
-            s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats);
+            s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats,
+            s.flags + 8, s.stg, s.stc);
       // the input overflow list has been consumed
       cudaMemsetAsync(s.ovf[cur].count, 0, sizeof(int32_t), st);
       cur = other;
     };
     // move of step0, then per step: collide (+sample) of step k and move of step k+1
     launch(4, step0, step0);
+    // sampled sums are staged in FP32 and folded into FP64 every
+    // STAGE_STEPS steps and on the last step of the call
+    constexpr int STAGE_STEPS = 16;
     for (int i = 0; i < nsteps; ++i) {
       const bool last = (i == nsteps - 1);
       const uint32_t sc = step0 + (uint32_t)i;
       if (!last) {
-        launch(1 | (do_sample ? 2 : 0) | 4, sc, sc + 1);
+        const int fold = ((i + 1) % STAGE_STEPS == 0) ? 8 : 0;
+        launch(1 | (do_sample ? 2 | fold : 0) | 4, sc, sc + 1);
       } else {
-        k_collide_sample<T><<<cblocks, WPB * 32, sm, st>>>(p, s.buf[cur], s.start[lay], s.count[cur], s.sgmax,
+        const int wblocks = (p.ncells + WPB - 1) / WPB;
+        k_collide_sample<T><<<wblocks, WPB * 32, sm, st>>>(p, s.buf[cur], s.start[lay], s.count[cur], s.sgmax,
                                                           s.acc, s.comp, s.owner, sc, 1 | (do_sample ? 2 : 0),
-                                                          s.tile, s.stats);
+                                                          s.tile, s.stats, s.stg, s.stc);
       }
     }
   } else {
@@ -972,8 +1131,9 @@ void Ops<T>::configure(int tile) {
   cudaFuncSetAttribute(k_dig_apply<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
   cudaFuncSetAttribute(k_dig_apply<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
   if constexpr (sizeof(T) == 4) {
-    cudaFuncSetAttribute(k_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    const int smf = (int)fused_smem_bytes(tile);
+    cudaFuncSetAttribute(k_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf);
+    cudaFuncSetAttribute(k_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf);
   }
 }
 
