@@ -177,7 +177,7 @@ int dig_correct(dsmc_handle *h, const double *dev_target);
  * stream (a cudaStream_t or NULL).  It calls no cudaMalloc, cudaFree or
  * allocating library routine.
  *  - Scratch: the solver's Newton scratch lives in one fixed device array in
- *    the library (about 1.5 MB, enough for DSMC_SYNTH_NOALLOC_MAX_CELLS
+ *    the library (about 1.8 MB, enough for DSMC_SYNTH_NOALLOC_MAX_CELLS
  *    cells); every GPU that loads the library holds it until the process
  *    exits.  nx above DSMC_SYNTH_NOALLOC_MAX_CELLS returns DSMC_ERR_CAPACITY
  *    and launches nothing.

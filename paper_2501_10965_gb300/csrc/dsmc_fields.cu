@@ -266,209 +266,374 @@ __device__ __forceinline__ void mv4(const double* a, const double* x, double* y)
   }
 }
 
-size_t synth1d_work_doubles(int n) { return (size_t)n * (4 * 6 + 16 * 4 + 4) + 64; }
+// Work layout (doubles unless noted), n cells:
+//   y (4n), yn (4n), R (4n), G (4n, dR/dP), h (4n, dR_P/dy), J (48n: A, B, C
+//   blocks, row-major 4x4), scalars (32); then FP32 cyclic-reduction
+//   storage: A, B, C, Binv (16n floats each), r1, r2 (4n floats each).
+size_t synth1d_work_doubles(int n) { return (size_t)n * (20 + 48) + 32 + ((size_t)n * 72 + 1) / 2 + 64; }
 
-__global__ void __launch_bounds__(256) k_synth1d(SynthArgs a, double* __restrict__ out, double* __restrict__ work,
-                                                 int n_m, double tol, double* __restrict__ info) {
-  const CellParams& cp = a.cp;
-  const int n = cp.nx;
-  double* y = work;             // 4n
-  double* R = y + 4 * n;        // 4n
-  double* Gp = R + 4 * n;       // 4n  dR_i/dP
-  double* z1 = Gp + 4 * n;      // 4n
-  double* z2 = z1 + 4 * n;      // 4n
-  double* yn = z2 + 4 * n;      // 4n
-  double* A = yn + 4 * n;       // 16n dR_i/dy_{i-1}
-  double* B = A + 16 * n;       // 16n dR_i/dy_i
-  double* C = B + 16 * n;       // 16n dR_i/dy_{i+1}
-  double* W = C + 16 * n;       // 16n Thomas: inverse of the reduced diagonal
-  double* hvec = W + 16 * n;    // 4n  dR_P/dy_i
-  __shared__ double s_P, s_M, s_red[256];
-  __shared__ int s_done, s_it, s_bad;
+struct SynthWork {
+  double *y, *yn, *R, *G, *h, *J, *sc;
+  float *A, *B, *C, *Bi, *r1, *r2;
+};
+
+__host__ __device__ inline SynthWork synth_work(double* w, int n) {
+  SynthWork s;
+  s.y = w;
+  s.yn = s.y + 4 * n;
+  s.R = s.yn + 4 * n;
+  s.G = s.R + 4 * n;
+  s.h = s.G + 4 * n;
+  s.J = s.h + 4 * n;
+  s.sc = s.J + 48 * n;
+  float* f = reinterpret_cast<float*>(s.sc + 32);
+  s.A = f;
+  s.B = s.A + 16 * n;
+  s.C = s.B + 16 * n;
+  s.Bi = s.C + 16 * n;
+  s.r1 = s.Bi + 16 * n;
+  s.r2 = s.r1 + 4 * n;
+  return s;
+}
+
+// scalar slots: 0 P, 1 mass, 2 done, 3 iterations, 4 status (0 converged,
+// 1 not (yet) converged, 2 numeric), 5 last max relative change
+enum { SC_P = 0, SC_M = 1, SC_DONE = 2, SC_IT = 3, SC_STATUS = 4, SC_DMAX = 5 };
+
+__device__ double block_sum(double v, double* red) {
   const int tid = threadIdx.x;
-  for (int i = tid; i < n; i += blockDim.x) {
-    const double* f = a.F + (size_t)i * 18;
-    y[4 * i + 0] = f[2];
-    y[4 * i + 1] = f[3];
-    y[4 * i + 2] = f[4];
-    y[4 * i + 3] = f[5];
+  red[tid] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (tid < o) red[tid] += red[tid + o];
+    __syncthreads();
   }
-  // sampled mass and the initial P (mean of rho T_t + HoT_xx)
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ double block_max(double v, double* red) {
+  const int tid = threadIdx.x;
+  red[tid] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (tid < o) red[tid] = fmax(red[tid], red[tid + o]);
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(1024) k_synth_init(SynthArgs a, double* work) {
+  __shared__ double red[1024];
+  const int n = a.cp.nx;
+  SynthWork w = synth_work(work, n);
   double m = 0.0, pm = 0.0;
-  for (int i = tid; i < n; i += blockDim.x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double* f = a.F + (size_t)i * 18;
-    m += f[0] * cp.dx;
+    w.y[4 * i + 0] = f[2];
+    w.y[4 * i + 1] = f[3];
+    w.y[4 * i + 2] = f[4];
+    w.y[4 * i + 3] = f[5];
+    m += f[0] * a.cp.dx;
     pm += f[0] * f[4] + a.hot[(size_t)i * 12];
   }
-  s_red[tid] = m;
+  const double M = block_sum(m, red);
+  const double PM = block_sum(pm, red);
+  if (threadIdx.x == 0) {
+    w.sc[SC_P] = PM / n;
+    w.sc[SC_M] = M;
+    w.sc[SC_DONE] = 0.0;
+    w.sc[SC_IT] = 0.0;
+    w.sc[SC_STATUS] = 1.0;
+    w.sc[SC_DMAX] = 0.0;
+  }
+}
+
+// one thread per (cell, column): columns 0..11 are d R_i / d(y_{i-1}, y_i,
+// y_{i+1}) by central differences, column 12 is dR_i/dP together with R_i
+// and the mass-row entries.
+__global__ void k_synth_jac(SynthArgs a, double* work) {
+  const int n = a.cp.nx;
+  SynthWork w = synth_work(work, n);
+  if (w.sc[SC_DONE] != 0.0) return;
+  const double P = w.sc[SC_P];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * 13) return;
+  const int i = t / 13, col = t % 13;
+  double ym[4], y0[4], yp[4], rp[4], rm[4];
+  for (int v = 0; v < 4; ++v) {
+    y0[v] = w.y[4 * i + v];
+    ym[v] = (i > 0) ? w.y[4 * (i - 1) + v] : y0[v];
+    yp[v] = (i < n - 1) ? w.y[4 * (i + 1) + v] : y0[v];
+  }
+  if (col < 12) {
+    const int blk = col / 4, v = col % 4;
+    double* J = w.J + 48 * (size_t)i + 16 * blk;
+    const bool exists = (blk == 1) || (blk == 0 && i > 0) || (blk == 2 && i < n - 1);
+    if (!exists) {
+      for (int r = 0; r < 4; ++r) J[r * 4 + v] = 0.0;
+      return;
+    }
+    double* yy = (blk == 0) ? ym : ((blk == 1) ? y0 : yp);
+    const double sv = yy[v];
+    const double hh = 1e-6 * fmax(fabs(sv), 1.0);
+    yy[v] = sv + hh;
+    local_res(a, i, n, ym, y0, yp, P, rp);
+    yy[v] = sv - hh;
+    local_res(a, i, n, ym, y0, yp, P, rm);
+    for (int r = 0; r < 4; ++r) J[r * 4 + v] = (rp[r] - rm[r]) / (2.0 * hh);
+  } else {
+    local_res(a, i, n, ym, y0, yp, P, w.R + 4 * i);
+    const double hP = 1e-6 * fmax(fabs(P), 1.0);
+    local_res(a, i, n, ym, y0, yp, P + hP, rp);
+    local_res(a, i, n, ym, y0, yp, P - hP, rm);
+    for (int r = 0; r < 4; ++r) w.G[4 * i + r] = (rp[r] - rm[r]) / (2.0 * hP);
+    const double Hi = a.hot[(size_t)i * 12];
+    w.h[4 * i + 0] = 0.0;
+    w.h[4 * i + 1] = 0.0;
+    w.h[4 * i + 2] = -a.cp.dx * (P - Hi) / (y0[2] * y0[2]);
+    w.h[4 * i + 3] = 0.0;
+  }
+}
+
+__device__ void inv4f(const float* m, float* r) {
+  float a[4][8];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      a[i][j] = m[i * 4 + j];
+      a[i][4 + j] = (i == j) ? 1.f : 0.f;
+    }
+  for (int c = 0; c < 4; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < 4; ++i)
+      if (fabsf(a[i][c]) > fabsf(a[piv][c])) piv = i;
+    if (piv != c)
+      for (int j = 0; j < 8; ++j) {
+        const float t = a[c][j];
+        a[c][j] = a[piv][j];
+        a[piv][j] = t;
+      }
+    const float d = a[c][c];
+    for (int j = 0; j < 8; ++j) a[c][j] /= d;
+    for (int i = 0; i < 4; ++i)
+      if (i != c) {
+        const float fct = a[i][c];
+        for (int j = 0; j < 8; ++j) a[i][j] -= fct * a[c][j];
+      }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) r[i * 4 + j] = a[i][4 + j];
+}
+
+__device__ __forceinline__ void mm4f(const float* a, const float* b, float* c) {
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      float s = 0.f;
+      for (int k = 0; k < 4; ++k) s += a[i * 4 + k] * b[k * 4 + j];
+      c[i * 4 + j] = s;
+    }
+}
+
+__device__ __forceinline__ void mv4f(const float* a, const float* x, float* y) {
+  for (int i = 0; i < 4; ++i) {
+    float s = 0.f;
+    for (int k = 0; k < 4; ++k) s += a[i * 4 + k] * x[k];
+    y[i] = s;
+  }
+}
+
+// Newton update: block cyclic reduction (FP32) of J z1 = -R, J z2 = G; the
+// bordered mass row in FP64; a damped update that keeps rho, T positive.
+__global__ void __launch_bounds__(1024) k_synth_solve(SynthArgs a, double* work, int n_m, double tol) {
+  __shared__ double red[1024];
+  const int n = a.cp.nx;
+  SynthWork w = synth_work(work, n);
+  if (w.sc[SC_DONE] != 0.0) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double P = w.sc[SC_P];
+  for (int i = tid; i < n; i += nt) {
+    for (int q = 0; q < 16; ++q) {
+      w.A[16 * i + q] = (float)w.J[48 * (size_t)i + q];
+      w.B[16 * i + q] = (float)w.J[48 * (size_t)i + 16 + q];
+      w.C[16 * i + q] = (float)w.J[48 * (size_t)i + 32 + q];
+    }
+    for (int v = 0; v < 4; ++v) {
+      w.r1[4 * i + v] = (float)(-w.R[4 * i + v]);
+      w.r2[4 * i + v] = (float)w.G[4 * i + v];
+    }
+  }
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (tid < o) s_red[tid] += s_red[tid + o];
+  // forward reduction: at stride s the rows i = 2s-1 (mod 2s) eliminate their
+  // neighbours i -/+ s, which keep their equations for back substitution
+  int s = 1;
+  for (; 2 * s - 1 < n; s *= 2) {
+    for (int j = s - 1 + tid * 2 * s; j < n; j += nt * 2 * s) inv4f(w.B + 16 * j, w.Bi + 16 * j);
     __syncthreads();
-  }
-  if (tid == 0) s_M = s_red[0];
-  __syncthreads();
-  s_red[tid] = pm;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (tid < o) s_red[tid] += s_red[tid + o];
-    __syncthreads();
-  }
-  if (tid == 0) {
-    s_P = s_red[0] / n;
-    s_done = 0;
-    s_it = 0;
-    s_bad = 0;
-  }
-  __syncthreads();
-  for (int it = 1; it <= n_m; ++it) {
-    const double P = s_P;
-    // residuals, local Jacobian blocks and the border
-    for (int i = tid; i < n; i += blockDim.x) {
-      double ym[4], y0[4], yp[4];
+    for (int i = 2 * s - 1 + tid * 2 * s; i < n; i += nt * 2 * s) {
+      const int lo = i - s, hi = i + s;
+      float al[16], ga[16], t1[16], t2[16];
+      mm4f(w.A + 16 * i, w.Bi + 16 * lo, al);
+      for (int q = 0; q < 16; ++q) al[q] = -al[q];
+      float Bn[16], An[16], Cn[16], x1[4], x2[4], v1[4], v2[4];
+      mm4f(al, w.A + 16 * lo, An);
+      mm4f(al, w.C + 16 * lo, t1);
+      for (int q = 0; q < 16; ++q) Bn[q] = w.B[16 * i + q] + t1[q];
+      mv4f(al, w.r1 + 4 * lo, v1);
+      mv4f(al, w.r2 + 4 * lo, v2);
       for (int v = 0; v < 4; ++v) {
-        y0[v] = y[4 * i + v];
-        ym[v] = (i > 0) ? y[4 * (i - 1) + v] : y0[v];
-        yp[v] = (i < n - 1) ? y[4 * (i + 1) + v] : y0[v];
+        x1[v] = w.r1[4 * i + v] + v1[v];
+        x2[v] = w.r2[4 * i + v] + v2[v];
       }
-      local_res(a, i, n, ym, y0, yp, P, R + 4 * i);
-      double rp[4], rm[4];
-      for (int blk = 0; blk < 3; ++blk) {
-        double* J = (blk == 0 ? A : (blk == 1 ? B : C)) + 16 * i;
-        double* yy = (blk == 0 ? ym : (blk == 1 ? y0 : yp));
-        const bool exists = (blk == 1) || (blk == 0 && i > 0) || (blk == 2 && i < n - 1);
+      if (hi < n) {
+        mm4f(w.C + 16 * i, w.Bi + 16 * hi, ga);
+        for (int q = 0; q < 16; ++q) ga[q] = -ga[q];
+        mm4f(ga, w.C + 16 * hi, Cn);
+        mm4f(ga, w.A + 16 * hi, t2);
+        for (int q = 0; q < 16; ++q) Bn[q] += t2[q];
+        mv4f(ga, w.r1 + 4 * hi, v1);
+        mv4f(ga, w.r2 + 4 * hi, v2);
         for (int v = 0; v < 4; ++v) {
-          if (!exists) {
-            for (int r = 0; r < 4; ++r) J[r * 4 + v] = 0.0;
-            continue;
-          }
-          const double sv = yy[v];
-          const double h = 1e-6 * fmax(fabs(sv), 1.0);
-          yy[v] = sv + h;
-          local_res(a, i, n, ym, y0, yp, P, rp);
-          yy[v] = sv - h;
-          local_res(a, i, n, ym, y0, yp, P, rm);
-          yy[v] = sv;
-          for (int r = 0; r < 4; ++r) J[r * 4 + v] = (rp[r] - rm[r]) / (2.0 * h);
+          x1[v] += v1[v];
+          x2[v] += v2[v];
         }
-      }
-      const double hP = 1e-6 * fmax(fabs(P), 1.0);
-      local_res(a, i, n, ym, y0, yp, P + hP, rp);
-      local_res(a, i, n, ym, y0, yp, P - hP, rm);
-      for (int r = 0; r < 4; ++r) Gp[4 * i + r] = (rp[r] - rm[r]) / (2.0 * hP);
-      // mass row: d(sum rho dx)/dT_t,i = -dx (P - H_i)/T_t,i^2
-      const double Hi = a.hot[(size_t)i * 12];
-      hvec[4 * i + 0] = 0.0;
-      hvec[4 * i + 1] = 0.0;
-      hvec[4 * i + 2] = -cp.dx * (P - Hi) / (y0[2] * y0[2]);
-      hvec[4 * i + 3] = 0.0;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      // mass residual and dR_P/dP
-      double mass = 0.0, dP = 0.0;
-      for (int i = 0; i < n; ++i) {
-        const double Hi = a.hot[(size_t)i * 12];
-        mass += (P - Hi) / y[4 * i + 2] * cp.dx;
-        dP += cp.dx / y[4 * i + 2];
-      }
-      const double RP = mass - s_M;
-      // block Thomas for T z1 = -R and T z2 = Gp
-      for (int i = 0; i < n; ++i) {
-        double Bi[16], r1[4], r2[4];
-        for (int q = 0; q < 16; ++q) Bi[q] = B[16 * i + q];
-        for (int v = 0; v < 4; ++v) {
-          r1[v] = -R[4 * i + v];
-          r2[v] = Gp[4 * i + v];
-        }
-        if (i > 0) {
-          // Bi -= A_i W_{i-1} C_{i-1};  r -= A_i W_{i-1} r_{i-1}
-          double AW[16], AWC[16], t1[4], t2[4];
-          mm4(A + 16 * i, W + 16 * (i - 1), AW);
-          mm4(AW, C + 16 * (i - 1), AWC);
-          for (int q = 0; q < 16; ++q) Bi[q] -= AWC[q];
-          mv4(AW, z1 + 4 * (i - 1), t1);
-          mv4(AW, z2 + 4 * (i - 1), t2);
-          for (int v = 0; v < 4; ++v) {
-            r1[v] -= t1[v];
-            r2[v] -= t2[v];
-          }
-        }
-        inv4(Bi, W + 16 * i);
-        for (int v = 0; v < 4; ++v) {
-          z1[4 * i + v] = r1[v];
-          z2[4 * i + v] = r2[v];
-        }
-      }
-      // back substitution: x_i = W_i (r_i - C_i x_{i+1})
-      for (int i = n - 1; i >= 0; --i) {
-        double t1[4], t2[4];
-        for (int v = 0; v < 4; ++v) {
-          t1[v] = z1[4 * i + v];
-          t2[v] = z2[4 * i + v];
-        }
-        if (i < n - 1) {
-          double c1[4], c2[4];
-          mv4(C + 16 * i, z1 + 4 * (i + 1), c1);
-          mv4(C + 16 * i, z2 + 4 * (i + 1), c2);
-          for (int v = 0; v < 4; ++v) {
-            t1[v] -= c1[v];
-            t2[v] -= c2[v];
-          }
-        }
-        mv4(W + 16 * i, t1, z1 + 4 * i);
-        mv4(W + 16 * i, t2, z2 + 4 * i);
-      }
-      // bordered correction: [T g; h^T d] [dy; dP] = [-R; -RP]
-      double hz1 = 0.0, hz2 = 0.0;
-      for (int i = 0; i < n; ++i)
-        for (int v = 0; v < 4; ++v) {
-          hz1 += hvec[4 * i + v] * z1[4 * i + v];
-          hz2 += hvec[4 * i + v] * z2[4 * i + v];
-        }
-      const double dPstep = (-RP - hz1) / (dP - hz2);
-      // damped update keeping rho > 0, T > 0
-      double lam = 1.0;
-      int ok = 0;
-      for (int tries = 0; tries < 40 && !ok; ++tries) {
-        ok = 1;
-        const double Pn = P + lam * dPstep;
-        for (int i = 0; i < n && ok; ++i) {
-          for (int v = 0; v < 4; ++v) yn[4 * i + v] = y[4 * i + v] + lam * (z1[4 * i + v] - z2[4 * i + v] * dPstep);
-          const double rho = (Pn - a.hot[(size_t)i * 12]) / yn[4 * i + 2];
-          if (!(yn[4 * i + 2] > 0.0) || !(yn[4 * i + 3] > 0.0) || !(rho > 0.0)) ok = 0;
-        }
-        if (!ok) lam *= 0.5;
-      }
-      double dmax = 0.0;
-      if (ok) {
-        for (int i = 0; i < n; ++i)
-          for (int v = 0; v < 4; ++v) {
-            const double d = fabs(yn[4 * i + v] - y[4 * i + v]) / fmax(fabs(y[4 * i + v]), 1e-3);
-            dmax = fmax(dmax, d);
-            y[4 * i + v] = yn[4 * i + v];
-          }
-        const double Pn = P + lam * dPstep;
-        dmax = fmax(dmax, fabs(Pn - P) / fmax(fabs(P), 1e-3));
-        s_P = Pn;
       } else {
-        s_bad = 1;
+        for (int q = 0; q < 16; ++q) Cn[q] = 0.f;
       }
-      s_it = it;
-      if (!ok || dmax < tol) s_done = 1;
+      for (int q = 0; q < 16; ++q) {
+        w.A[16 * i + q] = An[q];
+        w.B[16 * i + q] = Bn[q];
+        w.C[16 * i + q] = Cn[q];
+      }
+      for (int v = 0; v < 4; ++v) {
+        w.r1[4 * i + v] = x1[v];
+        w.r2[4 * i + v] = x2[v];
+      }
     }
     __syncthreads();
-    if (s_done) break;
   }
-  // final residual and output
-  const double P = s_P;
+  // the last remaining row (index s-1) is solved directly; z lives in r1, r2
+  if (tid == 0) {
+    const int i = s - 1;
+    float x1[4], x2[4];
+    inv4f(w.B + 16 * i, w.Bi + 16 * i);
+    mv4f(w.Bi + 16 * i, w.r1 + 4 * i, x1);
+    mv4f(w.Bi + 16 * i, w.r2 + 4 * i, x2);
+    for (int v = 0; v < 4; ++v) {
+      w.r1[4 * i + v] = x1[v];
+      w.r2[4 * i + v] = x2[v];
+    }
+  }
+  __syncthreads();
+  for (s /= 2; s >= 1; s /= 2) {
+    for (int j = s - 1 + tid * 2 * s; j < n; j += nt * 2 * s) {
+      float t1[4], t2[4], c1[4], c2[4];
+      for (int v = 0; v < 4; ++v) {
+        t1[v] = w.r1[4 * j + v];
+        t2[v] = w.r2[4 * j + v];
+      }
+      if (j - s >= 0) {
+        mv4f(w.A + 16 * j, w.r1 + 4 * (j - s), c1);
+        mv4f(w.A + 16 * j, w.r2 + 4 * (j - s), c2);
+        for (int v = 0; v < 4; ++v) {
+          t1[v] -= c1[v];
+          t2[v] -= c2[v];
+        }
+      }
+      if (j + s < n) {
+        mv4f(w.C + 16 * j, w.r1 + 4 * (j + s), c1);
+        mv4f(w.C + 16 * j, w.r2 + 4 * (j + s), c2);
+        for (int v = 0; v < 4; ++v) {
+          t1[v] -= c1[v];
+          t2[v] -= c2[v];
+        }
+      }
+      mv4f(w.Bi + 16 * j, t1, c1);
+      mv4f(w.Bi + 16 * j, t2, c2);
+      for (int v = 0; v < 4; ++v) {
+        w.r1[4 * j + v] = c1[v];
+        w.r2[4 * j + v] = c2[v];
+      }
+    }
+    __syncthreads();
+  }
+  // bordered correction in FP64: [J G; h^T d] [dy; dP] = [-R; -(mass - M)]
+  double mass = 0.0, dP = 0.0, hz1 = 0.0, hz2 = 0.0;
+  for (int i = tid; i < n; i += nt) {
+    const double Hi = a.hot[(size_t)i * 12];
+    mass += (P - Hi) / w.y[4 * i + 2] * a.cp.dx;
+    dP += a.cp.dx / w.y[4 * i + 2];
+    for (int v = 0; v < 4; ++v) {
+      hz1 += w.h[4 * i + v] * (double)w.r1[4 * i + v];
+      hz2 += w.h[4 * i + v] * (double)w.r2[4 * i + v];
+    }
+  }
+  mass = block_sum(mass, red);
+  dP = block_sum(dP, red);
+  hz1 = block_sum(hz1, red);
+  hz2 = block_sum(hz2, red);
+  const double RP = mass - w.sc[SC_M];
+  const double dPstep = (-RP - hz1) / (dP - hz2);
+  double lam = 1.0;
+  int ok = 0;
+  for (int tries = 0; tries < 40; ++tries) {
+    const double Pn = P + lam * dPstep;
+    int bad = 0;
+    for (int i = tid; i < n; i += nt) {
+      for (int v = 0; v < 4; ++v)
+        w.yn[4 * i + v] = w.y[4 * i + v] + lam * ((double)w.r1[4 * i + v] - (double)w.r2[4 * i + v] * dPstep);
+      const double rho = (Pn - a.hot[(size_t)i * 12]) / w.yn[4 * i + 2];
+      if (!(w.yn[4 * i + 2] > 0.0) || !(w.yn[4 * i + 3] > 0.0) || !(rho > 0.0)) bad = 1;
+    }
+    ok = !__syncthreads_or(bad);
+    if (ok) break;
+    lam *= 0.5;
+  }
+  double dmax = 0.0;
+  if (ok) {
+    for (int i = tid; i < n; i += nt)
+      for (int v = 0; v < 4; ++v) {
+        dmax = fmax(dmax, fabs(w.yn[4 * i + v] - w.y[4 * i + v]) / fmax(fabs(w.y[4 * i + v]), 1e-3));
+        w.y[4 * i + v] = w.yn[4 * i + v];
+      }
+  }
+  dmax = block_max(dmax, red);
+  if (tid == 0) {
+    const double it = w.sc[SC_IT] + 1.0;
+    w.sc[SC_IT] = it;
+    if (!ok) {
+      w.sc[SC_STATUS] = 2.0;
+      w.sc[SC_DONE] = 1.0;
+    } else {
+      const double Pn = P + lam * dPstep;
+      dmax = fmax(dmax, fabs(Pn - P) / fmax(fabs(P), 1e-3));
+      w.sc[SC_P] = Pn;
+      w.sc[SC_DMAX] = dmax;
+      if (dmax < tol) {
+        w.sc[SC_STATUS] = 0.0;
+        w.sc[SC_DONE] = 1.0;
+      } else if (it >= n_m) {
+        w.sc[SC_DONE] = 1.0;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_synth_final(SynthArgs a, double* work, double* out, int n_m,
+                                                      double* info) {
+  __shared__ double red[1024];
+  const int n = a.cp.nx;
+  SynthWork w = synth_work(work, n);
+  const double P = w.sc[SC_P];
   double rmax = 0.0;
-  for (int i = tid; i < n; i += blockDim.x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double ym[4], y0[4], yp[4], r[4];
     for (int v = 0; v < 4; ++v) {
-      y0[v] = y[4 * i + v];
-      ym[v] = (i > 0) ? y[4 * (i - 1) + v] : y0[v];
-      yp[v] = (i < n - 1) ? y[4 * (i + 1) + v] : y0[v];
+      y0[v] = w.y[4 * i + v];
+      ym[v] = (i > 0) ? w.y[4 * (i - 1) + v] : y0[v];
+      yp[v] = (i < n - 1) ? w.y[4 * (i + 1) + v] : y0[v];
     }
     local_res(a, i, n, ym, y0, yp, P, r);
     for (int v = 0; v < 4; ++v) rmax = fmax(rmax, fabs(r[v]));
@@ -480,23 +645,39 @@ __global__ void __launch_bounds__(256) k_synth1d(SynthArgs a, double* __restrict
     o[4] = y0[2];
     o[5] = y0[3];
   }
-  s_red[tid] = rmax;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (tid < o) s_red[tid] = fmax(s_red[tid], s_red[tid + o]);
-    __syncthreads();
-  }
-  if (tid == 0) {
-    info[0] = (double)s_it;
-    info[1] = s_red[0];
-    info[2] = s_bad ? 2.0 : (s_done ? 0.0 : 1.0);  // 0 converged, 1 not converged, 2 numeric
+  rmax = block_max(rmax, red);
+  if (threadIdx.x == 0) {
+    info[0] = w.sc[SC_IT];
+    info[1] = rmax;
+    // 0 converged, 1 not converged, 2 numeric
+    info[2] = w.sc[SC_STATUS];  // 0 converged, 1 iteration cap, 2 numeric
   }
 }
 
+// Newton iterations are launched in batches of 4 (a converged solve makes the
+// remaining launches return at once); the host reads the done flag between
+// batches.
 void launch_synth1d(const CellParams& cp, const double* fields, const double* hot, double* out, double* work,
                     int n_m, double tol, double* dev_info, cudaStream_t st) {
   SynthArgs a{cp, fields, hot};
-  k_synth1d<<<1, 256, 0, st>>>(a, out, work, n_m, tol, dev_info);
+  const int n = cp.nx;
+  SynthWork w = synth_work(work, n);
+  k_synth_init<<<1, 1024, 0, st>>>(a, work);
+  const int jt = 128, jb = (n * 13 + jt - 1) / jt;
+  int it = 0;
+  while (it < n_m) {
+    const int batch = (n_m - it) < 4 ? (n_m - it) : 4;
+    for (int b = 0; b < batch; ++b) {
+      k_synth_jac<<<jb, jt, 0, st>>>(a, work);
+      k_synth_solve<<<1, 1024, 0, st>>>(a, work, n_m, tol);
+    }
+    it += batch;
+    double done = 0.0;
+    cudaMemcpyAsync(&done, w.sc + SC_DONE, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    if (done != 0.0) break;
+  }
+  k_synth_final<<<1, 1024, 0, st>>>(a, work, out, n_m, dev_info);
 }
 
 }  // namespace dsmc

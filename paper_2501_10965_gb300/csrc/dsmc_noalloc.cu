@@ -7,7 +7,7 @@
 // or code that runs where cudaMalloc is not allowed (for example while a
 // stream is being captured).  This variant takes the configuration and the
 // field arrays directly and keeps the solver's scratch (the Newton iterate,
-// residuals, Jacobian blocks and the block-Thomas factors) in a fixed,
+// residuals, Jacobian blocks and the cyclic-reduction factors) in a fixed,
 // file-scope device array instead.  That array belongs to the library: every
 // GPU that loads the library holds it until the process exits.
 #include <cmath>
@@ -22,8 +22,8 @@
 namespace {
 
 // scratch doubles for DSMC_SYNTH_NOALLOC_MAX_CELLS cells (the solver needs
-// 92 per cell + 64) plus 8 for the iteration count / residual / status
-constexpr size_t kScratchDoubles = (size_t)DSMC_SYNTH_NOALLOC_MAX_CELLS * 96 + 128;
+// 104 per cell + 96) plus 8 for the iteration count / residual / status
+constexpr size_t kScratchDoubles = (size_t)DSMC_SYNTH_NOALLOC_MAX_CELLS * 112 + 256;
 constexpr size_t kInfoOffset = kScratchDoubles - 8;
 
 static __device__ __align__(256) double g_synth_scratch[kScratchDoubles];
