@@ -108,6 +108,22 @@ int dsmc_workspace_size(const dsmc_config *cfg, size_t *bytes);
 int dsmc_init(const dsmc_config *cfg, void *dev_workspace, size_t bytes, void *stream,
               dsmc_handle **out);
 
+/* A batch: ncases independent simulations (cfgs[0..ncases-1], same dim and
+ * precision; each with its own cells, gas, walls, time step, particles per
+ * cell and seed) held by one handle and advanced together, one kernel launch
+ * per stage for all of them.  Cells are numbered case after case: case k owns
+ * the cfgs[k].nx * ny cells that follow those of cases 0..k-1, and every
+ * array argument of the calls below (fields, HoT, targets, accumulators,
+ * (sigma g)_max) uses that numbering.  Random streams are keyed by each
+ * case's seed and its own cell numbers, so in FP64-deterministic mode a case
+ * evolves exactly as it would alone.  synth_solve solves every slab;
+ * dsmc_set_particles is not available for a batch.  The paper has no batch
+ * mode: it is how dozens of uneven cases (or replicas for ensemble averages)
+ * share the GPU. */
+int dsmc_batch_workspace_size(const dsmc_config *cfgs, int ncases, size_t *bytes);
+int dsmc_batch_init(const dsmc_config *cfgs, int ncases, void *dev_workspace, size_t bytes,
+                    void *stream, dsmc_handle **out);
+
 /* Release the handle (host memory only; the workspace stays the caller's). */
 int dsmc_destroy(dsmc_handle *h);
 
@@ -146,7 +162,10 @@ int dsmc_hot(dsmc_handle *h, const double *dev_fields, double *dev_hot, double *
  * iterations.  dev_out is ncells x DSMC_NTARGET.  host_iters / host_resid
  * (may be NULL) receive the iteration count and the final max |residual|.
  * Returns DSMC_ERR_NOT_CONVERGED (outputs written) when n_m is reached, and
- * DSMC_ERR_NUMERIC if the solution leaves rho > 0, T > 0. */
+ * DSMC_ERR_NUMERIC when no Newton update keeps rho > 0 and T > 0 (noisy HoT
+ * can make rho = (P - HoT_xx) / T_t negative); such a slab's output is its
+ * sampled fields, so that the outputs can still serve as dig_correct
+ * targets.  In a batch the worst status of the slabs is returned. */
 int synth_solve(dsmc_handle *h, const double *dev_fields, const double *dev_hot, double *dev_out,
                 int *host_iters, double *host_resid);
 

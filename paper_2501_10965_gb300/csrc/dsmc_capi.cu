@@ -2,9 +2,11 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -14,7 +16,17 @@
 using namespace dsmc;
 
 struct dsmc_handle {
-  dsmc_config cfg;
+  dsmc_config cfg;              // case 0 (the simulation, for a single case)
+  std::vector<dsmc_config> cfgs;  // every case
+  std::vector<int32_t> cell0;     // host copy of the case offsets (ncases + 1)
+  std::vector<int32_t> nx;        // cells per case
+  int ncases = 1;
+  Params<double>* d_pd = nullptr;  // device tables (see dsmc::Cases)
+  Params<float>* d_pf = nullptr;
+  CellParams* d_cp = nullptr;
+  int32_t* d_cell0 = nullptr;
+  int32_t* d_cell_case = nullptr;
+  int64_t* d_woff = nullptr;
   int ncells = 0;
   int det = 1;
   cudaStream_t stream = nullptr;
@@ -155,21 +167,31 @@ void carve_state(Carver& cv, const Plan& pl, State<T>& s) {
   s.tile = pl.tile;
 }
 
-Plan make_plan(const dsmc_config* c, char* base, dsmc_handle* h) {
+Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
   Plan pl{};
-  pl.ncells = c->nx * (c->dim == 2 ? c->ny : 1);
-  pl.det = c->precision == DSMC_PREC_FP64_DET;
-  const int64_t n0 = (int64_t)pl.ncells * c->ppc;
-  if (pl.det) {
-    pl.capacity = c->capacity > 0 ? c->capacity : 2 * n0 + 64;
-  } else {
-    const int64_t bins = (int64_t)pl.ncells * host_bin_cap(c->ppc, c->bin_slack);
-    pl.capacity = c->capacity > 0 ? c->capacity : bins + bins / 4 + 1024;
+  pl.det = cs[0].precision == DSMC_PREC_FP64_DET;
+  pl.ncells = 0;
+  int64_t capacity = 0;
+  int tile = 64;
+  size_t synth = 0;
+  for (int k = 0; k < ncases; ++k) {
+    const dsmc_config* c = &cs[k];
+    const int nc = c->nx * (c->dim == 2 ? c->ny : 1);
+    pl.ncells += nc;
+    const int64_t n0 = (int64_t)nc * c->ppc;
+    if (pl.det) {
+      capacity += c->capacity > 0 ? c->capacity : 2 * n0 + 64;
+    } else {
+      const int64_t bins = (int64_t)nc * host_bin_cap(c->ppc, c->bin_slack);
+      capacity += c->capacity > 0 ? c->capacity : bins + bins / 4 + 1024;
+    }
+    // particles staged per warp: room for density fluctuations above ppc;
+    // larger cells are processed in global memory
+    int t = pl.det ? 2 * c->ppc : (5 * c->ppc) / 4 + 32;
+    if (t > tile) tile = t;
+    if (c->dim == 1) synth += synth1d_work_doubles(nc);
   }
-  // particles staged per warp: room for density fluctuations above ppc;
-  // larger cells are processed in global memory
-  int tile = pl.det ? 2 * c->ppc : (5 * c->ppc) / 4 + 32;
-  if (tile < 64) tile = 64;
+  pl.capacity = capacity;
   tile = pl.det ? (tile + 31) & ~31 : (tile + 15) & ~15;  // FP32: 16-float multiple for bulk copies
   const int tmax = pl.det ? 256 : 512;
   if (tile > tmax) tile = tmax;
@@ -177,19 +199,31 @@ Plan make_plan(const dsmc_config* c, char* base, dsmc_handle* h) {
   pl.ovf_cap = pl.det ? 1 : (int)(pl.capacity / 16 + 1024);
   Carver cv{base};
   if (pl.det) {
-    State<double> s{};
-    carve_state(cv, pl, s);
-    if (h) h->sd = s;
+    State<double> st{};
+    carve_state(cv, pl, st);
+    if (h) h->sd = st;
   } else {
-    State<float> s{};
-    carve_state(cv, pl, s);
-    if (h) h->sf = s;
+    State<float> st{};
+    carve_state(cv, pl, st);
+    if (h) h->sf = st;
   }
-  double* sw = cv.take<double>(c->dim == 1 ? synth1d_work_doubles(pl.ncells) : 1);
-  double* si = cv.take<double>(8);
+  double* sw = cv.take<double>(synth > 0 ? synth : 1);
+  double* si = cv.take<double>(3 * (size_t)ncases + 8);
+  Params<double>* pd = cv.take<Params<double>>(ncases);
+  Params<float>* pf = cv.take<Params<float>>(ncases);
+  CellParams* cp = cv.take<CellParams>(ncases);
+  int32_t* c0 = cv.take<int32_t>(ncases + 1);
+  int32_t* cc = cv.take<int32_t>(pl.ncells);
+  int64_t* wo = cv.take<int64_t>(ncases);
   if (h) {
     h->synth_work = sw;
     h->synth_info = si;
+    h->d_pd = pd;
+    h->d_pf = pf;
+    h->d_cp = cp;
+    h->d_cell0 = c0;
+    h->d_cell_case = cc;
+    h->d_woff = wo;
   }
   pl.bytes = cv.off + 256;
   return pl;
@@ -233,6 +267,10 @@ void fill_params(const dsmc_config* c, Params<T>& p, CellParams& cp) {
   }
   p.k0 = (uint32_t)(c->seed & 0xffffffffu);
   p.k1 = (uint32_t)(c->seed >> 32);
+  p.ppc = c->ppc;
+  p.init_tt = (T)c->init_tt;
+  p.init_tr = (T)c->init_tr;
+  for (int q = 0; q < 3; ++q) p.init_u[q] = (T)c->init_u[q];
   // FP64 cell parameters
   cp.dim = c->dim;
   cp.nx = c->nx;
@@ -278,10 +316,10 @@ __global__ void k_fill(T* a, int n, T v) {
 }
 
 template <typename T>
-int init_state(dsmc_handle* h, State<T>& s, Params<T>& p) {
-  const dsmc_config* c = &h->cfg;
+int init_state(dsmc_handle* h, State<T>& s, Params<T>& p0, Params<T>* d_p) {
   cudaStream_t st = h->stream;
   const int nc = h->ncells;
+  const int ncases = h->ncases;
   cudaMemsetAsync(s.stats, 0, sizeof(unsigned long long) * ST_NSLOTS, st);
   cudaMemsetAsync(s.tally, 0, sizeof(double) * 20, st);
   cudaMemsetAsync(s.flags, 0, sizeof(int32_t) * 16, st);
@@ -297,23 +335,106 @@ int init_state(dsmc_handle* h, State<T>& s, Params<T>& p) {
   }
   cudaMemsetAsync(s.buf[0].y, 0, sizeof(T) * (size_t)s.capacity, st);
   cudaMemsetAsync(s.buf[1].y, 0, sizeof(T) * (size_t)s.capacity, st);
-  double csd;
-  {
-    Params<double> pd;
-    CellParams cpd;
-    fill_params<double>(c, pd, cpd);
-    csd = (double)pd.c_sigma;
+  // per-case tables, per-cell layout and (sigma g)_max
+  std::vector<Params<T>> pt(ncases);
+  std::vector<Params<double>> pdv(ncases);
+  std::vector<CellParams> cpt(ncases);
+  std::vector<int32_t> cell_case(nc), start(nc + 1);
+  std::vector<T> sg(nc);
+  std::vector<int64_t> woff(ncases);
+  int64_t total = 0, wacc = 0;
+  int32_t slot = 0;
+  for (int k = 0; k < ncases; ++k) {
+    const dsmc_config* c = &h->cfgs[k];
+    fill_params<T>(c, pt[k], cpt[k]);
+    fill_params<double>(c, pdv[k], cpt[k]);
+    const int32_t cap0 = h->det ? c->ppc : host_bin_cap(c->ppc, c->bin_slack);
+    const T sg0 = (T)sgmax0(c, (double)pdv[k].c_sigma);
+    for (int i = h->cell0[k]; i < h->cell0[k + 1]; ++i) {
+      cell_case[i] = k;
+      start[i] = slot;
+      slot += cap0;
+      sg[i] = sg0;
+    }
+    total += (int64_t)(h->cell0[k + 1] - h->cell0[k]) * c->ppc;
+    woff[k] = wacc;
+    if (c->dim == 1) wacc += (int64_t)synth1d_work_doubles(h->nx[k]);
   }
-  k_fill<T><<<(nc + 255) / 256, 256, 0, st>>>(s.sgmax, nc, (T)sgmax0(c, csd));
-  // layout: compact (det) or padded bins of equal capacity (FP32)
-  const int32_t cap0 = h->det ? c->ppc : host_bin_cap(c->ppc, c->bin_slack);
-  if ((int64_t)cap0 * nc > s.capacity) return set_err(h, DSMC_ERR_CAPACITY, "initial bins need %lld slots, capacity %lld", (long long)cap0 * nc, (long long)s.capacity);
+  start[nc] = slot;
+  if ((int64_t)slot > s.capacity)
+    return set_err(h, DSMC_ERR_CAPACITY, "initial bins need %lld slots, capacity %lld", (long long)slot,
+                   (long long)s.capacity);
+  cudaMemcpyAsync(d_p, pt.data(), sizeof(Params<T>) * ncases, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->d_cp, cpt.data(), sizeof(CellParams) * ncases, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->d_cell0, h->cell0.data(), sizeof(int32_t) * (ncases + 1), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->d_cell_case, cell_case.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->d_woff, woff.data(), sizeof(int64_t) * ncases, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(s.start[0], start.data(), sizeof(int32_t) * (nc + 1), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(s.sgmax, sg.data(), sizeof(T) * nc, cudaMemcpyHostToDevice, st);
+  s.cases = Cases<T>{d_p, h->d_cp, h->d_cell0, h->d_cell_case, ncases};
+  s.batch = ncases > 1;
+  s.ncells = nc;
   h->cur = 0;
   h->lay = 0;
-  Ops<T>::init(p, s, 0, 0, c->ppc, cap0, c->init_tt, c->init_tr, c->init_u, st);
-  s.nparticles = nc * c->ppc;
-  s.slack = c->bin_slack;
+  Ops<T>::init_batch(p0, s, nc, 0, 0, st);
+  s.nparticles = (int)total;
+  s.slack = h->cfgs[0].bin_slack;
+  // the host vectors above must outlive the copies
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_err(h, DSMC_ERR_CUDA, "dsmc_init: %s", cudaGetErrorString(e));
   return check_cuda(h, "dsmc_init");
+}
+
+int init_cases(const dsmc_config* cfgs, int ncases, void* dev_workspace, size_t bytes, void* stream,
+               dsmc_handle** out) {
+  if (!out || !cfgs || ncases < 1) return DSMC_ERR_ARG;
+  *out = nullptr;
+  char why[256];
+  for (int k = 0; k < ncases; ++k) {
+    const int rc = validate(&cfgs[k], why, sizeof why);
+    if (rc) return rc;
+    if (cfgs[k].dim != cfgs[0].dim || cfgs[k].precision != cfgs[0].precision) return DSMC_ERR_ARG;
+  }
+  const Plan pl = make_plan(cfgs, ncases, nullptr, nullptr);
+  if (!dev_workspace || bytes < pl.bytes) return DSMC_ERR_ARG;
+  dsmc_handle* h = new (std::nothrow) dsmc_handle();
+  if (!h) return DSMC_ERR_ARG;
+  h->cfgs.assign(cfgs, cfgs + ncases);
+  h->ncases = ncases;
+  h->cell0.assign(ncases + 1, 0);
+  h->nx.assign(ncases, 0);
+  for (int k = 0; k < ncases; ++k) {
+    dsmc_config& c = h->cfgs[k];
+    if (c.dim == 1) {
+      c.ny = 1;
+      c.ly = 1.0;
+    }
+    h->nx[k] = c.nx;
+    h->cell0[k + 1] = h->cell0[k] + c.nx * c.ny;
+  }
+  h->cfg = h->cfgs[0];
+  h->ncells = pl.ncells;
+  h->det = pl.det;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->ws = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(dev_workspace) + 255) & ~(uintptr_t)255);
+  h->ws_bytes = bytes;
+  make_plan(h->cfgs.data(), ncases, h->ws, h);
+  fill_params<double>(&h->cfg, h->pd, h->cp);
+  fill_params<float>(&h->cfg, h->pf, h->cp);
+  int r;
+  if (h->det) {
+    Ops<double>::configure(pl.tile);
+    r = init_state<double>(h, h->sd, h->pd, h->d_pd);
+  } else {
+    Ops<float>::configure(pl.tile);
+    r = init_state<float>(h, h->sf, h->pf, h->d_pf);
+  }
+  if (r) {
+    delete h;
+    return r;
+  }
+  *out = h;
+  return DSMC_OK;
 }
 
 }  // namespace
@@ -322,52 +443,28 @@ int init_state(dsmc_handle* h, State<T>& s, Params<T>& p) {
 extern "C" {
 
 int dsmc_workspace_size(const dsmc_config* cfg, size_t* bytes) {
-  char why[256];
-  if (!bytes) return DSMC_ERR_ARG;
-  const int rc = validate(cfg, why, sizeof why);
-  if (rc) return rc;
-  *bytes = make_plan(cfg, nullptr, nullptr).bytes;
-  return DSMC_OK;
+  return dsmc_batch_workspace_size(cfg, 1, bytes);
 }
 
 int dsmc_init(const dsmc_config* cfg, void* dev_workspace, size_t bytes, void* stream, dsmc_handle** out) {
-  if (!out) return DSMC_ERR_ARG;
-  *out = nullptr;
+  return init_cases(cfg, 1, dev_workspace, bytes, stream, out);
+}
+
+int dsmc_batch_workspace_size(const dsmc_config* cfgs, int ncases, size_t* bytes) {
   char why[256];
-  const int rc = validate(cfg, why, sizeof why);
-  if (rc) return rc;
-  const Plan pl = make_plan(cfg, nullptr, nullptr);
-  if (!dev_workspace || bytes < pl.bytes) return DSMC_ERR_ARG;
-  dsmc_handle* h = new (std::nothrow) dsmc_handle();
-  if (!h) return DSMC_ERR_ARG;
-  h->cfg = *cfg;
-  if (h->cfg.dim == 1) {
-    h->cfg.ny = 1;
-    h->cfg.ly = 1.0;
+  if (!bytes || !cfgs || ncases < 1) return DSMC_ERR_ARG;
+  for (int k = 0; k < ncases; ++k) {
+    const int rc = validate(&cfgs[k], why, sizeof why);
+    if (rc) return rc;
+    if (cfgs[k].dim != cfgs[0].dim || cfgs[k].precision != cfgs[0].precision) return DSMC_ERR_ARG;
   }
-  h->ncells = pl.ncells;
-  h->det = pl.det;
-  h->stream = reinterpret_cast<cudaStream_t>(stream);
-  h->ws = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(dev_workspace) + 255) & ~(uintptr_t)255);
-  h->ws_bytes = bytes;
-  make_plan(&h->cfg, h->ws, h);
-  fill_params<double>(&h->cfg, h->pd, h->cp);
-  fill_params<float>(&h->cfg, h->pf, h->cp);
-  int r;
-  if (h->det) {
-    Ops<double>::configure(pl.tile);
-    r = init_state<double>(h, h->sd, h->pd);
-  } else {
-    Ops<float>::configure(pl.tile);
-    r = init_state<float>(h, h->sf, h->pf);
-  }
-  if (r) {
-    const int code = r;
-    delete h;
-    return code;
-  }
-  *out = h;
+  *bytes = make_plan(cfgs, ncases, nullptr, nullptr).bytes;
   return DSMC_OK;
+}
+
+int dsmc_batch_init(const dsmc_config* cfgs, int ncases, void* dev_workspace, size_t bytes, void* stream,
+                    dsmc_handle** out) {
+  return init_cases(cfgs, ncases, dev_workspace, bytes, stream, out);
 }
 
 int dsmc_destroy(dsmc_handle* h) {
@@ -419,7 +516,7 @@ int dsmc_sample(dsmc_handle* h, double* dev_fields, int reset) {
   if (!h || !dev_fields) return set_err(h, DSMC_ERR_ARG, "bad arguments");
   const double* acc = h->det ? h->sd.acc : h->sf.acc;
   double* comp = h->det ? h->sd.comp : h->sf.comp;
-  launch_fields(h->cp, acc, comp, h->nsamples, dev_fields, h->stream);
+  launch_fields(h->d_cp, h->d_cell_case, h->ncells, acc, comp, h->nsamples, dev_fields, h->stream);
   if (reset) {
     cudaMemsetAsync(const_cast<double*>(acc), 0, sizeof(double) * h->ncells * NMOM, h->stream);
     cudaMemsetAsync(comp, 0, sizeof(double) * h->ncells * NMOM, h->stream);
@@ -430,34 +527,49 @@ int dsmc_sample(dsmc_handle* h, double* dev_fields, int reset) {
 
 int dsmc_hot(dsmc_handle* h, const double* dev_fields, double* dev_hot, double* dev_kngll, uint8_t* dev_mask) {
   if (!h || !dev_fields || !dev_hot) return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  launch_hot(h->cp, dev_fields, dev_hot, dev_kngll, dev_mask, h->stream);
+  launch_hot(h->d_cp, h->d_cell_case, h->d_cell0, h->ncells, dev_fields, dev_hot, dev_kngll, dev_mask, h->stream);
   return check_cuda(h, "dsmc_hot");
 }
 
 int synth_solve(dsmc_handle* h, const double* dev_fields, const double* dev_hot, double* dev_out, int* host_iters,
                 double* host_resid) {
   if (!h || !dev_fields || !dev_hot || !dev_out) return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  if (h->cfg.dim != 1) return set_err(h, DSMC_ERR_ARG, "synth_solve: only the 1D slab is implemented");
-  if (h->ncells < 3) return set_err(h, DSMC_ERR_ARG, "synth_solve needs at least 3 cells");
-  const int n_m = h->cfg.n_m > 0 ? h->cfg.n_m : 2000;
-  const double tol = h->cfg.synth_tol > 0 ? h->cfg.synth_tol : 1e-5;
-  launch_synth1d(h->cp, dev_fields, dev_hot, dev_out, h->synth_work, n_m, tol, h->synth_info, h->stream);
-  double info[3] = {0, 0, 0};
-  cudaMemcpyAsync(info, h->synth_info, sizeof info, cudaMemcpyDeviceToHost, h->stream);
+  int n_m = 0;
+  double tol = 1.0;
+  for (int k = 0; k < h->ncases; ++k) {
+    const dsmc_config& c = h->cfgs[k];
+    if (c.dim != 1) return set_err(h, DSMC_ERR_ARG, "synth_solve: only the 1D slab is implemented");
+    if (c.nx < 3) return set_err(h, DSMC_ERR_ARG, "synth_solve needs at least 3 cells per slab");
+    const int nm = c.n_m > 0 ? c.n_m : 2000;
+    const double tl = c.synth_tol > 0 ? c.synth_tol : 1e-5;
+    if (nm > n_m) n_m = nm;
+    if (tl < tol) tol = tl;
+  }
+  launch_synth1d(h->d_cp, h->d_cell_case, h->d_cell0, h->ncases, h->ncells, h->nx.data(), dev_fields, dev_hot,
+                 dev_out, h->synth_work, h->d_woff, n_m, tol, h->synth_info, h->stream);
+  std::vector<double> info(3 * (size_t)h->ncases);
+  cudaMemcpyAsync(info.data(), h->synth_info, sizeof(double) * info.size(), cudaMemcpyDeviceToHost, h->stream);
   const int r = sync_check(h, "synth_solve");
   if (r) return r;
-  if (host_iters) *host_iters = (int)info[0];
-  if (host_resid) *host_resid = info[1];
-  if (info[2] == 2.0) return set_err(h, DSMC_ERR_NUMERIC, "synth_solve: no update keeps rho, T positive");
-  if (info[2] == 1.0) return set_err(h, DSMC_ERR_NOT_CONVERGED, "synth_solve: %d iterations without convergence", n_m);
+  int its = 0, worst = 0;
+  double res = 0.0;
+  for (int k = 0; k < h->ncases; ++k) {
+    its = std::max(its, (int)info[3 * k]);
+    res = std::max(res, info[3 * k + 1]);
+    worst = std::max(worst, (int)info[3 * k + 2]);
+  }
+  if (host_iters) *host_iters = its;
+  if (host_resid) *host_resid = res;
+  if (worst == 2) return set_err(h, DSMC_ERR_NUMERIC, "synth_solve: no update keeps rho, T positive");
+  if (worst == 1) return set_err(h, DSMC_ERR_NOT_CONVERGED, "synth_solve: %d iterations without convergence", n_m);
   return DSMC_OK;
 }
 
 int dig_correct(dsmc_handle* h, const double* dev_target) {
   if (!h || !dev_target) return set_err(h, DSMC_ERR_ARG, "bad arguments");
   int32_t fl[4] = {0, 0, 0, 0};
-  if (h->det) Ops<double>::dig_counts(h->cp, h->sd, h->lay, dev_target, h->dig_iter, 1, h->stream);
-  else Ops<float>::dig_counts(h->cp, h->sf, h->lay, dev_target, h->dig_iter, 0, h->stream);
+  if (h->det) Ops<double>::dig_counts(h->sd, h->ncells, h->lay, dev_target, h->dig_iter, 1, h->stream);
+  else Ops<float>::dig_counts(h->sf, h->ncells, h->lay, dev_target, h->dig_iter, 0, h->stream);
   int32_t* flags = h->det ? h->sd.flags : h->sf.flags;
   cudaMemcpyAsync(fl, flags, sizeof fl, cudaMemcpyDeviceToHost, h->stream);
   int r = sync_check(h, "dig_correct (counts)");
@@ -465,10 +577,10 @@ int dig_correct(dsmc_handle* h, const double* dev_target) {
   if (fl[0] & 1) return set_err(h, DSMC_ERR_NUMERIC, "dig_correct: non-finite or non-positive target");
   if (fl[0] & 6) return set_err(h, DSMC_ERR_CAPACITY, "dig_correct: new particle count does not fit");
   if (h->det) {
-    Ops<double>::dig_apply(h->cp, h->sd, h->cur, h->lay, dev_target, h->dig_iter, 1, h->stream);
+    Ops<double>::dig_apply(h->cp, h->sd, h->ncells, h->cur, h->lay, dev_target, h->dig_iter, 1, h->stream);
     h->sd.nparticles = fl[1];
   } else {
-    Ops<float>::dig_apply(h->cp, h->sf, h->cur, h->lay, dev_target, h->dig_iter, 0, h->stream);
+    Ops<float>::dig_apply(h->cp, h->sf, h->ncells, h->cur, h->lay, dev_target, h->dig_iter, 0, h->stream);
     h->sf.nparticles = fl[3];
   }
   h->dig_iter += 1;
@@ -507,6 +619,7 @@ int dsmc_set_particles(dsmc_handle* h, int64_t n, const double* x, const double*
                        const double* vy, const double* vz, const double* ir) {
   if (!h || n < 0 || (n > 0 && (!x || !vx || !vy || !vz || !ir || (h->cfg.dim == 2 && !y))))
     return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (h->ncases > 1) return set_err(h, DSMC_ERR_ARG, "dsmc_set_particles: not available for a batch of cases");
   const int64_t cap = h->det ? h->sd.capacity : h->sf.capacity;
   if (n > cap) return set_err(h, DSMC_ERR_CAPACITY, "%lld particles exceed capacity %lld", (long long)n, (long long)cap);
   int32_t* flags = h->det ? h->sd.flags : h->sf.flags;

@@ -38,6 +38,8 @@ struct Params {
   T wall_t[4];
   T wall_u[4][3];
   uint32_t k0, k1;
+  int ppc;                           // initial particles per cell
+  T init_tt, init_tr, init_u[3];     // initial equilibrium state
 };
 
 // Per-step device counters (unsigned long long so they can be added atomically).

@@ -15,9 +15,11 @@ namespace dsmc {
 // fields from the accumulated raw sums (time average over nsamples steps;
 // central moments about the averaged velocity)
 // ---------------------------------------------------------------------------
-__global__ void k_fields(CellParams cp, const double* __restrict__ acc, const double* __restrict__ comp,
-                         double nsamples, double* __restrict__ out) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cp.ncells; c += gridDim.x * blockDim.x) {
+__global__ void k_fields(const CellParams* __restrict__ cps, const int32_t* __restrict__ cell_case, int ncells,
+                         const double* __restrict__ acc, const double* __restrict__ comp, double nsamples,
+                         double* __restrict__ out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+    const CellParams& cp = cps[cell_case[c]];
     double a[NMOM];
     for (int q = 0; q < NMOM; ++q) a[q] = acc[(size_t)c * NMOM + q] + comp[(size_t)c * NMOM + q];
     double* f = out + (size_t)c * 18;
@@ -62,10 +64,10 @@ __global__ void k_fields(CellParams cp, const double* __restrict__ acc, const do
   }
 }
 
-void launch_fields(const CellParams& cp, const double* acc, const double* comp, int64_t nsamples, double* out,
-                   cudaStream_t st) {
-  const int g = (cp.ncells + 255) / 256;
-  k_fields<<<g > 0 ? g : 1, 256, 0, st>>>(cp, acc, comp, (double)nsamples, out);
+void launch_fields(const CellParams* cp, const int32_t* cell_case, int ncells, const double* acc, const double* comp,
+                   int64_t nsamples, double* out, cudaStream_t st) {
+  const int g = (ncells + 255) / 256;
+  k_fields<<<g > 0 ? g : 1, 256, 0, st>>>(cp, cell_case, ncells, acc, comp, (double)nsamples, out);
 }
 
 __global__ void k_acc_sum(int n, const double* __restrict__ acc, const double* __restrict__ comp,
@@ -84,8 +86,8 @@ void launch_acc_sum(int ncells, const double* acc, const double* comp, double* o
 // Cell-centred gradient of field value f(cell): central inside, one-sided
 // first difference in the first/last cell of a line, 0 with a single cell.
 template <typename F>
-__device__ __forceinline__ void grad2(const CellParams& cp, int c, F f, double* gx, double* gy) {
-  const int ix = c % cp.nx, iy = c / cp.nx;
+__device__ __forceinline__ void grad2(const CellParams& cp, int c, int lc, F f, double* gx, double* gy) {
+  const int ix = lc % cp.nx, iy = lc / cp.nx;
   *gx = 0.0;
   *gy = 0.0;
   if (cp.nx >= 2) {
@@ -101,21 +103,25 @@ __device__ __forceinline__ void grad2(const CellParams& cp, int c, F f, double* 
   }
 }
 
-__global__ void k_hot(CellParams cp, const double* __restrict__ F, double* __restrict__ hot,
-                      double* __restrict__ kngll, uint8_t* __restrict__ mask) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cp.ncells; c += gridDim.x * blockDim.x) {
+__global__ void k_hot(const CellParams* __restrict__ cps, const int32_t* __restrict__ cell_case,
+                      const int32_t* __restrict__ cell0, int ncells, const double* __restrict__ F,
+                      double* __restrict__ hot, double* __restrict__ kngll, uint8_t* __restrict__ mask) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+    const int cs = cell_case[c];
+    const CellParams& cp = cps[cs];
+    const int lc = c - cell0[cs];
     const double* f = F + (size_t)c * 18;
     const double rho = f[0], ux = f[1], uy = f[2], tt = f[4], tr = f[5];
     const double T = (3.0 * tt + cp.d_r * tr) / (3.0 + cp.d_r);
     const double mu = cp.mu_ref * pow(T, cp.omega);
     double duxx, duxy, duyx, duyy, duzx, duzy, dttx, dtty, dtrx, dtry, drx, dry, dsx, dsy;
-    grad2(cp, c, [&](int k) { return F[(size_t)k * 18 + 1]; }, &duxx, &duxy);
-    grad2(cp, c, [&](int k) { return F[(size_t)k * 18 + 2]; }, &duyx, &duyy);
-    grad2(cp, c, [&](int k) { return F[(size_t)k * 18 + 3]; }, &duzx, &duzy);
-    grad2(cp, c, [&](int k) { return F[(size_t)k * 18 + 4]; }, &dttx, &dtty);
-    grad2(cp, c, [&](int k) { return F[(size_t)k * 18 + 5]; }, &dtrx, &dtry);
-    grad2(cp, c, [&](int k) { return F[(size_t)k * 18 + 0]; }, &drx, &dry);
-    grad2(cp, c, [&](int k) {
+    grad2(cp, c, lc, [&](int k) { return F[(size_t)k * 18 + 1]; }, &duxx, &duxy);
+    grad2(cp, c, lc, [&](int k) { return F[(size_t)k * 18 + 2]; }, &duyx, &duyy);
+    grad2(cp, c, lc, [&](int k) { return F[(size_t)k * 18 + 3]; }, &duzx, &duzy);
+    grad2(cp, c, lc, [&](int k) { return F[(size_t)k * 18 + 4]; }, &dttx, &dtty);
+    grad2(cp, c, lc, [&](int k) { return F[(size_t)k * 18 + 5]; }, &dtrx, &dtry);
+    grad2(cp, c, lc, [&](int k) { return F[(size_t)k * 18 + 0]; }, &drx, &dry);
+    grad2(cp, c, lc, [&](int k) {
             const double* g = F + (size_t)k * 18;
             return sqrt(g[1] * g[1] + g[2] * g[2] + g[3] * g[3]);
           },
@@ -149,10 +155,10 @@ __global__ void k_hot(CellParams cp, const double* __restrict__ F, double* __res
   }
 }
 
-void launch_hot(const CellParams& cp, const double* fields, double* hot, double* kngll, uint8_t* mask,
-                cudaStream_t st) {
-  const int g = (cp.ncells + 255) / 256;
-  k_hot<<<g > 0 ? g : 1, 256, 0, st>>>(cp, fields, hot, kngll, mask);
+void launch_hot(const CellParams* cp, const int32_t* cell_case, const int32_t* cell0, int ncells,
+                const double* fields, double* hot, double* kngll, uint8_t* mask, cudaStream_t st) {
+  const int g = (ncells + 255) / 256;
+  k_hot<<<g > 0 ? g : 1, 256, 0, st>>>(cp, cell_case, cell0, ncells, fields, hot, kngll, mask);
 }
 
 // ---------------------------------------------------------------------------
@@ -174,6 +180,36 @@ struct SynthArgs {
   const double* F;    // sampled fields, ncells x 18
   const double* hot;  // ncells x 12
 };
+
+// The slabs of a solve: either one slab described by cp1 (tables null) or
+// several, case c with parameters cps[c], cells [cell0[c], cell0[c+1]) and
+// work at work + woff[c].
+struct SynthCases {
+  CellParams cp1;
+  const CellParams* cps;
+  const int32_t* cell_case;
+  const int32_t* cell0;
+  const int64_t* woff;
+  const double* F;
+  const double* hot;
+  double* work;
+  double* info;  // 3 per case + a count of finished cases
+  int ncases;
+  int ncells;
+};
+
+__device__ __forceinline__ SynthArgs case_args(const SynthCases& sc, int c) {
+  const int off = sc.cell0 ? sc.cell0[c] : 0;
+  SynthArgs a;
+  a.cp = sc.cps ? sc.cps[c] : sc.cp1;
+  a.F = sc.F + (size_t)off * 18;
+  a.hot = sc.hot + (size_t)off * 12;
+  return a;
+}
+
+__device__ __forceinline__ double* case_work(const SynthCases& sc, int c) {
+  return sc.work + (sc.woff ? sc.woff[c] : 0);
+}
 
 __device__ __forceinline__ void face_flux(const SynthArgs& a, int i, const double* yl, const double* yr,
                                           double* sxy, double* sxz, double* qr, double* e) {
@@ -326,8 +362,11 @@ __device__ double block_max(double v, double* red) {
   return r;
 }
 
-__global__ void __launch_bounds__(1024) k_synth_init(SynthArgs a, double* work) {
+__global__ void __launch_bounds__(1024) k_synth_init(const __grid_constant__ SynthCases scs) {
   __shared__ double red[1024];
+  const int cs = blockIdx.x;
+  const SynthArgs a = case_args(scs, cs);
+  double* work = case_work(scs, cs);
   const int n = a.cp.nx;
   SynthWork w = synth_work(work, n);
   double m = 0.0, pm = 0.0;
@@ -355,14 +394,17 @@ __global__ void __launch_bounds__(1024) k_synth_init(SynthArgs a, double* work) 
 // one thread per (cell, column): columns 0..11 are d R_i / d(y_{i-1}, y_i,
 // y_{i+1}) by central differences, column 12 is dR_i/dP together with R_i
 // and the mass-row entries.
-__global__ void k_synth_jac(SynthArgs a, double* work) {
+__global__ void k_synth_jac(const __grid_constant__ SynthCases scs) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= scs.ncells * 13) return;
+  const int g = t / 13, col = t % 13;
+  const int cs = scs.cell_case ? scs.cell_case[g] : 0;
+  const SynthArgs a = case_args(scs, cs);
+  const int i = g - (scs.cell0 ? scs.cell0[cs] : 0);
   const int n = a.cp.nx;
-  SynthWork w = synth_work(work, n);
+  SynthWork w = synth_work(case_work(scs, cs), n);
   if (w.sc[SC_DONE] != 0.0) return;
   const double P = w.sc[SC_P];
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * 13) return;
-  const int i = t / 13, col = t % 13;
   double ym[4], y0[4], yp[4], rp[4], rm[4];
   for (int v = 0; v < 4; ++v) {
     y0[v] = w.y[4 * i + v];
@@ -447,11 +489,19 @@ __device__ __forceinline__ void mv4f(const float* a, const float* x, float* y) {
 
 // Newton update: block cyclic reduction (FP32) of J z1 = -R, J z2 = G; the
 // bordered mass row in FP64; a damped update that keeps rho, T positive.
-__global__ void __launch_bounds__(1024) k_synth_solve(SynthArgs a, double* work, int n_m, double tol) {
+// count_done: add 1 to the finished-slab count (info[3 ncases]) for every
+// slab that is finished after this launch
+__global__ void __launch_bounds__(1024) k_synth_solve(const __grid_constant__ SynthCases scs, int n_m, double tol,
+                                                      int count_done) {
   __shared__ double red[1024];
+  const int cs = blockIdx.x;
+  const SynthArgs a = case_args(scs, cs);
   const int n = a.cp.nx;
-  SynthWork w = synth_work(work, n);
-  if (w.sc[SC_DONE] != 0.0) return;
+  SynthWork w = synth_work(case_work(scs, cs), n);
+  if (w.sc[SC_DONE] != 0.0) {
+    if (count_done && threadIdx.x == 0) atomicAdd(scs.info + 3 * scs.ncases, 1.0);
+    return;
+  }
   const int tid = threadIdx.x, nt = blockDim.x;
   const double P = w.sc[SC_P];
   for (int i = tid; i < n; i += nt) {
@@ -618,14 +668,18 @@ __global__ void __launch_bounds__(1024) k_synth_solve(SynthArgs a, double* work,
         w.sc[SC_DONE] = 1.0;
       }
     }
+    if (count_done && w.sc[SC_DONE] != 0.0) atomicAdd(scs.info + 3 * scs.ncases, 1.0);
   }
 }
 
-__global__ void __launch_bounds__(1024) k_synth_final(SynthArgs a, double* work, double* out, int n_m,
-                                                      double* info) {
+__global__ void __launch_bounds__(1024) k_synth_final(const __grid_constant__ SynthCases scs, double* out_all) {
   __shared__ double red[1024];
+  const int cs = blockIdx.x;
+  const SynthArgs a = case_args(scs, cs);
   const int n = a.cp.nx;
-  SynthWork w = synth_work(work, n);
+  SynthWork w = synth_work(case_work(scs, cs), n);
+  double* out = out_all + (size_t)(scs.cell0 ? scs.cell0[cs] : 0) * 6;
+  double* info = scs.info + 3 * cs;
   const double P = w.sc[SC_P];
   double rmax = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -638,12 +692,18 @@ __global__ void __launch_bounds__(1024) k_synth_final(SynthArgs a, double* work,
     local_res(a, i, n, ym, y0, yp, P, r);
     for (int v = 0; v < 4; ++v) rmax = fmax(rmax, fabs(r[v]));
     double* o = out + (size_t)i * 6;
-    o[0] = (P - a.hot[(size_t)i * 12]) / y0[2];
-    o[1] = 0.0;
-    o[2] = y0[0];
-    o[3] = y0[1];
-    o[4] = y0[2];
-    o[5] = y0[3];
+    if (w.sc[SC_STATUS] == 2.0) {
+      // no admissible solution: the slab keeps its sampled fields
+      const double* f = a.F + (size_t)i * 18;
+      for (int v = 0; v < 6; ++v) o[v] = f[v];
+    } else {
+      o[0] = (P - a.hot[(size_t)i * 12]) / y0[2];
+      o[1] = 0.0;
+      o[2] = y0[0];
+      o[3] = y0[1];
+      o[4] = y0[2];
+      o[5] = y0[3];
+    }
   }
   rmax = block_max(rmax, red);
   if (threadIdx.x == 0) {
@@ -654,30 +714,61 @@ __global__ void __launch_bounds__(1024) k_synth_final(SynthArgs a, double* work,
   }
 }
 
-// Newton iterations are launched in batches of 4 (a converged solve makes the
-// remaining launches return at once); the host reads the done flag between
-// batches.
-void launch_synth1d(const CellParams& cp, const double* fields, const double* hot, double* out, double* work,
-                    int n_m, double tol, double* dev_info, cudaStream_t st) {
-  SynthArgs a{cp, fields, hot};
-  const int n = cp.nx;
-  SynthWork w = synth_work(work, n);
-  k_synth_init<<<1, 1024, 0, st>>>(a, work);
-  const int jt = 128, jb = (n * 13 + jt - 1) / jt;
+// Newton iterations are launched in batches of 4 (a finished slab makes the
+// remaining launches return at once); the host reads the count of finished
+// slabs between batches.
+static void run_synth(const SynthCases& sc, const int32_t* host_nx, double* out, int n_m, double tol,
+                      cudaStream_t st) {
+  k_synth_init<<<sc.ncases, 1024, 0, st>>>(sc);
+  const int jt = 128, jb = (sc.ncells * 13 + jt - 1) / jt;
+  (void)host_nx;
   int it = 0;
   while (it < n_m) {
     const int batch = (n_m - it) < 4 ? (n_m - it) : 4;
+    cudaMemsetAsync(sc.info + 3 * sc.ncases, 0, sizeof(double), st);
     for (int b = 0; b < batch; ++b) {
-      k_synth_jac<<<jb, jt, 0, st>>>(a, work);
-      k_synth_solve<<<1, 1024, 0, st>>>(a, work, n_m, tol);
+      k_synth_jac<<<jb, jt, 0, st>>>(sc);
+      k_synth_solve<<<sc.ncases, 1024, 0, st>>>(sc, n_m, tol, b == batch - 1 ? 1 : 0);
     }
     it += batch;
     double done = 0.0;
-    cudaMemcpyAsync(&done, w.sc + SC_DONE, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&done, sc.info + 3 * sc.ncases, sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
-    if (done != 0.0) break;
+    if (done >= (double)sc.ncases) break;
   }
-  k_synth_final<<<1, 1024, 0, st>>>(a, work, out, n_m, dev_info);
+  k_synth_final<<<sc.ncases, 1024, 0, st>>>(sc, out);
+}
+
+void launch_synth1d(const CellParams* cp, const int32_t* cell_case, const int32_t* cell0, int ncases, int ncells,
+                    const int32_t* host_nx, const double* fields, const double* hot, double* out, double* work,
+                    const int64_t* woff, int n_m, double tol, double* info, cudaStream_t st) {
+  SynthCases sc{};
+  sc.cps = cp;
+  sc.cell_case = cell_case;
+  sc.cell0 = cell0;
+  sc.woff = woff;
+  sc.F = fields;
+  sc.hot = hot;
+  sc.work = work;
+  sc.info = info;
+  sc.ncases = ncases;
+  sc.ncells = ncells;
+  run_synth(sc, host_nx, out, n_m, tol, st);
+}
+
+// one slab given by value (no device tables): used where nothing may be
+// allocated
+void launch_synth1d_single(const CellParams& cp, const double* fields, const double* hot, double* out, double* work,
+                           int n_m, double tol, double* info, cudaStream_t st) {
+  SynthCases sc{};
+  sc.cp1 = cp;
+  sc.F = fields;
+  sc.hot = hot;
+  sc.work = work;
+  sc.info = info;
+  sc.ncases = 1;
+  sc.ncells = cp.nx;
+  run_synth(sc, &cp.nx, out, n_m, tol, st);
 }
 
 }  // namespace dsmc

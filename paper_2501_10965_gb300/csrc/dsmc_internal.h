@@ -31,11 +31,24 @@ struct CellParams {
   uint32_t k0, k1;
 };
 
+// Per-case tables of a handle (device memory).  A single simulation is one
+// case; a batch holds several independent cases whose cells are numbered
+// consecutively: case c owns global cells [cell0[c], cell0[c+1]).
+template <typename T>
+struct Cases {
+  const Params<T>* p;        // per case
+  const CellParams* cp;      // per case
+  const int32_t* cell0;      // ncases + 1
+  const int32_t* cell_case;  // per global cell
+  int n;
+};
+
 // Everything a launch needs, carved out of the caller's workspace.
 template <typename T>
 struct State {
   int64_t capacity;
   int nparticles;  // host copy of the particle count (compact layout)
+  int ncells;      // total cells (all cases)
   int ovf_cap;
   int tile;        // particles staged per warp in shared memory
   double slack;    // FP32 bin capacity = slack * count + 32
@@ -59,6 +72,8 @@ struct State {
   unsigned long long* stats;  // ST_NSLOTS
   int32_t* flags;     // 16 device words: [0] error bits, [1] total, [2] over-capacity
   Ovf ovf[2];
+  Cases<T> cases;
+  bool batch;  // several cases: kernels read their parameters per cell
 };
 
 template <typename T>
@@ -66,6 +81,8 @@ struct Ops {
   static void configure(int tile);
   static void init(const Params<T>& p, State<T>& s, int cur, int lay, int ppc, int cap0, double tt,
                    double tr, const double* u3, cudaStream_t st);
+  // batch: the layout s.start[lay] is set; every case fills its cells
+  static void init_batch(const Params<T>& p0, State<T>& s, int ncells, int cur, int lay, cudaStream_t st);
   static void step_det(const Params<T>& p, State<T>& s, int& cur, int& lay, uint32_t step,
                        int do_sample, cudaStream_t st);
   static void step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint32_t step0,
@@ -79,25 +96,33 @@ struct Ops {
                                const double* x, const double* y, const double* vx,
                                const double* vy, const double* vz, const double* ir, int det,
                                cudaStream_t st);
-  static void dig_counts(const CellParams& cp, State<T>& s, int lay, const double* target,
-                         uint32_t iter, int det, cudaStream_t st);
-  static void dig_apply(const CellParams& cp, State<T>& s, int& cur, int& lay, const double* target,
-                        uint32_t iter, int det, cudaStream_t st);
+  static void dig_counts(State<T>& s, int ncells, int lay, const double* target, uint32_t iter, int det,
+                         cudaStream_t st);
+  static void dig_apply(const CellParams& cp0, State<T>& s, int ncells, int& cur, int& lay,
+                        const double* target, uint32_t iter, int det, cudaStream_t st);
   // writes the total of cnt[0..ncells) to s.tmp_start[ncells]
   static void total_count(State<T>& s, const int32_t* cnt, int ncells, cudaStream_t st);
   static void sgmax_io(State<T>& s, int ncells, double* out, const double* in, cudaStream_t st);
 };
 
-// FP64 cell-field kernels (dsmc_fields.cu)
-void launch_fields(const CellParams& cp, const double* acc, const double* comp, int64_t nsamples,
-                   double* out, cudaStream_t st);
-void launch_hot(const CellParams& cp, const double* fields, double* hot, double* kngll,
-                uint8_t* mask, cudaStream_t st);
+// FP64 cell-field kernels (dsmc_fields.cu); cp / cell_case / cell0 are
+// device tables (see Cases), ncells the total number of cells
+void launch_fields(const CellParams* cp, const int32_t* cell_case, int ncells, const double* acc,
+                   const double* comp, int64_t nsamples, double* out, cudaStream_t st);
+void launch_hot(const CellParams* cp, const int32_t* cell_case, const int32_t* cell0, int ncells,
+                const double* fields, double* hot, double* kngll, uint8_t* mask, cudaStream_t st);
 void launch_acc_sum(int ncells, const double* acc, const double* comp, double* out,
                     cudaStream_t st);
-// 1D synthetic equations; writes iterations / residual / status to dev_info (3 doubles)
-void launch_synth1d(const CellParams& cp, const double* fields, const double* hot, double* out,
-                    double* work, int n_m, double tol, double* dev_info, cudaStream_t st);
+// 1D synthetic equations of ncases slabs; case c uses work + woff[c] (device
+// table of offsets in doubles) and writes (iterations, max residual, status)
+// to info[3c .. 3c+2]; host_nx[c] are the slab sizes (host memory)
+void launch_synth1d(const CellParams* cp, const int32_t* cell_case, const int32_t* cell0, int ncases,
+                    int ncells, const int32_t* host_nx, const double* fields, const double* hot, double* out,
+                    double* work, const int64_t* woff, int n_m, double tol, double* info,
+                    cudaStream_t st);
+// one slab given by value, no device tables (info: 4 doubles)
+void launch_synth1d_single(const CellParams& cp, const double* fields, const double* hot, double* out,
+                           double* work, int n_m, double tol, double* info, cudaStream_t st);
 size_t synth1d_work_doubles(int ncells);
 
 }  // namespace dsmc

@@ -87,7 +87,7 @@ extern "C" int synth_solve_noalloc(const dsmc_config* cfg, const double* dev_fie
   double* info_dev = scratch + kInfoOffset;
   // every scratch word the kernel reads it has written first in the same
   // call, so nothing needs clearing between calls
-  dsmc::launch_synth1d(cp, dev_fields, dev_hot, dev_out, scratch, n_m, tol, info_dev, st);
+  dsmc::launch_synth1d_single(cp, dev_fields, dev_hot, dev_out, scratch, n_m, tol, info_dev, st);
   if (cudaGetLastError() != cudaSuccess) return DSMC_ERR_CUDA;
   double info[3] = {0, 0, 0};
   if (cudaMemcpyAsync(info, info_dev, sizeof info, cudaMemcpyDeviceToHost, st) != cudaSuccess) return DSMC_ERR_CUDA;

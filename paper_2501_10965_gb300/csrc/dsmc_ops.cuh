@@ -100,6 +100,38 @@ __global__ void k_init(Params<T> p, PBuf<T> b, const int32_t* __restrict__ start
   }
 }
 
+// Batch initial state: one warp per cell, the cell's case supplies ppc, the
+// initial state and the random key (same draws as k_init).
+template <typename T, int DIM>
+__global__ void k_init_cells(Cases<T> cases, int ncells, PBuf<T> b, const int32_t* __restrict__ start,
+                             int32_t* __restrict__ count, int32_t* __restrict__ cellof) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int cell = warp;
+  if (cell >= ncells) return;
+  const int cs = cases.cell_case[cell];
+  const Params<T>& p = cases.p[cs];
+  const int lcell = cell - cases.cell0[cs];
+  const int ix = lcell % p.nx, iy = lcell / p.nx;
+  const int ppc = p.ppc;
+  const T stt = m_sqrt(p.init_tt);
+  for (int k = lane; k < ppc; k += 32) {
+    Stream<T> st(TAG_INIT, (uint32_t)k, (uint32_t)lcell, 0u, p.k0, p.k1);
+    const T a0 = st.u(0), a1 = st.u(1);
+    T n1, n2, n3, n4;
+    box_muller(st.u(2), st.u(3), &n1, &n2);
+    box_muller(st.u(4), st.u(5), &n3, &n4);
+    const int slot = start[cell] + k;
+    b.x[slot] = ((T)ix + a0) * p.dx;
+    b.y[slot] = (DIM == 2) ? ((T)iy + a1) * p.dy : T(0);
+    b.vx[slot] = p.init_u[0] + stt * n1;
+    b.vy[slot] = p.init_u[1] + stt * n2;
+    b.vz[slot] = p.init_u[2] + stt * n3;
+    b.ir[slot] = -p.init_tr * m_log(st.u(6));
+    if (cellof) cellof[slot] = cell;
+  }
+  if (lane == 0) count[cell] = ppc;
+}
+
 static __global__ void k_layout_uniform(int ncells, int32_t cap, int32_t* start) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= ncells; c += gridDim.x * blockDim.x)
     start[c] = c * cap;
@@ -108,8 +140,9 @@ static __global__ void k_layout_uniform(int ncells, int32_t cap, int32_t* start)
 // ---------------------------------------------------------------------------
 // FP64-deterministic layout: move, stable sort, collide + sample
 // ---------------------------------------------------------------------------
-template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_move_det(Params<T> p, PBuf<T> b, const int32_t* __restrict__ cellof,
+template <typename T, int DIM, bool BATCH>
+__global__ void __launch_bounds__(256) k_move_det(const __grid_constant__ Params<T> pk, Cases<T> cases, PBuf<T> b,
+                                                  const int32_t* __restrict__ cellof,
                                                   const int32_t* __restrict__ start, int n,
                                                   uint32_t step, int32_t* __restrict__ key,
                                                   double* __restrict__ tally_g,
@@ -119,8 +152,11 @@ __global__ void __launch_bounds__(256) k_move_det(Params<T> p, PBuf<T> b, const 
   __syncthreads();
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     const int c = cellof[s];
+    const int cs = BATCH ? cases.cell_case[c] : 0;
+    const Params<T>& p = BATCH ? cases.p[cs] : pk;
+    const int c0 = BATCH ? cases.cell0[cs] : 0;
     T x = b.x[s], y = b.y[s], vx = b.vx[s], vy = b.vy[s], vz = b.vz[s], ir = b.ir[s];
-    fly<T, DIM, true>(p, x, y, vx, vy, vz, ir, (uint32_t)(s - start[c]), (uint32_t)c, step, s_tally,
+    fly<T, DIM, true>(p, x, y, vx, vy, vz, ir, (uint32_t)(s - start[c]), (uint32_t)(c - c0), step, s_tally,
                 stats + ST_HITS, stats + ST_MAXHIT);
     b.x[s] = x;
     b.y[s] = y;
@@ -128,7 +164,7 @@ __global__ void __launch_bounds__(256) k_move_det(Params<T> p, PBuf<T> b, const 
     b.vy[s] = vy;
     b.vz[s] = vz;
     b.ir[s] = ir;
-    key[s] = cell_of<T, DIM>(p, x, y);
+    key[s] = c0 + cell_of<T, DIM>(p, x, y);
   }
   __syncthreads();
   if (threadIdx.x < 20 && s_tally[threadIdx.x] != T(0))
@@ -207,8 +243,9 @@ __device__ __forceinline__ void flush_counts(const CollCount& cc, unsigned* s_cn
 // One warp per cell: stage the cell's velocities and rotational energies in
 // shared memory (cells above `tile` particles work in global memory), run
 // NTC collisions and/or sampling, write back.  flags: 1 collide, 2 sample.
-template <typename T>
-__global__ void __launch_bounds__(WPB * 32) k_collide_sample(Params<T> p, PBuf<T> b,
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(WPB * 32) k_collide_sample(const __grid_constant__ Params<T> pk, Cases<T> cases,
+                                                             int ncells, PBuf<T> b,
                                                              const int32_t* __restrict__ start,
                                                              const int32_t* __restrict__ count,
                                                              T* __restrict__ sgmax, double* __restrict__ acc,
@@ -224,7 +261,10 @@ __global__ void __launch_bounds__(WPB * 32) k_collide_sample(Params<T> p, PBuf<T
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cell = blockIdx.x * WPB + warp;
-  if (cell < p.ncells) {
+  if (cell < ncells) {
+    const int cs = BATCH ? cases.cell_case[cell] : 0;
+    const Params<T>& p = BATCH ? cases.p[cs] : pk;
+    const int lcell = cell - (BATCH ? cases.cell0[cs] : 0);
     const int base = start[cell], n = count[cell];
     T* tv = reinterpret_cast<T*>(smem) + (size_t)warp * tile * 4;
     uint32_t* tow = reinterpret_cast<uint32_t*>(smem + (size_t)WPB * tile * 4 * sizeof(T)) + (size_t)warp * tile;
@@ -253,7 +293,7 @@ __global__ void __launch_bounds__(WPB * 32) k_collide_sample(Params<T> p, PBuf<T
     __syncwarp();
     if (flags & 1) {
       CollCount cc{0, 0, 0, 0};
-      collide_cell<T>(p, vx, vy, vz, ir, n, (uint32_t)cell, step, sgmax + cell, own, cc);
+      collide_cell<T>(p, vx, vy, vz, ir, n, (uint32_t)lcell, step, sgmax + cell, own, cc);
       flush_counts<T>(cc, s_cnt);
       __syncwarp();
     }
@@ -315,6 +355,9 @@ __device__ __forceinline__ void append_particle(const Params<float>& p, const PB
     o.ir[w] = ir;
     if (slot >= cap - 8) atomicAdd(s_misc + 1, 1u);
   } else {
+    // the slot was reserved but is not used: give it back, so that the bin's
+    // count ends at its capacity
+    atomicSub(&cnt_out[d], 1);
     const int q = atomicAdd(ovo.count, 1);
     atomicAdd(s_misc + 0, 1u);
     if (q < ovf_cap) {
@@ -370,8 +413,10 @@ inline size_t fused_smem_bytes(int tile) { return (size_t)FWPB * tile * 28; }
 // destination bin reserves the slots; (M3) fly again (the same counter-based
 // random stream, so the same result) and store.  Counters are flushed by the
 // last warp of the block to finish, so warps never wait for one another.
-template <int DIM>
-__global__ void __launch_bounds__(FWPB * 32, 8) k_fused(Params<float> p, PBuf<float> in, PBuf<float> out,
+template <int DIM, bool BATCH>
+__global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ Params<float> pk,
+                                                        Cases<float> cases, int ncells, PBuf<float> in,
+                                                        PBuf<float> out,
                                                         const int32_t* __restrict__ start,
                                                         int32_t* __restrict__ cnt_in,
                                                         int32_t* __restrict__ cnt_out,
@@ -401,7 +446,11 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(Params<float> p, PBuf<fl
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if ((int)blockIdx.x < ncell_blocks) {
     const int cell = blockIdx.x * FWPB + warp;
-    if (cell < p.ncells) {
+    if (cell < ncells) {
+      const int cs = BATCH ? cases.cell_case[cell] : 0;
+      const Params<float>& p = BATCH ? cases.p[cs] : pk;
+      const int c0 = BATCH ? cases.cell0[cs] : 0;
+      const int lcell = cell - c0;
       const int base = start[cell], n = cnt_in[cell];
       const bool flush = (flags & 8) != 0;
       double pre[2] = {0.0, 0.0};
@@ -458,7 +507,7 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(Params<float> p, PBuf<fl
         }
         if (flags & 1) {
           CollCount cc{0, 0, 0, 0};
-          collide_cell<float>(p, vx, vy, vz, ir, n, (uint32_t)cell, step_c, sgmax + cell, own, cc);
+          collide_cell<float>(p, vx, vy, vz, ir, n, (uint32_t)lcell, step_c, sgmax + cell, own, cc);
           flush_counts<float>(cc, s_cnt);
           __syncwarp();
         }
@@ -474,7 +523,7 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(Params<float> p, PBuf<fl
           __syncwarp();
           // M1: destinations and ranks; a particle that reaches a wall is
           // placed individually in M3 (code 9)
-          const int cix = cell % p.nx, ciy = cell / p.nx;
+          const int cix = lcell % p.nx, ciy = lcell / p.nx;
           for (int q = lane; q < n; q += 32) {
             float xn, yn;
             int code = 9;
@@ -497,7 +546,7 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(Params<float> p, PBuf<fl
           for (int q = lane; q < n; q += 32) {
             float x = px[q], y = (DIM == 2) ? py[q] : 0.f;
             float a = vx[q], b = vy[q], c = vz[q], e = ir[q];
-            fly<float, DIM, true>(p, x, y, a, b, c, e, (uint32_t)q, (uint32_t)cell, step_m, s_tally,
+            fly<float, DIM, true>(p, x, y, a, b, c, e, (uint32_t)q, (uint32_t)lcell, step_m, s_tally,
                                   stats + ST_HITS, stats + ST_MAXHIT);
             const uint32_t tag = own[q];
             const int code = (int)(tag >> 24), r = (int)(tag & 0xFFFFFFu);
@@ -508,7 +557,7 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(Params<float> p, PBuf<fl
               s0 = nb_s0[code];
               cap = nb_cap[code];
             } else {
-              d = cell_of<float, DIM>(p, x, y);
+              d = c0 + cell_of<float, DIM>(p, x, y);
               slot = atomicAdd(&cnt_out[d], 1);
               s0 = start[d];
               cap = start[d + 1] - s0;
@@ -523,6 +572,9 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(Params<float> p, PBuf<fl
               out.ir[w] = e;
               if (slot >= cap - 8) atomicAdd(s_misc + 1, 1u);
             } else {
+              // reserved but unused slot: give it back (the bin's count ends
+              // at its capacity)
+              atomicSub(&cnt_out[d], 1);
               const int qo = atomicAdd(ovo.count, 1);
               atomicAdd(s_misc + 0, 1u);
               if (qo < ovf_cap) {
@@ -559,6 +611,9 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(Params<float> p, PBuf<fl
       float x = 0.f, y = 0.f, a = 0.f, bb = 0.f, c = 0.f, e = 0.f;
       int d = 0;
       if (active) {
+        const int cs = BATCH ? cases.cell_case[ovi.dest[q]] : 0;
+        const Params<float>& p = BATCH ? cases.p[cs] : pk;
+        const int c0 = BATCH ? cases.cell0[cs] : 0;
         x = ovi.x[q];
         y = ovi.y[q];
         a = ovi.vx[q];
@@ -567,9 +622,9 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(Params<float> p, PBuf<fl
         e = ovi.ir[q];
         fly<float, DIM, true>(p, x, y, a, bb, c, e, (uint32_t)q, (uint32_t)(p.ncells + 1), step_m, s_tally,
                               stats + ST_HITS, stats + ST_MAXHIT);
-        d = cell_of<float, DIM>(p, x, y);
+        d = c0 + cell_of<float, DIM>(p, x, y);
       }
-      append_particle<DIM>(p, out, start, cnt_out, ovo, ovf_cap, active, d, x, y, a, bb, c, e, s_misc);
+      append_particle<DIM>(pk, out, start, cnt_out, ovo, ovf_cap, active, d, x, y, a, bb, c, e, s_misc);
     }
   }
   // the last warp of the block to finish flushes the block's counters
@@ -601,10 +656,19 @@ static __global__ void k_rebin_add_ovf(const Ovf ov, int ovf_cap, int32_t* __res
 }
 
 // caps = bin_cap_of(tot, slack); halve the slack until the bins fit.
+// nominal particles per cell of a cell's case: rho = 1 with weight F
+__device__ __forceinline__ int32_t nominal_count(const CellParams* cps, const int32_t* cell_case, int c) {
+  if (!cps) return 0;
+  const CellParams& cp = cps[cell_case[c]];
+  return (int32_t)(cp.vcell / cp.fnum + 0.5);
+}
+
 static __global__ void __launch_bounds__(1024) k_caps_scan(const int32_t* __restrict__ tot, int ncells,
                                                     double slack, long long capacity,
                                                     int32_t* __restrict__ start_out,
-                                                    int32_t* __restrict__ flags) {
+                                                    int32_t* __restrict__ flags,
+                                                    const CellParams* __restrict__ cps = nullptr,
+                                                    const int32_t* __restrict__ cell_case = nullptr) {
   __shared__ double s_slack;
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
@@ -614,7 +678,8 @@ static __global__ void __launch_bounds__(1024) k_caps_scan(const int32_t* __rest
   __syncthreads();
   for (int attempt = 0; attempt < 8; ++attempt) {
     const double sl = s_slack;
-    cta_exclusive_scan(ncells, [&](int i) { return bin_cap_of(tot[i], sl); }, start_out);
+    cta_exclusive_scan(ncells, [&](int i) { return bin_cap_of(max(tot[i], nominal_count(cps, cell_case, i)), sl); },
+                       start_out);
     if (threadIdx.x == 0) {
       if ((long long)start_out[ncells] <= capacity) s_ok = 1;
       else s_slack = 1.0 + 0.5 * (s_slack - 1.0);
@@ -705,10 +770,15 @@ static __global__ void k_fill_zero_d(double* a, int n) {
 // ---------------------------------------------------------------------------
 // Sec. 3.2: particle modification
 // ---------------------------------------------------------------------------
-static __global__ void k_dig_counts(CellParams cp, const double* __restrict__ target, uint32_t iter,
-                             int det, double slack, int32_t* __restrict__ nt,
-                             int32_t* __restrict__ caps, int32_t* __restrict__ flags) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cp.ncells; c += gridDim.x * blockDim.x) {
+static __global__ void k_dig_counts(const CellParams* __restrict__ cps, const int32_t* __restrict__ cell_case,
+                                    const int32_t* __restrict__ cell0, int ncells,
+                                    const double* __restrict__ target, uint32_t iter,
+                                    int det, double slack, int32_t* __restrict__ nt,
+                                    int32_t* __restrict__ caps, int32_t* __restrict__ flags) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+    const int cs = cell_case[c];
+    const CellParams& cp = cps[cs];
+    const int lcell = c - cell0[cs];
     const double* t = target + (size_t)c * 6;
     bool bad = false;
     for (int q = 0; q < 6; ++q)
@@ -720,7 +790,7 @@ static __global__ void k_dig_counts(CellParams cp, const double* __restrict__ ta
       caps[c] = 0;
       continue;
     }
-    Stream<double> st(TAG_DIG_N, 0u, (uint32_t)c, iter, cp.k0, cp.k1);
+    Stream<double> st(TAG_DIG_N, 0u, (uint32_t)lcell, iter, cp.k0, cp.k1);
     const double xm = t[0] * cp.vcell / cp.fnum;
     long long v = iround(xm, st.u(0));
     if (v > 0x3fffffffLL) {
@@ -728,7 +798,10 @@ static __global__ void k_dig_counts(CellParams cp, const double* __restrict__ ta
       v = 0;
     }
     nt[c] = (int32_t)v;
-    caps[c] = det ? (int32_t)v : bin_cap_of((int32_t)v, slack);
+    // FP32 bins: room for slack x the larger of the new and the nominal count
+    const int32_t nominal = (int32_t)(cp.vcell / cp.fnum + 0.5);
+    caps[c] = det ? (int32_t)v : bin_cap_of(max((int32_t)v, nominal), slack);
+    atomicAdd(&flags[3], (int32_t)v);
   }
 }
 
@@ -743,7 +816,10 @@ static __global__ void __launch_bounds__(1024) k_scan_caps(const int32_t* __rest
 }
 
 template <typename T, int DIM>
-__global__ void __launch_bounds__(WPB * 32) k_dig_apply(CellParams cp, PBuf<T> in, PBuf<T> out,
+__global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __restrict__ cps,
+                                                        const int32_t* __restrict__ cell_case,
+                                                        const int32_t* __restrict__ cell0, int ncells,
+                                                        PBuf<T> in, PBuf<T> out,
                                                         const int32_t* __restrict__ start_in,
                                                         const int32_t* __restrict__ cnt_in,
                                                         const int32_t* __restrict__ start_out,
@@ -755,10 +831,13 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(CellParams cp, PBuf<T> i
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cell = blockIdx.x * WPB + warp;
-  if (cell >= cp.ncells) return;
+  if (cell >= ncells) return;
+  const int cs = cell_case[cell];
+  const CellParams& cp = cps[cs];
+  const int lcell = cell - cell0[cs];
   const int s0 = start_in[cell], n = cnt_in[cell], d0 = start_out[cell], ntg = nt[cell];
   const double* t = target + (size_t)cell * 6;
-  const int ix = cell % cp.nx, iy = cell / cp.nx;
+  const int ix = lcell % cp.nx, iy = lcell / cp.nx;
   int32_t* idx = (n <= tile) ? reinterpret_cast<int32_t*>(smem) + (size_t)warp * tile * 2 : idx_g + s0;
   int32_t* rm = (n <= tile) ? reinterpret_cast<int32_t*>(smem) + (size_t)warp * tile * 2 + tile : nullptr;
   // step ii
@@ -769,7 +848,7 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(CellParams cp, PBuf<T> i
       __syncwarp();
       if (lane == 0) {
         for (int q = 0; q < k; ++q) {
-          Stream<double> st(TAG_DIG_SEL, (uint32_t)q, (uint32_t)cell, iter, cp.k0, cp.k1);
+          Stream<double> st(TAG_DIG_SEL, (uint32_t)q, (uint32_t)lcell, iter, cp.k0, cp.k1);
           int r = q + (int)(st.u(0) * (double)(n - q));
           if (r > n - 1) r = n - 1;
           const int tmp = idx[q];
@@ -824,12 +903,12 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(CellParams cp, PBuf<T> i
       out.ir[d0 + q] = in.ir[s0 + q];
     }
     for (int q = lane; q < ntg - n; q += 32) {
-      Stream<double> sp(TAG_DIG_POS, (uint32_t)q, (uint32_t)cell, iter, cp.k0, cp.k1);
+      Stream<double> sp(TAG_DIG_POS, (uint32_t)q, (uint32_t)lcell, iter, cp.k0, cp.k1);
       const int w = d0 + n + q;
       out.x[w] = (T)(((double)ix + sp.u(0)) * cp.dx);
       out.y[w] = (T)((cp.dim == 2) ? ((double)iy + sp.u(1)) * cp.dy : 0.0);
       if (n > 0) {
-        Stream<double> ss(TAG_DIG_SEL, (uint32_t)q, (uint32_t)cell, iter, cp.k0, cp.k1);
+        Stream<double> ss(TAG_DIG_SEL, (uint32_t)q, (uint32_t)lcell, iter, cp.k0, cp.k1);
         int src = (int)(ss.u(0) * (double)n);
         if (src > n - 1) src = n - 1;
         out.vx[w] = in.vx[s0 + src];
@@ -912,8 +991,8 @@ inline int grid_for(long long n, int threads, int maxblocks = 152 * 16) {
 }
 
 template <typename T>
-void Ops<T>::init(const Params<T>& p, State<T>& s, int cur, int lay, int ppc, int cap0, double tt,
-                  double tr, const double* u3, cudaStream_t st) {
+void Ops<T>::init(const Params<T>& p, State<T>& s, int cur, int lay, int ppc, int cap0, double tt, double tr,
+                  const double* u3, cudaStream_t st) {
   k_layout_uniform<<<grid_for(p.ncells + 1, 256), 256, 0, st>>>(p.ncells, (int32_t)cap0, s.start[lay]);
   const long long total = (long long)p.ncells * ppc;
   const int g = grid_for(total, 256);
@@ -924,7 +1003,15 @@ void Ops<T>::init(const Params<T>& p, State<T>& s, int cur, int lay, int ppc, in
     k_init<T, 2><<<g, 256, 0, st>>>(p, s.buf[cur], s.start[lay], s.count[lay], s.cellof, ppc, (T)tt, (T)tr,
                                     (T)u3[0], (T)u3[1], (T)u3[2]);
   if (ppc == 0) k_zero_i32<<<grid_for(p.ncells, 256), 256, 0, st>>>(s.count[lay], p.ncells);
-  (void)cur;
+}
+
+template <typename T>
+void Ops<T>::init_batch(const Params<T>& p0, State<T>& s, int ncells, int cur, int lay, cudaStream_t st) {
+  const int blocks = (ncells * 32 + 255) / 256;
+  if (p0.dim == 1)
+    k_init_cells<T, 1><<<blocks, 256, 0, st>>>(s.cases, ncells, s.buf[cur], s.start[lay], s.count[lay], s.cellof);
+  else
+    k_init_cells<T, 2><<<blocks, 256, 0, st>>>(s.cases, ncells, s.buf[cur], s.start[lay], s.count[lay], s.cellof);
 }
 
 template <typename T>
@@ -932,28 +1019,51 @@ static size_t tile_smem(int tile) {
   return (size_t)WPB * tile * (4 * sizeof(T) + sizeof(uint32_t));
 }
 
+template <typename T, bool BATCH>
+static void launch_collide_sample(const Params<T>& p, State<T>& s, int ncells, const PBuf<T>& b, const int32_t* start,
+                                  const int32_t* count, uint32_t step, int flags, float* stg, float* stc,
+                                  cudaStream_t st) {
+  const int blocks = (ncells + WPB - 1) / WPB;
+  k_collide_sample<T, BATCH><<<blocks, WPB * 32, tile_smem<T>(s.tile), st>>>(
+      p, s.cases, ncells, b, start, count, s.sgmax, s.acc, s.comp, s.owner, step, flags, s.tile, s.stats, stg, stc);
+}
+
 template <typename T>
 void Ops<T>::step_det(const Params<T>& p, State<T>& s, int& cur, int& lay, uint32_t step, int do_sample,
                       cudaStream_t st) {
   const int n = s.nparticles;
+  const int ncells = s.ncells;
   const int other = cur ^ 1, olay = lay ^ 1;
   if (n > 0) {
-    if (p.dim == 1)
-      k_move_det<T, 1><<<grid_for(n, 256), 256, 0, st>>>(p, s.buf[cur], s.cellof, s.start[lay], n, step, s.key,
-                                                         s.tally, s.stats);
-    else
-      k_move_det<T, 2><<<grid_for(n, 256), 256, 0, st>>>(p, s.buf[cur], s.cellof, s.start[lay], n, step, s.key,
-                                                         s.tally, s.stats);
+    const int g = grid_for(n, 256);
+    if (p.dim == 1) {
+      if (s.batch)
+        k_move_det<T, 1, true><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step, s.key,
+                                                   s.tally, s.stats);
+      else
+        k_move_det<T, 1, false><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step, s.key,
+                                                    s.tally, s.stats);
+    } else {
+      if (s.batch)
+        k_move_det<T, 2, true><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step, s.key,
+                                                   s.tally, s.stats);
+      else
+        k_move_det<T, 2, false><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step, s.key,
+                                                    s.tally, s.stats);
+    }
   }
   const PBuf<T>& a = s.buf[cur];
-  k_sort_stable<T, T><<<1, 1024, 0, st>>>(a.x, a.y, a.vx, a.vy, a.vz, a.ir, s.buf[other], s.key, n, p.ncells,
+  k_sort_stable<T, T><<<1, 1024, 0, st>>>(a.x, a.y, a.vx, a.vy, a.vz, a.ir, s.buf[other], s.key, n, ncells,
                                           s.start[olay], s.count[olay], s.tmp2, s.dest, s.cellof);
   cur = other;
   lay = olay;
   const int flags = 1 | (do_sample ? 2 : 0);
-  const int blocks = (p.ncells + WPB - 1) / WPB;
-  k_collide_sample<T><<<blocks, WPB * 32, tile_smem<T>(s.tile), st>>>(
-      p, s.buf[cur], s.start[lay], s.count[lay], s.sgmax, s.acc, s.comp, s.owner, step, flags, s.tile, s.stats);
+  if (s.batch)
+    launch_collide_sample<T, true>(p, s, ncells, s.buf[cur], s.start[lay], s.count[lay], step, flags, nullptr,
+                                   nullptr, st);
+  else
+    launch_collide_sample<T, false>(p, s, ncells, s.buf[cur], s.start[lay], s.count[lay], step, flags, nullptr,
+                                    nullptr, st);
 }
 
 template <typename T>
@@ -961,22 +1071,24 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
                        int do_sample, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
     if (nsteps <= 0) return;
-    const int cblocks = (p.ncells + FWPB - 1) / FWPB;
+    const int ncells = s.ncells;
+    const int cblocks = (ncells + FWPB - 1) / FWPB;
     const int oblocks = 8;
-    const size_t sm = tile_smem<T>(s.tile);
     const size_t smf = fused_smem_bytes(s.tile);
     auto launch = [&](int flags, uint32_t sc, uint32_t sm_step) {
       const int other = cur ^ 1;
-      if (p.dim == 1)
-        k_fused<1><<<cblocks + oblocks, FWPB * 32, smf, st>>>(
-            p, s.buf[cur], s.buf[other], s.start[lay], s.count[cur], s.count[other], s.sgmax, s.acc, s.comp,
-            s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats,
-            s.flags + 8, s.stg, s.stc);
-      else
-        k_fused<2><<<cblocks + oblocks, FWPB * 32, smf, st>>>(
-            p, s.buf[cur], s.buf[other], s.start[lay], s.count[cur], s.count[other], s.sgmax, s.acc, s.comp,
-            s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats,
-            s.flags + 8, s.stg, s.stc);
+#define DSMC_FUSED_ARGS                                                                                         \
+  p, s.cases, ncells, s.buf[cur], s.buf[other], s.start[lay], s.count[cur], s.count[other], s.sgmax, s.acc,      \
+      s.comp, s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats, \
+      s.flags + 8, s.stg, s.stc
+      if (p.dim == 1) {
+        if (s.batch) k_fused<1, true><<<cblocks + oblocks, FWPB * 32, smf, st>>>(DSMC_FUSED_ARGS);
+        else k_fused<1, false><<<cblocks + oblocks, FWPB * 32, smf, st>>>(DSMC_FUSED_ARGS);
+      } else {
+        if (s.batch) k_fused<2, true><<<cblocks + oblocks, FWPB * 32, smf, st>>>(DSMC_FUSED_ARGS);
+        else k_fused<2, false><<<cblocks + oblocks, FWPB * 32, smf, st>>>(DSMC_FUSED_ARGS);
+      }
+#undef DSMC_FUSED_ARGS
       // the input overflow list has been consumed
       cudaMemsetAsync(s.ovf[cur].count, 0, sizeof(int32_t), st);
       cur = other;
@@ -993,10 +1105,13 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
         const int fold = ((i + 1) % STAGE_STEPS == 0) ? 8 : 0;
         launch(1 | (do_sample ? 2 | fold : 0) | 4, sc, sc + 1);
       } else {
-        const int wblocks = (p.ncells + WPB - 1) / WPB;
-        k_collide_sample<T><<<wblocks, WPB * 32, sm, st>>>(p, s.buf[cur], s.start[lay], s.count[cur], s.sgmax,
-                                                          s.acc, s.comp, s.owner, sc, 1 | (do_sample ? 2 : 0),
-                                                          s.tile, s.stats, s.stg, s.stc);
+        const int flags = 1 | (do_sample ? 2 : 0);
+        if (s.batch)
+          launch_collide_sample<T, true>(p, s, ncells, s.buf[cur], s.start[lay], s.count[cur], sc, flags, s.stg,
+                                         s.stc, st);
+        else
+          launch_collide_sample<T, false>(p, s, ncells, s.buf[cur], s.start[lay], s.count[cur], sc, flags, s.stg,
+                                          s.stc, st);
       }
     }
   } else {
@@ -1005,22 +1120,23 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
 }
 
 template <typename T>
-void Ops<T>::rebin(const Params<T>& p, State<T>& s, int& cur, int& lay, int with_ovf, double slack,
-                   cudaStream_t st) {
+void Ops<T>::rebin(const Params<T>& p, State<T>& s, int& cur, int& lay, int with_ovf, double slack, cudaStream_t st) {
   // tot (tmp in s.nt) = occupancy (+ overflow destinations)
+  const int ncells = s.ncells;
   const int other = cur ^ 1, olay = lay ^ 1;
-  cudaMemcpyAsync(s.nt, s.count[cur], sizeof(int32_t) * p.ncells, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(s.nt, s.count[cur], sizeof(int32_t) * ncells, cudaMemcpyDeviceToDevice, st);
   if constexpr (sizeof(T) == 4) {
     if (with_ovf) k_rebin_add_ovf<<<64, 256, 0, st>>>(s.ovf[cur], s.ovf_cap, s.nt);
   }
-  k_caps_scan<<<1, 1024, 0, st>>>(s.nt, p.ncells, slack, (long long)s.capacity, s.start[olay], s.flags);
-  const int blocks = (p.ncells + WPB - 1) / WPB;
+  k_caps_scan<<<1, 1024, 0, st>>>(s.nt, ncells, slack, (long long)s.capacity, s.start[olay], s.flags,
+                                  s.cases.cp, s.cases.cell_case);
+  const int blocks = (ncells + WPB - 1) / WPB;
   if (p.dim == 1)
     k_rebin_copy<T, 1><<<blocks, WPB * 32, 0, st>>>(s.buf[cur], s.buf[other], s.start[lay], s.count[cur],
-                                                    s.start[olay], s.count[other], p.ncells);
+                                                    s.start[olay], s.count[other], ncells);
   else
     k_rebin_copy<T, 2><<<blocks, WPB * 32, 0, st>>>(s.buf[cur], s.buf[other], s.start[lay], s.count[cur],
-                                                    s.start[olay], s.count[other], p.ncells);
+                                                    s.start[olay], s.count[other], ncells);
   if constexpr (sizeof(T) == 4) {
     if (with_ovf) {
       if (p.dim == 1)
@@ -1031,18 +1147,19 @@ void Ops<T>::rebin(const Params<T>& p, State<T>& s, int& cur, int& lay, int with
     }
   }
   // the old buffer's occupancies are cleared so that it can take appends
-  k_zero_i32<<<grid_for(p.ncells, 256), 256, 0, st>>>(s.count[cur], p.ncells);
+  k_zero_i32<<<grid_for(ncells, 256), 256, 0, st>>>(s.count[cur], ncells);
   cur = other;
   lay = olay;
 }
 
 template <typename T>
-void Ops<T>::export_particles(const Params<T>& p, State<T>& s, int cur, int lay, double* x, double* y,
-                              double* vx, double* vy, double* vz, double* ir, int32_t* cell, cudaStream_t st) {
+void Ops<T>::export_particles(const Params<T>& p, State<T>& s, int cur, int lay, double* x, double* y, double* vx,
+                              double* vy, double* vz, double* ir, int32_t* cell, cudaStream_t st) {
+  (void)p;
   const int cntlay = (sizeof(T) == 4) ? cur : lay;
-  k_scan_counts<<<1, 1024, 0, st>>>(s.count[cntlay], p.ncells, s.tmp_start);
-  const int blocks = (p.ncells + WPB - 1) / WPB;
-  k_export<T><<<blocks, WPB * 32, 0, st>>>(s.buf[cur], s.start[lay], s.count[cntlay], s.tmp_start, p.ncells, x, y,
+  k_scan_counts<<<1, 1024, 0, st>>>(s.count[cntlay], s.ncells, s.tmp_start);
+  const int blocks = (s.ncells + WPB - 1) / WPB;
+  k_export<T><<<blocks, WPB * 32, 0, st>>>(s.buf[cur], s.start[lay], s.count[cntlay], s.tmp_start, s.ncells, x, y,
                                           vx, vy, vz, ir, cell);
 }
 
@@ -1088,32 +1205,34 @@ void Ops<T>::import_particles(const Params<T>& p, State<T>& s, int& cur, int& la
 }
 
 template <typename T>
-void Ops<T>::dig_counts(const CellParams& cp, State<T>& s, int lay, const double* target, uint32_t iter, int det,
+void Ops<T>::dig_counts(State<T>& s, int ncells, int lay, const double* target, uint32_t iter, int det,
                         cudaStream_t st) {
   cudaMemsetAsync(s.flags, 0, sizeof(int32_t) * 4, st);
   // caps go to tmp_start (ncells), then scanned into the other layout's start
-  k_dig_counts<<<grid_for(cp.ncells, 256), 256, 0, st>>>(cp, target, iter, det, s.slack, s.nt, s.tmp_start,
-                                                         s.flags);
-  k_scan_caps<<<1, 1024, 0, st>>>(s.tmp_start, cp.ncells, (long long)s.capacity, s.start[lay ^ 1], s.flags);
+  k_dig_counts<<<grid_for(ncells, 256), 256, 0, st>>>(s.cases.cp, s.cases.cell_case, s.cases.cell0, ncells, target,
+                                                      iter, det, s.slack, s.nt, s.tmp_start, s.flags);
+  k_scan_caps<<<1, 1024, 0, st>>>(s.tmp_start, ncells, (long long)s.capacity, s.start[lay ^ 1], s.flags);
 }
 
 template <typename T>
-void Ops<T>::dig_apply(const CellParams& cp, State<T>& s, int& cur, int& lay, const double* target,
+void Ops<T>::dig_apply(const CellParams& cp0, State<T>& s, int ncells, int& cur, int& lay, const double* target,
                        uint32_t iter, int det, cudaStream_t st) {
   const int other = cur ^ 1, olay = lay ^ 1;
   const int cin = det ? lay : cur;    // occupancy array of the current state
   const int cout = det ? olay : other;
-  const int blocks = (cp.ncells + WPB - 1) / WPB;
+  const int blocks = (ncells + WPB - 1) / WPB;
   const size_t sm = (size_t)WPB * s.tile * 2 * sizeof(int32_t);
-  if (cp.dim == 1)
-    k_dig_apply<T, 1><<<blocks, WPB * 32, sm, st>>>(cp, s.buf[cur], s.buf[other], s.start[lay], s.count[cin],
-                                                    s.start[olay], s.count[cout], s.nt, target, iter, s.scratch_i,
+  if (cp0.dim == 1)
+    k_dig_apply<T, 1><<<blocks, WPB * 32, sm, st>>>(s.cases.cp, s.cases.cell_case, s.cases.cell0, ncells, s.buf[cur],
+                                                    s.buf[other], s.start[lay], s.count[cin], s.start[olay],
+                                                    s.count[cout], s.nt, target, iter, s.scratch_i,
                                                     det ? s.cellof : nullptr, s.tile);
   else
-    k_dig_apply<T, 2><<<blocks, WPB * 32, sm, st>>>(cp, s.buf[cur], s.buf[other], s.start[lay], s.count[cin],
-                                                    s.start[olay], s.count[cout], s.nt, target, iter, s.scratch_i,
+    k_dig_apply<T, 2><<<blocks, WPB * 32, sm, st>>>(s.cases.cp, s.cases.cell_case, s.cases.cell0, ncells, s.buf[cur],
+                                                    s.buf[other], s.start[lay], s.count[cin], s.start[olay],
+                                                    s.count[cout], s.nt, target, iter, s.scratch_i,
                                                     det ? s.cellof : nullptr, s.tile);
-  if (!det) k_zero_i32<<<grid_for(cp.ncells, 256), 256, 0, st>>>(s.count[cur], cp.ncells);
+  if (!det) k_zero_i32<<<grid_for(ncells, 256), 256, 0, st>>>(s.count[cur], ncells);
   cur = other;
   lay = olay;
 }
@@ -1127,13 +1246,16 @@ template <typename T>
 void Ops<T>::configure(int tile) {
   const int sm = (int)tile_smem<T>(tile);
   const int smd = WPB * tile * 2 * (int)sizeof(int32_t);
-  cudaFuncSetAttribute(k_collide_sample<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_collide_sample<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_collide_sample<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_dig_apply<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
   cudaFuncSetAttribute(k_dig_apply<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
   if constexpr (sizeof(T) == 4) {
     const int smf = (int)fused_smem_bytes(tile);
-    cudaFuncSetAttribute(k_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf);
-    cudaFuncSetAttribute(k_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf);
+    cudaFuncSetAttribute(k_fused<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf);
+    cudaFuncSetAttribute(k_fused<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf);
+    cudaFuncSetAttribute(k_fused<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf);
+    cudaFuncSetAttribute(k_fused<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf);
   }
 }
 

@@ -30,10 +30,10 @@ def dig_iteration(sim: "dsmc.Dsmc", n_s: int, allow_not_converged: bool = True) 
     sim.dsmc_step(n_s, sample=True)
     f = sim.dsmc_sample(reset=True)
     hot, kn, mask = sim.dsmc_hot(f)
-    out, iters, res = sim.synth_solve(f, hot, allow_not_converged=allow_not_converged)
+    out, iters, res = sim.synth_solve(f, hot, allow_not_converged=allow_not_converged, allow_fallback=True)
     sim.dig_correct(out)
     return {"fields": f, "target": out, "synth_iters": iters, "synth_resid": res,
-            "mask_fraction": float(mask.float().mean().item())}
+            "synth_status": sim.last_synth_status, "mask_fraction": float(mask.float().mean().item())}
 
 
 def total_temperature(f: np.ndarray, d_r: float = 2.0) -> np.ndarray:

@@ -27,7 +27,7 @@ SYMBOLS = ["dsmc_workspace_size", "dsmc_init", "dsmc_destroy", "dsmc_last_error"
            "dsmc_hot", "synth_solve", "dig_correct", "dsmc_num_particles", "dsmc_get_particles",
            "dsmc_set_particles", "dsmc_get_accumulators", "dsmc_get_sgmax", "dsmc_set_sgmax",
            "dsmc_get_counters", "dsmc_set_counters", "dsmc_get_stats", "dsmc_get_wall_tally",
-           "dsmc_get_constants", "synth_solve_noalloc"]
+           "dsmc_get_constants", "synth_solve_noalloc", "dsmc_batch_workspace_size", "dsmc_batch_init"]
 
 
 class DsmcConfig(ctypes.Structure):
@@ -99,6 +99,8 @@ def load(build_if_missing: bool = True):
         "dsmc_get_wall_tally": ([H, P], ctypes.c_int),
         "dsmc_get_constants": ([H, P], ctypes.c_int),
         "synth_solve_noalloc": ([P, P, P, P, P, P, P], ctypes.c_int),
+        "dsmc_batch_workspace_size": ([P, ctypes.c_int, P], ctypes.c_int),
+        "dsmc_batch_init": ([P, ctypes.c_int, P, ctypes.c_size_t, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -140,23 +142,38 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
-class Dsmc:
-    """One simulation: a handle of the C library plus its torch-owned workspace."""
+def _ncells(cfg: dict) -> int:
+    return int(cfg["nx"]) * (int(cfg.get("ny", 1)) if int(cfg["dim"]) == 2 else 1)
 
-    def __init__(self, cfg: dict, device="cuda", stream: torch.cuda.Stream | None = None):
+
+class Dsmc:
+    """One simulation, or a batch of independent ones (a list of configs),
+    held by a handle of the C library plus its torch-owned workspace.  In a
+    batch the cells are numbered case after case (``cell0`` gives the
+    offsets)."""
+
+    def __init__(self, cfg, device="cuda", stream: torch.cuda.Stream | None = None):
         L = load()
-        self.cfg = dict(cfg)
-        self._c = make_config(cfg)
+        cfgs = list(cfg) if isinstance(cfg, (list, tuple)) else [cfg]
+        self.cfgs = [dict(c) for c in cfgs]
+        self.cfg = self.cfgs[0]
+        arr = (DsmcConfig * len(cfgs))(*[make_config(c) for c in cfgs])
+        self._c = arr
+        n = len(cfgs)
         nbytes = ctypes.c_size_t()
-        self._check(L.dsmc_workspace_size(ctypes.byref(self._c), ctypes.byref(nbytes)), None)
+        self._check(L.dsmc_batch_workspace_size(arr, n, ctypes.byref(nbytes)), None)
         self.device = torch.device(device)
         self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = ctypes.c_void_p()
-        self._check(L.dsmc_init(ctypes.byref(self._c), _ptr(self.workspace), nbytes.value,
-                                ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), None)
+        self._check(L.dsmc_batch_init(arr, n, _ptr(self.workspace), nbytes.value,
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), None)
         self._h = h
-        self.ncells = int(cfg["nx"]) * (int(cfg.get("ny", 1)) if int(cfg["dim"]) == 2 else 1)
+        self.ncases = n
+        self.cell0 = [0]
+        for c in self.cfgs:
+            self.cell0.append(self.cell0[-1] + _ncells(c))
+        self.ncells = self.cell0[-1]
 
     def _check(self, rc, h="self", allow=()):
         if rc == DSMC_OK or rc in allow:
@@ -194,13 +211,19 @@ class Dsmc:
         self._check(load().dsmc_hot(self._h, _ptr(fields.contiguous()), _ptr(hot), _ptr(kn), _ptr(mask)))
         return hot, kn, mask
 
-    def synth_solve(self, fields: torch.Tensor, hot: torch.Tensor, allow_not_converged: bool = False):
+    def synth_solve(self, fields: torch.Tensor, hot: torch.Tensor, allow_not_converged: bool = False,
+                    allow_fallback: bool = False):
+        """Returns (targets, iterations, max residual); with allow_fallback a
+        slab without an admissible solution keeps its sampled fields instead
+        of raising (the status is in self.last_synth_status)."""
         out = torch.empty((self.ncells, NTARGET), dtype=torch.float64, device=self.device)
         it = ctypes.c_int()
         res = ctypes.c_double()
         rc = load().synth_solve(self._h, _ptr(fields.contiguous()), _ptr(hot.contiguous()), _ptr(out),
                                 ctypes.byref(it), ctypes.byref(res))
-        self._check(rc, allow=(-4,) if allow_not_converged else ())
+        allow = ((-4,) if allow_not_converged else ()) + ((-3,) if allow_fallback else ())
+        self._check(rc, allow=allow)
+        self.last_synth_status = rc
         return out, it.value, res.value
 
     def dig_correct(self, target: torch.Tensor):

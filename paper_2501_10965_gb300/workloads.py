@@ -120,3 +120,35 @@ def with_overrides(cfg: dict, **kw) -> dict:
     out = copy.deepcopy(cfg)
     out.update(kw)
     return out
+
+
+def ensemble_1d(ncases: int = 64, seed: int = 0, **kw) -> list:
+    """Batched ensemble: `ncases` independent 1D cases drawn with a seeded
+    generator: cells uniform in 50..800, particles per cell uniform in 50..200,
+    Kn log-uniform in [1e-3, 1], Z_rot in {2, 5, 10}; even cases are Fourier
+    (walls at 273 K / 373 K), odd ones Couette (walls at -/+100 m/s, 273 K);
+    FP32 particles; case k has Philox seed `seed` + k."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    cases = []
+    for k in range(ncases):
+        nx = int(rng.integers(50, 801))
+        ppc = int(rng.integers(50, 201))
+        kn = float(10 ** rng.uniform(-3, 0))
+        z = float(rng.choice([2.0, 5.0, 10.0]))
+        # dt: CFL rule, capped at half the mean free time Kn sqrt(pi/8)
+        tau = kn * math.sqrt(math.pi / 8.0)
+        if k % 2 == 0:
+            c = fourier_1d(nx=nx, ppc=ppc, kn=kn, z_rot=z, precision="fp32",
+                           dt=min(0.3 * (1.0 / nx) / math.sqrt(373.0 / T_REF_K), 0.5 * tau))
+        else:
+            c = couette_1d(kn=kn, nx=nx, ppc=ppc, z_rot=z, dt=min(0.3 * (1.0 / nx), 0.5 * tau))
+        c["seed"] = seed + k
+        c.update(kw)
+        cases.append(c)
+    return cases
+
+
+def replicas(cfg: dict, n: int, seed0: int = 0) -> list:
+    """`n` copies of one workload with Philox seeds seed0, seed0 + 1, ..."""
+    return [dict(copy.deepcopy(cfg), seed=seed0 + r) for r in range(n)]
