@@ -1,4 +1,5 @@
-"""Throughput benchmark of the DSMC hot path on one GB300.
+"""Throughput benchmark of the DSMC hot path on one GB300, plus the time to
+steady state of DIG against plain DSMC.
 
 A step is one DSMC time step of the whole particle path (free flight with
 diffuse walls, cell indexing and bin sort, NTC/VHS/Borgnakke-Larsen
@@ -67,7 +68,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
@@ -242,7 +243,7 @@ def run_gpu(args):
     # different step counts on the launching stream (the constant parts --
     # the first move-only and last collide-only launch and the bin check --
     # cancel)
-    k1, k2 = 4, 4 + max(8, args.steps // 2)
+    k1, k2 = 4, 4 + max(8, min(args.steps // 2, 200))
     t1 = min(_events_time(lambda: sim.dsmc_step(k1, sample=True), stream) for _ in range(2))
     t2 = min(_events_time(lambda: sim.dsmc_step(k2, sample=True), stream) for _ in range(2))
     per_launch = (t2 - t1) / (k2 - k1)
@@ -273,8 +274,18 @@ def run_gpu(args):
     barrier()
     te = _events_time(e2e, stream)
     e2e_value = n * args.steps * world / te
+    stats = sim.stats()
+    ncells = sim.ncells
 
     gpu_launches = (args.steps + 1) + 5 * (reb1 - reb0)
+    tts = None
+    if rank == 0 and not args.no_time_to_steady:
+        from paper_2501_10965_gb300 import dig, workloads as Wk
+        del sim, p, fields_host
+        torch.cuda.empty_cache()
+        tts = dig.time_to_steady_dig_vs_plain(Wk.couette_1d(kn=0.01, kn_ref=0.1), replicas=args.tts_replicas)
+        tts["workload"] = ("1D Couette, Kn 0.01, 200 cells x 200 particles, walls -/+100 m/s; DIG every 50 steps, "
+                           "Kn_ref 0.1; ensemble of replicas in one batched handle")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg)
@@ -283,7 +294,7 @@ def run_gpu(args):
                 "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
                 "data": "synthetic",
-                "config": {"workload": args.workload, "cells": sim.ncells, "particles": n,
+                "config": {"workload": args.workload, "cells": ncells, "particles": n,
                            "particles_per_cell": cfg["ppc"], "kn": cfg["kn"], "dt": cfg["dt"],
                            "precision": prec + " particles, fp64 compensated moments",
                            "l2": "inputs larger than L2 (particle state %.2f GB)" % (n * 24 / 1e9),
@@ -292,7 +303,8 @@ def run_gpu(args):
                 "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d / args.steps,
                         "d2h_bytes_per_step": d2h / args.steps},
                 "cpu_baseline": cpu,
-                "stats": sim.stats()}
+                "time_to_steady": tts,
+                "stats": stats}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -301,13 +313,15 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="cavity2d_20m")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per fused launch from an ncu capture of the current kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-steady", action="store_true")
+    ap.add_argument("--tts-replicas", type=int, default=800)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run warm-up + this many steps (for profiler captures)")
     args = ap.parse_args()

@@ -47,11 +47,15 @@ def binned(a: np.ndarray, nbins: int) -> np.ndarray:
 
 
 class Ensemble:
-    """R independent replicas of one workload (seeds seed0 + r)."""
+    """R independent replicas of one 1D workload (seeds seed0 + r), held in
+    one batched handle so that each stage is one launch for all of them."""
 
     def __init__(self, cfg: dict, replicas: int, seed0: int = 0):
+        from . import workloads
         self.cfg = dict(cfg)
-        self.sims = [dsmc.Dsmc(dict(cfg, seed=seed0 + r)) for r in range(replicas)]
+        self.R = replicas
+        self.nx = int(cfg["nx"])
+        self.sim = dsmc.Dsmc(workloads.replicas(cfg, replicas, seed0))
         self.steps = 0
         self.wall = 0.0  # GPU wall time spent in the method's calls, seconds
 
@@ -63,23 +67,25 @@ class Ensemble:
         self.wall += time.perf_counter() - t0
         return out
 
+    def _per_replica(self, f: torch.Tensor) -> np.ndarray:
+        return f.cpu().numpy().reshape(self.R, self.nx, -1)
+
     def advance_plain(self, nsteps: int) -> np.ndarray:
         def run():
-            fs = []
-            for s in self.sims:
-                s.dsmc_step(nsteps, sample=True)
-                fs.append(s.dsmc_sample(reset=True))
-            return fs
-        fs = self._timed(run)
+            self.sim.dsmc_step(nsteps, sample=True)
+            return self.sim.dsmc_sample(reset=True)
+        f = self._timed(run)
         self.steps += nsteps
-        return torch.stack(fs).cpu().numpy()
+        return self._per_replica(f)
+
+    def advance_quiet(self, nsteps: int):
+        self._timed(lambda: self.sim.dsmc_step(nsteps, sample=False))
+        self.steps += nsteps
 
     def advance_dig(self, n_s: int) -> np.ndarray:
-        def run():
-            return [dig_iteration(s, n_s)["fields"] for s in self.sims]
-        fs = self._timed(run)
+        f = self._timed(lambda: dig_iteration(self.sim, n_s)["fields"])
         self.steps += n_s
-        return torch.stack(fs).cpu().numpy()
+        return self._per_replica(f)
 
 
 def window_error(fs: np.ndarray, ref_u: np.ndarray, ref_t: np.ndarray, flow_axis: int, nbins: int):
@@ -115,16 +121,19 @@ def reference_solution(cfg: dict, replicas: int, transient_steps: int, average_s
     done = 0
     while done < transient_steps:
         k = min(window * 20, transient_steps - done)
-        for s in ens.sims:
-            s.dsmc_step(k, sample=False)
+        ens.advance_quiet(k)
         done += k
-    acc = None
+    wins = []
     nwin = max(1, average_steps // window)
     for _ in range(nwin):
-        fs = ens.advance_plain(window)
-        acc = fs.mean(0) if acc is None else acc + fs.mean(0)
-    mean = acc / nwin
-    return binned(mean[:, 1 + flow_axis], nbins), binned(total_temperature(mean), nbins), mean
+        wins.append(ens.advance_plain(window).mean(0))
+    mean = np.mean(wins, axis=0)
+    ref_u = binned(mean[:, 1 + flow_axis], nbins)
+    ref_t = binned(total_temperature(mean), nbins)
+    # noise floor of the window error at steady state: median over the
+    # averaging windows of their error against the long-run mean
+    floor = [max(window_error(w[None], ref_u, ref_t, flow_axis, nbins)) for w in wins]
+    return ref_u, ref_t, mean, float(np.median(floor))
 
 
 def measure(cfg: dict, method: str, replicas: int, window: int, max_steps: int, ref_u, ref_t, flow_axis: int,
@@ -151,3 +160,26 @@ def measure(cfg: dict, method: str, replicas: int, window: int, max_steps: int, 
                     "err_u": eu_hist, "err_T": et_hist, "steps": steps, "wall": walls}
     return {"method": method, "steady_step": None, "steady_wall_s": None, "err_u": eu_hist, "err_T": et_hist,
             "steps": steps, "wall": walls}
+
+
+def time_to_steady_dig_vs_plain(cfg: dict, replicas: int = 800, window: int = 100, nbins: int = 20,
+                                transient: int = 50000, average: int = 15000, threshold: float = 0.01,
+                                max_dig: int = 6000, max_plain: int = 60000) -> dict:
+    """Time to steady state at `threshold` field error, DIG against plain
+    DSMC, both on the GPU from the same uniform initial state, ensemble of
+    `replicas` (one batched handle) against the long-run plain-DSMC reference
+    of an independent ensemble."""
+    t0 = time.perf_counter()
+    ref_u, ref_t, _, floor = reference_solution(cfg, replicas, transient, average, window, 1, nbins)
+    t_ref = time.perf_counter() - t0
+    out = {"replicas": replicas, "particles": replicas * int(cfg["nx"]) * int(cfg["ppc"]), "window": window,
+           "bins": nbins, "threshold": threshold, "noise_floor": floor, "reference_wall_s": t_ref}
+    for method, cap in (("dig", max_dig), ("plain", max_plain)):
+        r = measure(cfg, method, replicas, window, cap, ref_u, ref_t, 1, nbins, threshold)
+        out[method] = {"steady_step": r["steady_step"], "steady_wall_s": r["steady_wall_s"],
+                       "final_err_u": r["err_u"][-1], "final_err_T": r["err_T"][-1]}
+    d, pl = out["dig"], out["plain"]
+    if d["steady_wall_s"] and pl["steady_wall_s"]:
+        out["speedup_wall"] = pl["steady_wall_s"] / d["steady_wall_s"]
+        out["speedup_steps"] = pl["steady_step"] / d["steady_step"]
+    return out
