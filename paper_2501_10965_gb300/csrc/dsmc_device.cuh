@@ -438,10 +438,14 @@ __device__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restri
   int pi = 0, pj = 0;
   T uacc = T(0), uinel = T(0);
   const T fn = T(n), fn1 = T(n - 1);
+  const unsigned below = (1u << lane) - 1u;
+  // A lane keeps its candidate until it runs; free lanes take the next
+  // candidates in order, so the window is always every unprocessed candidate
+  // below `next` (which lane holds which does not matter).
   for (;;) {
-    const int np = __popc(__ballot_sync(FULL, has));
+    const unsigned freem = __ballot_sync(FULL, !has);
     if (!has) {
-      const uint32_t kk = next + (uint32_t)(lane - np);
+      const uint32_t kk = next + (uint32_t)__popc(freem & below);
       if (kk < M) {
         T u4[4];
         draw4(TAG_COLL, kk, cell, step, 0u, p.k0, p.k1, u4);
@@ -460,7 +464,7 @@ __device__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restri
       }
     }
     {
-      const uint32_t room = (uint32_t)(32 - np);
+      const uint32_t room = (uint32_t)__popc(freem);
       next = (M - next > room) ? next + room : M;
     }
     if (__ballot_sync(FULL, has) == 0u) break;
@@ -481,8 +485,14 @@ __device__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restri
       const T gy = vy[pi] - vy[pj];
       const T gz = vz[pi] - vz[pj];
       const T g2 = gx * gx + gy * gy + gz * gz;
-      const T g = m_sqrt(g2);
-      const T sg = p.c_sigma * m_pow(g, p.vhs_e);
+      T sg;
+      if constexpr (sizeof(T) == 4) {
+        // g^(2 - 2 omega) = (g^2)^(1 - omega): no square root
+        const T he = T(0.5) * p.vhs_e;
+        sg = p.c_sigma * ((g2 > T(0)) ? m_pow(g2, he) : (he == T(0) ? T(1) : T(0)));
+      } else {
+        sg = p.c_sigma * m_pow(m_sqrt(g2), p.vhs_e);
+      }
       if (sg > obs) obs = sg;
       cc.cand += 1;
       if (uacc * sgmax < sg) {
@@ -523,15 +533,7 @@ __device__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restri
       }
     }
     __syncwarp();
-    const unsigned rem = __ballot_sync(FULL, has && !ready);
-    const int nr = __popc(rem);
-    const int src = (lane < nr) ? (int)__fns(rem, 0u, lane + 1) : lane;
-    k = __shfl_sync(FULL, k, src);
-    pi = __shfl_sync(FULL, pi, src);
-    pj = __shfl_sync(FULL, pj, src);
-    uacc = __shfl_sync(FULL, uacc, src);
-    uinel = __shfl_sync(FULL, uinel, src);
-    has = lane < nr;
+    has = has && !ready;
   }
   // (sigma g)_max takes the largest sigma g seen in the step
 #pragma unroll
@@ -620,6 +622,105 @@ __device__ void sample_cell(const T* __restrict__ vx, const T* __restrict__ vy,
     acc[lane] = t;
     comp[lane] = cprev + cmp;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Warp sum of 17 per-lane values by recursive halving (reduce-scatter): at
+// each level a lane keeps half of its values and adds its partner's copy of
+// that half (offsets 16, 8, 4, 2, 1; sizes 17 -> 9 -> 5 -> 3 -> 2 -> 1), 20
+// shuffles instead of 17 x 5.  Lane L ends with the warp total of value
+// halving_moment(L), or nothing (-1); every value lands on exactly one lane.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int halving_moment(int lane) {
+  int j = (lane & 1) ? 1 : 0;
+  bool ok = true;
+  j = (lane & 2) ? 2 + j : j;
+  ok = ok && j < 3;
+  j = (lane & 4) ? 3 + j : j;
+  ok = ok && j < 5;
+  j = (lane & 8) ? 5 + j : j;
+  ok = ok && j < 9;
+  j = (lane & 16) ? 9 + j : j;
+  ok = ok && j < 17;
+  return ok ? j : -1;
+}
+
+template <int S, int OFF>
+__device__ __forceinline__ void halving_level(const float* in, float* out, int lane) {
+  constexpr int H = (S + 1) / 2;
+  const bool up = (lane & OFF) != 0;
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const float lo = in[i];
+    const float hi = (i + H < S) ? in[i + H] : 0.f;
+    out[i] = (up ? hi : lo) + __shfl_xor_sync(FULL, up ? lo : hi, OFF);
+  }
+}
+
+__device__ __forceinline__ float halving_sum17(const float* v, int lane) {
+  float a[9], b[5], c[3], d[2], e[1];
+  halving_level<17, 16>(v, a, lane);
+  halving_level<9, 8>(a, b, lane);
+  halving_level<5, 4>(b, c, lane);
+  halving_level<3, 2>(c, d, lane);
+  halving_level<2, 1>(d, e, lane);
+  return e[0];
+}
+
+// FP32 particles: this step's sums of one cell, added to the Kahan-compensated
+// FP32 staging pair of moment `mom` (the lane's moment, halving_moment(lane);
+// pre32 holds the lane's (stg, stc) loaded earlier).  With `flush` the staged
+// sum is folded into the compensated FP64 accumulators (pre: the lane's acc,
+// comp) and the staging pair is cleared.
+__device__ inline void sample_cell_staged(const float* __restrict__ vx, const float* __restrict__ vy,
+                                   const float* __restrict__ vz, const float* __restrict__ ir, int n, int mom,
+                                   double* __restrict__ acc, double* __restrict__ comp, const double* pre,
+                                   float* __restrict__ stg, float* __restrict__ stc, const float* pre32,
+                                   bool flush) {
+  const int lane = threadIdx.x & 31;
+  float s[NMOM];
+#pragma unroll
+  for (int q = 0; q < NMOM; ++q) s[q] = 0.f;
+  for (int q = lane; q < n; q += 32) {
+    const float a = vx[q], b = vy[q], c = vz[q], e = ir[q];
+    const float v2 = a * a + b * b + c * c;
+    s[0] += 1.f;
+    s[1] += a;
+    s[2] += b;
+    s[3] += c;
+    s[4] += a * a;
+    s[5] += b * b;
+    s[6] += c * c;
+    s[7] += a * b;
+    s[8] += a * c;
+    s[9] += b * c;
+    s[10] += a * v2;
+    s[11] += b * v2;
+    s[12] += c * v2;
+    s[13] += e;
+    s[14] += e * a;
+    s[15] += e * b;
+    s[16] += e * c;
+  }
+  const float tot = halving_sum17(s, lane);
+  if (mom < 0) return;
+  const float s0 = pre32[0], c0 = pre32[1];
+  const float yk = tot - c0;
+  const float tk = s0 + yk;
+  const float ck = (tk - s0) - yk;
+  if (!flush) {
+    stg[mom] = tk;
+    stc[mom] = ck;
+    return;
+  }
+  stg[mom] = 0.f;
+  stc[mom] = 0.f;
+  const double v = (double)tk - (double)ck;
+  const double a = pre[0], cprev = pre[1];
+  const double t = a + v;
+  const double cmp = (fabs(a) >= fabs(v)) ? ((a - t) + v) : ((v - t) + a);
+  acc[mom] = t;
+  comp[mom] = cprev + cmp;
 }
 
 }  // namespace dsmc

@@ -433,12 +433,14 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ 
   __shared__ unsigned s_cnt[4];
   __shared__ unsigned s_misc[2];
   __shared__ float s_tally[20];
+  __shared__ unsigned long long s_hits[2];
   __shared__ unsigned s_done;
   __shared__ int s_nb[FWPB][4][12];  // per warp: count, base, bin start, bin capacity
   __shared__ __align__(8) uint64_t s_bar[FWPB];
   if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
   if (threadIdx.x < 2) s_misc[threadIdx.x] = 0;
   if (threadIdx.x < 20) s_tally[threadIdx.x] = 0.f;
+  if (threadIdx.x < 2) s_hits[threadIdx.x] = 0;
   if (threadIdx.x == 0) s_done = 0;
   if (threadIdx.x < FWPB) mbar_init(&s_bar[threadIdx.x], 1);
   mbar_fence_init();
@@ -455,12 +457,13 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ 
       const bool flush = (flags & 8) != 0;
       double pre[2] = {0.0, 0.0};
       float pre32[2] = {0.f, 0.f};
-      if ((flags & 2) && lane < NMOM) {
-        pre32[0] = stg[(size_t)cell * NMOM + lane];
-        pre32[1] = stc[(size_t)cell * NMOM + lane];
+      const int mom = halving_moment(lane);
+      if ((flags & 2) && mom >= 0) {
+        pre32[0] = stg[(size_t)cell * NMOM + mom];
+        pre32[1] = stc[(size_t)cell * NMOM + mom];
         if (flush) {
-          pre[0] = acc[(size_t)cell * NMOM + lane];
-          pre[1] = comp[(size_t)cell * NMOM + lane];
+          pre[0] = acc[(size_t)cell * NMOM + mom];
+          pre[1] = comp[(size_t)cell * NMOM + mom];
         }
       }
       float* tvx = reinterpret_cast<float*>(smem + (size_t)warp * tile * 28);
@@ -512,7 +515,7 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ 
           __syncwarp();
         }
         if (flags & 2)
-          sample_cell<float>(vx, vy, vz, ir, n, acc + (size_t)cell * NMOM, comp + (size_t)cell * NMOM, pre,
+          sample_cell_staged(vx, vy, vz, ir, n, mom, acc + (size_t)cell * NMOM, comp + (size_t)cell * NMOM, pre,
                              stg + (size_t)cell * NMOM, stc + (size_t)cell * NMOM, pre32, flush);
         if (flags & 4) {
           int* nb_cnt = s_nb[warp][0];
@@ -547,7 +550,7 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ 
             float x = px[q], y = (DIM == 2) ? py[q] : 0.f;
             float a = vx[q], b = vy[q], c = vz[q], e = ir[q];
             fly<float, DIM, true>(p, x, y, a, b, c, e, (uint32_t)q, (uint32_t)lcell, step_m, s_tally,
-                                  stats + ST_HITS, stats + ST_MAXHIT);
+                                  &s_hits[0], &s_hits[1]);
             const uint32_t tag = own[q];
             const int code = (int)(tag >> 24), r = (int)(tag & 0xFFFFFFu);
             int d, slot, s0, cap;
@@ -621,7 +624,7 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ 
         c = ovi.vz[q];
         e = ovi.ir[q];
         fly<float, DIM, true>(p, x, y, a, bb, c, e, (uint32_t)q, (uint32_t)(p.ncells + 1), step_m, s_tally,
-                              stats + ST_HITS, stats + ST_MAXHIT);
+                              &s_hits[0], &s_hits[1]);
         d = c0 + cell_of<float, DIM>(p, x, y);
       }
       append_particle<DIM>(pk, out, start, cnt_out, ovo, ovf_cap, active, d, x, y, a, bb, c, e, s_misc);
@@ -638,6 +641,8 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ 
     if (lane < 4 && s_cnt[lane]) atomicAdd(stats + lane, (unsigned long long)s_cnt[lane]);
     if (lane == 4 && s_misc[0]) atomicAdd(stats + ST_OVF, (unsigned long long)s_misc[0]);
     if (lane == 5 && s_misc[1]) atomicAdd(stats + ST_NEARFULL, (unsigned long long)s_misc[1]);
+    if (lane == 6 && s_hits[0]) atomicAdd(stats + ST_HITS, s_hits[0]);
+    if (lane == 7 && s_hits[1]) atomicAdd(stats + ST_MAXHIT, s_hits[1]);
     if (lane < 20 && s_tally[lane] != 0.f) atomicAdd(tally_g + lane, (double)s_tally[lane]);
   }
 }
