@@ -142,15 +142,22 @@ __device__ __forceinline__ void draw4(uint32_t tag, uint32_t c0, uint32_t c1, ui
 // uniforms 4..8 of the stream (blocks 2, 3, 4).  FP32: one block gives
 // u4..u7 from the top 23 bits of its four words and u8 from 23 of the 36
 // unused low bits (9 of word 0, 9 of word 1, 5 of word 2).
-__device__ __forceinline__ void draw_post(uint32_t m, uint32_t cell, uint32_t step, uint32_t k0, uint32_t k1,
-                                          float* u) {
-  const uint4 w = philox4x32_10(m, cell, step, (4u << 24) | 1u, k0, k1);
+__device__ __forceinline__ uint4 post_block(uint32_t m, uint32_t cell, uint32_t step, uint32_t k0, uint32_t k1) {
+  return philox4x32_10(m, cell, step, (4u << 24) | 1u, k0, k1);
+}
+
+__device__ __forceinline__ void post_from_block(const uint4& w, float* u) {
   u[0] = u01_from_word(w.x);
   u[1] = u01_from_word(w.y);
   u[2] = u01_from_word(w.z);
   u[3] = u01_from_word(w.w);
   const uint32_t m8 = ((w.x & 0x1FFu) << 14) | ((w.y & 0x1FFu) << 5) | (w.z & 0x1Fu);
   u[4] = ((float)m8 + 0.5f) * 0x1p-23f;
+}
+
+__device__ __forceinline__ void draw_post(uint32_t m, uint32_t cell, uint32_t step, uint32_t k0, uint32_t k1,
+                                          float* u) {
+  post_from_block(post_block(m, cell, step, k0, k1), u);
 }
 
 __device__ __forceinline__ void draw_post(uint32_t m, uint32_t cell, uint32_t step, uint32_t k0, uint32_t k1,
@@ -418,7 +425,7 @@ struct CollCount {
 };
 
 template <typename T>
-__device__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restrict__ vy,
+__device__ __forceinline__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restrict__ vy,
                              T* __restrict__ vz, T* __restrict__ ir, int n, uint32_t cell,
                              uint32_t step, T* sgmax_ptr, uint32_t* owner, CollCount& cc) {
   const int lane = threadIdx.x & 31;
@@ -437,6 +444,9 @@ __device__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restri
   uint32_t k = 0;
   int pi = 0, pj = 0;
   T uacc = T(0), uinel = T(0);
+  // FP32: the candidate's post-collision block is drawn with it, while every
+  // lane still has a candidate to draw (later rounds run with few lanes)
+  uint4 wpost = make_uint4(0u, 0u, 0u, 0u);
   const T fn = T(n), fn1 = T(n - 1);
   const unsigned below = (1u << lane) - 1u;
   // A lane keeps its candidate until it runs; free lanes take the next
@@ -449,6 +459,7 @@ __device__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restri
       if (kk < M) {
         T u4[4];
         draw4(TAG_COLL, kk, cell, step, 0u, p.k0, p.k1, u4);
+        if constexpr (sizeof(T) == 4) wpost = post_block(kk, cell, step, p.k0, p.k1);
         const T u0 = u4[0], u1 = u4[1];
         uacc = u4[2];
         uinel = u4[3];
@@ -499,7 +510,8 @@ __device__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restri
         cc.coll += 1;
         if (sg > sgmax) cc.clip += 1;
         T up[5];
-        draw_post(k, cell, step, p.k0, p.k1, up);
+        if constexpr (sizeof(T) == 4) post_from_block(wpost, up);
+        else draw_post(k, cell, step, p.k0, p.k1, up);
         T et = T(0.25) * g2;
         if (uinel < p.p_inel) {
           const T ec = et + ir[pi];
@@ -672,7 +684,7 @@ __device__ __forceinline__ float halving_sum17(const float* v, int lane) {
 // pre32 holds the lane's (stg, stc) loaded earlier).  With `flush` the staged
 // sum is folded into the compensated FP64 accumulators (pre: the lane's acc,
 // comp) and the staging pair is cleared.
-__device__ inline void sample_cell_staged(const float* __restrict__ vx, const float* __restrict__ vy,
+__device__ __forceinline__ void sample_cell_staged(const float* __restrict__ vx, const float* __restrict__ vy,
                                    const float* __restrict__ vz, const float* __restrict__ ir, int n, int mom,
                                    double* __restrict__ acc, double* __restrict__ comp, const double* pre,
                                    float* __restrict__ stg, float* __restrict__ stc, const float* pre32,

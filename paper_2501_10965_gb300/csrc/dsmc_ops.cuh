@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "dsmc_device.cuh"
@@ -487,11 +488,15 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ 
         if (!ok && lane == 0) atomicOr(errflag, 1);
       }
       ok = __all_sync(FULL, ok);
-      if (ok) {
+      // The cell body is instantiated twice: on the shared-memory tile (the
+      // compiler then addresses it as shared memory) and, for cells above
+      // `tile` particles, in global memory.
+      auto body = [&](auto staged_tag) {
+        constexpr bool STAGED = decltype(staged_tag)::value;
         float *vx, *vy, *vz, *ir;
         const float *px, *py;
         uint32_t* own;
-        if (staged) {
+        if constexpr (STAGED) {
           vx = tvx;
           vy = tvx + tile;
           vz = tvx + 2 * tile;
@@ -553,9 +558,8 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ 
                                   &s_hits[0], &s_hits[1]);
             const uint32_t tag = own[q];
             const int code = (int)(tag >> 24), r = (int)(tag & 0xFFFFFFu);
-            int d, slot, s0, cap;
+            int d = -1, slot, s0, cap;
             if (code < 9) {
-              d = neighbour_cell(p.nx, cell, code);
               slot = nb_base[code] + r;
               s0 = nb_s0[code];
               cap = nb_cap[code];
@@ -577,6 +581,7 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ 
             } else {
               // reserved but unused slot: give it back (the bin's count ends
               // at its capacity)
+              if (d < 0) d = neighbour_cell(p.nx, cell, code);
               atomicSub(&cnt_out[d], 1);
               const int qo = atomicAdd(ovo.count, 1);
               atomicAdd(s_misc + 0, 1u);
@@ -593,7 +598,7 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ 
           }
           __syncwarp();
           if (lane == 0) cnt_in[cell] = 0;
-        } else if (staged && (flags & 1)) {
+        } else if (STAGED && (flags & 1)) {
           for (int q = lane; q < n; q += 32) {
             in.vx[base + q] = vx[q];
             in.vy[base + q] = vy[q];
@@ -601,6 +606,10 @@ __global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ 
             in.ir[base + q] = ir[q];
           }
         }
+      };
+      if (ok) {
+        if (staged) body(std::true_type{});
+        else body(std::false_type{});
       }
     }
   } else if (flags & 4) {
