@@ -674,6 +674,7 @@ __global__ void __launch_bounds__(1024) k_synth_solve(const __grid_constant__ Sy
 
 __global__ void __launch_bounds__(1024) k_synth_final(const __grid_constant__ SynthCases scs, double* out_all) {
   __shared__ double red[1024];
+  __shared__ double s_status;
   const int cs = blockIdx.x;
   const SynthArgs a = case_args(scs, cs);
   const int n = a.cp.nx;
@@ -681,7 +682,11 @@ __global__ void __launch_bounds__(1024) k_synth_final(const __grid_constant__ Sy
   double* out = out_all + (size_t)(scs.cell0 ? scs.cell0[cs] : 0) * 6;
   double* info = scs.info + 3 * cs;
   const double P = w.sc[SC_P];
-  double rmax = 0.0;
+  // an iterate is used (converged, or at the iteration cap) only if it is
+  // finite and positive and keeps the sampled mass (the mass condition is
+  // not linear in the unknowns, so an unconverged iterate may break it);
+  // otherwise the slab keeps its sampled fields
+  double rmax = 0.0, msol = 0.0, msmp = 0.0, bad = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double ym[4], y0[4], yp[4], r[4];
     for (int v = 0; v < 4; ++v) {
@@ -691,12 +696,30 @@ __global__ void __launch_bounds__(1024) k_synth_final(const __grid_constant__ Sy
     }
     local_res(a, i, n, ym, y0, yp, P, r);
     for (int v = 0; v < 4; ++v) rmax = fmax(rmax, fabs(r[v]));
+    const double rho = (P - a.hot[(size_t)i * 12]) / y0[2];
+    if (!(rho > 0.0) || !(y0[2] > 0.0) || !(y0[3] > 0.0) || !isfinite(rho) || !isfinite(y0[0]) || !isfinite(y0[1]))
+      bad = 1.0;
+    msol += rho;
+    msmp += a.F[(size_t)i * 18];
+  }
+  rmax = block_max(rmax, red);
+  bad = block_max(bad, red);
+  msol = block_sum(msol, red);
+  msmp = block_sum(msmp, red);
+  if (threadIdx.x == 0) {
+    double st = w.sc[SC_STATUS];  // 0 converged, 1 iteration cap, 2 numeric
+    if (st != 2.0 && (bad > 0.0 || !(fabs(msol - msmp) <= 1e-6 * msmp))) st = 2.0;
+    s_status = st;
+  }
+  __syncthreads();
+  const bool keep = s_status == 2.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double* o = out + (size_t)i * 6;
-    if (w.sc[SC_STATUS] == 2.0) {
-      // no admissible solution: the slab keeps its sampled fields
+    if (keep) {
       const double* f = a.F + (size_t)i * 18;
       for (int v = 0; v < 6; ++v) o[v] = f[v];
     } else {
+      const double* y0 = w.y + 4 * i;
       o[0] = (P - a.hot[(size_t)i * 12]) / y0[2];
       o[1] = 0.0;
       o[2] = y0[0];
@@ -705,12 +728,10 @@ __global__ void __launch_bounds__(1024) k_synth_final(const __grid_constant__ Sy
       o[5] = y0[3];
     }
   }
-  rmax = block_max(rmax, red);
   if (threadIdx.x == 0) {
     info[0] = w.sc[SC_IT];
     info[1] = rmax;
-    // 0 converged, 1 not converged, 2 numeric
-    info[2] = w.sc[SC_STATUS];  // 0 converged, 1 iteration cap, 2 numeric
+    info[2] = s_status;
   }
 }
 

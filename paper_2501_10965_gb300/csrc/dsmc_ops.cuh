@@ -777,6 +777,46 @@ __global__ void k_keys_from_pos(Params<T> p, const double* __restrict__ x, const
     key[s] = cell_of<T, DIM>(p, (T)x[s], (DIM == 2) ? (T)y[s] : T(0));
 }
 
+// FP32 import: occupancy of every cell (one atomic per group of lanes with
+// the same cell: imported particles often come ordered by cell)
+static __global__ void k_count_keys(const int32_t* __restrict__ key, int n, int32_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  for (int s0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); s0 < n; s0 += gridDim.x * blockDim.x) {
+    const int s = s0 + lane;
+    const int k = (s < n) ? key[s] : -1;
+    const unsigned peers = __match_any_sync(FULL, k);
+    if (k >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[k], __popc(peers));
+  }
+}
+
+// FP32 import: every particle into a slot of its cell's padded bin (the
+// order inside a bin is that of the atomics; the FP32 layout keeps none)
+template <int DIM>
+static __global__ void k_scatter_bins(const double* __restrict__ x, const double* __restrict__ y,
+                                      const double* __restrict__ vx, const double* __restrict__ vy,
+                                      const double* __restrict__ vz, const double* __restrict__ ir,
+                                      const int32_t* __restrict__ key, int n, const int32_t* __restrict__ start,
+                                      int32_t* __restrict__ cnt, PBuf<float> o) {
+  const int lane = threadIdx.x & 31;
+  for (int s0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); s0 < n; s0 += gridDim.x * blockDim.x) {
+    const int s = s0 + lane;
+    const int k = (s < n) ? key[s] : -1;
+    const unsigned peers = __match_any_sync(FULL, k);
+    const int leader = __ffs(peers) - 1;
+    int b = 0;
+    if (k >= 0 && lane == leader) b = atomicAdd(&cnt[k], __popc(peers));
+    b = __shfl_sync(FULL, b, leader);
+    if (k < 0) continue;
+    const int w = start[k] + b + __popc(peers & ((1u << lane) - 1u));
+    o.x[w] = (float)x[s];
+    o.y[w] = (DIM == 2) ? (float)y[s] : 0.f;
+    o.vx[w] = (float)vx[s];
+    o.vy[w] = (float)vy[s];
+    o.vz[w] = (float)vz[s];
+    o.ir[w] = (float)ir[s];
+  }
+}
+
 static __global__ void k_fill_zero_d(double* a, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = 0.0;
 }
@@ -1200,19 +1240,22 @@ void Ops<T>::import_particles(const Params<T>& p, State<T>& s, int& cur, int& la
     return;
   }
   if constexpr (sizeof(T) == 4) {
-    // stable sort into the other buffer as a compact list (start tmp_start,
-    // counts nt), then copy into padded bins of buffer cur, layout lay
-    k_sort_stable<double, T><<<1, 1024, 0, st>>>(x, yy, vx, vy, vz, ir, s.buf[other], s.key, (int)n, p.ncells,
-                                                 s.tmp_start, s.nt, s.tmp2, s.dest, nullptr);
+    // occupancies, bin layout lay, then every particle straight into its bin
+    // of buffer cur (all in parallel; no order is kept inside a bin)
+    const int g = grid_for(p.ncells, 256);
+    k_zero_i32<<<g, 256, 0, st>>>(s.nt, p.ncells);
+    if (n > 0) k_count_keys<<<grid_for(n, 256), 256, 0, st>>>(s.key, (int)n, s.nt);
     k_caps_scan<<<1, 1024, 0, st>>>(s.nt, p.ncells, s.slack, (long long)s.capacity, s.start[lay], s.flags);
-    const int blocks = (p.ncells + WPB - 1) / WPB;
-    if (p.dim == 1)
-      k_rebin_copy<T, 1><<<blocks, WPB * 32, 0, st>>>(s.buf[other], s.buf[cur], s.tmp_start, s.nt, s.start[lay],
-                                                      s.count[cur], p.ncells);
-    else
-      k_rebin_copy<T, 2><<<blocks, WPB * 32, 0, st>>>(s.buf[other], s.buf[cur], s.tmp_start, s.nt, s.start[lay],
-                                                      s.count[cur], p.ncells);
-    k_zero_i32<<<grid_for(p.ncells, 256), 256, 0, st>>>(s.count[other], p.ncells);
+    k_zero_i32<<<g, 256, 0, st>>>(s.count[cur], p.ncells);
+    if (n > 0) {
+      if (p.dim == 1)
+        k_scatter_bins<1><<<grid_for(n, 256), 256, 0, st>>>(x, yy, vx, vy, vz, ir, s.key, (int)n, s.start[lay],
+                                                            s.count[cur], s.buf[cur]);
+      else
+        k_scatter_bins<2><<<grid_for(n, 256), 256, 0, st>>>(x, yy, vx, vy, vz, ir, s.key, (int)n, s.start[lay],
+                                                            s.count[cur], s.buf[cur]);
+    }
+    k_zero_i32<<<g, 256, 0, st>>>(s.count[other], p.ncells);
     cudaMemsetAsync(s.ovf[0].count, 0, sizeof(int32_t), st);
     cudaMemsetAsync(s.ovf[1].count, 0, sizeof(int32_t), st);
   }

@@ -121,6 +121,27 @@ def test_fields_hot_and_synth_match_oracle():
     assert np.allclose(out_g.cpu().numpy(), out_o, rtol=1e-9, atol=1e-11)
 
 
+def test_synth_iterate_keeps_mass_or_falls_back():
+    """An iterate stopped at the iteration cap is used only if it is positive
+    and keeps the sampled mass; otherwise the slab keeps its sampled fields
+    (status NUMERIC).  One Newton iteration on noisy dense-gas input."""
+    for seed in range(3):
+        cfg = W.couette_1d(0.002, nx=120, ppc=30, n_m=1, seed=seed)
+        g = _gpu(cfg)
+        g.dsmc_step(20)
+        g.dsmc_step(10, sample=True)
+        f = g.dsmc_sample(reset=True)
+        hot, _, _ = g.dsmc_hot(f)
+        out, it, res = g.synth_solve(f, hot, allow_not_converged=True, allow_fallback=True)
+        O, F = out.cpu().numpy(), f.cpu().numpy()
+        if g.last_synth_status == -3:
+            assert np.array_equal(O[:, 0], F[:, 0]) and np.array_equal(O[:, 2:6], F[:, 2:6])
+        else:
+            assert g.last_synth_status in (0, -4)
+            assert np.isfinite(O).all() and (O[:, 0] > 0).all() and (O[:, 4:6] > 0).all()
+            assert abs(O[:, 0].sum() / F[:, 0].sum() - 1.0) <= 1e-6
+
+
 def test_dig_correct_matches_oracle_fp64():
     cfg = W.fourier_1d(nx=40, ppc=50)
     g = _gpu(cfg)
@@ -160,7 +181,7 @@ def test_dig_correct_rejects_bad_target_gpu():
         assert np.array_equal(before[k], after[k])
 
 
-def test_set_particles_roundtrip_and_stable_binning():
+def test_set_particles_roundtrip_and_binning():
     for prec in ("fp64", "fp32"):
         cfg = W.cavity_2d(nx=7, ny=5, ppc=10, precision=prec)
         g = _gpu(cfg)
@@ -175,8 +196,15 @@ def test_set_particles_roundtrip_and_stable_binning():
         out = _np(g.get_particles())
         cell = np.minimum((x * 7).astype(int), 6) + 7 * np.minimum((y * 5).astype(int), 4)
         order = np.argsort(cell, kind="stable")
-        assert np.array_equal(out["vx"], vx[order])
         assert np.array_equal(out["cell"], cell[order])
+        if prec == "fp64":
+            # the deterministic layout keeps the input order inside a cell
+            assert np.array_equal(out["vx"], vx[order])
+        else:
+            # the FP32 bins keep no order: the same particles in every cell
+            for c in range(35):
+                assert np.array_equal(np.sort(out["vx"][out["cell"] == c]), np.sort(vx[cell == c]))
+            assert np.array_equal(np.sort(out["x"]), np.sort(x.astype(np.float32).astype(np.float64)))
 
 
 # ----------------------------------------------------------------------------
@@ -236,10 +264,14 @@ def test_fp32_steady_fourier_matches_fp64_oracle_within_3se():
         do, dg = fo[:, :, col].mean(1), fg[:, :, col].mean(1)
         se = math.sqrt(do.var(ddof=1) / 4 + dg.var(ddof=1) / 4) + 1e-12
         assert abs(do.mean() - dg.mean()) < 3.5 * se + (1e-9 if col == 0 else 0), (name, do, dg)
-        # profiles, cell by cell
+        # profiles, cell by cell; the variance of a cell mean varies smoothly
+        # along the slab, so each cell's is pooled over a 9-cell window (a
+        # 4-seed variance alone has 3 degrees of freedom, whose heavy tail
+        # would put several cells above 3 SE by chance)
         mo, mg = fo[:, :, col].mean(0), fg[:, :, col].mean(0)
-        sec = np.sqrt(fo[:, :, col].var(0, ddof=1) / 4 + fg[:, :, col].var(0, ddof=1) / 4) + 1e-12
-        z = np.abs(mo - mg) / sec
+        var = fo[:, :, col].var(0, ddof=1) / 4 + fg[:, :, col].var(0, ddof=1) / 4
+        pooled = np.convolve(np.pad(var, 4, mode="edge"), np.ones(9) / 9, mode="valid")
+        z = np.abs(mo - mg) / (np.sqrt(pooled) + 1e-12)
         assert (z > 3).sum() <= 5, (name, np.sort(z)[-6:])
     qo = (fo[:, :, 12] + fo[:, :, 15]).mean(1)
     qg = (fg[:, :, 12] + fg[:, :, 15]).mean(1)
