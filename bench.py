@@ -28,6 +28,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 ALGO_BYTES_PER_PARTICLE_STEP = {("fp32", 2): 48, ("fp32", 1): 40, ("fp64", 2): 96, ("fp64", 1): 80}
+# DRAM bytes (read + write) per particle-step of k_fused, from one ncu capture
+# of the current kernel on the 300 x 225-cell, 11.27 M-particle cavity
+# (dram__bytes_read.sum 336.86 MB + dram__bytes_write.sum 243.33 MB for one
+# launch; profiles/k_fused_cavity2d.md); scaled to a launch of the workload by
+# its particle count.  Re-measure whenever k_fused changes.
+NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP = {("fp32", 2): 580182784 / 11272500}
 METRIC = "particle-steps/s"
 
 
@@ -251,7 +257,10 @@ def run_gpu(args):
     peaks = measured_peaks()
     achieved = algo / per_launch / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": args.traffic,
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": args.traffic if args.traffic is not None else (
+                    NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP[(prec, dim)] * n
+                    if (prec, dim) in NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP else None),
                 "kernel": "k_fused (collide + sample + move + bin append, one launch per step)",
                 "algorithmic_bytes_per_launch": algo, "launch_ms": per_launch * 1e3,
                 "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
