@@ -211,48 +211,57 @@ __device__ __forceinline__ double* case_work(const SynthCases& sc, int c) {
   return sc.work + (sc.woff ? sc.woff[c] : 0);
 }
 
-__device__ __forceinline__ void face_flux(const SynthArgs& a, int i, const double* yl, const double* yr,
-                                          double* sxy, double* sxz, double* qr, double* e) {
+__device__ __forceinline__ double synth_pow(double x, double e) { return pow(x, e); }
+__device__ __forceinline__ float synth_pow(float x, float e) { return exp2f(e * __log2f(x)); }
+
+// Face i+1/2 fluxes: shear stresses, rotational heat flux and energy flux.
+// T = double for the residual; T = float for the finite-difference Jacobian
+// (it only steers Newton's steps: the residual decides the solution).
+template <typename T>
+__device__ __forceinline__ void face_flux(const SynthArgs& a, int i, const T* yl, const T* yr, T* sxy, T* sxz,
+                                          T* qr, T* e) {
   const CellParams& cp = a.cp;
-  const double ttf = 0.5 * (yl[2] + yr[2]);
-  const double trf = 0.5 * (yl[3] + yr[3]);
-  const double Tf = (3.0 * ttf + cp.d_r * trf) / (3.0 + cp.d_r);
-  const double muf = cp.mu_ref * pow(Tf, cp.omega);
+  const T d_r = (T)cp.d_r, dx = (T)cp.dx;
+  const T ttf = T(0.5) * (yl[2] + yr[2]);
+  const T trf = T(0.5) * (yl[3] + yr[3]);
+  const T Tf = (T(3) * ttf + d_r * trf) / (T(3) + d_r);
+  const T muf = (T)cp.mu_ref * synth_pow(Tf, (T)cp.omega);
   const double* hl = a.hot + (size_t)i * 12;
   const double* hr = a.hot + (size_t)(i + 1) * 12;
-  const double h3 = 0.5 * (hl[3] + hr[3]), h4 = 0.5 * (hl[4] + hr[4]);
-  const double h6 = 0.5 * (hl[6] + hr[6]), h9 = 0.5 * (hl[9] + hr[9]);
-  *sxy = -muf * (yr[0] - yl[0]) / cp.dx + h3;
-  *sxz = -muf * (yr[1] - yl[1]) / cp.dx + h4;
-  const double qt = -cp.kappa_t * muf * (yr[2] - yl[2]) / cp.dx + h6;
-  *qr = -cp.kappa_r * muf * (yr[3] - yl[3]) / cp.dx + h9;
-  const double uyf = 0.5 * (yl[0] + yr[0]), uzf = 0.5 * (yl[1] + yr[1]);
+  const T h3 = (T)(0.5 * (hl[3] + hr[3])), h4 = (T)(0.5 * (hl[4] + hr[4]));
+  const T h6 = (T)(0.5 * (hl[6] + hr[6])), h9 = (T)(0.5 * (hl[9] + hr[9]));
+  *sxy = -muf * (yr[0] - yl[0]) / dx + h3;
+  *sxz = -muf * (yr[1] - yl[1]) / dx + h4;
+  const T qt = -(T)cp.kappa_t * muf * (yr[2] - yl[2]) / dx + h6;
+  *qr = -(T)cp.kappa_r * muf * (yr[3] - yl[3]) / dx + h9;
+  const T uyf = T(0.5) * (yl[0] + yr[0]), uzf = T(0.5) * (yl[1] + yr[1]);
   *e = *sxy * uyf + *sxz * uzf + qt + *qr;
 }
 
 // residual rows of cell i from y_{i-1}, y_i, y_{i+1} and P
-__device__ void local_res(const SynthArgs& a, int i, int n, const double* ym, const double* y0,
-                          const double* yp, double P, double* R) {
+template <typename T>
+__device__ void local_res(const SynthArgs& a, int i, int n, const T* ym, const T* y0, const T* yp, T P, T* R) {
   const CellParams& cp = a.cp;
   if (i == 0 || i == n - 1) {
     const double* f = a.F + (size_t)i * 18;
-    R[0] = y0[0] - f[2];
-    R[1] = y0[1] - f[3];
-    R[2] = y0[2] - f[4];
-    R[3] = y0[3] - f[5];
+    R[0] = y0[0] - (T)f[2];
+    R[1] = y0[1] - (T)f[3];
+    R[2] = y0[2] - (T)f[4];
+    R[3] = y0[3] - (T)f[5];
     return;
   }
-  double sxy_p, sxz_p, qr_p, e_p, sxy_m, sxz_m, qr_m, e_m;
-  face_flux(a, i, y0, yp, &sxy_p, &sxz_p, &qr_p, &e_p);
-  face_flux(a, i - 1, ym, y0, &sxy_m, &sxz_m, &qr_m, &e_m);
-  const double rho = (P - a.hot[(size_t)i * 12 + 0]) / y0[2];
-  const double T = (3.0 * y0[2] + cp.d_r * y0[3]) / (3.0 + cp.d_r);
-  const double mu = cp.mu_ref * pow(T, cp.omega);
-  const double src = 0.5 * cp.d_r * rho * (rho * T) * (T - y0[3]) / (cp.z_rot * mu);
+  const T d_r = (T)cp.d_r;
+  T sxy_p, sxz_p, qr_p, e_p, sxy_m, sxz_m, qr_m, e_m;
+  face_flux<T>(a, i, y0, yp, &sxy_p, &sxz_p, &qr_p, &e_p);
+  face_flux<T>(a, i - 1, ym, y0, &sxy_m, &sxz_m, &qr_m, &e_m);
+  const T rho = (P - (T)a.hot[(size_t)i * 12 + 0]) / y0[2];
+  const T Tc = (T(3) * y0[2] + d_r * y0[3]) / (T(3) + d_r);
+  const T mu = (T)cp.mu_ref * synth_pow(Tc, (T)cp.omega);
+  const T src = T(0.5) * d_r * rho * (rho * Tc) * (Tc - y0[3]) / ((T)cp.z_rot * mu);
   R[0] = sxy_p - sxy_m;
   R[1] = sxz_p - sxz_m;
   R[2] = e_p - e_m;
-  R[3] = -(qr_p - qr_m) / cp.dx + src;
+  R[3] = -(qr_p - qr_m) / (T)cp.dx + src;
 }
 
 __device__ void inv4(const double* m, double* r) {
@@ -405,13 +414,15 @@ __global__ void k_synth_jac(const __grid_constant__ SynthCases scs) {
   SynthWork w = synth_work(case_work(scs, cs), n);
   if (w.sc[SC_DONE] != 0.0) return;
   const double P = w.sc[SC_P];
-  double ym[4], y0[4], yp[4], rp[4], rm[4];
+  double ym[4], y0[4], yp[4];
   for (int v = 0; v < 4; ++v) {
     y0[v] = w.y[4 * i + v];
     ym[v] = (i > 0) ? w.y[4 * (i - 1) + v] : y0[v];
     yp[v] = (i < n - 1) ? w.y[4 * (i + 1) + v] : y0[v];
   }
   if (col < 12) {
+    // Jacobian columns by central differences in FP32 (step ~ sqrt of the
+    // FP32 rounding unit)
     const int blk = col / 4, v = col % 4;
     double* J = w.J + 48 * (size_t)i + 16 * blk;
     const bool exists = (blk == 1) || (blk == 0 && i > 0) || (blk == 2 && i < n - 1);
@@ -419,20 +430,36 @@ __global__ void k_synth_jac(const __grid_constant__ SynthCases scs) {
       for (int r = 0; r < 4; ++r) J[r * 4 + v] = 0.0;
       return;
     }
-    double* yy = (blk == 0) ? ym : ((blk == 1) ? y0 : yp);
-    const double sv = yy[v];
-    const double hh = 1e-6 * fmax(fabs(sv), 1.0);
+    float fm[4], f0[4], fp[4], frp[4], frm[4];
+    for (int q = 0; q < 4; ++q) {
+      fm[q] = (float)ym[q];
+      f0[q] = (float)y0[q];
+      fp[q] = (float)yp[q];
+    }
+    float* yy = (blk == 0) ? fm : ((blk == 1) ? f0 : fp);
+    const float sv = yy[v];
+    const float hh = 1e-3f * fmaxf(fabsf(sv), 1.0f);
     yy[v] = sv + hh;
-    local_res(a, i, n, ym, y0, yp, P, rp);
+    local_res<float>(a, i, n, fm, f0, fp, (float)P, frp);
     yy[v] = sv - hh;
-    local_res(a, i, n, ym, y0, yp, P, rm);
-    for (int r = 0; r < 4; ++r) J[r * 4 + v] = (rp[r] - rm[r]) / (2.0 * hh);
+    local_res<float>(a, i, n, fm, f0, fp, (float)P, frm);
+    const float h2 = (sv + hh) - (sv - hh);  // the step actually taken
+    for (int r = 0; r < 4; ++r) J[r * 4 + v] = (double)((frp[r] - frm[r]) / h2);
   } else {
-    local_res(a, i, n, ym, y0, yp, P, w.R + 4 * i);
-    const double hP = 1e-6 * fmax(fabs(P), 1.0);
-    local_res(a, i, n, ym, y0, yp, P + hP, rp);
-    local_res(a, i, n, ym, y0, yp, P - hP, rm);
-    for (int r = 0; r < 4; ++r) w.G[4 * i + r] = (rp[r] - rm[r]) / (2.0 * hP);
+    // the column of P, also in FP32 (the FP64 residual is taken by the solve
+    // kernel, one thread per cell, away from these warps)
+    float fm[4], f0[4], fp[4], frp[4], frm[4];
+    for (int q = 0; q < 4; ++q) {
+      fm[q] = (float)ym[q];
+      f0[q] = (float)y0[q];
+      fp[q] = (float)yp[q];
+    }
+    const float Pf = (float)P;
+    const float hP = 1e-3f * fmaxf(fabsf(Pf), 1.0f);
+    local_res<float>(a, i, n, fm, f0, fp, Pf + hP, frp);
+    local_res<float>(a, i, n, fm, f0, fp, Pf - hP, frm);
+    const float h2 = (Pf + hP) - (Pf - hP);
+    for (int r = 0; r < 4; ++r) w.G[4 * i + r] = (double)((frp[r] - frm[r]) / h2);
     const double Hi = a.hot[(size_t)i * 12];
     w.h[4 * i + 0] = 0.0;
     w.h[4 * i + 1] = 0.0;
@@ -504,6 +531,17 @@ __global__ void __launch_bounds__(1024) k_synth_solve(const __grid_constant__ Sy
   }
   const int tid = threadIdx.x, nt = blockDim.x;
   const double P = w.sc[SC_P];
+  // FP64 residual of every cell at the current iterate
+  for (int i = tid; i < n; i += nt) {
+    double ym[4], y0[4], yp[4];
+    for (int v = 0; v < 4; ++v) {
+      y0[v] = w.y[4 * i + v];
+      ym[v] = (i > 0) ? w.y[4 * (i - 1) + v] : y0[v];
+      yp[v] = (i < n - 1) ? w.y[4 * (i + 1) + v] : y0[v];
+    }
+    local_res<double>(a, i, n, ym, y0, yp, P, w.R + 4 * i);
+  }
+  __syncthreads();
   for (int i = tid; i < n; i += nt) {
     for (int q = 0; q < 16; ++q) {
       w.A[16 * i + q] = (float)w.J[48 * (size_t)i + q];
@@ -694,7 +732,7 @@ __global__ void __launch_bounds__(1024) k_synth_final(const __grid_constant__ Sy
       ym[v] = (i > 0) ? w.y[4 * (i - 1) + v] : y0[v];
       yp[v] = (i < n - 1) ? w.y[4 * (i + 1) + v] : y0[v];
     }
-    local_res(a, i, n, ym, y0, yp, P, r);
+    local_res<double>(a, i, n, ym, y0, yp, P, r);
     for (int v = 0; v < 4; ++v) rmax = fmax(rmax, fabs(r[v]));
     const double rho = (P - a.hot[(size_t)i * 12]) / y0[2];
     if (!(rho > 0.0) || !(y0[2] > 0.0) || !(y0[3] > 0.0) || !isfinite(rho) || !isfinite(y0[0]) || !isfinite(y0[1]))
