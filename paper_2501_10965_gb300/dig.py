@@ -32,8 +32,10 @@ def dig_iteration(sim: "dsmc.Dsmc", n_s: int, allow_not_converged: bool = True) 
     hot, kn, mask = sim.dsmc_hot(f)
     out, iters, res = sim.synth_solve(f, hot, allow_not_converged=allow_not_converged, allow_fallback=True)
     sim.dig_correct(out)
+    # the HoT mask stays on the device (reducing it here would put a host
+    # round trip, and the first use of a framework kernel, into the loop)
     return {"fields": f, "target": out, "synth_iters": iters, "synth_resid": res,
-            "synth_status": sim.last_synth_status, "mask_fraction": float(mask.float().mean().item())}
+            "synth_status": sim.last_synth_status, "mask": mask}
 
 
 def total_temperature(f: np.ndarray, d_r: float = 2.0) -> np.ndarray:
