@@ -264,6 +264,59 @@ int dsmc_get_wall_tally(dsmc_handle *h, double *host_out20);
  * P_inelastic. */
 int dsmc_get_constants(dsmc_handle *h, double *host_out8);
 
+/* ------------------------------------------------------------------------
+ * HoT surrogate network (an extension; the paper has no counterpart: it
+ * takes the higher-order terms of Eq. (hot_constitutive) from the DSMC
+ * moments alone).  Each handle owns one network, 12 -> 64 -> 64 -> 64 -> 5
+ * with tanh hidden layers, FP32 master weights and bfloat16 copies that the
+ * forward and backward kernels use with FP32 accumulation.
+ *
+ * Inputs per cell (12): the gradients of rho, u_x, u_y, T_t, T_r along x and
+ * y, scaled by the local mean free path lambda = mu(T)/(rho T) sqrt(pi T/2)
+ * and by rho, sqrt(T), sqrt(T), T, T respectively, then Kn_GLL and T_r/T_t.
+ * Outputs (5): HoT sigma_xx, sigma_xy, sigma_yy divided by p = rho T, and the
+ * components of HoT q_t and q_r along grad T (x where grad T = 0) divided
+ * by p sqrt(T).  The cells with mask = 1 (Kn_GLL >= kn_ref, as returned by
+ * dsmc_hot) are the training set and the cells where the network replaces
+ * those components; every other HoT component comes from DSMC.
+ *
+ * Parameters (DSMC_MLP_NPARAM floats, host memory): for each layer k = 1..4
+ * the weights W_k (n_out x n_in, row major) then the biases b_k.  dsmc_init
+ * sets them as hot_mlp_init does with the configuration's seed. */
+#define DSMC_MLP_NPARAM 9477
+
+/* Glorot-uniform weights and zero biases from a seeded generator on the
+ * host; resets the Adam state. */
+int hot_mlp_init(dsmc_handle *h, uint64_t seed);
+/* Copy the FP32 master parameters in / out (host memory); set resets the
+ * Adam state and rejects non-finite values (DSMC_ERR_NUMERIC). */
+int hot_mlp_set_params(dsmc_handle *h, const float *host_params);
+int hot_mlp_get_params(dsmc_handle *h, float *host_params);
+
+/* Loss (mean over the mask = 1 cells of the mean squared error of the 5
+ * normalised outputs against the DSMC HoT) and its gradient with respect to
+ * the parameters (host_grad, DSMC_MLP_NPARAM floats, may be NULL), for the
+ * fields / HoT / Kn_GLL / mask of dsmc_sample and dsmc_hot (device).  The
+ * parameters are not changed.  DSMC_ERR_ARG if no cell has mask = 1. */
+int hot_mlp_grad(dsmc_handle *h, const double *dev_fields, const double *dev_hot, const double *dev_kngll,
+                 const uint8_t *dev_mask, float *host_grad, double *host_loss);
+
+/* nsteps full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, step size
+ * lr) on the same data; host_loss (may be NULL) receives the loss before the
+ * last step. */
+int hot_mlp_train(dsmc_handle *h, const double *dev_fields, const double *dev_hot, const double *dev_kngll,
+                  const uint8_t *dev_mask, int nsteps, double lr, double *host_loss);
+
+/* HoT for the synthetic equations: dev_hot_out (ncells x DSMC_NHOT) = the
+ * network's sigma_xx, sigma_xy, sigma_yy and q_t, q_r along grad T where
+ * mask = 1, the DSMC HoT (dev_hot) everywhere else and for every other
+ * component; a cell whose prediction is not finite keeps the DSMC HoT.
+ * host_judge (may be NULL) receives the mean squared difference between the
+ * network and the DSMC HoT over the mask = 1 cells (normalised units).
+ * dev_hot_out may equal dev_hot. */
+int hot_mlp_apply(dsmc_handle *h, const double *dev_fields, const double *dev_hot, const double *dev_kngll,
+                  const uint8_t *dev_mask, double *dev_hot_out, double *host_judge);
+
 #ifdef __cplusplus
 }
 #endif

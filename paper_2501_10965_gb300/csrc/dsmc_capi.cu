@@ -43,6 +43,8 @@ struct dsmc_handle {
   int64_t rebuilds = 0;
   double* synth_work = nullptr;
   double* synth_info = nullptr;
+  Mlp mlp{};       // HoT surrogate network
+  int mlp_t = 0;   // Adam steps taken since the parameters were set
   std::string err;
 };
 
@@ -215,7 +217,23 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
   int32_t* c0 = cv.take<int32_t>(ncases + 1);
   int32_t* cc = cv.take<int32_t>(pl.ncells);
   int64_t* wo = cv.take<int64_t>(ncases);
+  Mlp ml{};
+  ml.theta = cv.take<float>(MLP_NPARAM);
+  ml.wbf = cv.take<uint16_t>(MLP_NPARAM);
+  ml.m = cv.take<float>(MLP_NPARAM);
+  ml.v = cv.take<float>(MLP_NPARAM);
+  ml.grad = cv.take<float>(MLP_NPARAM);
+  ml.partial = cv.take<float>((size_t)MLP_GRID * MLP_NPARAM);
+  ml.part_loss = cv.take<double>(MLP_GRID);
+  ml.X = cv.take<float>((size_t)pl.ncells * 12);
+  ml.Y = cv.take<float>((size_t)pl.ncells * 5);
+  ml.S = cv.take<float>((size_t)pl.ncells * 4);
+  ml.w = cv.take<float>(pl.ncells);
+  ml.out = cv.take<float>((size_t)pl.ncells * 5);
+  ml.scal = cv.take<double>(8);
+  ml.count = cv.take<int32_t>(4);
   if (h) {
+    h->mlp = ml;
     h->synth_work = sw;
     h->synth_info = si;
     h->d_pd = pd;
@@ -385,6 +403,49 @@ int init_state(dsmc_handle* h, State<T>& s, Params<T>& p0, Params<T>* d_p) {
   return check_cuda(h, "dsmc_init");
 }
 
+// HoT network: Glorot-uniform weights (bounds sqrt(6 / (n_in + n_out))) and
+// zero biases from a splitmix64 stream, uploaded with the bfloat16 copies;
+// the Adam state is cleared
+int mlp_upload(dsmc_handle* h, const float* host) {
+  cudaMemcpyAsync(h->mlp.theta, host, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, h->stream);
+  cudaMemsetAsync(h->mlp.m, 0, sizeof(float) * MLP_NPARAM, h->stream);
+  cudaMemsetAsync(h->mlp.v, 0, sizeof(float) * MLP_NPARAM, h->stream);
+  mlp_to_bf16(h->mlp, h->stream);
+  h->mlp_t = 0;
+  return sync_check(h, "hot_mlp parameters");
+}
+
+int mlp_init_params(dsmc_handle* h, uint64_t seed) {
+  static const int nin[4] = {12, 64, 64, 64}, nout[4] = {64, 64, 64, 5};
+  std::vector<float> th(MLP_NPARAM, 0.f);
+  uint64_t z = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+  auto next = [&]() {
+    z += 0x9E3779B97F4A7C15ull;
+    uint64_t x = z;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return ((double)(x >> 11) + 0.5) * 0x1p-53;
+  };
+  int o = 0;
+  for (int k = 0; k < 4; ++k) {
+    const double lim = std::sqrt(6.0 / (double)(nin[k] + nout[k]));
+    for (int q = 0; q < nin[k] * nout[k]; ++q) th[o + q] = (float)((2.0 * next() - 1.0) * lim);
+    o += nin[k] * nout[k] + nout[k];
+  }
+  return mlp_upload(h, th.data());
+}
+
+// inputs of the cells (and targets where hot is given)
+void mlp_data(dsmc_handle* h, const double* fields, const double* hot, const double* kngll, const uint8_t* mask) {
+  mlp_prepare(h->mlp, h->d_cp, h->d_cell_case, h->d_cell0, h->ncells, fields, hot, kngll, mask, h->stream);
+}
+
+int mlp_count(dsmc_handle* h, int* n) {
+  cudaMemcpyAsync(n, h->mlp.count, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+  return sync_check(h, "hot_mlp");
+}
+
 int init_cases(const dsmc_config* cfgs, int ncases, void* dev_workspace, size_t bytes, void* stream,
                dsmc_handle** out) {
   if (!out || !cfgs || ncases < 1) return DSMC_ERR_ARG;
@@ -429,6 +490,7 @@ int init_cases(const dsmc_config* cfgs, int ncases, void* dev_workspace, size_t 
     Ops<float>::configure(pl.tile);
     r = init_state<float>(h, h->sf, h->pf, h->d_pf);
   }
+  if (!r) r = mlp_init_params(h, h->cfg.seed);
   if (r) {
     delete h;
     return r;
@@ -707,6 +769,79 @@ int dsmc_get_constants(dsmc_handle* h, double* out8) {
   out8[5] = 5.0 * (a + 1.0) * (a + 2.0) / (a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w));
   out8[6] = p.c_sigma;
   out8[7] = p.p_inel;
+  return DSMC_OK;
+}
+
+int hot_mlp_init(dsmc_handle* h, uint64_t seed) {
+  if (!h) return DSMC_ERR_ARG;
+  return mlp_init_params(h, seed);
+}
+
+int hot_mlp_set_params(dsmc_handle* h, const float* host_params) {
+  if (!h || !host_params) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  for (int q = 0; q < MLP_NPARAM; ++q)
+    if (!std::isfinite(host_params[q])) return set_err(h, DSMC_ERR_NUMERIC, "hot_mlp_set_params: parameter %d", q);
+  return mlp_upload(h, host_params);
+}
+
+int hot_mlp_get_params(dsmc_handle* h, float* host_params) {
+  if (!h || !host_params) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  cudaMemcpyAsync(host_params, h->mlp.theta, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, h->stream);
+  return sync_check(h, "hot_mlp_get_params");
+}
+
+int hot_mlp_grad(dsmc_handle* h, const double* dev_fields, const double* dev_hot, const double* dev_kngll,
+                 const uint8_t* dev_mask, float* host_grad, double* host_loss) {
+  if (!h || !dev_fields || !dev_hot || !dev_kngll || !dev_mask) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  mlp_data(h, dev_fields, dev_hot, dev_kngll, dev_mask);
+  int n = 0;
+  int r = mlp_count(h, &n);
+  if (r) return r;
+  if (n == 0) return set_err(h, DSMC_ERR_ARG, "hot_mlp_grad: no cell with mask = 1");
+  mlp_grad(h->mlp, h->ncells, h->stream);
+  double loss = 0.0;
+  cudaMemcpyAsync(&loss, h->mlp.scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (host_grad)
+    cudaMemcpyAsync(host_grad, h->mlp.grad, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, h->stream);
+  r = sync_check(h, "hot_mlp_grad");
+  if (r) return r;
+  if (host_loss) *host_loss = loss;
+  return DSMC_OK;
+}
+
+int hot_mlp_train(dsmc_handle* h, const double* dev_fields, const double* dev_hot, const double* dev_kngll,
+                  const uint8_t* dev_mask, int nsteps, double lr, double* host_loss) {
+  if (!h || !dev_fields || !dev_hot || !dev_kngll || !dev_mask || nsteps < 0 || !(lr > 0.0))
+    return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  mlp_data(h, dev_fields, dev_hot, dev_kngll, dev_mask);
+  int n = 0;
+  int r = mlp_count(h, &n);
+  if (r) return r;
+  if (n == 0) return set_err(h, DSMC_ERR_ARG, "hot_mlp_train: no cell with mask = 1");
+  for (int k = 0; k < nsteps; ++k) {
+    mlp_grad(h->mlp, h->ncells, h->stream);
+    h->mlp_t += 1;
+    mlp_adam(h->mlp, h->mlp_t, lr, h->stream);
+  }
+  double loss = 0.0;
+  cudaMemcpyAsync(&loss, h->mlp.scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  r = sync_check(h, "hot_mlp_train");
+  if (r) return r;
+  if (host_loss) *host_loss = loss;
+  return DSMC_OK;
+}
+
+int hot_mlp_apply(dsmc_handle* h, const double* dev_fields, const double* dev_hot, const double* dev_kngll,
+                  const uint8_t* dev_mask, double* dev_hot_out, double* host_judge) {
+  if (!h || !dev_fields || !dev_hot || !dev_kngll || !dev_mask || !dev_hot_out)
+    return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  mlp_data(h, dev_fields, dev_hot, dev_kngll, dev_mask);
+  mlp_apply(h->mlp, h->ncells, dev_hot, dev_hot_out, h->stream);
+  double j[2] = {0.0, 0.0};
+  cudaMemcpyAsync(j, h->mlp.scal + 2, sizeof j, cudaMemcpyDeviceToHost, h->stream);
+  const int r = sync_check(h, "hot_mlp_apply");
+  if (r) return r;
+  if (host_judge) *host_judge = j[1] > 0.0 ? j[0] / j[1] : 0.0;
   return DSMC_OK;
 }
 

@@ -125,4 +125,37 @@ void launch_synth1d_single(const CellParams& cp, const double* fields, const dou
                            double* work, int n_m, double tol, double* info, cudaStream_t st);
 size_t synth1d_work_doubles(int ncells);
 
+// HoT surrogate network (dsmc_mlp.cu): 12 -> 64 -> 64 -> 64 -> 5, tanh
+// hidden layers; parameters per layer: W (n_out x n_in, row major), then b.
+constexpr int MLP_NPARAM = 9477;
+constexpr int MLP_GRID = 304;  // largest grid of the forward/backward kernel
+struct Mlp {
+  float* theta;      // MLP_NPARAM FP32 master parameters
+  uint16_t* wbf;     // MLP_NPARAM bfloat16 copies used by the kernels
+  float* m;          // Adam first moments
+  float* v;          // Adam second moments
+  float* grad;       // MLP_NPARAM
+  float* partial;    // MLP_GRID x MLP_NPARAM per-CTA gradient sums
+  double* part_loss; // MLP_GRID per-CTA loss sums
+  float* X;          // ncells x 12 inputs
+  float* Y;          // ncells x 5 normalised DSMC HoT
+  float* S;          // ncells x 4: p, p sqrt(T), e_x, e_y
+  float* w;          // ncells: 1 for a training / replaced cell, else 0
+  float* out;        // ncells x 5 network outputs
+  double* scal;      // [0] loss, [2] judge sum, [3] judge count
+  int32_t* count;    // [0] number of cells with w = 1
+};
+// inputs, scales, targets (hot may be null) and weights of every cell
+void mlp_prepare(const Mlp& m, const CellParams* cp, const int32_t* cell_case, const int32_t* cell0, int ncells,
+                 const double* fields, const double* hot, const double* kngll, const uint8_t* mask,
+                 cudaStream_t st);
+// loss (scal[0]) and gradient (grad) of the weighted cells
+void mlp_grad(const Mlp& m, int ncells, cudaStream_t st);
+// one Adam step (step number t >= 1) and the bfloat16 copies
+void mlp_adam(const Mlp& m, int t, double lr, cudaStream_t st);
+// bfloat16 copies of the master parameters
+void mlp_to_bf16(const Mlp& m, cudaStream_t st);
+// network outputs, the HoT for the synthetic equations and the judge sums
+void mlp_apply(const Mlp& m, int ncells, const double* hot, double* hot_out, cudaStream_t st);
+
 }  // namespace dsmc

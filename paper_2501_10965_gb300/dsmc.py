@@ -27,7 +27,10 @@ SYMBOLS = ["dsmc_workspace_size", "dsmc_init", "dsmc_destroy", "dsmc_last_error"
            "dsmc_hot", "synth_solve", "dig_correct", "dsmc_num_particles", "dsmc_get_particles",
            "dsmc_set_particles", "dsmc_get_accumulators", "dsmc_get_sgmax", "dsmc_set_sgmax",
            "dsmc_get_counters", "dsmc_set_counters", "dsmc_get_stats", "dsmc_get_wall_tally",
-           "dsmc_get_constants", "synth_solve_noalloc", "dsmc_batch_workspace_size", "dsmc_batch_init"]
+           "dsmc_get_constants", "synth_solve_noalloc", "dsmc_batch_workspace_size", "dsmc_batch_init",
+           "hot_mlp_init", "hot_mlp_set_params", "hot_mlp_get_params", "hot_mlp_grad", "hot_mlp_train",
+           "hot_mlp_apply"]
+MLP_NPARAM = 9477
 
 
 class DsmcConfig(ctypes.Structure):
@@ -101,6 +104,12 @@ def load(build_if_missing: bool = True):
         "synth_solve_noalloc": ([P, P, P, P, P, P, P], ctypes.c_int),
         "dsmc_batch_workspace_size": ([P, ctypes.c_int, P], ctypes.c_int),
         "dsmc_batch_init": ([P, ctypes.c_int, P, ctypes.c_size_t, P, P], ctypes.c_int),
+        "hot_mlp_init": ([H, ctypes.c_uint64], ctypes.c_int),
+        "hot_mlp_set_params": ([H, P], ctypes.c_int),
+        "hot_mlp_get_params": ([H, P], ctypes.c_int),
+        "hot_mlp_grad": ([H, P, P, P, P, P, P], ctypes.c_int),
+        "hot_mlp_train": ([H, P, P, P, P, ctypes.c_int, ctypes.c_double, P], ctypes.c_int),
+        "hot_mlp_apply": ([H, P, P, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -225,6 +234,48 @@ class Dsmc:
         self._check(rc, allow=allow)
         self.last_synth_status = rc
         return out, it.value, res.value
+
+    # ---- HoT surrogate network (see the header) ----
+    def mlp_init(self, seed: int = 0):
+        self._check(load().hot_mlp_init(self._h, ctypes.c_uint64(seed)))
+
+    def mlp_set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == MLP_NPARAM
+        self._check(load().hot_mlp_set_params(self._h, a.ctypes.data_as(ctypes.c_void_p)))
+
+    def mlp_get_params(self):
+        import numpy as np
+        a = np.zeros(MLP_NPARAM, np.float32)
+        self._check(load().hot_mlp_get_params(self._h, a.ctypes.data_as(ctypes.c_void_p)))
+        return a
+
+    def mlp_grad(self, fields, hot, kngll, mask):
+        """(loss, gradient [MLP_NPARAM] as numpy float32) over the mask cells."""
+        import numpy as np
+        g = np.zeros(MLP_NPARAM, np.float32)
+        loss = ctypes.c_double()
+        self._check(load().hot_mlp_grad(self._h, _ptr(fields.contiguous()), _ptr(hot.contiguous()),
+                                        _ptr(kngll.contiguous()), _ptr(mask.contiguous()),
+                                        g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss)))
+        return loss.value, g
+
+    def mlp_train(self, fields, hot, kngll, mask, nsteps: int, lr: float = 1e-3) -> float:
+        loss = ctypes.c_double()
+        self._check(load().hot_mlp_train(self._h, _ptr(fields.contiguous()), _ptr(hot.contiguous()),
+                                         _ptr(kngll.contiguous()), _ptr(mask.contiguous()), int(nsteps),
+                                         float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def mlp_apply(self, fields, hot, kngll, mask):
+        """(HoT for the synthetic equations [ncells x 12], judge)."""
+        out = torch.empty_like(hot)
+        judge = ctypes.c_double()
+        self._check(load().hot_mlp_apply(self._h, _ptr(fields.contiguous()), _ptr(hot.contiguous()),
+                                         _ptr(kngll.contiguous()), _ptr(mask.contiguous()), _ptr(out),
+                                         ctypes.byref(judge)))
+        return out, judge.value
 
     def dig_correct(self, target: torch.Tensor):
         self._check(load().dig_correct(self._h, _ptr(target.contiguous())))
