@@ -1,0 +1,108 @@
+"""GPU HoT surrogate network against the FP64 oracle (oracle/mlp.py).
+
+The GPU network uses bfloat16 weights with FP32 accumulation; the oracle
+takes the same bfloat16-rounded weights in FP64, so the comparison measures
+the FP32 arithmetic of inputs, activations and sums (relative 1e-4 level),
+stated per quantity below.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp
+from paper_2501_10965_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _data(kn=0.1, seed=0, steps=400, sample=200):
+    from paper_2501_10965_gb300 import dsmc
+    cfg = W.couette_1d(kn=kn, nx=80, ppc=120, kn_ref=0.01, seed=seed)
+    g = dsmc.Dsmc(cfg)
+    g.dsmc_step(steps)
+    g.dsmc_sample(reset=True)
+    g.dsmc_step(sample, sample=True)
+    f = g.dsmc_sample(reset=True)
+    hot, kn_g, mask = g.dsmc_hot(f)
+    return cfg, g, f, hot, kn_g, mask
+
+
+def _oracle_set(cfg, f, hot, kn_g, mask):
+    F = f.cpu().numpy()
+    H = hot.cpu().numpy()
+    K = kn_g.cpu().numpy()
+    m = mask.cpu().numpy().astype(bool)
+    X, S = mlp.features(F, K, cfg)
+    Y = mlp.targets(H, S)
+    return F, H, K, m, X, S, Y
+
+
+def test_grad_and_loss_match_oracle():
+    cfg, g, f, hot, kn_g, mask = _data()
+    F, H, K, m, X, S, Y = _oracle_set(cfg, f, hot, kn_g, mask)
+    assert m.sum() > 20
+    theta = mlp.init_params(7).astype(np.float32)
+    g.mlp_set_params(theta)
+    assert np.array_equal(g.mlp_get_params(), theta)
+    loss_g, grad_g = g.mlp_grad(f, hot, kn_g, mask)
+    loss_o, grad_o = mlp.loss_and_grad(theta.astype(np.float64), X[m], Y[m], bf16=True)
+    assert abs(loss_g - loss_o) <= 1e-4 * loss_o, (loss_g, loss_o)
+    # every layer's weight and bias gradients, relative to the layer's largest
+    for (gw, gb), (ow, ob) in zip(mlp.unpack(grad_g.astype(np.float64)), mlp.unpack(grad_o)):
+        for a, b in ((gw, ow), (gb, ob)):
+            assert np.max(np.abs(a - b)) <= 1e-3 * np.max(np.abs(b)) + 1e-12, (np.max(np.abs(a - b)), np.max(np.abs(b)))
+
+
+def test_apply_matches_oracle_and_judges():
+    cfg, g, f, hot, kn_g, mask = _data(seed=1)
+    F, H, K, m, X, S, Y = _oracle_set(cfg, f, hot, kn_g, mask)
+    theta = mlp.init_params(3).astype(np.float32)
+    g.mlp_set_params(theta)
+    out, judge = g.mlp_apply(f, hot, kn_g, mask)
+    out = out.cpu().numpy()
+    Yo, _ = mlp.forward(theta.astype(np.float64), X, bf16=True)
+    ho = mlp.to_hot(Yo, S, H)
+    # network cells: the modelled components follow the oracle network
+    scale = np.max(np.abs(ho[m][:, [0, 1, 3, 6, 9]]))
+    assert np.max(np.abs(out[m] - ho[m])) <= 1e-4 * scale, np.max(np.abs(out[m] - ho[m]))
+    # every other cell keeps the DSMC HoT exactly
+    assert np.array_equal(out[~m], H[~m])
+    jo = np.mean((Yo[m] - Y[m]) ** 2)
+    assert abs(judge - jo) <= 1e-4 * jo, (judge, jo)
+
+
+def test_training_follows_oracle_and_reduces_the_loss():
+    cfg, g, f, hot, kn_g, mask = _data(seed=2)
+    F, H, K, m, X, S, Y = _oracle_set(cfg, f, hot, kn_g, mask)
+    theta = mlp.init_params(11).astype(np.float32)
+    g.mlp_set_params(theta)
+    lr, n = 2e-3, 30
+    g.mlp_train(f, hot, kn_g, mask, n, lr)
+    opt = mlp.Adam(mlp.NPARAM, lr)
+    th = theta.astype(np.float64)
+    losses = []
+    for _ in range(n):
+        l, gr = mlp.loss_and_grad(th, X[m], Y[m], bf16=True)
+        losses.append(l)
+        th = opt.step(th, gr)
+    lg, _ = g.mlp_grad(f, hot, kn_g, mask)
+    lo, _ = mlp.loss_and_grad(th, X[m], Y[m], bf16=True)
+    assert lo < 0.5 * losses[0]
+    # Adam moves each parameter by about lr per step whatever the gradient's
+    # size, so FP32 and FP64 runs drift apart where a gradient is near zero;
+    # the losses after the same steps stay within a few per cent
+    assert abs(lg - lo) <= 0.05 * lo, (lg, lo, losses[0])
+    # an Adam step moves a parameter by at most lr (1 - beta1) / sqrt(1 - beta2)
+    d = np.abs(g.mlp_get_params().astype(np.float64) - theta)
+    assert d.max() <= n * lr * 0.1 / np.sqrt(0.001) * 1.001
+
+
+def test_rejects_empty_mask_and_bad_params():
+    from paper_2501_10965_gb300 import dsmc
+    cfg, g, f, hot, kn_g, mask = _data(seed=3, steps=50, sample=20)
+    with pytest.raises(dsmc.DsmcError):
+        g.mlp_grad(f, hot, kn_g, torch.zeros_like(mask))
+    bad = mlp.init_params(0).astype(np.float32)
+    bad[5] = np.nan
+    with pytest.raises(dsmc.DsmcError):
+        g.mlp_set_params(bad)
