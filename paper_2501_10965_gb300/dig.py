@@ -25,17 +25,38 @@ import torch
 from . import dsmc
 
 
-def dig_iteration(sim: "dsmc.Dsmc", n_s: int, allow_not_converged: bool = True) -> dict:
-    """N_s DSMC steps, sample, HoT, synthetic solve, particle modification."""
+def target_as_fields(target: torch.Tensor) -> torch.Tensor:
+    """Cell fields (ncells x 18) holding a synthetic solution's rho, u, T_t,
+    T_r (stress and heat-flux slots zero): the smooth state the HoT network
+    reads its inputs from."""
+    f = torch.zeros((target.shape[0], dsmc.NFIELDS), dtype=torch.float64, device=target.device)
+    f[:, :6] = target
+    return f
+
+
+def dig_iteration(sim: "dsmc.Dsmc", n_s: int, allow_not_converged: bool = True,
+                  hot_model: bool = False, prev_target: torch.Tensor | None = None) -> dict:
+    """N_s DSMC steps, sample, HoT, synthetic solve, particle modification.
+
+    With hot_model, the higher-order terms where Kn_GLL >= Kn_ref are the
+    handle's HoT network evaluated on the previous synthetic solution (a
+    smooth state; the sampled fields' gradients are dominated by noise), with
+    the sampled HoT as fallback; the first iteration, with no previous
+    solution, uses the sampled HoT."""
     sim.dsmc_step(n_s, sample=True)
     f = sim.dsmc_sample(reset=True)
     hot, kn, mask = sim.dsmc_hot(f)
+    judge = None
+    if hot_model and prev_target is not None:
+        fs = target_as_fields(prev_target)
+        _, kn_s, mask_s = sim.dsmc_hot(fs)
+        hot, judge = sim.mlp_apply(fs, hot, kn_s, mask_s)
     out, iters, res = sim.synth_solve(f, hot, allow_not_converged=allow_not_converged, allow_fallback=True)
     sim.dig_correct(out)
     # the HoT mask stays on the device (reducing it here would put a host
     # round trip, and the first use of a framework kernel, into the loop)
     return {"fields": f, "target": out, "synth_iters": iters, "synth_resid": res,
-            "synth_status": sim.last_synth_status, "mask": mask}
+            "synth_status": sim.last_synth_status, "mask": mask, "judge": judge}
 
 
 def total_temperature(f: np.ndarray, d_r: float = 2.0) -> np.ndarray:
@@ -52,12 +73,16 @@ class Ensemble:
     """R independent replicas of one 1D workload (seeds seed0 + r), held in
     one batched handle so that each stage is one launch for all of them."""
 
-    def __init__(self, cfg: dict, replicas: int, seed0: int = 0):
+    def __init__(self, cfg: dict, replicas: int, seed0: int = 0, hot_params=None):
         from . import workloads
         self.cfg = dict(cfg)
         self.R = replicas
         self.nx = int(cfg["nx"])
         self.sim = dsmc.Dsmc(workloads.replicas(cfg, replicas, seed0))
+        self.hot_model = hot_params is not None
+        if self.hot_model:
+            self.sim.mlp_set_params(hot_params)
+        self.target = None
         self.steps = 0
         self.wall = 0.0  # GPU wall time spent in the method's calls, seconds
 
@@ -85,9 +110,11 @@ class Ensemble:
         self.steps += nsteps
 
     def advance_dig(self, n_s: int) -> np.ndarray:
-        f = self._timed(lambda: dig_iteration(self.sim, n_s)["fields"])
+        r = self._timed(lambda: dig_iteration(self.sim, n_s, hot_model=self.hot_model, prev_target=self.target))
+        self.target = r["target"]
+        self.last = r
         self.steps += n_s
-        return self._per_replica(f)
+        return self._per_replica(r["fields"])
 
 
 def window_error(fs: np.ndarray, ref_u: np.ndarray, ref_t: np.ndarray, flow_axis: int, nbins: int):
@@ -139,15 +166,16 @@ def reference_solution(cfg: dict, replicas: int, transient_steps: int, average_s
 
 
 def measure(cfg: dict, method: str, replicas: int, window: int, max_steps: int, ref_u, ref_t, flow_axis: int,
-            nbins: int, threshold: float = 0.01, seed0: int = 0) -> dict:
-    """Run `method` ("plain" or "dig") from the uniform initial state and
-    record err(t) per window; returns the time to steady (steps and GPU wall
-    seconds) and the error history."""
-    ens = Ensemble(cfg, replicas, seed0)
+            nbins: int, threshold: float = 0.01, seed0: int = 0, hot_params=None) -> dict:
+    """Run `method` ("plain", "dig" or "dig_mlp": DIG with the HoT network of
+    parameters hot_params) from the uniform initial state and record err(t)
+    per window; returns the time to steady (steps and GPU wall seconds) and
+    the error history."""
+    ens = Ensemble(cfg, replicas, seed0, hot_params=hot_params if method == "dig_mlp" else None)
     eu_hist, et_hist, walls, steps = [], [], [], []
     n_s = int(cfg["n_s"])
     while ens.steps < max_steps:
-        if method == "dig":
+        if method in ("dig", "dig_mlp"):
             fs = np.stack([ens.advance_dig(n_s) for _ in range(max(1, window // n_s))]).mean(0)
         else:
             fs = ens.advance_plain(window)
@@ -166,7 +194,7 @@ def measure(cfg: dict, method: str, replicas: int, window: int, max_steps: int, 
 
 def time_to_steady_dig_vs_plain(cfg: dict, replicas: int = 800, window: int = 100, nbins: int = 20,
                                 transient: int = 50000, average: int = 15000, threshold: float = 0.01,
-                                max_dig: int = 6000, max_plain: int = 60000) -> dict:
+                                max_dig: int = 6000, max_plain: int = 60000, hot_params=None) -> dict:
     """Time to steady state at `threshold` field error, DIG against plain
     DSMC, both on the GPU from the same uniform initial state, ensemble of
     `replicas` (one batched handle) against the long-run plain-DSMC reference
@@ -176,12 +204,46 @@ def time_to_steady_dig_vs_plain(cfg: dict, replicas: int = 800, window: int = 10
     t_ref = time.perf_counter() - t0
     out = {"replicas": replicas, "particles": replicas * int(cfg["nx"]) * int(cfg["ppc"]), "window": window,
            "bins": nbins, "threshold": threshold, "noise_floor": floor, "reference_wall_s": t_ref}
-    for method, cap in (("dig", max_dig), ("plain", max_plain)):
-        r = measure(cfg, method, replicas, window, cap, ref_u, ref_t, 1, nbins, threshold)
+    methods = [("dig", max_dig), ("plain", max_plain)]
+    if hot_params is not None:
+        methods.insert(1, ("dig_mlp", max_dig))
+    for method, cap in methods:
+        r = measure(cfg, method, replicas, window, cap, ref_u, ref_t, 1, nbins, threshold, hot_params=hot_params)
         out[method] = {"steady_step": r["steady_step"], "steady_wall_s": r["steady_wall_s"],
                        "final_err_u": r["err_u"][-1], "final_err_T": r["err_T"][-1]}
-    d, pl = out["dig"], out["plain"]
-    if d["steady_wall_s"] and pl["steady_wall_s"]:
-        out["speedup_wall"] = pl["steady_wall_s"] / d["steady_wall_s"]
-        out["speedup_steps"] = pl["steady_step"] / d["steady_step"]
+    pl = out["plain"]
+    for m, suffix in (("dig", ""), ("dig_mlp", "_mlp")):
+        d = out.get(m)
+        if d and d["steady_wall_s"] and pl["steady_wall_s"]:
+            out["speedup_wall" + suffix] = pl["steady_wall_s"] / d["steady_wall_s"]
+            out["speedup_steps" + suffix] = pl["steady_step"] / d["steady_step"]
     return out
+
+
+def train_hot_model(cfgs: list, replicas: int = 32, transient: int = 3000, average: int = 4000,
+                    phases=((3000, 2e-3), (2000, 5e-4)), seed0: int = 5000, init_seed: int = 0):
+    """Train the HoT network on the method's own DSMC samples: for every
+    configuration in cfgs, `replicas` runs with seeds from seed0 (independent
+    of the runs it will serve), `transient` steps, then `average` sampled
+    steps; all of them in one batched handle, trained full-batch with Adam
+    (phases of (steps, step size)) on every cell (Kn_ref 0 for training).
+    Returns (parameters as float32 numpy, a dict with the data's size and the
+    final loss)."""
+    from . import workloads
+    cases = []
+    for k, c in enumerate(cfgs):
+        cases += workloads.replicas(dict(c, kn_ref=0.0), replicas, seed0 + 1000 * k)
+    g = dsmc.Dsmc(cases)
+    g.mlp_init(init_seed)
+    g.dsmc_step(transient)
+    g.dsmc_sample(reset=True)
+    g.dsmc_step(average, sample=True)
+    f = g.dsmc_sample(reset=True)
+    hot, kn, mask = g.dsmc_hot(f)
+    loss = None
+    for nsteps, lr in phases:
+        loss = g.mlp_train(f, hot, kn, mask, nsteps, lr)
+    params = g.mlp_get_params()
+    info = {"cases": len(cases), "cells": g.ncells, "loss": loss}
+    del g
+    return params, info
