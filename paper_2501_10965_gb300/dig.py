@@ -220,30 +220,54 @@ def time_to_steady_dig_vs_plain(cfg: dict, replicas: int = 800, window: int = 10
     return out
 
 
-def train_hot_model(cfgs: list, replicas: int = 32, transient: int = 3000, average: int = 4000,
-                    phases=((3000, 2e-3), (2000, 5e-4)), seed0: int = 5000, init_seed: int = 0):
-    """Train the HoT network on the method's own DSMC samples: for every
-    configuration in cfgs, `replicas` runs with seeds from seed0 (independent
-    of the runs it will serve), `transient` steps, then `average` sampled
-    steps; all of them in one batched handle, trained full-batch with Adam
-    (phases of (steps, step size)) on every cell (Kn_ref 0 for training).
+def train_hot_model(cfgs: list, replicas: int = 32, snapshots=(100, 300, 700, 1500, 3000, 6000),
+                    window: int = 200, rounds: int = 20, steps_per_round: int = 100,
+                    lrs=(2e-3, 5e-4), seed0: int = 5000, init_seed: int = 0):
+    """Train the HoT network on the method's own DSMC samples.  Every
+    configuration in cfgs runs as `replicas` independent copies (seeds from
+    seed0, independent of the runs the network will serve), all in one
+    batched handle, from the uniform start; at each of `snapshots` (steps
+    from the start) a `window`-step sample is taken and averaged over the
+    copies of its configuration, so that the network learns HoT as a function
+    of clean inputs (a single run's gradients are dominated by sampling
+    noise), over the transient as well as the steady state.  Training: Adam,
+    full batch per snapshot, cycling through the snapshots for `rounds`
+    rounds of `steps_per_round` steps, the step size going from lrs[0] to
+    lrs[1] halfway; every cell is a training cell (Kn_ref 0).
     Returns (parameters as float32 numpy, a dict with the data's size and the
-    final loss)."""
+    last loss)."""
     from . import workloads
     cases = []
     for k, c in enumerate(cfgs):
         cases += workloads.replicas(dict(c, kn_ref=0.0), replicas, seed0 + 1000 * k)
     g = dsmc.Dsmc(cases)
     g.mlp_init(init_seed)
-    g.dsmc_step(transient)
-    g.dsmc_sample(reset=True)
-    g.dsmc_step(average, sample=True)
-    f = g.dsmc_sample(reset=True)
-    hot, kn, mask = g.dsmc_hot(f)
+    nc = [int(c["nx"]) * (int(c.get("ny", 1)) if int(c["dim"]) == 2 else 1) for c in cfgs]
+    data = []
+    done = 0
+    for t in snapshots:
+        if t - window > done:
+            g.dsmc_step(t - window - done)
+            done = t - window
+        g.dsmc_sample(reset=True)
+        g.dsmc_step(window, sample=True)
+        done += window
+        f = g.dsmc_sample(reset=True)
+        # average over the copies of each configuration, written back to all
+        parts, o = [], 0
+        for n in nc:
+            blk = f[o:o + replicas * n].view(replicas, n, -1)
+            parts.append(blk.mean(0, keepdim=True).expand(replicas, n, blk.shape[-1]).reshape(replicas * n, -1))
+            o += replicas * n
+        fa = torch.cat(parts).contiguous()
+        hot, kn, mask = g.dsmc_hot(fa)
+        data.append((fa, hot, kn, mask))
     loss = None
-    for nsteps, lr in phases:
-        loss = g.mlp_train(f, hot, kn, mask, nsteps, lr)
+    for r in range(rounds):
+        lr = lrs[0] if r < rounds // 2 else lrs[1]
+        for fa, hot, kn, mask in data:
+            loss = g.mlp_train(fa, hot, kn, mask, steps_per_round, lr)
     params = g.mlp_get_params()
-    info = {"cases": len(cases), "cells": g.ncells, "loss": loss}
+    info = {"cases": len(cases), "cells": g.ncells, "snapshots": len(data), "loss": loss}
     del g
     return params, info

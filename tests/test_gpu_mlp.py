@@ -106,3 +106,38 @@ def test_rejects_empty_mask_and_bad_params():
     bad[5] = np.nan
     with pytest.raises(dsmc.DsmcError):
         g.mlp_set_params(bad)
+
+
+def test_trained_network_estimates_hot_better_than_a_dsmc_window():
+    """What the trained network gains over the method without it: trained on
+    the method's own DSMC samples (copies averaged, transient and steady),
+    it gives the HoT of an independent run's steady state, from that state's
+    fields, far closer to the long-run DSMC HoT than the HoT that DIG
+    otherwise takes from one N_s = 50-step window of one run."""
+    from paper_2501_10965_gb300 import dig, dsmc
+    cfg = W.couette_1d(kn=0.1, nx=100, ppc=100)
+    params, info = dig.train_hot_model([cfg], replicas=32, snapshots=(300, 1500, 4000), window=1000,
+                                       rounds=20, steps_per_round=100)
+    assert np.isfinite(params).all() and info["loss"] < 1e-3
+    R, nx = 32, 100
+    ref = dsmc.Dsmc(W.replicas(dict(cfg, kn_ref=0.0), R, 9000))
+    ref.dsmc_step(3000)
+    ref.dsmc_sample(reset=True)
+    ref.dsmc_step(3000, sample=True)
+    f = ref.dsmc_sample(reset=True)
+    fr = f.view(R, nx, -1).mean(0, keepdim=True).expand(R, nx, f.shape[-1]).reshape(R * nx, -1).contiguous()
+    h_ref, k_ref, m_ref = ref.dsmc_hot(fr)
+    ref.mlp_set_params(params)
+    h_net, _ = ref.mlp_apply(fr, h_ref, k_ref, m_ref)
+    # one 50-step window of each copy
+    ref.dsmc_sample(reset=True)
+    ref.dsmc_step(50, sample=True)
+    fw = ref.dsmc_sample(reset=True)
+    h_win, _, _ = ref.dsmc_hot(fw)
+    H = h_ref.cpu().numpy().reshape(R, nx, 12)[0]
+    N = h_net.cpu().numpy().reshape(R, nx, 12)[0]
+    Wn = h_win.cpu().numpy().reshape(R, nx, 12)
+    for col in (3, 6, 9):  # sigma_xy, q_t,x, q_r,x
+        e_net = np.sqrt(np.mean((N[:, col] - H[:, col]) ** 2))
+        e_win = np.sqrt(np.mean((Wn[:, :, col] - H[None, :, col]) ** 2))
+        assert e_net < 0.2 * e_win, (col, e_net, e_win)
