@@ -287,6 +287,23 @@ def run_gpu(args):
     ncells = sim.ncells
 
     gpu_launches = (args.steps + 1) + 5 * (reb1 - reb0)
+
+    # batched ensemble: 64 independent 1D cases of uneven size in one handle
+    # (one launch per step for all of them), device-resident
+    ens = None
+    if rank == 0 and not args.no_ensemble:
+        from paper_2501_10965_gb300 import workloads as Wk
+        ge = dsmc.Dsmc(Wk.ensemble_1d(64))
+        ge.dsmc_step(10, sample=True)
+        ke = 200
+        t_e = _events_time(lambda: ge.dsmc_step(ke, sample=True), stream)
+        ne = ge.num_particles()
+        ens = {"workload": "64 1D cases (Fourier/Couette alternating), 50..800 cells, 50..200 particles per cell, "
+                           "Kn 1e-3..1, Z 2/5/10, FP32; seeds 0..63",
+               "cells": ge.ncells, "particles": ne, "steps": ke, "value": ne * ke / t_e, "unit": METRIC,
+               "ms_per_step": t_e / ke * 1e3}
+        del ge
+        torch.cuda.empty_cache()
     tts = None
     if rank == 0 and not args.no_time_to_steady:
         from paper_2501_10965_gb300 import dig, workloads as Wk
@@ -313,6 +330,7 @@ def run_gpu(args):
                         "d2h_bytes_per_step": d2h / args.steps},
                 "cpu_baseline": cpu,
                 "time_to_steady": tts,
+                "ensemble64": ens,
                 "stats": stats}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -330,6 +348,7 @@ def main():
                     help="DRAM bytes per fused launch from an ncu capture of the current kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-steady", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--tts-replicas", type=int, default=800)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run warm-up + this many steps (for profiler captures)")
