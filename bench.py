@@ -244,6 +244,7 @@ def run_gpu(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
     value = n * args.steps * world / t
+    cfg_line_shape = sim.launch_config()
 
     # average duration of one fused step kernel: difference of two runs with
     # different step counts on the launching stream (the constant parts --
@@ -324,7 +325,8 @@ def run_gpu(args):
                            "particles_per_cell": cfg["ppc"], "kn": cfg["kn"], "dt": cfg["dt"],
                            "precision": prec + " particles, fp64 compensated moments",
                            "l2": "inputs larger than L2 (particle state %.2f GB)" % (n * 24 / 1e9),
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "fused_warps_per_cta": cfg_line_shape},
                 "roofline": roofline, "clocks": clocks, "gpu_launches": gpu_launches,
                 "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d / args.steps,
                         "d2h_bytes_per_step": d2h / args.steps},

@@ -259,6 +259,14 @@ int dsmc_get_stats(dsmc_handle *h, int64_t *host_out8);
  * of a simulated particle (multiply by F = rho V / N for physical units). */
 int dsmc_get_wall_tally(dsmc_handle *h, double *host_out20);
 
+/* Launch shape of the FP32 fused step (host): warps (= cells) per CTA, 2
+ * or 4.  A handle times both shapes on real steps of its first dsmc_step call
+ * of at least 10 steps and keeps the faster one (which shape wins depends on
+ * the workload: 4 for the 400 x 300 cavity, 2 for the 64-case ensemble);
+ * 0 before that call and in the FP64-deterministic mode.  The paper has no
+ * counterpart. */
+int dsmc_get_launch_config(dsmc_handle *h, int *host_warps_per_cta);
+
 /* Derived constants (host, 8 entries): dx, dy, cell volume V, particle weight
  * F, mu_ref, K (nu = K p / mu), C_sigma (sigma g = C_sigma g^(2-2 omega)),
  * P_inelastic. */

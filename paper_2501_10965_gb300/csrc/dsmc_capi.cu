@@ -772,6 +772,12 @@ int dsmc_get_constants(dsmc_handle* h, double* out8) {
   return DSMC_OK;
 }
 
+int dsmc_get_launch_config(dsmc_handle* h, int* host_warps_per_cta) {
+  if (!h || !host_warps_per_cta) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  *host_warps_per_cta = h->det ? 0 : h->sf.fwpb;
+  return DSMC_OK;
+}
+
 int hot_mlp_init(dsmc_handle* h, uint64_t seed) {
   if (!h) return DSMC_ERR_ARG;
   return mlp_init_params(h, seed);

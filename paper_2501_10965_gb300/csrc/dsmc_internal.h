@@ -74,6 +74,7 @@ struct State {
   Ovf ovf[2];
   Cases<T> cases;
   bool batch;  // several cases: kernels read their parameters per cell
+  int fwpb;    // FP32 fused step: warps per CTA (0: not tuned yet)
 };
 
 template <typename T>

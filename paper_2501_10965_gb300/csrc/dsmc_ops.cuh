@@ -393,12 +393,14 @@ __device__ __forceinline__ int neighbour_cell(int nx, int cell, int code) {
   return cell + (code / 3 - 1) * nx + (code % 3 - 1);
 }
 
-constexpr int FWPB = 4;                      // warps per CTA of the fused step
+// warps per CTA of the fused step: 2 or 4, chosen per handle by timing both
+// on the handle's first long dsmc_step call (fused_tune)
+constexpr int FWPB_MAX = 4;
 constexpr uint32_t MBAR_POLL_LIMIT = 1u << 22;  // bounded wait for a cell's bulk copies
 
 // shared memory of the fused step: per warp, tile x (vx, vy, vz, I_r, x, y)
 // floats and tile x u32 (collision owners, then destination tags)
-inline size_t fused_smem_bytes(int tile) { return (size_t)FWPB * tile * 28; }
+inline size_t fused_smem_bytes(int tile, int fwpb) { return (size_t)fwpb * tile * 28; }
 
 // flags: 1 collide (step_c), 2 sample, 4 move (step_m) into `out`, 8 fold the
 // FP32 staging sums into the FP64 accumulators after sampling.
@@ -414,8 +416,8 @@ inline size_t fused_smem_bytes(int tile) { return (size_t)FWPB * tile * 28; }
 // destination bin reserves the slots; (M3) fly again (the same counter-based
 // random stream, so the same result) and store.  Counters are flushed by the
 // last warp of the block to finish, so warps never wait for one another.
-template <int DIM, bool BATCH>
-__global__ void __launch_bounds__(FWPB * 32, 8) k_fused(const __grid_constant__ Params<float> pk,
+template <int DIM, bool BATCH, int FWPB>
+__global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_constant__ Params<float> pk,
                                                         Cases<float> cases, int ncells, PBuf<float> in,
                                                         PBuf<float> out,
                                                         const int32_t* __restrict__ start,
@@ -1126,38 +1128,78 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
   if constexpr (sizeof(T) == 4) {
     if (nsteps <= 0) return;
     const int ncells = s.ncells;
-    const int cblocks = (ncells + FWPB - 1) / FWPB;
     const int oblocks = 8;
-    const size_t smf = fused_smem_bytes(s.tile);
-    auto launch = [&](int flags, uint32_t sc, uint32_t sm_step) {
+    auto launch = [&](int flags, uint32_t sc, uint32_t sm_step, int F) {
       const int other = cur ^ 1;
+      const int cblocks = (ncells + F - 1) / F;
+      const size_t smf = fused_smem_bytes(s.tile, F);
 #define DSMC_FUSED_ARGS                                                                                         \
   p, s.cases, ncells, s.buf[cur], s.buf[other], s.start[lay], s.count[cur], s.count[other], s.sgmax, s.acc,      \
       s.comp, s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats, \
       s.flags + 8, s.stg, s.stc
-      if (p.dim == 1) {
-        if (s.batch) k_fused<1, true><<<cblocks + oblocks, FWPB * 32, smf, st>>>(DSMC_FUSED_ARGS);
-        else k_fused<1, false><<<cblocks + oblocks, FWPB * 32, smf, st>>>(DSMC_FUSED_ARGS);
+#define DSMC_FUSED_LAUNCH(D, B, W) k_fused<D, B, W><<<cblocks + oblocks, W * 32, smf, st>>>(DSMC_FUSED_ARGS)
+      if (F == 2) {
+        if (p.dim == 1) {
+          if (s.batch) DSMC_FUSED_LAUNCH(1, true, 2);
+          else DSMC_FUSED_LAUNCH(1, false, 2);
+        } else {
+          if (s.batch) DSMC_FUSED_LAUNCH(2, true, 2);
+          else DSMC_FUSED_LAUNCH(2, false, 2);
+        }
       } else {
-        if (s.batch) k_fused<2, true><<<cblocks + oblocks, FWPB * 32, smf, st>>>(DSMC_FUSED_ARGS);
-        else k_fused<2, false><<<cblocks + oblocks, FWPB * 32, smf, st>>>(DSMC_FUSED_ARGS);
+        if (p.dim == 1) {
+          if (s.batch) DSMC_FUSED_LAUNCH(1, true, 4);
+          else DSMC_FUSED_LAUNCH(1, false, 4);
+        } else {
+          if (s.batch) DSMC_FUSED_LAUNCH(2, true, 4);
+          else DSMC_FUSED_LAUNCH(2, false, 4);
+        }
       }
+#undef DSMC_FUSED_LAUNCH
 #undef DSMC_FUSED_ARGS
       // the input overflow list has been consumed
       cudaMemsetAsync(s.ovf[cur].count, 0, sizeof(int32_t), st);
       cur = other;
     };
     // move of step0, then per step: collide (+sample) of step k and move of step k+1
-    launch(4, step0, step0);
+    launch(4, step0, step0, s.fwpb > 0 ? s.fwpb : FWPB_MAX);
     // sampled sums are staged in FP32 and folded into FP64 every
     // STAGE_STEPS steps and on the last step of the call
     constexpr int STAGE_STEPS = 16;
-    for (int i = 0; i < nsteps; ++i) {
+    auto fused_flags = [&](int i) {
+      const int fold = ((i + 1) % STAGE_STEPS == 0) ? 8 : 0;
+      return 1 | (do_sample ? 2 | fold : 0) | 4;
+    };
+    int i0 = 0;
+    if (s.fwpb == 0 && nsteps >= 10) {
+      // launch shape of the fused step: steps 2-4 timed with 4 warps per
+      // CTA, steps 6-8 with 2 (steps 0-1 and 5 warm each one up); every step
+      // is a real step of the call; 2 is kept only if it is faster by more
+      // than 1 % (the timing's resolution over three steps)
+      cudaEvent_t ev[4];
+      for (auto& e : ev) cudaEventCreate(&e);
+      for (int i = 0; i < 9; ++i) {
+        if (i == 2) cudaEventRecord(ev[0], st);
+        if (i == 6) cudaEventRecord(ev[2], st);
+        const uint32_t sc = step0 + (uint32_t)i;
+        launch(fused_flags(i), sc, sc + 1, i < 5 ? 4 : 2);
+        if (i == 4) cudaEventRecord(ev[1], st);
+        if (i == 8) cudaEventRecord(ev[3], st);
+      }
+      float t4 = 0.f, t2 = 0.f;
+      cudaEventSynchronize(ev[3]);
+      cudaEventElapsedTime(&t4, ev[0], ev[1]);
+      cudaEventElapsedTime(&t2, ev[2], ev[3]);
+      for (auto& e : ev) cudaEventDestroy(e);
+      s.fwpb = (t2 > 0.f && t2 < 0.99f * t4) ? 2 : 4;
+      i0 = 9;
+    }
+    const int F = s.fwpb > 0 ? s.fwpb : FWPB_MAX;
+    for (int i = i0; i < nsteps; ++i) {
       const bool last = (i == nsteps - 1);
       const uint32_t sc = step0 + (uint32_t)i;
       if (!last) {
-        const int fold = ((i + 1) % STAGE_STEPS == 0) ? 8 : 0;
-        launch(1 | (do_sample ? 2 | fold : 0) | 4, sc, sc + 1);
+        launch(fused_flags(i), sc, sc + 1, F);
       } else {
         const int flags = 1 | (do_sample ? 2 : 0);
         if (s.batch)
@@ -1308,11 +1350,15 @@ void Ops<T>::configure(int tile) {
   cudaFuncSetAttribute(k_dig_apply<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
   cudaFuncSetAttribute(k_dig_apply<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
   if constexpr (sizeof(T) == 4) {
-    const int smf = (int)fused_smem_bytes(tile);
-    cudaFuncSetAttribute(k_fused<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf);
-    cudaFuncSetAttribute(k_fused<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf);
-    cudaFuncSetAttribute(k_fused<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf);
-    cudaFuncSetAttribute(k_fused<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf);
+    const int sm4 = (int)fused_smem_bytes(tile, 4), sm2 = (int)fused_smem_bytes(tile, 2);
+    cudaFuncSetAttribute(k_fused<1, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<2, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<1, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<2, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<1, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<2, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<1, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<2, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
   }
 }
 

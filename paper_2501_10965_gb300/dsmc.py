@@ -29,7 +29,7 @@ SYMBOLS = ["dsmc_workspace_size", "dsmc_init", "dsmc_destroy", "dsmc_last_error"
            "dsmc_get_counters", "dsmc_set_counters", "dsmc_get_stats", "dsmc_get_wall_tally",
            "dsmc_get_constants", "synth_solve_noalloc", "dsmc_batch_workspace_size", "dsmc_batch_init",
            "hot_mlp_init", "hot_mlp_set_params", "hot_mlp_get_params", "hot_mlp_grad", "hot_mlp_train",
-           "hot_mlp_apply"]
+           "hot_mlp_apply", "dsmc_get_launch_config"]
 MLP_NPARAM = 9477
 
 
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True):
         "dsmc_batch_workspace_size": ([P, ctypes.c_int, P], ctypes.c_int),
         "dsmc_batch_init": ([P, ctypes.c_int, P, ctypes.c_size_t, P, P], ctypes.c_int),
         "hot_mlp_init": ([H, ctypes.c_uint64], ctypes.c_int),
+        "dsmc_get_launch_config": ([H, P], ctypes.c_int),
         "hot_mlp_set_params": ([H, P], ctypes.c_int),
         "hot_mlp_get_params": ([H, P], ctypes.c_int),
         "hot_mlp_grad": ([H, P, P, P, P, P, P], ctypes.c_int),
@@ -234,6 +235,12 @@ class Dsmc:
         self._check(rc, allow=allow)
         self.last_synth_status = rc
         return out, it.value, res.value
+
+    def launch_config(self) -> int:
+        """Warps (cells) per CTA of the FP32 fused step chosen by the tuner."""
+        v = ctypes.c_int()
+        self._check(load().dsmc_get_launch_config(self._h, ctypes.byref(v)))
+        return v.value
 
     # ---- HoT surrogate network (see the header) ----
     def mlp_init(self, seed: int = 0):

@@ -104,3 +104,21 @@ def test_batch_fp32_ensemble_of_64_uneven_cases():
     assert abs(n1 - n0) < 0.01 * n0
     g.dsmc_step(10)
     assert g.num_particles() == n1
+
+
+def test_fused_launch_shape_is_tuned_per_handle():
+    """The FP32 fused step times its two launch shapes on the first call of
+    at least 10 steps and keeps one; particles are conserved through the
+    tuning steps; the FP64 mode reports no shape."""
+    from paper_2501_10965_gb300 import dsmc
+    g = dsmc.Dsmc(W.ensemble_1d(8))
+    n0 = g.num_particles()
+    assert g.launch_config() == 0
+    g.dsmc_step(5)
+    assert g.launch_config() == 0
+    g.dsmc_step(20)
+    assert g.launch_config() in (2, 4)
+    assert g.num_particles() == n0
+    d = dsmc.Dsmc(W.fourier_1d(nx=20, ppc=30))
+    d.dsmc_step(12)
+    assert d.launch_config() == 0
