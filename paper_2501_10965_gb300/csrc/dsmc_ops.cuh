@@ -30,15 +30,24 @@ constexpr int CTA_SCAN = 1024;
 // ---------------------------------------------------------------------------
 template <typename F>
 __device__ void cta_exclusive_scan(int n, F value, int32_t* out) {
+  // each thread takes SCAN_ITEMS consecutive entries per pass, so that a pass
+  // covers SCAN_ITEMS x blockDim.x entries and its loads are issued together
+  constexpr int SCAN_ITEMS = 8;
   __shared__ int32_t wsum[32];
   __shared__ int32_t carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (int base = 0; base < n; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const int32_t v = (i < n) ? value(i) : 0;
-    int32_t x = v;
+  for (int base = 0; base < n; base += blockDim.x * SCAN_ITEMS) {
+    const int i0 = base + threadIdx.x * SCAN_ITEMS;
+    int32_t v[SCAN_ITEMS];
+    int32_t tsum = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+      v[j] = (i0 + j < n) ? value(i0 + j) : 0;
+      tsum += v[j];
+    }
+    int32_t x = tsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int32_t y = __shfl_up_sync(FULL, x, o);
@@ -56,10 +65,14 @@ __device__ void cta_exclusive_scan(int n, F value, int32_t* out) {
       wsum[lane] = w;
     }
     __syncthreads();
-    const int32_t excl = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - v;
-    if (i < n) out[i] = excl;
+    int32_t run = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - tsum;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+      if (i0 + j < n) out[i0 + j] = run;
+      run += v[j];
+    }
     __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    if (threadIdx.x == blockDim.x - 1) carry = run;
     __syncthreads();
   }
   if (threadIdx.x == 0) out[n] = carry;
@@ -831,33 +844,42 @@ static __global__ void k_dig_counts(const CellParams* __restrict__ cps, const in
                                     const double* __restrict__ target, uint32_t iter,
                                     int det, double slack, int32_t* __restrict__ nt,
                                     int32_t* __restrict__ caps, int32_t* __restrict__ flags) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
-    const int cs = cell_case[c];
-    const CellParams& cp = cps[cs];
-    const int lcell = c - cell0[cs];
-    const double* t = target + (size_t)c * 6;
-    bool bad = false;
-    for (int q = 0; q < 6; ++q)
-      if (!isfinite(t[q])) bad = true;
-    if (!(t[0] >= 0.0) || !(t[4] > 0.0) || !(t[5] > 0.0)) bad = true;
-    if (bad) {
-      atomicOr(flags, 1);
-      nt[c] = 0;
-      caps[c] = 0;
-      continue;
+  // the loop runs the same number of times in every lane of a warp, so that
+  // the new total is summed per warp and added with one atomic
+  const int stride = gridDim.x * blockDim.x;
+  for (int c0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < ncells; c0 += stride) {
+    const int c = c0 + (threadIdx.x & 31);
+    int32_t nv = 0;
+    if (c < ncells) {
+      const int cs = cell_case[c];
+      const CellParams& cp = cps[cs];
+      const int lcell = c - cell0[cs];
+      const double* t = target + (size_t)c * 6;
+      bool bad = false;
+      for (int q = 0; q < 6; ++q)
+        if (!isfinite(t[q])) bad = true;
+      if (!(t[0] >= 0.0) || !(t[4] > 0.0) || !(t[5] > 0.0)) bad = true;
+      if (bad) {
+        atomicOr(flags, 1);
+        nt[c] = 0;
+        caps[c] = 0;
+      } else {
+        Stream<double> st(TAG_DIG_N, 0u, (uint32_t)lcell, iter, cp.k0, cp.k1);
+        const double xm = t[0] * cp.vcell / cp.fnum;
+        long long v = iround(xm, st.u(0));
+        if (v > 0x3fffffffLL) {
+          atomicOr(flags, 2);
+          v = 0;
+        }
+        nv = (int32_t)v;
+        nt[c] = nv;
+        // FP32 bins: room for slack x the larger of the new and the nominal count
+        const int32_t nominal = (int32_t)(cp.vcell / cp.fnum + 0.5);
+        caps[c] = det ? nv : bin_cap_of(max(nv, nominal), slack);
+      }
     }
-    Stream<double> st(TAG_DIG_N, 0u, (uint32_t)lcell, iter, cp.k0, cp.k1);
-    const double xm = t[0] * cp.vcell / cp.fnum;
-    long long v = iround(xm, st.u(0));
-    if (v > 0x3fffffffLL) {
-      atomicOr(flags, 2);
-      v = 0;
-    }
-    nt[c] = (int32_t)v;
-    // FP32 bins: room for slack x the larger of the new and the nominal count
-    const int32_t nominal = (int32_t)(cp.vcell / cp.fnum + 0.5);
-    caps[c] = det ? (int32_t)v : bin_cap_of(max((int32_t)v, nominal), slack);
-    atomicAdd(&flags[3], (int32_t)v);
+    const int32_t wtot = __reduce_add_sync(FULL, nv);
+    if ((threadIdx.x & 31) == 0 && wtot) atomicAdd(&flags[3], wtot);
   }
 }
 
@@ -894,6 +916,23 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
   const int s0 = start_in[cell], n = cnt_in[cell], d0 = start_out[cell], ntg = nt[cell];
   const double* t = target + (size_t)cell * 6;
   const int ix = lcell % cp.nx, iy = lcell / cp.nx;
+  // FP32 particles: the sums of step iii are taken while the new population
+  // is written, of w = v - u_target (so that the second moment about the
+  // mean, E[w^2] - E[w]^2, keeps its digits when the mean is near the
+  // target); the FP64 layout sums in a second and third pass below
+  constexpr bool ONE_PASS = sizeof(T) == 4;
+  const float tux = (float)t[1], tuy = (float)t[2], tuz = (float)t[3];
+  float swx = 0.f, swy = 0.f, swz = 0.f, sir = 0.f, sw2 = 0.f;
+  auto tally = [&](T vx, T vy, T vz, T ir) {
+    if constexpr (ONE_PASS) {
+      const float wx = (float)vx - tux, wy = (float)vy - tuy, wz = (float)vz - tuz;
+      swx += wx;
+      swy += wy;
+      swz += wz;
+      sir += (float)ir;
+      sw2 = fmaf(wx, wx, fmaf(wy, wy, fmaf(wz, wz, sw2)));
+    }
+  };
   int32_t* idx = (n <= tile) ? reinterpret_cast<int32_t*>(smem) + (size_t)warp * tile * 2 : idx_g + s0;
   int32_t* rm = (n <= tile) ? reinterpret_cast<int32_t*>(smem) + (size_t)warp * tile * 2 + tile : nullptr;
   // step ii
@@ -902,14 +941,25 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
     if (k > 0) {
       for (int q = lane; q < n; q += 32) idx[q] = q;
       __syncwarp();
-      if (lane == 0) {
-        for (int q = 0; q < k; ++q) {
+      // partial Fisher-Yates: swap q draws r_q = q + floor(u_q (n - q)), which
+      // does not depend on the earlier swaps, so 32 lanes draw at once and
+      // lane 0 applies the swaps in order
+      for (int qb = 0; qb < k; qb += 32) {
+        const int q = qb + lane;
+        int r = 0;
+        if (q < k) {
           Stream<double> st(TAG_DIG_SEL, (uint32_t)q, (uint32_t)lcell, iter, cp.k0, cp.k1);
-          int r = q + (int)(st.u(0) * (double)(n - q));
+          r = q + (int)(st.u(0) * (double)(n - q));
           if (r > n - 1) r = n - 1;
-          const int tmp = idx[q];
-          idx[q] = idx[r];
-          idx[r] = tmp;
+        }
+        const int m = min(32, k - qb);
+        for (int j = 0; j < m; ++j) {
+          const int rj = __shfl_sync(FULL, r, j);
+          if (lane == 0) {
+            const int tmp = idx[qb + j];
+            idx[qb + j] = idx[rj];
+            idx[rj] = tmp;
+          }
         }
       }
       __syncwarp();
@@ -940,23 +990,27 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
       const unsigned m = __ballot_sync(FULL, keep);
       if (keep) {
         const int w = d0 + kept_before + __popc(m & ((1u << lane) - 1u));
+        const T vx = in.vx[s0 + q], vy = in.vy[s0 + q], vz = in.vz[s0 + q], ir = in.ir[s0 + q];
         out.x[w] = in.x[s0 + q];
         out.y[w] = in.y[s0 + q];
-        out.vx[w] = in.vx[s0 + q];
-        out.vy[w] = in.vy[s0 + q];
-        out.vz[w] = in.vz[s0 + q];
-        out.ir[w] = in.ir[s0 + q];
+        out.vx[w] = vx;
+        out.vy[w] = vy;
+        out.vz[w] = vz;
+        out.ir[w] = ir;
+        tally(vx, vy, vz, ir);
       }
       kept_before += __popc(m);
     }
   } else {
     for (int q = lane; q < n; q += 32) {
+      const T vx = in.vx[s0 + q], vy = in.vy[s0 + q], vz = in.vz[s0 + q], ir = in.ir[s0 + q];
       out.x[d0 + q] = in.x[s0 + q];
       out.y[d0 + q] = in.y[s0 + q];
-      out.vx[d0 + q] = in.vx[s0 + q];
-      out.vy[d0 + q] = in.vy[s0 + q];
-      out.vz[d0 + q] = in.vz[s0 + q];
-      out.ir[d0 + q] = in.ir[s0 + q];
+      out.vx[d0 + q] = vx;
+      out.vy[d0 + q] = vy;
+      out.vz[d0 + q] = vz;
+      out.ir[d0 + q] = ir;
+      tally(vx, vy, vz, ir);
     }
     for (int q = lane; q < ntg - n; q += 32) {
       Stream<double> sp(TAG_DIG_POS, (uint32_t)q, (uint32_t)lcell, iter, cp.k0, cp.k1);
@@ -967,26 +1021,58 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
         Stream<double> ss(TAG_DIG_SEL, (uint32_t)q, (uint32_t)lcell, iter, cp.k0, cp.k1);
         int src = (int)(ss.u(0) * (double)n);
         if (src > n - 1) src = n - 1;
-        out.vx[w] = in.vx[s0 + src];
-        out.vy[w] = in.vy[s0 + src];
-        out.vz[w] = in.vz[s0 + src];
-        out.ir[w] = in.ir[s0 + src];
+        const T vx = in.vx[s0 + src], vy = in.vy[s0 + src], vz = in.vz[s0 + src], ir = in.ir[s0 + src];
+        out.vx[w] = vx;
+        out.vy[w] = vy;
+        out.vz[w] = vz;
+        out.ir[w] = ir;
+        tally(vx, vy, vz, ir);
       } else {
         double n1, n2, n3, n4;
         box_muller(sp.u(2), sp.u(3), &n1, &n2);
         box_muller(sp.u(4), sp.u(5), &n3, &n4);
         const double stt = sqrt(t[4]);
-        out.vx[w] = (T)(t[1] + stt * n1);
-        out.vy[w] = (T)(t[2] + stt * n2);
-        out.vz[w] = (T)(t[3] + stt * n3);
-        out.ir[w] = (T)(-t[5] * log(sp.u(6)));
+        const T vx = (T)(t[1] + stt * n1), vy = (T)(t[2] + stt * n2), vz = (T)(t[3] + stt * n3);
+        const T ir = (T)(-t[5] * log(sp.u(6)));
+        out.vx[w] = vx;
+        out.vy[w] = vy;
+        out.vz[w] = vz;
+        out.ir[w] = ir;
+        tally(vx, vy, vz, ir);
       }
     }
   }
   __syncwarp();
-  // step iii: u*, T_t*, T_r* of the new population (FP64 sums)
+  // step iii: u*, T_t*, T_r* of the new population
   const int np = ntg;
-  if (np > 0) {
+  if constexpr (ONE_PASS) {
+    if (np > 0) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        swx += __shfl_xor_sync(FULL, swx, o);
+        swy += __shfl_xor_sync(FULL, swy, o);
+        swz += __shfl_xor_sync(FULL, swz, o);
+        sir += __shfl_xor_sync(FULL, sir, o);
+        sw2 += __shfl_xor_sync(FULL, sw2, o);
+      }
+      const float inv = 1.f / (float)np;
+      const float mx = swx * inv, my = swy * inv, mz = swz * inv;
+      const float tts = (sw2 * inv - (mx * mx + my * my + mz * mz)) * (1.f / 3.f);
+      const float trs = 2.f * sir * inv / (float)cp.d_r;
+      // step iv: v <- a v + b = u_target + a (v - u*), I_r <- c I_r
+      const float a = (np >= 2 && tts > 0.f) ? sqrtf((float)t[4] / tts) : 1.f;
+      const float bx = tux - (tux + mx) * a, by = tuy - (tuy + my) * a, bz = tuz - (tuz + mz) * a;
+      const float cc = (trs > 0.f) ? (float)t[5] / trs : 1.f;
+      for (int q = lane; q < np; q += 32) {
+        const int w = d0 + q;
+        out.vx[w] = (T)fmaf(a, (float)out.vx[w], bx);
+        out.vy[w] = (T)fmaf(a, (float)out.vy[w], by);
+        out.vz[w] = (T)fmaf(a, (float)out.vz[w], bz);
+        out.ir[w] = (T)(cc * (float)out.ir[w]);
+        if (cellof_out) cellof_out[w] = cell;
+      }
+    }
+  } else if (np > 0) {
     double sx = 0, sy = 0, sz = 0, si = 0;
     for (int q = lane; q < np; q += 32) {
       sx += (double)out.vx[d0 + q];

@@ -389,6 +389,62 @@ def test_fp32_cell_above_tile_conserves():
     assert g.stats()["n_coll"] > 0
 
 
+@pytest.mark.parametrize("case", ["cavity", "crowded"])
+def test_dig_correct_matches_oracle_fp32(case):
+    """FP32 layout, Sec. 3.2: given the GPU's own particles in the GPU's own
+    order, the oracle's modification draws the same target counts, removes
+    and replicates the same particles and places new ones at the same
+    positions (FP32 rounding of its FP64 positions); velocities and I_r
+    follow its FP64 transform to FP32 arithmetic (relative 1e-5 of
+    max(|v|, 1)), and each cell's new mean velocity, T_t and T_r equal the
+    target to that level.  "crowded": one cell of 900 particles (above the
+    shared-memory tile) loses 600 of them, so that the removal runs in
+    global memory and its draws span many warp-wide rounds."""
+    if case == "cavity":
+        cfg = W.cavity_2d(nx=9, ny=7, ppc=60, precision="fp32")
+        g = _gpu(cfg)
+        g.dsmc_step(5)
+    else:
+        cfg = W.fourier_1d(nx=12, ppc=60, kn=0.02, precision="fp32", capacity=20000)
+        g = _gpu(cfg)
+        g.set_particles({k: torch.tensor(v) for k, v in _crowded_state(12, 60, 5, 900, seed=6).items()})
+    nc = g.ncells
+    rng = np.random.default_rng(11)
+    t = np.zeros((nc, 6))
+    t[:, 0] = 0.6 + 0.8 * rng.random(nc)
+    t[1, 0] = 0.0  # empty a cell
+    t[:, 1:4] = 0.2 * rng.standard_normal((nc, 3))
+    t[:, 4] = 0.9 + 0.4 * rng.random(nc)
+    t[:, 5] = 0.8 + 0.4 * rng.random(nc)
+    if case == "crowded":
+        t[5, 0] = 5.0  # 300 of the cell's 900 particles stay
+    for rep in range(2):
+        p = _np(g.get_particles())
+        o = oracle.OracleSim(cfg)
+        o.set_particles({k: p[k] for k in KEYS})
+        assert np.array_equal(o.particles()["cell"], p["cell"])
+        o.set_step(0, dig_iter=rep)
+        g.dig_correct(torch.tensor(t, device="cuda"))
+        assert o.dig_correct(t) == 0
+        a, b = _np(g.get_particles()), o.particles()
+        assert np.array_equal(a["cell"], b["cell"]), f"dig {rep}: counts differ"
+        for k in KEYS:
+            tol = 1e-7 if k in ("x", "y") else 1e-5
+            err = np.abs(a[k] - b[k]) / np.maximum(np.abs(b[k]), 1.0)
+            assert err.max() <= tol, (rep, k, err.max())
+        cnt = np.bincount(a["cell"], minlength=nc)
+        full = cnt >= 2
+        for j, k in enumerate(("vx", "vy", "vz")):
+            mean = np.bincount(a["cell"], a[k], nc)[full] / cnt[full]
+            assert np.max(np.abs(mean - t[full, 1 + j])) <= 1e-5, (rep, k)
+        c2 = sum(np.bincount(a["cell"], (a[k] - t[a["cell"], 1 + j]) ** 2, nc) for j, k in enumerate(("vx", "vy", "vz")))
+        tt = c2[full] / (3 * cnt[full])
+        assert np.max(np.abs(tt / t[full, 4] - 1)) <= 1e-5, rep
+        tr = np.bincount(a["cell"], a["ir"], nc)[full] / cnt[full]  # 2 I_r / d_r with d_r = 2
+        assert np.max(np.abs(tr / t[full, 5] - 1)) <= 1e-5, rep
+        t[1, 0] = 1.0  # refill the empty cell from the target Maxwellian
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_nearly_empty_domain(prec):
     """Most cells empty, a few with one or two particles: steps run,
