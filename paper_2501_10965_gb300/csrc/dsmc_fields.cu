@@ -152,9 +152,10 @@ void launch_hot(const CellParams* cp, const int32_t* cell_case, const int32_t* c
 // inside, d/dx sigma_xy = 0, d/dx sigma_xz = 0,
 // d/dx (sigma_xy u_y + sigma_xz u_z + q_t + q_r) = 0,
 // -d/dx q_r + (d_r/2) rho p (T - T_r) / (Z mu) = 0 with p = rho T;
-// plus sum rho_i dx = sampled mass.  Newton with a Jacobian by central
-// differences of each cell's local residual, and a bordered block-tridiagonal
-// solve (block Thomas, one thread).
+// plus sum rho_i dx = sampled mass.  Newton: the residual in FP64 (each face's
+// fluxes once, then each cell's rows), the Jacobian by central differences in
+// FP32, a bordered block-tridiagonal solve by cyclic reduction in FP32 with
+// the mass row in FP64.
 // ---------------------------------------------------------------------------
 struct SynthArgs {
   CellParams cp;
@@ -192,115 +193,65 @@ __device__ __forceinline__ double* case_work(const SynthCases& sc, int c) {
   return sc.work + (sc.woff ? sc.woff[c] : 0);
 }
 
-__device__ __forceinline__ double synth_pow(double x, double e) { return pow(x, e); }
-__device__ __forceinline__ float synth_pow(float x, float e) { return exp2f(e * __log2f(x)); }
-
-// Face i+1/2 fluxes: shear stresses, rotational heat flux and energy flux.
-// T = double for the residual; T = float for the finite-difference Jacobian
-// (it only steers Newton's steps: the residual decides the solution).
-template <typename T>
-__device__ __forceinline__ void face_flux(const SynthArgs& a, int i, const T* yl, const T* yr, T* sxy, T* sxz,
-                                          T* qr, T* e) {
+// FP64 fluxes at face i+1/2 from the states of cells i (yl) and i+1 (yr):
+// f = (sigma_xy, sigma_xz, q_r, sigma_xy u_y + sigma_xz u_z + q_t + q_r)
+__device__ __forceinline__ void face_flux(const SynthArgs& a, int i, const double* yl, const double* yr, double* f) {
   const CellParams& cp = a.cp;
-  const T d_r = (T)cp.d_r, dx = (T)cp.dx;
-  const T ttf = T(0.5) * (yl[2] + yr[2]);
-  const T trf = T(0.5) * (yl[3] + yr[3]);
-  const T Tf = (T(3) * ttf + d_r * trf) / (T(3) + d_r);
-  const T muf = (T)cp.mu_ref * synth_pow(Tf, (T)cp.omega);
+  const double d_r = cp.d_r, dx = cp.dx;
+  const double ttf = 0.5 * (yl[2] + yr[2]);
+  const double trf = 0.5 * (yl[3] + yr[3]);
+  const double Tf = (3.0 * ttf + d_r * trf) / (3.0 + d_r);
+  const double muf = cp.mu_ref * pow(Tf, cp.omega);
   const double* hl = a.hot + (size_t)i * 12;
   const double* hr = a.hot + (size_t)(i + 1) * 12;
-  const T h3 = (T)(0.5 * (hl[3] + hr[3])), h4 = (T)(0.5 * (hl[4] + hr[4]));
-  const T h6 = (T)(0.5 * (hl[6] + hr[6])), h9 = (T)(0.5 * (hl[9] + hr[9]));
-  *sxy = -muf * (yr[0] - yl[0]) / dx + h3;
-  *sxz = -muf * (yr[1] - yl[1]) / dx + h4;
-  const T qt = -(T)cp.kappa_t * muf * (yr[2] - yl[2]) / dx + h6;
-  *qr = -(T)cp.kappa_r * muf * (yr[3] - yl[3]) / dx + h9;
-  const T uyf = T(0.5) * (yl[0] + yr[0]), uzf = T(0.5) * (yl[1] + yr[1]);
-  *e = *sxy * uyf + *sxz * uzf + qt + *qr;
+  const double h3 = 0.5 * (hl[3] + hr[3]), h4 = 0.5 * (hl[4] + hr[4]);
+  const double h6 = 0.5 * (hl[6] + hr[6]), h9 = 0.5 * (hl[9] + hr[9]);
+  const double sxy = -muf * (yr[0] - yl[0]) / dx + h3;
+  const double sxz = -muf * (yr[1] - yl[1]) / dx + h4;
+  const double qt = -cp.kappa_t * muf * (yr[2] - yl[2]) / dx + h6;
+  const double qr = -cp.kappa_r * muf * (yr[3] - yl[3]) / dx + h9;
+  const double uyf = 0.5 * (yl[0] + yr[0]), uzf = 0.5 * (yl[1] + yr[1]);
+  f[0] = sxy;
+  f[1] = sxz;
+  f[2] = qr;
+  f[3] = sxy * uyf + sxz * uzf + qt + qr;
 }
 
-// residual rows of cell i from y_{i-1}, y_i, y_{i+1} and P
-template <typename T>
-__device__ void local_res(const SynthArgs& a, int i, int n, const T* ym, const T* y0, const T* yp, T P, T* R) {
+// FP64 residual rows of cell i from its state y0, the fluxes fm, fp of faces
+// i-1/2 and i+1/2, and P
+__device__ __forceinline__ void cell_rows(const SynthArgs& a, int i, int n, const double* y0, const double* fm,
+                                          const double* fp, double P, double* R) {
   const CellParams& cp = a.cp;
   if (i == 0 || i == n - 1) {
     const double* f = a.F + (size_t)i * 18;
-    R[0] = y0[0] - (T)f[2];
-    R[1] = y0[1] - (T)f[3];
-    R[2] = y0[2] - (T)f[4];
-    R[3] = y0[3] - (T)f[5];
+    R[0] = y0[0] - f[2];
+    R[1] = y0[1] - f[3];
+    R[2] = y0[2] - f[4];
+    R[3] = y0[3] - f[5];
     return;
   }
-  const T d_r = (T)cp.d_r;
-  T sxy_p, sxz_p, qr_p, e_p, sxy_m, sxz_m, qr_m, e_m;
-  face_flux<T>(a, i, y0, yp, &sxy_p, &sxz_p, &qr_p, &e_p);
-  face_flux<T>(a, i - 1, ym, y0, &sxy_m, &sxz_m, &qr_m, &e_m);
-  const T rho = (P - (T)a.hot[(size_t)i * 12 + 0]) / y0[2];
-  const T Tc = (T(3) * y0[2] + d_r * y0[3]) / (T(3) + d_r);
-  const T mu = (T)cp.mu_ref * synth_pow(Tc, (T)cp.omega);
-  const T src = T(0.5) * d_r * rho * (rho * Tc) * (Tc - y0[3]) / ((T)cp.z_rot * mu);
-  R[0] = sxy_p - sxy_m;
-  R[1] = sxz_p - sxz_m;
-  R[2] = e_p - e_m;
-  R[3] = -(qr_p - qr_m) / (T)cp.dx + src;
+  const double d_r = cp.d_r;
+  const double rho = (P - a.hot[(size_t)i * 12 + 0]) / y0[2];
+  const double Tc = (3.0 * y0[2] + d_r * y0[3]) / (3.0 + d_r);
+  const double mu = cp.mu_ref * pow(Tc, cp.omega);
+  const double src = 0.5 * d_r * rho * (rho * Tc) * (Tc - y0[3]) / (cp.z_rot * mu);
+  R[0] = fp[0] - fm[0];
+  R[1] = fp[1] - fm[1];
+  R[2] = fp[3] - fm[3];
+  R[3] = -(fp[2] - fm[2]) / cp.dx + src;
 }
 
-__device__ void inv4(const double* m, double* r) {
-  // Gauss-Jordan with partial pivoting on a 4x4 matrix
-  double a[4][8];
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) {
-      a[i][j] = m[i * 4 + j];
-      a[i][4 + j] = (i == j) ? 1.0 : 0.0;
-    }
-  for (int c = 0; c < 4; ++c) {
-    int piv = c;
-    for (int i = c + 1; i < 4; ++i)
-      if (fabs(a[i][c]) > fabs(a[piv][c])) piv = i;
-    if (piv != c)
-      for (int j = 0; j < 8; ++j) {
-        const double t = a[c][j];
-        a[c][j] = a[piv][j];
-        a[piv][j] = t;
-      }
-    const double d = a[c][c];
-    for (int j = 0; j < 8; ++j) a[c][j] /= d;
-    for (int i = 0; i < 4; ++i)
-      if (i != c) {
-        const double fct = a[i][c];
-        for (int j = 0; j < 8; ++j) a[i][j] -= fct * a[c][j];
-      }
-  }
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) r[i * 4 + j] = a[i][4 + j];
-}
-
-__device__ __forceinline__ void mm4(const double* a, const double* b, double* c) {
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) {
-      double s = 0.0;
-      for (int k = 0; k < 4; ++k) s += a[i * 4 + k] * b[k * 4 + j];
-      c[i * 4 + j] = s;
-    }
-}
-
-__device__ __forceinline__ void mv4(const double* a, const double* x, double* y) {
-  for (int i = 0; i < 4; ++i) {
-    double s = 0.0;
-    for (int k = 0; k < 4; ++k) s += a[i * 4 + k] * x[k];
-    y[i] = s;
-  }
-}
-
-// Work layout (doubles unless noted), n cells:
-//   y (4n), yn (4n), R (4n), G (4n, dR/dP), h (4n, dR_P/dy), J (48n: A, B, C
-//   blocks, row-major 4x4), scalars (32); then FP32 cyclic-reduction
-//   storage: A, B, C, Binv (16n floats each), r1, r2 (4n floats each).
-size_t synth1d_work_doubles(int n) { return (size_t)n * (20 + 48) + 32 + ((size_t)n * 72 + 1) / 2 + 64; }
+// Work layout, n cells.  Doubles: y (4n), yn (4n; also the face fluxes of
+// the residual), R (4n), scalars (32).  Floats: A, B, C, Binv (16n each;
+// the blocks d R_i / d y_{i-1}, d y_i, d y_{i+1}), r1, r2 (4n each; -R and
+// dR/dP, overwritten by the reduction), yf (4n; y in FP32), hf (4n; HoT
+// sigma_xy, sigma_xz, q_t,x, q_r,x at face i+1/2), h0 (n; HoT sigma_xx per
+// cell), kf (16; constants and P in FP32).
+size_t synth1d_work_doubles(int n) { return (size_t)n * 12 + 32 + ((size_t)n * 85 + 16 + 1) / 2 + 64; }
 
 struct SynthWork {
-  double *y, *yn, *R, *G, *h, *J, *sc;
-  float *A, *B, *C, *Bi, *r1, *r2;
+  double *y, *yn, *R, *sc;
+  float *A, *B, *C, *Bi, *r1, *r2, *yf, *hf, *h0, *kf;
 };
 
 __host__ __device__ inline SynthWork synth_work(double* w, int n) {
@@ -308,10 +259,7 @@ __host__ __device__ inline SynthWork synth_work(double* w, int n) {
   s.y = w;
   s.yn = s.y + 4 * n;
   s.R = s.yn + 4 * n;
-  s.G = s.R + 4 * n;
-  s.h = s.G + 4 * n;
-  s.J = s.h + 4 * n;
-  s.sc = s.J + 48 * n;
+  s.sc = s.R + 4 * n;
   float* f = reinterpret_cast<float*>(s.sc + 32);
   s.A = f;
   s.B = s.A + 16 * n;
@@ -319,18 +267,26 @@ __host__ __device__ inline SynthWork synth_work(double* w, int n) {
   s.Bi = s.C + 16 * n;
   s.r1 = s.Bi + 16 * n;
   s.r2 = s.r1 + 4 * n;
+  s.yf = s.r2 + 4 * n;
+  s.hf = s.yf + 4 * n;
+  s.h0 = s.hf + 4 * n;
+  s.kf = s.h0 + n;
   return s;
 }
 
 // scalar slots: 0 P, 1 mass, 2 done, 3 iterations, 4 status (0 converged,
 // 1 not (yet) converged, 2 numeric), 5 last max relative change
 enum { SC_P = 0, SC_M = 1, SC_DONE = 2, SC_IT = 3, SC_STATUS = 4, SC_DMAX = 5 };
+// FP32 constants of the Jacobian
+enum { KF_DR = 0, KF_IDX, KF_I3DR, KF_MUREF, KF_OMEGA, KF_KT, KF_KR, KF_IZ, KF_P };
 
+template <int NT>
 __device__ double block_sum(double v, double* red) {
   const int tid = threadIdx.x;
   red[tid] = v;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+#pragma unroll
+  for (int o = NT / 2; o > 0; o >>= 1) {
     if (tid < o) red[tid] += red[tid + o];
     __syncthreads();
   }
@@ -339,11 +295,13 @@ __device__ double block_sum(double v, double* red) {
   return r;
 }
 
+template <int NT>
 __device__ double block_max(double v, double* red) {
   const int tid = threadIdx.x;
   red[tid] = v;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+#pragma unroll
+  for (int o = NT / 2; o > 0; o >>= 1) {
     if (tid < o) red[tid] = fmax(red[tid], red[tid + o]);
     __syncthreads();
   }
@@ -352,104 +310,190 @@ __device__ double block_max(double v, double* red) {
   return r;
 }
 
-__global__ void __launch_bounds__(1024) k_synth_init(const __grid_constant__ SynthCases scs) {
-  __shared__ double red[1024];
+// FP64 residual of every cell into w.R (the face fluxes go through w.yn)
+template <int NT>
+__device__ void residual_fp64(const SynthArgs& a, const SynthWork& w, int n, double P) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n - 1; i += NT) face_flux(a, i, w.y + 4 * i, w.y + 4 * (i + 1), w.yn + 4 * i);
+  __syncthreads();
+  for (int i = tid; i < n; i += NT) {
+    const double* fm = (i > 0) ? w.yn + 4 * (i - 1) : nullptr;
+    const double* fp = (i < n - 1) ? w.yn + 4 * i : nullptr;
+    cell_rows(a, i, n, w.y + 4 * i, fm, fp, P, w.R + 4 * i);
+  }
+  __syncthreads();
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_synth_init(const __grid_constant__ SynthCases scs) {
+  __shared__ double red[NT];
   const int cs = blockIdx.x;
   const SynthArgs a = case_args(scs, cs);
   double* work = case_work(scs, cs);
   const int n = a.cp.nx;
   SynthWork w = synth_work(work, n);
   double m = 0.0, pm = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = threadIdx.x; i < n; i += NT) {
     const double* f = a.F + (size_t)i * 18;
-    w.y[4 * i + 0] = f[2];
-    w.y[4 * i + 1] = f[3];
-    w.y[4 * i + 2] = f[4];
-    w.y[4 * i + 3] = f[5];
+    const double* h = a.hot + (size_t)i * 12;
+    for (int v = 0; v < 4; ++v) {
+      w.y[4 * i + v] = f[2 + v];
+      w.yf[4 * i + v] = (float)f[2 + v];
+    }
+    w.h0[i] = (float)h[0];
+    if (i < n - 1) {
+      const double* hr = h + 12;
+      w.hf[4 * i + 0] = (float)(0.5 * (h[3] + hr[3]));
+      w.hf[4 * i + 1] = (float)(0.5 * (h[4] + hr[4]));
+      w.hf[4 * i + 2] = (float)(0.5 * (h[6] + hr[6]));
+      w.hf[4 * i + 3] = (float)(0.5 * (h[9] + hr[9]));
+    }
     m += f[0] * a.cp.dx;
-    pm += f[0] * f[4] + a.hot[(size_t)i * 12];
+    pm += f[0] * f[4] + h[0];
   }
-  const double M = block_sum(m, red);
-  const double PM = block_sum(pm, red);
+  const double M = block_sum<NT>(m, red);
+  const double PM = block_sum<NT>(pm, red);
   if (threadIdx.x == 0) {
+    const CellParams& cp = a.cp;
     w.sc[SC_P] = PM / n;
     w.sc[SC_M] = M;
     w.sc[SC_DONE] = 0.0;
     w.sc[SC_IT] = 0.0;
     w.sc[SC_STATUS] = 1.0;
     w.sc[SC_DMAX] = 0.0;
+    w.kf[KF_DR] = (float)cp.d_r;
+    w.kf[KF_IDX] = (float)(1.0 / cp.dx);
+    w.kf[KF_I3DR] = (float)(1.0 / (3.0 + cp.d_r));
+    w.kf[KF_MUREF] = (float)cp.mu_ref;
+    w.kf[KF_OMEGA] = (float)cp.omega;
+    w.kf[KF_KT] = (float)cp.kappa_t;
+    w.kf[KF_KR] = (float)cp.kappa_r;
+    w.kf[KF_IZ] = (float)(1.0 / cp.z_rot);
+    w.kf[KF_P] = (float)(PM / n);
   }
+}
+
+// FP32 counterparts for the Jacobian (they only steer Newton's steps: the
+// FP64 residual decides the solution)
+struct SynthKf {
+  float d_r, idx, i3dr, mu_ref, omega, kt, kr, iz;
+};
+
+__device__ __forceinline__ float synth_powf(float x, float e) { return exp2f(e * __log2f(x)); }
+
+__device__ __forceinline__ void face_flux_f(const SynthKf& k, const float* hf, const float* yl, const float* yr,
+                                            float* f) {
+  const float ttf = 0.5f * (yl[2] + yr[2]);
+  const float trf = 0.5f * (yl[3] + yr[3]);
+  const float Tf = (3.f * ttf + k.d_r * trf) * k.i3dr;
+  const float muf = k.mu_ref * synth_powf(Tf, k.omega);
+  const float sxy = -muf * (yr[0] - yl[0]) * k.idx + hf[0];
+  const float sxz = -muf * (yr[1] - yl[1]) * k.idx + hf[1];
+  const float qt = -k.kt * muf * (yr[2] - yl[2]) * k.idx + hf[2];
+  const float qr = -k.kr * muf * (yr[3] - yl[3]) * k.idx + hf[3];
+  f[0] = sxy;
+  f[1] = sxz;
+  f[2] = qr;
+  f[3] = sxy * (0.5f * (yl[0] + yr[0])) + sxz * (0.5f * (yl[1] + yr[1])) + qt + qr;
+}
+
+__device__ __forceinline__ float source_f(const SynthKf& k, float h0, const float* y0, float P) {
+  const float rho = __fdividef(P - h0, y0[2]);
+  const float Tc = (3.f * y0[2] + k.d_r * y0[3]) * k.i3dr;
+  const float mu = k.mu_ref * synth_powf(Tc, k.omega);
+  return __fdividef(0.5f * k.d_r * rho * (rho * Tc) * (Tc - y0[3]) * k.iz, mu);
+}
+
+__device__ __forceinline__ void rows_f(const SynthKf& k, const float* hfm, const float* hfp, float h0,
+                                       const float* ym, const float* y0, const float* yp, float P, float* R) {
+  float fm[4], fp[4];
+  face_flux_f(k, hfm, ym, y0, fm);
+  face_flux_f(k, hfp, y0, yp, fp);
+  R[0] = fp[0] - fm[0];
+  R[1] = fp[1] - fm[1];
+  R[2] = fp[3] - fm[3];
+  R[3] = -(fp[2] - fm[2]) * k.idx + source_f(k, h0, y0, P);
 }
 
 // one thread per (cell, column): columns 0..11 are d R_i / d(y_{i-1}, y_i,
-// y_{i+1}) by central differences, column 12 is dR_i/dP together with R_i
-// and the mass-row entries.
+// y_{i+1}) by central differences, written into the blocks A, B, C; column
+// 12 is dR_i/dP (only the rotational source depends on P), written into r2.
+// A column of a neighbour's state changes only that face's fluxes.
 __global__ void k_synth_jac(const __grid_constant__ SynthCases scs) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= scs.ncells * 13) return;
-  const int g = t / 13, col = t % 13;
+  const int g = t / 13, col = t - 13 * (t / 13);
   const int cs = scs.cell_case ? scs.cell_case[g] : 0;
-  const SynthArgs a = case_args(scs, cs);
   const int i = g - (scs.cell0 ? scs.cell0[cs] : 0);
-  const int n = a.cp.nx;
+  const int n = scs.cps ? scs.cps[cs].nx : scs.cp1.nx;
   SynthWork w = synth_work(case_work(scs, cs), n);
   if (w.sc[SC_DONE] != 0.0) return;
-  const double P = w.sc[SC_P];
-  double ym[4], y0[4], yp[4];
-  for (int v = 0; v < 4; ++v) {
-    y0[v] = w.y[4 * i + v];
-    ym[v] = (i > 0) ? w.y[4 * (i - 1) + v] : y0[v];
-    yp[v] = (i < n - 1) ? w.y[4 * (i + 1) + v] : y0[v];
+  const int blk = col >> 2, v = col & 3;
+  float* J = (blk == 0) ? w.A + 16 * i : ((blk == 1) ? w.B + 16 * i : w.C + 16 * i);
+  if (i == 0 || i == n - 1) {
+    // boundary rows R = y_i - sampled: the identity in B
+    if (col < 12)
+      for (int r = 0; r < 4; ++r) J[r * 4 + v] = (blk == 1 && r == v) ? 1.f : 0.f;
+    else
+      for (int r = 0; r < 4; ++r) w.r2[4 * i + r] = 0.f;
+    return;
   }
-  if (col < 12) {
-    // Jacobian columns by central differences in FP32 (step ~ sqrt of the
-    // FP32 rounding unit)
-    const int blk = col / 4, v = col % 4;
-    double* J = w.J + 48 * (size_t)i + 16 * blk;
-    const bool exists = (blk == 1) || (blk == 0 && i > 0) || (blk == 2 && i < n - 1);
-    if (!exists) {
-      for (int r = 0; r < 4; ++r) J[r * 4 + v] = 0.0;
-      return;
-    }
-    float fm[4], f0[4], fp[4], frp[4], frm[4];
-    for (int q = 0; q < 4; ++q) {
-      fm[q] = (float)ym[q];
-      f0[q] = (float)y0[q];
-      fp[q] = (float)yp[q];
-    }
-    float* yy = (blk == 0) ? fm : ((blk == 1) ? f0 : fp);
-    const float sv = yy[v];
-    const float hh = 1e-3f * fmaxf(fabsf(sv), 1.0f);
+  const SynthKf k{w.kf[KF_DR], w.kf[KF_IDX], w.kf[KF_I3DR], w.kf[KF_MUREF],
+                  w.kf[KF_OMEGA], w.kf[KF_KT], w.kf[KF_KR], w.kf[KF_IZ]};
+  const float P = w.kf[KF_P];
+  float ym[4], y0[4], yp[4];
+  for (int q = 0; q < 4; ++q) {
+    ym[q] = w.yf[4 * (i - 1) + q];
+    y0[q] = w.yf[4 * i + q];
+    yp[q] = w.yf[4 * (i + 1) + q];
+  }
+  const float* hfm = w.hf + 4 * (i - 1);
+  const float* hfp = w.hf + 4 * i;
+  if (col == 12) {
+    const float hP = 1e-3f * fmaxf(fabsf(P), 1.0f);
+    const float h2 = (P + hP) - (P - hP);
+    const float ds = source_f(k, w.h0[i], y0, P + hP) - source_f(k, w.h0[i], y0, P - hP);
+    w.r2[4 * i + 0] = 0.f;
+    w.r2[4 * i + 1] = 0.f;
+    w.r2[4 * i + 2] = 0.f;
+    w.r2[4 * i + 3] = ds / h2;
+    return;
+  }
+  // step ~ sqrt of the FP32 rounding unit
+  float* yy = (blk == 0) ? ym : ((blk == 1) ? y0 : yp);
+  const float sv = yy[v];
+  const float hh = 1e-3f * fmaxf(fabsf(sv), 1.0f);
+  const float h2 = (sv + hh) - (sv - hh);  // the step actually taken
+  float d[4];
+  if (blk == 1) {
+    float rp[4], rm[4];
     yy[v] = sv + hh;
-    local_res<float>(a, i, n, fm, f0, fp, (float)P, frp);
+    rows_f(k, hfm, hfp, w.h0[i], ym, y0, yp, P, rp);
     yy[v] = sv - hh;
-    local_res<float>(a, i, n, fm, f0, fp, (float)P, frm);
-    const float h2 = (sv + hh) - (sv - hh);  // the step actually taken
-    for (int r = 0; r < 4; ++r) J[r * 4 + v] = (double)((frp[r] - frm[r]) / h2);
+    rows_f(k, hfm, hfp, w.h0[i], ym, y0, yp, P, rm);
+    for (int r = 0; r < 4; ++r) d[r] = rp[r] - rm[r];
   } else {
-    // the column of P, also in FP32 (the FP64 residual is taken by the solve
-    // kernel, one thread per cell, away from these warps)
-    float fm[4], f0[4], fp[4], frp[4], frm[4];
-    for (int q = 0; q < 4; ++q) {
-      fm[q] = (float)ym[q];
-      f0[q] = (float)y0[q];
-      fp[q] = (float)yp[q];
-    }
-    const float Pf = (float)P;
-    const float hP = 1e-3f * fmaxf(fabsf(Pf), 1.0f);
-    local_res<float>(a, i, n, fm, f0, fp, Pf + hP, frp);
-    local_res<float>(a, i, n, fm, f0, fp, Pf - hP, frm);
-    const float h2 = (Pf + hP) - (Pf - hP);
-    for (int r = 0; r < 4; ++r) w.G[4 * i + r] = (double)((frp[r] - frm[r]) / h2);
-    const double Hi = a.hot[(size_t)i * 12];
-    w.h[4 * i + 0] = 0.0;
-    w.h[4 * i + 1] = 0.0;
-    w.h[4 * i + 2] = -a.cp.dx * (P - Hi) / (y0[2] * y0[2]);
-    w.h[4 * i + 3] = 0.0;
+    // the face shared with the perturbed neighbour: R = f(i+1/2) - f(i-1/2)
+    // in rows 0..2 and -(q_r(i+1/2) - q_r(i-1/2)) / dx in row 3
+    float fp[4], fm[4];
+    const float* hfc = (blk == 0) ? hfm : hfp;
+    const float* yl = (blk == 0) ? ym : y0;
+    const float* yr = (blk == 0) ? y0 : yp;
+    yy[v] = sv + hh;
+    face_flux_f(k, hfc, yl, yr, fp);
+    yy[v] = sv - hh;
+    face_flux_f(k, hfc, yl, yr, fm);
+    const float sg = (blk == 0) ? -1.f : 1.f;
+    d[0] = sg * (fp[0] - fm[0]);
+    d[1] = sg * (fp[1] - fm[1]);
+    d[2] = sg * (fp[3] - fm[3]);
+    d[3] = -sg * (fp[2] - fm[2]) * k.idx;
   }
+  for (int r = 0; r < 4; ++r) J[r * 4 + v] = d[r] / h2;
 }
 
 __device__ void inv4f(const float* m, float* r) {
+  // Gauss-Jordan with partial pivoting on a 4x4 matrix
   float a[4][8];
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
@@ -466,12 +510,12 @@ __device__ void inv4f(const float* m, float* r) {
         a[c][j] = a[piv][j];
         a[piv][j] = t;
       }
-    const float d = a[c][c];
-    for (int j = 0; j < 8; ++j) a[c][j] /= d;
+    const float dinv = 1.f / a[c][c];
+    for (int j = 0; j < 8; ++j) a[c][j] *= dinv;
     for (int i = 0; i < 4; ++i)
       if (i != c) {
         const float fct = a[i][c];
-        for (int j = 0; j < 8; ++j) a[i][j] -= fct * a[c][j];
+        for (int j = 0; j < 8; ++j) a[i][j] = __fmaf_rn(-fct, a[c][j], a[i][j]);
       }
   }
   for (int i = 0; i < 4; ++i)
@@ -482,7 +526,7 @@ __device__ __forceinline__ void mm4f(const float* a, const float* b, float* c) {
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
       float s = 0.f;
-      for (int k = 0; k < 4; ++k) s += a[i * 4 + k] * b[k * 4 + j];
+      for (int k = 0; k < 4; ++k) s = __fmaf_rn(a[i * 4 + k], b[k * 4 + j], s);
       c[i * 4 + j] = s;
     }
 }
@@ -490,7 +534,7 @@ __device__ __forceinline__ void mm4f(const float* a, const float* b, float* c) {
 __device__ __forceinline__ void mv4f(const float* a, const float* x, float* y) {
   for (int i = 0; i < 4; ++i) {
     float s = 0.f;
-    for (int k = 0; k < 4; ++k) s += a[i * 4 + k] * x[k];
+    for (int k = 0; k < 4; ++k) s = __fmaf_rn(a[i * 4 + k], x[k], s);
     y[i] = s;
   }
 }
@@ -499,9 +543,10 @@ __device__ __forceinline__ void mv4f(const float* a, const float* x, float* y) {
 // bordered mass row in FP64; a damped update that keeps rho, T positive.
 // count_done: add 1 to the finished-slab count (info[3 ncases]) for every
 // slab that is finished after this launch
-__global__ void __launch_bounds__(1024) k_synth_solve(const __grid_constant__ SynthCases scs, int n_m, double tol,
-                                                      int count_done) {
-  __shared__ double red[1024];
+template <int NT>
+__global__ void __launch_bounds__(NT) k_synth_solve(const __grid_constant__ SynthCases scs, int n_m, double tol,
+                                                    int count_done) {
+  __shared__ double red[NT];
   const int cs = blockIdx.x;
   const SynthArgs a = case_args(scs, cs);
   const int n = a.cp.nx;
@@ -510,30 +555,11 @@ __global__ void __launch_bounds__(1024) k_synth_solve(const __grid_constant__ Sy
     if (count_done && threadIdx.x == 0) atomicAdd(scs.info + 3 * scs.ncases, 1.0);
     return;
   }
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = NT;
   const double P = w.sc[SC_P];
-  // FP64 residual of every cell at the current iterate
-  for (int i = tid; i < n; i += nt) {
-    double ym[4], y0[4], yp[4];
-    for (int v = 0; v < 4; ++v) {
-      y0[v] = w.y[4 * i + v];
-      ym[v] = (i > 0) ? w.y[4 * (i - 1) + v] : y0[v];
-      yp[v] = (i < n - 1) ? w.y[4 * (i + 1) + v] : y0[v];
-    }
-    local_res<double>(a, i, n, ym, y0, yp, P, w.R + 4 * i);
-  }
-  __syncthreads();
-  for (int i = tid; i < n; i += nt) {
-    for (int q = 0; q < 16; ++q) {
-      w.A[16 * i + q] = (float)w.J[48 * (size_t)i + q];
-      w.B[16 * i + q] = (float)w.J[48 * (size_t)i + 16 + q];
-      w.C[16 * i + q] = (float)w.J[48 * (size_t)i + 32 + q];
-    }
-    for (int v = 0; v < 4; ++v) {
-      w.r1[4 * i + v] = (float)(-w.R[4 * i + v]);
-      w.r2[4 * i + v] = (float)w.G[4 * i + v];
-    }
-  }
+  residual_fp64<NT>(a, w, n, P);
+  for (int i = tid; i < n; i += nt)
+    for (int v = 0; v < 4; ++v) w.r1[4 * i + v] = (float)(-w.R[4 * i + v]);
   __syncthreads();
   // forward reduction: at stride s the rows i = 2s-1 (mod 2s) eliminate their
   // neighbours i -/+ s, which keep their equations for back substitution
@@ -628,21 +654,23 @@ __global__ void __launch_bounds__(1024) k_synth_solve(const __grid_constant__ Sy
     }
     __syncthreads();
   }
-  // bordered correction in FP64: [J G; h^T d] [dy; dP] = [-R; -(mass - M)]
+  // bordered correction in FP64: [J G; h^T d] [dy; dP] = [-R; -(mass - M)],
+  // h the derivative of the mass sum dx (P - H_i) / T_t,i by T_t,i
   double mass = 0.0, dP = 0.0, hz1 = 0.0, hz2 = 0.0;
   for (int i = tid; i < n; i += nt) {
     const double Hi = a.hot[(size_t)i * 12];
-    mass += (P - Hi) / w.y[4 * i + 2] * a.cp.dx;
-    dP += a.cp.dx / w.y[4 * i + 2];
-    for (int v = 0; v < 4; ++v) {
-      hz1 += w.h[4 * i + v] * (double)w.r1[4 * i + v];
-      hz2 += w.h[4 * i + v] * (double)w.r2[4 * i + v];
-    }
+    const double tt = w.y[4 * i + 2];
+    const double itt = 1.0 / tt;
+    mass += (P - Hi) / tt * a.cp.dx;
+    dP += a.cp.dx * itt;
+    const double hi = -a.cp.dx * (P - Hi) * itt * itt;
+    hz1 += hi * (double)w.r1[4 * i + 2];
+    hz2 += hi * (double)w.r2[4 * i + 2];
   }
-  mass = block_sum(mass, red);
-  dP = block_sum(dP, red);
-  hz1 = block_sum(hz1, red);
-  hz2 = block_sum(hz2, red);
+  mass = block_sum<NT>(mass, red);
+  dP = block_sum<NT>(dP, red);
+  hz1 = block_sum<NT>(hz1, red);
+  hz2 = block_sum<NT>(hz2, red);
   const double RP = mass - w.sc[SC_M];
   const double dPstep = (-RP - hz1) / (dP - hz2);
   double lam = 1.0;
@@ -666,9 +694,10 @@ __global__ void __launch_bounds__(1024) k_synth_solve(const __grid_constant__ Sy
       for (int v = 0; v < 4; ++v) {
         dmax = fmax(dmax, fabs(w.yn[4 * i + v] - w.y[4 * i + v]) / fmax(fabs(w.y[4 * i + v]), 1e-3));
         w.y[4 * i + v] = w.yn[4 * i + v];
+        w.yf[4 * i + v] = (float)w.yn[4 * i + v];
       }
   }
-  dmax = block_max(dmax, red);
+  dmax = block_max<NT>(dmax, red);
   if (tid == 0) {
     const double it = w.sc[SC_IT] + 1.0;
     w.sc[SC_IT] = it;
@@ -679,6 +708,7 @@ __global__ void __launch_bounds__(1024) k_synth_solve(const __grid_constant__ Sy
       const double Pn = P + lam * dPstep;
       dmax = fmax(dmax, fabs(Pn - P) / fmax(fabs(P), 1e-3));
       w.sc[SC_P] = Pn;
+      w.kf[KF_P] = (float)Pn;
       w.sc[SC_DMAX] = dmax;
       if (dmax < tol) {
         w.sc[SC_STATUS] = 0.0;
@@ -691,8 +721,9 @@ __global__ void __launch_bounds__(1024) k_synth_solve(const __grid_constant__ Sy
   }
 }
 
-__global__ void __launch_bounds__(1024) k_synth_final(const __grid_constant__ SynthCases scs, double* out_all) {
-  __shared__ double red[1024];
+template <int NT>
+__global__ void __launch_bounds__(NT) k_synth_final(const __grid_constant__ SynthCases scs, double* out_all) {
+  __shared__ double red[NT];
   __shared__ double s_status;
   const int cs = blockIdx.x;
   const SynthArgs a = case_args(scs, cs);
@@ -705,26 +736,21 @@ __global__ void __launch_bounds__(1024) k_synth_final(const __grid_constant__ Sy
   // finite and positive and keeps the sampled mass (the mass condition is
   // not linear in the unknowns, so an unconverged iterate may break it);
   // otherwise the slab keeps its sampled fields
+  residual_fp64<NT>(a, w, n, P);
   double rmax = 0.0, msol = 0.0, msmp = 0.0, bad = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double ym[4], y0[4], yp[4], r[4];
-    for (int v = 0; v < 4; ++v) {
-      y0[v] = w.y[4 * i + v];
-      ym[v] = (i > 0) ? w.y[4 * (i - 1) + v] : y0[v];
-      yp[v] = (i < n - 1) ? w.y[4 * (i + 1) + v] : y0[v];
-    }
-    local_res<double>(a, i, n, ym, y0, yp, P, r);
-    for (int v = 0; v < 4; ++v) rmax = fmax(rmax, fabs(r[v]));
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const double* y0 = w.y + 4 * i;
+    for (int v = 0; v < 4; ++v) rmax = fmax(rmax, fabs(w.R[4 * i + v]));
     const double rho = (P - a.hot[(size_t)i * 12]) / y0[2];
     if (!(rho > 0.0) || !(y0[2] > 0.0) || !(y0[3] > 0.0) || !isfinite(rho) || !isfinite(y0[0]) || !isfinite(y0[1]))
       bad = 1.0;
     msol += rho;
     msmp += a.F[(size_t)i * 18];
   }
-  rmax = block_max(rmax, red);
-  bad = block_max(bad, red);
-  msol = block_sum(msol, red);
-  msmp = block_sum(msmp, red);
+  rmax = block_max<NT>(rmax, red);
+  bad = block_max<NT>(bad, red);
+  msol = block_sum<NT>(msol, red);
+  msmp = block_sum<NT>(msmp, red);
   if (threadIdx.x == 0) {
     double st = w.sc[SC_STATUS];  // 0 converged, 1 iteration cap, 2 numeric
     if (st != 2.0 && (bad > 0.0 || !(fabs(msol - msmp) <= 1e-6 * msmp))) st = 2.0;
@@ -732,7 +758,7 @@ __global__ void __launch_bounds__(1024) k_synth_final(const __grid_constant__ Sy
   }
   __syncthreads();
   const bool keep = s_status == 2.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = threadIdx.x; i < n; i += NT) {
     double* o = out + (size_t)i * 6;
     if (keep) {
       const double* f = a.F + (size_t)i * 18;
@@ -756,19 +782,19 @@ __global__ void __launch_bounds__(1024) k_synth_final(const __grid_constant__ Sy
 
 // Newton iterations are launched in batches of 4 (a finished slab makes the
 // remaining launches return at once); the host reads the count of finished
-// slabs between batches.
-static void run_synth(const SynthCases& sc, const int32_t* host_nx, double* out, int n_m, double tol,
-                      cudaStream_t st) {
-  k_synth_init<<<sc.ncases, 1024, 0, st>>>(sc);
+// slabs between batches.  One CTA per slab, NT threads: the smallest power
+// of two from 128 to 1024 that covers the largest slab.
+template <int NT>
+static void run_synth_nt(const SynthCases& sc, double* out, int n_m, double tol, cudaStream_t st) {
+  k_synth_init<NT><<<sc.ncases, NT, 0, st>>>(sc);
   const int jt = 128, jb = (sc.ncells * 13 + jt - 1) / jt;
-  (void)host_nx;
   int it = 0;
   while (it < n_m) {
     const int batch = (n_m - it) < 4 ? (n_m - it) : 4;
     cudaMemsetAsync(sc.info + 3 * sc.ncases, 0, sizeof(double), st);
     for (int b = 0; b < batch; ++b) {
       k_synth_jac<<<jb, jt, 0, st>>>(sc);
-      k_synth_solve<<<sc.ncases, 1024, 0, st>>>(sc, n_m, tol, b == batch - 1 ? 1 : 0);
+      k_synth_solve<NT><<<sc.ncases, NT, 0, st>>>(sc, n_m, tol, b == batch - 1 ? 1 : 0);
     }
     it += batch;
     double done = 0.0;
@@ -776,7 +802,17 @@ static void run_synth(const SynthCases& sc, const int32_t* host_nx, double* out,
     cudaStreamSynchronize(st);
     if (done >= (double)sc.ncases) break;
   }
-  k_synth_final<<<sc.ncases, 1024, 0, st>>>(sc, out);
+  k_synth_final<NT><<<sc.ncases, NT, 0, st>>>(sc, out);
+}
+
+static void run_synth(const SynthCases& sc, const int32_t* host_nx, double* out, int n_m, double tol,
+                      cudaStream_t st) {
+  int nmax = 1;
+  for (int c = 0; c < sc.ncases; ++c) nmax = host_nx[c] > nmax ? host_nx[c] : nmax;
+  if (nmax <= 128) run_synth_nt<128>(sc, out, n_m, tol, st);
+  else if (nmax <= 256) run_synth_nt<256>(sc, out, n_m, tol, st);
+  else if (nmax <= 512) run_synth_nt<512>(sc, out, n_m, tol, st);
+  else run_synth_nt<1024>(sc, out, n_m, tol, st);
 }
 
 void launch_synth1d(const CellParams* cp, const int32_t* cell_case, const int32_t* cell0, int ncases, int ncells,
