@@ -19,7 +19,7 @@ from . import build as _build
 
 _lib = None
 
-OR_TAGS = {"init": 1, "wall": 2, "ntc": 3, "coll": 4, "dig_n": 5, "dig_sel": 6, "dig_pos": 7}
+OR_TAGS = {"init": 1, "wall": 2, "ntc": 3, "coll": 4, "dig_n": 5, "dig_sel": 6, "dig_pos": 7, "inj": 8}
 
 
 class OrConfig(ctypes.Structure):
@@ -36,6 +36,9 @@ class OrConfig(ctypes.Structure):
         ("init_u", ctypes.c_double * 3),
         ("collisions", ctypes.c_int32), ("pad0", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("capacity", ctypes.c_int64),
+        ("mesh", ctypes.c_int32), ("pad1", ctypes.c_int32),
+        ("r_in", ctypes.c_double), ("r_out", ctypes.c_double), ("stretch", ctypes.c_double),
+        ("fs_rho", ctypes.c_double), ("fs_t", ctypes.c_double), ("fs_u", ctypes.c_double * 3),
     ]
 
 
@@ -79,6 +82,11 @@ def lib():
         L.or_uniform.restype = ctypes.c_double
         L.or_iround_pub.argtypes = [ctypes.c_double, ctypes.c_double]
         L.or_iround_pub.restype = ctypes.c_int64
+        for name in ("or_inflow_ginf_pub",):
+            getattr(L, name).argtypes = [ctypes.c_double]
+            getattr(L, name).restype = ctypes.c_double
+        L.or_inflow_speed_pub.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.or_inflow_speed_pub.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -91,6 +99,16 @@ def philox_block(c0, c1, c2, c3, k0, k1) -> np.ndarray:
     out = np.zeros(4, np.uint32)
     lib().or_philox(c0, c1, c2, c3, k0, k1, _ptr(out))
     return out
+
+
+def inflow_speed(s: float, u: float) -> float:
+    """Scaled inward normal speed z = v_n / sqrt(2T) of an entering particle
+    whose CDF value is u (speed ratio s of the normal drift)."""
+    return lib().or_inflow_speed_pub(s, u)
+
+
+def inflow_ginf(s: float) -> float:
+    return lib().or_inflow_ginf_pub(s)
 
 
 def uniform(seed, tag, c0, c1, c2, j) -> float:
@@ -118,6 +136,12 @@ def make_config(cfg: dict) -> OrConfig:
     c.collisions = 1 if cfg.get("collisions", True) else 0
     c.seed = int(cfg.get("seed", 0))
     c.capacity = int(cfg.get("capacity", 0) or 0)
+    c.mesh = 1 if cfg.get("mesh", "box") == "annulus" else 0
+    c.r_in, c.r_out = float(cfg.get("r_in", 0.5)), float(cfg.get("r_out", 5.5))
+    c.stretch = float(cfg.get("stretch", 1.0))
+    c.fs_rho, c.fs_t = float(cfg.get("fs_rho", 1.0)), float(cfg.get("fs_t", 1.0))
+    for k in range(3):
+        c.fs_u[k] = float(cfg.get("fs_u", (0.0, 0.0, 0.0))[k])
     return c
 
 
@@ -221,6 +245,19 @@ class OracleSim:
         out = np.zeros(6, np.int64)
         lib().or_get_stats(self._h, _ptr(out))
         return dict(zip(("n_cand", "n_coll", "n_clip", "n_inel", "n_hits", "n_maxhit"), out.tolist()))
+
+    def volumes(self) -> np.ndarray:
+        """Cell volumes (areas per unit depth in 2D)."""
+        out = np.zeros(self.ncells, np.float64)
+        lib().or_get_vol(self._h, _ptr(out))
+        return out
+
+    def flow(self) -> dict:
+        """Particles that entered through the outer circle and that left
+        (annulus)."""
+        out = np.zeros(2, np.int64)
+        lib().or_get_flow(self._h, _ptr(out))
+        return {"n_in": int(out[0]), "n_out": int(out[1])}
 
     def wall_tally(self) -> np.ndarray:
         out = np.zeros((4, 5), np.float64)

@@ -12,7 +12,11 @@
  * and one candidate pair at a time, with no blocking, fusion or reordering:
  *
  *   move + diffuse walls   Sec. 2.2 (free flight, then collisions) and Sec. 4
- *                          ("fully diffuse" gas-surface interaction)
+ *                          ("fully diffuse" gas-surface interaction); for the
+ *                          flow past a cylinder (Sec. 5, annular mesh) the
+ *                          cylinder is a diffuse wall, particles leave through
+ *                          the outer circle and the freestream enters through
+ *                          it with the one-sided flux of a drifting Maxwellian
  *   cell index + sort      implied by the per-cell collisions of Sec. 2.2
  *   NTC / VHS / BL         Sec. 2.2, Eq. (P_inelastic); Sec. 4 gas constants
  *   sampling               Eq. (DSMC_macroscopic), time averaged (Sec. 3 step 2)
@@ -47,6 +51,7 @@
 #define OR_TAG_DIG_N 5u
 #define OR_TAG_DIG_SEL 6u
 #define OR_TAG_DIG_POS 7u
+#define OR_TAG_INJ 8u
 
 #define OR_MAX_HITS 8
 #define OR_NMOM 17
@@ -65,6 +70,14 @@ typedef struct or_config {
   int32_t pad0;
   uint64_t seed;
   int64_t capacity;
+  /* mesh 1: annulus r_in <= r <= r_out around a cylinder, nx angular x ny
+   * radial cells, cell = j nx + k; the radial width grows by the factor
+   * stretch from ring to ring; wall 0 is the cylinder; the freestream
+   * (fs_rho, fs_t, fs_u) enters through the outer circle */
+  int32_t mesh;
+  int32_t pad1;
+  double r_in, r_out, stretch;
+  double fs_rho, fs_t, fs_u[3];
 } or_config;
 
 typedef struct or_state {
@@ -84,6 +97,11 @@ typedef struct or_state {
   double dx, dy, vcell, fnum, mu_ref, k_visc, c_sigma, p_inel;
   int64_t n_cand, n_coll, n_clip, n_inel, n_hits, n_maxhit;
   double wall_tally[4][5];
+  double *vol;      /* ncells cell volumes (areas per unit depth in 2D) */
+  double *rt, *r2t; /* annulus: ny + 1 ring radii and their squares */
+  double *rc, *rs;  /* annulus: nx + 1 rays (cos, sin of 2 pi k / nx) */
+  double *fc, *fs;  /* annulus: nx outer-face centre directions */
+  int64_t n_inj, n_out;
 } or_state;
 
 /* ------------------------------------------------------------------------ */
@@ -172,14 +190,54 @@ int64_t or_iround_pub(double x, double u) { return or_iround(x, u); }
  * distribution at temperature T is (4T)^{k/2} (2/sqrt(pi)) Gamma((k+3)/2),
  * so sigma g = C_sigma g^{2-2w} with the C_sigma below reproduces nu at
  * rho = T = 1. */
+/* Annulus geometry: ring radii R_j = r_in + (r_out - r_in) (q^j - 1) / (q^ny
+ * - 1) (q = stretch; uniform for q = 1), rays at 2 pi k / nx, cell volume
+ * (pi / nx) (R_{j+1}^2 - R_j^2). */
+static void or_annulus_tables(or_state *S) {
+  const or_config *c = &S->c;
+  int nr = c->ny, nt = c->nx;
+  double q = c->stretch;
+  for (int j = 0; j <= nr; ++j) {
+    double f = (q == 1.0) ? (double)j / (double)nr : (pow(q, (double)j) - 1.0) / (pow(q, (double)nr) - 1.0);
+    S->rt[j] = c->r_in + (c->r_out - c->r_in) * f;
+  }
+  S->rt[0] = c->r_in;
+  S->rt[nr] = c->r_out;
+  for (int j = 0; j <= nr; ++j) S->r2t[j] = S->rt[j] * S->rt[j];
+  for (int k = 0; k < nt; ++k) {
+    double th = 2.0 * M_PI * (double)k / (double)nt;
+    S->rc[k] = cos(th);
+    S->rs[k] = sin(th);
+    double tm = 2.0 * M_PI * ((double)k + 0.5) / (double)nt;
+    S->fc[k] = cos(tm);
+    S->fs[k] = sin(tm);
+  }
+  S->rc[nt] = S->rc[0];
+  S->rs[nt] = S->rs[0];
+  double half = M_PI / (double)nt;
+  for (int j = 0; j < nr; ++j)
+    for (int k = 0; k < nt; ++k) S->vol[j * nt + k] = half * (S->r2t[j + 1] - S->r2t[j]);
+}
+
 static void or_constants_compute(or_state *S) {
   const or_config *c = &S->c;
   double w = c->omega, a = c->alpha;
-  S->dx = c->lx / (double)c->nx;
-  S->dy = (c->dim == 2) ? c->ly / (double)c->ny : 1.0;
-  S->vcell = S->dx * S->dy;
-  /* particle weight F = rho V / N_p (Eq. DSMC_macroscopic); a state created
-   * empty is weighted as if it had one particle per cell */
+  if (c->mesh == 1) {
+    or_annulus_tables(S);
+    S->dx = 2.0 * M_PI / (double)c->nx;
+    S->dy = (c->r_out - c->r_in) / (double)c->ny;
+    double area = 0.0;
+    for (int i = 0; i < S->ncells; ++i) area += S->vol[i];
+    S->vcell = area / (double)S->ncells;
+  } else {
+    S->dx = c->lx / (double)c->nx;
+    S->dy = (c->dim == 2) ? c->ly / (double)c->ny : 1.0;
+    S->vcell = S->dx * S->dy;
+    for (int i = 0; i < S->ncells; ++i) S->vol[i] = S->vcell;
+  }
+  /* particle weight F = rho V / N_p (Eq. DSMC_macroscopic) with the mean cell
+   * volume; a state created empty is weighted as if it had one particle per
+   * cell */
   S->fnum = c->init_rho * S->vcell / (double)(c->ppc > 0 ? c->ppc : 1);
   S->mu_ref = c->kn * sqrt(2.0 / M_PI);
   S->k_visc = 5.0 * (a + 1.0) * (a + 2.0) / (a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w));
@@ -200,8 +258,37 @@ void or_constants(const or_state *S, double out[8]) {
   out[7] = S->p_inel;
 }
 
+/* Annulus: ring j is the largest with R_j^2 <= r^2 (the first ring below
+ * r_in, which rounding can give); sector k holds the points with
+ * cross(ray_k, p) >= 0 > cross(ray_{k+1}, p), found from the atan2 guess by
+ * those two signs; -1 outside r_out (the particle has left). */
+static int or_cell_of_annulus(const or_state *S, double x, double y) {
+  const or_config *c = &S->c;
+  int nr = c->ny, nt = c->nx;
+  double r2 = x * x + y * y;
+  if (!(r2 < S->r2t[nr])) return -1;
+  int lo = 0, hi = nr - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) / 2;
+    if (S->r2t[mid] <= r2) lo = mid;
+    else hi = mid - 1;
+  }
+  double th = atan2(y, x);
+  if (th < 0.0) th += 2.0 * M_PI;
+  int k = (int)(th * ((double)nt / (2.0 * M_PI)));
+  if (k < 0) k = 0;
+  if (k > nt - 1) k = nt - 1;
+  for (int it = 0; it < 4; ++it) {
+    if (S->rc[k] * y - S->rs[k] * x < 0.0) k = (k == 0) ? nt - 1 : k - 1;
+    else if (S->rc[k + 1] * y - S->rs[k + 1] * x >= 0.0) k = (k == nt - 1) ? 0 : k + 1;
+    else break;
+  }
+  return lo * nt + k;
+}
+
 static int or_cell_of(const or_state *S, double x, double y) {
   const or_config *c = &S->c;
+  if (c->mesh == 1) return or_cell_of_annulus(S, x, y);
   int ix = (int)(x * ((double)c->nx / c->lx));
   if (ix < 0) ix = 0;
   if (ix > c->nx - 1) ix = c->nx - 1;
@@ -230,6 +317,14 @@ static int or_alloc(or_state *S, int64_t cap) {
   S->sgmax = (double *)calloc((size_t)S->ncells, sizeof(double));
   S->acc = (double *)calloc((size_t)S->ncells * OR_NMOM, sizeof(double));
   if (!S->key || !S->cell || !S->start || !S->cnt || !S->sgmax || !S->acc) return OR_ERR_CAPACITY;
+  S->vol = (double *)calloc((size_t)S->ncells, sizeof(double));
+  S->rt = (double *)calloc((size_t)S->c.ny + 1, sizeof(double));
+  S->r2t = (double *)calloc((size_t)S->c.ny + 1, sizeof(double));
+  S->rc = (double *)calloc((size_t)S->c.nx + 1, sizeof(double));
+  S->rs = (double *)calloc((size_t)S->c.nx + 1, sizeof(double));
+  S->fc = (double *)calloc((size_t)S->c.nx, sizeof(double));
+  S->fs = (double *)calloc((size_t)S->c.nx, sizeof(double));
+  if (!S->vol || !S->rt || !S->r2t || !S->rc || !S->rs || !S->fc || !S->fs) return OR_ERR_CAPACITY;
   return OR_OK;
 }
 
@@ -244,6 +339,13 @@ void or_destroy(or_state *S) {
   free(S->cnt);
   free(S->sgmax);
   free(S->acc);
+  free(S->vol);
+  free(S->rt);
+  free(S->r2t);
+  free(S->rc);
+  free(S->rs);
+  free(S->fc);
+  free(S->fs);
   free(S);
 }
 
@@ -264,6 +366,10 @@ int or_create(const or_config *cfg, or_state **out) {
   if (cfg->dim != 1 && cfg->dim != 2) return OR_ERR_ARG;
   if (cfg->nx <= 0 || (cfg->dim == 2 && cfg->ny <= 0) || cfg->ppc < 0) return OR_ERR_ARG;
   if (cfg->d_r != 2.0 || cfg->alpha != 1.0) return OR_ERR_ARG;
+  if (cfg->mesh != 0 && cfg->mesh != 1) return OR_ERR_ARG;
+  if (cfg->mesh == 1 && (cfg->dim != 2 || cfg->nx < 3 || !(cfg->r_in > 0.0) || !(cfg->r_out > cfg->r_in) ||
+                         !(cfg->stretch > 0.0) || !(cfg->fs_t > 0.0) || !(cfg->fs_rho >= 0.0)))
+    return OR_ERR_ARG;
   or_state *S = (or_state *)calloc(1, sizeof(or_state));
   if (!S) return OR_ERR_CAPACITY;
   S->c = *cfg;
@@ -274,7 +380,7 @@ int or_create(const or_config *cfg, or_state **out) {
   S->ncells = S->c.nx * S->c.ny;
   int64_t n0 = (int64_t)S->ncells * (int64_t)S->c.ppc;
   int64_t cap = S->c.capacity > 0 ? S->c.capacity : n0 * 2 + 64;
-  if (n0 > cap) {
+  if (S->c.mesh == 0 && n0 > cap) {
     free(S);
     return OR_ERR_CAPACITY;
   }
@@ -290,7 +396,18 @@ int or_create(const or_config *cfg, or_state **out) {
   for (int cell = 0; cell < S->ncells; ++cell) {
     int ix = cell % c->nx, iy = cell / c->nx;
     S->start[cell] = s;
-    for (int k = 0; k < c->ppc; ++k, ++s) {
+    int64_t np = c->ppc;
+    if (c->mesh == 1) {
+      /* annulus: the equilibrium density in cells of unequal volume */
+      or_stream sc;
+      or_stream_init(&sc, c->seed, OR_TAG_INIT, 0xFFFFFFFFu, (uint32_t)cell, 0u);
+      np = or_iround(c->init_rho * S->vol[cell] / S->fnum, or_uni(&sc, 0));
+      if (s + np > cap) {
+        or_destroy(S);
+        return OR_ERR_CAPACITY;
+      }
+    }
+    for (int k = 0; k < np; ++k, ++s) {
       or_stream st;
       or_stream_init(&st, c->seed, OR_TAG_INIT, (uint32_t)k, (uint32_t)cell, 0u);
       double u0 = or_uni(&st, 0), u1 = or_uni(&st, 1);
@@ -298,8 +415,16 @@ int or_create(const or_config *cfg, or_state **out) {
       or_box_muller(or_uni(&st, 2), or_uni(&st, 3), &n1, &n2);
       or_box_muller(or_uni(&st, 4), or_uni(&st, 5), &n3, &n4);
       (void)n4;
-      S->x[s] = ((double)ix + u0) * S->dx;
-      S->y[s] = (c->dim == 2) ? ((double)iy + u1) * S->dy : 0.0;
+      if (c->mesh == 1) {
+        /* uniform in the annular sector: r^2 uniform, angle uniform */
+        double r = sqrt(S->r2t[iy] + u0 * (S->r2t[iy + 1] - S->r2t[iy]));
+        double th = 2.0 * M_PI * ((double)ix + u1) / (double)c->nx;
+        S->x[s] = r * cos(th);
+        S->y[s] = r * sin(th);
+      } else {
+        S->x[s] = ((double)ix + u0) * S->dx;
+        S->y[s] = (c->dim == 2) ? ((double)iy + u1) * S->dy : 0.0;
+      }
       S->vx[s] = c->init_u[0] + stt * n1;
       S->vy[s] = c->init_u[1] + stt * n2;
       S->vz[s] = c->init_u[2] + stt * n3;
@@ -313,7 +438,7 @@ int or_create(const or_config *cfg, or_state **out) {
   double tref = c->init_tt, uref = sqrt(c->init_u[0] * c->init_u[0] + c->init_u[1] * c->init_u[1] +
                                         c->init_u[2] * c->init_u[2]);
   double umax = 0.0;
-  int nwalls = 2 * c->dim;
+  int nwalls = (c->mesh == 1) ? 1 : 2 * c->dim;
   for (int w = 0; w < nwalls; ++w) {
     if (c->wall_kind[w] == 0 && c->wall_t[w] > tref) tref = c->wall_t[w];
     double uw = sqrt(c->wall_u[w][0] * c->wall_u[w][0] + c->wall_u[w][1] * c->wall_u[w][1] +
@@ -374,8 +499,201 @@ static void or_wall_emit(or_state *S, int w, or_stream *st, int hit, double v[3]
   S->n_hits += 1;
 }
 
+/* Re-emission from the cylinder (wall 0 of the annulus) at the surface point
+ * with outward unit normal (nx, ny): diffuse at T_w about a resting wall
+ * (normal speed sqrt(-2 T_w ln u), Maxwellian tangential and z components,
+ * I_r drawn at T_w) or specular (normal component reversed). */
+static void or_cyl_emit(or_state *S, or_stream *st, uint32_t j0, double nx, double ny, double v[3], double *ir) {
+  const or_config *c = &S->c;
+  double vin[3] = {v[0], v[1], v[2]}, irin = *ir;
+  if (c->wall_kind[0] == 1) {
+    double vn = v[0] * nx + v[1] * ny;
+    v[0] = v[0] - 2.0 * vn * nx;
+    v[1] = v[1] - 2.0 * vn * ny;
+  } else {
+    double T = c->wall_t[0];
+    double ua = or_uni(st, j0 + 0u), ub = or_uni(st, j0 + 1u), uc = or_uni(st, j0 + 2u), ud = or_uni(st, j0 + 3u);
+    double vn = sqrt(-2.0 * T * log(ua));
+    double n1, n2;
+    or_box_muller(ub, uc, &n1, &n2);
+    double sT = sqrt(T);
+    double vt = sT * n1;
+    v[0] = vn * nx - vt * ny;
+    v[1] = vn * ny + vt * nx;
+    v[2] = sT * n2;
+    *ir = -T * log(ud);
+  }
+  double *t = S->wall_tally[0];
+  t[0] += 1.0;
+  t[1] += vin[0] - v[0];
+  t[2] += vin[1] - v[1];
+  t[3] += vin[2] - v[2];
+  t[4] += (0.5 * (vin[0] * vin[0] + vin[1] * vin[1] + vin[2] * vin[2]) + irin) -
+          (0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) + *ir);
+  S->n_hits += 1;
+}
+
+/* Free flight for time t in the annulus.  The first crossing of the cylinder
+ * r = r_in along the straight path p + v s is the smaller root of
+ * |p + v s|^2 = r_in^2 (taken when the particle moves inward); the particle
+ * is put on the circle, re-emitted and flies the rest of the step (a path
+ * leaving a convex body does not meet it again).  Hit h draws uniforms
+ * j0 + 4h .. j0 + 4h + 3 of the stream.  Returns 0 if the particle ends at or
+ * beyond r_out (it has left the domain). */
+static int or_fly_annulus(or_state *S, or_stream *st, uint32_t j0, double *px, double *py, double v[3], double *ir,
+                          double t) {
+  double x = *px, y = *py;
+  int hits = 0;
+  for (;;) {
+    double a = v[0] * v[0] + v[1] * v[1];
+    double b = x * v[0] + y * v[1];
+    double s1 = INFINITY;
+    if (b < 0.0 && a > 0.0) {
+      double cc = x * x + y * y - S->r2t[0];
+      double disc = b * b - a * cc;
+      if (disc > 0.0) {
+        s1 = (-b - sqrt(disc)) / a;
+        if (s1 < 0.0) s1 = 0.0;
+      }
+    }
+    if (!(s1 < t)) {
+      x = x + v[0] * t;
+      y = y + v[1] * t;
+      break;
+    }
+    double xh = x + v[0] * s1, yh = y + v[1] * s1;
+    double rh = sqrt(xh * xh + yh * yh);
+    double nx = xh / rh, ny = yh / rh;
+    x = S->rt[0] * nx;
+    y = S->rt[0] * ny;
+    if (hits == OR_MAX_HITS) {
+      S->n_maxhit += 1;
+      break;
+    }
+    t = t - s1;
+    if (t < 0.0) t = 0.0;
+    or_cyl_emit(S, st, j0 + 4u * (uint32_t)hits, nx, ny, v, ir);
+    hits += 1;
+  }
+  *px = x;
+  *py = y;
+  return (x * x + y * y < S->r2t[S->c.ny]) ? 1 : 0;
+}
+
+/* One-sided number flux (per unit length and time) of a Maxwellian of
+ * density rho, temperature T and velocity component un along the inward
+ * normal: rho sqrt(T/(2 pi)) [exp(-s^2) + sqrt(pi) s erfc(-s)], s = un /
+ * sqrt(2T), written as rho G(inf) / (beta sqrt(pi)) with beta = 1/sqrt(2T). */
+static double or_inflow_ginf(double s) { return 0.5 * exp(-s * s) + s * (0.5 * sqrt(M_PI)) * erfc(-s); }
+
+/* Inward normal speed of an entering particle, in units of 1/beta: the
+ * density of z = beta v_n > 0 is proportional to z exp(-(z - s)^2), with
+ * CDF G(z) = [exp(-s^2) - exp(-(z-s)^2)] / 2 + s (sqrt(pi)/2) [erfc(-s) -
+ * erfc(z - s)]; G(z) = u G(inf) is solved by Newton steps kept inside a
+ * bisection bracket (at most 100 steps). */
+static double or_inflow_speed(double s, double u) {
+  double target = u * or_inflow_ginf(s);
+  double lo = 0.0, hi = (s > 0.0 ? s : 0.0) + 8.0;
+  double z = 0.5 * (lo + hi);
+  for (int it = 0; it < 100; ++it) {
+    double w = z - s;
+    double g = 0.5 * (exp(-s * s) - exp(-w * w)) + s * (0.5 * sqrt(M_PI)) * (erfc(-s) - erfc(w));
+    double f = g - target;
+    if (f > 0.0) hi = z;
+    else lo = z;
+    double d = z * exp(-w * w);
+    double zn = (d > 0.0) ? z - f / d : 0.5 * (lo + hi);
+    if (!(zn > lo && zn < hi)) zn = 0.5 * (lo + hi);
+    if (fabs(zn - z) <= 1e-15 * (1.0 + z) || hi - lo <= 1e-15 * (1.0 + z)) {
+      z = zn;
+      break;
+    }
+    z = zn;
+  }
+  return z;
+}
+
+/* Freestream entry through the outer circle during one step.  Outer face k
+ * (between rays k and k+1 at r_out) admits Iround(flux L dt / F) particles,
+ * the flux taken with the face-centre inward normal n and L = r_out 2 pi /
+ * nx.  Particle q of face k (stream (q, k, step)): normal speed from the
+ * inflow distribution, tangential and z components Maxwellian about the
+ * freestream, I_r at the freestream temperature, the entry angle uniform on
+ * the face, and a flight over a uniform fraction of the step.  New
+ * particles follow the existing ones, face by face. */
+static void or_inject(or_state *S) {
+  const or_config *c = &S->c;
+  int nt = c->nx;
+  double T = c->fs_t, sT = sqrt(T), beta = 1.0 / sqrt(2.0 * T);
+  double len = c->r_out * 2.0 * M_PI / (double)nt;
+  for (int k = 0; k < nt; ++k) {
+    double nx = -S->fc[k], ny = -S->fs[k]; /* inward normal */
+    double tx = -ny, ty = nx;
+    double un = c->fs_u[0] * nx + c->fs_u[1] * ny, ut = c->fs_u[0] * tx + c->fs_u[1] * ty;
+    double sn = un * beta;
+    double mu = c->fs_rho * or_inflow_ginf(sn) / (beta * sqrt(M_PI)) * len * c->dt / S->fnum;
+    or_stream sc;
+    or_stream_init(&sc, c->seed, OR_TAG_INJ, 0xFFFFFFFFu, (uint32_t)k, S->step);
+    int64_t m = or_iround(mu, or_uni(&sc, 0));
+    for (int64_t q = 0; q < m; ++q) {
+      or_stream st;
+      or_stream_init(&st, c->seed, OR_TAG_INJ, (uint32_t)q, (uint32_t)k, S->step);
+      double vn = or_inflow_speed(sn, or_uni(&st, 0)) / beta;
+      double n1, n2;
+      or_box_muller(or_uni(&st, 1), or_uni(&st, 2), &n1, &n2);
+      double vt = ut + sT * n1;
+      double v[3] = {vn * nx + vt * tx, vn * ny + vt * ty, c->fs_u[2] + sT * n2};
+      double th = 2.0 * M_PI * ((double)k + or_uni(&st, 3)) / (double)nt;
+      double ir = -T * log(or_uni(&st, 4));
+      double x = c->r_out * cos(th), y = c->r_out * sin(th);
+      int in = or_fly_annulus(S, &st, 8u, &x, &y, v, &ir, or_uni(&st, 5) * c->dt);
+      if (!in || S->n >= S->cap) {
+        S->n_out += 1;
+        continue;
+      }
+      int64_t s = S->n++;
+      S->x[s] = x;
+      S->y[s] = y;
+      S->vx[s] = v[0];
+      S->vy[s] = v[1];
+      S->vz[s] = v[2];
+      S->ir[s] = ir;
+      S->key[s] = or_cell_of(S, x, y);
+      S->n_inj += 1;
+    }
+  }
+}
+
+/* exported for the tests of the inflow sampler */
+double or_inflow_ginf_pub(double s) { return or_inflow_ginf(s); }
+double or_inflow_speed_pub(double s, double u) { return or_inflow_speed(s, u); }
+
 void or_move(or_state *S) {
   const or_config *c = &S->c;
+  if (c->mesh == 1) {
+    /* annulus: particles in slot order, each with its cell's wall stream;
+     * leavers get key -1 and the sort drops them; then the freestream entry */
+    for (int cell = 0; cell < S->ncells; ++cell) {
+      for (int64_t s = S->start[cell]; s < S->start[cell + 1]; ++s) {
+        or_stream st;
+        or_stream_init(&st, c->seed, OR_TAG_WALL, (uint32_t)(s - S->start[cell]), (uint32_t)cell, S->step);
+        double x = S->x[s], y = S->y[s];
+        double v[3] = {S->vx[s], S->vy[s], S->vz[s]};
+        double ir = S->ir[s];
+        int in = or_fly_annulus(S, &st, 0u, &x, &y, v, &ir, c->dt);
+        S->x[s] = x;
+        S->y[s] = y;
+        S->vx[s] = v[0];
+        S->vy[s] = v[1];
+        S->vz[s] = v[2];
+        S->ir[s] = ir;
+        S->key[s] = in ? or_cell_of(S, x, y) : -1;
+        if (!in) S->n_out += 1;
+      }
+    }
+    or_inject(S);
+    return;
+  }
   for (int cell = 0; cell < S->ncells; ++cell) {
     for (int64_t s = S->start[cell]; s < S->start[cell + 1]; ++s) {
       or_stream st;
@@ -460,7 +778,8 @@ void or_move(or_state *S) {
 void or_sort(or_state *S) {
   int nc = S->ncells;
   for (int i = 0; i <= nc; ++i) S->cnt[i] = 0;
-  for (int64_t s = 0; s < S->n; ++s) S->cnt[S->key[s]] += 1;
+  for (int64_t s = 0; s < S->n; ++s)
+    if (S->key[s] >= 0) S->cnt[S->key[s]] += 1;
   int64_t acc = 0;
   for (int i = 0; i < nc; ++i) {
     S->start[i] = acc;
@@ -470,6 +789,7 @@ void or_sort(or_state *S) {
   S->start[nc] = acc;
   for (int64_t s = 0; s < S->n; ++s) {
     int k = S->key[s];
+    if (k < 0) continue; /* left the domain */
     int64_t d = S->cnt[k]++;
     S->tx[d] = S->x[s];
     S->ty[d] = S->y[s];
@@ -486,6 +806,7 @@ void or_sort(or_state *S) {
   t = S->vy; S->vy = S->tvy; S->tvy = t;
   t = S->vz; S->vz = S->tvz; S->tvz = t;
   t = S->ir; S->ir = S->tir; S->tir = t;
+  S->n = acc;
   for (int64_t s = 0; s < S->n; ++s) S->key[s] = S->cell[s];
 }
 
@@ -510,7 +831,7 @@ static void or_collide_cell(or_state *S, int cell) {
   int64_t n = S->start[cell + 1] - s0;
   if (!c->collisions || n < 2) return;
   double sgmax = S->sgmax[cell];
-  double xm = 0.5 * (double)n * (double)(n - 1) * S->fnum * sgmax * c->dt / S->vcell;
+  double xm = 0.5 * (double)n * (double)(n - 1) * S->fnum * sgmax * c->dt / S->vol[cell];
   or_stream sn;
   or_stream_init(&sn, c->seed, OR_TAG_NTC, 0u, (uint32_t)cell, S->step);
   int64_t m = or_iround(xm, or_uni(&sn, 0));
@@ -625,6 +946,7 @@ void or_step(or_state *S, int nsteps, int sample) {
 int or_dig_correct(or_state *S, const double *target) {
   const or_config *c = &S->c;
   int nc = S->ncells;
+  if (c->mesh != 0) return OR_ERR_ARG;
   for (int cell = 0; cell < nc; ++cell) {
     const double *t = target + (size_t)cell * 6;
     for (int q = 0; q < 6; ++q)
@@ -843,6 +1165,15 @@ void or_get_stats(const or_state *S, int64_t out[6]) {
   out[3] = S->n_inel;
   out[4] = S->n_hits;
   out[5] = S->n_maxhit;
+}
+
+/* cell volumes */
+void or_get_vol(const or_state *S, double *out) { memcpy(out, S->vol, sizeof(double) * (size_t)S->ncells); }
+
+/* particles that entered (annulus freestream) and that left */
+void or_get_flow(const or_state *S, int64_t out[2]) {
+  out[0] = S->n_inj;
+  out[1] = S->n_out;
 }
 
 /* per wall: hits, momentum delivered (3), energy delivered */

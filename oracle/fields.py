@@ -17,7 +17,7 @@ F_RHO, F_U, F_TT, F_TR, F_SIG, F_QT, F_QR = 0, 1, 4, 5, 6, 12, 15
 SIG_IJ = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
 
 
-def fields_from_sums(acc: np.ndarray, nsamples: int, fnum: float, vcell: float, d_r: float) -> np.ndarray:
+def fields_from_sums(acc: np.ndarray, nsamples: int, fnum: float, vcell, d_r: float) -> np.ndarray:
     """Eq. (DSMC_macroscopic), time averaged over ``nsamples`` steps.
 
     The raw sums over all sampled steps are combined into central moments about
@@ -48,8 +48,9 @@ def fields_from_sums(acc: np.ndarray, nsamples: int, fnum: float, vcell: float, 
         sv2 = float(np.trace(svv))
         sc3 = (sv3 - 2.0 * (svv @ u) + u2 * sv
                - u * sv2 + 2.0 * u * float(u @ sv) - N * u * u2)
-        n_over_v = fnum / (vcell * S)
-        out[c, F_RHO] = fnum * N / (S * vcell)
+        vc = float(vcell[c]) if np.ndim(vcell) else vcell  # per-cell volumes (annulus)
+        n_over_v = fnum / (vc * S)
+        out[c, F_RHO] = fnum * N / (S * vc)
         out[c, F_U:F_U + 3] = u
         out[c, F_TT] = sc2 / (3.0 * N)
         out[c, F_TR] = 2.0 * si / (d_r * N)

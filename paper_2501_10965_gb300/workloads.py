@@ -49,6 +49,13 @@ def base_config(**kw) -> dict:
         "kn_ref": 0.01,
         "synth_tol": 1e-5,
         "bin_slack": 2.0,
+        # mesh "box": the Cartesian box above; "annulus": r_in <= r <= r_out
+        # around a cylinder (nx angular x ny radial cells, radial widths
+        # growing by `stretch` per ring), wall 0 the cylinder, freestream
+        # (fs_rho, fs_t, fs_u) entering through the outer circle
+        "mesh": "box",
+        "r_in": 0.5, "r_out": 5.5, "stretch": 1.0,
+        "fs_rho": 1.0, "fs_t": 1.0, "fs_u": (0.0, 0.0, 0.0),
     }
     cfg.update(kw)
     return cfg
@@ -101,6 +108,49 @@ def cavity_2d_20m(**kw) -> dict:
     ~167 particles per cell, 20.0 M particles, Kn 0.01, FP32): a 4:3 cavity
     with square cells and a 50 m/s lid."""
     cfg = cavity_2d(nx=400, ny=300, ppc=167, kn=0.01, lx=4.0 / 3.0, ly=1.0)
+    cfg.update(kw)
+    return cfg
+
+
+def radial_stretch(dr1: float, nr: int, span: float) -> float:
+    """Ratio q > 1 of consecutive radial widths with first width dr1 and nr
+    rings spanning `span`: dr1 (q^nr - 1) / (q - 1) = span (bisection)."""
+    if dr1 * nr >= span:
+        return 1.0
+    lo, hi = 1.0 + 1e-12, 2.0
+    for _ in range(200):
+        q = 0.5 * (lo + hi)
+        if dr1 * (q ** nr - 1.0) / (q - 1.0) > span:
+            hi = q
+        else:
+            lo = q
+    return 0.5 * (lo + hi)
+
+
+def cylinder_2d(ntheta: int = 400, nr: int = 300, ppc: int = 167, kn: float = 0.01, mach: float = 5.0,
+                t_wall: float = 2.5, r_in: float = 0.5, r_out: float = 5.5, dr1: float | None = None,
+                **kw) -> dict:
+    """Hypersonic flow past a cylinder of diameter 1 (L0): Mach 5 N2-like
+    freestream at 200 K (the temperature unit here), diffuse cylinder wall at
+    500 K, annular mesh r in [0.5, 5.5] of ntheta x nr cells whose radial
+    widths grow geometrically from dr1 (default 0.2 of the freestream mean
+    free path, Kn L0), ~ppc particles per cell on average, FP32.  The gas
+    starts as the uniform freestream; the freestream enters through the outer
+    circle and particles leave through it."""
+    gamma = 7.0 / 5.0
+    u_inf = mach * math.sqrt(gamma * 1.0)
+    dr1 = 0.2 * kn if dr1 is None else dr1
+    q = radial_stretch(dr1, nr, r_out - r_in)
+    dr_min = dr1 if q > 1.0 else (r_out - r_in) / nr
+    dx_min = min(dr_min, r_in * 2.0 * math.pi / ntheta)
+    t_max = max(1.0, t_wall)
+    tau = kn * math.sqrt(math.pi / 8.0)
+    dt = min(0.3 * dx_min / (u_inf + 3.0 * math.sqrt(t_max)), 0.5 * tau)
+    cfg = base_config(dim=2, nx=ntheta, ny=nr, ppc=ppc, kn=kn, z_rot=5.0, mesh="annulus",
+                      lx=2.0 * math.pi, ly=r_out - r_in, r_in=r_in, r_out=r_out, stretch=q,
+                      walls=[_wall(T=t_wall), _wall(), _wall(), _wall()],
+                      init_u=(u_inf, 0.0, 0.0), fs_rho=1.0, fs_t=1.0, fs_u=(u_inf, 0.0, 0.0),
+                      precision="fp32", dt=dt, kn_ref=0.05, n_s=100)
     cfg.update(kw)
     return cfg
 

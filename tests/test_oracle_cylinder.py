@@ -1,0 +1,179 @@
+"""Pins of the oracle's flow past a cylinder (annular mesh, Sec. 5).
+
+Each test checks the oracle against something it does not compute itself:
+
+* the mesh: cell volumes sum to the annulus area, and cells found by brute
+  force from (r, theta) of random points;
+* the inflow sampler: the inverse of the entering particles' normal-speed
+  CDF against numerical quadrature of the density z exp(-(z - s)^2);
+* the freestream entry: the number of particles entering per step against
+  the one-sided flux of a drifting Maxwellian;
+* a gas at rest around a cylinder at the gas temperature stays uniform
+  (detailed balance of entry, exit and diffuse re-emission);
+* free-molecular drag and hit rate on the cylinder against the integral of
+  the freestream's one-sided momentum and number fluxes over its surface
+  (truncated-normal moments), with diffuse re-emission at T_w.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.fields import fields_from_sums
+from paper_2501_10965_gb300 import workloads as W
+
+
+def _cfg(**kw):
+    base = dict(ntheta=24, nr=8, ppc=40, kn=0.1, r_in=0.5, r_out=2.5, dr1=0.25, precision="fp64")
+    base.update(kw)
+    return W.cylinder_2d(**base)
+
+
+def _ring_radii(cfg):
+    nr, q = int(cfg["ny"]), float(cfg["stretch"])
+    j = np.arange(nr + 1)
+    f = j / nr if q == 1.0 else (q ** j - 1.0) / (q ** nr - 1.0)
+    return cfg["r_in"] + (cfg["r_out"] - cfg["r_in"]) * f
+
+
+def test_annulus_volumes_and_cells():
+    cfg = _cfg(dr1=0.05)  # stretched rings
+    assert cfg["stretch"] > 1.05
+    nt, nr = int(cfg["nx"]), int(cfg["ny"])
+    o = oracle.OracleSim(cfg)
+    v = o.volumes()
+    assert math.isclose(v.sum(), math.pi * (2.5 ** 2 - 0.5 ** 2), rel_tol=1e-12)
+    R = _ring_radii(cfg)
+    assert math.isclose(R[1] - R[0], 0.05, rel_tol=1e-9)
+    np.testing.assert_allclose(v.reshape(nr, nt), np.repeat((np.pi / nt) * np.diff(R ** 2)[:, None], nt, 1),
+                               rtol=1e-12)
+    rng = np.random.default_rng(0)
+    n = 6000
+    r = np.sqrt(rng.uniform(0.5 ** 2, 2.5 ** 2, n))
+    th = rng.uniform(0.0, 2.0 * np.pi, n)
+    j = np.searchsorted(R, r, side="right") - 1
+    k = np.floor(th / (2.0 * np.pi / nt)).astype(int)
+    # keep points clear of the cell boundaries (rounding decides there)
+    far = (np.min(np.abs(r[:, None] - R[None, :]), axis=1) > 1e-9) & \
+          (np.abs(th / (2 * np.pi / nt) - np.round(th / (2 * np.pi / nt))) > 1e-9)
+    r, th, j, k = r[far], th[far], j[far], k[far]
+    m = len(r)
+    # two points outside the outer circle leave at once
+    x = np.concatenate([r * np.cos(th), [2.6, 0.0]])
+    y = np.concatenate([r * np.sin(th), [0.0, -3.0]])
+    ids = np.arange(m + 2, dtype=np.float64)
+    o.set_particles({"x": x, "y": y, "vx": ids, "vy": np.zeros(m + 2), "vz": np.zeros(m + 2),
+                     "ir": np.ones(m + 2)})
+    p = o.particles()
+    assert len(p["x"]) == m
+    got = p["cell"][np.argsort(p["vx"])]
+    np.testing.assert_array_equal(got, j * nt + k)
+
+
+@pytest.mark.parametrize("s", [-3.0, -1.0, 0.0, 0.7, 2.0, 4.2])
+def test_inflow_speed_sampler_inverts_the_flux_cdf(s):
+    z = np.linspace(0.0, max(s, 0.0) + 10.0, 400001)
+    dens = z * np.exp(-(z - s) ** 2)
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (dens[1:] + dens[:-1]) * np.diff(z))])
+    total = cdf[-1]
+    assert math.isclose(oracle.inflow_ginf(s), total, rel_tol=1e-7)
+    cdf /= total
+    for u in (0.001, 0.1, 0.37, 0.5, 0.9, 0.999):
+        zs = oracle.inflow_speed(s, u)
+        ze = float(np.interp(u, cdf, z))
+        assert abs(zs - ze) <= 2e-5 * (1.0 + ze), (s, u, zs, ze)
+
+
+def test_entry_count_is_the_one_sided_flux():
+    cfg = _cfg(ntheta=48, nr=4, ppc=10, mach=2.0, collisions=False)
+    o = oracle.OracleSim(cfg)
+    c = o.constants()
+    steps = 2000
+    o.step(steps)
+    nt, U, dt = 48, cfg["fs_u"][0], cfg["dt"]
+    th = 2.0 * np.pi * (np.arange(nt) + 0.5) / nt
+    un = -U * np.cos(th)  # freestream along x, inward normal -(cos, sin)
+    s = un / math.sqrt(2.0)
+    erfc = np.vectorize(math.erfc)
+    flux = math.sqrt(1.0 / (2.0 * math.pi)) * (np.exp(-s * s) + math.sqrt(math.pi) * s * erfc(-s))
+    mu = flux * (2.5 * 2.0 * np.pi / nt) * dt / c["fnum"]
+    expect = steps * mu.sum()
+    frac = mu - np.floor(mu)
+    sd = math.sqrt(steps * float((frac * (1.0 - frac)).sum()))
+    got = o.flow()["n_in"]
+    assert abs(got - expect) <= 4.0 * sd + 0.002 * expect, (got, expect, sd)
+
+
+def _ring_density(o, cfg, nsamples):
+    nt, nr = int(cfg["nx"]), int(cfg["ny"])
+    acc = o.accumulators()
+    c = o.constants()
+    N = acc[:, 0].reshape(nr, nt).sum(1)
+    area = o.volumes().reshape(nr, nt).sum(1)
+    return N * c["fnum"] / (nsamples * area)
+
+
+def test_gas_at_rest_around_a_cylinder_at_its_temperature_stays_uniform():
+    cfg = _cfg(ntheta=48, nr=6, ppc=40, mach=0.0, t_wall=1.0, kn=0.1)
+    o = oracle.OracleSim(cfg)
+    n0 = o.n
+    o.step(200)
+    batches, dens, temps, counts = 16, [], [], []
+    for _ in range(batches):
+        o.reset_accumulators()
+        o.step(100, sample=True)
+        dens.append(_ring_density(o, cfg, 100))
+        f = fields_from_sums(o.accumulators(), 100, o.constants()["fnum"], o.volumes(), 2.0)
+        T = (3.0 * f[:, 4] + 2.0 * f[:, 5]) / 5.0
+        temps.append(np.mean(T))
+        counts.append(o.n)
+    dens = np.array(dens)
+    m, se = dens.mean(0), dens.std(0, ddof=1) / math.sqrt(batches)
+    assert (np.abs(m - 1.0) <= 4.0 * se + 0.005).all(), (m, se)
+    assert abs(np.mean(temps) - 1.0) <= 0.01, np.mean(temps)
+    assert abs(np.mean(counts) / n0 - 1.0) <= 0.01, (np.mean(counts), n0)
+
+
+def _free_molecular_cylinder(rho, U, T, Tw, R, nphi=20000):
+    """Force (x) and hit rate per unit length on a cylinder of radius R in a
+    freestream (rho, U along x, T), free-molecular, diffuse re-emission at Tw
+    from a resting wall.  At the surface point with outward normal n =
+    (cos phi, sin phi) the speed into the wall w = -c.n is N(mu, T) with mu =
+    -U cos phi; its one-sided moments are the truncated-normal moments
+    E[w; w > 0] = mu Phi + sd phi_n, E[w^2; w > 0] = (mu^2 + T) Phi + mu sd phi_n."""
+    phi = (np.arange(nphi) + 0.5) * (2.0 * np.pi / nphi)
+    sd = math.sqrt(T)
+    mu = -U * np.cos(phi)
+    a = mu / sd
+    Phi = 0.5 * (1.0 + np.vectorize(math.erf)(a / math.sqrt(2.0)))
+    pdf = np.exp(-0.5 * a * a) / math.sqrt(2.0 * math.pi)
+    g1 = mu * Phi + sd * pdf
+    g2 = (mu * mu + T) * Phi + mu * sd * pdf
+    gamma = rho * g1
+    # momentum delivered per unit area: incoming normal (-n) and tangential
+    # (t = (-sin, cos), U.t = -U sin phi) parts, minus the re-emitted mean
+    # momentum sqrt(pi Tw / 2) n per emitted particle
+    fx = -rho * g2 * np.cos(phi) + U * np.sin(phi) ** 2 * gamma - gamma * math.sqrt(math.pi * Tw / 2.0) * np.cos(phi)
+    dphi = 2.0 * np.pi / nphi
+    return float(fx.sum() * R * dphi), float(gamma.sum() * R * dphi)
+
+
+def test_free_molecular_drag_and_hit_rate_on_the_cylinder():
+    cfg = _cfg(ntheta=48, nr=6, ppc=40, mach=2.0, t_wall=2.0, collisions=False)
+    o = oracle.OracleSim(cfg)
+    c = o.constants()
+    U, dt = cfg["fs_u"][0], cfg["dt"]
+    fx_ref, hits_ref = _free_molecular_cylinder(1.0, U, 1.0, 2.0, 0.5)
+    batches, K = 20, 300
+    fx, hits = [], []
+    for _ in range(batches):
+        w0 = o.wall_tally()[0].copy()
+        o.step(K)
+        d = o.wall_tally()[0] - w0
+        fx.append(d[1] * c["fnum"] / (K * dt))
+        hits.append(d[0] * c["fnum"] / (K * dt))
+    for got, ref in ((np.array(fx), fx_ref), (np.array(hits), hits_ref)):
+        m, se = got.mean(), got.std(ddof=1) / math.sqrt(batches)
+        assert abs(m - ref) <= 4.0 * se + 0.003 * abs(ref), (m, se, ref)
+    assert o.stats()["n_maxhit"] == 0
