@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define DSMC_ABI_VERSION 1
+#define DSMC_ABI_VERSION 2
 
 #define DSMC_OK 0
 #define DSMC_ERR_ARG (-1)           /* invalid argument or configuration */
@@ -90,7 +90,26 @@ typedef struct dsmc_config {
   uint64_t seed;      /* Philox4x32-10 key */
   int64_t capacity;   /* maximum particles; 0 = chosen from ppc and bin_slack */
   double bin_slack;   /* FP32 layout: a cell's bin holds slack x its count (+32) */
+  /* Mesh (DSMC_MESH_*).  DSMC_MESH_ANNULUS is the flow past a cylinder of
+   * Sec. 5: r_in <= r <= r_out, nx angular x ny radial cells (cell j nx + k,
+   * sector k between the rays at 2 pi k / nx and 2 pi (k+1) / nx, ring j
+   * between R_j and R_{j+1}, R_j = r_in + (r_out - r_in) (q^j - 1) /
+   * (q^ny - 1) with q = stretch, uniform for q = 1); wall 0 is the cylinder
+   * (at rest; walls 1-3 are unused); particles leave through the outer
+   * circle and the freestream (fs_rho, fs_t, fs_u) enters through it with
+   * the one-sided flux of a drifting Maxwellian.  lx, ly are not used; ppc
+   * is the mean number of particles per cell, the weight F = init_rho x
+   * (annulus area / cells) / ppc, and cell c starts with Iround(init_rho
+   * V_c / F) particles.  Single case only; dsmc_hot, synth_solve,
+   * dig_correct and the HoT network calls return DSMC_ERR_ARG on it. */
+  int32_t mesh;
+  int32_t pad1;
+  double r_in, r_out, stretch;
+  double fs_rho, fs_t, fs_u[3];
 } dsmc_config;
+
+#define DSMC_MESH_BOX 0
+#define DSMC_MESH_ANNULUS 1
 
 typedef struct dsmc_handle dsmc_handle;
 
@@ -253,6 +272,16 @@ int dsmc_set_counters(dsmc_handle *h, uint32_t step, uint32_t dig_iter);
  * their cell bin (FP32 layout, kept in an overflow list until the next
  * rebuild), bin rebuilds. */
 int dsmc_get_stats(dsmc_handle *h, int64_t *host_out8);
+
+/* Annulus: particles that entered through the outer circle and particles
+ * that left through it since dsmc_init (host, 2 entries), so that the count
+ * is the initial one + entered - left; an entering particle whose partial
+ * flight ends outside never entered and is in neither.  Zero on the box. */
+int dsmc_get_flow(dsmc_handle *h, int64_t *host_out2);
+
+/* Cell volumes (areas per unit depth in 2D, lengths in 1D) of every cell
+ * (host, ncells doubles).  Fields from dsmc_sample use them for rho. */
+int dsmc_get_volumes(dsmc_handle *h, double *host_out);
 
 /* Wall tallies since dsmc_init (host, 4 walls x 5): hits, momentum (3) and
  * energy (translational + rotational) delivered to the wall, per unit mass

@@ -647,10 +647,7 @@ static void or_inject(or_state *S) {
       double ir = -T * log(or_uni(&st, 4));
       double x = c->r_out * cos(th), y = c->r_out * sin(th);
       int in = or_fly_annulus(S, &st, 8u, &x, &y, v, &ir, or_uni(&st, 5) * c->dt);
-      if (!in || S->n >= S->cap) {
-        S->n_out += 1;
-        continue;
-      }
+      if (!in || S->n >= S->cap) continue; /* it does not enter */
       int64_t s = S->n++;
       S->x[s] = x;
       S->y[s] = y;
@@ -1170,7 +1167,8 @@ void or_get_stats(const or_state *S, int64_t out[6]) {
 /* cell volumes */
 void or_get_vol(const or_state *S, double *out) { memcpy(out, S->vol, sizeof(double) * (size_t)S->ncells); }
 
-/* particles that entered (annulus freestream) and that left */
+/* particles that entered (annulus freestream) and that left; an entering
+ * particle whose partial flight ends outside never entered and is in neither */
 void or_get_flow(const or_state *S, int64_t out[2]) {
   out[0] = S->n_inj;
   out[1] = S->n_out;

@@ -45,6 +45,10 @@ struct dsmc_handle {
   double* synth_info = nullptr;
   Mlp mlp{};       // HoT surrogate network
   int mlp_t = 0;   // Adam steps taken since the parameters were set
+  // annulus tables (device): squared ring radii, rays, outer-face
+  // directions, cell volumes, in FP64 and FP32
+  double *ann_r2t_d = nullptr, *ann_ray_d = nullptr, *ann_fn_d = nullptr, *ann_vol_d = nullptr;
+  float *ann_r2t_f = nullptr, *ann_ray_f = nullptr, *ann_fn_f = nullptr, *ann_vol_f = nullptr;
   std::string err;
 };
 
@@ -85,14 +89,31 @@ int validate(const dsmc_config* c, char* why, size_t n) {
   if (c->dim != 1 && c->dim != 2) return snprintf(why, n, "dim must be 1 or 2"), DSMC_ERR_ARG;
   if (c->nx <= 0 || (c->dim == 2 && c->ny <= 0)) return snprintf(why, n, "cell counts must be positive"), DSMC_ERR_ARG;
   if (c->ppc < 0) return snprintf(why, n, "ppc must be >= 0"), DSMC_ERR_ARG;
-  if (!(c->lx > 0) || (c->dim == 2 && !(c->ly > 0))) return snprintf(why, n, "domain lengths must be positive"), DSMC_ERR_ARG;
+  if (c->mesh != DSMC_MESH_BOX && c->mesh != DSMC_MESH_ANNULUS) return snprintf(why, n, "bad mesh"), DSMC_ERR_ARG;
+  const bool ann = c->mesh == DSMC_MESH_ANNULUS;
+  if (ann) {
+    if (c->dim != 2 || c->nx < 3) return snprintf(why, n, "the annulus is 2D with nx >= 3"), DSMC_ERR_ARG;
+    if (!(c->r_in > 0) || !(c->r_out > c->r_in) || !(c->stretch > 0))
+      return snprintf(why, n, "annulus needs 0 < r_in < r_out and stretch > 0"), DSMC_ERR_ARG;
+    if (!(c->fs_t > 0) || !(c->fs_rho >= 0) || !std::isfinite(c->fs_u[0]) || !std::isfinite(c->fs_u[1]) ||
+        !std::isfinite(c->fs_u[2]))
+      return snprintf(why, n, "bad freestream"), DSMC_ERR_ARG;
+    if (c->wall_kind[0] != DSMC_WALL_DIFFUSE && c->wall_kind[0] != DSMC_WALL_SPECULAR)
+      return snprintf(why, n, "bad wall kind"), DSMC_ERR_ARG;
+    if (c->wall_kind[0] == DSMC_WALL_DIFFUSE && !(c->wall_t[0] > 0))
+      return snprintf(why, n, "wall temperature must be positive"), DSMC_ERR_ARG;
+    if (c->wall_u[0][0] != 0.0 || c->wall_u[0][1] != 0.0 || c->wall_u[0][2] != 0.0)
+      return snprintf(why, n, "the cylinder is at rest"), DSMC_ERR_ARG;
+  } else if (!(c->lx > 0) || (c->dim == 2 && !(c->ly > 0))) {
+    return snprintf(why, n, "domain lengths must be positive"), DSMC_ERR_ARG;
+  }
   if (!(c->kn > 0) || !(c->dt > 0) || !(c->z_rot > 0)) return snprintf(why, n, "kn, dt, z_rot must be positive"), DSMC_ERR_ARG;
   if (!(c->omega > 0.5 && c->omega <= 1.0)) return snprintf(why, n, "omega must lie in (0.5, 1]"), DSMC_ERR_ARG;
   if (c->alpha != 1.0) return snprintf(why, n, "only alpha = 1 (VHS scattering) is supported"), DSMC_ERR_ARG;
   if (c->d_r != 2.0) return snprintf(why, n, "only d_r = 2 is supported"), DSMC_ERR_ARG;
   if (c->precision != DSMC_PREC_FP64_DET && c->precision != DSMC_PREC_FP32) return snprintf(why, n, "bad precision"), DSMC_ERR_ARG;
   if (!(c->init_rho > 0) || !(c->init_tt > 0) || !(c->init_tr > 0)) return snprintf(why, n, "initial rho, T must be positive"), DSMC_ERR_ARG;
-  const int nw = 2 * c->dim;
+  const int nw = ann ? 0 : 2 * c->dim;
   for (int w = 0; w < nw; ++w) {
     if (c->wall_kind[w] != DSMC_WALL_DIFFUSE && c->wall_kind[w] != DSMC_WALL_SPECULAR) return snprintf(why, n, "bad wall kind"), DSMC_ERR_ARG;
     if (c->wall_kind[w] == DSMC_WALL_DIFFUSE && !(c->wall_t[w] > 0)) return snprintf(why, n, "wall temperature must be positive"), DSMC_ERR_ARG;
@@ -232,7 +253,26 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
   ml.out = cv.take<float>((size_t)pl.ncells * 5);
   ml.scal = cv.take<double>(8);
   ml.count = cv.take<int32_t>(4);
+  const bool ann = cs[0].mesh == DSMC_MESH_ANNULUS;
+  const size_t nr1 = ann ? (size_t)cs[0].ny + 1 : 1, nray = ann ? 2 * ((size_t)cs[0].nx + 1) : 1;
+  const size_t nfn = ann ? 2 * (size_t)cs[0].nx : 1, nvol = ann ? (size_t)pl.ncells : 1;
+  double* a_r2d = cv.take<double>(nr1);
+  double* a_rayd = cv.take<double>(nray);
+  double* a_fnd = cv.take<double>(nfn);
+  double* a_vold = cv.take<double>(nvol);
+  float* a_r2f = cv.take<float>(nr1);
+  float* a_rayf = cv.take<float>(nray);
+  float* a_fnf = cv.take<float>(nfn);
+  float* a_volf = cv.take<float>(nvol);
   if (h) {
+    h->ann_r2t_d = a_r2d;
+    h->ann_ray_d = a_rayd;
+    h->ann_fn_d = a_fnd;
+    h->ann_vol_d = a_vold;
+    h->ann_r2t_f = a_r2f;
+    h->ann_ray_f = a_rayf;
+    h->ann_fn_f = a_fnf;
+    h->ann_vol_f = a_volf;
     h->mlp = ml;
     h->synth_work = sw;
     h->synth_info = si;
@@ -247,14 +287,58 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
   return pl;
 }
 
+// Annulus geometry: ring radii R_j = r_in + (r_out - r_in) (q^j - 1) / (q^ny -
+// 1) (q = stretch, uniform for q = 1) and their squares, rays (cos, sin) at
+// 2 pi k / nx (ray nx = ray 0), outer-face centre directions at 2 pi (k +
+// 1/2) / nx, cell volumes (pi / nx) (R_{j+1}^2 - R_j^2).
+struct AnnTables {
+  std::vector<double> r2t, ray, fn, vol;
+  double area = 0.0;
+};
+
+AnnTables ann_tables(const dsmc_config* c) {
+  AnnTables t;
+  const int nr = c->ny, nt = c->nx;
+  const double q = c->stretch;
+  std::vector<double> rt(nr + 1);
+  for (int j = 0; j <= nr; ++j) {
+    const double f = (q == 1.0) ? (double)j / (double)nr : (std::pow(q, (double)j) - 1.0) / (std::pow(q, (double)nr) - 1.0);
+    rt[j] = c->r_in + (c->r_out - c->r_in) * f;
+  }
+  rt[0] = c->r_in;
+  rt[nr] = c->r_out;
+  t.r2t.resize(nr + 1);
+  for (int j = 0; j <= nr; ++j) t.r2t[j] = rt[j] * rt[j];
+  t.ray.resize(2 * (nt + 1));
+  t.fn.resize(2 * nt);
+  for (int k = 0; k < nt; ++k) {
+    const double th = 2.0 * M_PI * (double)k / (double)nt;
+    t.ray[2 * k] = std::cos(th);
+    t.ray[2 * k + 1] = std::sin(th);
+    const double tm = 2.0 * M_PI * ((double)k + 0.5) / (double)nt;
+    t.fn[2 * k] = std::cos(tm);
+    t.fn[2 * k + 1] = std::sin(tm);
+  }
+  t.ray[2 * nt] = t.ray[0];
+  t.ray[2 * nt + 1] = t.ray[1];
+  const double half = M_PI / (double)nt;
+  t.vol.resize((size_t)nr * nt);
+  for (int j = 0; j < nr; ++j)
+    for (int k = 0; k < nt; ++k) t.vol[(size_t)j * nt + k] = half * (t.r2t[j + 1] - t.r2t[j]);
+  for (double v : t.vol) t.area += v;
+  return t;
+}
+
 template <typename T>
 void fill_params(const dsmc_config* c, Params<T>& p, CellParams& cp) {
   const double w = c->omega, a = c->alpha;
+  const bool ann = c->mesh == DSMC_MESH_ANNULUS;
   const int ny = (c->dim == 2) ? c->ny : 1;
-  const double lx = c->lx, ly = (c->dim == 2) ? c->ly : 1.0;
+  const double lx = ann ? 2.0 * M_PI : c->lx, ly = ann ? c->r_out - c->r_in : ((c->dim == 2) ? c->ly : 1.0);
   const double dx = lx / (double)c->nx;
   const double dy = (c->dim == 2) ? ly / (double)ny : 1.0;
-  const double vcell = dx * dy;
+  // annulus: the mean cell volume (cells differ; per-cell volumes in tables)
+  const double vcell = ann ? ann_tables(c).area / (double)(c->nx * ny) : dx * dy;
   const double fnum = c->init_rho * vcell / (double)(c->ppc > 0 ? c->ppc : 1);
   const double mu_ref = c->kn * std::sqrt(2.0 / M_PI);
   const double kv = 5.0 * (a + 1.0) * (a + 2.0) / (a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w));
@@ -289,6 +373,14 @@ void fill_params(const dsmc_config* c, Params<T>& p, CellParams& cp) {
   p.init_tt = (T)c->init_tt;
   p.init_tr = (T)c->init_tr;
   for (int q = 0; q < 3; ++q) p.init_u[q] = (T)c->init_u[q];
+  p.init_rho = (T)c->init_rho;
+  p.mesh = ann ? 1 : 0;
+  p.r2t = p.ray = p.fnrm = p.vol = nullptr;  // annulus tables: set_ann_tables
+  p.r_in = (T)c->r_in;
+  p.r_out = (T)c->r_out;
+  p.fs_rho = (T)c->fs_rho;
+  p.fs_t = (T)c->fs_t;
+  for (int q = 0; q < 3; ++q) p.fs_u[q] = (T)c->fs_u[q];
   // FP64 cell parameters
   cp.dim = c->dim;
   cp.nx = c->nx;
@@ -312,13 +404,48 @@ void fill_params(const dsmc_config* c, Params<T>& p, CellParams& cp) {
   cp.kn_ref = c->kn_ref;
   cp.k0 = p.k0;
   cp.k1 = p.k1;
+  cp.mesh = p.mesh;
+  cp.vol = nullptr;
+}
+
+// annulus: upload the tables (FP64 and FP32) and point the parameters at them
+int set_ann_tables(dsmc_handle* h) {
+  const AnnTables t = ann_tables(&h->cfg);
+  auto f32 = [](const std::vector<double>& v) {
+    std::vector<float> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+    return o;
+  };
+  const std::vector<float> r2f = f32(t.r2t), rayf = f32(t.ray), fnf = f32(t.fn), volf = f32(t.vol);
+  cudaStream_t st = h->stream;
+  cudaMemcpyAsync(h->ann_r2t_d, t.r2t.data(), sizeof(double) * t.r2t.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ann_ray_d, t.ray.data(), sizeof(double) * t.ray.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ann_fn_d, t.fn.data(), sizeof(double) * t.fn.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ann_vol_d, t.vol.data(), sizeof(double) * t.vol.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ann_r2t_f, r2f.data(), sizeof(float) * r2f.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ann_ray_f, rayf.data(), sizeof(float) * rayf.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ann_fn_f, fnf.data(), sizeof(float) * fnf.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ann_vol_f, volf.data(), sizeof(float) * volf.size(), cudaMemcpyHostToDevice, st);
+  const cudaError_t e = cudaStreamSynchronize(st);  // the host vectors die here
+  if (e != cudaSuccess) return set_err(h, DSMC_ERR_CUDA, "annulus tables: %s", cudaGetErrorString(e));
+  h->pd.r2t = h->ann_r2t_d;
+  h->pd.ray = h->ann_ray_d;
+  h->pd.fnrm = h->ann_fn_d;
+  h->pd.vol = h->ann_vol_d;
+  h->pf.r2t = h->ann_r2t_f;
+  h->pf.ray = h->ann_ray_f;
+  h->pf.fnrm = h->ann_fn_f;
+  h->pf.vol = h->ann_vol_f;
+  h->cp.vol = h->ann_vol_d;
+  return DSMC_OK;
 }
 
 double sgmax0(const dsmc_config* c, double c_sigma) {
   double tref = c->init_tt;
   double uref = std::sqrt(c->init_u[0] * c->init_u[0] + c->init_u[1] * c->init_u[1] + c->init_u[2] * c->init_u[2]);
   double umax = 0.0;
-  for (int w = 0; w < 2 * c->dim; ++w) {
+  const int nw = (c->mesh == DSMC_MESH_ANNULUS) ? 1 : 2 * c->dim;  // annulus: the cylinder
+  for (int w = 0; w < nw; ++w) {
     if (c->wall_kind[w] == 0 && c->wall_t[w] > tref) tref = c->wall_t[w];
     const double uw = std::sqrt(c->wall_u[w][0] * c->wall_u[w][0] + c->wall_u[w][1] * c->wall_u[w][1] +
                                 c->wall_u[w][2] * c->wall_u[w][2]);
@@ -362,22 +489,46 @@ int init_state(dsmc_handle* h, State<T>& s, Params<T>& p0, Params<T>* d_p) {
   std::vector<int64_t> woff(ncases);
   int64_t total = 0, wacc = 0;
   int32_t slot = 0;
+  // annulus (one case): the initial count of every cell, drawn on the device
+  const bool ann = h->cfg.mesh == DSMC_MESH_ANNULUS;
+  std::vector<int32_t> counts;
+  std::vector<double> vol;
+  if (ann) {
+    counts.resize(nc);
+    vol = ann_tables(&h->cfg).vol;
+    Ops<T>::ann_counts(h->pd, nc, s.nt, st);
+    cudaMemcpyAsync(counts.data(), s.nt, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, st);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_err(h, DSMC_ERR_CUDA, "dsmc_init: %s", cudaGetErrorString(e));
+  }
   for (int k = 0; k < ncases; ++k) {
     const dsmc_config* c = &h->cfgs[k];
     fill_params<T>(c, pt[k], cpt[k]);
     fill_params<double>(c, pdv[k], cpt[k]);
+    if (ann) {
+      pt[k] = p0;  // with the table pointers
+      pdv[k] = h->pd;
+      cpt[k] = h->cp;
+    }
     const int32_t cap0 = h->det ? c->ppc : host_bin_cap(c->ppc, c->bin_slack);
     const T sg0 = (T)sgmax0(c, (double)pdv[k].c_sigma);
     for (int i = h->cell0[k]; i < h->cell0[k + 1]; ++i) {
       cell_case[i] = k;
       start[i] = slot;
-      slot += cap0;
+      if (ann) {
+        const int32_t nominal = (int32_t)(vol[i] / h->cp.fnum + 0.5);
+        slot += h->det ? counts[i] : host_bin_cap(std::max(counts[i], nominal), c->bin_slack);
+        total += counts[i];
+      } else {
+        slot += cap0;
+      }
       sg[i] = sg0;
     }
-    total += (int64_t)(h->cell0[k + 1] - h->cell0[k]) * c->ppc;
+    if (!ann) total += (int64_t)(h->cell0[k + 1] - h->cell0[k]) * c->ppc;
     woff[k] = wacc;
     if (c->dim == 1) wacc += (int64_t)synth1d_work_doubles(h->nx[k]);
   }
+  s.pinj = h->pd;
   start[nc] = slot;
   if ((int64_t)slot > s.capacity)
     return set_err(h, DSMC_ERR_CAPACITY, "initial bins need %lld slots, capacity %lld", (long long)slot,
@@ -394,7 +545,7 @@ int init_state(dsmc_handle* h, State<T>& s, Params<T>& p0, Params<T>* d_p) {
   s.ncells = nc;
   h->cur = 0;
   h->lay = 0;
-  Ops<T>::init_batch(p0, s, nc, 0, 0, st);
+  Ops<T>::init_batch(p0, s, nc, 0, 0, st, ann ? s.nt : nullptr);
   s.nparticles = (int)total;
   s.slack = h->cfgs[0].bin_slack;
   // the host vectors above must outlive the copies
@@ -455,6 +606,7 @@ int init_cases(const dsmc_config* cfgs, int ncases, void* dev_workspace, size_t 
     const int rc = validate(&cfgs[k], why, sizeof why);
     if (rc) return rc;
     if (cfgs[k].dim != cfgs[0].dim || cfgs[k].precision != cfgs[0].precision) return DSMC_ERR_ARG;
+    if (cfgs[k].mesh == DSMC_MESH_ANNULUS && ncases != 1) return DSMC_ERR_ARG;  // the annulus runs alone
   }
   const Plan pl = make_plan(cfgs, ncases, nullptr, nullptr);
   if (!dev_workspace || bytes < pl.bytes) return DSMC_ERR_ARG;
@@ -483,6 +635,13 @@ int init_cases(const dsmc_config* cfgs, int ncases, void* dev_workspace, size_t 
   fill_params<double>(&h->cfg, h->pd, h->cp);
   fill_params<float>(&h->cfg, h->pf, h->cp);
   int r;
+  if (h->cfg.mesh == DSMC_MESH_ANNULUS) {
+    r = set_ann_tables(h);
+    if (r) {
+      delete h;
+      return r;
+    }
+  }
   if (h->det) {
     Ops<double>::configure(pl.tile);
     r = init_state<double>(h, h->sd, h->pd, h->d_pd);
@@ -519,6 +678,7 @@ int dsmc_batch_workspace_size(const dsmc_config* cfgs, int ncases, size_t* bytes
     const int rc = validate(&cfgs[k], why, sizeof why);
     if (rc) return rc;
     if (cfgs[k].dim != cfgs[0].dim || cfgs[k].precision != cfgs[0].precision) return DSMC_ERR_ARG;
+    if (cfgs[k].mesh == DSMC_MESH_ANNULUS && ncases != 1) return DSMC_ERR_ARG;
   }
   *bytes = make_plan(cfgs, ncases, nullptr, nullptr).bytes;
   return DSMC_OK;
@@ -589,6 +749,7 @@ int dsmc_sample(dsmc_handle* h, double* dev_fields, int reset) {
 
 int dsmc_hot(dsmc_handle* h, const double* dev_fields, double* dev_hot, double* dev_kngll, uint8_t* dev_mask) {
   if (!h || !dev_fields || !dev_hot) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "dsmc_hot: the gradients need the box mesh");
   launch_hot(h->d_cp, h->d_cell_case, h->d_cell0, h->ncells, dev_fields, dev_hot, dev_kngll, dev_mask, h->stream);
   return check_cuda(h, "dsmc_hot");
 }
@@ -596,6 +757,7 @@ int dsmc_hot(dsmc_handle* h, const double* dev_fields, double* dev_hot, double* 
 int synth_solve(dsmc_handle* h, const double* dev_fields, const double* dev_hot, double* dev_out, int* host_iters,
                 double* host_resid) {
   if (!h || !dev_fields || !dev_hot || !dev_out) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "synth_solve: only the 1D slab is implemented");
   int n_m = 0;
   double tol = 1.0;
   for (int k = 0; k < h->ncases; ++k) {
@@ -629,6 +791,7 @@ int synth_solve(dsmc_handle* h, const double* dev_fields, const double* dev_hot,
 
 int dig_correct(dsmc_handle* h, const double* dev_target) {
   if (!h || !dev_target) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "dig_correct: not on the annulus");
   int32_t fl[4] = {0, 0, 0, 0};
   if (h->det) Ops<double>::dig_counts(h->sd, h->ncells, h->lay, dev_target, h->dig_iter, 1, h->stream);
   else Ops<float>::dig_counts(h->sf, h->ncells, h->lay, dev_target, h->dig_iter, 0, h->stream);
@@ -749,6 +912,32 @@ int dsmc_get_stats(dsmc_handle* h, int64_t* out8) {
   return DSMC_OK;
 }
 
+int dsmc_get_flow(dsmc_handle* h, int64_t* out2) {
+  if (!h || !out2) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  unsigned long long s[ST_NSLOTS];
+  cudaMemcpyAsync(s, h->det ? h->sd.stats : h->sf.stats, sizeof s, cudaMemcpyDeviceToHost, h->stream);
+  const int r = sync_check(h, "dsmc_get_flow");
+  if (r) return r;
+  out2[0] = (int64_t)s[ST_INJ];
+  out2[1] = (int64_t)s[ST_OUT];
+  return DSMC_OK;
+}
+
+int dsmc_get_volumes(dsmc_handle* h, double* host_out) {
+  if (!h || !host_out) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (h->cfg.mesh == DSMC_MESH_ANNULUS) {
+    cudaMemcpyAsync(host_out, h->ann_vol_d, sizeof(double) * h->ncells, cudaMemcpyDeviceToHost, h->stream);
+    return sync_check(h, "dsmc_get_volumes");
+  }
+  for (int k = 0; k < h->ncases; ++k) {
+    Params<double> p;
+    CellParams cp;
+    fill_params<double>(&h->cfgs[k], p, cp);
+    for (int i = h->cell0[k]; i < h->cell0[k + 1]; ++i) host_out[i] = cp.vcell;
+  }
+  return DSMC_OK;
+}
+
 int dsmc_get_wall_tally(dsmc_handle* h, double* out20) {
   if (!h || !out20) return set_err(h, DSMC_ERR_ARG, "bad arguments");
   cudaMemcpyAsync(out20, h->det ? h->sd.tally : h->sf.tally, sizeof(double) * 20, cudaMemcpyDeviceToHost, h->stream);
@@ -799,6 +988,7 @@ int hot_mlp_get_params(dsmc_handle* h, float* host_params) {
 int hot_mlp_grad(dsmc_handle* h, const double* dev_fields, const double* dev_hot, const double* dev_kngll,
                  const uint8_t* dev_mask, float* host_grad, double* host_loss) {
   if (!h || !dev_fields || !dev_hot || !dev_kngll || !dev_mask) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "HoT network: the features need the box mesh");
   mlp_data(h, dev_fields, dev_hot, dev_kngll, dev_mask);
   int n = 0;
   int r = mlp_count(h, &n);
@@ -819,6 +1009,7 @@ int hot_mlp_train(dsmc_handle* h, const double* dev_fields, const double* dev_ho
                   const uint8_t* dev_mask, int nsteps, double lr, double* host_loss) {
   if (!h || !dev_fields || !dev_hot || !dev_kngll || !dev_mask || nsteps < 0 || !(lr > 0.0))
     return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "HoT network: the features need the box mesh");
   mlp_data(h, dev_fields, dev_hot, dev_kngll, dev_mask);
   int n = 0;
   int r = mlp_count(h, &n);
@@ -841,6 +1032,7 @@ int hot_mlp_apply(dsmc_handle* h, const double* dev_fields, const double* dev_ho
                   const uint8_t* dev_mask, double* dev_hot_out, double* host_judge) {
   if (!h || !dev_fields || !dev_hot || !dev_kngll || !dev_mask || !dev_hot_out)
     return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "HoT network: the features need the box mesh");
   mlp_data(h, dev_fields, dev_hot, dev_kngll, dev_mask);
   mlp_apply(h->mlp, h->ncells, dev_hot, dev_hot_out, h->stream);
   double j[2] = {0.0, 0.0};

@@ -11,6 +11,9 @@
 //   TAG_NTC   (0, cell, step)   Iround of the candidate-pair count
 //   TAG_COLL  (m, cell, step)   candidate pair m of a cell
 //   TAG_DIG_* (q, cell, iter)   particle modification, always FP64 layout
+//   TAG_INJ   (q, face, step)   freestream entry through outer face `face` of
+//                               the annulus, always FP64; (~0, face, step)
+//                               draws the face's count
 #pragma once
 
 #include <cstdint>
@@ -19,7 +22,7 @@
 namespace dsmc {
 
 constexpr uint32_t TAG_INIT = 1u, TAG_WALL = 2u, TAG_NTC = 3u, TAG_COLL = 4u;
-constexpr uint32_t TAG_DIG_N = 5u, TAG_DIG_SEL = 6u, TAG_DIG_POS = 7u;
+constexpr uint32_t TAG_DIG_N = 5u, TAG_DIG_SEL = 6u, TAG_DIG_POS = 7u, TAG_INJ = 8u;
 constexpr int MAX_HITS = 8;
 constexpr int NMOM = 17;
 constexpr uint32_t OWNER_FREE = 0xFFFFFFFFu;
@@ -40,12 +43,22 @@ struct Params {
   uint32_t k0, k1;
   int ppc;                           // initial particles per cell
   T init_tt, init_tr, init_u[3];     // initial equilibrium state
+  T init_rho;
+  // mesh 1: annulus r_in <= r <= r_out around a cylinder (Sec. 5), nx
+  // angular x ny radial cells, cell = j nx + k; wall 0 is the cylinder
+  int mesh;
+  const T* r2t;   // ny + 1 squared ring radii
+  const T* ray;   // nx + 1 rays (cos, sin) at 2 pi k / nx; ray nx = ray 0
+  const T* fnrm;  // nx outer-face centre directions (cos, sin)
+  const T* vol;   // cell volumes (null on the box: vcell)
+  T r_in, r_out;
+  T fs_rho, fs_t, fs_u[3];  // freestream entering through the outer circle
 };
 
 // Per-step device counters (unsigned long long so they can be added atomically).
 enum StatSlot {
   ST_CAND = 0, ST_COLL = 1, ST_CLIP = 2, ST_INEL = 3, ST_HITS = 4, ST_MAXHIT = 5, ST_OVF = 6,
-  ST_REBIN = 7, ST_NEARFULL = 8, ST_NSLOTS = 16
+  ST_REBIN = 7, ST_NEARFULL = 8, ST_OUT = 9, ST_INJ = 10, ST_NSLOTS = 16
 };
 
 // ---------------------------------------------------------------------------
@@ -188,6 +201,12 @@ __device__ __forceinline__ void m_sincos_2pi(double u, double* s, double* c) {
 __device__ __forceinline__ void m_sincos_2pi(float u, float* s, float* c) {
   sincospif(2.0f * u, s, c);
 }
+__device__ __forceinline__ double m_cos(double x) { return cos(x); }
+__device__ __forceinline__ float m_cos(float x) { return cosf(x); }
+__device__ __forceinline__ double m_sin(double x) { return sin(x); }
+__device__ __forceinline__ float m_sin(float x) { return sinf(x); }
+__device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 
@@ -215,6 +234,33 @@ __device__ __forceinline__ int cell_of(const Params<T>& p, T x, T y) {
   int iy = (int)(y * p.sy);
   iy = iy < 0 ? 0 : (iy > p.ny - 1 ? p.ny - 1 : iy);
   return iy * p.nx + ix;
+}
+
+// Annulus cell of (x, y), -1 at or beyond r_out (the particle has left).
+// Ring j is the largest with R_j^2 <= r^2 (ring 0 below r_in, where rounding
+// can put a particle); sector k holds the points with cross(ray_k, p) >= 0 >
+// cross(ray_{k+1}, p), reached from the atan2 guess by those two signs.
+template <typename T>
+__device__ __forceinline__ int cell_of_ann(const Params<T>& p, T x, T y) {
+  const int nr = p.ny, nt = p.nx;
+  const T r2 = x * x + y * y;
+  if (!(r2 < p.r2t[nr])) return -1;
+  int lo = 0, hi = nr - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.r2t[mid] <= r2) lo = mid;
+    else hi = mid - 1;
+  }
+  T th = m_atan2(y, x);
+  if (th < T(0)) th += T(2.0 * PI_D);
+  int k = (int)(th * ((T)nt / T(2.0 * PI_D)));
+  k = k < 0 ? 0 : (k > nt - 1 ? nt - 1 : k);
+  for (int it = 0; it < 4; ++it) {
+    if (p.ray[2 * k] * y - p.ray[2 * k + 1] * x < T(0)) k = (k == 0) ? nt - 1 : k - 1;
+    else if (p.ray[2 * k + 2] * y - p.ray[2 * k + 3] * x >= T(0)) k = (k == nt - 1) ? 0 : k + 1;
+    else break;
+  }
+  return lo * nt + k;
 }
 
 // ---------------------------------------------------------------------------
@@ -379,6 +425,118 @@ __device__ void fly_walls(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T
   if (TALLY && hits) atomicAdd(hits_out, (unsigned long long)hits);
 }
 
+// Free flight over t in the annulus (flow past a cylinder).  The first
+// crossing of the cylinder along p + v s is the smaller root of |p + v s|^2 =
+// r_in^2, taken when the particle moves inward; the particle is put on the
+// circle, re-emitted (diffuse at T_w about the resting wall, or specular)
+// and flies the rest of the step; a path leaving a convex body does not
+// meet it again.  Hit h draws uniforms j0 + 4h .. j0 + 4h + 3 of stream
+// (tag, idx, cell, step).  Returns false if the particle ends at or beyond
+// r_out (it leaves the domain).  tally[0..4]: hits, momentum (3) and energy
+// delivered to the cylinder.
+template <typename T, bool TALLY>
+__device__ bool fly_ann(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& ir, uint32_t tag, uint32_t idx,
+                        uint32_t cell, uint32_t step, uint32_t j0, T t, T* tally, unsigned long long* hits_out,
+                        unsigned long long* maxhit_out) {
+  int hits = 0;
+  const T rin2 = p.r2t[0];
+  for (;;) {
+    const T a = vx * vx + vy * vy;
+    const T b = x * vx + y * vy;
+    T s1 = T(0);
+    bool hit = false;
+    if (b < T(0) && a > T(0)) {
+      const T cc = x * x + y * y - rin2;
+      const T disc = b * b - a * cc;
+      if (disc > T(0)) {
+        s1 = (-b - m_sqrt(disc)) / a;
+        if (s1 < T(0)) s1 = T(0);
+        hit = s1 < t;
+      }
+    }
+    if (!hit) {
+      x = x + vx * t;
+      y = y + vy * t;
+      break;
+    }
+    const T xh = x + vx * s1, yh = y + vy * s1;
+    const T rh = m_sqrt(xh * xh + yh * yh);
+    const T nx = xh / rh, ny = yh / rh;
+    x = p.r_in * nx;
+    y = p.r_in * ny;
+    if (hits == MAX_HITS) {
+      if (TALLY) atomicAdd(maxhit_out, 1ull);
+      break;
+    }
+    t = t - s1;
+    if (t < T(0)) t = T(0);
+    const T vix = vx, viy = vy, viz = vz, iri = ir;
+    if (p.wall_kind[0] == 1) {
+      const T vn = vx * nx + vy * ny;
+      vx = vx - T(2) * vn * nx;
+      vy = vy - T(2) * vn * ny;
+    } else {
+      const T Tw = p.wall_t[0];
+      T u4[4];
+      draw4(tag, idx, cell, step, j0 + 4u * (uint32_t)hits, p.k0, p.k1, u4);
+      const T vn = m_sqrt(T(-2) * Tw * m_log(u4[0]));
+      T n1, n2;
+      box_muller(u4[1], u4[2], &n1, &n2);
+      const T sT = m_sqrt(Tw);
+      const T vt = sT * n1;
+      vx = vn * nx - vt * ny;
+      vy = vn * ny + vt * nx;
+      vz = sT * n2;
+      ir = -Tw * m_log(u4[3]);
+    }
+    if (TALLY) {
+      atomicAdd(tally + 0, T(1));
+      atomicAdd(tally + 1, vix - vx);
+      atomicAdd(tally + 2, viy - vy);
+      atomicAdd(tally + 3, viz - vz);
+      atomicAdd(tally + 4, (T(0.5) * (vix * vix + viy * viy + viz * viz) + iri) -
+                               (T(0.5) * (vx * vx + vy * vy + vz * vz) + ir));
+    }
+    hits += 1;
+  }
+  if (TALLY && hits) atomicAdd(hits_out, (unsigned long long)hits);
+  return x * x + y * y < p.r2t[p.ny];
+}
+
+// Freestream entry (annulus), FP64.  One-sided number flux per unit length
+// and time of a Maxwellian (rho, T, normal drift u_n inward) through a
+// boundary: rho G(inf) / (beta sqrt(pi)), beta = 1/sqrt(2T), s = u_n beta,
+// G(inf) = exp(-s^2)/2 + s (sqrt(pi)/2) erfc(-s).
+__device__ __forceinline__ double inflow_ginf(double s) {
+  return 0.5 * exp(-s * s) + s * (0.5 * sqrt(PI_D)) * erfc(-s);
+}
+
+// Inward normal speed of an entering particle in units of 1/beta: z > 0 has
+// density z exp(-(z - s)^2) with CDF G(z) = [exp(-s^2) - exp(-(z-s)^2)] / 2 +
+// s (sqrt(pi)/2) [erfc(-s) - erfc(z - s)]; G(z) = u G(inf) is solved by
+// Newton steps kept inside a bisection bracket, at most 100 of them.
+__device__ inline double inflow_speed(double s, double u) {
+  const double target = u * inflow_ginf(s);
+  double lo = 0.0, hi = (s > 0.0 ? s : 0.0) + 8.0;
+  double z = 0.5 * (lo + hi);
+  for (int it = 0; it < 100; ++it) {
+    const double w = z - s;
+    const double g = 0.5 * (exp(-s * s) - exp(-w * w)) + s * (0.5 * sqrt(PI_D)) * (erfc(-s) - erfc(w));
+    const double f = g - target;
+    if (f > 0.0) hi = z;
+    else lo = z;
+    const double d = z * exp(-w * w);
+    double zn = (d > 0.0) ? z - f / d : 0.5 * (lo + hi);
+    if (!(zn > lo && zn < hi)) zn = 0.5 * (lo + hi);
+    if (fabs(zn - z) <= 1e-15 * (1.0 + z) || hi - lo <= 1e-15 * (1.0 + z)) {
+      z = zn;
+      break;
+    }
+    z = zn;
+  }
+  return z;
+}
+
 // true if a free flight over dt stays inside the domain (no wall is reached)
 template <typename T, int DIM>
 __device__ __forceinline__ bool flight_stays_inside(const Params<T>& p, T x, T y, T vx, T vy, T* xn, T* yn) {
@@ -431,7 +589,8 @@ __device__ __forceinline__ void collide_cell(const Params<T>& p, T* __restrict__
   const int lane = threadIdx.x & 31;
   if (!p.collisions || n < 2) return;
   const T sgmax = *sgmax_ptr;
-  const T xm = T(0.5) * T(n) * T(n - 1) * p.fnum * sgmax * p.dt / p.vcell;
+  const T vc = p.vol ? p.vol[cell] : p.vcell;  // the annulus's cells differ in volume
+  const T xm = T(0.5) * T(n) * T(n - 1) * p.fnum * sgmax * p.dt / vc;
   Stream<T> sn(TAG_NTC, 0u, cell, step, p.k0, p.k1);
   const long long Mll = iround(xm, sn.u(0));
   const uint32_t M = (uint32_t)(Mll < 0 ? 0 : Mll);

@@ -43,8 +43,9 @@ __global__ void k_fields(const CellParams* __restrict__ cps, const int32_t* __re
     const double q3x = a[10] - 2.0 * Sux - ux * trS + 2.0 * N * ux * u2;
     const double q3y = a[11] - 2.0 * Suy - uy * trS + 2.0 * N * uy * u2;
     const double q3z = a[12] - 2.0 * Suz - uz * trS + 2.0 * N * uz * u2;
-    const double nv = cp.fnum / (cp.vcell * nsamples);
-    f[0] = cp.fnum * N / (nsamples * cp.vcell);
+    const double vc = cp.vol ? cp.vol[c] : cp.vcell;  // annulus: one case, global cell = local cell
+    const double nv = cp.fnum / (vc * nsamples);
+    f[0] = cp.fnum * N / (nsamples * vc);
     f[1] = ux;
     f[2] = uy;
     f[3] = uz;

@@ -29,6 +29,8 @@ struct CellParams {
   double kappa_t, kappa_r;  // kappa / mu from Eq. (kappa_A)
   double kn_ref;
   uint32_t k0, k1;
+  int mesh;            // 0 Cartesian box, 1 annulus (single case)
+  const double* vol;   // annulus: cell volumes (null on the box: vcell)
 };
 
 // Per-case tables of a handle (device memory).  A single simulation is one
@@ -75,6 +77,7 @@ struct State {
   Cases<T> cases;
   bool batch;  // several cases: kernels read their parameters per cell
   int fwpb;    // FP32 fused step: warps per CTA (0: not tuned yet)
+  Params<double> pinj;  // annulus: FP64 parameters of the freestream entry
 };
 
 template <typename T>
@@ -83,7 +86,11 @@ struct Ops {
   static void init(const Params<T>& p, State<T>& s, int cur, int lay, int ppc, int cap0, double tt,
                    double tr, const double* u3, cudaStream_t st);
   // batch: the layout s.start[lay] is set; every case fills its cells
-  static void init_batch(const Params<T>& p0, State<T>& s, int ncells, int cur, int lay, cudaStream_t st);
+  // (counts[c] particles in cell c when counts is given, else ppc)
+  static void init_batch(const Params<T>& p0, State<T>& s, int ncells, int cur, int lay, cudaStream_t st,
+                         const int32_t* counts = nullptr);
+  // annulus: initial particles per cell (FP64 draws, both layouts)
+  static void ann_counts(const Params<double>& pd, int ncells, int32_t* counts, cudaStream_t st);
   static void step_det(const Params<T>& p, State<T>& s, int& cur, int& lay, uint32_t step,
                        int do_sample, cudaStream_t st);
   static void step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint32_t step0,

@@ -118,7 +118,8 @@ __global__ void k_init(Params<T> p, PBuf<T> b, const int32_t* __restrict__ start
 // initial state and the random key (same draws as k_init).
 template <typename T, int DIM>
 __global__ void k_init_cells(Cases<T> cases, int ncells, PBuf<T> b, const int32_t* __restrict__ start,
-                             int32_t* __restrict__ count, int32_t* __restrict__ cellof) {
+                             int32_t* __restrict__ count, int32_t* __restrict__ cellof,
+                             const int32_t* __restrict__ counts) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int cell = warp;
   if (cell >= ncells) return;
@@ -126,7 +127,7 @@ __global__ void k_init_cells(Cases<T> cases, int ncells, PBuf<T> b, const int32_
   const Params<T>& p = cases.p[cs];
   const int lcell = cell - cases.cell0[cs];
   const int ix = lcell % p.nx, iy = lcell / p.nx;
-  const int ppc = p.ppc;
+  const int ppc = counts ? counts[cell] : p.ppc;
   const T stt = m_sqrt(p.init_tt);
   for (int k = lane; k < ppc; k += 32) {
     Stream<T> st(TAG_INIT, (uint32_t)k, (uint32_t)lcell, 0u, p.k0, p.k1);
@@ -135,8 +136,16 @@ __global__ void k_init_cells(Cases<T> cases, int ncells, PBuf<T> b, const int32_
     box_muller(st.u(2), st.u(3), &n1, &n2);
     box_muller(st.u(4), st.u(5), &n3, &n4);
     const int slot = start[cell] + k;
-    b.x[slot] = ((T)ix + a0) * p.dx;
-    b.y[slot] = (DIM == 2) ? ((T)iy + a1) * p.dy : T(0);
+    if (p.mesh == 1) {
+      // annulus: uniform in the sector (r^2 and the angle uniform)
+      const T r = m_sqrt(p.r2t[iy] + a0 * (p.r2t[iy + 1] - p.r2t[iy]));
+      const T th = T(2.0 * PI_D) * ((T)ix + a1) / (T)p.nx;
+      b.x[slot] = r * m_cos(th);
+      b.y[slot] = r * m_sin(th);
+    } else {
+      b.x[slot] = ((T)ix + a0) * p.dx;
+      b.y[slot] = (DIM == 2) ? ((T)iy + a1) * p.dy : T(0);
+    }
     b.vx[slot] = p.init_u[0] + stt * n1;
     b.vy[slot] = p.init_u[1] + stt * n2;
     b.vz[slot] = p.init_u[2] + stt * n3;
@@ -144,6 +153,15 @@ __global__ void k_init_cells(Cases<T> cases, int ncells, PBuf<T> b, const int32_
     if (cellof) cellof[slot] = cell;
   }
   if (lane == 0) count[cell] = ppc;
+}
+
+// Annulus: initial particles of every cell, Iround(rho V_cell / F) with the
+// draw (~0, cell, 0) of the initial stream (FP64 in both layouts)
+static __global__ void k_ann_counts(const __grid_constant__ Params<double> pd, int ncells, int32_t* __restrict__ counts) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+    Stream<double> st(TAG_INIT, 0xFFFFFFFFu, (uint32_t)c, 0u, pd.k0, pd.k1);
+    counts[c] = (int32_t)iround(pd.init_rho * pd.vol[c] / pd.fnum, st.u(0));
+  }
 }
 
 static __global__ void k_layout_uniform(int ncells, int32_t cap, int32_t* start) {
@@ -154,7 +172,7 @@ static __global__ void k_layout_uniform(int ncells, int32_t cap, int32_t* start)
 // ---------------------------------------------------------------------------
 // FP64-deterministic layout: move, stable sort, collide + sample
 // ---------------------------------------------------------------------------
-template <typename T, int DIM, bool BATCH>
+template <typename T, int DIM, bool BATCH, bool ANN>
 __global__ void __launch_bounds__(256) k_move_det(const __grid_constant__ Params<T> pk, Cases<T> cases, PBuf<T> b,
                                                   const int32_t* __restrict__ cellof,
                                                   const int32_t* __restrict__ start, int n,
@@ -170,15 +188,26 @@ __global__ void __launch_bounds__(256) k_move_det(const __grid_constant__ Params
     const Params<T>& p = BATCH ? cases.p[cs] : pk;
     const int c0 = BATCH ? cases.cell0[cs] : 0;
     T x = b.x[s], y = b.y[s], vx = b.vx[s], vy = b.vy[s], vz = b.vz[s], ir = b.ir[s];
-    fly<T, DIM, true>(p, x, y, vx, vy, vz, ir, (uint32_t)(s - start[c]), (uint32_t)(c - c0), step, s_tally,
-                stats + ST_HITS, stats + ST_MAXHIT);
+    bool in = true;
+    if constexpr (ANN)
+      in = fly_ann<T, true>(p, x, y, vx, vy, vz, ir, TAG_WALL, (uint32_t)(s - start[c]), (uint32_t)c, step, 0u, p.dt,
+                            s_tally, stats + ST_HITS, stats + ST_MAXHIT);
+    else
+      fly<T, DIM, true>(p, x, y, vx, vy, vz, ir, (uint32_t)(s - start[c]), (uint32_t)(c - c0), step, s_tally,
+                        stats + ST_HITS, stats + ST_MAXHIT);
     b.x[s] = x;
     b.y[s] = y;
     b.vx[s] = vx;
     b.vy[s] = vy;
     b.vz[s] = vz;
     b.ir[s] = ir;
-    key[s] = c0 + cell_of<T, DIM>(p, x, y);
+    if constexpr (ANN) {
+      // a particle that left keeps key -1: the sort drops it
+      key[s] = in ? cell_of_ann<T>(p, x, y) : -1;
+      if (!in) atomicAdd(stats + ST_OUT, 1ull);
+    } else {
+      key[s] = c0 + cell_of<T, DIM>(p, x, y);
+    }
   }
   __syncthreads();
   if (threadIdx.x < 20 && s_tally[threadIdx.x] != T(0))
@@ -200,7 +229,8 @@ __global__ void __launch_bounds__(1024) k_sort_stable(const Tin* __restrict__ ix
                                                       int32_t* __restrict__ cellof_out) {
   for (int c = threadIdx.x; c < ncells; c += blockDim.x) count_out[c] = 0;
   __syncthreads();
-  for (int s = threadIdx.x; s < n; s += blockDim.x) atomicAdd(&count_out[key[s]], 1);
+  for (int s = threadIdx.x; s < n; s += blockDim.x)
+    if (key[s] >= 0) atomicAdd(&count_out[key[s]], 1);  // key -1: the particle left
   __syncthreads();
   cta_exclusive_scan(ncells, [&](int i) { return count_out[i]; }, start_out);
   for (int c = threadIdx.x; c < ncells; c += blockDim.x) fill[c] = start_out[c];
@@ -214,18 +244,19 @@ __global__ void __launch_bounds__(1024) k_sort_stable(const Tin* __restrict__ ix
       const int leader = __ffs(peers) - 1;
       const int rank = __popc(peers & ((1u << lane) - 1u));
       int b = 0;
-      if (s < n && lane == leader) {
+      if (s < n && k >= 0 && lane == leader) {
         b = fill[k];
         fill[k] = b + __popc(peers);
       }
       b = __shfl_sync(FULL, b, leader);
-      if (s < n) dest[s] = b + rank;
+      if (s < n) dest[s] = (k >= 0) ? b + rank : -1;
       __syncwarp();
     }
   }
   __syncthreads();
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
     const int d = dest[s];
+    if (d < 0) continue;
     o.x[d] = (Tout)ix[s];
     o.y[d] = (Tout)iy[s];
     o.vx[d] = (Tout)ivx[s];
@@ -234,6 +265,153 @@ __global__ void __launch_bounds__(1024) k_sort_stable(const Tin* __restrict__ ix
     o.ir[d] = (Tout)iir[s];
     if (cellof_out) cellof_out[d] = key[s];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Freestream entry through the outer circle of the annulus (FP64 arithmetic
+// in both layouts).  Outer face k (between rays k and k+1 at r_out) admits
+// Iround(flux L dt / F) particles, the flux that of the drifting freestream
+// Maxwellian through the face with its centre normal, L = r_out 2 pi / nx.
+// Particle q of face k (stream (q, k, step)): inward normal speed from the
+// inflow distribution, tangential and z components Maxwellian about the
+// freestream, I_r at its temperature, entry angle uniform on the face, then
+// a flight over a uniform fraction of the step.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long inflow_count(const Params<double>& p, int k, uint32_t step) {
+  const double beta = 1.0 / sqrt(2.0 * p.fs_t);
+  const double len = p.r_out * 2.0 * PI_D / (double)p.nx;
+  const double nx = -p.fnrm[2 * k], ny = -p.fnrm[2 * k + 1];  // inward normal
+  const double sn = (p.fs_u[0] * nx + p.fs_u[1] * ny) * beta;
+  const double mu = p.fs_rho * inflow_ginf(sn) / (beta * sqrt(PI_D)) * len * p.dt / p.fnum;
+  Stream<double> sc(TAG_INJ, 0xFFFFFFFFu, (uint32_t)k, step, p.k0, p.k1);
+  return iround(mu, sc.u(0));
+}
+
+// false if the entering particle ends outside (it does not enter)
+template <bool TALLY>
+__device__ __forceinline__ bool inflow_particle(const Params<double>& p, int k, int q, uint32_t step, double* tally,
+                                                unsigned long long* hits, unsigned long long* maxhit, double& x,
+                                                double& y, double& vx, double& vy, double& vz, double& ir) {
+  const double sT = sqrt(p.fs_t), beta = 1.0 / sqrt(2.0 * p.fs_t);
+  const double nx = -p.fnrm[2 * k], ny = -p.fnrm[2 * k + 1];
+  const double tx = -ny, ty = nx;
+  const double un = p.fs_u[0] * nx + p.fs_u[1] * ny, ut = p.fs_u[0] * tx + p.fs_u[1] * ty;
+  Stream<double> st(TAG_INJ, (uint32_t)q, (uint32_t)k, step, p.k0, p.k1);
+  const double vn = inflow_speed(un * beta, st.u(0)) / beta;
+  double n1, n2;
+  box_muller(st.u(1), st.u(2), &n1, &n2);
+  const double vt = ut + sT * n1;
+  vx = vn * nx + vt * tx;
+  vy = vn * ny + vt * ty;
+  vz = p.fs_u[2] + sT * n2;
+  const double th = 2.0 * PI_D * ((double)k + st.u(3)) / (double)p.nx;
+  ir = -p.fs_t * log(st.u(4));
+  x = p.r_out * cos(th);
+  y = p.r_out * sin(th);
+  return fly_ann<double, TALLY>(p, x, y, vx, vy, vz, ir, TAG_INJ, (uint32_t)q, (uint32_t)k, step, 8u, st.u(5) * p.dt,
+                                tally, hits, maxhit);
+}
+
+// FP64 layout, one CTA: a scan gives each face its run of slots after the n
+// moved particles, so that new particles follow face by face and, within a
+// face, in draw order (the sequential algorithm's order).  One that ends
+// outside keeps key -1 (the sort drops it).  cnt, off: nx and nx + 1 ints;
+// off[nx] is the number of slots used.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_inject_det(const __grid_constant__ Params<double> p, PBuf<T> b,
+                                                     int32_t* __restrict__ key, int n, long long capacity,
+                                                     uint32_t step, int32_t* __restrict__ cnt,
+                                                     int32_t* __restrict__ off, int32_t* __restrict__ flags,
+                                                     double* __restrict__ tally_g,
+                                                     unsigned long long* __restrict__ stats) {
+  __shared__ double s_tally[5];
+  if (threadIdx.x < 5) s_tally[threadIdx.x] = 0.0;
+  const int nt = p.nx;
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    const long long m = inflow_count(p, k, step);
+    cnt[k] = (int32_t)(m < 0 ? 0 : (m > (1 << 24) ? (1 << 24) : m));
+  }
+  __syncthreads();
+  cta_exclusive_scan(nt, [&](int i) { return cnt[i]; }, off);
+  if (threadIdx.x == 0 && (long long)n + off[nt] > capacity) atomicOr(flags, 4);
+  unsigned long long nin = 0;
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    for (int q = 0; q < cnt[k]; ++q) {
+      const long long slot = (long long)n + off[k] + q;
+      if (slot >= capacity) break;
+      double x, y, vx, vy, vz, ir;
+      const bool in = inflow_particle<true>(p, k, q, step, s_tally, stats + ST_HITS, stats + ST_MAXHIT, x, y, vx, vy,
+                                            vz, ir);
+      b.x[slot] = (T)x;
+      b.y[slot] = (T)y;
+      b.vx[slot] = (T)vx;
+      b.vy[slot] = (T)vy;
+      b.vz[slot] = (T)vz;
+      b.ir[slot] = (T)ir;
+      key[slot] = in ? cell_of_ann<double>(p, x, y) : -1;
+      if (in) ++nin;  // one that ends outside never entered
+    }
+  }
+  if (nin) atomicAdd(stats + ST_INJ, nin);
+  __syncthreads();
+  if (threadIdx.x < 5 && s_tally[threadIdx.x] != 0.0) atomicAdd(tally_g + threadIdx.x, s_tally[threadIdx.x]);
+}
+
+template <int DIM>
+__device__ __forceinline__ void append_particle(const Params<float>& p, const PBuf<float>& o,
+                                                const int32_t* __restrict__ start,
+                                                int32_t* __restrict__ cnt_out, const Ovf& ovo,
+                                                int ovf_cap, bool active, int d, float x, float y,
+                                                float vx, float vy, float vz, float ir,
+                                                unsigned* s_misc);
+
+// FP32 layout: one warp per outer face; new particles go into the bins of
+// the next step like moved ones (warp-aggregated append, overflow list when
+// a bin is full)
+static __global__ void __launch_bounds__(256) k_inject_bins(const __grid_constant__ Params<double> pd,
+                                                            const __grid_constant__ Params<float> pf, PBuf<float> out,
+                                                            const int32_t* __restrict__ start,
+                                                            int32_t* __restrict__ cnt_out, Ovf ovo, int ovf_cap,
+                                                            uint32_t step, double* __restrict__ tally_g,
+                                                            unsigned long long* __restrict__ stats) {
+  __shared__ double s_tally[5];
+  __shared__ unsigned s_misc[2];
+  __shared__ unsigned s_flow[2];
+  __shared__ unsigned long long s_hits[2];
+  if (threadIdx.x < 5) s_tally[threadIdx.x] = 0.0;
+  if (threadIdx.x < 2) {
+    s_misc[threadIdx.x] = 0;
+    s_flow[threadIdx.x] = 0;
+    s_hits[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int k = gw; k < pd.nx; k += nwarps) {
+    long long m = 0;
+    if (lane == 0) m = inflow_count(pd, k, step);
+    m = __shfl_sync(FULL, m, 0);
+    if (m > (1 << 24)) m = 1 << 24;
+    for (long long qb = 0; qb < m; qb += 32) {
+      const long long q = qb + lane;
+      double x = 0.0, y = 0.0, vx = 0.0, vy = 0.0, vz = 0.0, ir = 0.0;
+      int d = -1;
+      if (q < m) {
+        if (inflow_particle<true>(pd, k, (int)q, step, s_tally, &s_hits[0], &s_hits[1], x, y, vx, vy, vz, ir))
+          d = cell_of_ann<float>(pf, (float)x, (float)y);
+        if (d >= 0) atomicAdd(&s_flow[0], 1u);  // one that ends outside never entered
+      }
+      append_particle<2>(pf, out, start, cnt_out, ovo, ovf_cap, d >= 0, d, (float)x, (float)y, (float)vx, (float)vy,
+                         (float)vz, (float)ir, s_misc);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 5 && s_tally[threadIdx.x] != 0.0) atomicAdd(tally_g + threadIdx.x, s_tally[threadIdx.x]);
+  if (threadIdx.x == 5 && s_flow[0]) atomicAdd(stats + ST_INJ, (unsigned long long)s_flow[0]);
+  if (threadIdx.x == 7 && s_misc[0]) atomicAdd(stats + ST_OVF, (unsigned long long)s_misc[0]);
+  if (threadIdx.x == 8 && s_misc[1]) atomicAdd(stats + ST_NEARFULL, (unsigned long long)s_misc[1]);
+  if (threadIdx.x == 9 && s_hits[0]) atomicAdd(stats + ST_HITS, s_hits[0]);
+  if (threadIdx.x == 10 && s_hits[1]) atomicAdd(stats + ST_MAXHIT, s_hits[1]);
 }
 
 template <typename T>
@@ -406,6 +584,65 @@ __device__ __forceinline__ int neighbour_cell(int nx, int cell, int code) {
   return cell + (code / 3 - 1) * nx + (code % 3 - 1);
 }
 
+// Annulus: the straight flight over dt, true if it does not meet the
+// cylinder (the test of fly_ann)
+__device__ __forceinline__ bool ann_straight(const Params<float>& p, float x, float y, float vx, float vy, float* xn,
+                                             float* yn) {
+  *xn = x + vx * p.dt;
+  *yn = y + vy * p.dt;
+  const float a = vx * vx + vy * vy, b = x * vx + y * vy;
+  if (b < 0.f && a > 0.f) {
+    const float cc = x * x + y * y - p.r2t[0];
+    const float disc = b * b - a * cc;
+    if (disc > 0.f) {
+      float s1 = (-b - sqrtf(disc)) / a;
+      if (s1 < 0.f) s1 = 0.f;
+      if (s1 < p.dt) return false;
+    }
+  }
+  return true;
+}
+
+// Annulus: code (dj + 1) * 3 + (dk + 1) of the cell (ring j + dj, sector
+// k + dk mod nx) holding (x, y), from the squared radii of ring j's
+// neighbours and the signs against sector k's neighbouring rays; 9 when the
+// particle is farther or outside r_out.
+__device__ __forceinline__ int neighbour_code_ann(const Params<float>& p, int k, int j, float x, float y) {
+  const float r2 = x * x + y * y;
+  int dj = 0;
+  if (r2 < p.r2t[j]) {
+    if (j > 0) {
+      if (!(r2 >= p.r2t[j - 1])) return 9;
+      dj = -1;
+    }
+  } else if (!(r2 < p.r2t[j + 1])) {
+    if (j + 1 >= p.ny || !(r2 < p.r2t[j + 2])) return 9;
+    dj = 1;
+  }
+  const int nt = p.nx;
+  const float* ray = p.ray;
+  const bool lo = ray[2 * k] * y - ray[2 * k + 1] * x >= 0.f;
+  const bool up = ray[2 * k + 2] * y - ray[2 * k + 3] * x >= 0.f;
+  int dk = 0;
+  if (!lo) {
+    const int km = (k == 0) ? nt - 1 : k - 1;
+    if (!(ray[2 * km] * y - ray[2 * km + 1] * x >= 0.f)) return 9;
+    dk = -1;
+  } else if (up) {
+    const int kp = (k + 2 > nt) ? k + 2 - nt : k + 2;
+    if (!(ray[2 * kp] * y - ray[2 * kp + 1] * x < 0.f)) return 9;
+    dk = 1;
+  }
+  return (dj + 1) * 3 + (dk + 1);
+}
+
+__device__ __forceinline__ int neighbour_cell_ann(int nx, int cell, int code) {
+  const int j = cell / nx + code / 3 - 1;
+  int k = cell % nx + code % 3 - 1;
+  k = (k < 0) ? k + nx : (k >= nx ? k - nx : k);
+  return j * nx + k;
+}
+
 // warps per CTA of the fused step: 2 or 4, chosen per handle by timing both
 // on the handle's first long dsmc_step call (fused_tune)
 constexpr int FWPB_MAX = 4;
@@ -429,7 +666,7 @@ inline size_t fused_smem_bytes(int tile, int fwpb) { return (size_t)fwpb * tile 
 // destination bin reserves the slots; (M3) fly again (the same counter-based
 // random stream, so the same result) and store.  Counters are flushed by the
 // last warp of the block to finish, so warps never wait for one another.
-template <int DIM, bool BATCH, int FWPB>
+template <int DIM, bool BATCH, int FWPB, bool ANN>
 __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_constant__ Params<float> pk,
                                                         Cases<float> cases, int ncells, PBuf<float> in,
                                                         PBuf<float> out,
@@ -451,6 +688,7 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
   __shared__ float s_tally[20];
   __shared__ unsigned long long s_hits[2];
   __shared__ unsigned s_done;
+  __shared__ unsigned s_out;  // annulus: particles that left
   __shared__ int s_nb[FWPB][4][12];  // per warp: count, base, bin start, bin capacity
   __shared__ __align__(8) uint64_t s_bar[FWPB];
   if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
@@ -458,6 +696,7 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
   if (threadIdx.x < 20) s_tally[threadIdx.x] = 0.f;
   if (threadIdx.x < 2) s_hits[threadIdx.x] = 0;
   if (threadIdx.x == 0) s_done = 0;
+  if (threadIdx.x == 0) s_out = 0;
   if (threadIdx.x < FWPB) mbar_init(&s_bar[threadIdx.x], 1);
   mbar_fence_init();
   __syncthreads();
@@ -550,15 +789,20 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
           for (int q = lane; q < n; q += 32) {
             float xn, yn;
             int code = 9;
-            if (flight_stays_inside<float, DIM>(p, px[q], (DIM == 2) ? py[q] : 0.f, vx[q], vy[q], &xn, &yn))
-              code = neighbour_code<DIM>(p, cix, ciy, xn, yn);
+            if constexpr (ANN) {
+              if (ann_straight(p, px[q], py[q], vx[q], vy[q], &xn, &yn))
+                code = neighbour_code_ann(p, cix, ciy, xn, yn);
+            } else {
+              if (flight_stays_inside<float, DIM>(p, px[q], (DIM == 2) ? py[q] : 0.f, vx[q], vy[q], &xn, &yn))
+                code = neighbour_code<DIM>(p, cix, ciy, xn, yn);
+            }
             const int r = atomicAdd(&nb_cnt[code], 1);
             own[q] = ((uint32_t)code << 24) | (uint32_t)r;
           }
           __syncwarp();
           // M2: reserve the slots, one atomic per destination bin
           if (lane < 9 && nb_cnt[lane] > 0) {
-            const int d = neighbour_cell(p.nx, cell, lane);
+            const int d = ANN ? neighbour_cell_ann(p.nx, cell, lane) : neighbour_cell(p.nx, cell, lane);
             nb_base[lane] = atomicAdd(&cnt_out[d], nb_cnt[lane]);
             const int s0 = start[d];
             nb_s0[lane] = s0;
@@ -569,17 +813,32 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
           for (int q = lane; q < n; q += 32) {
             float x = px[q], y = (DIM == 2) ? py[q] : 0.f;
             float a = vx[q], b = vy[q], c = vz[q], e = ir[q];
-            fly<float, DIM, true>(p, x, y, a, b, c, e, (uint32_t)q, (uint32_t)lcell, step_m, s_tally,
-                                  &s_hits[0], &s_hits[1]);
             const uint32_t tag = own[q];
             const int code = (int)(tag >> 24), r = (int)(tag & 0xFFFFFFu);
+            if constexpr (ANN) {
+              if (code < 9) {
+                x = x + a * p.dt;
+                y = y + b * p.dt;
+              } else if (!fly_ann<float, true>(p, x, y, a, b, c, e, TAG_WALL, (uint32_t)q, (uint32_t)lcell, step_m, 0u,
+                                               p.dt, s_tally, &s_hits[0], &s_hits[1])) {
+                atomicAdd(&s_out, 1u);  // left through the outer circle
+                continue;
+              }
+            } else {
+              fly<float, DIM, true>(p, x, y, a, b, c, e, (uint32_t)q, (uint32_t)lcell, step_m, s_tally, &s_hits[0],
+                                    &s_hits[1]);
+            }
             int d = -1, slot, s0, cap;
             if (code < 9) {
               slot = nb_base[code] + r;
               s0 = nb_s0[code];
               cap = nb_cap[code];
             } else {
-              d = c0 + cell_of<float, DIM>(p, x, y);
+              d = ANN ? cell_of_ann<float>(p, x, y) : c0 + cell_of<float, DIM>(p, x, y);
+              if (ANN && d < 0) {
+                atomicAdd(&s_out, 1u);
+                continue;
+              }
               slot = atomicAdd(&cnt_out[d], 1);
               s0 = start[d];
               cap = start[d + 1] - s0;
@@ -596,7 +855,7 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
             } else {
               // reserved but unused slot: give it back (the bin's count ends
               // at its capacity)
-              if (d < 0) d = neighbour_cell(p.nx, cell, code);
+              if (d < 0) d = ANN ? neighbour_cell_ann(p.nx, cell, code) : neighbour_cell(p.nx, cell, code);
               atomicSub(&cnt_out[d], 1);
               const int qo = atomicAdd(ovo.count, 1);
               atomicAdd(s_misc + 0, 1u);
@@ -647,11 +906,19 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
         bb = ovi.vy[q];
         c = ovi.vz[q];
         e = ovi.ir[q];
-        fly<float, DIM, true>(p, x, y, a, bb, c, e, (uint32_t)q, (uint32_t)(p.ncells + 1), step_m, s_tally,
-                              &s_hits[0], &s_hits[1]);
-        d = c0 + cell_of<float, DIM>(p, x, y);
+        if constexpr (ANN) {
+          d = fly_ann<float, true>(p, x, y, a, bb, c, e, TAG_WALL, (uint32_t)q, (uint32_t)(p.ncells + 1), step_m, 0u,
+                                   p.dt, s_tally, &s_hits[0], &s_hits[1])
+                  ? cell_of_ann<float>(p, x, y)
+                  : -1;
+          if (d < 0) atomicAdd(&s_out, 1u);
+        } else {
+          fly<float, DIM, true>(p, x, y, a, bb, c, e, (uint32_t)q, (uint32_t)(p.ncells + 1), step_m, s_tally,
+                                &s_hits[0], &s_hits[1]);
+          d = c0 + cell_of<float, DIM>(p, x, y);
+        }
       }
-      append_particle<DIM>(pk, out, start, cnt_out, ovo, ovf_cap, active, d, x, y, a, bb, c, e, s_misc);
+      append_particle<DIM>(pk, out, start, cnt_out, ovo, ovf_cap, active && d >= 0, d, x, y, a, bb, c, e, s_misc);
     }
   }
   // the last warp of the block to finish flushes the block's counters
@@ -667,6 +934,7 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
     if (lane == 5 && s_misc[1]) atomicAdd(stats + ST_NEARFULL, (unsigned long long)s_misc[1]);
     if (lane == 6 && s_hits[0]) atomicAdd(stats + ST_HITS, s_hits[0]);
     if (lane == 7 && s_hits[1]) atomicAdd(stats + ST_MAXHIT, s_hits[1]);
+    if (lane == 8 && s_out) atomicAdd(stats + ST_OUT, (unsigned long long)s_out);
     if (lane < 20 && s_tally[lane] != 0.f) atomicAdd(tally_g + lane, (double)s_tally[lane]);
   }
 }
@@ -689,7 +957,7 @@ static __global__ void k_rebin_add_ovf(const Ovf ov, int ovf_cap, int32_t* __res
 __device__ __forceinline__ int32_t nominal_count(const CellParams* cps, const int32_t* cell_case, int c) {
   if (!cps) return 0;
   const CellParams& cp = cps[cell_case[c]];
-  return (int32_t)(cp.vcell / cp.fnum + 0.5);
+  return (int32_t)((cp.vol ? cp.vol[c] : cp.vcell) / cp.fnum + 0.5);
 }
 
 static __global__ void __launch_bounds__(1024) k_caps_scan(const int32_t* __restrict__ tot, int ncells,
@@ -785,11 +1053,14 @@ __global__ void __launch_bounds__(WPB * 32) k_export(PBuf<T> b, const int32_t* _
   }
 }
 
+// DIM 3: the annulus (key -1 outside it)
 template <typename T, int DIM>
 __global__ void k_keys_from_pos(Params<T> p, const double* __restrict__ x, const double* __restrict__ y,
                                 int n, int32_t* __restrict__ key) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
-    key[s] = cell_of<T, DIM>(p, (T)x[s], (DIM == 2) ? (T)y[s] : T(0));
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    if constexpr (DIM == 3) key[s] = cell_of_ann<T>(p, (T)x[s], (T)y[s]);
+    else key[s] = cell_of<T, DIM>(p, (T)x[s], (DIM == 2) ? (T)y[s] : T(0));
+  }
 }
 
 // FP32 import: occupancy of every cell (one atomic per group of lanes with
@@ -1148,12 +1419,20 @@ void Ops<T>::init(const Params<T>& p, State<T>& s, int cur, int lay, int ppc, in
 }
 
 template <typename T>
-void Ops<T>::init_batch(const Params<T>& p0, State<T>& s, int ncells, int cur, int lay, cudaStream_t st) {
+void Ops<T>::init_batch(const Params<T>& p0, State<T>& s, int ncells, int cur, int lay, cudaStream_t st,
+                        const int32_t* counts) {
   const int blocks = (ncells * 32 + 255) / 256;
   if (p0.dim == 1)
-    k_init_cells<T, 1><<<blocks, 256, 0, st>>>(s.cases, ncells, s.buf[cur], s.start[lay], s.count[lay], s.cellof);
+    k_init_cells<T, 1><<<blocks, 256, 0, st>>>(s.cases, ncells, s.buf[cur], s.start[lay], s.count[lay], s.cellof,
+                                               counts);
   else
-    k_init_cells<T, 2><<<blocks, 256, 0, st>>>(s.cases, ncells, s.buf[cur], s.start[lay], s.count[lay], s.cellof);
+    k_init_cells<T, 2><<<blocks, 256, 0, st>>>(s.cases, ncells, s.buf[cur], s.start[lay], s.count[lay], s.cellof,
+                                               counts);
+}
+
+template <typename T>
+void Ops<T>::ann_counts(const Params<double>& pd, int ncells, int32_t* counts, cudaStream_t st) {
+  k_ann_counts<<<grid_for(ncells, 256), 256, 0, st>>>(pd, ncells, counts);
 }
 
 template <typename T>
@@ -1178,27 +1457,48 @@ void Ops<T>::step_det(const Params<T>& p, State<T>& s, int& cur, int& lay, uint3
   const int other = cur ^ 1, olay = lay ^ 1;
   if (n > 0) {
     const int g = grid_for(n, 256);
-    if (p.dim == 1) {
+    if (p.mesh == 1) {
+      k_move_det<T, 2, false, true><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step,
+                                                       s.key, s.tally, s.stats);
+    } else if (p.dim == 1) {
       if (s.batch)
-        k_move_det<T, 1, true><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step, s.key,
-                                                   s.tally, s.stats);
+        k_move_det<T, 1, true, false><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step,
+                                                         s.key, s.tally, s.stats);
       else
-        k_move_det<T, 1, false><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step, s.key,
-                                                    s.tally, s.stats);
+        k_move_det<T, 1, false, false><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step,
+                                                          s.key, s.tally, s.stats);
     } else {
       if (s.batch)
-        k_move_det<T, 2, true><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step, s.key,
-                                                   s.tally, s.stats);
+        k_move_det<T, 2, true, false><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step,
+                                                         s.key, s.tally, s.stats);
       else
-        k_move_det<T, 2, false><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step, s.key,
-                                                    s.tally, s.stats);
+        k_move_det<T, 2, false, false><<<g, 256, 0, st>>>(p, s.cases, s.buf[cur], s.cellof, s.start[lay], n, step,
+                                                          s.key, s.tally, s.stats);
     }
   }
+  int ntot = n;
+  if (p.mesh == 1) {
+    // annulus: freestream entry after the moved particles; the host learns
+    // how many slots it used, the sort drops the particles that left
+    k_inject_det<T><<<1, 1024, 0, st>>>(s.pinj, s.buf[cur], s.key, n, (long long)s.capacity, step, s.nt, s.tmp2,
+                                        s.flags, s.tally, s.stats);
+    int32_t add = 0;
+    cudaMemcpyAsync(&add, s.tmp2 + p.nx, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    const long long tot = (long long)n + add;
+    ntot = (int)(tot < s.capacity ? tot : s.capacity);
+  }
   const PBuf<T>& a = s.buf[cur];
-  k_sort_stable<T, T><<<1, 1024, 0, st>>>(a.x, a.y, a.vx, a.vy, a.vz, a.ir, s.buf[other], s.key, n, ncells,
+  k_sort_stable<T, T><<<1, 1024, 0, st>>>(a.x, a.y, a.vx, a.vy, a.vz, a.ir, s.buf[other], s.key, ntot, ncells,
                                           s.start[olay], s.count[olay], s.tmp2, s.dest, s.cellof);
   cur = other;
   lay = olay;
+  if (p.mesh == 1) {
+    int32_t kept = 0;
+    cudaMemcpyAsync(&kept, s.start[lay] + ncells, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    s.nparticles = kept;
+  }
   const int flags = 1 | (do_sample ? 2 : 0);
   if (s.batch)
     launch_collide_sample<T, true>(p, s, ncells, s.buf[cur], s.start[lay], s.count[lay], step, flags, nullptr,
@@ -1223,26 +1523,35 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
   p, s.cases, ncells, s.buf[cur], s.buf[other], s.start[lay], s.count[cur], s.count[other], s.sgmax, s.acc,      \
       s.comp, s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats, \
       s.flags + 8, s.stg, s.stc
-#define DSMC_FUSED_LAUNCH(D, B, W) k_fused<D, B, W><<<cblocks + oblocks, W * 32, smf, st>>>(DSMC_FUSED_ARGS)
-      if (F == 2) {
+#define DSMC_FUSED_LAUNCH(D, B, W, A) k_fused<D, B, W, A><<<cblocks + oblocks, W * 32, smf, st>>>(DSMC_FUSED_ARGS)
+      if (p.mesh == 1) {
+        if (F == 2) DSMC_FUSED_LAUNCH(2, false, 2, true);
+        else DSMC_FUSED_LAUNCH(2, false, 4, true);
+      } else if (F == 2) {
         if (p.dim == 1) {
-          if (s.batch) DSMC_FUSED_LAUNCH(1, true, 2);
-          else DSMC_FUSED_LAUNCH(1, false, 2);
+          if (s.batch) DSMC_FUSED_LAUNCH(1, true, 2, false);
+          else DSMC_FUSED_LAUNCH(1, false, 2, false);
         } else {
-          if (s.batch) DSMC_FUSED_LAUNCH(2, true, 2);
-          else DSMC_FUSED_LAUNCH(2, false, 2);
+          if (s.batch) DSMC_FUSED_LAUNCH(2, true, 2, false);
+          else DSMC_FUSED_LAUNCH(2, false, 2, false);
         }
       } else {
         if (p.dim == 1) {
-          if (s.batch) DSMC_FUSED_LAUNCH(1, true, 4);
-          else DSMC_FUSED_LAUNCH(1, false, 4);
+          if (s.batch) DSMC_FUSED_LAUNCH(1, true, 4, false);
+          else DSMC_FUSED_LAUNCH(1, false, 4, false);
         } else {
-          if (s.batch) DSMC_FUSED_LAUNCH(2, true, 4);
-          else DSMC_FUSED_LAUNCH(2, false, 4);
+          if (s.batch) DSMC_FUSED_LAUNCH(2, true, 4, false);
+          else DSMC_FUSED_LAUNCH(2, false, 4, false);
         }
       }
 #undef DSMC_FUSED_LAUNCH
 #undef DSMC_FUSED_ARGS
+      if (p.mesh == 1 && (flags & 4)) {
+        // annulus: freestream entry into the bins of the step just moved
+        const int wpb = 8, fb = (p.nx + wpb - 1) / wpb;
+        k_inject_bins<<<fb, wpb * 32, 0, st>>>(s.pinj, p, s.buf[other], s.start[lay], s.count[other], s.ovf[other],
+                                               s.ovf_cap, sm_step, s.tally, s.stats);
+      }
       // the input overflow list has been consumed
       cudaMemsetAsync(s.ovf[cur].count, 0, sizeof(int32_t), st);
       cur = other;
@@ -1351,7 +1660,9 @@ void Ops<T>::import_particles(const Params<T>& p, State<T>& s, int& cur, int& la
                               const double* ir, int det, cudaStream_t st) {
   const int other = cur ^ 1, olay = lay ^ 1;
   if (n > 0) {
-    if (p.dim == 1)
+    if (p.mesh == 1)
+      k_keys_from_pos<T, 3><<<grid_for(n, 256), 256, 0, st>>>(p, x, y, (int)n, s.key);
+    else if (p.dim == 1)
       k_keys_from_pos<T, 1><<<grid_for(n, 256), 256, 0, st>>>(p, x, y, (int)n, s.key);
     else
       k_keys_from_pos<T, 2><<<grid_for(n, 256), 256, 0, st>>>(p, x, y, (int)n, s.key);
@@ -1364,6 +1675,13 @@ void Ops<T>::import_particles(const Params<T>& p, State<T>& s, int& cur, int& la
                                                  s.start[olay], s.count[olay], s.tmp2, s.dest, s.cellof);
     cur = other;
     lay = olay;
+    if (p.mesh == 1) {
+      // particles outside the annulus were dropped
+      int32_t kept = 0;
+      cudaMemcpyAsync(&kept, s.start[lay] + p.ncells, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      s.nparticles = kept;
+    }
     if (p.dim == 1) cudaMemsetAsync(s.buf[cur].y, 0, sizeof(T) * (size_t)n, st);
     return;
   }
@@ -1437,14 +1755,16 @@ void Ops<T>::configure(int tile) {
   cudaFuncSetAttribute(k_dig_apply<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
   if constexpr (sizeof(T) == 4) {
     const int sm4 = (int)fused_smem_bytes(tile, 4), sm2 = (int)fused_smem_bytes(tile, 2);
-    cudaFuncSetAttribute(k_fused<1, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
-    cudaFuncSetAttribute(k_fused<2, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
-    cudaFuncSetAttribute(k_fused<1, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
-    cudaFuncSetAttribute(k_fused<2, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
-    cudaFuncSetAttribute(k_fused<1, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
-    cudaFuncSetAttribute(k_fused<2, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
-    cudaFuncSetAttribute(k_fused<1, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
-    cudaFuncSetAttribute(k_fused<2, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<2, false, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<2, false, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<1, false, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<2, false, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<1, true, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<2, true, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<1, false, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<2, false, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<1, true, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<2, true, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
   }
 }
 

@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -17,10 +18,11 @@ from . import build as _build
 DSMC_OK = 0
 ERRORS = {-1: "DSMC_ERR_ARG", -2: "DSMC_ERR_CAPACITY", -3: "DSMC_ERR_NUMERIC",
           -4: "DSMC_ERR_NOT_CONVERGED", -5: "DSMC_ERR_TIMEOUT", -6: "DSMC_ERR_CUDA"}
-ABI_VERSION = 1
+ABI_VERSION = 2
 NFIELDS, NHOT, NTARGET, NMOM = 18, 12, 6, 17
 PREC = {"fp64": 0, "fp32": 1}
 WALL = {"diffuse": 0, "specular": 1}
+MESH = {"box": 0, "annulus": 1}
 
 # every symbol the header declares
 SYMBOLS = ["dsmc_workspace_size", "dsmc_init", "dsmc_destroy", "dsmc_last_error", "dsmc_step", "dsmc_sample",
@@ -29,7 +31,7 @@ SYMBOLS = ["dsmc_workspace_size", "dsmc_init", "dsmc_destroy", "dsmc_last_error"
            "dsmc_get_counters", "dsmc_set_counters", "dsmc_get_stats", "dsmc_get_wall_tally",
            "dsmc_get_constants", "synth_solve_noalloc", "dsmc_batch_workspace_size", "dsmc_batch_init",
            "hot_mlp_init", "hot_mlp_set_params", "hot_mlp_get_params", "hot_mlp_grad", "hot_mlp_train",
-           "hot_mlp_apply", "dsmc_get_launch_config"]
+           "hot_mlp_apply", "dsmc_get_launch_config", "dsmc_get_flow", "dsmc_get_volumes"]
 MLP_NPARAM = 9477
 
 
@@ -51,6 +53,9 @@ class DsmcConfig(ctypes.Structure):
         ("kn_ref", ctypes.c_double), ("synth_tol", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("capacity", ctypes.c_int64),
         ("bin_slack", ctypes.c_double),
+        ("mesh", ctypes.c_int32), ("pad1", ctypes.c_int32),
+        ("r_in", ctypes.c_double), ("r_out", ctypes.c_double), ("stretch", ctypes.c_double),
+        ("fs_rho", ctypes.c_double), ("fs_t", ctypes.c_double), ("fs_u", ctypes.c_double * 3),
     ]
 
 
@@ -106,6 +111,8 @@ def load(build_if_missing: bool = True):
         "dsmc_batch_init": ([P, ctypes.c_int, P, ctypes.c_size_t, P, P], ctypes.c_int),
         "hot_mlp_init": ([H, ctypes.c_uint64], ctypes.c_int),
         "dsmc_get_launch_config": ([H, P], ctypes.c_int),
+        "dsmc_get_flow": ([H, P], ctypes.c_int),
+        "dsmc_get_volumes": ([H, P], ctypes.c_int),
         "hot_mlp_set_params": ([H, P], ctypes.c_int),
         "hot_mlp_get_params": ([H, P], ctypes.c_int),
         "hot_mlp_grad": ([H, P, P, P, P, P, P], ctypes.c_int),
@@ -145,6 +152,12 @@ def make_config(cfg: dict) -> DsmcConfig:
     c.seed = int(cfg.get("seed", 0))
     c.capacity = int(cfg.get("capacity", 0) or 0)
     c.bin_slack = float(cfg.get("bin_slack", 2.0))
+    c.mesh = MESH[cfg.get("mesh", "box")]
+    c.r_in, c.r_out = float(cfg.get("r_in", 0.5)), float(cfg.get("r_out", 5.5))
+    c.stretch = float(cfg.get("stretch", 1.0))
+    c.fs_rho, c.fs_t = float(cfg.get("fs_rho", 1.0)), float(cfg.get("fs_t", 1.0))
+    for k in range(3):
+        c.fs_u[k] = float(cfg.get("fs_u", (0.0, 0.0, 0.0))[k])
     return c
 
 
@@ -339,6 +352,19 @@ class Dsmc:
         self._check(load().dsmc_get_stats(self._h, out))
         return dict(zip(("n_cand", "n_coll", "n_clip", "n_inel", "n_hits", "n_maxhit", "n_overflow", "n_rebuild"),
                         list(out)))
+
+    def flow(self) -> dict:
+        """Annulus: particles that entered through the outer circle and that
+        left through it since the start."""
+        out = np.zeros(2, np.int64)
+        self._check(load().dsmc_get_flow(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return {"n_in": int(out[0]), "n_out": int(out[1])}
+
+    def volumes(self) -> np.ndarray:
+        """Cell volumes (areas per unit depth in 2D)."""
+        out = np.zeros(self.ncells, np.float64)
+        self._check(load().dsmc_get_volumes(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
 
     def wall_tally(self):
         out = (ctypes.c_double * 20)()

@@ -118,6 +118,8 @@ def radial_stretch(dr1: float, nr: int, span: float) -> float:
     if dr1 * nr >= span:
         return 1.0
     lo, hi = 1.0 + 1e-12, 2.0
+    while dr1 * (hi ** nr - 1.0) / (hi - 1.0) < span:
+        lo, hi = hi, 2.0 * hi
     for _ in range(200):
         q = 0.5 * (lo + hi)
         if dr1 * (q ** nr - 1.0) / (q - 1.0) > span:

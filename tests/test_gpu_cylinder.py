@@ -1,0 +1,166 @@
+"""GPU flow past a cylinder (annular mesh, Sec. 5) against the oracle.
+
+FP64-deterministic mode: particle states, (sigma g)_max, event counts, wall
+tallies and the entry / exit counts equal the oracle's over 10 steps
+(relative 1e-12), on uniform and stretched rings, with particles entering
+and leaving every step.  FP32 mode: the particle count obeys n = n0 +
+entered - left exactly; free-molecular drag and hit rate on the cylinder
+against the surface integral of the freestream fluxes; in a gas at rest the
+collision count follows the equilibrium collision frequency with per-cell
+volumes and the density stays uniform; the full-size 400 x 300 workload
+runs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2501_10965_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("x", "y", "vx", "vy", "vz", "ir")
+
+
+def _gpu(cfg):
+    from paper_2501_10965_gb300 import dsmc
+    return dsmc.Dsmc(cfg)
+
+
+def _np(p):
+    return {k: v.cpu().numpy() for k, v in p.items()}
+
+
+def _compare_states(g, o, rtol=1e-12, what=""):
+    assert len(g["x"]) == len(o["x"]), f"{what}: particle count {len(g['x'])} vs {len(o['x'])}"
+    assert np.array_equal(g["cell"], o["cell"]), f"{what}: cell order differs"
+    for k in KEYS:
+        err = np.abs(g[k] - o[k]) / np.maximum(np.abs(o[k]), 1.0)
+        i = int(np.argmax(err)) if len(err) else 0
+        assert len(err) == 0 or err.max() <= rtol, f"{what}: {k} differs at {i}: {g[k][i]!r} vs {o[k][i]!r}"
+
+
+def _small(**kw):
+    base = dict(ntheta=24, nr=8, ppc=20, kn=0.1, mach=2.0, t_wall=2.0, r_in=0.5, r_out=2.5, dr1=0.25,
+                precision="fp64")
+    base.update(kw)
+    return W.cylinder_2d(**base)
+
+
+@pytest.mark.parametrize("dr1", [0.25, 0.05])
+def test_cylinder_steps_match_oracle_fp64(dr1):
+    cfg = _small(dr1=dr1)
+    g = _gpu(cfg)
+    o = oracle.OracleSim(cfg)
+    np.testing.assert_array_equal(g.volumes(), o.volumes())
+    _compare_states(_np(g.get_particles()), o.particles(), what="init")
+    counts = []
+    for k in range(10):
+        g.dsmc_step(1)
+        o.step(1)
+        _compare_states(_np(g.get_particles()), o.particles(), what=f"step {k}")
+        counts.append(o.n)
+    assert np.allclose(g.sgmax().cpu().numpy(), o.sgmax(), rtol=1e-12, atol=0)
+    gs, os_ = g.stats(), o.stats()
+    for key in ("n_cand", "n_coll", "n_clip", "n_inel", "n_hits", "n_maxhit"):
+        assert gs[key] == os_[key], (key, gs[key], os_[key])
+    assert gs["n_hits"] > 0 and gs["n_coll"] > 0
+    fg, fo = g.flow(), o.flow()
+    assert fg == fo and fo["n_in"] > 0 and fo["n_out"] > 0, (fg, fo)
+    np.testing.assert_allclose(np.array(g.wall_tally()[0]), o.wall_tally()[0], rtol=1e-11, atol=1e-12)
+
+
+def _free_molecular_cylinder(rho, U, T, Tw, R, nphi=20000):
+    """Force (x) and hit rate per unit length on a cylinder in a free-molecular
+    freestream with diffuse re-emission at Tw (truncated-normal moments of
+    the speed into the wall, integrated over the surface)."""
+    phi = (np.arange(nphi) + 0.5) * (2.0 * np.pi / nphi)
+    sd = math.sqrt(T)
+    mu = -U * np.cos(phi)
+    a = mu / sd
+    Phi = 0.5 * (1.0 + np.vectorize(math.erf)(a / math.sqrt(2.0)))
+    pdf = np.exp(-0.5 * a * a) / math.sqrt(2.0 * math.pi)
+    g1 = mu * Phi + sd * pdf
+    g2 = (mu * mu + T) * Phi + mu * sd * pdf
+    gamma = rho * g1
+    fx = -rho * g2 * np.cos(phi) + U * np.sin(phi) ** 2 * gamma - gamma * math.sqrt(math.pi * Tw / 2.0) * np.cos(phi)
+    dphi = 2.0 * np.pi / nphi
+    return float(fx.sum() * R * dphi), float(gamma.sum() * R * dphi)
+
+
+def test_cylinder_fp32_free_molecular_drag_and_particle_balance():
+    cfg = _small(ntheta=48, nr=6, ppc=40, dr1=1.0, collisions=False, precision="fp32")
+    g = _gpu(cfg)
+    n0 = g.num_particles()
+    c = g.constants()
+    U, dt = cfg["fs_u"][0], cfg["dt"]
+    fx_ref, hits_ref = _free_molecular_cylinder(1.0, U, 1.0, 2.0, 0.5)
+    batches, K = 20, 300
+    fx, hits = [], []
+    for _ in range(batches):
+        w0 = np.array(g.wall_tally()[0])
+        g.dsmc_step(K)
+        d = np.array(g.wall_tally()[0]) - w0
+        fx.append(d[1] * c["fnum"] / (K * dt))
+        hits.append(d[0] * c["fnum"] / (K * dt))
+    for got, ref in ((np.array(fx), fx_ref), (np.array(hits), hits_ref)):
+        m, se = got.mean(), got.std(ddof=1) / math.sqrt(batches)
+        assert abs(m - ref) <= 4.0 * se + 0.003 * abs(ref), (m, se, ref)
+    f = g.flow()
+    assert f["n_in"] > 1000 and f["n_out"] > 1000
+    assert g.num_particles() == n0 + f["n_in"] - f["n_out"]
+    assert g.stats()["n_maxhit"] == 0
+
+
+def test_cylinder_fp32_gas_at_rest_collision_rate_and_uniform_density():
+    """Stretched rings (cell volumes differ 30-fold): the accepted collisions
+    per step follow N nu dt / 2 with the equilibrium collision frequency nu
+    = K / mu_ref (rho = T = 1), and the ring densities stay 1."""
+    cfg = _small(ntheta=48, nr=8, ppc=40, mach=0.0, t_wall=1.0, dr1=0.05, precision="fp32")
+    assert cfg["stretch"] > 1.2
+    g = _gpu(cfg)
+    c = g.constants()
+    nt, nr = 48, 8
+    g.dsmc_step(100)
+    g.dsmc_sample(reset=True)
+    c0 = g.stats()["n_coll"]
+    steps, nsum = 0, 0
+    for _ in range(20):
+        nsum += 10 * g.num_particles()
+        g.dsmc_step(10, sample=True)
+        steps += 10
+    coll = g.stats()["n_coll"] - c0
+    nu = c["k_visc"] / c["mu_ref"]
+    expect = 0.5 * nu * cfg["dt"] * nsum
+    assert abs(coll / expect - 1.0) < 0.03, (coll, expect)
+    f = g.dsmc_sample(reset=True).cpu().numpy()
+    vol = g.volumes()
+    mass = (f[:, 0] * vol).reshape(nr, nt).sum(1)
+    ring = vol.reshape(nr, nt).sum(1)
+    rho = mass / ring
+    assert np.all(np.abs(rho - 1.0) < 0.05), rho
+    T = (3.0 * f[:, 4] + 2.0 * f[:, 5]) / 5.0
+    assert abs(np.average(T, weights=f[:, 0] * vol) - 1.0) < 0.01
+
+
+def test_cylinder_fp32_full_size_workload():
+    """The 400 x 300 annulus of the Mach 5 cylinder case (~20 M particles):
+    a few steps run, the particle count balances exactly, the fields are
+    finite and the freestream density holds at the outer boundary."""
+    cfg = W.cylinder_2d()
+    g = _gpu(cfg)
+    n0 = g.num_particles()
+    assert abs(n0 / (400 * 300 * 167) - 1.0) < 0.01
+    g.dsmc_step(20, sample=True)
+    f = g.flow()
+    assert g.num_particles() == n0 + f["n_in"] - f["n_out"]
+    assert f["n_in"] > 0 and f["n_out"] > 0
+    fields = g.dsmc_sample(reset=True).cpu().numpy()
+    assert np.isfinite(fields).all()
+    outer = fields.reshape(300, 400, -1)[-20:, :, 0]
+    assert abs(outer.mean() - 1.0) < 0.05, outer.mean()
+    st = g.stats()
+    assert st["n_hits"] > 0 and st["n_coll"] > 0 and st["n_maxhit"] == 0

@@ -89,8 +89,11 @@ def test_entry_count_is_the_one_sided_flux():
     cfg = _cfg(ntheta=48, nr=4, ppc=10, mach=2.0, collisions=False)
     o = oracle.OracleSim(cfg)
     c = o.constants()
+    n0 = o.n
     steps = 2000
     o.step(steps)
+    f = o.flow()
+    assert o.n == n0 + f["n_in"] - f["n_out"] and f["n_out"] > 0
     nt, U, dt = 48, cfg["fs_u"][0], cfg["dt"]
     th = 2.0 * np.pi * (np.arange(nt) + 0.5) / nt
     un = -U * np.cos(th)  # freestream along x, inward normal -(cos, sin)
