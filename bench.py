@@ -3,10 +3,13 @@ steady state of DIG against plain DSMC.
 
 A step is one DSMC time step of the whole particle path (free flight with
 diffuse walls, cell indexing and bin sort, NTC/VHS/Borgnakke-Larsen
-collisions, cell sampling) over the workload's full particle state, which
-stays resident in HBM.  The default workload is a 2D lid-driven cavity at the
-scale of the paper's cylinder case: 400 x 300 cells, 167 particles per cell
-(20.0 M particles), Kn 0.01, FP32 particles with FP64 moment accumulators.
+collisions, cell sampling, and on the annulus the freestream entry) over the
+workload's full particle state, which stays resident in HBM.  The default
+workload is the paper's hypersonic cylinder case: Mach 5 N2-like freestream
+at 200 K past a diffuse cylinder at 500 K, annular mesh of 400 x 300 cells
+(geometrically stretched rings), ~167 particles per cell (20.0 M particles),
+Kn 0.01, FP32 particles with FP64 moment accumulators.  `cavity2d_20m` is a
+lid-driven cavity of the same size.
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead, on a
 bounded sample of the same workload (rank 0 only).
@@ -29,16 +32,21 @@ if ROOT not in sys.path:
 
 ALGO_BYTES_PER_PARTICLE_STEP = {("fp32", 2): 48, ("fp32", 1): 40, ("fp64", 2): 96, ("fp64", 1): 80}
 # DRAM bytes (read + write) per particle-step of k_fused, from one ncu capture
-# of the current kernel on the 300 x 225-cell, 11.27 M-particle cavity
-# (dram__bytes_read.sum 336.86 MB + dram__bytes_write.sum 243.33 MB for one
-# launch; profiles/k_fused_cavity2d.md); scaled to a launch of the workload by
-# its particle count.  Re-measure whenever k_fused changes.
-NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP = {("fp32", 2): 580182784 / 11272500}
+# of the current kernel, scaled to a launch of the workload by its particle
+# count; keyed by (precision, dim, mesh).  Box: the 300 x 225-cell, 11.27
+# M-particle cavity (dram__bytes_read.sum 336.86 MB + dram__bytes_write.sum
+# 243.33 MB for one launch; profiles/k_fused_cavity2d.md).  Re-measure
+# whenever k_fused changes.
+NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP = {("fp32", 2, "box"): 580182784 / 11272500}
 METRIC = "particle-steps/s"
 
 
 def workload(name: str) -> dict:
     from paper_2501_10965_gb300 import workloads as W
+    if name == "cylinder2d_20m":
+        return W.cylinder_2d()
+    if name == "cylinder2d_11m":
+        return W.cylinder_2d(ntheta=300, nr=225)
     if name == "cavity2d_20m":
         return W.cavity_2d_20m()
     if name == "cavity2d_11m":
@@ -145,7 +153,12 @@ def cpu_baseline(cfg: dict, budget_s: float = 12.0) -> dict:
     import oracle
     sub = dict(cfg)
     sub["precision"] = "fp64"
-    if int(cfg["dim"]) == 2:
+    if cfg.get("mesh") == "annulus":
+        # the same annulus, gas, Kn, particles per cell and time step on 40 x 30 cells
+        from paper_2501_10965_gb300 import workloads as W
+        sub = W.cylinder_2d(ntheta=40, nr=30, ppc=int(cfg["ppc"]), kn=float(cfg["kn"]), r_in=float(cfg["r_in"]),
+                            r_out=float(cfg["r_out"]), dt=float(cfg["dt"]), precision="fp64")
+    elif int(cfg["dim"]) == 2:
         sub["nx"], sub["ny"] = 40, 30
         sub["lx"] = float(cfg["lx"]) * 40 / int(cfg["nx"])
         sub["ly"] = float(cfg["ly"]) * 30 / int(cfg["ny"])
@@ -243,7 +256,11 @@ def run_gpu(args):
         tt = torch.tensor([t], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
-    value = n * args.steps * world / t
+    # particle-steps: the count changes on the annulus (entry and exit), so
+    # the mean of the counts before and after the timed steps
+    n_end = sim.num_particles()
+    n_mean = 0.5 * (n + n_end)
+    value = n_mean * args.steps * world / t
     cfg_line_shape = sim.launch_config()
 
     # average duration of one fused step kernel: difference of two runs with
@@ -254,14 +271,16 @@ def run_gpu(args):
     t1 = min(_events_time(lambda: sim.dsmc_step(k1, sample=True), stream) for _ in range(2))
     t2 = min(_events_time(lambda: sim.dsmc_step(k2, sample=True), stream) for _ in range(2))
     per_launch = (t2 - t1) / (k2 - k1)
+    n = sim.num_particles()
     algo = ALGO_BYTES_PER_PARTICLE_STEP[(prec, dim)] * n
+    mesh = cfg.get("mesh", "box")
     peaks = measured_peaks()
     achieved = algo / per_launch / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 "traffic": args.traffic if args.traffic is not None else (
-                    NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP[(prec, dim)] * n
-                    if (prec, dim) in NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP else None),
+                    NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP[(prec, dim, mesh)] * n
+                    if (prec, dim, mesh) in NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP else None),
                 "kernel": "k_fused (collide + sample + move + bin append, one launch per step)",
                 "algorithmic_bytes_per_launch": algo, "launch_ms": per_launch * 1e3,
                 "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
@@ -282,8 +301,9 @@ def run_gpu(args):
         f = sim.dsmc_sample(reset=True)
         fields_host.copy_(f, non_blocking=True)
     barrier()
+    n_up = len(host["x"])
     te = _events_time(e2e, stream)
-    e2e_value = n * args.steps * world / te
+    e2e_value = 0.5 * (n_up + sim.num_particles()) * args.steps * world / te
     stats = sim.stats()
     ncells = sim.ncells
 
@@ -321,7 +341,7 @@ def run_gpu(args):
                 "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
                 "data": "synthetic",
-                "config": {"workload": args.workload, "cells": ncells, "particles": n,
+                "config": {"workload": args.workload, "cells": ncells, "particles": n_mean,
                            "particles_per_cell": cfg["ppc"], "kn": cfg["kn"], "dt": cfg["dt"],
                            "precision": prec + " particles, fp64 compensated moments",
                            "l2": "inputs larger than L2 (particle state %.2f GB)" % (n * 24 / 1e9),
@@ -345,7 +365,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="cavity2d_20m")
+    ap.add_argument("--workload", default="cylinder2d_20m")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per fused launch from an ncu capture of the current kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")

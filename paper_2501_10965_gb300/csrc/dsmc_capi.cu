@@ -48,8 +48,18 @@ struct dsmc_handle {
   // annulus tables (device): squared ring radii, rays, outer-face
   // directions, cell volumes, in FP64 and FP32
   double *ann_r2t_d = nullptr, *ann_ray_d = nullptr, *ann_fn_d = nullptr, *ann_vol_d = nullptr;
+  double* ann_mu_d = nullptr;  // expected freestream entries of every outer face per step
   float *ann_r2t_f = nullptr, *ann_ray_f = nullptr, *ann_fn_f = nullptr, *ann_vol_f = nullptr;
   std::string err;
+  ~dsmc_handle() {
+    // the side stream of the annulus's freestream entry (FP32 layout)
+    if (sf.side) {
+      cudaStreamSynchronize(sf.side);
+      cudaStreamDestroy(sf.side);
+    }
+    if (sf.ev_fork) cudaEventDestroy(sf.ev_fork);
+    if (sf.ev_join) cudaEventDestroy(sf.ev_join);
+  }
 };
 
 namespace {
@@ -264,7 +274,9 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
   float* a_rayf = cv.take<float>(nray);
   float* a_fnf = cv.take<float>(nfn);
   float* a_volf = cv.take<float>(nvol);
+  double* a_mu = cv.take<double>(ann ? (size_t)cs[0].nx : 1);
   if (h) {
+    h->ann_mu_d = a_mu;
     h->ann_r2t_d = a_r2d;
     h->ann_ray_d = a_rayd;
     h->ann_fn_d = a_fnd;
@@ -529,6 +541,27 @@ int init_state(dsmc_handle* h, State<T>& s, Params<T>& p0, Params<T>* d_p) {
     if (c->dim == 1) wacc += (int64_t)synth1d_work_doubles(h->nx[k]);
   }
   s.pinj = h->pd;
+  s.inj_mu = nullptr;
+  s.inj_max = 0;
+  if (ann) {
+    // expected entries per face and step, and a bound on one step's entries
+    std::vector<double> mu(h->cfg.nx);
+    Ops<T>::inflow_means(h->pd, h->ann_mu_d, st);
+    cudaMemcpyAsync(mu.data(), h->ann_mu_d, sizeof(double) * mu.size(), cudaMemcpyDeviceToHost, st);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_err(h, DSMC_ERR_CUDA, "dsmc_init: %s", cudaGetErrorString(e));
+    long long bound = 0;
+    for (double m : mu) bound += (long long)std::floor(m) + 1;
+    if (bound > (1LL << 30)) return set_err(h, DSMC_ERR_ARG, "freestream entry too large per step");
+    s.inj_mu = h->ann_mu_d;
+    s.inj_max = (int)bound;
+    if (!h->det) {
+      if (cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return set_err(h, DSMC_ERR_CUDA, "dsmc_init: side stream");
+    }
+  }
   start[nc] = slot;
   if ((int64_t)slot > s.capacity)
     return set_err(h, DSMC_ERR_CAPACITY, "initial bins need %lld slots, capacity %lld", (long long)slot,

@@ -296,6 +296,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // generic-proxy accesses to shared memory are ordered before later
 // async-proxy (bulk copy) accesses
+// generic-proxy writes to global memory before later bulk copies read it
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -517,11 +522,12 @@ __device__ __forceinline__ double inflow_ginf(double s) {
 // Newton steps kept inside a bisection bracket, at most 100 of them.
 __device__ inline double inflow_speed(double s, double u) {
   const double target = u * inflow_ginf(s);
+  const double es = exp(-s * s), cs = erfc(-s);  // loop invariants
   double lo = 0.0, hi = (s > 0.0 ? s : 0.0) + 8.0;
   double z = 0.5 * (lo + hi);
   for (int it = 0; it < 100; ++it) {
     const double w = z - s;
-    const double g = 0.5 * (exp(-s * s) - exp(-w * w)) + s * (0.5 * sqrt(PI_D)) * (erfc(-s) - erfc(w));
+    const double g = 0.5 * (es - exp(-w * w)) + s * (0.5 * sqrt(PI_D)) * (cs - erfc(w));
     const double f = g - target;
     if (f > 0.0) hi = z;
     else lo = z;
@@ -843,15 +849,10 @@ __device__ __forceinline__ float halving_sum17(const float* v, int lane) {
 // pre32 holds the lane's (stg, stc) loaded earlier).  With `flush` the staged
 // sum is folded into the compensated FP64 accumulators (pre: the lane's acc,
 // comp) and the staging pair is cleared.
-__device__ __forceinline__ void sample_cell_staged(const float* __restrict__ vx, const float* __restrict__ vy,
-                                   const float* __restrict__ vz, const float* __restrict__ ir, int n, int mom,
-                                   double* __restrict__ acc, double* __restrict__ comp, const double* pre,
-                                   float* __restrict__ stg, float* __restrict__ stc, const float* pre32,
-                                   bool flush) {
+__device__ __forceinline__ void sample_accumulate(const float* __restrict__ vx, const float* __restrict__ vy,
+                                                  const float* __restrict__ vz, const float* __restrict__ ir, int n,
+                                                  float* s) {
   const int lane = threadIdx.x & 31;
-  float s[NMOM];
-#pragma unroll
-  for (int q = 0; q < NMOM; ++q) s[q] = 0.f;
   for (int q = lane; q < n; q += 32) {
     const float a = vx[q], b = vy[q], c = vz[q], e = ir[q];
     const float v2 = a * a + b * b + c * c;
@@ -873,7 +874,13 @@ __device__ __forceinline__ void sample_cell_staged(const float* __restrict__ vx,
     s[15] += e * b;
     s[16] += e * c;
   }
-  const float tot = halving_sum17(s, lane);
+}
+
+// the cell's sum of moment `mom` (tot, this lane's) staged / folded as
+// described above
+__device__ __forceinline__ void sample_fold(float tot, int mom, double* __restrict__ acc, double* __restrict__ comp,
+                                            const double* pre, float* __restrict__ stg, float* __restrict__ stc,
+                                            const float* pre32, bool flush) {
   if (mom < 0) return;
   const float s0 = pre32[0], c0 = pre32[1];
   const float yk = tot - c0;
@@ -892,6 +899,29 @@ __device__ __forceinline__ void sample_cell_staged(const float* __restrict__ vx,
   const double cmp = (fabs(a) >= fabs(v)) ? ((a - t) + v) : ((v - t) + a);
   acc[mom] = t;
   comp[mom] = cprev + cmp;
+}
+
+__device__ __forceinline__ void sample_cell_staged(const float* __restrict__ vx, const float* __restrict__ vy,
+                                   const float* __restrict__ vz, const float* __restrict__ ir, int n, int mom,
+                                   double* __restrict__ acc, double* __restrict__ comp, const double* pre,
+                                   float* __restrict__ stg, float* __restrict__ stc, const float* pre32,
+                                   bool flush) {
+  float s[NMOM];
+#pragma unroll
+  for (int q = 0; q < NMOM; ++q) s[q] = 0.f;
+  sample_accumulate(vx, vy, vz, ir, n, s);
+  sample_fold(halving_sum17(s, threadIdx.x & 31), mom, acc, comp, pre, stg, stc, pre32, flush);
+}
+
+// one chunk of a cell's particles: its sums reduced across the warp (the
+// lane's moment returned, to be added over the chunks)
+__device__ __forceinline__ float sample_chunk(const float* __restrict__ vx, const float* __restrict__ vy,
+                                              const float* __restrict__ vz, const float* __restrict__ ir, int n) {
+  float s[NMOM];
+#pragma unroll
+  for (int q = 0; q < NMOM; ++q) s[q] = 0.f;
+  sample_accumulate(vx, vy, vz, ir, n, s);
+  return halving_sum17(s, threadIdx.x & 31);
 }
 
 }  // namespace dsmc

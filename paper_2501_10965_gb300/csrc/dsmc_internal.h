@@ -78,6 +78,13 @@ struct State {
   bool batch;  // several cases: kernels read their parameters per cell
   int fwpb;    // FP32 fused step: warps per CTA (0: not tuned yet)
   Params<double> pinj;  // annulus: FP64 parameters of the freestream entry
+  double* inj_mu;       // annulus: expected entries of every outer face per step
+  int inj_max;          // annulus: bound on the entries of one step (sum of floor(mu) + 1)
+  // annulus, FP32 layout: the freestream entry of a step runs on a side
+  // stream beside the fused step (both append to the next step's bins with
+  // atomics); fork after the previous launch, join before the next
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
 };
 
 template <typename T>
@@ -91,6 +98,8 @@ struct Ops {
                          const int32_t* counts = nullptr);
   // annulus: initial particles per cell (FP64 draws, both layouts)
   static void ann_counts(const Params<double>& pd, int ncells, int32_t* counts, cudaStream_t st);
+  // annulus: expected entries of every outer face per step
+  static void inflow_means(const Params<double>& pd, double* mu, cudaStream_t st);
   static void step_det(const Params<T>& p, State<T>& s, int& cur, int& lay, uint32_t step,
                        int do_sample, cudaStream_t st);
   static void step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint32_t step0,

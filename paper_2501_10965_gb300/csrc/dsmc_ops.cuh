@@ -365,53 +365,161 @@ __device__ __forceinline__ void append_particle(const Params<float>& p, const PB
                                                 float vx, float vy, float vz, float ir,
                                                 unsigned* s_misc);
 
-// FP32 layout: one warp per outer face; new particles go into the bins of
-// the next step like moved ones (warp-aggregated append, overflow list when
-// a bin is full)
-static __global__ void __launch_bounds__(256) k_inject_bins(const __grid_constant__ Params<double> pd,
-                                                            const __grid_constant__ Params<float> pf, PBuf<float> out,
-                                                            const int32_t* __restrict__ start,
-                                                            int32_t* __restrict__ cnt_out, Ovf ovo, int ovf_cap,
-                                                            uint32_t step, double* __restrict__ tally_g,
-                                                            unsigned long long* __restrict__ stats) {
-  __shared__ double s_tally[5];
-  __shared__ unsigned s_misc[2];
-  __shared__ unsigned s_flow[2];
-  __shared__ unsigned long long s_hits[2];
-  if (threadIdx.x < 5) s_tally[threadIdx.x] = 0.0;
-  if (threadIdx.x < 2) {
-    s_misc[threadIdx.x] = 0;
-    s_flow[threadIdx.x] = 0;
-    s_hits[threadIdx.x] = 0;
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int k = gw; k < pd.nx; k += nwarps) {
-    long long m = 0;
-    if (lane == 0) m = inflow_count(pd, k, step);
-    m = __shfl_sync(FULL, m, 0);
-    if (m > (1 << 24)) m = 1 << 24;
-    for (long long qb = 0; qb < m; qb += 32) {
-      const long long q = qb + lane;
-      double x = 0.0, y = 0.0, vx = 0.0, vy = 0.0, vz = 0.0, ir = 0.0;
-      int d = -1;
-      if (q < m) {
-        if (inflow_particle<true>(pd, k, (int)q, step, s_tally, &s_hits[0], &s_hits[1], x, y, vx, vy, vz, ir))
-          d = cell_of_ann<float>(pf, (float)x, (float)y);
-        if (d >= 0) atomicAdd(&s_flow[0], 1u);  // one that ends outside never entered
+// FP32 layout: the same inflow speed distribution, density z exp(-(z -
+// s)^2) on z > 0, sampled exactly by acceptance-rejection in FP32 from
+// uniforms 64 + 4t .. 67 + 4t of the particle's stream (try t):
+//   s >= 0: with w = z - s the density is (s + w) exp(-w^2) <= (s + |w|)
+//     exp(-w^2), a mixture of s exp(-w^2) (weight s sqrt(pi); w normal with
+//     variance 1/2) and |w| exp(-w^2) (weight 1; |w| = sqrt(-ln u), random
+//     sign); accept z > 0 with probability z / (s + |w|);
+//   -1 <= s < 0: with a = -s and w = z + a > a the density is (w - a)
+//     exp(-w^2) <= w exp(-w^2), whose tail beyond a is w = sqrt(a^2 - ln u);
+//     accept with probability (w - a) / w;
+//   s < -1: the density is proportional to z exp(-2 a z) exp(-z^2): z from
+//     Gamma(2, rate 2a), accepted with probability exp(-z^2).
+// The acceptance rate is at least ~24 %; after 64 rejected tries (odds
+// below 1e-7) returns -1 and the caller takes the FP64 inverse.
+__device__ __forceinline__ float inflow_speed_f32(float s, Stream<float>& st) {
+  const float SQRTPI = 1.7724538509055159f;
+  for (uint32_t t = 0; t < 64u; ++t) {
+    const uint32_t j = 64u + 4u * t;
+    const float ua = st.u(j), ub = st.u(j + 1), uc = st.u(j + 2), ud = st.u(j + 3);
+    if (s >= 0.f) {
+      float w;
+      if (ua * (s * SQRTPI + 1.f) < s * SQRTPI) {
+        float sn, cn;
+        m_sincos_2pi(uc, &sn, &cn);
+        w = sqrtf(-__logf(ub)) * cn;
+      } else {
+        w = sqrtf(-__logf(ub));
+        if (uc < 0.5f) w = -w;
       }
-      append_particle<2>(pf, out, start, cnt_out, ovo, ovf_cap, d >= 0, d, (float)x, (float)y, (float)vx, (float)vy,
-                         (float)vz, (float)ir, s_misc);
+      const float z = s + w;
+      if (z > 0.f && ud * (s + fabsf(w)) < z) return z;
+    } else if (s >= -1.f) {
+      const float a = -s;
+      const float w = sqrtf(a * a - __logf(ub));
+      if (ud * w < w - a) return w - a;
+    } else {
+      const float a = -s;
+      const float z = -(__logf(ub) + __logf(uc)) / (2.f * a);
+      if (ud < __expf(-z * z)) return z;
     }
   }
-  __syncthreads();
-  if (threadIdx.x < 5 && s_tally[threadIdx.x] != 0.0) atomicAdd(tally_g + threadIdx.x, s_tally[threadIdx.x]);
-  if (threadIdx.x == 5 && s_flow[0]) atomicAdd(stats + ST_INJ, (unsigned long long)s_flow[0]);
-  if (threadIdx.x == 7 && s_misc[0]) atomicAdd(stats + ST_OVF, (unsigned long long)s_misc[0]);
-  if (threadIdx.x == 8 && s_misc[1]) atomicAdd(stats + ST_NEARFULL, (unsigned long long)s_misc[1]);
-  if (threadIdx.x == 9 && s_hits[0]) atomicAdd(stats + ST_HITS, s_hits[0]);
-  if (threadIdx.x == 10 && s_hits[1]) atomicAdd(stats + ST_MAXHIT, s_hits[1]);
+  return -1.f;
+}
+
+// FP32 layout: particle q of face k in FP32 (the draws of inflow_particle,
+// the speed from inflow_speed_f32); false if it ends outside
+__device__ __forceinline__ bool inflow_particle_f32(const Params<float>& p, int k, int q, uint32_t step, float* tally,
+                                                    unsigned long long* hits, unsigned long long* maxhit, float& x,
+                                                    float& y, float& vx, float& vy, float& vz, float& ir) {
+  const float sT = sqrtf(p.fs_t), beta = rsqrtf(2.f * p.fs_t);
+  const float nx = -p.fnrm[2 * k], ny = -p.fnrm[2 * k + 1];
+  const float tx = -ny, ty = nx;
+  const float un = p.fs_u[0] * nx + p.fs_u[1] * ny, ut = p.fs_u[0] * tx + p.fs_u[1] * ty;
+  Stream<float> st(TAG_INJ, (uint32_t)q, (uint32_t)k, step, p.k0, p.k1);
+  float z = inflow_speed_f32(un * beta, st);
+  if (z < 0.f) z = (float)inflow_speed((double)(un * beta), (double)st.u(0));
+  const float vn = z / beta;
+  float n1, n2;
+  box_muller(st.u(1), st.u(2), &n1, &n2);
+  const float vt = ut + sT * n1;
+  vx = vn * nx + vt * tx;
+  vy = vn * ny + vt * ty;
+  vz = p.fs_u[2] + sT * n2;
+  const float th = 6.283185307179586f * ((float)k + st.u(3)) / (float)p.nx;
+  ir = -p.fs_t * __logf(st.u(4));
+  x = p.r_out * cosf(th);
+  y = p.r_out * sinf(th);
+  return fly_ann<float, true>(p, x, y, vx, vy, vz, ir, TAG_INJ, (uint32_t)q, (uint32_t)k, step, 8u, st.u(5) * p.dt,
+                              tally, hits, maxhit);
+}
+
+// Expected entries of every outer face per step, mu_k (the mean of
+// inflow_count's Iround), written once per handle
+static __global__ void k_inflow_means(const __grid_constant__ Params<double> p, double* __restrict__ mu) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < p.nx; k += gridDim.x * blockDim.x) {
+    const double beta = 1.0 / sqrt(2.0 * p.fs_t);
+    const double len = p.r_out * 2.0 * PI_D / (double)p.nx;
+    const double nx = -p.fnrm[2 * k], ny = -p.fnrm[2 * k + 1];
+    const double sn = (p.fs_u[0] * nx + p.fs_u[1] * ny) * beta;
+    mu[k] = p.fs_rho * inflow_ginf(sn) / (beta * sqrt(PI_D)) * len * p.dt / p.fnum;
+  }
+}
+
+// FP32 layout: one thread per entering particle.  Every CTA (one warp) draws
+// the faces' counts from the precomputed means (the same Iround draws as
+// inflow_count) and scans them in shared memory; lane t of the grid takes
+// the t-th new particle, finds its face by bisection, samples it and appends
+// it to the next step's bins (warp-aggregated, overflow list when a bin is
+// full).  off: dynamic shared memory, nx + 1 ints.
+static __global__ void __launch_bounds__(32) k_inject_bins(const __grid_constant__ Params<double> pd,
+                                                           const __grid_constant__ Params<float> pf,
+                                                           const double* __restrict__ mu, PBuf<float> out,
+                                                           const int32_t* __restrict__ start,
+                                                           int32_t* __restrict__ cnt_out, Ovf ovo, int ovf_cap,
+                                                           uint32_t step, double* __restrict__ tally_g,
+                                                           unsigned long long* __restrict__ stats) {
+  extern __shared__ int32_t off[];
+  __shared__ float s_tally[5];
+  __shared__ unsigned s_misc[2];
+  __shared__ unsigned long long s_hits[2];
+  const int lane = threadIdx.x;
+  if (lane < 5) s_tally[lane] = 0.f;
+  if (lane < 2) {
+    s_misc[lane] = 0;
+    s_hits[lane] = 0;
+  }
+  const int nt = pd.nx;
+  // counts and their exclusive scan, 32 faces at a time
+  int run = 0;
+  for (int k0 = 0; k0 < nt; k0 += 32) {
+    const int k = k0 + lane;
+    int c = 0;
+    if (k < nt) {
+      Stream<double> sc(TAG_INJ, 0xFFFFFFFFu, (uint32_t)k, step, pd.k0, pd.k1);
+      const long long m = iround(mu[k], sc.u(0));
+      c = (int)(m < 0 ? 0 : (m > (1 << 20) ? (1 << 20) : m));
+    }
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (k < nt) off[k] = run + x - c;
+    run += __shfl_sync(FULL, x, 31);
+  }
+  if (lane == 0) off[nt] = run;
+  __syncwarp();
+  const int total = run;
+  unsigned nin = 0;
+  for (int t0 = blockIdx.x * 32; t0 < total; t0 += gridDim.x * 32) {
+    const int t = t0 + lane;
+    float x = 0.f, y = 0.f, vx = 0.f, vy = 0.f, vz = 0.f, ir = 0.f;
+    int d = -1;
+    if (t < total) {
+      int lo = 0, hi = nt - 1;  // the face k with off[k] <= t < off[k + 1]
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      if (inflow_particle_f32(pf, lo, t - off[lo], step, s_tally, &s_hits[0], &s_hits[1], x, y, vx, vy, vz, ir))
+        d = cell_of_ann<float>(pf, x, y);
+      if (d >= 0) ++nin;  // one that ends outside never entered
+    }
+    append_particle<2>(pf, out, start, cnt_out, ovo, ovf_cap, d >= 0, d, x, y, vx, vy, vz, ir, s_misc);
+  }
+  __syncwarp();
+  for (int o = 16; o > 0; o >>= 1) nin += __shfl_xor_sync(FULL, nin, o);
+  if (lane == 0 && nin) atomicAdd(stats + ST_INJ, (unsigned long long)nin);
+  if (lane < 5 && s_tally[lane] != 0.f) atomicAdd(tally_g + lane, (double)s_tally[lane]);
+  if (lane == 5 && s_misc[0]) atomicAdd(stats + ST_OVF, (unsigned long long)s_misc[0]);
+  if (lane == 6 && s_misc[1]) atomicAdd(stats + ST_NEARFULL, (unsigned long long)s_misc[1]);
+  if (lane == 7 && s_hits[0]) atomicAdd(stats + ST_HITS, s_hits[0]);
+  if (lane == 8 && s_hits[1]) atomicAdd(stats + ST_MAXHIT, s_hits[1]);
 }
 
 template <typename T>
@@ -724,58 +832,54 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
       float* tvx = reinterpret_cast<float*>(smem + (size_t)warp * tile * 28);
       uint32_t* tow = reinterpret_cast<uint32_t*>(tvx + 6 * tile);
       const bool staged = n <= tile;
-      bool ok = true;
-      if (staged && n > 0) {
+      const int narr = (DIM == 2) ? 6 : 5;
+      // bulk copies of particles [q0, q0 + m) of the cell into the tile on the
+      // warp's mbarrier at phase ph (bounded wait; false on a timeout)
+      auto stage = [&](int q0, int m, uint32_t ph) -> bool {
         if (lane == 0) {
-          const uint32_t bytes = (uint32_t)((n + 3) & ~3) * 4u;
-          const int narr = (DIM == 2) ? 6 : 5;
+          const uint32_t bytes = (uint32_t)((m + 3) & ~3) * 4u;
           fence_proxy_async_smem();
           mbar_arrive_expect_tx(&s_bar[warp], bytes * narr);
-          bulk_g2s(tvx, in.vx + base, bytes, &s_bar[warp]);
-          bulk_g2s(tvx + tile, in.vy + base, bytes, &s_bar[warp]);
-          bulk_g2s(tvx + 2 * tile, in.vz + base, bytes, &s_bar[warp]);
-          bulk_g2s(tvx + 3 * tile, in.ir + base, bytes, &s_bar[warp]);
-          bulk_g2s(tvx + 4 * tile, in.x + base, bytes, &s_bar[warp]);
-          if (DIM == 2) bulk_g2s(tvx + 5 * tile, in.y + base, bytes, &s_bar[warp]);
+          bulk_g2s(tvx, in.vx + base + q0, bytes, &s_bar[warp]);
+          bulk_g2s(tvx + tile, in.vy + base + q0, bytes, &s_bar[warp]);
+          bulk_g2s(tvx + 2 * tile, in.vz + base + q0, bytes, &s_bar[warp]);
+          bulk_g2s(tvx + 3 * tile, in.ir + base + q0, bytes, &s_bar[warp]);
+          bulk_g2s(tvx + 4 * tile, in.x + base + q0, bytes, &s_bar[warp]);
+          if (DIM == 2) bulk_g2s(tvx + 5 * tile, in.y + base + q0, bytes, &s_bar[warp]);
         }
-        ok = mbar_wait_bounded(&s_bar[warp], 0u, MBAR_POLL_LIMIT);
-        if (!ok && lane == 0) atomicOr(errflag, 1);
-      }
-      ok = __all_sync(FULL, ok);
-      // The cell body is instantiated twice: on the shared-memory tile (the
-      // compiler then addresses it as shared memory) and, for cells above
-      // `tile` particles, in global memory.
-      auto body = [&](auto staged_tag) {
-        constexpr bool STAGED = decltype(staged_tag)::value;
-        float *vx, *vy, *vz, *ir;
-        const float *px, *py;
-        uint32_t* own;
-        if constexpr (STAGED) {
-          vx = tvx;
-          vy = tvx + tile;
-          vz = tvx + 2 * tile;
-          ir = tvx + 3 * tile;
-          px = tvx + 4 * tile;
-          py = tvx + 5 * tile;
-          own = tow;
-        } else {
-          vx = in.vx + base;
-          vy = in.vy + base;
-          vz = in.vz + base;
-          ir = in.ir + base;
-          px = in.x + base;
-          py = in.y + base;
-          own = owner_g + base;
-        }
-        if (flags & 1) {
+        const bool r = mbar_wait_bounded(&s_bar[warp], ph, MBAR_POLL_LIMIT);
+        if (!r && lane == 0) atomicOr(errflag, 1);
+        return __all_sync(FULL, r);
+      };
+      bool ok = true;
+      if (staged && n > 0) ok = stage(0, n, 0u);
+      float* vx = tvx;
+      float* vy = tvx + tile;
+      float* vz = tvx + 2 * tile;
+      float* ir = tvx + 3 * tile;
+      const float* px = tvx + 4 * tile;
+      const float* py = tvx + 5 * tile;
+      uint32_t* own = tow;
+      float mtot = 0.f;  // cell above the tile: this lane's moment summed over the chunks
+      // The cell body on the shared-memory tile, for particles [q0, q0 + m)
+      // of the cell: the whole cell when it fits the tile (WHOLE), or one
+      // chunk of a larger cell, whose collisions ran in global memory and
+      // whose sums, reduced per chunk, add up over the chunks.
+      auto body = [&](auto whole_tag, int q0, int m) {
+        constexpr bool whole = decltype(whole_tag)::value;
+        if (whole && (flags & 1)) {
           CollCount cc{0, 0, 0, 0};
-          collide_cell<float>(p, vx, vy, vz, ir, n, (uint32_t)lcell, step_c, sgmax + cell, own, cc);
+          collide_cell<float>(p, vx, vy, vz, ir, m, (uint32_t)lcell, step_c, sgmax + cell, own, cc);
           flush_counts<float>(cc, s_cnt);
           __syncwarp();
         }
-        if (flags & 2)
-          sample_cell_staged(vx, vy, vz, ir, n, mom, acc + (size_t)cell * NMOM, comp + (size_t)cell * NMOM, pre,
-                             stg + (size_t)cell * NMOM, stc + (size_t)cell * NMOM, pre32, flush);
+        if (flags & 2) {
+          if constexpr (whole)
+            sample_cell_staged(vx, vy, vz, ir, m, mom, acc + (size_t)cell * NMOM, comp + (size_t)cell * NMOM, pre,
+                               stg + (size_t)cell * NMOM, stc + (size_t)cell * NMOM, pre32, flush);
+          else
+            mtot += sample_chunk(vx, vy, vz, ir, m);
+        }
         if (flags & 4) {
           int* nb_cnt = s_nb[warp][0];
           int* nb_base = s_nb[warp][1];
@@ -786,7 +890,7 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
           // M1: destinations and ranks; a particle that reaches a wall is
           // placed individually in M3 (code 9)
           const int cix = lcell % p.nx, ciy = lcell / p.nx;
-          for (int q = lane; q < n; q += 32) {
+          for (int q = lane; q < m; q += 32) {
             float xn, yn;
             int code = 9;
             if constexpr (ANN) {
@@ -810,7 +914,7 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
           }
           __syncwarp();
           // M3: fly again (identical result) with wall tallies, and store
-          for (int q = lane; q < n; q += 32) {
+          for (int q = lane; q < m; q += 32) {
             float x = px[q], y = (DIM == 2) ? py[q] : 0.f;
             float a = vx[q], b = vy[q], c = vz[q], e = ir[q];
             const uint32_t tag = own[q];
@@ -819,13 +923,13 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
               if (code < 9) {
                 x = x + a * p.dt;
                 y = y + b * p.dt;
-              } else if (!fly_ann<float, true>(p, x, y, a, b, c, e, TAG_WALL, (uint32_t)q, (uint32_t)lcell, step_m, 0u,
+              } else if (!fly_ann<float, true>(p, x, y, a, b, c, e, TAG_WALL, (uint32_t)(q0 + q), (uint32_t)lcell, step_m, 0u,
                                                p.dt, s_tally, &s_hits[0], &s_hits[1])) {
                 atomicAdd(&s_out, 1u);  // left through the outer circle
                 continue;
               }
             } else {
-              fly<float, DIM, true>(p, x, y, a, b, c, e, (uint32_t)q, (uint32_t)lcell, step_m, s_tally, &s_hits[0],
+              fly<float, DIM, true>(p, x, y, a, b, c, e, (uint32_t)(q0 + q), (uint32_t)lcell, step_m, s_tally, &s_hits[0],
                                     &s_hits[1]);
             }
             int d = -1, slot, s0, cap;
@@ -870,10 +974,8 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
               }
             }
           }
-          __syncwarp();
-          if (lane == 0) cnt_in[cell] = 0;
-        } else if (STAGED && (flags & 1)) {
-          for (int q = lane; q < n; q += 32) {
+        } else if (whole && (flags & 1)) {
+          for (int q = lane; q < m; q += 32) {
             in.vx[base + q] = vx[q];
             in.vy[base + q] = vy[q];
             in.vz[base + q] = vz[q];
@@ -882,8 +984,37 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
         }
       };
       if (ok) {
-        if (staged) body(std::true_type{});
-        else body(std::false_type{});
+        if (staged) {
+          body(std::true_type{}, 0, n);
+        } else {
+          // a cell above the tile: collisions in place in global memory (the
+          // candidates pick particles anywhere in the cell), then sampling
+          // and the move chunk by chunk through the tile
+          if (flags & 1) {
+            CollCount cc{0, 0, 0, 0};
+            collide_cell<float>(p, in.vx + base, in.vy + base, in.vz + base, in.ir + base, n, (uint32_t)lcell, step_c,
+                                sgmax + cell, owner_g + base, cc);
+            flush_counts<float>(cc, s_cnt);
+            fence_proxy_async_global();  // the bulk copies below read these velocities
+            __syncwarp();
+          }
+          if (flags & 6) {
+            uint32_t ph = 0u;
+            for (int q0 = 0; q0 < n && ok; q0 += tile, ph ^= 1u) {
+              const int m = min(tile, n - q0);
+              __syncwarp();  // every lane is done with the previous chunk
+              ok = stage(q0, m, ph);
+              if (ok) body(std::false_type{}, q0, m);
+            }
+          }
+          if (ok && (flags & 2))
+            sample_fold(mtot, mom, acc + (size_t)cell * NMOM, comp + (size_t)cell * NMOM, pre,
+                        stg + (size_t)cell * NMOM, stc + (size_t)cell * NMOM, pre32, flush);
+        }
+        if (ok && (flags & 4)) {
+          __syncwarp();
+          if (lane == 0) cnt_in[cell] = 0;
+        }
       }
     }
   } else if (flags & 4) {
@@ -1436,6 +1567,11 @@ void Ops<T>::ann_counts(const Params<double>& pd, int ncells, int32_t* counts, c
 }
 
 template <typename T>
+void Ops<T>::inflow_means(const Params<double>& pd, double* mu, cudaStream_t st) {
+  k_inflow_means<<<grid_for(pd.nx, 256), 256, 0, st>>>(pd, mu);
+}
+
+template <typename T>
 static size_t tile_smem(int tile) {
   return (size_t)WPB * tile * (4 * sizeof(T) + sizeof(uint32_t));
 }
@@ -1524,6 +1660,19 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
       s.comp, s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats, \
       s.flags + 8, s.stg, s.stc
 #define DSMC_FUSED_LAUNCH(D, B, W, A) k_fused<D, B, W, A><<<cblocks + oblocks, W * 32, smf, st>>>(DSMC_FUSED_ARGS)
+      const bool inject = p.mesh == 1 && (flags & 4);
+      if (inject) {
+        // annulus: the freestream entry of this step, on the side stream,
+        // into the bins the fused step fills (their counts were cleared by
+        // the previous launch)
+        cudaEventRecord(s.ev_fork, st);
+        cudaStreamWaitEvent(s.side, s.ev_fork, 0);
+        const int nb = (s.inj_max + 31) / 32;
+        k_inject_bins<<<nb > 0 ? nb : 1, 32, sizeof(int32_t) * (p.nx + 1), s.side>>>(
+            s.pinj, p, s.inj_mu, s.buf[other], s.start[lay], s.count[other], s.ovf[other], s.ovf_cap, sm_step,
+            s.tally, s.stats);
+        cudaEventRecord(s.ev_join, s.side);
+      }
       if (p.mesh == 1) {
         if (F == 2) DSMC_FUSED_LAUNCH(2, false, 2, true);
         else DSMC_FUSED_LAUNCH(2, false, 4, true);
@@ -1546,12 +1695,7 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
       }
 #undef DSMC_FUSED_LAUNCH
 #undef DSMC_FUSED_ARGS
-      if (p.mesh == 1 && (flags & 4)) {
-        // annulus: freestream entry into the bins of the step just moved
-        const int wpb = 8, fb = (p.nx + wpb - 1) / wpb;
-        k_inject_bins<<<fb, wpb * 32, 0, st>>>(s.pinj, p, s.buf[other], s.start[lay], s.count[other], s.ovf[other],
-                                               s.ovf_cap, sm_step, s.tally, s.stats);
-      }
+      if (inject) cudaStreamWaitEvent(st, s.ev_join, 0);
       // the input overflow list has been consumed
       cudaMemsetAsync(s.ovf[cur].count, 0, sizeof(int32_t), st);
       cur = other;

@@ -127,23 +127,34 @@ def test_cylinder_fp32_gas_at_rest_collision_rate_and_uniform_density():
     g.dsmc_step(100)
     g.dsmc_sample(reset=True)
     c0 = g.stats()["n_coll"]
-    steps, nsum = 0, 0
-    for _ in range(20):
-        nsum += 10 * g.num_particles()
-        g.dsmc_step(10, sample=True)
-        steps += 10
+    vol = g.volumes()
+    ring = vol.reshape(nr, nt).sum(1)
+    nsum, dens, temps = 0, [], []
+    for _ in range(16):
+        for _ in range(4):
+            nsum += 10 * g.num_particles()
+            g.dsmc_step(10, sample=True)
+        f = g.dsmc_sample(reset=True).cpu().numpy()
+        dens.append((f[:, 0] * vol).reshape(nr, nt).sum(1) / ring)
+        # the gas is at rest: T from the particles' |v|^2 and I_r directly
+        # (cell moments about a sampled mean carry a -1/N bias in small cells)
+        pp = _np(g.get_particles())
+        tt = np.mean(pp["vx"] ** 2 + pp["vy"] ** 2 + pp["vz"] ** 2) / 3.0
+        temps.append((3.0 * tt + 2.0 * np.mean(pp["ir"])) / 5.0)
     coll = g.stats()["n_coll"] - c0
     nu = c["k_visc"] / c["mu_ref"]
     expect = 0.5 * nu * cfg["dt"] * nsum
     assert abs(coll / expect - 1.0) < 0.03, (coll, expect)
-    f = g.dsmc_sample(reset=True).cpu().numpy()
-    vol = g.volumes()
-    mass = (f[:, 0] * vol).reshape(nr, nt).sum(1)
-    ring = vol.reshape(nr, nt).sum(1)
-    rho = mass / ring
-    assert np.all(np.abs(rho - 1.0) < 0.05), rho
-    T = (3.0 * f[:, 4] + 2.0 * f[:, 5]) / 5.0
-    assert abs(np.average(T, weights=f[:, 0] * vol) - 1.0) < 0.01
+    # uniformity: ring densities relative to the domain's (the total count
+    # wanders slowly, over a domain transit of ~200 steps, so it is checked
+    # on its own against the freestream density with its Poisson spread)
+    dens = np.array(dens)
+    total = (dens * ring).sum(1) / ring.sum()
+    rel = dens / total[:, None]
+    m, se = rel.mean(0), rel.std(0, ddof=1) / math.sqrt(len(rel))
+    assert np.all(np.abs(m - 1.0) <= 4.0 * se + 0.01), (m, se)
+    assert abs(total.mean() - 1.0) < 0.03, total.mean()
+    assert abs(np.mean(temps) - 1.0) < 0.01, np.mean(temps)
 
 
 def test_cylinder_fp32_full_size_workload():
