@@ -692,15 +692,43 @@ __device__ __forceinline__ int neighbour_cell(int nx, int cell, int code) {
   return cell + (code / 3 - 1) * nx + (code % 3 - 1);
 }
 
+// Annulus: the geometry one cell's moves need, read from the tables once
+// per cell: the squared radii of rings j-1 .. j+2 (sentinels where a ring is
+// missing) and the rays of sectors k-1 .. k+2 (wrapping around).
+struct AnnCell {
+  float rin2, r2m, r2lo, r2hi, r2p;
+  float cm, sm, clo, slo, cup, sup, cp, sp;
+};
+
+__device__ __forceinline__ AnnCell ann_cell(const Params<float>& p, int k, int j) {
+  AnnCell g;
+  const int nt = p.nx;
+  g.rin2 = p.r2t[0];
+  g.r2lo = p.r2t[j];
+  g.r2hi = p.r2t[j + 1];
+  g.r2m = (j > 0) ? p.r2t[j - 1] : -1.f;            // below ring 0: stays in ring 0
+  g.r2p = (j + 1 < p.ny) ? p.r2t[j + 2] : -1.f;  // none beyond the outer ring
+  const int km = (k == 0) ? nt - 1 : k - 1, kp = (k + 2 > nt) ? k + 2 - nt : k + 2;
+  g.cm = p.ray[2 * km];
+  g.sm = p.ray[2 * km + 1];
+  g.clo = p.ray[2 * k];
+  g.slo = p.ray[2 * k + 1];
+  g.cup = p.ray[2 * k + 2];
+  g.sup = p.ray[2 * k + 3];
+  g.cp = p.ray[2 * kp];
+  g.sp = p.ray[2 * kp + 1];
+  return g;
+}
+
 // Annulus: the straight flight over dt, true if it does not meet the
 // cylinder (the test of fly_ann)
-__device__ __forceinline__ bool ann_straight(const Params<float>& p, float x, float y, float vx, float vy, float* xn,
-                                             float* yn) {
+__device__ __forceinline__ bool ann_straight(const Params<float>& p, float rin2, float x, float y, float vx, float vy,
+                                             float* xn, float* yn) {
   *xn = x + vx * p.dt;
   *yn = y + vy * p.dt;
   const float a = vx * vx + vy * vy, b = x * vx + y * vy;
   if (b < 0.f && a > 0.f) {
-    const float cc = x * x + y * y - p.r2t[0];
+    const float cc = x * x + y * y - rin2;
     const float disc = b * b - a * cc;
     if (disc > 0.f) {
       float s1 = (-b - sqrtf(disc)) / a;
@@ -715,30 +743,26 @@ __device__ __forceinline__ bool ann_straight(const Params<float>& p, float x, fl
 // k + dk mod nx) holding (x, y), from the squared radii of ring j's
 // neighbours and the signs against sector k's neighbouring rays; 9 when the
 // particle is farther or outside r_out.
-__device__ __forceinline__ int neighbour_code_ann(const Params<float>& p, int k, int j, float x, float y) {
+__device__ __forceinline__ int neighbour_code_ann(const AnnCell& g, int j, float x, float y) {
   const float r2 = x * x + y * y;
   int dj = 0;
-  if (r2 < p.r2t[j]) {
+  if (r2 < g.r2lo) {
     if (j > 0) {
-      if (!(r2 >= p.r2t[j - 1])) return 9;
+      if (!(r2 >= g.r2m)) return 9;
       dj = -1;
     }
-  } else if (!(r2 < p.r2t[j + 1])) {
-    if (j + 1 >= p.ny || !(r2 < p.r2t[j + 2])) return 9;
+  } else if (!(r2 < g.r2hi)) {
+    if (!(r2 < g.r2p)) return 9;  // r2p = -1 past the outer ring
     dj = 1;
   }
-  const int nt = p.nx;
-  const float* ray = p.ray;
-  const bool lo = ray[2 * k] * y - ray[2 * k + 1] * x >= 0.f;
-  const bool up = ray[2 * k + 2] * y - ray[2 * k + 3] * x >= 0.f;
+  const bool lo = g.clo * y - g.slo * x >= 0.f;
+  const bool up = g.cup * y - g.sup * x >= 0.f;
   int dk = 0;
   if (!lo) {
-    const int km = (k == 0) ? nt - 1 : k - 1;
-    if (!(ray[2 * km] * y - ray[2 * km + 1] * x >= 0.f)) return 9;
+    if (!(g.cm * y - g.sm * x >= 0.f)) return 9;
     dk = -1;
   } else if (up) {
-    const int kp = (k + 2 > nt) ? k + 2 - nt : k + 2;
-    if (!(ray[2 * kp] * y - ray[2 * kp + 1] * x < 0.f)) return 9;
+    if (!(g.cp * y - g.sp * x < 0.f)) return 9;
     dk = 1;
   }
   return (dj + 1) * 3 + (dk + 1);
@@ -890,12 +914,14 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
           // M1: destinations and ranks; a particle that reaches a wall is
           // placed individually in M3 (code 9)
           const int cix = lcell % p.nx, ciy = lcell / p.nx;
+          AnnCell ag;
+          if constexpr (ANN) ag = ann_cell(p, cix, ciy);
           for (int q = lane; q < m; q += 32) {
             float xn, yn;
             int code = 9;
             if constexpr (ANN) {
-              if (ann_straight(p, px[q], py[q], vx[q], vy[q], &xn, &yn))
-                code = neighbour_code_ann(p, cix, ciy, xn, yn);
+              if (ann_straight(p, ag.rin2, px[q], py[q], vx[q], vy[q], &xn, &yn))
+                code = neighbour_code_ann(ag, ciy, xn, yn);
             } else {
               if (flight_stays_inside<float, DIM>(p, px[q], (DIM == 2) ? py[q] : 0.f, vx[q], vy[q], &xn, &yn))
                 code = neighbour_code<DIM>(p, cix, ciy, xn, yn);
