@@ -825,15 +825,20 @@ int synth_solve(dsmc_handle* h, const double* dev_fields, const double* dev_hot,
 int dig_correct(dsmc_handle* h, const double* dev_target) {
   if (!h || !dev_target) return set_err(h, DSMC_ERR_ARG, "bad arguments");
   if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "dig_correct: not on the annulus");
-  int32_t fl[4] = {0, 0, 0, 0};
+  int32_t fl[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (h->det) Ops<double>::dig_counts(h->sd, h->ncells, h->lay, dev_target, h->dig_iter, 1, h->stream);
   else Ops<float>::dig_counts(h->sf, h->ncells, h->lay, dev_target, h->dig_iter, 0, h->stream);
   int32_t* flags = h->det ? h->sd.flags : h->sf.flags;
   cudaMemcpyAsync(fl, flags, sizeof fl, cudaMemcpyDeviceToHost, h->stream);
   int r = sync_check(h, "dig_correct (counts)");
   if (r) return r;
+  unsigned long long tot64 = 0, caps64 = 0;
+  std::memcpy(&tot64, fl + 4, sizeof tot64);
+  std::memcpy(&caps64, fl + 6, sizeof caps64);
+  const unsigned long long cap = (unsigned long long)(h->det ? h->sd.capacity : h->sf.capacity);
   if (fl[0] & 1) return set_err(h, DSMC_ERR_NUMERIC, "dig_correct: non-finite or non-positive target");
-  if (fl[0] & 6) return set_err(h, DSMC_ERR_CAPACITY, "dig_correct: new particle count does not fit");
+  if ((fl[0] & 6) || tot64 > cap || caps64 > cap)
+    return set_err(h, DSMC_ERR_CAPACITY, "dig_correct: new particle count does not fit");
   if (h->det) {
     Ops<double>::dig_apply(h->cp, h->sd, h->ncells, h->cur, h->lay, dev_target, h->dig_iter, 1, h->stream);
     h->sd.nparticles = fl[1];

@@ -1308,6 +1308,19 @@ static __global__ void k_dig_counts(const CellParams* __restrict__ cps, const in
     }
     const int32_t wtot = __reduce_add_sync(FULL, nv);
     if ((threadIdx.x & 31) == 0 && wtot) atomicAdd(&flags[3], wtot);
+    // the totals of the new counts and of the bin capacities in 64 bits
+    // (flags 4-5 and 6-7), so that the host sees a target too large for
+    // the workspace before an int32 sum or the layout scan could wrap
+    unsigned long long c64 = (unsigned long long)nv, k64 = (c < ncells) ? (unsigned long long)caps[c] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      c64 += __shfl_xor_sync(FULL, c64, o);
+      k64 += __shfl_xor_sync(FULL, k64, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (c64) atomicAdd(reinterpret_cast<unsigned long long*>(flags + 4), c64);
+      if (k64) atomicAdd(reinterpret_cast<unsigned long long*>(flags + 6), k64);
+    }
   }
 }
 
@@ -1880,7 +1893,7 @@ void Ops<T>::import_particles(const Params<T>& p, State<T>& s, int& cur, int& la
 template <typename T>
 void Ops<T>::dig_counts(State<T>& s, int ncells, int lay, const double* target, uint32_t iter, int det,
                         cudaStream_t st) {
-  cudaMemsetAsync(s.flags, 0, sizeof(int32_t) * 4, st);
+  cudaMemsetAsync(s.flags, 0, sizeof(int32_t) * 8, st);
   // caps go to tmp_start (ncells), then scanned into the other layout's start
   k_dig_counts<<<grid_for(ncells, 256), 256, 0, st>>>(s.cases.cp, s.cases.cell_case, s.cases.cell0, ncells, target,
                                                       iter, det, s.slack, s.nt, s.tmp_start, s.flags);

@@ -179,6 +179,20 @@ def test_dig_correct_rejects_bad_target_gpu():
     after = _np(g.get_particles())
     for k in KEYS:
         assert np.array_equal(before[k], after[k])
+    # finite but far too dense for the workspace: every cell's count fits
+    # an int32, their total does not (the 64-bit totals catch it), in both
+    # layouts; nothing changes
+    for prec in ("fp64", "fp32"):
+        g = _gpu(W.fourier_1d(nx=10, ppc=10, precision=prec))
+        before = _np(g.get_particles())
+        t = torch.ones((10, 6), dtype=torch.float64, device="cuda")
+        t[:, 0] = 5e7  # 5e8 particles per cell
+        with pytest.raises(DsmcError) as e:
+            g.dig_correct(t)
+        assert e.value.code == -2, prec
+        after = _np(g.get_particles())
+        for k in KEYS:
+            assert np.array_equal(before[k], after[k]), prec
 
 
 def test_set_particles_roundtrip_and_binning():
