@@ -69,6 +69,32 @@ def dist_env():
     return rank, world, local
 
 
+def replica_config(cfg: dict, rank: int) -> dict:
+    """Rank r runs its own seeded copy of the workload (independent
+    replicas, no data-path exchange): Philox seed + 1000 r."""
+    out = dict(cfg)
+    out["seed"] = int(cfg.get("seed", 0)) + 1000 * rank
+    return out
+
+
+def over_ranks(x: float, world: int, op: str, device=None) -> float:
+    """max or sum of a per-rank number over the process group (identity on
+    one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(particles: float, steps: int, t_max: float, world: int, device=None) -> float:
+    """Whole-job particle-steps/s: the particles of every rank over the
+    slowest rank's time."""
+    return over_ranks(particles, world, "sum", device) * steps / t_max
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -232,9 +258,8 @@ def run_gpu(args):
         dist.init_process_group("nccl", rank=rank, world_size=world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = workload(args.workload)
     # independent replicas: every rank runs its own seeded copy of the workload
-    cfg["seed"] = int(cfg.get("seed", 0)) + 1000 * rank
+    cfg = replica_config(workload(args.workload), rank)
     prec = cfg["precision"]
     dim = int(cfg["dim"])
     stream = torch.cuda.current_stream(dev)
@@ -256,15 +281,12 @@ def run_gpu(args):
         barrier()
     clocks = clk.summary()
     reb1 = sim.stats()["n_rebuild"]
-    if world > 1:
-        tt = torch.tensor([t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = over_ranks(t, world, "max", dev)
     # particle-steps: the count changes on the annulus (entry and exit), so
     # the mean of the counts before and after the timed steps
     n_end = sim.num_particles()
     n_mean = 0.5 * (n + n_end)
-    value = n_mean * args.steps * world / t
+    value = job_throughput(n_mean, args.steps, t, world, dev)
     cfg_line_shape = sim.launch_config()
 
     # average duration of one fused step kernel: difference of two runs with
@@ -306,8 +328,8 @@ def run_gpu(args):
         fields_host.copy_(f, non_blocking=True)
     barrier()
     n_up = len(host["x"])
-    te = _events_time(e2e, stream)
-    e2e_value = 0.5 * (n_up + sim.num_particles()) * args.steps * world / te
+    te = over_ranks(_events_time(e2e, stream), world, "max", dev)
+    e2e_value = job_throughput(0.5 * (n_up + sim.num_particles()), args.steps, te, world, dev)
     stats = sim.stats()
     ncells = sim.ncells
 
