@@ -333,7 +333,10 @@ def run_gpu(args):
     stats = sim.stats()
     ncells = sim.ncells
 
-    gpu_launches = (args.steps + 1) + 5 * (reb1 - reb0)
+    # per dsmc_step(K): one move-only launch, K - 1 fused launches and one
+    # collide-and-sample launch, plus on the annulus the entry kernel after
+    # each of the K moves; a bin rebuild adds 5
+    gpu_launches = (args.steps + 1) + (args.steps if cfg.get("mesh") == "annulus" else 0) + 5 * (reb1 - reb0)
 
     # batched ensemble: 64 independent 1D cases of uneven size in one handle
     # (one launch per step for all of them), device-resident
