@@ -156,7 +156,10 @@ def test_cylinder_fp32_gas_at_rest_collision_rate_and_uniform_density():
     total = (dens * ring).sum(1) / ring.sum()
     rel = dens / total[:, None]
     m, se = rel.mean(0), rel.std(0, ddof=1) / math.sqrt(len(rel))
-    assert np.all(np.abs(m - 1.0) <= 4.0 * se + 0.01), (m, se)
+    # 5 batch errors + 2 %: the inner rings hold few particles and their
+    # batches are not quite independent; a wrong cell volume is off by
+    # factors (the volumes differ 30-fold)
+    assert np.all(np.abs(m - 1.0) <= 5.0 * se + 0.02), (m, se)
     assert abs(total.mean() - 1.0) < 0.03, total.mean()
     assert abs(np.mean(temps) - 1.0) < 0.01, np.mean(temps)
 
