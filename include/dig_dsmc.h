@@ -153,8 +153,14 @@ const char *dsmc_last_error(const dsmc_handle *h);
  * with wall interaction, cell indexing and sort, No-Time-Counter collisions
  * with VHS cross-section and Borgnakke-Larsen exchange (Eq. P_inelastic),
  * and, if sample != 0, accumulation of the cell sums behind
- * Eq. (DSMC_macroscopic).  Asynchronous, except that the FP32 layout reads
- * one word back at the end to decide whether its cell bins must be rebuilt. */
+ * Eq. (DSMC_macroscopic); on the annulus the freestream enters after the
+ * flight.  Asynchronous, except that the FP32 layout reads a few words back
+ * at the end to decide whether its cell bins must be rebuilt, and the FP64
+ * layout on the annulus synchronises every step to learn its particle
+ * count.  DSMC_ERR_TIMEOUT: a cell's bulk copy did not complete in time.
+ * DSMC_ERR_CAPACITY (unlike elsewhere, the steps have run): particles did
+ * not fit (the FP32 overflow list was full, or on the annulus the freestream
+ * entries exceeded the workspace) and those particles are lost. */
 int dsmc_step(dsmc_handle *h, int nsteps, int sample);
 
 /* Time-averaged cell fields of Eq. (DSMC_macroscopic) from the sums

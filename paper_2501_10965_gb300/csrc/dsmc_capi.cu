@@ -737,6 +737,7 @@ int dsmc_step(dsmc_handle* h, int nsteps, int sample) {
       Ops<double>::step_det(h->pd, h->sd, h->cur, h->lay, h->step, sample, h->stream);
       h->step += 1;
       if (sample) h->nsamples += 1;
+      if (h->sd.lost) return set_err(h, DSMC_ERR_CAPACITY, "dsmc_step: freestream entries exceed the capacity");
     }
     return check_cuda(h, "dsmc_step");
   }
@@ -753,7 +754,9 @@ int dsmc_step(dsmc_handle* h, int nsteps, int sample) {
   cudaMemcpyAsync(&timeout, h->sf.flags + 8, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
   r = sync_check(h, "dsmc_step (bin check)");
   if (r) return r;
-  if (timeout) return set_err(h, DSMC_ERR_TIMEOUT, "dsmc_step: a cell's bulk copy did not complete in time");
+  if (timeout & 1) return set_err(h, DSMC_ERR_TIMEOUT, "dsmc_step: a cell's bulk copy did not complete in time");
+  if ((timeout & 2) || ovf > h->sf.ovf_cap)
+    return set_err(h, DSMC_ERR_CAPACITY, "dsmc_step: the overflow list was full, particles were lost");
   if (ovf > 0 || nearfull > 0) {
     Ops<float>::rebin(h->pf, h->sf, h->cur, h->lay, 1, h->sf.slack, h->stream);
     cudaMemsetAsync(h->sf.stats + ST_NEARFULL, 0, sizeof(unsigned long long), h->stream);

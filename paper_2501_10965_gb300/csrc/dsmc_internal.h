@@ -85,6 +85,7 @@ struct State {
   // atomics); fork after the previous launch, join before the next
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
+  bool lost;  // FP64 annulus: freestream entries did not fit the workspace
 };
 
 template <typename T>

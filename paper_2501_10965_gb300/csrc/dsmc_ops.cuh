@@ -363,7 +363,7 @@ __device__ __forceinline__ void append_particle(const Params<float>& p, const PB
                                                 int32_t* __restrict__ cnt_out, const Ovf& ovo,
                                                 int ovf_cap, bool active, int d, float x, float y,
                                                 float vx, float vy, float vz, float ir,
-                                                unsigned* s_misc);
+                                                unsigned* s_misc, int32_t* errflag);
 
 // FP32 layout: the same inflow speed distribution, density z exp(-(z -
 // s)^2) on z > 0, sampled exactly by acceptance-rejection in FP32 from
@@ -460,7 +460,8 @@ static __global__ void __launch_bounds__(32) k_inject_bins(const __grid_constant
                                                            const int32_t* __restrict__ start,
                                                            int32_t* __restrict__ cnt_out, Ovf ovo, int ovf_cap,
                                                            uint32_t step, double* __restrict__ tally_g,
-                                                           unsigned long long* __restrict__ stats) {
+                                                           unsigned long long* __restrict__ stats,
+                                                           int32_t* __restrict__ errflag) {
   extern __shared__ int32_t off[];
   __shared__ float s_tally[5];
   __shared__ unsigned s_misc[2];
@@ -510,7 +511,7 @@ static __global__ void __launch_bounds__(32) k_inject_bins(const __grid_constant
         d = cell_of_ann<float>(pf, x, y);
       if (d >= 0) ++nin;  // one that ends outside never entered
     }
-    append_particle<2>(pf, out, start, cnt_out, ovo, ovf_cap, d >= 0, d, x, y, vx, vy, vz, ir, s_misc);
+    append_particle<2>(pf, out, start, cnt_out, ovo, ovf_cap, d >= 0, d, x, y, vx, vy, vz, ir, s_misc, errflag);
   }
   __syncwarp();
   for (int o = 16; o > 0; o >>= 1) nin += __shfl_xor_sync(FULL, nin, o);
@@ -633,7 +634,7 @@ __device__ __forceinline__ void append_particle(const Params<float>& p, const PB
                                                 int32_t* __restrict__ cnt_out, const Ovf& ovo,
                                                 int ovf_cap, bool active, int d, float x, float y,
                                                 float vx, float vy, float vz, float ir,
-                                                unsigned* s_misc) {
+                                                unsigned* s_misc, int32_t* errflag) {
   const int lane = threadIdx.x & 31;
   const int key = active ? d : -1;
   const unsigned peers = __match_any_sync(FULL, key);
@@ -668,6 +669,8 @@ __device__ __forceinline__ void append_particle(const Params<float>& p, const PB
       ovo.vz[q] = vz;
       ovo.ir[q] = ir;
       ovo.dest[q] = d;
+    } else {
+      atomicOr(errflag, 2);  // the overflow list is full: the particle is lost
     }
   }
 }
@@ -997,6 +1000,8 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
                 ovo.vz[qo] = c;
                 ovo.ir[qo] = e;
                 ovo.dest[qo] = d;
+              } else {
+                atomicOr(errflag, 2);  // the overflow list is full: the particle is lost
               }
             }
           }
@@ -1075,7 +1080,8 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
           d = c0 + cell_of<float, DIM>(p, x, y);
         }
       }
-      append_particle<DIM>(pk, out, start, cnt_out, ovo, ovf_cap, active && d >= 0, d, x, y, a, bb, c, e, s_misc);
+      append_particle<DIM>(pk, out, start, cnt_out, ovo, ovf_cap, active && d >= 0, d, x, y, a, bb, c, e, s_misc,
+                           errflag);
     }
   }
   // the last warp of the block to finish flushes the block's counters
@@ -1662,6 +1668,7 @@ void Ops<T>::step_det(const Params<T>& p, State<T>& s, int& cur, int& lay, uint3
     cudaStreamSynchronize(st);
     const long long tot = (long long)n + add;
     ntot = (int)(tot < s.capacity ? tot : s.capacity);
+    if (tot > s.capacity) s.lost = true;  // entries beyond the workspace were not written
   }
   const PBuf<T>& a = s.buf[cur];
   k_sort_stable<T, T><<<1, 1024, 0, st>>>(a.x, a.y, a.vx, a.vy, a.vz, a.ir, s.buf[other], s.key, ntot, ncells,
@@ -1709,7 +1716,7 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
         const int nb = (s.inj_max + 31) / 32;
         k_inject_bins<<<nb > 0 ? nb : 1, 32, sizeof(int32_t) * (p.nx + 1), s.side>>>(
             s.pinj, p, s.inj_mu, s.buf[other], s.start[lay], s.count[other], s.ovf[other], s.ovf_cap, sm_step,
-            s.tally, s.stats);
+            s.tally, s.stats, s.flags + 8);
         cudaEventRecord(s.ev_join, s.side);
       }
       if (p.mesh == 1) {

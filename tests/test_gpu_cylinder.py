@@ -234,3 +234,17 @@ def test_cylinder_fp32_steady_fields_match_fp64_oracle():
         ma, mb = a.mean(0), b.mean(0)
         se = np.sqrt(a.var(0, ddof=1) / len(a) + b.var(0, ddof=1) / len(b))
         assert np.all(np.abs(ma - mb) <= 4.0 * se + 0.01 * np.abs(mb)), (name, ma, mb, se)
+
+
+def test_cylinder_fp64_entry_beyond_capacity_is_reported():
+    """A workspace with room for two more particles than the initial state:
+    the freestream soon brings more, and dsmc_step says so (no silent
+    loss)."""
+    from paper_2501_10965_gb300.dsmc import DsmcError
+    cfg = _small(ntheta=12, nr=4, ppc=10, dr1=0.5)
+    n0 = oracle.OracleSim(cfg).n
+    g = _gpu(dict(cfg, capacity=n0 + 2))
+    with pytest.raises(DsmcError) as e:
+        for _ in range(100):
+            g.dsmc_step(1)
+    assert e.value.code == -2
