@@ -226,7 +226,7 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
   }
   pl.capacity = capacity;
   tile = pl.det ? (tile + 31) & ~31 : (tile + 15) & ~15;  // FP32: 16-float multiple for bulk copies
-  const int tmax = pl.det ? 256 : 512;
+  const int tmax = pl.det ? TILE_MAX_OF<double> : TILE_MAX_OF<float>;
   if (tile > tmax) tile = tmax;
   pl.tile = tile;
   pl.ovf_cap = pl.det ? 1 : (int)(pl.capacity / 16 + 1024);

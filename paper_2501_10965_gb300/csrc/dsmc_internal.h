@@ -15,6 +15,10 @@ struct PBuf {
   T *x, *y, *vx, *vy, *vz, *ir;
 };
 
+// largest particles-per-warp tile of a layout (a handle caps its tile here)
+template <typename T>
+constexpr int TILE_MAX_OF = sizeof(T) == 8 ? 256 : 512;
+
 // Particles that did not fit their destination bin (FP32 layout only).
 struct Ovf {
   float *x, *y, *vx, *vy, *vz, *ir;

@@ -1937,6 +1937,12 @@ void Ops<T>::total_count(State<T>& s, const int32_t* cnt, int ncells, cudaStream
 
 template <typename T>
 void Ops<T>::configure(int tile) {
+  // The limit is an attribute of the kernel, shared by every handle in the
+  // process: it is set for the largest tile a handle of this layout can
+  // have (only a limit; each launch still asks for its own tile's bytes),
+  // so that a later handle with a smaller tile cannot lower it under an
+  // earlier one's launches.
+  tile = TILE_MAX_OF<T>;
   const int sm = (int)tile_smem<T>(tile);
   const int smd = WPB * tile * 2 * (int)sizeof(int32_t);
   cudaFuncSetAttribute(k_collide_sample<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);

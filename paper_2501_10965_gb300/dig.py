@@ -220,6 +220,50 @@ def time_to_steady_dig_vs_plain(cfg: dict, replicas: int = 800, window: int = 10
     return out
 
 
+def train_hot_model_on_dig(cfgs: list, replicas: int = 64, iterations: int = 40, n_s: int | None = None,
+                           rounds: int = 10, steps_per_round: int = 100, lrs=(2e-3, 5e-4), seed0: int = 7000,
+                           init_seed: int = 0):
+    """Train the HoT network on the states it serves inside DIG.  Plain DIG
+    (no network) runs on `replicas` copies of each configuration (seeds from
+    seed0, independent of the runs the network will serve); after every
+    iteration the previous synthetic target -- a smooth state, the network's
+    input when it is coupled into DIG -- is paired with the HoT of the DSMC
+    window that followed it (noisy: the network learns its mean over copies
+    and iterations).  Features and labels come from a handle of the same
+    cells with Kn_ref 0 (every cell a training cell), which also holds and
+    trains the network (Adam, full batch per iteration's pairs, `rounds`
+    rounds of `steps_per_round` steps, step size lrs[0] then lrs[1]).
+    Returns (parameters as float32 numpy, a dict with the data's size and the
+    last loss)."""
+    from . import workloads
+    cases = []
+    for k, c in enumerate(cfgs):
+        cases += workloads.replicas(c, replicas, seed0 + 1000 * k)
+    g = dsmc.Dsmc(cases)
+    lab = dsmc.Dsmc([dict(c, kn_ref=0.0, ppc=1) for c in cases])
+    lab.mlp_init(init_seed)
+    ns = int(n_s if n_s is not None else cfgs[0].get("n_s", 50))
+    data, prev = [], None
+    for _ in range(iterations):
+        r = dig_iteration(g, ns, allow_not_converged=True)
+        if prev is not None:
+            fs = target_as_fields(prev)
+            _, kn_s, mask_s = lab.dsmc_hot(fs)
+            hot_w, _, _ = lab.dsmc_hot(r["fields"])
+            data.append((fs, hot_w, kn_s, mask_s))
+        prev = r["target"]
+    del g
+    loss = None
+    for rr in range(rounds):
+        lr = lrs[0] if rr < rounds // 2 else lrs[1]
+        for fs, hot_w, kn_s, mask_s in data:
+            loss = lab.mlp_train(fs, hot_w, kn_s, mask_s, steps_per_round, lr)
+    params = lab.mlp_get_params()
+    info = {"cases": len(cases), "cells": lab.ncells, "pairs": len(data), "loss": loss}
+    del lab
+    return params, info
+
+
 def train_hot_model(cfgs: list, replicas: int = 32, snapshots=(100, 300, 700, 1500, 3000, 6000),
                     window: int = 200, rounds: int = 20, steps_per_round: int = 100,
                     lrs=(2e-3, 5e-4), seed0: int = 5000, init_seed: int = 0):

@@ -122,3 +122,16 @@ def test_fused_launch_shape_is_tuned_per_handle():
     d = dsmc.Dsmc(W.fourier_1d(nx=20, ppc=30))
     d.dsmc_step(12)
     assert d.launch_config() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_handles_with_different_tiles_coexist(prec):
+    """Kernel limits are process-wide: a handle with a small tile created
+    after one with a large tile must not break the first one's steps."""
+    from paper_2501_10965_gb300 import dsmc
+    ppc = 300 if prec == "fp32" else 120
+    big = dsmc.Dsmc(W.cavity_2d(nx=8, ny=8, ppc=ppc, precision=prec))
+    small = dsmc.Dsmc(W.cavity_2d(nx=8, ny=8, ppc=2, precision=prec))
+    big.dsmc_step(3, sample=True)
+    small.dsmc_step(3, sample=True)
+    assert big.num_particles() == 8 * 8 * ppc and small.num_particles() == 8 * 8 * 2
