@@ -38,10 +38,10 @@ ALGO_BYTES_PER_PARTICLE_STEP = {("fp32", 2): 48, ("fp32", 1): 40, ("fp64", 2): 9
 # 243.33 MB for one launch; profiles/k_fused_cavity2d.md).  Re-measure
 # whenever k_fused changes.
 # Annulus: the 300 x 225-cell, 11.27 M-particle cylinder case
-# (dram__bytes_read.sum 352.43 MB + dram__bytes_write.sum 279.66 MB for one
+# (dram__bytes_read.sum 352.47 MB + dram__bytes_write.sum 279.12 MB for one
 # launch; profiles/k_fused_cylinder2d.md).
 NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP = {("fp32", 2, "box"): 580182784 / 11272500,
-                                       ("fp32", 2, "annulus"): 632093440 / 11272500}
+                                       ("fp32", 2, "annulus"): 631591424 / 11272500}
 METRIC = "particle-steps/s"
 
 
