@@ -34,15 +34,15 @@ ALGO_BYTES_PER_PARTICLE_STEP = {("fp32", 2): 48, ("fp32", 1): 40, ("fp64", 2): 9
 # DRAM bytes (read + write) per particle-step of k_fused, from one ncu capture
 # of the current kernel, scaled to a launch of the workload by its particle
 # count; keyed by (precision, dim, mesh).  Box: the 300 x 225-cell, 11.27
-# M-particle cavity (dram__bytes_read.sum 336.86 MB + dram__bytes_write.sum
-# 243.33 MB for one launch, captured before the annulus and chunked paths
-# were added; the cavity runs the whole-cell path, compiled as then).
-# Re-measure whenever k_fused changes.
+# M-particle cavity (dram__bytes_read.sum 336.42 MB + dram__bytes_write.sum
+# 243.00 MB for one launch of the current kernel, `--workload cavity2d_11m
+# --profile-steps 4 --warmup 3`, third fused launch).  Re-measure whenever
+# k_fused changes.
 # Annulus: the 300 x 225-cell, 11.27 M-particle cylinder case
 # (dram__bytes_read.sum 352.47 MB + dram__bytes_write.sum 279.12 MB for one
 # launch of the current kernel, `--workload cylinder2d_11m --profile-steps 4
 # --warmup 3`, third fused launch).
-NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP = {("fp32", 2, "box"): 580182784 / 11272500,
+NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP = {("fp32", 2, "box"): 579425536 / 11272500,
                                        ("fp32", 2, "annulus"): 631591424 / 11272500}
 METRIC = "particle-steps/s"
 
