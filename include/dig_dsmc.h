@@ -103,7 +103,12 @@ typedef struct dsmc_config {
    * V_c / F) particles.  Single case only; dsmc_hot, synth_solve,
    * dig_correct and the HoT network calls return DSMC_ERR_ARG on it. */
   int32_t mesh;
-  int32_t pad1;
+  /* 1: reserve workspace for the 2D synthetic solve of a single box case
+   * (synth_solve on dim 2).  Its banded factorisation takes about
+   * 8 N (40 m + 28) bytes, N = 5 nx ny unknowns, m = min(nx, ny) (23 MB at
+   * 24 x 24, 1.6 GB at 100 x 100); 0 leaves it out (synth_solve on a 2D
+   * handle then returns DSMC_ERR_ARG). */
+  int32_t synth2d;
   double r_in, r_out, stretch;
   double fs_rho, fs_t, fs_u[3];
 } dsmc_config;
@@ -180,15 +185,25 @@ int dsmc_hot(dsmc_handle *h, const double *dev_fields, double *dev_hot, double *
              uint8_t *dev_mask);
 
 /* Steady synthetic equations (Eq. macroscopic_equation with the
- * constitutive relations of Eq. full_constitutive), Sec. 3 step 3, for the 1D
- * slab: u_x = 0; the first and last cell keep the sampled u_y, u_z, T_t, T_r
- * (Dirichlet); total mass equals the sampled mass.  Newton iterations from
+ * constitutive relations of Eq. full_constitutive), Sec. 3 step 3.
+ * 1D slab: u_x = 0; the first and last cell keep the sampled u_y, u_z, T_t,
+ * T_r (Dirichlet); total mass equals the sampled mass.
+ * 2D box (single case, synth2d = 1, nx, ny >= 3): unknowns rho, u_x, u_y,
+ * T_t, T_r per cell (u_z keeps its sampled value); cells next to a wall keep
+ * the sampled u_x, u_y, T_t, T_r and balance their mass; the four corner
+ * cells keep their sampled state and exchange no flux; cell (1, 0)'s mass
+ * balance is replaced by the total mass; face fluxes with a fourth-difference
+ * dissipation of the conserved variables (1/32 of the face's |u_n| + sound
+ * speed).  Each Newton step factorises the central-difference Jacobian
+ * (banded, partial pivoting) in FP64; the number of Newton iterations is
+ * min(n_m, 100).  Newton iterations from
  * dev_fields until the largest relative update is below synth_tol or n_m
  * iterations.  dev_out is ncells x DSMC_NTARGET.  host_iters / host_resid
  * (may be NULL) receive the iteration count and the final max |residual|.
  * Returns DSMC_ERR_NOT_CONVERGED (outputs written) when n_m is reached, and
  * DSMC_ERR_NUMERIC when no Newton update keeps rho > 0 and T > 0 (noisy HoT
- * can make rho = (P - HoT_xx) / T_t negative); such a slab's output is its
+ * can make rho = (P - HoT_xx) / T_t negative, and a 2D case whose discrete
+ * system is singular gives no admissible update); such a case's output is its
  * sampled fields, so that the outputs can still serve as dig_correct
  * targets.  In a batch the worst status of the slabs is returned. */
 int synth_solve(dsmc_handle *h, const double *dev_fields, const double *dev_hot, double *dev_out,

@@ -132,6 +132,14 @@ int validate(const dsmc_config* c, char* why, size_t n) {
   }
   const long long ncells = (long long)c->nx * (c->dim == 2 ? c->ny : 1);
   if (ncells > (1LL << 26)) return snprintf(why, n, "too many cells"), DSMC_ERR_ARG;
+  if (c->synth2d != 0 && c->synth2d != 1) return snprintf(why, n, "synth2d must be 0 or 1"), DSMC_ERR_ARG;
+  if (c->synth2d) {
+    if (c->dim != 2 || ann || c->nx < 3 || c->ny < 3)
+      return snprintf(why, n, "synth2d needs a 2D box of at least 3 x 3 cells"), DSMC_ERR_ARG;
+    // the band storage must stay addressable with 64-bit offsets and the
+    // unknowns with int
+    if (ncells * 5 > (1LL << 28)) return snprintf(why, n, "synth2d: too many cells"), DSMC_ERR_ARG;
+  }
   if (ncells * (long long)c->ppc > (1LL << 30)) return snprintf(why, n, "too many particles"), DSMC_ERR_ARG;
   if (c->precision == DSMC_PREC_FP32 && !(c->bin_slack >= 1.0)) return snprintf(why, n, "bin_slack must be >= 1"), DSMC_ERR_ARG;
   return DSMC_OK;
@@ -223,6 +231,7 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
     int t = pl.det ? 2 * c->ppc : (5 * c->ppc) / 4 + 32;
     if (t > tile) tile = t;
     if (c->dim == 1) synth += synth1d_work_doubles(nc);
+    if (c->dim == 2 && c->synth2d) synth += synth2d_work_doubles(c->nx, c->ny);
   }
   pl.capacity = capacity;
   tile = pl.det ? (tile + 31) & ~31 : (tile + 15) & ~15;  // FP32: 16-float multiple for bulk copies
@@ -640,6 +649,7 @@ int init_cases(const dsmc_config* cfgs, int ncases, void* dev_workspace, size_t 
     if (rc) return rc;
     if (cfgs[k].dim != cfgs[0].dim || cfgs[k].precision != cfgs[0].precision) return DSMC_ERR_ARG;
     if (cfgs[k].mesh == DSMC_MESH_ANNULUS && ncases != 1) return DSMC_ERR_ARG;  // the annulus runs alone
+    if (cfgs[k].synth2d && ncases != 1) return DSMC_ERR_ARG;                    // so does the 2D solve
   }
   const Plan pl = make_plan(cfgs, ncases, nullptr, nullptr);
   if (!dev_workspace || bytes < pl.bytes) return DSMC_ERR_ARG;
@@ -712,6 +722,7 @@ int dsmc_batch_workspace_size(const dsmc_config* cfgs, int ncases, size_t* bytes
     if (rc) return rc;
     if (cfgs[k].dim != cfgs[0].dim || cfgs[k].precision != cfgs[0].precision) return DSMC_ERR_ARG;
     if (cfgs[k].mesh == DSMC_MESH_ANNULUS && ncases != 1) return DSMC_ERR_ARG;
+    if (cfgs[k].synth2d && ncases != 1) return DSMC_ERR_ARG;
   }
   *bytes = make_plan(cfgs, ncases, nullptr, nullptr).bytes;
   return DSMC_OK;
@@ -790,10 +801,37 @@ int dsmc_hot(dsmc_handle* h, const double* dev_fields, double* dev_hot, double* 
   return check_cuda(h, "dsmc_hot");
 }
 
+// the 2D box (single case, workspace reserved by synth2d)
+static int synth_solve_2d(dsmc_handle* h, const double* dev_fields, const double* dev_hot, double* dev_out,
+                          int* host_iters, double* host_resid) {
+  const dsmc_config& c = h->cfg;
+  if (h->ncases != 1 || !c.synth2d)
+    return set_err(h, DSMC_ERR_ARG, "synth_solve: a 2D case needs synth2d = 1 (workspace for the banded solve)");
+  const int n_m = std::min(c.n_m > 0 ? c.n_m : 2000, 100);
+  const double tol = c.synth_tol > 0 ? c.synth_tol : 1e-5;
+  int singular = 0;
+  const int e = launch_synth2d(h->cp, dev_fields, dev_hot, dev_out, h->synth_work, n_m, tol, h->synth_info,
+                               &singular, h->stream);
+  if (e) return set_err(h, DSMC_ERR_CUDA, "synth_solve: %s", cudaGetErrorString((cudaError_t)e));
+  double info[3];
+  cudaMemcpyAsync(info, h->synth_info, sizeof info, cudaMemcpyDeviceToHost, h->stream);
+  const int r = sync_check(h, "synth_solve");
+  if (r) return r;
+  if (host_iters) *host_iters = (int)info[0];
+  if (host_resid) *host_resid = info[1];
+  const int status = (int)info[2];
+  if (status == 2)
+    return set_err(h, DSMC_ERR_NUMERIC, "synth_solve: no update keeps rho, T positive%s",
+                   singular ? " (singular Jacobian)" : "");
+  if (status == 1) return set_err(h, DSMC_ERR_NOT_CONVERGED, "synth_solve: %d iterations without convergence", n_m);
+  return DSMC_OK;
+}
+
 int synth_solve(dsmc_handle* h, const double* dev_fields, const double* dev_hot, double* dev_out, int* host_iters,
                 double* host_resid) {
   if (!h || !dev_fields || !dev_hot || !dev_out) return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "synth_solve: only the 1D slab is implemented");
+  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "synth_solve: not on the annulus");
+  if (h->cfg.dim == 2) return synth_solve_2d(h, dev_fields, dev_hot, dev_out, host_iters, host_resid);
   int n_m = 0;
   double tol = 1.0;
   for (int k = 0; k < h->ncases; ++k) {

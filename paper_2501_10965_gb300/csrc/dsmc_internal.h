@@ -146,6 +146,12 @@ void launch_synth1d(const CellParams* cp, const int32_t* cell_case, const int32_
 void launch_synth1d_single(const CellParams& cp, const double* fields, const double* hot, double* out,
                            double* work, int n_m, double tol, double* info, cudaStream_t st);
 size_t synth1d_work_doubles(int ncells);
+// 2D synthetic equations of one box case (dsmc_synth2d.cu): doubles of work,
+// and the solve (info = iterations, max residual, status; *singular set when
+// a zero pivot was met); returns a cudaError_t value
+size_t synth2d_work_doubles(int nx, int ny);
+int launch_synth2d(const CellParams& cp, const double* fields, const double* hot, double* out, double* work,
+                   int n_m, double tol, double* info, int* singular, cudaStream_t st);
 
 // HoT surrogate network (dsmc_mlp.cu): 12 -> 64 -> 64 -> 64 -> 5, tanh
 // hidden layers; parameters per layer: W (n_out x n_in, row major), then b.

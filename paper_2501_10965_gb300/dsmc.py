@@ -53,7 +53,7 @@ class DsmcConfig(ctypes.Structure):
         ("kn_ref", ctypes.c_double), ("synth_tol", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("capacity", ctypes.c_int64),
         ("bin_slack", ctypes.c_double),
-        ("mesh", ctypes.c_int32), ("pad1", ctypes.c_int32),
+        ("mesh", ctypes.c_int32), ("synth2d", ctypes.c_int32),
         ("r_in", ctypes.c_double), ("r_out", ctypes.c_double), ("stretch", ctypes.c_double),
         ("fs_rho", ctypes.c_double), ("fs_t", ctypes.c_double), ("fs_u", ctypes.c_double * 3),
     ]
@@ -153,6 +153,7 @@ def make_config(cfg: dict) -> DsmcConfig:
     c.capacity = int(cfg.get("capacity", 0) or 0)
     c.bin_slack = float(cfg.get("bin_slack", 2.0))
     c.mesh = MESH[cfg.get("mesh", "box")]
+    c.synth2d = 1 if cfg.get("synth2d", False) else 0
     c.r_in, c.r_out = float(cfg.get("r_in", 0.5)), float(cfg.get("r_out", 5.5))
     c.stretch = float(cfg.get("stretch", 1.0))
     c.fs_rho, c.fs_t = float(cfg.get("fs_rho", 1.0)), float(cfg.get("fs_t", 1.0))
