@@ -104,10 +104,10 @@ typedef struct dsmc_config {
    * dig_correct and the HoT network calls return DSMC_ERR_ARG on it. */
   int32_t mesh;
   /* 1: reserve workspace for the 2D synthetic solve of a single box case
-   * (synth_solve on dim 2).  Its banded factorisation takes about
-   * 8 N (40 m + 28) bytes, N = 5 nx ny unknowns, m = min(nx, ny) (23 MB at
-   * 24 x 24, 1.6 GB at 100 x 100); 0 leaves it out (synth_solve on a 2D
-   * handle then returns DSMC_ERR_ARG). */
+   * (synth_solve on dim 2; min(nx, ny) <= 500).  Its banded factorisation
+   * takes about 8 N (20 m + 104) bytes, N = 5 nx ny unknowns,
+   * m = min(nx, ny) (14 MB at 24 x 24, 0.84 GB at 100 x 100); 0 leaves it
+   * out (synth_solve on a 2D handle then returns DSMC_ERR_ARG). */
   int32_t synth2d;
   double r_in, r_out, stretch;
   double fs_rho, fs_t, fs_u[3];
@@ -194,9 +194,11 @@ int dsmc_hot(dsmc_handle *h, const double *dev_fields, double *dev_hot, double *
  * cells keep their sampled state and exchange no flux; cell (1, 0)'s mass
  * balance is replaced by the total mass; face fluxes with a fourth-difference
  * dissipation of the conserved variables (1/32 of the face's |u_n| + sound
- * speed).  Each Newton step factorises the central-difference Jacobian
- * (banded, partial pivoting) in FP64; the number of Newton iterations is
- * min(n_m, 100).  Newton iterations from
+ * speed).  Residual and central-difference Jacobian in FP64; each Newton step
+ * solves with a blocked banded LU factorisation (partial pivoting) of the
+ * Jacobian in FP32 and one sweep of iterative refinement with an FP64
+ * residual; the number of
+ * Newton iterations is min(n_m, 100).  Newton iterations from
  * dev_fields until the largest relative update is below synth_tol or n_m
  * iterations.  dev_out is ncells x DSMC_NTARGET.  host_iters / host_resid
  * (may be NULL) receive the iteration count and the final max |residual|.

@@ -23,7 +23,7 @@ UNITS = {
     "dsmc_fields.cu": ["-fmad=false"],
     "dsmc_capi.cu": ["-fmad=false"],
     "dsmc_noalloc.cu": ["-fmad=false"],
-    "dsmc_synth2d.cu": ["-fmad=false"],
+    "dsmc_synth2d.cu": [],
     "dsmc_mlp.cu": [],
 }
 

@@ -136,6 +136,8 @@ int validate(const dsmc_config* c, char* why, size_t n) {
   if (c->synth2d) {
     if (c->dim != 2 || ann || c->nx < 3 || c->ny < 3)
       return snprintf(why, n, "synth2d needs a 2D box of at least 3 x 3 cells"), DSMC_ERR_ARG;
+    if (std::min(c->nx, c->ny) > 500)
+      return snprintf(why, n, "synth2d: the shorter side must have at most 500 cells"), DSMC_ERR_ARG;
     // the band storage must stay addressable with 64-bit offsets and the
     // unknowns with int
     if (ncells * 5 > (1LL << 28)) return snprintf(why, n, "synth2d: too many cells"), DSMC_ERR_ARG;

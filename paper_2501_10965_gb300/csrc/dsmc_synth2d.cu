@@ -1,18 +1,20 @@
 // dsmc_synth2d.cu -- the steady 2D synthetic equations of the DIG method
 // (Sec. 3 step 3) on the GPU: Newton's method with the residual and a
-// central-difference Jacobian in FP64 (dsmc_synth2d.cuh), and a direct
-// banded LU factorisation with partial pivoting for each Newton step.
+// central-difference Jacobian in FP64 (dsmc_synth2d.cuh); each Newton step
+// solves with a blocked banded LU factorisation (partial pivoting) of the
+// Jacobian in FP32, substitutions in FP32 and one sweep of iterative
+// refinement with FP64 residuals.
 //
 // The total-mass row (cell (1, 0)'s mass balance replaced by the total mass)
 // couples every cell; the factorised matrix B has e_r / n there instead, and
 // the Newton step of J = B + e_r w^T (w = 1/n on the density of every other
 // cell) follows from two solves with B (Sherman-Morrison).
 //
-// The factorisation runs one launch per pivot column k: CTA b updates column
-// k + 1 + b (interchange and elimination with the multipliers of column k),
-// and CTA 0, which owns column k + 1, then finds that column's pivot and
-// multipliers for the next launch.  The launches on one stream order the
-// steps; within a launch no two CTAs touch one column.
+// Factorisation: per panel of nb columns, one CTA factorises the panel in
+// shared memory, then one launch applies it to the up to kl + ku trailing
+// columns, cb columns per CTA.  Substitution: one CTA walks the panels,
+// forward then backward, with the panel's window of the right-hand sides in
+// shared memory.  The launches on one stream order the panels.
 #include <climits>
 #include <cmath>
 #include <cstdint>
@@ -39,38 +41,74 @@ enum {
   S2_NSC = 16
 };
 
+constexpr int S2_NT = 256;        // threads of the factorisation and substitution kernels
+constexpr int S2_UPD_NT = 512;    // the Newton update
+constexpr int S2_SUB_NT = 512;    // the substitutions
+constexpr int S2_PNL_NT = 512;    // the panel factorisation
+constexpr int S2_NREF = 1;        // refinement sweeps per Newton step
+constexpr int S2_SMEM_CAP = 200 * 1024;
+
+// Panel width nb and trailing columns per CTA cb (4: enough CTAs to fill the
+// GPU for the kl + ku trailing columns): the largest nb of 32, 16, 8 whose
+// panel and nb + cb trailing columns (H = kl + nb rows, FP32) fit the
+// shared-memory budget.
+struct S2Blocking {
+  int nb, cb;
+};
+
+inline S2Blocking s2_blocking(const s2::Grid& g) {
+  for (int nb = 32; nb >= 8; nb /= 2) {
+    const long long col = 4LL * (g.kl + nb);
+    const long long cb = S2_SMEM_CAP / col - nb;
+    if (cb >= 4 || (nb == 8 && cb >= 1)) return {nb, cb >= 4 ? 4 : (int)cb};
+  }
+  return {0, 0};
+}
+
 struct S2Work {
-  double *x, *R, *d, *b0, *b1, *y0, *y1, *z, *yv, *ud, *sc, *AB, *Lm;
+  double *x, *R, *d, *rhs0, *rhs1, *b0, *b1, *y0, *y1, *v0, *v1, *s0, *s1, *sc, *Jc;
+  float *AB, *Lp, *ud;
   int32_t* piv;
+  int nb, cb;
 };
 
 inline size_t round32(size_t n) { return (n + 31) & ~(size_t)31; }  // 256-byte multiples
 
+inline size_t s2_lp_floats(const s2::Grid& g, int nb) { return (size_t)((g.N + nb - 1) / nb) * nb * (g.kl + nb); }
+
 inline size_t s2_doubles(const s2::Grid& g) {
+  const S2Blocking bl = s2_blocking(g);
   const size_t N = (size_t)g.N;
-  const size_t vec = (N + 31) & ~(size_t)31;
-  return 10 * vec + 32 + (((size_t)g.ld * N + 31) & ~(size_t)31) + (((size_t)g.kl * N + 31) & ~(size_t)31) +
-         ((N / 2 + 1 + 31) & ~(size_t)31);
+  const size_t vec = round32(N);
+  const size_t jc = round32((size_t)g.n * s2::NSTENCIL * s2::NV * s2::NV);
+  const size_t f32 = (size_t)g.ld * N + s2_lp_floats(g, bl.nb) + N + N;  // AB, Lp, ud, piv
+  return 13 * vec + 32 + jc + round32((f32 + 1) / 2) + 32;
 }
 
 S2Work s2_carve(const s2::Grid& g, double* w) {
+  const S2Blocking bl = s2_blocking(g);
   const size_t vec = round32((size_t)g.N);
   S2Work s;
   double* p = w;
-  s.x = p; p += vec;
-  s.R = p; p += vec;
-  s.d = p; p += vec;
-  s.b0 = p; p += vec;
-  s.b1 = p; p += vec;
-  s.y0 = p; p += vec;
-  s.y1 = p; p += vec;
-  s.z = p; p += vec;
-  s.yv = p; p += vec;
-  s.ud = p; p += vec;
-  s.sc = p; p += 32;
-  s.AB = p; p += round32((size_t)g.ld * g.N);
-  s.Lm = p; p += round32((size_t)g.kl * g.N);
-  s.piv = reinterpret_cast<int32_t*>(p);
+  double** vecs[13] = {&s.x, &s.R, &s.d, &s.rhs0, &s.rhs1, &s.b0, &s.b1, &s.y0, &s.y1, &s.v0, &s.v1, &s.s0, &s.s1};
+  for (double** v : vecs) {
+    *v = p;
+    p += vec;
+  }
+  s.sc = p;
+  p += 32;
+  s.Jc = p;
+  p += round32((size_t)g.n * s2::NSTENCIL * s2::NV * s2::NV);
+  float* f = reinterpret_cast<float*>(p);
+  s.AB = f;
+  f += (size_t)g.ld * g.N;
+  s.Lp = f;
+  f += s2_lp_floats(g, bl.nb);
+  s.ud = f;
+  f += g.N;
+  s.piv = reinterpret_cast<int32_t*>(f);
+  s.nb = bl.nb;
+  s.cb = bl.cb;
   return s;
 }
 
@@ -104,45 +142,7 @@ __device__ double s2_block_max(double v, double* red) {
   return r;
 }
 
-// First row of largest |A(r, k)|, r = k .. min(k + kl, N - 1), as
-// s2::pivot_seq; rows whose magnitude is not a number never win, and a
-// column without any number pivots on its diagonal.
-template <int NT>
-__device__ int s2_block_argmax(const s2::Grid& g, const double* AB, int k, double* sv, int* si) {
-  const int tid = threadIdx.x;
-  double best = -1.0;
-  int bi = INT_MAX;
-  const int rmax = s2::last_row(g, k);
-  for (int r = k + tid; r <= rmax; r += NT) {
-    const double a = fabs(AB[s2::band_at(g, r, k)]);
-    if (a > best) {
-      best = a;
-      bi = r;
-    }
-  }
-  sv[tid] = best;
-  si[tid] = bi;
-  __syncthreads();
-#pragma unroll
-  for (int o = NT / 2; o > 0; o >>= 1) {
-    if (tid < o) {
-      const double v2 = sv[tid + o];
-      const int i2 = si[tid + o];
-      if (v2 > sv[tid] || (v2 == sv[tid] && i2 < si[tid])) {
-        sv[tid] = v2;
-        si[tid] = i2;
-      }
-    }
-    __syncthreads();
-  }
-  const int p = si[0];
-  __syncthreads();
-  return p == INT_MAX ? k : p;
-}
-
-constexpr int S2_NT = 256;    // single-CTA kernels
-constexpr int S2_STEP_NT = 128;
-constexpr int S2_SOLVE_NT = 512;
+extern __shared__ __align__(16) unsigned char s2_smem[];
 
 __global__ void __launch_bounds__(S2_NT) k_s2_init(const s2::Grid g, S2Work w) {
   __shared__ double red[S2_NT];
@@ -194,85 +194,322 @@ __global__ void k_s2_jac(const s2::Grid g, S2Work w) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t == 0) {
     const int mr = s2::mass_row(g);
-    w.AB[s2::band_at(g, mr, mr)] = 1.0 / g.n;
+    w.AB[s2::band_at(g, mr, mr)] = (float)(1.0 / g.n);
   }
   if (t >= g.n * s2::NSTENCIL * s2::NV) return;
   const int b = t / (s2::NSTENCIL * s2::NV);
   const int rem = t - b * (s2::NSTENCIL * s2::NV);
-  s2::jacobian_entries(g, w.x, b, rem / s2::NV, rem % s2::NV, w.AB);
+  s2::jacobian_entries(g, w.x, b, rem / s2::NV, rem % s2::NV, w.AB, w.Jc);
 }
 
-// pivot and multipliers of column 0
-__global__ void __launch_bounds__(S2_STEP_NT) k_s2_piv0(const s2::Grid g, S2Work w) {
-  __shared__ double sv[S2_STEP_NT];
-  __shared__ int si[S2_STEP_NT];
-  const int p = s2_block_argmax<S2_STEP_NT>(g, w.AB, 0, sv, si);
-  const int sing = s2::pivot_write(g, w.AB, w.Lm, w.piv, w.ud, 0, p, threadIdx.x, S2_STEP_NT);
-  if (sing && threadIdx.x == 0) w.sc[S2_SING] = 1.0;
-}
-
-// elimination step k on columns k+1 .. last_col(k) (one CTA each); CTA 0 then
-// pivots column k + 1
-__global__ void __launch_bounds__(S2_STEP_NT) k_s2_step(const s2::Grid g, S2Work w, int k) {
-  __shared__ double sv[S2_STEP_NT];
-  __shared__ int si[S2_STEP_NT];
-  const int c = k + 1 + blockIdx.x;
-  if (c > s2::last_col(g, k)) return;
-  const s2::ColHead h = s2::col_head(g, w.AB, w.piv, k, c);
+// First row of largest |P(r, j)|, r = j .. panel_rmax, as s2::panel_pivot_seq
+// (magnitudes that are not numbers never win; such a column pivots on its
+// diagonal); *best gets the pivot's magnitude.
+__device__ int s2_panel_argmax(const s2::Grid& g, const float* P, int H, int j, float* sv, int* si, float& best_out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = S2_PNL_NT / 32;
+  const float* col = P + (size_t)j * H;
+  const int rmax = s2::panel_rmax(g, H, j);
+  float best = -1.0f;
+  int bi = INT_MAX;
+  for (int r = j + tid; r <= rmax; r += S2_PNL_NT) {
+    const float a = fabsf(col[r]);
+    if (a > best) {
+      best = a;
+      bi = r;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_down_sync(0xffffffffu, best, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  if (lane == 0) {
+    sv[warp] = best;
+    si[warp] = bi;
+  }
   __syncthreads();
-  s2::lu_column(g, w.AB, w.Lm, w.piv, k, c, h, threadIdx.x, S2_STEP_NT);
-  if (blockIdx.x != 0) return;
+  if (warp == 0) {
+    best = lane < NW ? sv[lane] : -1.0f;
+    bi = lane < NW ? si[lane] : INT_MAX;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ob = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      sv[NW] = best;
+      si[NW] = bi;
+    }
+  }
   __syncthreads();
-  const int p = s2_block_argmax<S2_STEP_NT>(g, w.AB, k + 1, sv, si);
-  const int sing = s2::pivot_write(g, w.AB, w.Lm, w.piv, w.ud, k + 1, p, threadIdx.x, S2_STEP_NT);
-  if (sing && threadIdx.x == 0) w.sc[S2_SING] = 1.0;
+  const int p = si[NW];
+  best_out = sv[NW];
+  __syncthreads();
+  return p == INT_MAX ? j : p;
 }
 
-// Solves with the factors (right-hand sides -R and e_r), the rank-one
-// correction for the total-mass row, the damped update that keeps rho, T_t,
-// T_r positive and finite (step halved up to 60 times), and the convergence
-// test on the largest relative update (|lam dx| / max(|x|, 1e-3) < tol).
-__global__ void __launch_bounds__(S2_SOLVE_NT) k_s2_solve(const s2::Grid g, S2Work w, int n_m, double tol) {
-  __shared__ double red[S2_SOLVE_NT];
+// factorisation of the panel at column k0 (one CTA; panel in shared memory)
+__global__ void __launch_bounds__(S2_PNL_NT) k_s2_panel(const s2::Grid g, S2Work w, int k0) {
+  __shared__ float sv[S2_PNL_NT / 32 + 1];
+  __shared__ int si[S2_PNL_NT / 32 + 1];
+  float* P = reinterpret_cast<float*>(s2_smem);
+  const int tid = threadIdx.x;
+  const int wd = s2::panel_width(g, w.nb, k0), H = s2::panel_height(g, wd, k0);
+  s2::panel_load(g, w.AB, k0, wd, H, P, tid, S2_PNL_NT);
+  __syncthreads();
+  for (int j = 0; j < wd; ++j) {
+    float best;
+    const int p = s2_panel_argmax(g, P, H, j, sv, si, best);
+    if (tid == 0) {
+      w.piv[k0 + j] = k0 + p;
+      if (!(best > 0.0f)) w.sc[S2_SING] = 1.0;
+    }
+    s2::panel_swap(P, H, wd, j, p, tid, S2_PNL_NT);
+    __syncthreads();
+    s2::panel_scale(g, P, H, j, tid, S2_PNL_NT);
+    __syncthreads();
+    s2::panel_rank1(g, P, H, wd, j, tid, S2_PNL_NT, 4);
+    __syncthreads();
+  }
+  s2::panel_store(g, w.nb, w.AB, w.Lp, w.ud, k0, wd, H, P, tid, S2_PNL_NT);
+}
+
+// the panel's interchanges and eliminations on cb trailing columns per CTA
+__global__ void __launch_bounds__(S2_NT) k_s2_trail(const s2::Grid g, S2Work w, int k0) {
+  const int tid = threadIdx.x;
+  const int wd = s2::panel_width(g, w.nb, k0), H = s2::panel_height(g, wd, k0);
+  const int cfirst = k0 + wd + blockIdx.x * w.cb;
+  const int clast = s2::trail_last(g, k0, wd);
+  const int ncols = clast - cfirst + 1 < w.cb ? clast - cfirst + 1 : w.cb;
+  if (ncols <= 0) return;
+  float* Ls = reinterpret_cast<float*>(s2_smem);
+  float* Cs = Ls + (size_t)wd * H;
+  s2::trail_load_l(g, w.nb, w.Lp, k0, wd, H, Ls, tid, S2_NT);
+  s2::trail_load_cols(g, w.AB, k0, H, cfirst, ncols, Cs, tid, S2_NT);
+  __syncthreads();
+  s2::trail_swaps(w.piv, k0, wd, H, ncols, Cs, tid, S2_NT);
+  __syncthreads();
+  // unit-lower solve with the panel's top block: one warp per column, lane i
+  // holding row i (the same eliminations as s2::trail_l11_step, in order)
+  {
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int cc = warp; cc < ncols; cc += S2_NT / 32) {
+      float* a = Cs + (size_t)cc * H;
+      float ai = lane < wd ? a[lane] : 0.0f;
+      for (int j = 0; j < wd; ++j) {
+        const float aj = __shfl_sync(0xffffffffu, ai, j);
+        if (lane > j && lane < wd) ai -= Ls[(size_t)j * H + lane] * aj;
+      }
+      if (lane < wd) a[lane] = ai;
+    }
+  }
+  __syncthreads();
+  s2::trail_l21(Ls, wd, H, ncols, Cs, tid, S2_NT);
+  __syncthreads();
+  s2::trail_store(g, w.AB, k0, H, cfirst, ncols, Cs, tid, S2_NT);
+}
+
+// Forward and backward substitution with the FP32 factors for two
+// right-hand sides in FP32 arithmetic (the refinement's FP64 residuals make
+// up the precision): b0, b1 (consumed) -> o0, o1; y0, y1 scratch.  One CTA;
+// the current panel's window of the right-hand sides and its pivots in
+// shared memory.
+__global__ void __launch_bounds__(S2_SUB_NT) k_s2_subst(const s2::Grid g, S2Work w, double* b0, double* b1, double* o0,
+                                                        double* o1) {
+  __shared__ int spiv[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = w.nb, N = g.N;
+  const int span = g.kl + g.ku + nb;
+  const int ldp = g.kl + nb;
+  float* t0 = reinterpret_cast<float*>(s2_smem);
+  float* t1 = t0 + span;
+  double* y0 = w.y0;
+  double* y1 = w.y1;
+  for (int k0 = 0; k0 < N; k0 += nb) {
+    const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
+    for (int r = tid; r < H; r += S2_SUB_NT) {
+      t0[r] = (float)b0[k0 + r];
+      t1[r] = (float)b1[k0 + r];
+    }
+    if (tid < wd) spiv[tid] = w.piv[k0 + tid] - k0;
+    __syncthreads();
+    if (tid == 0) {
+      for (int j = 0; j < wd; ++j) {
+        const int p = spiv[j];
+        if (p != j) {
+          float t = t0[j];
+          t0[j] = t0[p];
+          t0[p] = t;
+          t = t1[j];
+          t1[j] = t1[p];
+          t1[p] = t;
+        }
+      }
+    }
+    __syncthreads();
+    const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
+    if (warp == 0) {
+      const int i = lane;
+      float a0 = i < wd ? t0[i] : 0.0f, a1 = i < wd ? t1[i] : 0.0f;
+      float lr[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) lr[jj] = (jj < i && i < wd) ? Lk[(size_t)jj * ldp + i] : 0.0f;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        if (jj < wd) {
+          const float y0j = __shfl_sync(0xffffffffu, a0, jj);
+          const float y1j = __shfl_sync(0xffffffffu, a1, jj);
+          if (i > jj && i < wd) {
+            a0 -= lr[jj] * y0j;
+            a1 -= lr[jj] * y1j;
+          }
+        }
+      }
+      if (i < wd) {
+        t0[i] = a0;
+        t1[i] = a1;
+        y0[k0 + i] = a0;
+        y1[k0 + i] = a1;
+      }
+    }
+    __syncthreads();
+    for (int r = wd + tid; r < H; r += S2_SUB_NT) {
+      float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        if (jj < wd) {
+          const float l = Lk[(size_t)jj * ldp + r];
+          acc0 += l * t0[jj];
+          acc1 += l * t1[jj];
+        }
+      }
+      b0[k0 + r] = t0[r] - acc0;
+      b1[k0 + r] = t1[r] - acc1;
+    }
+    __syncthreads();
+  }
+  for (int k0 = ((N - 1) / nb) * nb; k0 >= 0; k0 -= nb) {
+    const int wd = s2::panel_width(g, nb, k0);
+    const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
+    const int nwin = k0 + wd - lo;
+    for (int r = tid; r < nwin; r += S2_SUB_NT) {
+      t0[r] = (float)y0[lo + r];
+      t1[r] = (float)y1[lo + r];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int i = lane;
+      float a0 = i < wd ? t0[k0 - lo + i] : 0.0f, a1 = i < wd ? t1[k0 - lo + i] : 0.0f;
+      const float dg = i < wd ? w.ud[k0 + i] : 1.0f;
+      float ur[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) ur[jj] = (jj > i && jj < wd) ? s2::umul(g, w.AB, k0 + i, k0 + jj) : 0.0f;
+      float x0i = 0.0f, x1i = 0.0f;
+#pragma unroll
+      for (int jj = 31; jj >= 0; --jj) {
+        if (jj < wd) {
+          const float x0j = __shfl_sync(0xffffffffu, a0 / dg, jj);
+          const float x1j = __shfl_sync(0xffffffffu, a1 / dg, jj);
+          if (i == jj) {
+            x0i = x0j;
+            x1i = x1j;
+          }
+          if (i < jj) {
+            a0 -= ur[jj] * x0j;
+            a1 -= ur[jj] * x1j;
+          }
+        }
+      }
+      if (i < wd) {
+        t0[k0 - lo + i] = x0i;
+        t1[k0 - lo + i] = x1i;
+        o0[k0 + i] = x0i;
+        o1[k0 + i] = x1i;
+      }
+    }
+    __syncthreads();
+    for (int r = lo + tid; r < k0; r += S2_SUB_NT) {
+      float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        if (jj < wd) {
+          const float u = s2::umul(g, w.AB, r, k0 + jj);
+          acc0 += u * t0[k0 - lo + jj];
+          acc1 += u * t1[k0 - lo + jj];
+        }
+      }
+      y0[r] = t0[r - lo] - acc0;
+      y1[r] = t1[r - lo] - acc1;
+    }
+    __syncthreads();
+  }
+}
+
+// right-hand sides of a Newton step: -R and e_r (the total-mass row)
+__global__ void k_s2_prep(const s2::Grid g, S2Work w) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= g.N) return;
+  const double r0 = -w.R[u], r1 = u == s2::mass_row(g) ? 1.0 : 0.0;
+  w.rhs0[u] = r0;
+  w.rhs1[u] = r1;
+  w.b0[u] = r0;
+  w.b1[u] = r1;
+}
+
+// refinement residuals in FP64: b = rhs - B v
+__global__ void k_s2_bmv(const s2::Grid g, S2Work w) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= g.N) return;
+  w.b0[u] = w.rhs0[u] - s2::bmv_row(g, w.Jc, w.v0, u);
+  w.b1[u] = w.rhs1[u] - s2::bmv_row(g, w.Jc, w.v1, u);
+}
+
+__global__ void k_s2_add(const s2::Grid g, S2Work w) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= g.N) return;
+  w.v0[u] += w.s0[u];
+  w.v1[u] += w.s1[u];
+}
+
+// The rank-one correction for the total-mass row (z = v0, y = v1), the damped
+// update that keeps rho, T_t, T_r positive and finite (step halved up to 60
+// times), and the convergence test on the largest relative update
+// (|lam dx| / max(|x|, 1e-3) < tol).
+__global__ void __launch_bounds__(S2_UPD_NT) k_s2_newton(const s2::Grid g, S2Work w, int n_m, double tol) {
+  __shared__ double red[S2_UPD_NT];
   const int tid = threadIdx.x;
   const int N = g.N;
   const int mr = s2::mass_row(g);
-  for (int u = tid; u < N; u += S2_SOLVE_NT) {
-    w.b0[u] = -w.R[u];
-    w.b1[u] = u == mr ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  for (int k = 0; k < N; ++k) {
-    const s2::FwdHead h = s2::fwd_head(w.piv, k, w.b0, w.b1);
-    __syncthreads();
-    s2::fwd_step(g, w.Lm, w.piv, k, h, w.b0, w.b1, w.y0, w.y1, tid, S2_SOLVE_NT);
-    __syncthreads();
-  }
-  for (int k = N - 1; k >= 0; --k) {
-    s2::back_step(g, w.AB, w.ud, k, w.y0, w.y1, w.z, w.yv, tid, S2_SOLVE_NT);
-    __syncthreads();
-  }
   double wz = 0.0, wy = 0.0;
-  for (int b = tid; b < g.n; b += S2_SOLVE_NT) {
+  for (int b = tid; b < g.n; b += S2_UPD_NT) {
     if (s2::NV * b == mr) continue;
-    wz += w.z[s2::NV * b];
-    wy += w.yv[s2::NV * b];
+    wz += w.v0[s2::NV * b];
+    wy += w.v1[s2::NV * b];
   }
-  wz = s2_block_sum<S2_SOLVE_NT>(wz, red) / g.n;
-  wy = s2_block_sum<S2_SOLVE_NT>(wy, red) / g.n;
+  wz = s2_block_sum<S2_UPD_NT>(wz, red) / g.n;
+  wy = s2_block_sum<S2_UPD_NT>(wy, red) / g.n;
   const double f = wz / (1.0 + wy);
-  for (int u = tid; u < N; u += S2_SOLVE_NT) w.d[u] = w.z[u] - w.yv[u] * f;
+  for (int u = tid; u < N; u += S2_UPD_NT) w.d[u] = w.v0[u] - w.v1[u] * f;
   __syncthreads();
   double lam = 1.0;
   bool ok = false;
   for (int hv = 0; hv < 60 && !ok; ++hv) {
     double bad = 0.0;
-    for (int u = tid; u < N; u += S2_SOLVE_NT) {
+    for (int u = tid; u < N; u += S2_UPD_NT) {
       const double xn = w.x[u] + lam * w.d[u];
       const int v = u % s2::NV;
       if (!isfinite(xn) || ((v == 0 || v >= 3) && xn <= 0.0)) bad = 1.0;
     }
-    ok = s2_block_max<S2_SOLVE_NT>(bad, red) == 0.0;
+    ok = s2_block_max<S2_UPD_NT>(bad, red) == 0.0;
     if (!ok) lam *= 0.5;
   }
   if (!ok) {
@@ -283,13 +520,13 @@ __global__ void __launch_bounds__(S2_SOLVE_NT) k_s2_solve(const s2::Grid g, S2Wo
     return;
   }
   double dm = 0.0;
-  for (int u = tid; u < N; u += S2_SOLVE_NT) {
+  for (int u = tid; u < N; u += S2_UPD_NT) {
     const double x = w.x[u];
     const double step = lam * w.d[u];
     dm = fmax(dm, fabs(step) / fmax(fabs(x), 1e-3));
     w.x[u] = x + step;
   }
-  dm = s2_block_max<S2_SOLVE_NT>(dm, red);
+  dm = s2_block_max<S2_UPD_NT>(dm, red);
   if (tid == 0) {
     const double it = w.sc[S2_IT] + 1.0;
     w.sc[S2_IT] = it;
@@ -341,6 +578,20 @@ __global__ void __launch_bounds__(S2_NT) k_s2_final(const s2::Grid g, S2Work w, 
   }
 }
 
+// shared-memory limits of the dynamic-size kernels, raised (never lowered)
+// to what a solve needs
+void s2_smem_limits(size_t panel, size_t trail, size_t subst) {
+  static size_t set[3] = {48 * 1024, 48 * 1024, 48 * 1024};
+  const void* fn[3] = {(const void*)k_s2_panel, (const void*)k_s2_trail, (const void*)k_s2_subst};
+  const size_t need[3] = {panel, trail, subst};
+  for (int k = 0; k < 3; ++k) {
+    if (need[k] > set[k]) {
+      cudaFuncSetAttribute(fn[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need[k]);
+      set[k] = need[k];
+    }
+  }
+}
+
 }  // namespace
 
 size_t synth2d_work_doubles(int nx, int ny) {
@@ -353,20 +604,40 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
   const s2::Grid g = s2::make_grid(cp.nx, cp.ny, cp.dx, cp.dy, cp.d_r, cp.omega, cp.mu_ref, cp.z_rot, cp.kappa_t,
                                    cp.kappa_r, fields, hot);
   const S2Work w = s2_carve(g, work);
-  const int nb = 256;
-  const int res_grid = (g.n + nb - 1) / nb;
+  if (w.nb == 0) return (int)cudaErrorInvalidValue;
+  const int nb = w.nb;
+  const size_t hmax = (size_t)g.kl + nb;
+  const size_t sm_panel = sizeof(float) * nb * hmax;
+  const size_t sm_trail = sizeof(float) * (nb + w.cb) * hmax;
+  const size_t sm_subst = sizeof(float) * 2 * ((size_t)g.kl + g.ku + nb);
+  s2_smem_limits(sm_panel, sm_trail, sm_subst);
+  const int nt = 256;
+  const int cell_grid = (g.n + nt - 1) / nt;
+  const int vec_grid = (g.N + nt - 1) / nt;
   const long long jac_threads = (long long)g.n * s2::NSTENCIL * s2::NV;
-  const int jac_grid = (int)((jac_threads + nb - 1) / nb);
+  const int jac_grid = (int)((jac_threads + nt - 1) / nt);
   double sc[S2_NSC];
   k_s2_init<<<1, S2_NT, 0, st>>>(g, w);
   for (int it = 0; it < n_m; ++it) {
     k_s2_mass<<<1, S2_NT, 0, st>>>(g, w);
-    k_s2_res<<<res_grid, nb, 0, st>>>(g, w);
-    cudaMemsetAsync(w.AB, 0, sizeof(double) * (size_t)g.ld * g.N, st);
-    k_s2_jac<<<jac_grid, nb, 0, st>>>(g, w);
-    k_s2_piv0<<<1, S2_STEP_NT, 0, st>>>(g, w);
-    for (int k = 0; k < g.N - 1; ++k) k_s2_step<<<s2::last_col(g, k) - k, S2_STEP_NT, 0, st>>>(g, w, k);
-    k_s2_solve<<<1, S2_SOLVE_NT, 0, st>>>(g, w, n_m, tol);
+    k_s2_res<<<cell_grid, nt, 0, st>>>(g, w);
+    cudaMemsetAsync(w.AB, 0, sizeof(float) * (size_t)g.ld * g.N, st);
+    k_s2_jac<<<jac_grid, nt, 0, st>>>(g, w);
+    for (int k0 = 0; k0 < g.N; k0 += nb) {
+      const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
+      k_s2_panel<<<1, S2_PNL_NT, sizeof(float) * (size_t)wd * H, st>>>(g, w, k0);
+      const int ntrail = s2::trail_last(g, k0, wd) - (k0 + wd) + 1;
+      if (ntrail > 0)
+        k_s2_trail<<<(ntrail + w.cb - 1) / w.cb, S2_NT, sizeof(float) * (size_t)(wd + w.cb) * H, st>>>(g, w, k0);
+    }
+    k_s2_prep<<<vec_grid, nt, 0, st>>>(g, w);
+    k_s2_subst<<<1, S2_SUB_NT, sm_subst, st>>>(g, w, w.b0, w.b1, w.v0, w.v1);
+    for (int r = 0; r < S2_NREF; ++r) {
+      k_s2_bmv<<<vec_grid, nt, 0, st>>>(g, w);
+      k_s2_subst<<<1, S2_SUB_NT, sm_subst, st>>>(g, w, w.b0, w.b1, w.s0, w.s1);
+      k_s2_add<<<vec_grid, nt, 0, st>>>(g, w);
+    }
+    k_s2_newton<<<1, S2_UPD_NT, 0, st>>>(g, w, n_m, tol);
     cudaMemcpyAsync(sc, w.sc, sizeof(double) * 9, cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -374,7 +645,7 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
     if (sc[S2_DONE] != 0.0) break;
   }
   k_s2_mass<<<1, S2_NT, 0, st>>>(g, w);
-  k_s2_res<<<res_grid, nb, 0, st>>>(g, w);
+  k_s2_res<<<cell_grid, nt, 0, st>>>(g, w);
   k_s2_final<<<1, S2_NT, 0, st>>>(g, w, out, info);
   cudaMemcpyAsync(sc, w.sc, sizeof(double) * 9, cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);

@@ -2,7 +2,8 @@
 // (Eq. macroscopic_equation with the constitutive relations of
 // Eq. full_constitutive, Sec. 3 step 3) on a rectangle of nx x ny uniform
 // cells closed by walls: per-cell residual, finite-difference Jacobian
-// entries and the steps of a banded LU factorisation with partial pivoting.
+// entries, and the steps of a blocked banded LU factorisation with partial
+// pivoting in FP32 and of its substitutions.
 //
 // Everything here is __host__ __device__ and works on plain arrays, so the
 // kernels of dsmc_synth2d.cu are thin loops over these functions.
@@ -314,14 +315,26 @@ __host__ __device__ inline size_t band_at(const Grid& g, int r, int c) {
 
 // Jacobian entries of one (cell, stencil neighbour, variable): column
 // 5 k + v, rows 5 b .. 5 b + 4, by central differences with
-// h = 1e-6 max(|x|, 1).  The total-mass row is left out (written by the
-// caller as e_r / n; the rest of it is carried by a rank-one correction).
-__host__ __device__ inline void jacobian_entries(const Grid& g, const double* x, int b, int s, int v, double* AB) {
+// h = 1e-6 max(|x|, 1).  Written twice: in FP32 into the band AB32 (for the
+// factorisation) and in FP64 into the compact blocks
+// Jc[((b NSTENCIL + s) NV + r) NV + v] (for the refinement's products; zero
+// where the neighbour is outside the domain).  The total-mass row is left out
+// of both (its factorised row is e_r / n; the rest is carried by a rank-one
+// correction).
+__host__ __device__ inline size_t jc_at(int b, int s, int r, int v) {
+  return (((size_t)b * NSTENCIL + s) * NV + r) * NV + v;
+}
+
+__host__ __device__ inline void jacobian_entries(const Grid& g, const double* x, int b, int s, int v, float* AB32,
+                                                 double* Jc) {
   int i, j, di, dj;
   cell_of_band(g, b, i, j);
   stencil_offset(s, di, dj);
   const int ik = i + di, jk = j + dj;
-  if (ik < 0 || ik >= g.nx || jk < 0 || jk >= g.ny) return;
+  if (ik < 0 || ik >= g.nx || jk < 0 || jk >= g.ny) {
+    for (int r = 0; r < NV; ++r) Jc[jc_at(b, s, r, v)] = 0.0;
+    return;
+  }
   const int kb = band_cell(g, ik, jk);
   const double xv = x[NV * kb + v];
   const double h = 1e-6 * fmax(fabs(xv), 1.0);
@@ -333,55 +346,76 @@ __host__ __device__ inline void jacobian_entries(const Grid& g, const double* x,
   const int mr = mass_row(g);
   for (int r = 0; r < NV; ++r) {
     const int row = NV * b + r;
-    if (row == mr) continue;
-    AB[band_at(g, row, col)] = (Rp[r] - Rm[r]) / (2.0 * h);
+    const double val = row == mr ? 0.0 : (Rp[r] - Rm[r]) / (2.0 * h);
+    Jc[jc_at(b, s, r, v)] = val;
+    if (row != mr) AB32[band_at(g, row, col)] = (float)val;
   }
 }
 
-// Elimination step k (k = 0 .. N-2) on one column c in k+1 .. k+kl+ku:
-// interchange rows k and p = piv[k], then subtract l_r times row k from rows
-// r = k+1 .. min(k+kl, N-1), multipliers l_r in Lm[k kl + r - k - 1].  The
-// two head entries (rows k and p) are read by every thread before any thread
-// writes (col_head, then a barrier, then lu_column); thread 0 writes row k,
-// the owner of row p writes row p from row k's old value, so no two threads
-// touch one entry.
-struct ColHead {
-  double akc_old;  // A(k, c) before the interchange
-  double ukc;      // U(k, c): A(p, c) before the interchange
-};
-
-__host__ __device__ inline ColHead col_head(const Grid& g, const double* AB, const int32_t* piv, int k, int c) {
-  ColHead h;
-  h.akc_old = AB[band_at(g, k, c)];
-  h.ukc = AB[band_at(g, piv[k], c)];
-  return h;
-}
-
-__host__ __device__ inline int last_row(const Grid& g, int k) { return k + g.kl < g.N - 1 ? k + g.kl : g.N - 1; }
-__host__ __device__ inline int last_col(const Grid& g, int k) {
-  return k + g.kl + g.ku < g.N - 1 ? k + g.kl + g.ku : g.N - 1;
-}
-
-__host__ __device__ inline void lu_column(const Grid& g, double* AB, const double* Lm, const int32_t* piv, int k,
-                                          int c, const ColHead& h, int tid, int nthr) {
-  const int p = piv[k];
-  if (tid == 0 && p != k) AB[band_at(g, k, c)] = h.ukc;
-  const double* l = Lm + (size_t)k * g.kl;
-  const int rmax = last_row(g, k);
-  for (int r = k + 1 + tid; r <= rmax; r += nthr) {
-    const double a = (r == p) ? h.akc_old : AB[band_at(g, r, c)];
-    AB[band_at(g, r, c)] = a - l[r - k - 1] * h.ukc;
+// (B v) of unknown u in FP64 from the compact blocks; B's total-mass row is
+// e_r / n
+__host__ __device__ inline double bmv_row(const Grid& g, const double* Jc, const double* vec, int u) {
+  if (u == mass_row(g)) return vec[u] / g.n;
+  const int b = u / NV, r = u - b * NV;
+  int i, j;
+  cell_of_band(g, b, i, j);
+  double acc = 0.0;
+  for (int s = 0; s < NSTENCIL; ++s) {
+    int di, dj;
+    stencil_offset(s, di, dj);
+    const int ik = i + di, jk = j + dj;
+    if (ik < 0 || ik >= g.nx || jk < 0 || jk >= g.ny) continue;
+    const double* blk = Jc + jc_at(b, s, r, 0);
+    const double* xv = vec + NV * band_cell(g, ik, jk);
+    for (int v = 0; v < NV; ++v) acc += blk[v] * xv[v];
   }
+  return acc;
 }
 
-// Pivot of column k once steps 0 .. k-1 have updated it: the first row of
-// largest |A(r, k)|, r = k .. min(k+kl, N-1) (sequential form; the kernel
-// reduces the same order).
-__host__ __device__ inline int pivot_seq(const Grid& g, const double* AB, int k) {
-  int p = k;
-  double best = fabs(AB[band_at(g, k, k)]);
-  for (int r = k + 1; r <= last_row(g, k); ++r) {
-    const double a = fabs(AB[band_at(g, r, k)]);
+// ---------------------------------------------------------------------------
+// Blocked factorisation in FP32 (right-looking, panels of w <= nb columns):
+// the panel of columns k0 .. k0+w-1 and rows k0 .. k0+H-1 (H = min(w + kl,
+// N - k0)) is factorised in shared memory with partial pivoting, row
+// interchanges applied across the whole panel (its multipliers are stored in
+// the panel's own final row order); then every column c of k0+w ..
+// min(k0+w-1+kl+ku, N-1) takes the panel's interchanges, the unit-lower
+// solve with the panel's top w x w block (rows k0 .. k0+w-1 of U) and the
+// update of rows k0+w .. k0+H-1 by the panel's multipliers.  Substitution
+// takes the panels in the same order (forward) and in reverse (backward).
+//
+// FP32 storage: AB32 the band as above (U above and on the diagonal; the
+// diagonal also in ud32), piv[k] the row interchanged with row k, and the
+// multipliers panel by panel: L(k0 + r, k0 + j) at
+// Lp[(k0 / nb) nb (kl + nb) + j (kl + nb) + r], r = j+1 .. H-1 (a later
+// interchange of the panel can move a multiplier of column j down to row
+// w - 1 + kl, past the kl rows below the diagonal).  Panel arrays in shared
+// memory are column-major with leading dimension H.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline bool in_band(const Grid& g, int r, int c) {
+  return r - c <= g.kl && c - r <= g.kl + g.ku;
+}
+
+__host__ __device__ inline int panel_width(const Grid& g, int nb, int k0) { return g.N - k0 < nb ? g.N - k0 : nb; }
+__host__ __device__ inline int panel_height(const Grid& g, int w, int k0) {
+  return g.N - k0 < w + g.kl ? g.N - k0 : w + g.kl;
+}
+// last row (local) column j of the panel reaches
+__host__ __device__ inline int panel_rmax(const Grid& g, int H, int j) { return j + g.kl < H - 1 ? j + g.kl : H - 1; }
+
+__host__ __device__ inline void panel_load(const Grid& g, const float* AB32, int k0, int w, int H, float* P, int tid,
+                                           int nthr) {
+  for (int c = 0; c < w; ++c)
+    for (int r = tid; r < H; r += nthr)
+      P[(size_t)c * H + r] = in_band(g, k0 + r, k0 + c) ? AB32[band_at(g, k0 + r, k0 + c)] : 0.0f;
+}
+
+// first row of largest |P(r, j)|, r = j .. panel_rmax (sequential form)
+__host__ __device__ inline int panel_pivot_seq(const Grid& g, const float* P, int H, int j) {
+  const float* col = P + (size_t)j * H;
+  int p = j;
+  float best = fabsf(col[j]);
+  for (int r = j + 1; r <= panel_rmax(g, H, j); ++r) {
+    const float a = fabsf(col[r]);
     if (a > best) {
       best = a;
       p = r;
@@ -390,77 +424,157 @@ __host__ __device__ inline int pivot_seq(const Grid& g, const double* AB, int k)
   return p;
 }
 
-// With the pivot p of column k: U(k, k) into ud[k], p into piv[k] and the
-// multipliers of rows k+1 .. into Lm (column k of the band is not written).
-// Returns 1 when the pivot is zero (the matrix is singular; multipliers 0).
-__host__ __device__ inline int pivot_write(const Grid& g, const double* AB, double* Lm, int32_t* piv, double* ud,
-                                           int k, int p, int tid, int nthr) {
-  const double up = AB[band_at(g, p, k)];
-  const double akk = AB[band_at(g, k, k)];
-  if (tid == 0) {
-    ud[k] = up;
-    piv[k] = p;
-  }
-  double* l = Lm + (size_t)k * g.kl;
-  const int rmax = last_row(g, k);
-  for (int r = k + 1 + tid; r <= rmax; r += nthr) {
-    const double a = (r == p) ? akk : AB[band_at(g, r, k)];
-    l[r - k - 1] = up != 0.0 ? a / up : 0.0;
-  }
-  return up == 0.0 ? 1 : 0;
-}
-
-// Forward substitution step k with P and L (two right-hand sides b0, b1;
-// results y0[k], y1[k]).  Heads read first (fwd_head), barrier, then
-// fwd_step, barrier.
-struct FwdHead {
-  double bk0, bk1;      // b(p) before the interchange: y(k)
-  double old0, old1;    // b(k) before the interchange
-};
-
-__host__ __device__ inline FwdHead fwd_head(const int32_t* piv, int k, const double* b0, const double* b1) {
-  const int p = piv[k];
-  FwdHead h;
-  h.bk0 = b0[p];
-  h.bk1 = b1[p];
-  h.old0 = b0[k];
-  h.old1 = b1[k];
-  return h;
-}
-
-__host__ __device__ inline void fwd_step(const Grid& g, const double* Lm, const int32_t* piv, int k, const FwdHead& h,
-                                         double* b0, double* b1, double* y0, double* y1, int tid, int nthr) {
-  const int p = piv[k];
-  if (tid == 0) {
-    y0[k] = h.bk0;
-    y1[k] = h.bk1;
-  }
-  const double* l = Lm + (size_t)k * g.kl;
-  const int rmax = last_row(g, k);
-  for (int r = k + 1 + tid; r <= rmax; r += nthr) {
-    const double a0 = (r == p) ? h.old0 : b0[r];
-    const double a1 = (r == p) ? h.old1 : b1[r];
-    b0[r] = a0 - l[r - k - 1] * h.bk0;
-    b1[r] = a1 - l[r - k - 1] * h.bk1;
+// interchange rows j and p of the panel (all w columns)
+__host__ __device__ inline void panel_swap(float* P, int H, int w, int j, int p, int tid, int nthr) {
+  if (p == j) return;
+  for (int c = tid; c < w; c += nthr) {
+    float* col = P + (size_t)c * H;
+    const float t = col[j];
+    col[j] = col[p];
+    col[p] = t;
   }
 }
 
-// Back substitution step k (k = N-1 .. 0) with U: x(k) = y(k) / U(k, k), then
-// y(r) -= U(r, k) x(k) for r = k-kl-ku .. k-1 (y overwritten; barrier after).
-__host__ __device__ inline void back_step(const Grid& g, const double* AB, const double* ud, int k, double* y0,
-                                          double* y1, double* x0, double* x1, int tid, int nthr) {
-  const double xk0 = y0[k] / ud[k];
-  const double xk1 = y1[k] / ud[k];
-  if (tid == 0) {
-    x0[k] = xk0;
-    x1[k] = xk1;
+// multipliers of column j (divided by the pivot; 0 if the pivot is 0)
+__host__ __device__ inline void panel_scale(const Grid& g, float* P, int H, int j, int tid, int nthr) {
+  float* lj = P + (size_t)j * H;
+  const float piv = lj[j];
+  const int rmax = panel_rmax(g, H, j);
+  for (int r = j + 1 + tid; r <= rmax; r += nthr) lj[r] = piv != 0.0f ? lj[r] / piv : 0.0f;
+}
+
+// Rank-one update of columns j+1 .. w-1 by column j's multipliers; the
+// threads split into ngrp column groups (thread tid: group tid % ngrp, rows
+// strided by nthr / ngrp).
+__host__ __device__ inline void panel_rank1(const Grid& g, float* P, int H, int w, int j, int tid, int nthr, int ngrp) {
+  const float* lj = P + (size_t)j * H;
+  const int rmax = panel_rmax(g, H, j);
+  const int grp = tid % ngrp, rstride = nthr / ngrp;
+  for (int r = j + 1 + tid / ngrp; r <= rmax; r += rstride) {
+    const float l = lj[r];
+    for (int c = j + 1 + grp; c < w; c += ngrp) {
+      float* col = P + (size_t)c * H;
+      col[r] -= l * col[j];
+    }
   }
-  const int rmin = k - g.kl - g.ku > 0 ? k - g.kl - g.ku : 0;
-  for (int r = rmin + tid; r < k; r += nthr) {
-    const double u = AB[band_at(g, r, k)];
-    y0[r] -= u * xk0;
-    y1[r] -= u * xk1;
+}
+
+// start of panel k0's multipliers in Lp
+__host__ __device__ inline size_t lp_base(const Grid& g, int nb, int k0) {
+  return (size_t)(k0 / nb) * nb * (size_t)(g.kl + nb);
+}
+
+// U (rows above and on the diagonal), its diagonal and the multipliers back
+// to global memory
+__host__ __device__ inline void panel_store(const Grid& g, int nb, float* AB32, float* Lp, float* ud32, int k0, int w,
+                                            int H, const float* P, int tid, int nthr) {
+  const size_t base = lp_base(g, nb, k0);
+  const int ldp = g.kl + nb;
+  for (int c = 0; c < w; ++c) {
+    const int k = k0 + c;
+    for (int r = tid; r < H; r += nthr) {
+      const float v = P[(size_t)c * H + r];
+      if (r < c) {
+        AB32[band_at(g, k0 + r, k)] = v;
+      } else if (r == c) {
+        ud32[k] = v;
+        AB32[band_at(g, k, k)] = v;
+      } else {
+        Lp[base + (size_t)c * ldp + r] = v;
+      }
+    }
   }
+}
+
+// Trailing columns of the panel at k0: c0 .. c1 (c1 = min(k0+w-1+kl+ku, N-1)).
+__host__ __device__ inline int trail_last(const Grid& g, int k0, int w) {
+  return k0 + w - 1 + g.kl + g.ku < g.N - 1 ? k0 + w - 1 + g.kl + g.ku : g.N - 1;
+}
+
+// the panel's multipliers in shared memory: Ls[j H + r] = L(k0 + r, k0 + j)
+__host__ __device__ inline void trail_load_l(const Grid& g, int nb, const float* Lp, int k0, int w, int H, float* Ls,
+                                             int tid, int nthr) {
+  const float* L = Lp + lp_base(g, nb, k0);
+  const int ldp = g.kl + nb;
+  for (int j = 0; j < w; ++j)
+    for (int r = tid; r < H; r += nthr) Ls[(size_t)j * H + r] = r > j ? L[(size_t)j * ldp + r] : 0.0f;
+}
+
+// column segments (rows k0 .. k0+H-1) of columns cfirst .. cfirst+ncols-1
+__host__ __device__ inline void trail_load_cols(const Grid& g, const float* AB32, int k0, int H, int cfirst, int ncols,
+                                                float* Cs, int tid, int nthr) {
+  for (int cc = 0; cc < ncols; ++cc) {
+    const int c = cfirst + cc;
+    for (int r = tid; r < H; r += nthr) Cs[(size_t)cc * H + r] = in_band(g, k0 + r, c) ? AB32[band_at(g, k0 + r, c)] : 0.0f;
+  }
+}
+
+// the panel's interchanges, in order, on each column (one thread per column)
+__host__ __device__ inline void trail_swaps(const int32_t* piv, int k0, int w, int H, int ncols, float* Cs, int tid,
+                                            int nthr) {
+  for (int cc = tid; cc < ncols; cc += nthr) {
+    float* a = Cs + (size_t)cc * H;
+    for (int j = 0; j < w; ++j) {
+      const int p = piv[k0 + j] - k0;
+      if (p != j) {
+        const float t = a[j];
+        a[j] = a[p];
+        a[p] = t;
+      }
+    }
+  }
+}
+
+// unit-lower solve, elimination j (rows j+1 .. w-1 of every column)
+__host__ __device__ inline void trail_l11_step(const float* Ls, int w, int H, int ncols, int j, float* Cs, int tid,
+                                               int nthr) {
+  const int nr = w - j - 1;
+  if (nr <= 0) return;
+  const float* lj = Ls + (size_t)j * H;
+  for (int t = tid; t < ncols * nr; t += nthr) {
+    const int cc = t / nr;
+    const int i = j + 1 + (t - cc * nr);
+    float* a = Cs + (size_t)cc * H;
+    a[i] -= lj[i] * a[j];
+  }
+}
+
+// rows w .. H-1: a(r) -= sum_j L(r, j) a(j)
+__host__ __device__ inline void trail_l21(const float* Ls, int w, int H, int ncols, float* Cs, int tid, int nthr) {
+  for (int r = w + tid; r < H; r += nthr) {
+    for (int cc = 0; cc < ncols; ++cc) {
+      float* a = Cs + (size_t)cc * H;
+      float acc = 0.0f;
+      for (int j = 0; j < w; ++j) acc += Ls[(size_t)j * H + r] * a[j];
+      a[r] -= acc;
+    }
+  }
+}
+
+__host__ __device__ inline void trail_store(const Grid& g, float* AB32, int k0, int H, int cfirst, int ncols,
+                                            const float* Cs, int tid, int nthr) {
+  for (int cc = 0; cc < ncols; ++cc) {
+    const int c = cfirst + cc;
+    for (int r = tid; r < H; r += nthr)
+      if (in_band(g, k0 + r, c)) AB32[band_at(g, k0 + r, c)] = Cs[(size_t)cc * H + r];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Substitution with the FP32 factors on FP64 vectors (two right-hand sides).
+// Forward, panel k0: window s[r] = b(k0 + r), r < H; the panel's
+// interchanges; the unit-lower solve with L11 (the panel's y); rows w .. H-1
+// less L21 y.  Backward, panel k0 (last to first): window rows
+// k0 - kl - ku .. k0 + w - 1 (clipped at 0); the upper solve with U11 (x);
+// the rows above less U12 x.
+// ---------------------------------------------------------------------------
+// L(k0 + r, k0 + j) of panel k0 for local rows j < r < H
+__host__ __device__ inline float lmul(const Grid& g, int nb, const float* Lp, int k0, int r, int j) {
+  return Lp[lp_base(g, nb, k0) + (size_t)j * (g.kl + nb) + r];
+}
+
+__host__ __device__ inline float umul(const Grid& g, const float* AB32, int r, int c) {
+  return in_band(g, r, c) ? AB32[band_at(g, r, c)] : 0.0f;
 }
 
 }  // namespace s2
