@@ -196,8 +196,9 @@ int dsmc_hot(dsmc_handle *h, const double *dev_fields, double *dev_hot, double *
  * dissipation of the conserved variables (1/32 of the face's |u_n| + sound
  * speed).  Residual and central-difference Jacobian in FP64; each Newton step
  * solves with a blocked banded LU factorisation (partial pivoting) of the
- * Jacobian in FP32 and one sweep of iterative refinement with an FP64
- * residual; the number of
+ * Jacobian in FP32 and iterative refinement with FP64 residuals (later
+ * Newton steps reuse the factorisation while the updates keep halving); the
+ * number of
  * Newton iterations is min(n_m, 100).  Newton iterations from
  * dev_fields until the largest relative update is below synth_tol or n_m
  * iterations.  dev_out is ncells x DSMC_NTARGET.  host_iters / host_resid

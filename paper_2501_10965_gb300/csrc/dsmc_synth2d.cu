@@ -2,8 +2,9 @@
 // (Sec. 3 step 3) on the GPU: Newton's method with the residual and a
 // central-difference Jacobian in FP64 (dsmc_synth2d.cuh); each Newton step
 // solves with a blocked banded LU factorisation (partial pivoting) of the
-// Jacobian in FP32, substitutions in FP32 and one sweep of iterative
-// refinement with FP64 residuals.
+// Jacobian in FP32, substitutions in FP32 and iterative refinement with FP64
+// residuals; later Newton steps reuse the factorisation while the updates
+// keep shrinking.
 //
 // The total-mass row (cell (1, 0)'s mass balance replaced by the total mass)
 // couples every cell; the factorised matrix B has e_r / n there instead, and
@@ -45,7 +46,8 @@ constexpr int S2_NT = 256;        // threads of the factorisation and substituti
 constexpr int S2_UPD_NT = 512;    // the Newton update
 constexpr int S2_SUB_NT = 512;    // the substitutions
 constexpr int S2_PNL_NT = 512;    // the panel factorisation
-constexpr int S2_NREF = 1;        // refinement sweeps per Newton step
+constexpr int S2_NREF = 1;        // refinement sweeps after a fresh factorisation
+constexpr int S2_NREF_REUSE = 3;  // refinement sweeps when an earlier factorisation is reused
 constexpr int S2_SMEM_CAP = 200 * 1024;
 
 // Panel width nb and trailing columns per CTA cb (4: enough CTAs to fill the
@@ -190,16 +192,18 @@ __global__ void k_s2_res(const s2::Grid g, S2Work w) {
   s2::cell_residual(g, X, i, j, w.sc[S2_MASS], w.R + s2::NV * b);
 }
 
-__global__ void k_s2_jac(const s2::Grid g, S2Work w) {
+// the Jacobian: compact FP64 blocks always, the FP32 band only when it is
+// to be factorised
+__global__ void k_s2_jac(const s2::Grid g, S2Work w, int band) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) {
+  if (band && t == 0) {
     const int mr = s2::mass_row(g);
     w.AB[s2::band_at(g, mr, mr)] = (float)(1.0 / g.n);
   }
   if (t >= g.n * s2::NSTENCIL * s2::NV) return;
   const int b = t / (s2::NSTENCIL * s2::NV);
   const int rem = t - b * (s2::NSTENCIL * s2::NV);
-  s2::jacobian_entries(g, w.x, b, rem / s2::NV, rem % s2::NV, w.AB, w.Jc);
+  s2::jacobian_entries(g, w.x, b, rem / s2::NV, rem % s2::NV, band ? w.AB : nullptr, w.Jc);
 }
 
 // First row of largest |P(r, j)|, r = j .. panel_rmax, as s2::panel_pivot_seq
@@ -336,6 +340,7 @@ __global__ void __launch_bounds__(S2_SUB_NT) k_s2_subst(const s2::Grid g, S2Work
   double* y1 = w.y1;
   for (int k0 = 0; k0 < N; k0 += nb) {
     const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
+#pragma unroll 4
     for (int r = tid; r < H; r += S2_SUB_NT) {
       t0[r] = (float)b0[k0 + r];
       t1[r] = (float)b1[k0 + r];
@@ -360,9 +365,15 @@ __global__ void __launch_bounds__(S2_SUB_NT) k_s2_subst(const s2::Grid g, S2Work
     if (warp == 0) {
       const int i = lane;
       float a0 = i < wd ? t0[i] : 0.0f, a1 = i < wd ? t1[i] : 0.0f;
+      // every lane loads all 32 entries at clamped (valid) indices, so the
+      // loads issue together; the unused ones are dropped by the selects
+      const int ic = i < wd ? i : wd - 1;
       float lr[32];
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) lr[jj] = (jj < i && i < wd) ? Lk[(size_t)jj * ldp + i] : 0.0f;
+      for (int jj = 0; jj < 32; ++jj) {
+        const float l = Lk[(size_t)(jj < wd ? jj : wd - 1) * ldp + ic];
+        lr[jj] = (jj < i && i < wd) ? l : 0.0f;
+      }
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         if (jj < wd) {
@@ -383,14 +394,14 @@ __global__ void __launch_bounds__(S2_SUB_NT) k_s2_subst(const s2::Grid g, S2Work
     }
     __syncthreads();
     for (int r = wd + tid; r < H; r += S2_SUB_NT) {
+      float lv[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) lv[jj] = Lk[(size_t)(jj < wd ? jj : wd - 1) * ldp + r];
       float acc0 = 0.0f, acc1 = 0.0f;
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
-        if (jj < wd) {
-          const float l = Lk[(size_t)jj * ldp + r];
-          acc0 += l * t0[jj];
-          acc1 += l * t1[jj];
-        }
+        acc0 += jj < wd ? lv[jj] * t0[jj] : 0.0f;
+        acc1 += jj < wd ? lv[jj] * t1[jj] : 0.0f;
       }
       b0[k0 + r] = t0[r] - acc0;
       b1[k0 + r] = t1[r] - acc1;
@@ -401,6 +412,7 @@ __global__ void __launch_bounds__(S2_SUB_NT) k_s2_subst(const s2::Grid g, S2Work
     const int wd = s2::panel_width(g, nb, k0);
     const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
     const int nwin = k0 + wd - lo;
+#pragma unroll 4
     for (int r = tid; r < nwin; r += S2_SUB_NT) {
       t0[r] = (float)y0[lo + r];
       t1[r] = (float)y1[lo + r];
@@ -410,9 +422,13 @@ __global__ void __launch_bounds__(S2_SUB_NT) k_s2_subst(const s2::Grid g, S2Work
       const int i = lane;
       float a0 = i < wd ? t0[k0 - lo + i] : 0.0f, a1 = i < wd ? t1[k0 - lo + i] : 0.0f;
       const float dg = i < wd ? w.ud[k0 + i] : 1.0f;
+      const int ic = i < wd ? i : wd - 1;
       float ur[32];
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) ur[jj] = (jj > i && jj < wd) ? s2::umul(g, w.AB, k0 + i, k0 + jj) : 0.0f;
+      for (int jj = 0; jj < 32; ++jj) {
+        const float u = s2::umul(g, w.AB, k0 + ic, k0 + (jj < wd ? jj : wd - 1));
+        ur[jj] = (jj > i && jj < wd) ? u : 0.0f;
+      }
       float x0i = 0.0f, x1i = 0.0f;
 #pragma unroll
       for (int jj = 31; jj >= 0; --jj) {
@@ -438,14 +454,14 @@ __global__ void __launch_bounds__(S2_SUB_NT) k_s2_subst(const s2::Grid g, S2Work
     }
     __syncthreads();
     for (int r = lo + tid; r < k0; r += S2_SUB_NT) {
+      float uv[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) uv[jj] = s2::umul(g, w.AB, r, k0 + (jj < wd ? jj : wd - 1));
       float acc0 = 0.0f, acc1 = 0.0f;
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
-        if (jj < wd) {
-          const float u = s2::umul(g, w.AB, r, k0 + jj);
-          acc0 += u * t0[k0 - lo + jj];
-          acc1 += u * t1[k0 - lo + jj];
-        }
+        acc0 += jj < wd ? uv[jj] * t0[k0 - lo + jj] : 0.0f;
+        acc1 += jj < wd ? uv[jj] * t1[k0 - lo + jj] : 0.0f;
       }
       y0[r] = t0[r - lo] - acc0;
       y1[r] = t1[r - lo] - acc1;
@@ -618,21 +634,30 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
   const int jac_grid = (int)((jac_threads + nt - 1) / nt);
   double sc[S2_NSC];
   k_s2_init<<<1, S2_NT, 0, st>>>(g, w);
+  // The factorisation of the first Newton step is reused while the updates
+  // keep shrinking (by half or more per step), with more refinement sweeps
+  // against each step's fresh FP64 Jacobian; otherwise the next step
+  // refactorises.
+  bool refactor = true;
+  double dm_prev = 0.0;
   for (int it = 0; it < n_m; ++it) {
     k_s2_mass<<<1, S2_NT, 0, st>>>(g, w);
     k_s2_res<<<cell_grid, nt, 0, st>>>(g, w);
-    cudaMemsetAsync(w.AB, 0, sizeof(float) * (size_t)g.ld * g.N, st);
-    k_s2_jac<<<jac_grid, nt, 0, st>>>(g, w);
-    for (int k0 = 0; k0 < g.N; k0 += nb) {
-      const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
-      k_s2_panel<<<1, S2_PNL_NT, sizeof(float) * (size_t)wd * H, st>>>(g, w, k0);
-      const int ntrail = s2::trail_last(g, k0, wd) - (k0 + wd) + 1;
-      if (ntrail > 0)
-        k_s2_trail<<<(ntrail + w.cb - 1) / w.cb, S2_NT, sizeof(float) * (size_t)(wd + w.cb) * H, st>>>(g, w, k0);
+    if (refactor) cudaMemsetAsync(w.AB, 0, sizeof(float) * (size_t)g.ld * g.N, st);
+    k_s2_jac<<<jac_grid, nt, 0, st>>>(g, w, refactor ? 1 : 0);
+    if (refactor) {
+      for (int k0 = 0; k0 < g.N; k0 += nb) {
+        const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
+        k_s2_panel<<<1, S2_PNL_NT, sizeof(float) * (size_t)wd * H, st>>>(g, w, k0);
+        const int ntrail = s2::trail_last(g, k0, wd) - (k0 + wd) + 1;
+        if (ntrail > 0)
+          k_s2_trail<<<(ntrail + w.cb - 1) / w.cb, S2_NT, sizeof(float) * (size_t)(wd + w.cb) * H, st>>>(g, w, k0);
+      }
     }
+    const int nsweep = refactor ? S2_NREF : S2_NREF_REUSE;
     k_s2_prep<<<vec_grid, nt, 0, st>>>(g, w);
     k_s2_subst<<<1, S2_SUB_NT, sm_subst, st>>>(g, w, w.b0, w.b1, w.v0, w.v1);
-    for (int r = 0; r < S2_NREF; ++r) {
+    for (int r = 0; r < nsweep; ++r) {
       k_s2_bmv<<<vec_grid, nt, 0, st>>>(g, w);
       k_s2_subst<<<1, S2_SUB_NT, sm_subst, st>>>(g, w, w.b0, w.b1, w.s0, w.s1);
       k_s2_add<<<vec_grid, nt, 0, st>>>(g, w);
@@ -643,6 +668,8 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
     if (sc[S2_DONE] != 0.0) break;
+    refactor = it > 0 && !(sc[S2_DMAX] <= 0.5 * dm_prev);
+    dm_prev = sc[S2_DMAX];
   }
   k_s2_mass<<<1, S2_NT, 0, st>>>(g, w);
   k_s2_res<<<cell_grid, nt, 0, st>>>(g, w);

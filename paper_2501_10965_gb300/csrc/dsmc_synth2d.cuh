@@ -316,7 +316,8 @@ __host__ __device__ inline size_t band_at(const Grid& g, int r, int c) {
 // Jacobian entries of one (cell, stencil neighbour, variable): column
 // 5 k + v, rows 5 b .. 5 b + 4, by central differences with
 // h = 1e-6 max(|x|, 1).  Written twice: in FP32 into the band AB32 (for the
-// factorisation) and in FP64 into the compact blocks
+// factorisation; skipped when AB32 is null, as when an earlier factorisation
+// is reused) and in FP64 into the compact blocks
 // Jc[((b NSTENCIL + s) NV + r) NV + v] (for the refinement's products; zero
 // where the neighbour is outside the domain).  The total-mass row is left out
 // of both (its factorised row is e_r / n; the rest is carried by a rank-one
@@ -348,7 +349,7 @@ __host__ __device__ inline void jacobian_entries(const Grid& g, const double* x,
     const int row = NV * b + r;
     const double val = row == mr ? 0.0 : (Rp[r] - Rm[r]) / (2.0 * h);
     Jc[jc_at(b, s, r, v)] = val;
-    if (row != mr) AB32[band_at(g, row, col)] = (float)val;
+    if (AB32 && row != mr) AB32[band_at(g, row, col)] = (float)val;
   }
 }
 
@@ -404,9 +405,11 @@ __host__ __device__ inline int panel_rmax(const Grid& g, int H, int j) { return 
 
 __host__ __device__ inline void panel_load(const Grid& g, const float* AB32, int k0, int w, int H, float* P, int tid,
                                            int nthr) {
-  for (int c = 0; c < w; ++c)
+  for (int c = 0; c < w; ++c) {
+#pragma unroll 8
     for (int r = tid; r < H; r += nthr)
       P[(size_t)c * H + r] = in_band(g, k0 + r, k0 + c) ? AB32[band_at(g, k0 + r, k0 + c)] : 0.0f;
+  }
 }
 
 // first row of largest |P(r, j)|, r = j .. panel_rmax (sequential form)
@@ -496,8 +499,10 @@ __host__ __device__ inline void trail_load_l(const Grid& g, int nb, const float*
                                              int tid, int nthr) {
   const float* L = Lp + lp_base(g, nb, k0);
   const int ldp = g.kl + nb;
-  for (int j = 0; j < w; ++j)
+  for (int j = 0; j < w; ++j) {
+#pragma unroll 8
     for (int r = tid; r < H; r += nthr) Ls[(size_t)j * H + r] = r > j ? L[(size_t)j * ldp + r] : 0.0f;
+  }
 }
 
 // column segments (rows k0 .. k0+H-1) of columns cfirst .. cfirst+ncols-1
@@ -505,6 +510,7 @@ __host__ __device__ inline void trail_load_cols(const Grid& g, const float* AB32
                                                 float* Cs, int tid, int nthr) {
   for (int cc = 0; cc < ncols; ++cc) {
     const int c = cfirst + cc;
+#pragma unroll 8
     for (int r = tid; r < H; r += nthr) Cs[(size_t)cc * H + r] = in_band(g, k0 + r, c) ? AB32[band_at(g, k0 + r, c)] : 0.0f;
   }
 }

@@ -94,8 +94,13 @@ static void subst(const Grid& g, int nb, const F32& f, double* b0, double* b1, d
   }
 }
 
+// Newton as the GPU runs it: a fresh factorisation with nref refinement
+// sweeps; with reuse, later steps keep the factorisation (nref_reuse sweeps
+// against their fresh FP64 Jacobian) while each update is at most half the
+// previous one.
 extern "C" int h_solve_blk(int nx, int ny, double dx, double dy, const double* c, const double* F, const double* hot,
-                           int n_m, double tol, int nb, int nref, double* out, int* iters, double* resid, int* status, double* dn) {
+                           int n_m, double tol, int nb, int nref, int reuse, int nref_reuse, double* out, int* iters,
+                           double* resid, int* status, int* nfactor) {
   Grid g = G(nx, ny, dx, dy, c, F, hot);
   const int N = g.N;
   F32 f; f.AB.assign((size_t)N * g.ld, 0.f); f.Lm.assign(lp_size(g, nb), 0.f); f.ud.assign(N, 0.f); f.piv.assign(N, 0);
@@ -107,17 +112,23 @@ extern "C" int h_solve_blk(int nx, int ny, double dx, double dy, const double* c
     x[NV * b + 0] = D[0]; x[NV * b + 1] = D[1]; x[NV * b + 2] = D[2]; x[NV * b + 3] = D[4]; x[NV * b + 4] = D[5];
   }
   const int mr = mass_row(g);
-  int st = 1, it = 0, sing = 0;
+  int st = 1, it = 0, sing = 0, nf = 0;
+  bool refac = true;
+  double dm_prev = 0.0;
   for (it = 1; it <= n_m; ++it) {
     residual_all(g, x.data(), R.data());
-    std::fill(f.AB.begin(), f.AB.end(), 0.f);
+    if (refac) std::fill(f.AB.begin(), f.AB.end(), 0.f);
     for (int b = 0; b < g.n; ++b) for (int s = 0; s < NSTENCIL; ++s) for (int v = 0; v < NV; ++v)
-      jacobian_entries(g, x.data(), b, s, v, f.AB.data(), Jc.data());
-    f.AB[band_at(g, mr, mr)] = (float)(1.0 / g.n);
-    sing |= factor(g, nb, f);
+      jacobian_entries(g, x.data(), b, s, v, refac ? f.AB.data() : nullptr, Jc.data());
+    if (refac) {
+      f.AB[band_at(g, mr, mr)] = (float)(1.0 / g.n);
+      sing |= factor(g, nb, f);
+      ++nf;
+    }
+    const int nsw = refac ? nref : nref_reuse;
     for (int u = 0; u < N; ++u) { rhs0[u] = -R[u]; rhs1[u] = u == mr ? 1.0 : 0.0; b0[u] = rhs0[u]; b1[u] = rhs1[u]; }
     subst(g, nb, f, b0.data(), b1.data(), y0.data(), y1.data(), v0.data(), v1.data());
-    for (int rr = 0; rr < nref; ++rr) {
+    for (int rr = 0; rr < nsw; ++rr) {
       for (int u = 0; u < N; ++u) { b0[u] = rhs0[u] - bmv_row(g, Jc.data(), v0.data(), u); b1[u] = rhs1[u] - bmv_row(g, Jc.data(), v1.data(), u); }
       subst(g, nb, f, b0.data(), b1.data(), y0.data(), y1.data(), s0.data(), s1.data());
       for (int u = 0; u < N; ++u) { v0[u] += s0[u]; v1[u] += s1[u]; }
@@ -127,7 +138,6 @@ extern "C" int h_solve_blk(int nx, int ny, double dx, double dy, const double* c
     wz /= g.n; wy /= g.n;
     const double fct = wz / (1.0 + wy);
     for (int u = 0; u < N; ++u) d[u] = v0[u] - v1[u] * fct;
-    if (it == 1 && dn) for (int u = 0; u < N; ++u) dn[u] = d[u];
     double lam = 1.0; bool ok = false;
     for (int h = 0; h < 60 && !ok; ++h) {
       ok = true;
@@ -141,6 +151,8 @@ extern "C" int h_solve_blk(int nx, int ny, double dx, double dy, const double* c
     double dm = 0;
     for (int u = 0; u < N; ++u) { dm = std::max(dm, std::fabs(lam * d[u]) / std::max(std::fabs(x[u]), 1e-3)); x[u] += lam * d[u]; }
     if (dm < tol) { st = 0; break; }
+    refac = !reuse || (it > 1 && !(dm <= 0.5 * dm_prev));
+    dm_prev = dm;
   }
   if (it > n_m) it = n_m;
   residual_all(g, x.data(), R.data());
@@ -152,6 +164,7 @@ extern "C" int h_solve_blk(int nx, int ny, double dx, double dy, const double* c
     o[0] = x[NV * b]; o[1] = x[NV * b + 1]; o[2] = x[NV * b + 2]; o[3] = D[3]; o[4] = x[NV * b + 3]; o[5] = x[NV * b + 4];
   }
   *iters = it; *resid = rm; *status = st | (sing ? 4 : 0);
+  if (nfactor) *nfactor = nf;
   return 0;
 }
 
