@@ -37,8 +37,7 @@ enum {
   S2_STATUS = 4, // 0 converged, 1 not (yet) converged, 2 numeric
   S2_DMAX = 5,
   S2_SING = 6,   // a zero pivot was met
-  S2_RMAX = 7,
-  S2_LAM = 8,
+  S2_LAM = 7,    // length of the last Newton update (1 = full step)
   S2_NSC = 16
 };
 
@@ -169,7 +168,6 @@ __global__ void __launch_bounds__(S2_NT) k_s2_init(const s2::Grid g, S2Work w) {
     w.sc[S2_STATUS] = 1.0;
     w.sc[S2_DMAX] = 0.0;
     w.sc[S2_SING] = 0.0;
-    w.sc[S2_RMAX] = 0.0;
     w.sc[S2_LAM] = 0.0;
   }
 }
@@ -663,7 +661,7 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
       k_s2_add<<<vec_grid, nt, 0, st>>>(g, w);
     }
     k_s2_newton<<<1, S2_UPD_NT, 0, st>>>(g, w, n_m, tol);
-    cudaMemcpyAsync(sc, w.sc, sizeof(double) * 9, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(sc, w.sc, sizeof(double) * (S2_LAM + 1), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
@@ -674,7 +672,7 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
   k_s2_mass<<<1, S2_NT, 0, st>>>(g, w);
   k_s2_res<<<cell_grid, nt, 0, st>>>(g, w);
   k_s2_final<<<1, S2_NT, 0, st>>>(g, w, out, info);
-  cudaMemcpyAsync(sc, w.sc, sizeof(double) * 9, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(sc, w.sc, sizeof(double) * (S2_LAM + 1), cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
