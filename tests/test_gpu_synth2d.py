@@ -138,3 +138,29 @@ def test_dig_iteration_on_a_cavity():
     sd = np.sqrt(np.sum(frac * (1.0 - frac)))
     assert abs(g.num_particles() - m.sum()) <= 6.0 * sd + 1.0, (g.num_particles(), m.sum(), sd)
     assert abs(t[:, 0].sum() / r["fields"][:, 0].sum().item() - 1.0) < 1e-8
+
+
+def test_full_size_cavity_solution_satisfies_the_oracle_equations():
+    """The paper's cavity grid, 100 x 100 cells (50 000 unknowns), where the
+    oracle's Newton solver is too slow to run: the GPU's converged solution
+    makes the oracle's residual of the discrete equations vanish at every
+    cell (to 1e-9, against O(100) terms), keeps the sampled total mass, and
+    keeps the wall cells' u, T and the corner cells' whole state."""
+    nx = ny = 100
+    cfg = _cfg(nx, ny, ppc=2, synth_tol=1e-10)
+    d, h = _smooth(nx, ny, seed=5)
+    g = _gpu(cfg)
+    out, it, res = g.synth_solve(_dev(d), _dev(h))
+    assert res < 1e-9 and it <= 10
+    O = out.cpu().numpy()
+    x = np.concatenate([O[:, 0], O[:, 1], O[:, 2], O[:, 4], O[:, 5]])
+    R = synth2d.residual(x, d, h, cfg)
+    assert np.max(np.abs(R)) < 1e-9, np.max(np.abs(R))
+    assert abs(O[:, 0].sum() / d[:, F_RHO].sum() - 1.0) < 1e-12
+    ring = np.zeros((ny, nx), bool)
+    ring[0, :] = ring[-1, :] = ring[:, 0] = ring[:, -1] = True
+    ring = ring.ravel()
+    for k, col in ((1, F_U), (2, F_U + 1), (4, F_TT), (5, F_TR)):
+        np.testing.assert_allclose(O[ring, k], d[ring, col], rtol=0, atol=1e-12)
+    corners = [0, nx - 1, nx * (ny - 1), nx * ny - 1]
+    np.testing.assert_allclose(O[corners, 0], d[corners, F_RHO], rtol=0, atol=1e-12)
