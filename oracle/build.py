@@ -1,6 +1,6 @@
 """Compile the oracle's C source into a shared library (test infrastructure only).
 
-The oracle is the checker the CUDA library is compared with; building it is
+The oracle is the reference the CUDA library is compared with; building it is
 not using it.  Only the tests, the smoke check and the benchmark's CPU-baseline
 leg load the library this script writes.
 """
