@@ -185,30 +185,36 @@ int dsmc_hot(dsmc_handle *h, const double *dev_fields, double *dev_hot, double *
              uint8_t *dev_mask);
 
 /* Steady synthetic equations (Eq. macroscopic_equation with the
- * constitutive relations of Eq. full_constitutive), Sec. 3 step 3.
+ * constitutive relations of Eq. full_constitutive), Sec. 3 step 3, solved
+ * by Newton's method from dev_fields (ncells x DSMC_NFIELDS) with the
+ * higher-order terms dev_hot (ncells x DSMC_NHOT) until the largest relative
+ * update is below synth_tol or n_m iterations.
+ *
  * 1D slab: u_x = 0; the first and last cell keep the sampled u_y, u_z, T_t,
- * T_r (Dirichlet); total mass equals the sampled mass.
- * 2D box (single case, synth2d = 1, nx, ny >= 3): unknowns rho, u_x, u_y,
- * T_t, T_r per cell (u_z keeps its sampled value); cells next to a wall keep
- * the sampled u_x, u_y, T_t, T_r and balance their mass; the four corner
- * cells keep their sampled state and exchange no flux; cell (1, 0)'s mass
- * balance is replaced by the total mass; face fluxes with a fourth-difference
- * dissipation of the conserved variables (1/32 of the face's |u_n| + sound
- * speed).  Residual and central-difference Jacobian in FP64; each Newton step
- * solves with a blocked banded LU factorisation (partial pivoting) of the
- * Jacobian in FP32 and iterative refinement with FP64 residuals (later
- * Newton steps reuse the factorisation while the updates keep halving); the
- * number of
- * Newton iterations is min(n_m, 100).  Newton iterations from
- * dev_fields until the largest relative update is below synth_tol or n_m
- * iterations.  dev_out is ncells x DSMC_NTARGET.  host_iters / host_resid
- * (may be NULL) receive the iteration count and the final max |residual|.
- * Returns DSMC_ERR_NOT_CONVERGED (outputs written) when n_m is reached, and
- * DSMC_ERR_NUMERIC when no Newton update keeps rho > 0 and T > 0 (noisy HoT
- * can make rho = (P - HoT_xx) / T_t negative, and a 2D case whose discrete
- * system is singular gives no admissible update); such a case's output is its
- * sampled fields, so that the outputs can still serve as dig_correct
- * targets.  In a batch the worst status of the slabs is returned. */
+ * T_r (Dirichlet); total mass equals the sampled mass.  Block cyclic
+ * reduction of the block-tridiagonal Newton system.
+ *
+ * 2D box (single case with synth2d = 1; nx, ny >= 3): unknowns rho, u_x,
+ * u_y, T_t, T_r per cell (u_z keeps its sampled value); cells next to a wall
+ * keep the sampled u_x, u_y, T_t, T_r and balance their mass; the four
+ * corner cells keep their sampled state and exchange no flux; cell (1, 0)'s
+ * mass balance is replaced by the total mass; face fluxes carry a
+ * fourth-difference dissipation of the conserved variables (1/32 of the
+ * face's |u_n| + sound speed).  Residual and central-difference Jacobian in
+ * FP64; each Newton step solves with a blocked banded LU factorisation
+ * (partial pivoting) of the Jacobian in FP32 and iterative refinement with
+ * FP64 residuals; later Newton steps reuse the factorisation while the
+ * updates keep halving.  At most min(n_m, 100) Newton iterations.
+ *
+ * dev_out is ncells x DSMC_NTARGET.  host_iters / host_resid (may be NULL)
+ * receive the iteration count and the final max |residual|.  Returns
+ * DSMC_ERR_ARG on the annulus and on a 2D handle without synth2d;
+ * DSMC_ERR_NOT_CONVERGED (outputs written) when the iteration limit is
+ * reached; DSMC_ERR_NUMERIC when no Newton update keeps rho > 0 and T > 0
+ * (noisy HoT can make rho = (P - HoT_xx) / T_t negative in 1D, and a
+ * singular 2D system admits no update), in which case the output is the
+ * sampled fields, so that it can still serve as a dig_correct target.  In a
+ * batch the worst status of the slabs is returned. */
 int synth_solve(dsmc_handle *h, const double *dev_fields, const double *dev_hot, double *dev_out,
                 int *host_iters, double *host_resid);
 
