@@ -91,7 +91,7 @@ typedef struct dsmc_config {
   int64_t capacity;   /* maximum particles; 0 = chosen from ppc and bin_slack */
   double bin_slack;   /* FP32 layout: a cell's bin holds slack x its count (+32) */
   /* Mesh (DSMC_MESH_*).  DSMC_MESH_ANNULUS is the flow past a cylinder of
-   * Sec. 5: r_in <= r <= r_out, nx angular x ny radial cells (cell j nx + k,
+   * Sec. 4.2: r_in <= r <= r_out, nx angular x ny radial cells (cell j nx + k,
    * sector k between the rays at 2 pi k / nx and 2 pi (k+1) / nx, ring j
    * between R_j and R_{j+1}, R_j = r_in + (r_out - r_in) (q^j - 1) /
    * (q^ny - 1) with q = stretch, uniform for q = 1); wall 0 is the cylinder
@@ -234,11 +234,12 @@ int dig_correct(dsmc_handle *h, const double *dev_target);
 
 /* synth_solve for callers that cannot allocate device memory.  The paper has
  * no counterpart: this is a library convenience.  Callers such as a host code
- * whose device memory is owned by another allocator, or code running where
- * cudaMalloc is not allowed (for example during stream capture), cannot
- * create a handle, because dsmc_init needs a workspace they would have to
- * allocate.  This call needs no handle and no workspace: it reads the
- * configuration from cfg (dim must be 1, nx >= 3) and solves the same
+ * whose device memory is owned by another allocator (a pool it may not grow
+ * or bypass), or one that runs under a device-memory budget fixed at
+ * start-up, where a new allocation is not permitted, cannot create a handle,
+ * because dsmc_init needs a workspace they would have to allocate.  This
+ * call needs no handle and no workspace: it reads the configuration from
+ * cfg (dim must be 1, nx >= 3) and solves the same
  * discrete equations as synth_solve, from the same kind of inputs
  * (dev_fields ncells x DSMC_NFIELDS, dev_hot ncells x DSMC_NHOT) into
  * dev_out (ncells x DSMC_NTARGET), all caller-owned device arrays, on
@@ -256,8 +257,10 @@ int dig_correct(dsmc_handle *h, const double *dev_target);
  *    the solver writes each scratch word before it reads it.  Calls that
  *    overlap on the GPU (other streams, other host threads) race on the
  *    array and corrupt each other's results: serialise them.
- *  - Synchronises stream; host_iters / host_resid (may be NULL) receive the
- *    iteration count and the final max |residual|.  Returns DSMC_OK,
+ *  - Waits on stream between batches of Newton iterations (it reads the
+ *    convergence count back) and synchronises it before returning;
+ *    host_iters / host_resid (may be NULL) receive the iteration count and
+ *    the final max |residual|.  Returns DSMC_OK,
  *    DSMC_ERR_NOT_CONVERGED (outputs written), DSMC_ERR_NUMERIC,
  *    DSMC_ERR_ARG, DSMC_ERR_CAPACITY or DSMC_ERR_CUDA. */
 int synth_solve_noalloc(const dsmc_config *cfg, const double *dev_fields, const double *dev_hot,

@@ -13,7 +13,7 @@
  *
  *   move + diffuse walls   Sec. 2.2 (free flight, then collisions) and Sec. 4
  *                          ("fully diffuse" gas-surface interaction); for the
- *                          flow past a cylinder (Sec. 5, annular mesh) the
+ *                          flow past a cylinder (Sec. 4.2, annular mesh) the
  *                          cylinder is a diffuse wall, particles leave through
  *                          the outer circle and the freestream enters through
  *                          it with the one-sided flux of a drifting Maxwellian

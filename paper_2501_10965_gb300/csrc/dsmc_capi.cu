@@ -845,8 +845,10 @@ int synth_solve(dsmc_handle* h, const double* dev_fields, const double* dev_hot,
     if (nm > n_m) n_m = nm;
     if (tl < tol) tol = tl;
   }
-  launch_synth1d(h->d_cp, h->d_cell_case, h->d_cell0, h->ncases, h->ncells, h->nx.data(), dev_fields, dev_hot,
-                 dev_out, h->synth_work, h->d_woff, n_m, tol, h->synth_info, h->stream);
+  const cudaError_t le = launch_synth1d(h->d_cp, h->d_cell_case, h->d_cell0, h->ncases, h->ncells, h->nx.data(),
+                                        dev_fields, dev_hot, dev_out, h->synth_work, h->d_woff, n_m, tol,
+                                        h->synth_info, h->stream);
+  if (le != cudaSuccess) return set_err(h, DSMC_ERR_CUDA, "synth_solve: %s", cudaGetErrorString(le));
   std::vector<double> info(3 * (size_t)h->ncases);
   cudaMemcpyAsync(info.data(), h->synth_info, sizeof(double) * info.size(), cudaMemcpyDeviceToHost, h->stream);
   const int r = sync_check(h, "synth_solve");

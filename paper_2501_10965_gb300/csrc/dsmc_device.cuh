@@ -44,7 +44,7 @@ struct Params {
   int ppc;                           // initial particles per cell
   T init_tt, init_tr, init_u[3];     // initial equilibrium state
   T init_rho;
-  // mesh 1: annulus r_in <= r <= r_out around a cylinder (Sec. 5), nx
+  // mesh 1: annulus r_in <= r <= r_out around a cylinder (Sec. 4.2), nx
   // angular x ny radial cells, cell = j nx + k; wall 0 is the cylinder
   int mesh;
   const T* r2t;   // ny + 1 squared ring radii

@@ -784,41 +784,51 @@ __global__ void __launch_bounds__(NT) k_synth_final(const __grid_constant__ Synt
 // Newton iterations are launched in batches of 4 (a finished slab makes the
 // remaining launches return at once); the host reads the count of finished
 // slabs between batches.  One CTA per slab, NT threads: the smallest power
-// of two from 128 to 1024 that covers the largest slab.
+// of two from 128 to 1024 that covers the largest slab.  The first CUDA
+// error (a launch, the copy of the count or the wait) stops the loop before
+// any further launch and is returned.
 template <int NT>
-static void run_synth_nt(const SynthCases& sc, double* out, int n_m, double tol, cudaStream_t st) {
+static cudaError_t run_synth_nt(const SynthCases& sc, double* out, int n_m, double tol, cudaStream_t st) {
   k_synth_init<NT><<<sc.ncases, NT, 0, st>>>(sc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const int jt = 128, jb = (sc.ncells * 13 + jt - 1) / jt;
   int it = 0;
   while (it < n_m) {
     const int batch = (n_m - it) < 4 ? (n_m - it) : 4;
-    cudaMemsetAsync(sc.info + 3 * sc.ncases, 0, sizeof(double), st);
+    e = cudaMemsetAsync(sc.info + 3 * sc.ncases, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
     for (int b = 0; b < batch; ++b) {
       k_synth_jac<<<jb, jt, 0, st>>>(sc);
       k_synth_solve<NT><<<sc.ncases, NT, 0, st>>>(sc, n_m, tol, b == batch - 1 ? 1 : 0);
     }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     it += batch;
     double done = 0.0;
-    cudaMemcpyAsync(&done, sc.info + 3 * sc.ncases, sizeof(double), cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
+    e = cudaMemcpyAsync(&done, sc.info + 3 * sc.ncases, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
     if (done >= (double)sc.ncases) break;
   }
   k_synth_final<NT><<<sc.ncases, NT, 0, st>>>(sc, out);
+  return cudaGetLastError();
 }
 
-static void run_synth(const SynthCases& sc, const int32_t* host_nx, double* out, int n_m, double tol,
-                      cudaStream_t st) {
+static cudaError_t run_synth(const SynthCases& sc, const int32_t* host_nx, double* out, int n_m, double tol,
+                             cudaStream_t st) {
   int nmax = 1;
   for (int c = 0; c < sc.ncases; ++c) nmax = host_nx[c] > nmax ? host_nx[c] : nmax;
-  if (nmax <= 128) run_synth_nt<128>(sc, out, n_m, tol, st);
-  else if (nmax <= 256) run_synth_nt<256>(sc, out, n_m, tol, st);
-  else if (nmax <= 512) run_synth_nt<512>(sc, out, n_m, tol, st);
-  else run_synth_nt<1024>(sc, out, n_m, tol, st);
+  if (nmax <= 128) return run_synth_nt<128>(sc, out, n_m, tol, st);
+  if (nmax <= 256) return run_synth_nt<256>(sc, out, n_m, tol, st);
+  if (nmax <= 512) return run_synth_nt<512>(sc, out, n_m, tol, st);
+  return run_synth_nt<1024>(sc, out, n_m, tol, st);
 }
 
-void launch_synth1d(const CellParams* cp, const int32_t* cell_case, const int32_t* cell0, int ncases, int ncells,
-                    const int32_t* host_nx, const double* fields, const double* hot, double* out, double* work,
-                    const int64_t* woff, int n_m, double tol, double* info, cudaStream_t st) {
+cudaError_t launch_synth1d(const CellParams* cp, const int32_t* cell_case, const int32_t* cell0, int ncases,
+                           int ncells, const int32_t* host_nx, const double* fields, const double* hot, double* out,
+                           double* work, const int64_t* woff, int n_m, double tol, double* info, cudaStream_t st) {
   SynthCases sc{};
   sc.cps = cp;
   sc.cell_case = cell_case;
@@ -830,13 +840,13 @@ void launch_synth1d(const CellParams* cp, const int32_t* cell_case, const int32_
   sc.info = info;
   sc.ncases = ncases;
   sc.ncells = ncells;
-  run_synth(sc, host_nx, out, n_m, tol, st);
+  return run_synth(sc, host_nx, out, n_m, tol, st);
 }
 
 // one slab given by value (no device tables): used where nothing may be
 // allocated
-void launch_synth1d_single(const CellParams& cp, const double* fields, const double* hot, double* out, double* work,
-                           int n_m, double tol, double* info, cudaStream_t st) {
+cudaError_t launch_synth1d_single(const CellParams& cp, const double* fields, const double* hot, double* out,
+                                  double* work, int n_m, double tol, double* info, cudaStream_t st) {
   SynthCases sc{};
   sc.cp1 = cp;
   sc.F = fields;
@@ -845,7 +855,7 @@ void launch_synth1d_single(const CellParams& cp, const double* fields, const dou
   sc.info = info;
   sc.ncases = 1;
   sc.ncells = cp.nx;
-  run_synth(sc, &cp.nx, out, n_m, tol, st);
+  return run_synth(sc, &cp.nx, out, n_m, tol, st);
 }
 
 }  // namespace dsmc

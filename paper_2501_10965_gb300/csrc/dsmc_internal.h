@@ -138,13 +138,13 @@ void launch_acc_sum(int ncells, const double* acc, const double* comp, double* o
 // 1D synthetic equations of ncases slabs; case c uses work + woff[c] (device
 // table of offsets in doubles) and writes (iterations, max residual, status)
 // to info[3c .. 3c+2]; host_nx[c] are the slab sizes (host memory)
-void launch_synth1d(const CellParams* cp, const int32_t* cell_case, const int32_t* cell0, int ncases,
-                    int ncells, const int32_t* host_nx, const double* fields, const double* hot, double* out,
-                    double* work, const int64_t* woff, int n_m, double tol, double* info,
-                    cudaStream_t st);
+cudaError_t launch_synth1d(const CellParams* cp, const int32_t* cell_case, const int32_t* cell0, int ncases,
+                           int ncells, const int32_t* host_nx, const double* fields, const double* hot,
+                           double* out, double* work, const int64_t* woff, int n_m, double tol, double* info,
+                           cudaStream_t st);
 // one slab given by value, no device tables (info: 4 doubles)
-void launch_synth1d_single(const CellParams& cp, const double* fields, const double* hot, double* out,
-                           double* work, int n_m, double tol, double* info, cudaStream_t st);
+cudaError_t launch_synth1d_single(const CellParams& cp, const double* fields, const double* hot, double* out,
+                                  double* work, int n_m, double tol, double* info, cudaStream_t st);
 size_t synth1d_work_doubles(int ncells);
 // 2D synthetic equations of one box case (dsmc_synth2d.cu): doubles of work,
 // and the solve (info = iterations, max residual, status; *singular set when

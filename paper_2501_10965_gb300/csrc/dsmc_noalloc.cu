@@ -3,12 +3,12 @@
 //
 // The ordinary entry point (synth_solve) needs a handle, and a handle needs a
 // workspace that the caller allocates.  Some callers cannot do that: a host
-// code whose device memory belongs to another allocator and may not be grown,
-// or code that runs where cudaMalloc is not allowed (for example while a
-// stream is being captured).  This variant takes the configuration and the
-// field arrays directly and keeps the solver's scratch (the Newton iterate,
-// residuals, Jacobian blocks and the cyclic-reduction factors) in a fixed,
-// file-scope device array instead.  That array belongs to the library: every
+// code whose device memory belongs to another allocator (a pool it may not
+// grow or bypass), or one that runs under a device-memory budget fixed at
+// start-up, where a new allocation is not permitted.  This variant takes the
+// configuration and the field arrays directly and keeps the solver's scratch
+// (the Newton iterate, residuals, Jacobian blocks and the cyclic-reduction
+// factors) in a fixed, file-scope device array instead.  That array belongs to the library: every
 // GPU that loads the library holds it until the process exits.
 #include <cmath>
 #include <cstdint>
@@ -87,8 +87,8 @@ extern "C" int synth_solve_noalloc(const dsmc_config* cfg, const double* dev_fie
   double* info_dev = scratch + kInfoOffset;
   // every scratch word the kernel reads it has written first in the same
   // call, so nothing needs clearing between calls
-  dsmc::launch_synth1d_single(cp, dev_fields, dev_hot, dev_out, scratch, n_m, tol, info_dev, st);
-  if (cudaGetLastError() != cudaSuccess) return DSMC_ERR_CUDA;
+  if (dsmc::launch_synth1d_single(cp, dev_fields, dev_hot, dev_out, scratch, n_m, tol, info_dev, st) != cudaSuccess)
+    return DSMC_ERR_CUDA;
   double info[3] = {0, 0, 0};
   if (cudaMemcpyAsync(info, info_dev, sizeof info, cudaMemcpyDeviceToHost, st) != cudaSuccess) return DSMC_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return DSMC_ERR_CUDA;

@@ -1363,21 +1363,22 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
   const int s0 = start_in[cell], n = cnt_in[cell], d0 = start_out[cell], ntg = nt[cell];
   const double* t = target + (size_t)cell * 6;
   const int ix = lcell % cp.nx, iy = lcell / cp.nx;
-  // FP32 particles: the sums of step iii are taken while the new population
-  // is written, of w = v - u_target (so that the second moment about the
-  // mean, E[w^2] - E[w]^2, keeps its digits when the mean is near the
-  // target); the FP64 layout sums in a second and third pass below
+  // FP32 particles: the sums of step iii are taken in FP64 while the new
+  // population is written, of w = v - u_target, so that the second moment
+  // about the mean, E[w^2] - E[w]^2, keeps its digits however far the cell's
+  // mean lies from the target; the factors of step iv are FP64 too.  The
+  // FP64 layout sums in a second and third pass below.
   constexpr bool ONE_PASS = sizeof(T) == 4;
-  const float tux = (float)t[1], tuy = (float)t[2], tuz = (float)t[3];
-  float swx = 0.f, swy = 0.f, swz = 0.f, sir = 0.f, sw2 = 0.f;
+  const double tux = t[1], tuy = t[2], tuz = t[3];
+  double swx = 0.0, swy = 0.0, swz = 0.0, sir = 0.0, sw2 = 0.0;
   auto tally = [&](T vx, T vy, T vz, T ir) {
     if constexpr (ONE_PASS) {
-      const float wx = (float)vx - tux, wy = (float)vy - tuy, wz = (float)vz - tuz;
+      const double wx = (double)vx - tux, wy = (double)vy - tuy, wz = (double)vz - tuz;
       swx += wx;
       swy += wy;
       swz += wz;
-      sir += (float)ir;
-      sw2 = fmaf(wx, wx, fmaf(wy, wy, fmaf(wz, wz, sw2)));
+      sir += (double)ir;
+      sw2 = fma(wx, wx, fma(wy, wy, fma(wz, wz, sw2)));
     }
   };
   int32_t* idx = (n <= tile) ? reinterpret_cast<int32_t*>(smem) + (size_t)warp * tile * 2 : idx_g + s0;
@@ -1502,20 +1503,22 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
         sir += __shfl_xor_sync(FULL, sir, o);
         sw2 += __shfl_xor_sync(FULL, sw2, o);
       }
-      const float inv = 1.f / (float)np;
-      const float mx = swx * inv, my = swy * inv, mz = swz * inv;
-      const float tts = (sw2 * inv - (mx * mx + my * my + mz * mz)) * (1.f / 3.f);
-      const float trs = 2.f * sir * inv / (float)cp.d_r;
-      // step iv: v <- a v + b = u_target + a (v - u*), I_r <- c I_r
-      const float a = (np >= 2 && tts > 0.f) ? sqrtf((float)t[4] / tts) : 1.f;
-      const float bx = tux - (tux + mx) * a, by = tuy - (tuy + my) * a, bz = tuz - (tuz + mz) * a;
-      const float cc = (trs > 0.f) ? (float)t[5] / trs : 1.f;
+      // u* = u_target + m, T_t* = (E[w^2] - m^2) / 3 with m = E[w]
+      const double inv = 1.0 / (double)np;
+      const double mx = swx * inv, my = swy * inv, mz = swz * inv;
+      const double tts = (sw2 * inv - (mx * mx + my * my + mz * mz)) * (1.0 / 3.0);
+      const double trs = 2.0 * sir * inv / cp.d_r;
+      // step iv: v <- a v + b = u_target + a (v - u*), I_r <- c I_r, in FP64
+      // and rounded once to the FP32 particle
+      const double a = (np >= 2 && tts > 0.0) ? sqrt(t[4] / tts) : 1.0;
+      const double bx = tux - (tux + mx) * a, by = tuy - (tuy + my) * a, bz = tuz - (tuz + mz) * a;
+      const double cc = (trs > 0.0) ? t[5] / trs : 1.0;
       for (int q = lane; q < np; q += 32) {
         const int w = d0 + q;
-        out.vx[w] = (T)fmaf(a, (float)out.vx[w], bx);
-        out.vy[w] = (T)fmaf(a, (float)out.vy[w], by);
-        out.vz[w] = (T)fmaf(a, (float)out.vz[w], bz);
-        out.ir[w] = (T)(cc * (float)out.ir[w]);
+        out.vx[w] = (T)fma(a, (double)out.vx[w], bx);
+        out.vy[w] = (T)fma(a, (double)out.vy[w], by);
+        out.vz[w] = (T)fma(a, (double)out.vz[w], bz);
+        out.ir[w] = (T)(cc * (double)out.ir[w]);
         if (cellof_out) cellof_out[w] = cell;
       }
     }

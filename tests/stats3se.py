@@ -1,0 +1,71 @@
+"""The "within 3 standard errors" comparisons of the statistical tests.
+
+A standard error comes from the spread of independent replicas (different
+seeds), never from batches of one run, whose correlation understates it.
+With k replicas the estimated SE has k - 1 degrees of freedom, so the
+difference over its SE follows a t distribution, not a normal one; the bound
+is taken at the same two-sided 99.73 % level as 3 standard errors of a
+normal variable (t_{0.99865, dof}: 3.64 for 14 degrees of freedom, 3.26
+for 31, 3.0 for many).
+
+Where many values are compared at once (cells, rings, regions), chance alone
+puts some outside the bound: p = 0.27 % each.  The number allowed outside is
+the smallest k that independent comparisons exceed with probability below
+1 %, i.e. 0 for up to 3 values, 1 for up to 55, 2 for up to 162; every
+value must still lie within 5 of its standard errors.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+P_OUT = 0.0027      # two-sided tail beyond 3 standard errors of a normal variable
+ALPHA = 0.01        # false-alarm probability of a whole comparison
+HARD = 5.0          # no value beyond this many standard errors
+
+
+def t_bound(dof: float) -> float:
+    """Two-sided 99.73 % point of Student's t with dof degrees of freedom."""
+    from scipy import stats
+    return float(stats.t.ppf(1.0 - P_OUT / 2.0, max(dof, 1.0)))
+
+
+def allowed_outside(n: int) -> int:
+    """Smallest k with P(Binomial(n, P_OUT) > k) < ALPHA."""
+    k, cdf = 0, 0.0
+    while True:
+        cdf += math.comb(n, k) * P_OUT ** k * (1.0 - P_OUT) ** (n - k)
+        if 1.0 - cdf < ALPHA:
+            return k
+        k += 1
+
+
+def welch(a: np.ndarray, b: np.ndarray | None = None):
+    """Difference of the replica means of a and b (axis 0; b None: a's mean
+    against 0), its standard error and the Welch degrees of freedom."""
+    a = np.asarray(a, dtype=np.float64)
+    va = a.var(0, ddof=1) / a.shape[0]
+    if b is None:
+        return a.mean(0), np.sqrt(va), np.full(np.shape(va), a.shape[0] - 1.0)
+    b = np.asarray(b, dtype=np.float64)
+    vb = b.var(0, ddof=1) / b.shape[0]
+    dof = (va + vb) ** 2 / (va ** 2 / (a.shape[0] - 1) + vb ** 2 / (b.shape[0] - 1) + 1e-300)
+    return a.mean(0) - b.mean(0), np.sqrt(va + vb), dof
+
+
+def assert_within_3se(a, b=None, what: str = "", floor: float = 0.0):
+    """Replicas a against replicas b (or against 0): every compared value
+    within the 3-SE bound, up to allowed_outside(n) of them, and none beyond
+    HARD standard errors.  floor: an absolute SE floor for values whose
+    spread is exactly zero (e.g. a conserved total)."""
+    d, se, dof = welch(a, b)
+    d, se, dof = np.atleast_1d(d), np.atleast_1d(se) + floor, np.atleast_1d(dof)
+    z = np.abs(d) / np.where(se > 0, se, 1e-300)
+    thr = np.array([t_bound(v) for v in dof])
+    out = int((z > thr).sum())
+    k = allowed_outside(z.size)
+    assert out <= k and np.all(z <= np.maximum(HARD, thr)), (
+        f"{what}: {out} of {z.size} beyond 3 SE (allowed {k}); largest |diff|/SE "
+        f"{np.sort(z)[-3:]}, diff {d[np.argsort(z)[-3:]]}, SE {se[np.argsort(z)[-3:]]}")
+    return z

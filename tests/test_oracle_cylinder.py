@@ -1,4 +1,4 @@
-"""Pins of the oracle's flow past a cylinder (annular mesh, Sec. 5).
+"""Pins of the oracle's flow past a cylinder (annular mesh, Sec. 4.2).
 
 Each test checks the oracle against something it does not compute itself:
 

@@ -32,8 +32,13 @@ def _inputs(cfg, seed):
     return torch.tensor(f, device="cuda"), torch.tensor(hot, device="cuda")
 
 
-def test_noalloc_synth_equals_synth_solve_on_two_calls():
-    cfg = W.couette_1d(kn=0.05, nx=150, ppc=4, synth_tol=1e-12, n_m=60, precision="fp64")
+@pytest.mark.parametrize("nx", [150, 1030, "max"])
+def test_noalloc_synth_equals_synth_solve_on_two_calls(nx):
+    """150 cells run the 128-thread solver; 1030 the 1024-thread one with
+    strided loops; the largest slab accepted fills nearly all of the fixed
+    array."""
+    nx = dsmc_max() if nx == "max" else nx
+    cfg = W.couette_1d(kn=0.05, nx=nx, ppc=4, synth_tol=1e-12, n_m=60, precision="fp64")
     ref_sim = dsmc.Dsmc(cfg)
     for call, seed in enumerate((1, 2)):
         fields, hot = _inputs(cfg, seed)
