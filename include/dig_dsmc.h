@@ -71,9 +71,9 @@ typedef struct dsmc_config {
   double lx, ly;     /* domain lengths */
   double kn;         /* global Knudsen number, Sec. 2: mu_ref = Kn sqrt(2/pi) */
   double omega;      /* VHS viscosity index (Sec. 4: 0.74) */
-  double alpha;      /* VSS scattering parameter; only 1 (VHS) is supported */
+  double alpha;      /* VSS scattering exponent, 0 < alpha <= 2 (1: VHS, isotropic) */
   double z_rot;      /* rotational collision number Z, Eq. (P_inelastic) */
-  double d_r;        /* rotational degrees of freedom; only 2 is supported */
+  double d_r;        /* rotational degrees of freedom: 2 (linear) or 3 (non-linear molecules) */
   double a_matrix[4]; /* A_tt, A_tr, A_rt, A_rr of Eq. (heat_flux_relaxation) */
   double dt;          /* time step */
   int32_t wall_kind[4];
@@ -126,8 +126,9 @@ int dsmc_workspace_size(const dsmc_config *cfg, size_t *bytes);
  * bytes) on stream (a cudaStream_t, or NULL for the legacy default stream) and
  * fill it with the uniform equilibrium state of cfg: in every cell, ppc
  * particles uniform in the cell with Maxwellian velocities at (init_u,
- * init_tt) and exponential rotational energies of mean init_tr (d_r = 2)
- * (Sec. 3 step 1: particles initialised from an equilibrium distribution).
+ * init_tt) and rotational energies I_r with I_r / init_tr Gamma(d_r / 2)
+ * distributed (exponential for d_r = 2) (Sec. 3 step 1: particles
+ * initialised from an equilibrium distribution).
  * The workspace must stay allocated until dsmc_destroy. */
 int dsmc_init(const dsmc_config *cfg, void *dev_workspace, size_t bytes, void *stream,
               dsmc_handle **out);

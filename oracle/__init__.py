@@ -87,6 +87,11 @@ def lib():
             getattr(L, name).restype = ctypes.c_double
         L.or_inflow_speed_pub.argtypes = [ctypes.c_double, ctypes.c_double]
         L.or_inflow_speed_pub.restype = ctypes.c_double
+        L.or_bl_fraction_pub.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_uint64] + [ctypes.c_uint32] * 3 + [
+            ctypes.c_double, ctypes.c_uint32]
+        L.or_bl_fraction_pub.restype = ctypes.c_double
+        L.or_scatter_pub.argtypes = [ctypes.c_double] * 7 + [P]
+        L.or_scatter_pub.restype = None
         _lib = L
     return _lib
 
@@ -109,6 +114,22 @@ def inflow_speed(s: float, u: float) -> float:
 
 def inflow_ginf(s: float) -> float:
     return lib().or_inflow_ginf_pub(s)
+
+
+def bl_fraction(omega: float, d_r: float, seed: int, k: int, cell: int, step: int, u: float,
+                jx: int = 2048) -> float:
+    """Fraction of E_c kept as rotational energy in one Borgnakke-Larsen
+    exchange of candidate k of (cell, step), main uniform u (Beta(d_r/2,
+    5/2 - omega))."""
+    return lib().or_bl_fraction_pub(omega, d_r, seed, k, cell, step, u, jx)
+
+
+def scatter(alpha: float, g, gn: float, u: float, v: float) -> np.ndarray:
+    """Half the post-collision relative velocity for the pre-collision
+    relative velocity g, new magnitude gn and the two scattering uniforms."""
+    out = np.zeros(3)
+    lib().or_scatter_pub(alpha, float(g[0]), float(g[1]), float(g[2]), gn, u, v, _ptr(out))
+    return out
 
 
 def uniform(seed, tag, c0, c1, c2, j) -> float:

@@ -357,15 +357,118 @@ static void or_box_muller(double ua, double ub, double *n1, double *n2) {
   *n2 = r * sin(th);
 }
 
+/* Rotational energy of one molecule in equilibrium at temperature T: d_r
+ * quadratic degrees of freedom share (d_r/2) T on average, so I_r / T is
+ * Gamma(d_r/2) distributed (Sec. 2.1, e_r = d_r T_r / 2).  d_r = 2 (linear
+ * molecules): -T ln u with u the draw's main uniform.  d_r = 3 (non-linear
+ * molecules): Gamma(3/2) = Gamma(1) + Gamma(1/2), the Gamma(1/2) part as
+ * Z^2/2 of a Box-Muller normal Z = sqrt(-2 ln u_a) cos(2 pi u_b), with u_a,
+ * u_b the uniforms jx, jx + 1 of the same stream. */
+static double or_ir_draw(const or_state *S, double T, double u, or_stream *st, uint32_t jx) {
+  double e = -log(u);
+  if (S->c.d_r == 3.0) {
+    double cb = cos(2.0 * M_PI * or_uni(st, jx + 1u));
+    e += -log(or_uni(st, jx)) * cb * cb;
+  }
+  return T * e;
+}
+
+/* Uniform indices of the extra draws (d_r = 3 only): I_r of a particle's own
+ * stream takes 1024-1025; the wall hit whose four uniforms start at jh takes
+ * 1026 + jh/2 and 1027 + jh/2; the Borgnakke-Larsen acceptance-rejection of
+ * candidate pair k takes 2048 + 4t .. 2051 + 4t (try t). */
+#define OR_JX_OWN 1024u
+#define OR_JX_HIT(jh) (1026u + (jh) / 2u)
+#define OR_JX_BL 2048u
+#define OR_BL_TRIES 32
+
+/* Fraction x = I_r,k' / E_c kept as rotational energy in one
+ * Borgnakke-Larsen exchange (Sec. 2.2): the equilibrium partition of E_c
+ * between the d_r rotational degrees of freedom of one molecule and the
+ * relative translation of a VHS/VSS pair, whose collision-weighted energy
+ * has 5/2 - w degrees of freedom in units of 2, i.e. x ~ Beta(a, b) with a =
+ * d_r/2, b = 5/2 - w.  d_r = 2 (a = 1): x = 1 - u^{1/b} (inverse CDF, u the
+ * main uniform).  d_r = 3: acceptance-rejection under the uniform envelope
+ * of the density x^{a-1} (1-x)^{b-1}, whose maximum is at x* = (a-1)/(a+b-2):
+ * try t proposes x (the main uniform at t = 0, else uniform jx + 4t) and
+ * accepts it when ln(uniform jx + 4t + 1) < (a-1) ln(x/x*) + (b-1) ln((1-x)/
+ * (1-x*)); after OR_BL_TRIES rejections (odds below 1e-18) it takes x*. */
+static double or_bl_fraction(const or_state *S, double u, or_stream *st, uint32_t jx) {
+  double b = 2.5 - S->c.omega;
+  if (S->c.d_r == 2.0) return 1.0 - pow(u, 1.0 / b);
+  double a = 0.5 * S->c.d_r;
+  double xs = (a - 1.0) / (a + b - 2.0);
+  for (int t = 0; t < OR_BL_TRIES; ++t) {
+    double x = (t == 0) ? u : or_uni(st, jx + 4u * (uint32_t)t);
+    double acc = or_uni(st, jx + 4u * (uint32_t)t + 1u);
+    if (log(acc) < (a - 1.0) * log(x / xs) + (b - 1.0) * log((1.0 - x) / (1.0 - xs))) return x;
+  }
+  return xs;
+}
+
+/* Post-collision relative velocity h = g'/2 of magnitude gn/2.  VHS (alpha
+ * = 1): isotropic, cos(theta) = 2 u - 1 and azimuth 2 pi v in the lab frame.
+ * VSS (alpha != 1, Sec. 2.2): the deflection chi from the pre-collision
+ * direction e = g/|g| has cos(chi) = 2 u^{1/alpha} - 1 and the azimuth 2 pi
+ * v about e, measured from e1 = the unit vector along the coordinate axis
+ * least aligned with e, made orthogonal to e (e2 = e x e1). */
+static void or_scatter(const or_state *S, double gx, double gy, double gz, double gn, double u, double v,
+                       double h[3]) {
+  double ph = 2.0 * M_PI * v;
+  if (S->c.alpha == 1.0) {
+    double cth = 2.0 * u - 1.0;
+    double sth = sqrt(1.0 - cth * cth);
+    h[0] = 0.5 * gn * cth;
+    h[1] = 0.5 * gn * sth * cos(ph);
+    h[2] = 0.5 * gn * sth * sin(ph);
+    return;
+  }
+  double g = sqrt(gx * gx + gy * gy + gz * gz);
+  double e[3] = {gx / g, gy / g, gz / g};
+  double ax[3] = {0.0, 0.0, 0.0};
+  double m0 = fabs(e[0]), m1 = fabs(e[1]), m2 = fabs(e[2]);
+  ax[(m0 <= m1 && m0 <= m2) ? 0 : (m1 <= m2 ? 1 : 2)] = 1.0;
+  double d = ax[0] * e[0] + ax[1] * e[1] + ax[2] * e[2];
+  double e1[3] = {ax[0] - d * e[0], ax[1] - d * e[1], ax[2] - d * e[2]};
+  double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  e1[0] /= l1;
+  e1[1] /= l1;
+  e1[2] /= l1;
+  double e2[3] = {e[1] * e1[2] - e[2] * e1[1], e[2] * e1[0] - e[0] * e1[2], e[0] * e1[1] - e[1] * e1[0]};
+  double cch = 2.0 * pow(u, 1.0 / S->c.alpha) - 1.0;
+  double sch = sqrt(1.0 - cch * cch);
+  double cp = cos(ph), sp = sin(ph);
+  for (int k = 0; k < 3; ++k) h[k] = 0.5 * gn * (cch * e[k] + sch * (cp * e1[k] + sp * e2[k]));
+}
+
+/* exported for the tests of the Borgnakke-Larsen partition, the rotational
+ * energy draw and the scattering law */
+double or_bl_fraction_pub(double omega, double d_r, uint64_t seed, uint32_t k, uint32_t cell, uint32_t step,
+                          double u, uint32_t jx) {
+  or_state S;
+  memset(&S, 0, sizeof S);
+  S.c.omega = omega;
+  S.c.d_r = d_r;
+  or_stream st;
+  or_stream_init(&st, seed, OR_TAG_COLL, k, cell, step);
+  return or_bl_fraction(&S, u, &st, jx);
+}
+void or_scatter_pub(double alpha, double gx, double gy, double gz, double gn, double u, double v, double h[3]) {
+  or_state S;
+  memset(&S, 0, sizeof S);
+  S.c.alpha = alpha;
+  or_scatter(&S, gx, gy, gz, gn, u, v, h);
+}
+
 /* Equilibrium (Maxwellian) initial state, ppc particles per cell, cell by cell
- * (Sec. 3 step 1; Sec. 4: particles sampled from an equilibrium distribution).
- * For d_r = 2 the rotational energy of one molecule is exponential with mean
- * T_r. */
+ * (Sec. 3 step 1; Sec. 4: particles sampled from an equilibrium distribution),
+ * I_r drawn at T_r (or_ir_draw). */
 int or_create(const or_config *cfg, or_state **out) {
   *out = NULL;
   if (cfg->dim != 1 && cfg->dim != 2) return OR_ERR_ARG;
   if (cfg->nx <= 0 || (cfg->dim == 2 && cfg->ny <= 0) || cfg->ppc < 0) return OR_ERR_ARG;
-  if (cfg->d_r != 2.0 || cfg->alpha != 1.0) return OR_ERR_ARG;
+  /* d_r = 2 (linear) or 3 (non-linear molecules); VSS exponent 0 < alpha <= 2 */
+  if ((cfg->d_r != 2.0 && cfg->d_r != 3.0) || !(cfg->alpha > 0.0 && cfg->alpha <= 2.0)) return OR_ERR_ARG;
   if (cfg->mesh != 0 && cfg->mesh != 1) return OR_ERR_ARG;
   if (cfg->mesh == 1 && (cfg->dim != 2 || cfg->nx < 3 || !(cfg->r_in > 0.0) || !(cfg->r_out > cfg->r_in) ||
                          !(cfg->stretch > 0.0) || !(cfg->fs_t > 0.0) || !(cfg->fs_rho >= 0.0)))
@@ -428,7 +531,7 @@ int or_create(const or_config *cfg, or_state **out) {
       S->vx[s] = c->init_u[0] + stt * n1;
       S->vy[s] = c->init_u[1] + stt * n2;
       S->vz[s] = c->init_u[2] + stt * n3;
-      S->ir[s] = -c->init_tr * log(or_uni(&st, 6));
+      S->ir[s] = or_ir_draw(S, c->init_tr, or_uni(&st, 6), &st, OR_JX_OWN);
       S->cell[s] = cell;
     }
   }
@@ -487,7 +590,7 @@ static void or_wall_emit(or_state *S, int w, or_stream *st, int hit, double v[3]
       v[1] = sgn * vn;
       v[2] = c->wall_u[w][2] + sT * n2;
     }
-    *ir = -T * log(ud);
+    *ir = or_ir_draw(S, T, ud, st, OR_JX_HIT((uint32_t)(4 * hit)));
   }
   double *t = S->wall_tally[w];
   t[0] += 1.0;
@@ -521,7 +624,7 @@ static void or_cyl_emit(or_state *S, or_stream *st, uint32_t j0, double nx, doub
     v[0] = vn * nx - vt * ny;
     v[1] = vn * ny + vt * nx;
     v[2] = sT * n2;
-    *ir = -T * log(ud);
+    *ir = or_ir_draw(S, T, ud, st, OR_JX_HIT(j0));
   }
   double *t = S->wall_tally[0];
   t[0] += 1.0;
@@ -644,7 +747,7 @@ static void or_inject(or_state *S) {
       double vt = ut + sT * n1;
       double v[3] = {vn * nx + vt * tx, vn * ny + vt * ty, c->fs_u[2] + sT * n2};
       double th = 2.0 * M_PI * ((double)k + or_uni(&st, 3)) / (double)nt;
-      double ir = -T * log(or_uni(&st, 4));
+      double ir = or_ir_draw(S, T, or_uni(&st, 4), &st, OR_JX_OWN);
       double x = c->r_out * cos(th), y = c->r_out * sin(th);
       int in = or_fly_annulus(S, &st, 8u, &x, &y, v, &ir, or_uni(&st, 5) * c->dt);
       if (!in || S->n >= S->cap) continue; /* it does not enter */
@@ -817,11 +920,11 @@ void or_sort(or_state *S) {
  * each of i then j independently undergoes a Borgnakke-Larsen exchange with
  * probability P_inelastic (Bird's particle selection permitting double
  * relaxation, Sec. 2.2): with E_c = E_t + I_r,k the particle keeps
- * I_r,k' = E_c (1 - U^{1/(5/2 - w)}) (the d_r = 2 case of the BL partition)
- * and E_t = E_c - I_r,k'.  The pair then scatters isotropically (VHS, alpha =
- * 1) about the centre-of-mass velocity with |g'| = sqrt(4 E_t).  (sigma g)_max
- * stays fixed over the candidates of the step and takes the largest sigma g
- * seen afterwards. */
+ * I_r,k' = x E_c, x from or_bl_fraction (Beta(d_r/2, 5/2 - w)), and
+ * E_t = E_c - I_r,k'.  The pair then scatters about the centre-of-mass
+ * velocity with |g'| = sqrt(4 E_t) (or_scatter: isotropic for VHS, alpha =
+ * 1; the VSS deflection law otherwise).  (sigma g)_max stays fixed over the
+ * candidates of the step and takes the largest sigma g seen afterwards. */
 static void or_collide_cell(or_state *S, int cell) {
   const or_config *c = &S->c;
   int64_t s0 = S->start[cell];
@@ -833,7 +936,6 @@ static void or_collide_cell(or_state *S, int cell) {
   or_stream_init(&sn, c->seed, OR_TAG_NTC, 0u, (uint32_t)cell, S->step);
   int64_t m = or_iround(xm, or_uni(&sn, 0));
   double e = 2.0 - 2.0 * c->omega;
-  double bl_exp = 1.0 / (2.5 - c->omega);
   double obs = 0.0;
   for (int64_t k = 0; k < m; ++k) {
     or_stream st;
@@ -858,23 +960,20 @@ static void or_collide_cell(or_state *S, int cell) {
     double et = 0.25 * g2;
     if (or_uni(&st, 3) < S->p_inel) {
       double ec = et + S->ir[pi];
-      S->ir[pi] = ec * (1.0 - pow(or_uni(&st, 4), bl_exp));
+      S->ir[pi] = ec * or_bl_fraction(S, or_uni(&st, 4), &st, OR_JX_BL);
       et = ec - S->ir[pi];
       S->n_inel += 1;
     }
     if (or_uni(&st, 5) < S->p_inel) {
       double ec = et + S->ir[pj];
-      S->ir[pj] = ec * (1.0 - pow(or_uni(&st, 6), bl_exp));
+      S->ir[pj] = ec * or_bl_fraction(S, or_uni(&st, 6), &st, OR_JX_BL + 2u);
       et = ec - S->ir[pj];
       S->n_inel += 1;
     }
     double gn = 2.0 * sqrt(et);
-    double cth = 2.0 * or_uni(&st, 7) - 1.0;
-    double sth = sqrt(1.0 - cth * cth);
-    double ph = 2.0 * M_PI * or_uni(&st, 8);
-    double hx = 0.5 * gn * cth;
-    double hy = 0.5 * gn * sth * cos(ph);
-    double hz = 0.5 * gn * sth * sin(ph);
+    double h[3];
+    or_scatter(S, gx, gy, gz, gn, or_uni(&st, 7), or_uni(&st, 8), h);
+    double hx = h[0], hy = h[1], hz = h[2];
     double cx = 0.5 * (S->vx[pi] + S->vx[pj]);
     double cy = 0.5 * (S->vy[pi] + S->vy[pj]);
     double cz = 0.5 * (S->vz[pi] + S->vz[pj]);
@@ -1033,7 +1132,7 @@ int or_dig_correct(or_state *S, const double *target) {
           S->tvx[d] = t[1] + st_ * n1;
           S->tvy[d] = t[2] + st_ * n2;
           S->tvz[d] = t[3] + st_ * n3;
-          S->tir[d] = -t[5] * log(or_uni(&sp, 6));
+          S->tir[d] = or_ir_draw(S, t[5], or_uni(&sp, 6), &sp, OR_JX_OWN);
         }
         ++d;
       }

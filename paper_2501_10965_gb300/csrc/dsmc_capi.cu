@@ -119,8 +119,8 @@ int validate(const dsmc_config* c, char* why, size_t n) {
   }
   if (!(c->kn > 0) || !(c->dt > 0) || !(c->z_rot > 0)) return snprintf(why, n, "kn, dt, z_rot must be positive"), DSMC_ERR_ARG;
   if (!(c->omega > 0.5 && c->omega <= 1.0)) return snprintf(why, n, "omega must lie in (0.5, 1]"), DSMC_ERR_ARG;
-  if (c->alpha != 1.0) return snprintf(why, n, "only alpha = 1 (VHS scattering) is supported"), DSMC_ERR_ARG;
-  if (c->d_r != 2.0) return snprintf(why, n, "only d_r = 2 is supported"), DSMC_ERR_ARG;
+  if (!(c->alpha > 0.0 && c->alpha <= 2.0)) return snprintf(why, n, "alpha (VSS) must lie in (0, 2]"), DSMC_ERR_ARG;
+  if (c->d_r != 2.0 && c->d_r != 3.0) return snprintf(why, n, "d_r must be 2 or 3"), DSMC_ERR_ARG;
   if (c->precision != DSMC_PREC_FP64_DET && c->precision != DSMC_PREC_FP32) return snprintf(why, n, "bad precision"), DSMC_ERR_ARG;
   if (!(c->init_rho > 0) || !(c->init_tt > 0) || !(c->init_tr > 0)) return snprintf(why, n, "initial rho, T must be positive"), DSMC_ERR_ARG;
   const int nw = ann ? 0 : 2 * c->dim;
@@ -384,6 +384,16 @@ void fill_params(const dsmc_config* c, Params<T>& p, CellParams& cp) {
   p.p_inel = (T)p_inel;
   p.vhs_e = (T)(2.0 - 2.0 * w);
   p.bl_exp = (T)(1.0 / (2.5 - w));
+  {
+    // Borgnakke-Larsen partition Beta(a, b) and its mode (used for d_r = 3)
+    const double ba = 0.5 * c->d_r, bb = 2.5 - w;
+    p.d_r3 = (c->d_r == 3.0) ? 1 : 0;
+    p.bl_am1 = (T)(ba - 1.0);
+    p.bl_bm1 = (T)(bb - 1.0);
+    p.bl_xs = (T)((ba - 1.0) / (ba + bb - 2.0));
+  }
+  p.vss = (a != 1.0) ? 1 : 0;
+  p.vss_ia = (T)(1.0 / a);
   p.collisions = c->collisions ? 1 : 0;
   for (int k = 0; k < 4; ++k) {
     p.wall_kind[k] = c->wall_kind[k];
@@ -586,6 +596,9 @@ int init_state(dsmc_handle* h, State<T>& s, Params<T>& p0, Params<T>* d_p) {
   cudaMemcpyAsync(s.sgmax, sg.data(), sizeof(T) * nc, cudaMemcpyHostToDevice, st);
   s.cases = Cases<T>{d_p, h->d_cp, h->d_cell0, h->d_cell_case, ncases};
   s.batch = ncases > 1;
+  s.gen = false;
+  for (int k = 0; k < ncases; ++k)
+    if (h->cfgs[k].d_r != 2.0 || h->cfgs[k].alpha != 1.0) s.gen = true;
   s.ncells = nc;
   h->cur = 0;
   h->lay = 0;
@@ -652,6 +665,9 @@ int init_cases(const dsmc_config* cfgs, int ncases, void* dev_workspace, size_t 
     if (cfgs[k].dim != cfgs[0].dim || cfgs[k].precision != cfgs[0].precision) return DSMC_ERR_ARG;
     if (cfgs[k].mesh == DSMC_MESH_ANNULUS && ncases != 1) return DSMC_ERR_ARG;  // the annulus runs alone
     if (cfgs[k].synth2d && ncases != 1) return DSMC_ERR_ARG;                    // so does the 2D solve
+    // the FP32 fused step has its d_r = 3 / VSS instantiation for single cases only
+    if (ncases != 1 && cfgs[k].precision == DSMC_PREC_FP32 && (cfgs[k].d_r != 2.0 || cfgs[k].alpha != 1.0))
+      return DSMC_ERR_ARG;
   }
   const Plan pl = make_plan(cfgs, ncases, nullptr, nullptr);
   if (!dev_workspace || bytes < pl.bytes) return DSMC_ERR_ARG;
@@ -725,6 +741,8 @@ int dsmc_batch_workspace_size(const dsmc_config* cfgs, int ncases, size_t* bytes
     if (cfgs[k].dim != cfgs[0].dim || cfgs[k].precision != cfgs[0].precision) return DSMC_ERR_ARG;
     if (cfgs[k].mesh == DSMC_MESH_ANNULUS && ncases != 1) return DSMC_ERR_ARG;
     if (cfgs[k].synth2d && ncases != 1) return DSMC_ERR_ARG;
+    if (ncases != 1 && cfgs[k].precision == DSMC_PREC_FP32 && (cfgs[k].d_r != 2.0 || cfgs[k].alpha != 1.0))
+      return DSMC_ERR_ARG;
   }
   *bytes = make_plan(cfgs, ncases, nullptr, nullptr).bytes;
   return DSMC_OK;

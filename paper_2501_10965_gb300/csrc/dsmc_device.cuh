@@ -36,6 +36,15 @@ struct Params {
   T lx, ly, dx, dy, sx, sy;  // sx = nx / lx, sy = ny / ly
   T vcell, fnum, dt;
   T c_sigma, p_inel, vhs_e, bl_exp;  // vhs_e = 2 - 2 omega, bl_exp = 1/(5/2 - omega)
+  // rotational degrees of freedom: d_r3 = 0 for d_r = 2, 1 for d_r = 3; the
+  // Borgnakke-Larsen partition Beta(a, b), a = d_r/2, b = 5/2 - omega, for
+  // d_r = 3 by acceptance-rejection: bl_am1 = a - 1, bl_bm1 = b - 1 and its
+  // mode bl_xs = (a - 1)/(a + b - 2)
+  int d_r3;
+  T bl_am1, bl_bm1, bl_xs;
+  // VSS scattering (vss = 1 for alpha != 1): cos chi = 2 u^{vss_ia} - 1, vss_ia = 1/alpha
+  int vss;
+  T vss_ia;
   int collisions;
   int wall_kind[4];
   T wall_t[4];
@@ -210,6 +219,15 @@ __device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x)
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 
+// Indices of the extra uniforms that only d_r = 3 draws (rot_energy) and the
+// Borgnakke-Larsen acceptance-rejection (bl_fraction) take from a stream:
+// 1024-1025 for the I_r of a particle's own stream, 1026 + jh/2 and 1027 +
+// jh/2 for a wall hit whose four uniforms start at jh, 2048 + 4t .. 2051 + 4t
+// for try t of a candidate pair (2048 + 4t, +1: particle i; +2, +3: j).
+constexpr uint32_t JX_OWN = 1024u, JX_BL = 2048u;
+constexpr int BL_TRIES = 32;
+__host__ __device__ __forceinline__ uint32_t jx_hit(uint32_t jh) { return 1026u + jh / 2u; }
+
 template <typename T>
 __device__ __forceinline__ void box_muller(T ua, T ub, T* n1, T* n2) {
   const T r = m_sqrt(T(-2) * m_log(ua));
@@ -217,6 +235,95 @@ __device__ __forceinline__ void box_muller(T ua, T ub, T* n1, T* n2) {
   m_sincos_2pi(ub, &s, &c);
   *n1 = r * c;
   *n2 = r * s;
+}
+
+// Rotational energy of one molecule in equilibrium at temperature tq (Sec.
+// 2.1, e_r = d_r T_r / 2): I_r / tq is Gamma(d_r / 2).  d_r = 2: -tq ln u
+// with u the draw's main uniform; d_r = 3: Gamma(1) + Gamma(1/2), the second
+// as Z^2 / 2 of a Box-Muller normal, -ln(u_a) cos^2(2 pi u_b), with u_a, u_b
+// the uniforms jx, jx + 1 of stream st.
+// (The d_r = 3 and VSS parts are compiled only where the GEN template switch
+// of the caller asks for them, so that the fused step of an N2-like gas keeps
+// its registers.)
+template <typename T, typename S>
+__device__ __forceinline__ T gamma_half_part(S& st, uint32_t jx) {
+  T sb, cb;
+  m_sincos_2pi(st.u(jx + 1u), &sb, &cb);
+  return -m_log(st.u(jx)) * cb * cb;
+}
+
+template <typename T, typename S>
+__device__ __forceinline__ T rot_energy(bool d_r3, T tq, T u, S& st, uint32_t jx) {
+  T e = -m_log(u);
+  if (d_r3) e += gamma_half_part<T>(st, jx);
+  return tq * e;
+}
+
+// Fraction x = I_r,k' / E_c kept as rotational energy in one
+// Borgnakke-Larsen exchange (Sec. 2.2): x ~ Beta(d_r/2, 5/2 - omega).  d_r
+// = 2: the inverse CDF 1 - u^{1/(5/2 - omega)} at the main uniform u.  d_r =
+// 3: acceptance-rejection under the uniform envelope of x^{a-1} (1-x)^{b-1}
+// (maximum at its mode x*): try t proposes x (u at t = 0, else uniform jx +
+// 4t) and accepts it when ln(uniform jx + 4t + 1) < (a-1) ln(x/x*) + (b-1)
+// ln((1-x)/(1-x*)); after BL_TRIES rejections (odds below 1e-18) x = x*.
+template <typename T>
+__device__ __forceinline__ T bl_fraction_ar(const Params<T>& p, T u, uint32_t k, uint32_t cell, uint32_t step,
+                                         uint32_t jx) {
+  Stream<T> st(4u, k, cell, step, p.k0, p.k1);  // the candidate's stream (TAG_COLL)
+  const T xs = p.bl_xs;
+  for (int t = 0; t < BL_TRIES; ++t) {
+    const T x = (t == 0) ? u : st.u(jx + 4u * (uint32_t)t);
+    const T acc = st.u(jx + 4u * (uint32_t)t + 1u);
+    if (m_log(acc) < p.bl_am1 * m_log(x / xs) + p.bl_bm1 * m_log((T(1) - x) / (T(1) - xs))) return x;
+  }
+  return xs;
+}
+
+template <typename T, bool GEN>
+__device__ __forceinline__ T bl_fraction(const Params<T>& p, T u, uint32_t k, uint32_t cell, uint32_t step,
+                                         uint32_t jx) {
+  if (!GEN || !p.d_r3) return T(1) - m_pow(u, p.bl_exp);
+  return bl_fraction_ar(p, u, k, cell, step, jx);
+}
+
+// Half the post-collision relative velocity, h = g'/2, |g'| = gn.  VHS
+// (alpha = 1): isotropic, cos(theta) = 2 u - 1 and azimuth 2 pi v in the lab
+// frame.  VSS (Sec. 2.2): deflection chi from the pre-collision direction e
+// = g/|g| with cos(chi) = 2 u^{1/alpha} - 1, azimuth 2 pi v about e measured
+// from e1, the coordinate axis least aligned with e made orthogonal to e (e2
+// = e x e1).
+template <typename T>
+__device__ __forceinline__ void scatter_vss(const Params<T>& p, T gx, T gy, T gz, T gn, T u, T v, T* h) {
+  T sph, cph;
+  m_sincos_2pi(v, &sph, &cph);
+  const T g = m_sqrt(gx * gx + gy * gy + gz * gz);
+  const T e[3] = {gx / g, gy / g, gz / g};
+  const T m0 = e[0] < T(0) ? -e[0] : e[0], m1 = e[1] < T(0) ? -e[1] : e[1], m2 = e[2] < T(0) ? -e[2] : e[2];
+  const int ax = (m0 <= m1 && m0 <= m2) ? 0 : (m1 <= m2 ? 1 : 2);
+  const T d = e[ax];
+  T e1[3];
+  for (int k = 0; k < 3; ++k) e1[k] = ((k == ax) ? T(1) : T(0)) - d * e[k];
+  const T l1 = m_sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  for (int k = 0; k < 3; ++k) e1[k] = e1[k] / l1;
+  const T e2[3] = {e[1] * e1[2] - e[2] * e1[1], e[2] * e1[0] - e[0] * e1[2], e[0] * e1[1] - e[1] * e1[0]};
+  const T cch = T(2) * m_pow(u, p.vss_ia) - T(1);
+  const T sch = m_sqrt(T(1) - cch * cch);
+  for (int k = 0; k < 3; ++k) h[k] = T(0.5) * gn * (cch * e[k] + sch * (cph * e1[k] + sph * e2[k]));
+}
+
+template <typename T, bool GEN>
+__device__ __forceinline__ void scatter(const Params<T>& p, T gx, T gy, T gz, T gn, T u, T v, T* h) {
+  if (GEN && p.vss) {
+    scatter_vss(p, gx, gy, gz, gn, u, v, h);
+    return;
+  }
+  T sph, cph;
+  m_sincos_2pi(v, &sph, &cph);
+  const T cth = T(2) * u - T(1);
+  const T sth = m_sqrt(T(1) - cth * cth);
+  h[0] = T(0.5) * gn * cth;
+  h[1] = T(0.5) * gn * sth * cph;
+  h[2] = T(0.5) * gn * sth * sph;
 }
 
 // Iround of Sec. 3.2 step i: floor(x) + 1 with probability x - floor(x).
@@ -321,6 +428,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// d_r = 3: rotational energy re-emitted by a wall hit whose four uniforms of
+// stream (tag, idx, cell, step) start at jh (ud the fourth), out of line
+template <typename T>
+__device__ __forceinline__ T wall_rot_energy3(const Params<T>& p, T tw, T ud, uint32_t tag, uint32_t idx, uint32_t cell,
+                                           uint32_t step, uint32_t jh) {
+  Stream<T> sx(tag, idx, cell, step, p.k0, p.k1);
+  return rot_energy(true, tw, ud, sx, jx_hit(jh));
+}
+
 // ---------------------------------------------------------------------------
 // Stage (a): free flight with wall interaction (Sec. 2.2; fully diffuse
 // walls of Sec. 4).  A diffuse wall re-emits with normal speed
@@ -329,7 +445,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // at T_w; the particle then flies the rest of the step; at most MAX_HITS hits.
 // tally[w*5 + q]: hits, momentum (3) and energy delivered to wall w.
 // ---------------------------------------------------------------------------
-template <typename T, int DIM, bool TALLY>
+template <typename T, int DIM, bool TALLY, bool GEN = true>
 __device__ void fly_walls(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& ir, uint32_t idx,
                           uint32_t cell, uint32_t step, T* tally, unsigned long long* hits_out,
                           unsigned long long* maxhit_out) {
@@ -415,6 +531,7 @@ __device__ void fly_walls(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T
         vz = p.wall_u[w][2] + sT * n2;
       }
       ir = -Tw * m_log(ud);
+      if (GEN && p.d_r3) ir = wall_rot_energy3(p, Tw, ud, TAG_WALL, idx, cell, step, 4u * (uint32_t)hits);
     }
     if (TALLY) {
       T* tl = tally + 5 * w;
@@ -439,7 +556,7 @@ __device__ void fly_walls(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T
 // (tag, idx, cell, step).  Returns false if the particle ends at or beyond
 // r_out (it leaves the domain).  tally[0..4]: hits, momentum (3) and energy
 // delivered to the cylinder.
-template <typename T, bool TALLY>
+template <typename T, bool TALLY, bool GEN = true>
 __device__ bool fly_ann(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& ir, uint32_t tag, uint32_t idx,
                         uint32_t cell, uint32_t step, uint32_t j0, T t, T* tally, unsigned long long* hits_out,
                         unsigned long long* maxhit_out) {
@@ -493,6 +610,7 @@ __device__ bool fly_ann(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& 
       vy = vn * ny + vt * nx;
       vz = sT * n2;
       ir = -Tw * m_log(u4[3]);
+      if (GEN && p.d_r3) ir = wall_rot_energy3(p, Tw, u4[3], tag, idx, cell, step, j0 + 4u * (uint32_t)hits);
     }
     if (TALLY) {
       atomicAdd(tally + 0, T(1));
@@ -555,7 +673,7 @@ __device__ __forceinline__ bool flight_stays_inside(const Params<T>& p, T x, T y
 
 // Full flight: the common straight flight inline, the wall loop only when a
 // wall is reached (the loop repeats the first straight step identically).
-template <typename T, int DIM, bool TALLY>
+template <typename T, int DIM, bool TALLY, bool GEN = true>
 __device__ __forceinline__ void fly(const Params<T>& p, T& x, T& y, T& vx, T& vy, T& vz, T& ir, uint32_t idx,
                                     uint32_t cell, uint32_t step, T* tally, unsigned long long* hits_out,
                                     unsigned long long* maxhit_out) {
@@ -565,7 +683,7 @@ __device__ __forceinline__ void fly(const Params<T>& p, T& x, T& y, T& vx, T& vy
     y = yn;
     return;
   }
-  fly_walls<T, DIM, TALLY>(p, x, y, vx, vy, vz, ir, idx, cell, step, tally, hits_out, maxhit_out);
+  fly_walls<T, DIM, TALLY, GEN>(p, x, y, vx, vy, vz, ir, idx, cell, step, tally, hits_out, maxhit_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -588,7 +706,7 @@ struct CollCount {
   unsigned cand, coll, clip, inel;
 };
 
-template <typename T>
+template <typename T, bool GEN = true>
 __device__ __forceinline__ void collide_cell(const Params<T>& p, T* __restrict__ vx, T* __restrict__ vy,
                              T* __restrict__ vz, T* __restrict__ ir, int n, uint32_t cell,
                              uint32_t step, T* sgmax_ptr, uint32_t* owner, CollCount& cc) {
@@ -680,24 +798,20 @@ __device__ __forceinline__ void collide_cell(const Params<T>& p, T* __restrict__
         T et = T(0.25) * g2;
         if (uinel < p.p_inel) {
           const T ec = et + ir[pi];
-          ir[pi] = ec * (T(1) - m_pow(up[0], p.bl_exp));
+          ir[pi] = ec * bl_fraction<T, GEN>(p, up[0], k, cell, step, JX_BL);
           et = ec - ir[pi];
           cc.inel += 1;
         }
         if (up[1] < p.p_inel) {
           const T ec = et + ir[pj];
-          ir[pj] = ec * (T(1) - m_pow(up[2], p.bl_exp));
+          ir[pj] = ec * bl_fraction<T, GEN>(p, up[2], k, cell, step, JX_BL + 2u);
           et = ec - ir[pj];
           cc.inel += 1;
         }
         const T gn = T(2) * m_sqrt(et);
-        const T cth = T(2) * up[3] - T(1);
-        const T sth = m_sqrt(T(1) - cth * cth);
-        T sph, cph;
-        m_sincos_2pi(up[4], &sph, &cph);
-        const T hx = T(0.5) * gn * cth;
-        const T hy = T(0.5) * gn * sth * cph;
-        const T hz = T(0.5) * gn * sth * sph;
+        T hv[3];
+        scatter<T, GEN>(p, gx, gy, gz, gn, up[3], up[4], hv);
+        const T hx = hv[0], hy = hv[1], hz = hv[2];
         const T cx = T(0.5) * (vx[pi] + vx[pj]);
         const T cy = T(0.5) * (vy[pi] + vy[pj]);
         const T cz = T(0.5) * (vz[pi] + vz[pj]);

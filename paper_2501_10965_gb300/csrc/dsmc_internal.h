@@ -80,6 +80,7 @@ struct State {
   Ovf ovf[2];
   Cases<T> cases;
   bool batch;  // several cases: kernels read their parameters per cell
+  bool gen;    // a gas with d_r = 3 or VSS scattering: the fused step's general instantiation
   int fwpb;    // FP32 fused step: warps per CTA (0: not tuned yet)
   Params<double> pinj;  // annulus: FP64 parameters of the freestream entry
   double* inj_mu;       // annulus: expected entries of every outer face per step

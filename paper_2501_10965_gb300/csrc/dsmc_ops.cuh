@@ -108,7 +108,7 @@ __global__ void k_init(Params<T> p, PBuf<T> b, const int32_t* __restrict__ start
     b.vx[slot] = u0x + stt * n1;
     b.vy[slot] = u0y + stt * n2;
     b.vz[slot] = u0z + stt * n3;
-    b.ir[slot] = -tr * m_log(st.u(6));
+    b.ir[slot] = rot_energy(p.d_r3 != 0, tr, st.u(6), st, JX_OWN);
     if (cellof) cellof[slot] = cell;
     if (k == 0) count[cell] = ppc;
   }
@@ -149,7 +149,7 @@ __global__ void k_init_cells(Cases<T> cases, int ncells, PBuf<T> b, const int32_
     b.vx[slot] = p.init_u[0] + stt * n1;
     b.vy[slot] = p.init_u[1] + stt * n2;
     b.vz[slot] = p.init_u[2] + stt * n3;
-    b.ir[slot] = -p.init_tr * m_log(st.u(6));
+    b.ir[slot] = rot_energy(p.d_r3 != 0, p.init_tr, st.u(6), st, JX_OWN);
     if (cellof) cellof[slot] = cell;
   }
   if (lane == 0) count[cell] = ppc;
@@ -305,7 +305,7 @@ __device__ __forceinline__ bool inflow_particle(const Params<double>& p, int k, 
   vy = vn * ny + vt * ty;
   vz = p.fs_u[2] + sT * n2;
   const double th = 2.0 * PI_D * ((double)k + st.u(3)) / (double)p.nx;
-  ir = -p.fs_t * log(st.u(4));
+  ir = rot_energy(p.d_r3 != 0, p.fs_t, st.u(4), st, JX_OWN);
   x = p.r_out * cos(th);
   y = p.r_out * sin(th);
   return fly_ann<double, TALLY>(p, x, y, vx, vy, vz, ir, TAG_INJ, (uint32_t)q, (uint32_t)k, step, 8u, st.u(5) * p.dt,
@@ -429,7 +429,7 @@ __device__ __forceinline__ bool inflow_particle_f32(const Params<float>& p, int 
   vy = vn * ny + vt * ty;
   vz = p.fs_u[2] + sT * n2;
   const float th = 6.283185307179586f * ((float)k + st.u(3)) / (float)p.nx;
-  ir = -p.fs_t * __logf(st.u(4));
+  ir = rot_energy(p.d_r3 != 0, p.fs_t, st.u(4), st, JX_OWN);
   x = p.r_out * cosf(th);
   y = p.r_out * sinf(th);
   return fly_ann<float, true>(p, x, y, vx, vy, vz, ir, TAG_INJ, (uint32_t)q, (uint32_t)k, step, 8u, st.u(5) * p.dt,
@@ -801,7 +801,7 @@ inline size_t fused_smem_bytes(int tile, int fwpb) { return (size_t)fwpb * tile 
 // destination bin reserves the slots; (M3) fly again (the same counter-based
 // random stream, so the same result) and store.  Counters are flushed by the
 // last warp of the block to finish, so warps never wait for one another.
-template <int DIM, bool BATCH, int FWPB, bool ANN>
+template <int DIM, bool BATCH, int FWPB, bool ANN, bool GEN>
 __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_constant__ Params<float> pk,
                                                         Cases<float> cases, int ncells, PBuf<float> in,
                                                         PBuf<float> out,
@@ -896,7 +896,7 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
         constexpr bool whole = decltype(whole_tag)::value;
         if (whole && (flags & 1)) {
           CollCount cc{0, 0, 0, 0};
-          collide_cell<float>(p, vx, vy, vz, ir, m, (uint32_t)lcell, step_c, sgmax + cell, own, cc);
+          collide_cell<float, GEN>(p, vx, vy, vz, ir, m, (uint32_t)lcell, step_c, sgmax + cell, own, cc);
           flush_counts<float>(cc, s_cnt);
           __syncwarp();
         }
@@ -952,13 +952,13 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
               if (code < 9) {
                 x = x + a * p.dt;
                 y = y + b * p.dt;
-              } else if (!fly_ann<float, true>(p, x, y, a, b, c, e, TAG_WALL, (uint32_t)(q0 + q), (uint32_t)lcell, step_m, 0u,
+              } else if (!fly_ann<float, true, GEN>(p, x, y, a, b, c, e, TAG_WALL, (uint32_t)(q0 + q), (uint32_t)lcell, step_m, 0u,
                                                p.dt, s_tally, &s_hits[0], &s_hits[1])) {
                 atomicAdd(&s_out, 1u);  // left through the outer circle
                 continue;
               }
             } else {
-              fly<float, DIM, true>(p, x, y, a, b, c, e, (uint32_t)(q0 + q), (uint32_t)lcell, step_m, s_tally, &s_hits[0],
+              fly<float, DIM, true, GEN>(p, x, y, a, b, c, e, (uint32_t)(q0 + q), (uint32_t)lcell, step_m, s_tally, &s_hits[0],
                                     &s_hits[1]);
             }
             int d = -1, slot, s0, cap;
@@ -1023,7 +1023,7 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
           // and the move chunk by chunk through the tile
           if (flags & 1) {
             CollCount cc{0, 0, 0, 0};
-            collide_cell<float>(p, in.vx + base, in.vy + base, in.vz + base, in.ir + base, n, (uint32_t)lcell, step_c,
+            collide_cell<float, GEN>(p, in.vx + base, in.vy + base, in.vz + base, in.ir + base, n, (uint32_t)lcell, step_c,
                                 sgmax + cell, owner_g + base, cc);
             flush_counts<float>(cc, s_cnt);
             fence_proxy_async_global();  // the bulk copies below read these velocities
@@ -1069,13 +1069,13 @@ __global__ void __launch_bounds__(FWPB * 32, 32 / FWPB) k_fused(const __grid_con
         c = ovi.vz[q];
         e = ovi.ir[q];
         if constexpr (ANN) {
-          d = fly_ann<float, true>(p, x, y, a, bb, c, e, TAG_WALL, (uint32_t)q, (uint32_t)(p.ncells + 1), step_m, 0u,
+          d = fly_ann<float, true, GEN>(p, x, y, a, bb, c, e, TAG_WALL, (uint32_t)q, (uint32_t)(p.ncells + 1), step_m, 0u,
                                    p.dt, s_tally, &s_hits[0], &s_hits[1])
                   ? cell_of_ann<float>(p, x, y)
                   : -1;
           if (d < 0) atomicAdd(&s_out, 1u);
         } else {
-          fly<float, DIM, true>(p, x, y, a, bb, c, e, (uint32_t)q, (uint32_t)(p.ncells + 1), step_m, s_tally,
+          fly<float, DIM, true, GEN>(p, x, y, a, bb, c, e, (uint32_t)q, (uint32_t)(p.ncells + 1), step_m, s_tally,
                                 &s_hits[0], &s_hits[1]);
           d = c0 + cell_of<float, DIM>(p, x, y);
         }
@@ -1481,7 +1481,7 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
         box_muller(sp.u(4), sp.u(5), &n3, &n4);
         const double stt = sqrt(t[4]);
         const T vx = (T)(t[1] + stt * n1), vy = (T)(t[2] + stt * n2), vz = (T)(t[3] + stt * n3);
-        const T ir = (T)(-t[5] * log(sp.u(6)));
+        const T ir = (T)rot_energy(cp.d_r == 3.0, t[5], sp.u(6), sp, JX_OWN);
         out.vx[w] = vx;
         out.vy[w] = vy;
         out.vz[w] = vz;
@@ -1708,7 +1708,8 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
   p, s.cases, ncells, s.buf[cur], s.buf[other], s.start[lay], s.count[cur], s.count[other], s.sgmax, s.acc,      \
       s.comp, s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats, \
       s.flags + 8, s.stg, s.stc
-#define DSMC_FUSED_LAUNCH(D, B, W, A) k_fused<D, B, W, A><<<cblocks + oblocks, W * 32, smf, st>>>(DSMC_FUSED_ARGS)
+#define DSMC_FUSED_LAUNCH(D, B, W, A) k_fused<D, B, W, A, false><<<cblocks + oblocks, W * 32, smf, st>>>(DSMC_FUSED_ARGS)
+#define DSMC_FUSED_LAUNCH_GEN(D, A) k_fused<D, false, 4, A, true><<<cblocks + oblocks, 128, smf, st>>>(DSMC_FUSED_ARGS)
       const bool inject = p.mesh == 1 && (flags & 4);
       if (inject) {
         // annulus: the freestream entry of this step, on the side stream,
@@ -1722,7 +1723,12 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
             s.tally, s.stats, s.flags + 8);
         cudaEventRecord(s.ev_join, s.side);
       }
-      if (p.mesh == 1) {
+      if (s.gen) {
+        // d_r = 3 or VSS: one instantiation per mesh, 4 warps per CTA
+        if (p.mesh == 1) DSMC_FUSED_LAUNCH_GEN(2, true);
+        else if (p.dim == 1) DSMC_FUSED_LAUNCH_GEN(1, false);
+        else DSMC_FUSED_LAUNCH_GEN(2, false);
+      } else if (p.mesh == 1) {
         if (F == 2) DSMC_FUSED_LAUNCH(2, false, 2, true);
         else DSMC_FUSED_LAUNCH(2, false, 4, true);
       } else if (F == 2) {
@@ -1743,6 +1749,7 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
         }
       }
 #undef DSMC_FUSED_LAUNCH
+#undef DSMC_FUSED_LAUNCH_GEN
 #undef DSMC_FUSED_ARGS
       if (inject) cudaStreamWaitEvent(st, s.ev_join, 0);
       // the input overflow list has been consumed
@@ -1759,6 +1766,7 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
       return 1 | (do_sample ? 2 | fold : 0) | 4;
     };
     int i0 = 0;
+    if (s.gen) s.fwpb = 4;  // the general gas has the 4-warp shape only
     if (s.fwpb == 0 && nsteps >= 10) {
       // launch shape of the fused step: steps 2-4 timed with 4 warps per
       // CTA, steps 6-8 with 2 (steps 0-1 and 5 warm each one up); every step
@@ -1954,16 +1962,19 @@ void Ops<T>::configure(int tile) {
   cudaFuncSetAttribute(k_dig_apply<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
   if constexpr (sizeof(T) == 4) {
     const int sm4 = (int)fused_smem_bytes(tile, 4), sm2 = (int)fused_smem_bytes(tile, 2);
-    cudaFuncSetAttribute(k_fused<2, false, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
-    cudaFuncSetAttribute(k_fused<2, false, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
-    cudaFuncSetAttribute(k_fused<1, false, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
-    cudaFuncSetAttribute(k_fused<2, false, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
-    cudaFuncSetAttribute(k_fused<1, true, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
-    cudaFuncSetAttribute(k_fused<2, true, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
-    cudaFuncSetAttribute(k_fused<1, false, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
-    cudaFuncSetAttribute(k_fused<2, false, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
-    cudaFuncSetAttribute(k_fused<1, true, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
-    cudaFuncSetAttribute(k_fused<2, true, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<2, false, 4, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<1, false, 4, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<2, false, 4, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<2, false, 4, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<2, false, 2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<1, false, 4, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<2, false, 4, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<1, true, 4, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<2, true, 4, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm4);
+    cudaFuncSetAttribute(k_fused<1, false, 2, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<2, false, 2, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<1, true, 2, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+    cudaFuncSetAttribute(k_fused<2, true, 2, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
   }
 }
 

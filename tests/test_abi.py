@@ -64,8 +64,15 @@ def test_workspace_size_and_argument_errors():
     assert rc == 0 and n > 2 * 6 * 4 * 20_040_000  # two FP32 particle buffers at least
     rc, n64 = _ws(W.fourier_1d())
     assert rc == 0 and n64 > 2 * 6 * 8 * 10000
-    assert _ws(W.fourier_1d(d_r=3.0))[0] == -1
-    assert _ws(W.fourier_1d(alpha=1.5))[0] == -1
+    # d_r 2 or 3, VSS alpha in (0, 2]
+    assert _ws(W.fourier_1d(d_r=3.0))[0] == 0 and _ws(W.fourier_1d(alpha=1.5))[0] == 0
+    assert _ws(W.fourier_1d(d_r=4.0))[0] == -1 and _ws(W.fourier_1d(d_r=2.5))[0] == -1
+    assert _ws(W.fourier_1d(alpha=0.0))[0] == -1 and _ws(W.fourier_1d(alpha=2.5))[0] == -1
+    # a batch of FP32 general-gas cases has no fused-step instantiation
+    L = dsmc.load()
+    arr = (dsmc.DsmcConfig * 2)(*[dsmc.make_config(W.fourier_1d(precision="fp32", d_r=3.0, seed=k)) for k in range(2)])
+    n = ctypes.c_size_t()
+    assert L.dsmc_batch_workspace_size(arr, 2, ctypes.byref(n)) == -1
     assert _ws(W.fourier_1d(nx=0))[0] == -1
     assert _ws(W.fourier_1d(dt=-1.0))[0] == -1
     bad = W.fourier_1d()
