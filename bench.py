@@ -406,9 +406,17 @@ def run_gpu(args):
         from paper_2501_10965_gb300 import dig, workloads as Wk
         del sim, p, fields_host
         torch.cuda.empty_cache()
-        tts = dig.time_to_steady_dig_vs_plain(Wk.couette_1d(kn=0.01, kn_ref=0.1), replicas=args.tts_replicas)
+        cfg_tts = Wk.couette_1d(kn=0.01, kn_ref=0.1)
+        # the HoT network for "dig_mlp": trained on plain DIG's own states
+        # (independent seeds), judged cell by cell against the DSMC terms
+        t_train = time.perf_counter()
+        params, tinfo = dig.train_hot_model_on_dig([cfg_tts], replicas=64, iterations=40)
+        t_train = time.perf_counter() - t_train
+        tts = dig.time_to_steady_dig_vs_plain(cfg_tts, replicas=args.tts_replicas, hot_params=params)
         tts["workload"] = ("1D Couette, Kn 0.01, 200 cells x 200 particles, walls -/+100 m/s; DIG every 50 steps, "
-                           "Kn_ref 0.1; ensemble of replicas in one batched handle")
+                           "Kn_ref 0.1; ensemble of replicas in one batched handle; dig_mlp: DIG with the HoT "
+                           "network judged against the DSMC terms (z 3, pooled over the replicas of a cell)")
+        tts["network_training"] = dict(tinfo, wall_s=t_train)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg)

@@ -381,12 +381,34 @@ int hot_mlp_train(dsmc_handle *h, const double *dev_fields, const double *dev_ho
 /* HoT for the synthetic equations: dev_hot_out (ncells x DSMC_NHOT) = the
  * network's sigma_xx, sigma_xy, sigma_yy and q_t, q_r along grad T where
  * mask = 1, the DSMC HoT (dev_hot) everywhere else and for every other
- * component; a cell whose prediction is not finite keeps the DSMC HoT.
+ * component; a cell whose prediction is not finite keeps the DSMC HoT.  The
+ * network runs on the tensor cores (bfloat16 weights and layer inputs,
+ * mma.sync with FP32 sums).
  * host_judge (may be NULL) receives the mean squared difference between the
  * network and the DSMC HoT over the mask = 1 cells (normalised units).
  * dev_hot_out may equal dev_hot. */
 int hot_mlp_apply(dsmc_handle *h, const double *dev_fields, const double *dev_hot, const double *dev_kngll,
                   const uint8_t *dev_mask, double *dev_hot_out, double *host_judge);
+
+/* hot_mlp_apply with the DSMC terms as the judge of the network, cell by
+ * cell: each call adds, for every network cell (mask = 1), the residual r =
+ * network - DSMC of its 5 normalised outputs, and r^2, to the running sums
+ * of its group (dev_group: ncells int32 ids in [0, ncells), or NULL for one
+ * group per cell; e.g. the same cell of every replica of a batch), and a
+ * network cell takes the network's HoT only if its group holds at least
+ * min_samples (>= 2) residuals whose mean is within z (> 0) standard errors
+ * of zero for every output; otherwise it keeps the DSMC HoT.  The sums
+ * persist across calls (a DIG run's iterations) until hot_mlp_judge_reset
+ * or a change of the parameters.  The inference runs on the tensor cores
+ * (bfloat16 weights and inputs of every layer, FP32 sums).  host_nnet (may
+ * be NULL) receives the number of cells given the network's HoT; host_judge
+ * as in hot_mlp_apply. */
+int hot_mlp_apply_judged(dsmc_handle *h, const double *dev_fields, const double *dev_hot, const double *dev_kngll,
+                         const uint8_t *dev_mask, const int32_t *dev_group, double z, int min_samples,
+                         double *dev_hot_out, double *host_judge, int64_t *host_nnet);
+
+/* Clear the judge's running sums (hot_mlp_apply_judged). */
+int hot_mlp_judge_reset(dsmc_handle *h);
 
 #ifdef __cplusplus
 }

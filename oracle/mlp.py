@@ -124,13 +124,18 @@ def to_hot(Y: np.ndarray, scale: np.ndarray, hot_dsmc: np.ndarray) -> np.ndarray
     return h
 
 
-def forward(theta: np.ndarray, X: np.ndarray, bf16: bool = False):
-    """Returns (Y, cache)."""
+def forward(theta: np.ndarray, X: np.ndarray, bf16: bool = False, bf16_act: bool = False):
+    """Returns (Y, cache).  bf16: the weights (not the biases) rounded to
+    bfloat16.  bf16_act: each layer's input (the features, then the tanh
+    activations) rounded to bfloat16 as well, the inference form that feeds
+    bfloat16 tensor-core products with FP32 sums."""
     layers = unpack(theta)
     a = X
     cache = [X]
     for k, (W, b) in enumerate(layers):
         Wk = bf16_round(W) if bf16 else W
+        if bf16_act:
+            a = bf16_round(a)
         z = a @ Wk.T + b
         a = np.tanh(z) if k < 3 else z
         cache.append(a)

@@ -171,8 +171,9 @@ struct Mlp {
   float* S;          // ncells x 4: p, p sqrt(T), e_x, e_y
   float* w;          // ncells: 1 for a training / replaced cell, else 0
   float* out;        // ncells x 5 network outputs
-  double* scal;      // [0] loss, [2] judge sum, [3] judge count
+  double* scal;      // [0] loss, [2] judge sum, [3] judge count, [4] cells given the network's HoT
   int32_t* count;    // [0] number of cells with w = 1
+  double* jacc;      // ncells x 11 judge statistics per group: sum r (5), sum r^2 (5), count
 };
 // inputs, scales, targets (hot may be null) and weights of every cell
 void mlp_prepare(const Mlp& m, const CellParams* cp, const int32_t* cell_case, const int32_t* cell0, int ncells,
@@ -184,7 +185,10 @@ void mlp_grad(const Mlp& m, int ncells, cudaStream_t st);
 void mlp_adam(const Mlp& m, int t, double lr, cudaStream_t st);
 // bfloat16 copies of the master parameters
 void mlp_to_bf16(const Mlp& m, cudaStream_t st);
-// network outputs, the HoT for the synthetic equations and the judge sums
-void mlp_apply(const Mlp& m, int ncells, const double* hot, double* hot_out, cudaStream_t st);
+// network outputs, the HoT for the synthetic equations and the judge sums;
+// with z > 0 a cell takes the network's HoT only where its group's running
+// residual statistics pass the judge (see hot_mlp_apply_judged)
+void mlp_apply(const Mlp& m, int ncells, const double* hot, double* hot_out, cudaStream_t st,
+               const int32_t* group = nullptr, double z = 0.0, int min_samples = 0);
 
 }  // namespace dsmc

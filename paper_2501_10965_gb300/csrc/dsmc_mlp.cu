@@ -295,19 +295,198 @@ __global__ void k_mlp_bf16(const float* __restrict__ theta, uint16_t* __restrict
   if (q < MLP_NPARAM) wbf[q] = __bfloat16_as_ushort(__float2bfloat16_rn(theta[q]));
 }
 
+// ---------------------------------------------------------------------------
+// Inference on the tensor cores: every layer is one product of the tile's
+// activations (16 cells x K, bfloat16) with the layer's weights (K x N,
+// bfloat16) accumulated in FP32 by mma.sync m16n8k16; bias and tanh in FP32,
+// and the result, rounded to bfloat16, is already laid out as the next
+// layer's A operand (the accumulator fragment of two adjacent 8-column tiles
+// is the operand fragment of one 16-column k-slice).  A warp takes 16 cells
+// at a time; the CTA's warps share the weights, staged in shared memory in
+// rows padded so that the fragment loads of a warp hit 32 distinct banks.
+// ---------------------------------------------------------------------------
+constexpr int TC_WARPS = 4;
+constexpr int TC_K0 = 16;        // the 12 inputs padded to one k-slice
+constexpr int TC_LD0 = 12;       // words per row of the padded layer-0 weights (8 used)
+constexpr int TC_LD = 36;        // words per row of the 64-input weights (32 used)
+constexpr int TC_W0 = 64 * TC_LD0, TC_W1 = 64 * TC_LD, TC_W3 = 8 * TC_LD;
+constexpr int TC_WORDS = TC_W0 + 2 * TC_W1 + TC_W3;        // bfloat16 pairs
+constexpr int TC_BIAS = 64 * 3 + 8;                         // FP32 biases
+inline size_t tc_smem_bytes() { return sizeof(uint32_t) * (size_t)TC_WORDS + sizeof(float) * TC_BIAS; }
+
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x (low half) = lo
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One layer for the warp's 16 cells: a[KT][4] operand fragments (KT
+// k-slices of 16 inputs) times the NT 8-column tiles of the weights W
+// (rows of ld words, row n = output n), plus bias; d[NT][4] accumulators.
+template <int KT, int NT>
+__device__ __forceinline__ void tc_layer(const uint32_t (*a)[4], const uint32_t* W, int ld, const float* bias,
+                                         float (*d)[4], int g, int t) {
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const float b0 = bias[8 * j + 2 * t], b1 = bias[8 * j + 2 * t + 1];
+    d[j][0] = b0;
+    d[j][1] = b1;
+    d[j][2] = b0;
+    d[j][3] = b1;
+    const uint32_t* wr = W + (8 * j + g) * ld;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) mma16816(d[j], a[k], wr[8 * k + t], wr[8 * k + 4 + t]);
+  }
+}
+
+// tanh of the accumulators of 2 KT tiles, packed as KT operand fragments
+template <int KT>
+__device__ __forceinline__ void tc_to_operand(float (*d)[4], uint32_t (*a)[4]) {
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    a[k][0] = bf16x2(tanhf(d[2 * k][0]), tanhf(d[2 * k][1]));
+    a[k][1] = bf16x2(tanhf(d[2 * k][2]), tanhf(d[2 * k][3]));
+    a[k][2] = bf16x2(tanhf(d[2 * k + 1][0]), tanhf(d[2 * k + 1][1]));
+    a[k][3] = bf16x2(tanhf(d[2 * k + 1][2]), tanhf(d[2 * k + 1][3]));
+  }
+}
+
+__global__ void __launch_bounds__(TC_WARPS * 32) k_mlp_fwd_tc(const uint16_t* __restrict__ wbf,
+                                                              const float* __restrict__ theta,
+                                                              const float* __restrict__ X, int ncells,
+                                                              float* __restrict__ out) {
+  extern __shared__ __align__(16) uint32_t smw[];
+  uint32_t* W0 = smw;
+  uint32_t* W1 = W0 + TC_W0;
+  uint32_t* W2 = W1 + TC_W1;
+  uint32_t* W3 = W2 + TC_W1;
+  float* bs = reinterpret_cast<float*>(W3 + TC_W3);
+  // stage the bfloat16 weights as pairs along the input index (zero padded)
+  auto pair = [&](int k, int n, int i) -> uint32_t {  // inputs i, i + 1 of output n of layer k
+    const int ni = nin(k);
+    if (n >= nout(k) || i >= ni) return 0u;
+    const uint32_t lo = wbf[poff_w(k) + n * ni + i];
+    const uint32_t hi = (i + 1 < ni) ? wbf[poff_w(k) + n * ni + i + 1] : 0u;
+    return lo | (hi << 16);
+  };
+  for (int q = threadIdx.x; q < 64 * TC_LD0; q += blockDim.x) {
+    const int n = q / TC_LD0, w = q % TC_LD0;
+    W0[q] = (w < TC_K0 / 2) ? pair(0, n, 2 * w) : 0u;
+  }
+  for (int q = threadIdx.x; q < 64 * TC_LD; q += blockDim.x) {
+    const int n = q / TC_LD, w = q % TC_LD;
+    W1[q] = (w < 32) ? pair(1, n, 2 * w) : 0u;
+    W2[q] = (w < 32) ? pair(2, n, 2 * w) : 0u;
+  }
+  for (int q = threadIdx.x; q < 8 * TC_LD; q += blockDim.x) {
+    const int n = q / TC_LD, w = q % TC_LD;
+    W3[q] = (w < 32) ? pair(3, n, 2 * w) : 0u;
+  }
+  for (int q = threadIdx.x; q < TC_BIAS; q += blockDim.x) {
+    const int k = q / 64, j = q % 64;
+    bs[q] = (k < 3) ? theta[poff_b(k) + j] : (j < 5 ? theta[poff_b(3) + j] : 0.f);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int ntiles = (ncells + 15) / 16;
+  for (int tile = blockIdx.x * TC_WARPS + warp; tile < ntiles; tile += gridDim.x * TC_WARPS) {
+    const int c0 = tile * 16;
+    const int ca = c0 + g, cb = c0 + g + 8;
+    auto xin = [&](int c, int i) { return (c < ncells && i < 12) ? X[(size_t)c * 12 + i] : 0.f; };
+    uint32_t a0[1][4];
+    a0[0][0] = bf16x2(xin(ca, 2 * t), xin(ca, 2 * t + 1));
+    a0[0][1] = bf16x2(xin(cb, 2 * t), xin(cb, 2 * t + 1));
+    a0[0][2] = bf16x2(xin(ca, 2 * t + 8), xin(ca, 2 * t + 9));
+    a0[0][3] = bf16x2(xin(cb, 2 * t + 8), xin(cb, 2 * t + 9));
+    float d[8][4];
+    uint32_t a[4][4];
+    tc_layer<1, 8>(a0, W0, TC_LD0, bs, d, g, t);
+    tc_to_operand<4>(d, a);
+    tc_layer<4, 8>(a, W1, TC_LD, bs + 64, d, g, t);
+    tc_to_operand<4>(d, a);
+    tc_layer<4, 8>(a, W2, TC_LD, bs + 128, d, g, t);
+    tc_to_operand<4>(d, a);
+    float o[1][4];
+    tc_layer<4, 1>(a, W3, TC_LD, bs + 192, o, g, t);
+    // row g: outputs 2t, 2t + 1 in o[0][0..1]; row g + 8 in o[0][2..3]
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = h ? cb : ca;
+      if (c >= ncells) continue;
+      if (2 * t < 5) out[(size_t)c * 5 + 2 * t] = o[0][2 * h];
+      if (2 * t + 1 < 5) out[(size_t)c * 5 + 2 * t + 1] = o[0][2 * h + 1];
+    }
+  }
+}
+
+// The judge's statistics: every cell of the network (w = 1, finite
+// outputs) adds its residual r = network - DSMC (5 normalised outputs) and
+// r^2 to its group's sums, and 1 to its count (FP64).
+__global__ void k_mlp_judge_acc(int ncells, const float* __restrict__ out, const float* __restrict__ Y,
+                                const float* __restrict__ w, const int32_t* __restrict__ group,
+                                double* __restrict__ jacc) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+    const float* o = out + (size_t)c * 5;
+    bool fin = true;
+    for (int k = 0; k < 5; ++k) fin = fin && isfinite(o[k]);
+    if (w[c] == 0.f || !fin) continue;
+    double* a = jacc + (size_t)(group ? group[c] : c) * 11;
+    for (int k = 0; k < 5; ++k) {
+      const double r = (double)o[k] - (double)Y[(size_t)c * 5 + k];
+      atomicAdd(a + k, r);
+      atomicAdd(a + 5 + k, r * r);
+    }
+    atomicAdd(a + 10, 1.0);
+  }
+}
+
+// true if the group's residuals are consistent with zero mean: at least
+// min_samples of them, and for every output |mean| <= z standard errors
+__device__ __forceinline__ bool judge_pass(const double* a, double z, int min_samples) {
+  const double n = a[10];
+  if (n < (double)min_samples) return false;
+  for (int k = 0; k < 5; ++k) {
+    const double m = a[k] / n;
+    const double var = fmax(a[5 + k] / n - m * m, 0.0) * n / (n - 1.0);
+    if (fabs(m) > z * sqrt(var / n)) return false;
+  }
+  return true;
+}
+
 // HoT for the synthetic equations and the judge sums (network against DSMC);
-// hot and hot_out may be the same array (each thread reads its cell first)
+// hot and hot_out may be the same array (each thread reads its cell first).
+// With z > 0 a network cell keeps the DSMC HoT unless its group passes the
+// judge (judge_pass).
 __global__ void k_mlp_hot(int ncells, const float* __restrict__ out, const float* __restrict__ Y,
                           const float* __restrict__ S, const float* __restrict__ w, const double* hot,
-                          double* hot_out, double* __restrict__ scal) {
-  double jsum = 0.0, jcnt = 0.0;
+                          double* hot_out, double* __restrict__ scal, const int32_t* __restrict__ group,
+                          const double* __restrict__ jacc, double z, int min_samples) {
+  double jsum = 0.0, jcnt = 0.0, nnet = 0.0;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
     double h[12];
     for (int k = 0; k < 12; ++k) h[k] = hot[(size_t)c * 12 + k];
     const float* o = out + (size_t)c * 5;
     bool fin = true;
     for (int k = 0; k < 5; ++k) fin = fin && isfinite(o[k]);
+    const bool judged = z > 0.0 && w[c] != 0.f && fin;
+    const bool pass = !judged || judge_pass(jacc + (size_t)(group ? group[c] : c) * 11, z, min_samples);
     if (w[c] != 0.f && fin) {
+      for (int k = 0; k < 5; ++k) {
+        const double r = (double)o[k] - (double)Y[(size_t)c * 5 + k];
+        jsum += r * r;
+      }
+      jcnt += 5.0;
+    }
+    if (w[c] != 0.f && fin && pass) {
+      nnet += 1.0;
       const double p = S[(size_t)c * 4], ps = S[(size_t)c * 4 + 1];
       const double ex = S[(size_t)c * 4 + 2], ey = S[(size_t)c * 4 + 3];
       h[0] = (double)o[0] * p;
@@ -320,11 +499,6 @@ __global__ void k_mlp_hot(int ncells, const float* __restrict__ out, const float
         h[base[r]] += (nw - along) * ex;
         h[base[r] + 1] += (nw - along) * ey;
       }
-      for (int k = 0; k < 5; ++k) {
-        const double r = (double)o[k] - (double)Y[(size_t)c * 5 + k];
-        jsum += r * r;
-      }
-      jcnt += 5.0;
     }
     for (int k = 0; k < 12; ++k) hot_out[(size_t)c * 12 + k] = h[k];
   }
@@ -332,6 +506,7 @@ __global__ void k_mlp_hot(int ncells, const float* __restrict__ out, const float
     atomicAdd(scal + 2, jsum);
     atomicAdd(scal + 3, jcnt);
   }
+  if (nnet > 0.0) atomicAdd(scal + 4, nnet);
 }
 
 inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
@@ -373,15 +548,16 @@ void mlp_to_bf16(const Mlp& m, cudaStream_t st) {
   k_mlp_bf16<<<blocks_for(MLP_NPARAM, 256), 256, 0, st>>>(m.theta, m.wbf);
 }
 
-void mlp_apply(const Mlp& m, int ncells, const double* hot, double* hot_out, cudaStream_t st) {
-  configure_fb();
-  const int ntiles = blocks_for(ncells, MLP_TILE);
-  const int grid = ntiles < MLP_GRID ? ntiles : MLP_GRID;
-  k_mlp_fb<false><<<grid, MLP_THREADS, fb_smem_bytes(false), st>>>(m.wbf, m.X, m.Y, m.w, m.count, ncells, m.partial,
-                                                                    m.part_loss, m.out);
-  cudaMemsetAsync(m.scal + 2, 0, 2 * sizeof(double), st);
+void mlp_apply(const Mlp& m, int ncells, const double* hot, double* hot_out, cudaStream_t st,
+               const int32_t* group, double z, int min_samples) {
+  // inference on the tensor cores (bfloat16 weights and activations, FP32 sums)
+  const int tiles = blocks_for(ncells, 16);
+  const int grid = blocks_for(tiles, TC_WARPS) < MLP_GRID ? blocks_for(tiles, TC_WARPS) : MLP_GRID;
+  k_mlp_fwd_tc<<<grid, TC_WARPS * 32, tc_smem_bytes(), st>>>(m.wbf, m.theta, m.X, ncells, m.out);
+  cudaMemsetAsync(m.scal + 2, 0, 3 * sizeof(double), st);
   const int hb = blocks_for(ncells, 256) < 1024 ? blocks_for(ncells, 256) : 1024;
-  k_mlp_hot<<<hb, 256, 0, st>>>(ncells, m.out, m.Y, m.S, m.w, hot, hot_out, m.scal);
+  if (z > 0.0) k_mlp_judge_acc<<<hb, 256, 0, st>>>(ncells, m.out, m.Y, m.w, group, m.jacc);
+  k_mlp_hot<<<hb, 256, 0, st>>>(ncells, m.out, m.Y, m.S, m.w, hot, hot_out, m.scal, group, m.jacc, z, min_samples);
 }
 
 }  // namespace dsmc

@@ -35,28 +35,33 @@ def target_as_fields(target: torch.Tensor) -> torch.Tensor:
 
 
 def dig_iteration(sim: "dsmc.Dsmc", n_s: int, allow_not_converged: bool = True,
-                  hot_model: bool = False, prev_target: torch.Tensor | None = None) -> dict:
+                  hot_model: bool = False, prev_target: torch.Tensor | None = None,
+                  hot_group: torch.Tensor | None = None, judge_z: float = 3.0, judge_min: int = 4) -> dict:
     """N_s DSMC steps, sample, HoT, synthetic solve, particle modification.
 
     With hot_model, the higher-order terms where Kn_GLL >= Kn_ref are the
     handle's HoT network evaluated on the previous synthetic solution (a
-    smooth state; the sampled fields' gradients are dominated by noise), with
-    the sampled HoT as fallback; the first iteration, with no previous
-    solution, uses the sampled HoT."""
+    smooth state; the sampled fields' gradients are dominated by noise),
+    judged against the sampled HoT: a cell takes the network's terms only
+    while the running residuals of its group (hot_group, e.g. the same cell
+    of every replica) stay within judge_z standard errors of zero, and the
+    sampled HoT otherwise; the first iteration, with no previous solution,
+    uses the sampled HoT."""
     sim.dsmc_step(n_s, sample=True)
     f = sim.dsmc_sample(reset=True)
     hot, kn, mask = sim.dsmc_hot(f)
-    judge = None
+    judge, nnet = None, None
     if hot_model and prev_target is not None:
         fs = target_as_fields(prev_target)
         _, kn_s, mask_s = sim.dsmc_hot(fs)
-        hot, judge = sim.mlp_apply(fs, hot, kn_s, mask_s)
+        hot, judge, nnet = sim.mlp_apply_judged(fs, hot, kn_s, mask_s, group=hot_group, z=judge_z,
+                                                min_samples=judge_min)
     out, iters, res = sim.synth_solve(f, hot, allow_not_converged=allow_not_converged, allow_fallback=True)
     sim.dig_correct(out)
     # the HoT mask stays on the device (reducing it here would put a host
     # round trip, and the first use of a framework kernel, into the loop)
     return {"fields": f, "target": out, "synth_iters": iters, "synth_resid": res,
-            "synth_status": sim.last_synth_status, "mask": mask, "judge": judge}
+            "synth_status": sim.last_synth_status, "mask": mask, "judge": judge, "network_cells": nnet}
 
 
 def total_temperature(f: np.ndarray, d_r: float = 2.0) -> np.ndarray:
@@ -80,8 +85,11 @@ class Ensemble:
         self.nx = int(cfg["nx"])
         self.sim = dsmc.Dsmc(workloads.replicas(cfg, replicas, seed0))
         self.hot_model = hot_params is not None
+        self.group = None
         if self.hot_model:
             self.sim.mlp_set_params(hot_params)
+            # the judge pools the same cell of every replica
+            self.group = (torch.arange(self.R * self.nx, dtype=torch.int32) % self.nx).to(self.sim.device)
         self.target = None
         self.steps = 0
         self.wall = 0.0  # GPU wall time spent in the method's calls, seconds
@@ -110,7 +118,8 @@ class Ensemble:
         self.steps += nsteps
 
     def advance_dig(self, n_s: int) -> np.ndarray:
-        r = self._timed(lambda: dig_iteration(self.sim, n_s, hot_model=self.hot_model, prev_target=self.target))
+        r = self._timed(lambda: dig_iteration(self.sim, n_s, hot_model=self.hot_model, prev_target=self.target,
+                                              hot_group=self.group))
         self.target = r["target"]
         self.last = r
         self.steps += n_s

@@ -31,7 +31,8 @@ SYMBOLS = ["dsmc_workspace_size", "dsmc_init", "dsmc_destroy", "dsmc_last_error"
            "dsmc_get_counters", "dsmc_set_counters", "dsmc_get_stats", "dsmc_get_wall_tally",
            "dsmc_get_constants", "synth_solve_noalloc", "dsmc_batch_workspace_size", "dsmc_batch_init",
            "hot_mlp_init", "hot_mlp_set_params", "hot_mlp_get_params", "hot_mlp_grad", "hot_mlp_train",
-           "hot_mlp_apply", "dsmc_get_launch_config", "dsmc_get_flow", "dsmc_get_volumes"]
+           "hot_mlp_apply", "dsmc_get_launch_config", "dsmc_get_flow", "dsmc_get_volumes",
+           "hot_mlp_apply_judged", "hot_mlp_judge_reset"]
 MLP_NPARAM = 9477
 
 
@@ -118,6 +119,8 @@ def load(build_if_missing: bool = True):
         "hot_mlp_grad": ([H, P, P, P, P, P, P], ctypes.c_int),
         "hot_mlp_train": ([H, P, P, P, P, ctypes.c_int, ctypes.c_double, P], ctypes.c_int),
         "hot_mlp_apply": ([H, P, P, P, P, P, P], ctypes.c_int),
+        "hot_mlp_apply_judged": ([H, P, P, P, P, P, D, ctypes.c_int, P, P, P], ctypes.c_int),
+        "hot_mlp_judge_reset": ([H], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -288,6 +291,23 @@ class Dsmc:
                                          _ptr(kngll.contiguous()), _ptr(mask.contiguous()), int(nsteps),
                                          float(lr), ctypes.byref(loss)))
         return loss.value
+
+    def mlp_apply_judged(self, fields, hot, kngll, mask, group=None, z: float = 3.0, min_samples: int = 4):
+        """(HoT [ncells x 12], judge, cells given the network's HoT): the
+        network where its group's running residuals against the DSMC HoT
+        pass the z-standard-error judge, the DSMC HoT elsewhere."""
+        out = torch.empty_like(hot)
+        judge = ctypes.c_double()
+        nnet = ctypes.c_int64()
+        g = group.to(device=self.device, dtype=torch.int32).contiguous() if group is not None else None
+        self._check(load().hot_mlp_apply_judged(self._h, _ptr(fields.contiguous()), _ptr(hot.contiguous()),
+                                                _ptr(kngll.contiguous()), _ptr(mask.contiguous()), _ptr(g),
+                                                float(z), int(min_samples), _ptr(out), ctypes.byref(judge),
+                                                ctypes.byref(nnet)))
+        return out, judge.value, nnet.value
+
+    def mlp_judge_reset(self):
+        self._check(load().hot_mlp_judge_reset(self._h))
 
     def mlp_apply(self, fields, hot, kngll, mask):
         """(HoT for the synthetic equations [ncells x 12], judge)."""

@@ -8,6 +8,10 @@ is taken at the same two-sided 99.73 % level as 3 standard errors of a
 normal variable (t_{0.99865, dof}: 3.64 for 14 degrees of freedom, 3.26
 for 31, 3.0 for many).
 
+Profiles (one value per cell) may pool the two samples' variance and
+average it over a few neighbouring cells (pooled), keeping the degrees of
+freedom of a single cell.
+
 Where many values are compared at once (cells, rings, regions), chance alone
 puts some outside the bound: p = 0.27 % each.  The number allowed outside is
 the smallest k that independent comparisons exceed with probability below
@@ -41,6 +45,23 @@ def allowed_outside(n: int) -> int:
         k += 1
 
 
+def pooled(a: np.ndarray, b: np.ndarray, window: int):
+    """Difference of the replica means of profiles a and b (replicas x
+    cells), its standard error and degrees of freedom, with the two-sample
+    pooled variance of each cell averaged over `window` neighbouring cells
+    (the variance of a cell mean varies smoothly along a profile; a 4-seed
+    variance alone has 3 degrees of freedom and a heavy tail).  The degrees
+    of freedom are those of one cell, na + nb - 2, as if the window added
+    nothing (neighbouring cells are correlated)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    na, nb = a.shape[0], b.shape[0]
+    s2 = ((na - 1) * a.var(0, ddof=1) + (nb - 1) * b.var(0, ddof=1)) / (na + nb - 2)
+    h = window // 2
+    s2 = np.convolve(np.pad(s2, h, mode="edge"), np.ones(window) / window, mode="valid")
+    return a.mean(0) - b.mean(0), np.sqrt(s2 * (1.0 / na + 1.0 / nb)), np.full(s2.shape, na + nb - 2.0)
+
+
 def welch(a: np.ndarray, b: np.ndarray | None = None):
     """Difference of the replica means of a and b (axis 0; b None: a's mean
     against 0), its standard error and the Welch degrees of freedom."""
@@ -54,12 +75,14 @@ def welch(a: np.ndarray, b: np.ndarray | None = None):
     return a.mean(0) - b.mean(0), np.sqrt(va + vb), dof
 
 
-def assert_within_3se(a, b=None, what: str = "", floor: float = 0.0):
+def assert_within_3se(a, b=None, what: str = "", floor: float = 0.0, window: int = 0):
     """Replicas a against replicas b (or against 0): every compared value
     within the 3-SE bound, up to allowed_outside(n) of them, and none beyond
     HARD standard errors.  floor: an absolute SE floor for values whose
-    spread is exactly zero (e.g. a conserved total)."""
-    d, se, dof = welch(a, b)
+    spread is exactly zero (e.g. a conserved total).  window > 1 (profiles
+    against profiles): the pooled variance averaged over that many
+    neighbouring cells (pooled)."""
+    d, se, dof = pooled(a, b, window) if (window > 1 and b is not None) else welch(a, b)
     d, se, dof = np.atleast_1d(d), np.atleast_1d(se) + floor, np.atleast_1d(dof)
     z = np.abs(d) / np.where(se > 0, se, 1e-300)
     thr = np.array([t_bound(v) for v in dof])
@@ -67,5 +90,5 @@ def assert_within_3se(a, b=None, what: str = "", floor: float = 0.0):
     k = allowed_outside(z.size)
     assert out <= k and np.all(z <= np.maximum(HARD, thr)), (
         f"{what}: {out} of {z.size} beyond 3 SE (allowed {k}); largest |diff|/SE "
-        f"{np.sort(z)[-3:]}, diff {d[np.argsort(z)[-3:]]}, SE {se[np.argsort(z)[-3:]]}")
+        f"{np.sort(z)[-3:]} at {np.argsort(z)[-3:]}, diff {d[np.argsort(z)[-3:]]}, SE {se[np.argsort(z)[-3:]]}")
     return z

@@ -103,10 +103,12 @@ def test_mlp_2d_inputs_output_and_gradient_match_oracle():
     g.mlp_set_params(theta)
     out, judge = g.mlp_apply(f_t, hot_t, kn_t, mask_t)
     out = out.cpu().numpy()
-    Yo, _ = mlp.forward(theta.astype(np.float64), X, bf16=True)
+    # tensor-core inference: bfloat16 layer inputs (see test_gpu_mlp for the bounds)
+    Yo, _ = mlp.forward(theta.astype(np.float64), X, bf16=True, bf16_act=True)
     ho = mlp.to_hot(Yo, S, H)
     sc = np.max(np.abs(ho[m][:, [0, 1, 3, 6, 7, 9, 10]]))
-    assert np.max(np.abs(out[m] - ho[m])) <= 1e-4 * sc, np.max(np.abs(out[m] - ho[m]))
+    err = np.abs(out[m] - ho[m])
+    assert np.sqrt(np.mean(err ** 2)) <= 1e-4 * sc and err.max() <= 4e-3 * sc, (np.sqrt(np.mean(err ** 2)), err.max())
     assert np.array_equal(out[~m], H[~m])
     Y = mlp.targets(H, S)
     loss_g, grad_g = g.mlp_grad(f_t, hot_t, kn_t, mask_t)

@@ -60,15 +60,22 @@ def test_apply_matches_oracle_and_judges():
     g.mlp_set_params(theta)
     out, judge = g.mlp_apply(f, hot, kn_g, mask)
     out = out.cpu().numpy()
-    Yo, _ = mlp.forward(theta.astype(np.float64), X, bf16=True)
+    # inference runs on the tensor cores: bfloat16 weights and layer inputs
+    Yo, _ = mlp.forward(theta.astype(np.float64), X, bf16=True, bf16_act=True)
     ho = mlp.to_hot(Yo, S, H)
-    # network cells: the modelled components follow the oracle network
+    # network cells: the modelled components follow the oracle network.  An
+    # activation whose FP32 and FP64 values straddle a bfloat16 rounding
+    # boundary rounds one bfloat16 unit (2^-8 relative) apart, which moves
+    # an output by up to ~1e-3 of its scale; such cells are rare, so the
+    # RMS difference stays at the FP32 level
     scale = np.max(np.abs(ho[m][:, [0, 1, 3, 6, 9]]))
-    assert np.max(np.abs(out[m] - ho[m])) <= 1e-4 * scale, np.max(np.abs(out[m] - ho[m]))
+    err = np.abs(out[m] - ho[m])
+    assert np.sqrt(np.mean(err ** 2)) <= 1e-4 * scale, np.sqrt(np.mean(err ** 2))
+    assert err.max() <= 4e-3 * scale, err.max()
     # every other cell keeps the DSMC HoT exactly
     assert np.array_equal(out[~m], H[~m])
     jo = np.mean((Yo[m] - Y[m]) ** 2)
-    assert abs(judge - jo) <= 1e-4 * jo, (judge, jo)
+    assert abs(judge - jo) <= 1e-3 * jo, (judge, jo)
 
 
 def test_training_follows_oracle_and_reduces_the_loss():
@@ -141,3 +148,83 @@ def test_trained_network_estimates_hot_better_than_a_dsmc_window():
         e_net = np.sqrt(np.mean((N[:, col] - H[:, col]) ** 2))
         e_win = np.sqrt(np.mean((Wn[:, :, col] - H[None, :, col]) ** 2))
         assert e_net < 0.2 * e_win, (col, e_net, e_win)
+
+
+def test_tensor_core_inference_against_fp32_activations():
+    """The bfloat16 rounding of the layer inputs moves the outputs by less
+    than 1 % of their scale against the same network with FP32 inputs."""
+    cfg, g, f, hot, kn_g, mask = _data(seed=4)
+    F, H, K, m, X, S, Y = _oracle_set(cfg, f, hot, kn_g, mask)
+    theta = mlp.init_params(9)
+    Y32, _ = mlp.forward(theta, X, bf16=True)
+    Y16, _ = mlp.forward(theta, X, bf16=True, bf16_act=True)
+    assert np.max(np.abs(Y16 - Y32)) <= 1e-2 * np.max(np.abs(Y32))
+
+
+def _judge_inputs(g, f, hot, kn_g, mask, rng, bias, noise):
+    """DSMC HoT made of the network's own HoT plus a bias and zero-mean noise
+    in the normalised units (components sigma_xx, sigma_xy, sigma_yy, q along
+    grad T), so the residual of each network cell is -(bias + noise)."""
+    net, _ = g.mlp_apply(f, hot, kn_g, mask)
+    h = net.clone()
+    n = h.shape[0]
+    F = f.cpu().numpy()
+    T = (3 * F[:, 4] + 2 * F[:, 5]) / 5
+    p = torch.tensor(F[:, 0] * T, device=h.device)
+    e = torch.tensor(rng.standard_normal((n, 3)), device=h.device) * noise + bias
+    for j, col in enumerate((0, 3, 1)):
+        h[:, col] += e[:, j] * p
+    return h
+
+
+def test_judge_keeps_the_network_only_where_it_agrees_with_dsmc():
+    """The statistical judge (Sec. 3.1's DSMC terms as the judge of the
+    network): with unbiased noisy DSMC terms the network is used once a
+    group holds enough residuals; with a bias of 5 noise units it is
+    rejected; a rejected cell keeps the DSMC HoT and an accepted one the
+    network's."""
+    cfg, g, f, hot, kn_g, mask = _data(seed=5)
+    m = mask.cpu().numpy().astype(bool)
+    g.mlp_set_params(mlp.init_params(4).astype(np.float32))
+    net, _ = g.mlp_apply(f, hot, kn_g, mask)
+    rng = np.random.default_rng(0)
+    counts = []
+    for it in range(8):
+        h = _judge_inputs(g, f, hot, kn_g, mask, rng, 0.0, 0.05)
+        out, _, nnet = g.mlp_apply_judged(f, h, kn_g, mask, z=3.0, min_samples=4)
+        counts.append(nnet)
+        o, hn, nt = out.cpu().numpy(), h.cpu().numpy(), net.cpu().numpy()
+        used = np.all(np.isclose(o, nt, rtol=0, atol=1e-12), axis=1)
+        kept = np.all(o == hn, axis=1)
+        assert np.all(used | kept) and used.sum() == nnet and np.all(kept[~m])
+    assert counts[:3] == [0, 0, 0] and counts[-1] >= 0.7 * m.sum(), counts
+    g.mlp_judge_reset()
+    for it in range(8):
+        h = _judge_inputs(g, f, hot, kn_g, mask, rng, 0.25, 0.05)
+        _, _, nnet = g.mlp_apply_judged(f, h, kn_g, mask, z=3.0, min_samples=4)
+    assert nnet <= 0.05 * m.sum(), nnet
+    # pooled groups: all cells of one group from the first call on
+    g.mlp_judge_reset()
+    grp = torch.zeros(g.ncells, dtype=torch.int32)
+    h = _judge_inputs(g, f, hot, kn_g, mask, rng, 0.0, 0.05)
+    _, _, nnet = g.mlp_apply_judged(f, h, kn_g, mask, group=grp, z=4.0, min_samples=4)
+    assert nnet >= 0.9 * m.sum(), (nnet, m.sum())
+
+
+def test_dig_with_judged_network_reaches_steady_no_later_than_dig():
+    """DIG with the HoT network (trained on DIG's own states, judged cell by
+    cell against the DSMC terms, pooled over the replicas of each cell)
+    reaches 1 % field error on the 1D Couette flow at Kn 0.1 no later than
+    DIG without it (to the 100-step window of the measurement)."""
+    from paper_2501_10965_gb300 import dig
+    cfg = W.couette_1d(kn=0.1, kn_ref=0.01, n_s=50)
+    params, info = dig.train_hot_model_on_dig([cfg], replicas=32, iterations=30)
+    R = 200
+    ref_u, ref_t, _, floor = dig.reference_solution(cfg, R, 6000, 6000, 100, 1, 20)
+    assert floor < 0.005
+    res = {}
+    for method in ("dig", "dig_mlp"):
+        res[method] = dig.measure(cfg, method, R, 100, 3000, ref_u, ref_t, 1, 20, 0.01, hot_params=params)
+    sd, sm = res["dig"]["steady_step"], res["dig_mlp"]["steady_step"]
+    print("steady step DIG", sd, "DIG + network", sm, "noise floor", floor)
+    assert sd is not None and sm is not None and sm <= sd + 100, (sd, sm)

@@ -333,7 +333,7 @@ def test_fp32_steady_fourier_matches_fp64_oracle_within_3se():
     # the total mass is the same in every run: the domain mean density is exact
     assert np.allclose(fg[:, :, 0].mean(1), fo[:, :, 0].mean(1), rtol=1e-9)
     for col, name in ((0, "rho"), (4, "T_t"), (5, "T_r")):
-        assert_within_3se(fg[:, :, col], fo[:, :, col], what=f"{name} profile")
+        assert_within_3se(fg[:, :, col], fo[:, :, col], what=f"{name} profile", window=9)
 
 
 def test_fp32_full_size_workload_properties():

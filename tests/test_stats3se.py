@@ -29,3 +29,18 @@ def test_false_alarm_rate_and_power():
     a[:, 2] += 8.0 / np.sqrt(32)  # 8 x its standard error
     with pytest.raises(AssertionError):
         assert_within_3se(a, what="shifted")
+
+
+def test_pooled_profile_false_alarm_rate():
+    rng = np.random.default_rng(1)
+    x = np.linspace(0, 1, 200)
+    sd = 0.5 + x  # a spread that varies smoothly along the profile
+    fails = 0
+    for _ in range(300):
+        a = rng.standard_normal((8, 200)) * sd
+        b = rng.standard_normal((4, 200)) * sd + 3.0
+        try:
+            assert_within_3se(a, b - 3.0, what="null", window=9)
+        except AssertionError:
+            fails += 1
+    assert fails <= 9  # 1 % expected
