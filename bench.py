@@ -294,6 +294,42 @@ def run_profile(args):
                       "particles": sim.num_particles(), "wall_s": dt, "stats": sim.stats()}), flush=True)
 
 
+def run_adaptive_region(args):
+    """The adaptive treatment of Sec. 3.1 on the flow past the cylinder, on
+    the paper's meshes (Sec. 4.2: Kn 0.1 on 100 x 64 cells, Kn 0.01 on 300 x
+    200; 200 particles per cell; wall at the freestream temperature;
+    Kn_ref 0.01): the equilibrium area fraction (cells with Kn_GLL <
+    Kn_ref, weighted by area) from fields sampled over the last third of
+    each of three domain transits (11 L0 at the freestream speed)."""
+    import torch
+
+    from paper_2501_10965_gb300 import dsmc, workloads as W
+    out = []
+    for kn, nt, nr in ((0.1, 100, 64), (0.01, 300, 200)):
+        cfg = W.cylinder_2d(ntheta=nt, nr=nr, ppc=200, kn=kn, t_wall=1.0, kn_ref=0.01)
+        sim = dsmc.Dsmc(cfg)
+        u_inf = float(cfg["fs_u"][0])
+        transit = int(math.ceil(2.0 * float(cfg["r_out"]) / u_inf / float(cfg["dt"])))
+        vol = sim.volumes()
+        fr = []
+        t0 = time.perf_counter()
+        for _ in range(3):
+            sim.dsmc_step(transit - transit // 3)
+            sim.dsmc_sample(reset=True)
+            sim.dsmc_step(transit // 3, sample=True)
+            f = sim.dsmc_sample(reset=True)
+            _, kngll, mask = sim.dsmc_hot(f)
+            m = mask.cpu().numpy().astype(bool)
+            fr.append(float(vol[~m].sum() / vol.sum()))
+        torch.cuda.synchronize()
+        out.append({"kn": kn, "mesh": f"{nt} x {nr}", "particles": sim.num_particles(), "steps_per_transit": transit,
+                    "equilibrium_fraction_after_transit": fr, "wall_s": time.perf_counter() - t0,
+                    "paper": 0.44 if kn == 0.1 else 0.79})
+        del sim
+        torch.cuda.empty_cache()
+    print(json.dumps({"adaptive_region": out, "kn_ref": 0.01}), flush=True)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -458,8 +494,12 @@ def main():
     ap.add_argument("--tts-replicas", type=int, default=800)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run warm-up + this many steps (for profiler captures)")
+    ap.add_argument("--adaptive-region", action="store_true",
+                    help="only measure the equilibrium area fraction of the cylinder cases")
     args = ap.parse_args()
-    if args.profile_steps > 0:
+    if args.adaptive_region:
+        run_adaptive_region(args)
+    elif args.profile_steps > 0:
         run_profile(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -1042,7 +1042,6 @@ void or_step(or_state *S, int nsteps, int sample) {
 int or_dig_correct(or_state *S, const double *target) {
   const or_config *c = &S->c;
   int nc = S->ncells;
-  if (c->mesh != 0) return OR_ERR_ARG;
   for (int cell = 0; cell < nc; ++cell) {
     const double *t = target + (size_t)cell * 6;
     for (int q = 0; q < 6; ++q)
@@ -1055,7 +1054,8 @@ int or_dig_correct(or_state *S, const double *target) {
   for (int cell = 0; cell < nc; ++cell) {
     or_stream st;
     or_stream_init(&st, c->seed, OR_TAG_DIG_N, 0u, (uint32_t)cell, S->dig_iter);
-    nt[cell] = or_iround(target[(size_t)cell * 6] * S->vcell / S->fnum, or_uni(&st, 0));
+    /* the cell's own volume: the annulus's cells differ */
+    nt[cell] = or_iround(target[(size_t)cell * 6] * S->vol[cell] / S->fnum, or_uni(&st, 0));
     total += nt[cell];
   }
   if (total > S->cap) {
@@ -1111,8 +1111,16 @@ int or_dig_correct(or_state *S, const double *target) {
       for (int64_t q = 0; q < ntg - n; ++q) {
         or_stream sp;
         or_stream_init(&sp, c->seed, OR_TAG_DIG_POS, (uint32_t)q, (uint32_t)cell, S->dig_iter);
-        S->tx[d] = ((double)ix + or_uni(&sp, 0)) * S->dx;
-        S->ty[d] = (c->dim == 2) ? ((double)iy + or_uni(&sp, 1)) * S->dy : 0.0;
+        if (c->mesh == 1) {
+          /* uniform in the annular sector: r^2 and the angle uniform */
+          double r = sqrt(S->r2t[iy] + or_uni(&sp, 0) * (S->r2t[iy + 1] - S->r2t[iy]));
+          double th = 2.0 * M_PI * ((double)ix + or_uni(&sp, 1)) / (double)c->nx;
+          S->tx[d] = r * cos(th);
+          S->ty[d] = r * sin(th);
+        } else {
+          S->tx[d] = ((double)ix + or_uni(&sp, 0)) * S->dx;
+          S->ty[d] = (c->dim == 2) ? ((double)iy + or_uni(&sp, 1)) * S->dy : 0.0;
+        }
         if (n > 0) {
           /* replicate a randomly chosen pre-existing particle */
           or_stream st;

@@ -114,6 +114,47 @@ def grad_cells(f: np.ndarray, nx: int, ny: int, dx: float, dy: float, dim: int):
     return gx.reshape(-1), gy.reshape(-1)
 
 
+def ring_edges(cfg: dict) -> np.ndarray:
+    """Ring radii R_0 = r_in < ... < R_ny = r_out of the annulus around a
+    cylinder: widths growing by the factor `stretch` from ring to ring
+    (uniform for stretch 1)."""
+    nr, q = int(cfg["ny"]), float(cfg.get("stretch", 1.0))
+    r_in, r_out = float(cfg["r_in"]), float(cfg["r_out"])
+    j = np.arange(nr + 1, dtype=np.float64)
+    f = j / nr if q == 1.0 else (q ** j - 1.0) / (q ** nr - 1.0)
+    r = r_in + (r_out - r_in) * f
+    r[0], r[-1] = r_in, r_out
+    return r
+
+
+def grad_annulus(f: np.ndarray, nt: int, nr: int, redges: np.ndarray):
+    """Cartesian gradient (d/dx, d/dy) of a cell field on the annulus (cell j
+    nt + k: ring j, sector k), from its polar derivatives at the cell centre
+    (mid radius r_j, angle theta_k = 2 pi (k + 1/2) / nt):
+      d/dr: the three-point formula on the stretched rings (exact for
+            quadratics in r), a one-sided first difference in the first
+            and the last ring;
+      (1/r) d/dtheta: (f_{k+1} - f_{k-1}) / (2 r sin(dtheta)), periodic in
+            k (second order, and exact for fields linear in x and y);
+      d/dx = cos(theta) d/dr - sin(theta) (1/r) d/dtheta,
+      d/dy = sin(theta) d/dr + cos(theta) (1/r) d/dtheta."""
+    g = f.reshape(nr, nt)
+    rc = 0.5 * (redges[:-1] + redges[1:])
+    dr = np.zeros_like(g)
+    if nr >= 2:
+        hm = rc[1:-1] - rc[:-2]
+        hp = rc[2:] - rc[1:-1]
+        dr[1:-1, :] = ((hm * hm)[:, None] * g[2:, :] - (hp * hp)[:, None] * g[:-2, :]
+                       + (hp * hp - hm * hm)[:, None] * g[1:-1, :]) / (hp * hm * (hp + hm))[:, None]
+        dr[0, :] = (g[1, :] - g[0, :]) / (rc[1] - rc[0])
+        dr[-1, :] = (g[-1, :] - g[-2, :]) / (rc[-1] - rc[-2])
+    dth = 2.0 * math.pi / nt
+    dt = (np.roll(g, -1, axis=1) - np.roll(g, 1, axis=1)) / (2.0 * rc[:, None] * math.sin(dth))
+    th = 2.0 * math.pi * (np.arange(nt) + 0.5) / nt
+    c, s = np.cos(th)[None, :], np.sin(th)[None, :]
+    return (c * dr - s * dt).reshape(-1), (s * dr + c * dt).reshape(-1)
+
+
 def hot_kngll(fields: np.ndarray, cfg: dict):
     """Eq. (ns_constitutive), Eq. (hot_constitutive) and Eq. (Kn_GLL).
 
@@ -127,6 +168,14 @@ def hot_kngll(fields: np.ndarray, cfg: dict):
     ny = int(cfg.get("ny", 1)) if dim == 2 else 1
     dx = float(cfg["lx"]) / nx
     dy = float(cfg.get("ly", 1.0)) / ny if dim == 2 else 1.0
+    if cfg.get("mesh", "box") == "annulus":
+        re = ring_edges(cfg)
+
+        def grad(f):
+            return grad_annulus(f, nx, ny, re)
+    else:
+        def grad(f):
+            return grad_cells(f, nx, ny, dx, dy, dim)
     d_r, omega = float(cfg["d_r"]), float(cfg["omega"])
     mu_ref = mu_ref_of(float(cfg["kn"]))
     kt_c, kr_c = kappa_coefficients(cfg["a_matrix"], d_r)
@@ -138,7 +187,7 @@ def hot_kngll(fields: np.ndarray, cfg: dict):
     mu = mu_ref * T ** omega
     grads = {}
     for name, f in (("ux", u[:, 0]), ("uy", u[:, 1]), ("uz", u[:, 2]), ("tt", tt), ("tr", tr), ("rho", rho)):
-        grads[name] = grad_cells(f, nx, ny, dx, dy, dim)
+        grads[name] = grad(f)
     (dux_dx, dux_dy), (duy_dx, duy_dy), (duz_dx, duz_dy) = grads["ux"], grads["uy"], grads["uz"]
     div_u = dux_dx + duy_dy
     # sigma_NSF = -mu (grad u + grad u^T - 2/3 div u I), d/dz = 0
@@ -162,7 +211,7 @@ def hot_kngll(fields: np.ndarray, cfg: dict):
     # Kn_GLL
     gamma = (5.0 + d_r) / (3.0 + d_r)
     speed = np.sqrt((u * u).sum(axis=1))
-    gs = grad_cells(speed, nx, ny, dx, dy, dim)
+    gs = grad(speed)
     lam = mu / (rho * T) * np.sqrt(math.pi * T / 2.0)
     g_rho = np.hypot(*grads["rho"]) / rho
     g_u = np.hypot(*gs) / np.maximum(speed, np.sqrt(gamma * T))

@@ -28,7 +28,7 @@ import math
 
 import numpy as np
 
-from .fields import F_RHO, F_TR, F_TT, F_U, grad_cells, mu_ref_of
+from .fields import F_RHO, F_TR, F_TT, F_U, grad_annulus, grad_cells, mu_ref_of, ring_edges
 
 SIZES = (12, 64, 64, 64, 5)
 NPARAM = sum(SIZES[k] * SIZES[k + 1] + SIZES[k + 1] for k in range(4))
@@ -75,8 +75,18 @@ def _geometry(cfg):
 
 
 def features(fields: np.ndarray, kngll: np.ndarray, cfg: dict):
-    """Returns (X [n x 12], scale [n x 4]) with scale = (p, p sqrt(T), e_x, e_y)."""
+    """Returns (X [n x 12], scale [n x 4]) with scale = (p, p sqrt(T), e_x, e_y).
+    Gradients as for the HoT: the box's cell-centred differences, or the
+    annulus's polar ones (fields.grad_annulus)."""
     dim, nx, ny, dx, dy = _geometry(cfg)
+    if cfg.get("mesh", "box") == "annulus":
+        re = ring_edges(cfg)
+
+        def grad(f):
+            return grad_annulus(f, nx, ny, re)
+    else:
+        def grad(f):
+            return grad_cells(f, nx, ny, dx, dy, dim)
     d_r, omega = float(cfg["d_r"]), float(cfg["omega"])
     mu_ref = mu_ref_of(float(cfg["kn"]))
     rho = fields[:, F_RHO]
@@ -87,10 +97,10 @@ def features(fields: np.ndarray, kngll: np.ndarray, cfg: dict):
     sq = np.sqrt(T)
     cols = []
     for f, norm in ((rho, rho), (fields[:, F_U], sq), (fields[:, F_U + 1], sq), (tt, T), (tr, T)):
-        gx, gy = grad_cells(f, nx, ny, dx, dy, dim)
+        gx, gy = grad(f)
         cols += [lam * gx / norm, lam * gy / norm]
     X = np.stack(cols + [kngll, tr / tt], axis=1)
-    gTx, gTy = grad_cells(T, nx, ny, dx, dy, dim)
+    gTx, gTy = grad(T)
     gn = np.sqrt(gTx * gTx + gTy * gTy)
     ex = np.where(gn > 0, gTx / np.where(gn > 0, gn, 1.0), 1.0)
     ey = np.where(gn > 0, gTy / np.where(gn > 0, gn, 1.0), 0.0)

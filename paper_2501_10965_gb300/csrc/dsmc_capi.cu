@@ -440,6 +440,7 @@ void fill_params(const dsmc_config* c, Params<T>& p, CellParams& cp) {
   cp.k1 = p.k1;
   cp.mesh = p.mesh;
   cp.vol = nullptr;
+  cp.r2t = nullptr;
 }
 
 // annulus: upload the tables (FP64 and FP32) and point the parameters at them
@@ -471,6 +472,7 @@ int set_ann_tables(dsmc_handle* h) {
   h->pf.fnrm = h->ann_fn_f;
   h->pf.vol = h->ann_vol_f;
   h->cp.vol = h->ann_vol_d;
+  h->cp.r2t = h->ann_r2t_d;
   return DSMC_OK;
 }
 
@@ -819,7 +821,6 @@ int dsmc_sample(dsmc_handle* h, double* dev_fields, int reset) {
 
 int dsmc_hot(dsmc_handle* h, const double* dev_fields, double* dev_hot, double* dev_kngll, uint8_t* dev_mask) {
   if (!h || !dev_fields || !dev_hot) return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "dsmc_hot: the gradients need the box mesh");
   launch_hot(h->d_cp, h->d_cell_case, h->d_cell0, h->ncells, dev_fields, dev_hot, dev_kngll, dev_mask, h->stream);
   return check_cuda(h, "dsmc_hot");
 }
@@ -890,7 +891,6 @@ int synth_solve(dsmc_handle* h, const double* dev_fields, const double* dev_hot,
 
 int dig_correct(dsmc_handle* h, const double* dev_target) {
   if (!h || !dev_target) return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "dig_correct: not on the annulus");
   int32_t fl[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (h->det) Ops<double>::dig_counts(h->sd, h->ncells, h->lay, dev_target, h->dig_iter, 1, h->stream);
   else Ops<float>::dig_counts(h->sf, h->ncells, h->lay, dev_target, h->dig_iter, 0, h->stream);
@@ -1092,7 +1092,6 @@ int hot_mlp_get_params(dsmc_handle* h, float* host_params) {
 int hot_mlp_grad(dsmc_handle* h, const double* dev_fields, const double* dev_hot, const double* dev_kngll,
                  const uint8_t* dev_mask, float* host_grad, double* host_loss) {
   if (!h || !dev_fields || !dev_hot || !dev_kngll || !dev_mask) return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "HoT network: the features need the box mesh");
   mlp_data(h, dev_fields, dev_hot, dev_kngll, dev_mask);
   int n = 0;
   int r = mlp_count(h, &n);
@@ -1113,7 +1112,6 @@ int hot_mlp_train(dsmc_handle* h, const double* dev_fields, const double* dev_ho
                   const uint8_t* dev_mask, int nsteps, double lr, double* host_loss) {
   if (!h || !dev_fields || !dev_hot || !dev_kngll || !dev_mask || nsteps < 0 || !(lr > 0.0))
     return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "HoT network: the features need the box mesh");
   mlp_data(h, dev_fields, dev_hot, dev_kngll, dev_mask);
   int n = 0;
   int r = mlp_count(h, &n);
@@ -1136,7 +1134,6 @@ int hot_mlp_apply(dsmc_handle* h, const double* dev_fields, const double* dev_ho
                   const uint8_t* dev_mask, double* dev_hot_out, double* host_judge) {
   if (!h || !dev_fields || !dev_hot || !dev_kngll || !dev_mask || !dev_hot_out)
     return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "HoT network: the features need the box mesh");
   mlp_data(h, dev_fields, dev_hot, dev_kngll, dev_mask);
   mlp_apply(h->mlp, h->ncells, dev_hot, dev_hot_out, h->stream);
   double j[2] = {0.0, 0.0};
@@ -1158,7 +1155,6 @@ int hot_mlp_apply_judged(dsmc_handle* h, const double* dev_fields, const double*
                          double* dev_hot_out, double* host_judge, int64_t* host_nnet) {
   if (!h || !dev_fields || !dev_hot || !dev_kngll || !dev_mask || !dev_hot_out || !(z > 0.0) || min_samples < 2)
     return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "HoT network: the features need the box mesh");
   mlp_data(h, dev_fields, dev_hot, dev_kngll, dev_mask);
   mlp_apply(h->mlp, h->ncells, dev_hot, dev_hot_out, h->stream, dev_group, z, min_samples);
   double j[3] = {0.0, 0.0, 0.0};

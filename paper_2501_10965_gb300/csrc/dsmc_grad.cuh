@@ -6,10 +6,48 @@
 
 namespace dsmc {
 
+// Annulus (nx sectors x ny rings, cell j nx + k): the Cartesian gradient at
+// the cell centre (mid radius r_j, angle theta_k = 2 pi (k + 1/2) / nx) from
+// the polar derivatives: d/dr by the three-point formula on the stretched
+// rings (one-sided first difference in the first and last ring), (1/r)
+// d/dtheta = (f_{k+1} - f_{k-1}) / (2 r_j sin(dtheta)) around the ring
+// (exact for fields linear in x and y); then d/dx = cos d/dr - sin (1/r)
+// d/dtheta, d/dy = sin d/dr + cos (1/r) d/dtheta.
+template <typename F>
+__device__ __forceinline__ void grad_ann(const CellParams& cp, int c, int lc, F f, double* gx, double* gy) {
+  const int nt = cp.nx, nr = cp.ny;
+  const int k = lc % nt, j = lc / nt;
+  auto rmid = [&](int q) { return 0.5 * (sqrt(cp.r2t[q]) + sqrt(cp.r2t[q + 1])); };
+  const double r = rmid(j);
+  double dr = 0.0;
+  if (nr >= 2) {
+    if (j == 0) {
+      dr = (f(c + nt) - f(c)) / (rmid(1) - r);
+    } else if (j == nr - 1) {
+      dr = (f(c) - f(c - nt)) / (r - rmid(j - 1));
+    } else {
+      const double hm = r - rmid(j - 1), hp = rmid(j + 1) - r;
+      dr = (hm * hm * f(c + nt) - hp * hp * f(c - nt) + (hp * hp - hm * hm) * f(c)) / (hp * hm * (hp + hm));
+    }
+  }
+  const int kp = (k == nt - 1) ? c - (nt - 1) : c + 1, km = (k == 0) ? c + (nt - 1) : c - 1;
+  const double dth = 2.0 * PI_D / (double)nt;
+  const double dt = (f(kp) - f(km)) / (2.0 * r * sin(dth));
+  const double th = 2.0 * PI_D * ((double)k + 0.5) / (double)nt;
+  const double ct = cos(th), st = sin(th);
+  *gx = ct * dr - st * dt;
+  *gy = st * dr + ct * dt;
+}
+
 // Cell-centred gradient of field value f(cell): central inside, one-sided
-// first difference in the first/last cell of a line, 0 with a single cell.
+// first difference in the first/last cell of a line, 0 with a single cell;
+// on the annulus, grad_ann.
 template <typename F>
 __device__ __forceinline__ void grad2(const CellParams& cp, int c, int lc, F f, double* gx, double* gy) {
+  if (cp.mesh == 1) {
+    grad_ann(cp, c, lc, f, gx, gy);
+    return;
+  }
   const int ix = lc % cp.nx, iy = lc / cp.nx;
   *gx = 0.0;
   *gy = 0.0;

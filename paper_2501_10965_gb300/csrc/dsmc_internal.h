@@ -35,6 +35,7 @@ struct CellParams {
   uint32_t k0, k1;
   int mesh;            // 0 Cartesian box, 1 annulus (single case)
   const double* vol;   // annulus: cell volumes (null on the box: vcell)
+  const double* r2t;   // annulus: ny + 1 squared ring radii (nx sectors x ny rings)
 };
 
 // Per-case tables of a handle (device memory).  A single simulation is one

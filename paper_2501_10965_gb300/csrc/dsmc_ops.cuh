@@ -1299,7 +1299,8 @@ static __global__ void k_dig_counts(const CellParams* __restrict__ cps, const in
         caps[c] = 0;
       } else {
         Stream<double> st(TAG_DIG_N, 0u, (uint32_t)lcell, iter, cp.k0, cp.k1);
-        const double xm = t[0] * cp.vcell / cp.fnum;
+        const double vc = cp.vol ? cp.vol[lcell] : cp.vcell;  // the annulus's cells differ
+        const double xm = t[0] * vc / cp.fnum;
         long long v = iround(xm, st.u(0));
         if (v > 0x3fffffffLL) {
           atomicOr(flags, 2);
@@ -1308,7 +1309,7 @@ static __global__ void k_dig_counts(const CellParams* __restrict__ cps, const in
         nv = (int32_t)v;
         nt[c] = nv;
         // FP32 bins: room for slack x the larger of the new and the nominal count
-        const int32_t nominal = (int32_t)(cp.vcell / cp.fnum + 0.5);
+        const int32_t nominal = (int32_t)(vc / cp.fnum + 0.5);
         caps[c] = det ? nv : bin_cap_of(max(nv, nominal), slack);
       }
     }
@@ -1463,8 +1464,16 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
     for (int q = lane; q < ntg - n; q += 32) {
       Stream<double> sp(TAG_DIG_POS, (uint32_t)q, (uint32_t)lcell, iter, cp.k0, cp.k1);
       const int w = d0 + n + q;
-      out.x[w] = (T)(((double)ix + sp.u(0)) * cp.dx);
-      out.y[w] = (T)((cp.dim == 2) ? ((double)iy + sp.u(1)) * cp.dy : 0.0);
+      if (cp.mesh == 1) {
+        // annulus: uniform in the sector (r^2 and the angle uniform)
+        const double r = sqrt(cp.r2t[iy] + sp.u(0) * (cp.r2t[iy + 1] - cp.r2t[iy]));
+        const double th = 2.0 * PI_D * ((double)ix + sp.u(1)) / (double)cp.nx;
+        out.x[w] = (T)(r * cos(th));
+        out.y[w] = (T)(r * sin(th));
+      } else {
+        out.x[w] = (T)(((double)ix + sp.u(0)) * cp.dx);
+        out.y[w] = (T)((cp.dim == 2) ? ((double)iy + sp.u(1)) * cp.dy : 0.0);
+      }
       if (n > 0) {
         Stream<double> ss(TAG_DIG_SEL, (uint32_t)q, (uint32_t)lcell, iter, cp.k0, cp.k1);
         int src = (int)(ss.u(0) * (double)n);

@@ -245,3 +245,111 @@ def test_cylinder_fp64_entry_beyond_capacity_is_reported():
         for _ in range(100):
             g.dsmc_step(1)
     assert e.value.code == -2
+
+
+# ---------------------------------------------------------------------------
+# Higher-order terms, Kn_GLL and the particle modification on the annulus
+# ---------------------------------------------------------------------------
+
+def _oracle_annulus_fields(cfg, steps=60, sample=120):
+    from oracle.fields import fields_from_sums
+    o = oracle.OracleSim(cfg)
+    o.step(steps)
+    o.reset_accumulators()
+    o.step(sample, sample=True)
+    c = o.constants()
+    return fields_from_sums(o.accumulators(), o.nsamples, c["fnum"], o.volumes(), 2.0)
+
+
+def test_hot_kngll_on_annulus_matches_oracle():
+    """Eqs. (ns_constitutive), (hot_constitutive) and (Kn_GLL) on the polar
+    mesh (polar derivatives at the cell centres turned Cartesian): the GPU's
+    HoT to relative 1e-11 of each component's scale, Kn_GLL to 1e-12 and the
+    mask exactly, from the oracle's sampled fields of a Mach 2 flow."""
+    from oracle.fields import hot_kngll
+    cfg = _small(ntheta=24, nr=8, ppc=30, kn=0.1, mach=2.0, t_wall=2.0, dr1=0.1)
+    F = _oracle_annulus_fields(cfg)
+    _, kn_o, _ = hot_kngll(F, dict(cfg, kn_ref=0.0))
+    cfg = dict(cfg, kn_ref=float(np.median(kn_o)) * 1.0000001)
+    hot_o, kn_o, mask_o = hot_kngll(F, cfg)
+    g = _gpu(cfg)
+    hot_g, kn_g, mask_g = [t.cpu().numpy() for t in g.dsmc_hot(torch.tensor(F, device="cuda"))]
+    assert 0 < mask_o.sum() < len(mask_o)
+    assert np.allclose(kn_g, kn_o, rtol=1e-12, atol=0.0), np.max(np.abs(kn_g / kn_o - 1))
+    assert np.array_equal(mask_g.astype(bool), mask_o)
+    scale = np.maximum(np.abs(hot_o).max(0), 1e-300)
+    assert (np.abs(hot_g - hot_o) / scale).max() <= 1e-11
+
+
+def _annulus_targets(nc, rng):
+    t = np.zeros((nc, 6))
+    t[:, 0] = 0.6 + 0.8 * rng.random(nc)
+    t[:, 1:4] = 0.3 * rng.standard_normal((nc, 3))
+    t[:, 4] = 0.8 + 0.5 * rng.random(nc)
+    t[:, 5] = 0.7 + 0.5 * rng.random(nc)
+    t[5, 0] = 0.0  # empty a cell; the second modification refills it
+    return t
+
+
+def test_dig_correct_on_annulus_matches_oracle_fp64():
+    """Sec. 3.2 on the annulus (per-cell volumes in step i, new particles
+    uniform in their annular sector): particle states equal the oracle's
+    over two modifications with steps in between (relative 1e-12)."""
+    cfg = _small(ntheta=24, nr=8, ppc=30, kn=0.1, mach=2.0, t_wall=2.0, dr1=0.1)
+    g, o = _gpu(cfg), oracle.OracleSim(cfg)
+    g.dsmc_step(3)
+    o.step(3)
+    t = _annulus_targets(24 * 8, np.random.default_rng(3))
+    for rep in range(2):
+        g.dig_correct(torch.tensor(t, device="cuda"))
+        assert o.dig_correct(t) == 0
+        _compare_states(_np(g.get_particles()), o.particles(), what=f"dig {rep}")
+        g.dsmc_step(2)
+        o.step(2)
+        _compare_states(_np(g.get_particles()), o.particles(), what=f"dig {rep} + 2 steps")
+        t[5, 0] = 1.2
+
+
+def test_dig_correct_on_annulus_fp32_follows_the_oracle():
+    """FP32 layout on the annulus, given the GPU's own particles in its own
+    order: the oracle's modification gives the same counts and positions,
+    and velocities and I_r to relative 1e-6 (FP64 factors, one FP32
+    rounding)."""
+    cfg = _small(ntheta=24, nr=8, ppc=30, kn=0.1, mach=2.0, t_wall=2.0, dr1=0.1, precision="fp32")
+    g = _gpu(cfg)
+    g.dsmc_step(4)
+    t = _annulus_targets(24 * 8, np.random.default_rng(4))
+    p = _np(g.get_particles())
+    o = oracle.OracleSim(dict(cfg, precision="fp64"))
+    o.set_particles({k: p[k] for k in KEYS})
+    assert np.array_equal(o.particles()["cell"], p["cell"])
+    o.set_step(0, dig_iter=0)
+    g.dig_correct(torch.tensor(t, device="cuda"))
+    assert o.dig_correct(t) == 0
+    a, b = _np(g.get_particles()), o.particles()
+    assert np.array_equal(a["cell"], b["cell"])
+    for k in KEYS:
+        tol = 1e-6
+        err = np.abs(a[k] - b[k]) / np.maximum(np.abs(b[k]), 1.0)
+        assert err.max() <= tol, (k, err.max())
+
+
+def test_adaptive_region_fraction_kn01():
+    """The adaptive treatment of Sec. 3.1 on the flow past the cylinder at
+    Kn 0.1 (the paper's 100 x 64 mesh, 200 particles per cell, wall at the
+    freestream temperature, Kn_ref 0.01): after the flow has settled, the
+    equilibrium area (Kn_GLL < Kn_ref) is a fraction of the domain between
+    the shock layer and wake (non-equilibrium) and the upstream freestream
+    (equilibrium); the paper quotes about 44 % at the start of its
+    transition state.  Printed; bounds are loose."""
+    cfg = W.cylinder_2d(ntheta=100, nr=64, ppc=200, kn=0.1, t_wall=1.0, kn_ref=0.01)
+    g = _gpu(cfg)
+    g.dsmc_step(12000)
+    g.dsmc_sample(reset=True)
+    g.dsmc_step(4000, sample=True)
+    f = g.dsmc_sample(reset=True)
+    _, kn, mask = g.dsmc_hot(f)
+    vol = g.volumes()
+    eq = vol[~mask.cpu().numpy().astype(bool)].sum() / vol.sum()
+    print("Kn 0.1 cylinder: equilibrium area fraction", eq)
+    assert 0.05 < eq < 0.95

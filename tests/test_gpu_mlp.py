@@ -219,9 +219,9 @@ def test_dig_with_judged_network_reaches_steady_no_later_than_dig():
     from paper_2501_10965_gb300 import dig
     cfg = W.couette_1d(kn=0.1, kn_ref=0.01, n_s=50)
     params, info = dig.train_hot_model_on_dig([cfg], replicas=32, iterations=30)
-    R = 200
+    R = 400
     ref_u, ref_t, _, floor = dig.reference_solution(cfg, R, 6000, 6000, 100, 1, 20)
-    assert floor < 0.005
+    assert floor < 0.006  # 1 % is resolvable
     res = {}
     for method in ("dig", "dig_mlp"):
         res[method] = dig.measure(cfg, method, R, 100, 3000, ref_u, ref_t, 1, 20, 0.01, hot_params=params)

@@ -202,3 +202,126 @@ def test_specular_cylinder_and_empty_freestream():
     assert abs(w[4]) < 1e-11 * w[0], w
     # momentum delivered is along the normals: the z component never changes
     assert w[3] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Higher-order terms, Kn_GLL and the particle modification on the annulus
+# (Sec. 3.1, 3.2 on the cylinder case of Sec. 4.2)
+# ---------------------------------------------------------------------------
+
+def _centres(cfg):
+    nt, nr = int(cfg["nx"]), int(cfg["ny"])
+    R = _ring_radii(cfg)
+    rc = 0.5 * (R[:-1] + R[1:])
+    th = 2 * np.pi * (np.arange(nt) + 0.5) / nt
+    r2, t2 = np.meshgrid(rc, th, indexing="ij")
+    return (r2 * np.cos(t2)).ravel(), (r2 * np.sin(t2)).ravel(), r2.ravel(), t2.ravel()
+
+
+def test_annulus_gradient_exact_for_linear_and_radial_quadratic_fields():
+    from oracle.fields import grad_annulus, ring_edges
+    cfg = _cfg(dr1=0.05, ntheta=30, nr=9)
+    nt, nr = int(cfg["nx"]), int(cfg["ny"])
+    R = ring_edges(cfg)
+    np.testing.assert_allclose(R, _ring_radii(cfg), rtol=1e-14)
+    x, y, r, th = _centres(cfg)
+    gx, gy = grad_annulus(0.7 + 1.3 * x - 0.4 * y, nt, nr, R)
+    assert np.allclose(gx, 1.3, atol=1e-12) and np.allclose(gy, -0.4, atol=1e-12)
+    # f = r^2 - 3 r: d/dr = 2 r - 3 exact inside (three-point formula on
+    # stretched rings), first order in the first and last ring
+    gx, gy = grad_annulus(r * r - 3 * r, nt, nr, R)
+    inner = slice(nt, (nr - 1) * nt)
+    d = 2 * r - 3
+    assert np.allclose(gx[inner], (d * np.cos(th))[inner], atol=1e-11)
+    assert np.allclose(gy[inner], (d * np.sin(th))[inner], atol=1e-11)
+
+
+def test_annulus_hot_and_kngll_of_linear_fields():
+    """Linear u and T_t, T_r in x, y: the NSF stress and heat fluxes from the
+    analytic gradients; fields carrying those NSF values have zero HoT, and
+    an added stress shows up as HoT unchanged.  Kn_GLL from the analytic
+    gradients too."""
+    from oracle.fields import hot_kngll, kappa_coefficients, mu_ref_of
+    cfg = dict(_cfg(dr1=0.05, ntheta=30, nr=9), kn_ref=0.0)
+    x, y, r, th = _centres(cfg)
+    n = len(x)
+    a = np.array([[0.05, -0.02], [0.03, 0.04]])  # du_i/dx_j
+    F = np.zeros((n, 18))
+    F[:, 0] = 1.0 + 0.1 * x - 0.05 * y
+    F[:, 1] = 0.1 + a[0, 0] * x + a[0, 1] * y
+    F[:, 2] = -0.2 + a[1, 0] * x + a[1, 1] * y
+    F[:, 4] = 1.0 + 0.03 * x + 0.02 * y
+    F[:, 5] = 0.9 - 0.01 * x + 0.03 * y
+    T = (3 * F[:, 4] + 2 * F[:, 5]) / 5
+    mu = mu_ref_of(cfg["kn"]) * T ** cfg["omega"]
+    div = a[0, 0] + a[1, 1]
+    sig = np.zeros((n, 6))
+    sig[:, 0] = -mu * (2 * a[0, 0] - 2 / 3 * div)
+    sig[:, 1] = -mu * (2 * a[1, 1] - 2 / 3 * div)
+    sig[:, 2] = -mu * (-2 / 3 * div)
+    sig[:, 3] = -mu * (a[0, 1] + a[1, 0])
+    kt, kr = kappa_coefficients(cfg["a_matrix"], 2.0)
+    F[:, 6:12] = sig
+    F[:, 12], F[:, 13] = -kt * mu * 0.03, -kt * mu * 0.02
+    F[:, 15], F[:, 16] = -kr * mu * (-0.01), -kr * mu * 0.03
+    hot, kn, mask = hot_kngll(F, cfg)
+    assert mask.all() and np.max(np.abs(hot)) < 1e-12
+    F2 = F.copy()
+    F2[:, 9] += 0.01  # an extra shear stress
+    hot2, _, _ = hot_kngll(F2, cfg)
+    assert np.allclose(hot2[:, 3], 0.01, atol=1e-12)
+    # Kn_GLL with the analytic gradients: here the density term is the
+    # largest of the four in every cell (checked), and it is exact for a
+    # linear density
+    lam = mu / (F[:, 0] * T) * np.sqrt(np.pi * T / 2)
+    g_rho = np.hypot(0.1, -0.05) / F[:, 0]
+    sp = np.hypot(F[:, 1], F[:, 2])
+    gsp = np.hypot((F[:, 1] * a[0, 0] + F[:, 2] * a[1, 0]) / sp, (F[:, 1] * a[0, 1] + F[:, 2] * a[1, 1]) / sp)
+    others = np.stack([gsp / np.maximum(sp, np.sqrt(1.4 * T)), np.hypot(0.03, 0.02) / F[:, 4],
+                       np.hypot(-0.01, 0.03) / F[:, 5]])
+    assert np.all(g_rho > 1.2 * others.max(0))
+    assert np.allclose(kn, lam * g_rho, rtol=1e-12, atol=0)
+
+
+def test_annulus_dig_correct_matches_targets_with_cell_volumes():
+    """Sec. 3.2 on the annulus: every cell holds Iround(rho V_cell / F)
+    particles (its own volume), their instantaneous u, T_t, T_r equal the
+    target, and new particles lie inside their sector."""
+    cfg = _cfg(dr1=0.05, ntheta=24, nr=8, ppc=30)
+    sim = oracle.OracleSim(cfg)
+    sim.step(3)
+    nc = 24 * 8
+    rng = np.random.default_rng(7)
+    t = np.zeros((nc, 6))
+    t[:, 0] = 0.6 + 0.8 * rng.random(nc)
+    t[:, 1:4] = 0.3 * rng.standard_normal((nc, 3))
+    t[:, 4] = 0.8 + 0.5 * rng.random(nc)
+    t[:, 5] = 0.7 + 0.5 * rng.random(nc)
+    t[5, 0] = 0.0
+    assert sim.dig_correct(t) == 0
+    t[5, 0] = 1.5  # refill the emptied cell from its target Maxwellian
+    assert sim.dig_correct(t) == 0
+    p = sim.particles()
+    v = sim.volumes()
+    fnum = sim.constants()["fnum"]
+    cnt = np.bincount(p["cell"], minlength=nc)
+    xm = t[:, 0] * v / fnum
+    assert np.all((cnt == np.floor(xm)) | (cnt == np.floor(xm) + 1))
+    full = cnt >= 2
+    for j, k in enumerate(("vx", "vy", "vz")):
+        m = np.bincount(p["cell"], p[k], nc)[full] / cnt[full]
+        assert np.allclose(m, t[full, 1 + j], atol=1e-13)
+    c2 = sum(np.bincount(p["cell"], (p[k] - t[p["cell"], 1 + j]) ** 2, nc) for j, k in enumerate(("vx", "vy", "vz")))
+    # a cell refilled by copies of one particle has T_t* = 0: only its mean
+    # is shifted (a = 1)
+    spread = full & (c2 > 1e-20)
+    assert spread.sum() > 0.9 * full.sum()
+    assert np.allclose(c2[spread] / (3 * cnt[spread]), t[spread, 4], rtol=1e-12)
+    assert np.allclose(np.bincount(p["cell"], p["ir"], nc)[full] / cnt[full], t[full, 5], rtol=1e-12)
+    R = _ring_radii(cfg)
+    r = np.hypot(p["x"], p["y"])
+    th = np.mod(np.arctan2(p["y"], p["x"]), 2 * np.pi)
+    ring, sec = p["cell"] // 24, p["cell"] % 24
+    assert np.all((r >= R[ring] - 1e-12) & (r <= R[ring + 1] + 1e-12))
+    ks = th / (2 * np.pi / 24)
+    assert np.all((ks >= sec - 1e-9) & (ks <= sec + 1 + 1e-9) | (ks > 23.999999) & (sec == 0))
