@@ -392,19 +392,21 @@ int hot_mlp_apply(dsmc_handle *h, const double *dev_fields, const double *dev_ho
 
 /* hot_mlp_apply with the DSMC terms as the judge of the network, cell by
  * cell: each call adds, for every network cell (mask = 1), the residual r =
- * network - DSMC of its 5 normalised outputs, and r^2, to the running sums
- * of its group (dev_group: ncells int32 ids in [0, ncells), or NULL for one
- * group per cell; e.g. the same cell of every replica of a batch), and a
- * network cell takes the network's HoT only if its group holds at least
- * min_samples (>= 2) residuals whose mean is within z (> 0) standard errors
- * of zero for every output; otherwise it keeps the DSMC HoT.  The sums
+ * network - DSMC of its 5 normalised outputs, r^2 and the DSMC terms Y to
+ * the running sums of its group (dev_group: ncells int32 ids in [0,
+ * ncells), or NULL for one group per cell; e.g. the same cell of every
+ * replica of a batch), and a network cell takes the network's HoT only if
+ * its group holds at least min_samples (>= 2) residuals and, for every
+ * output, |mean r| + z SE(r) <= rel |mean Y| (z > 0, rel > 0: the network's
+ * bias is bounded, with z standard errors of confidence, by the fraction
+ * rel of the DSMC terms); otherwise it keeps the DSMC HoT.  The sums
  * persist across calls (a DIG run's iterations) until hot_mlp_judge_reset
  * or a change of the parameters.  The inference runs on the tensor cores
  * (bfloat16 weights and inputs of every layer, FP32 sums).  host_nnet (may
  * be NULL) receives the number of cells given the network's HoT; host_judge
  * as in hot_mlp_apply. */
 int hot_mlp_apply_judged(dsmc_handle *h, const double *dev_fields, const double *dev_hot, const double *dev_kngll,
-                         const uint8_t *dev_mask, const int32_t *dev_group, double z, int min_samples,
+                         const uint8_t *dev_mask, const int32_t *dev_group, double z, int min_samples, double rel,
                          double *dev_hot_out, double *host_judge, int64_t *host_nnet);
 
 /* Clear the judge's running sums (hot_mlp_apply_judged). */

@@ -274,7 +274,7 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
   ml.out = cv.take<float>((size_t)pl.ncells * 5);
   ml.scal = cv.take<double>(8);
   ml.count = cv.take<int32_t>(4);
-  ml.jacc = cv.take<double>((size_t)pl.ncells * 11);
+  ml.jacc = cv.take<double>((size_t)pl.ncells * 16);
   const bool ann = cs[0].mesh == DSMC_MESH_ANNULUS;
   const size_t nr1 = ann ? (size_t)cs[0].ny + 1 : 1, nray = ann ? 2 * ((size_t)cs[0].nx + 1) : 1;
   const size_t nfn = ann ? 2 * (size_t)cs[0].nx : 1, nvol = ann ? (size_t)pl.ncells : 1;
@@ -622,7 +622,7 @@ int mlp_upload(dsmc_handle* h, const float* host) {
   cudaMemsetAsync(h->mlp.m, 0, sizeof(float) * MLP_NPARAM, h->stream);
   cudaMemsetAsync(h->mlp.v, 0, sizeof(float) * MLP_NPARAM, h->stream);
   // a new network starts the judge's statistics afresh
-  cudaMemsetAsync(h->mlp.jacc, 0, sizeof(double) * 11 * (size_t)h->ncells, h->stream);
+  cudaMemsetAsync(h->mlp.jacc, 0, sizeof(double) * 16 * (size_t)h->ncells, h->stream);
   mlp_to_bf16(h->mlp, h->stream);
   h->mlp_t = 0;
   return sync_check(h, "hot_mlp parameters");
@@ -1146,17 +1146,18 @@ int hot_mlp_apply(dsmc_handle* h, const double* dev_fields, const double* dev_ho
 
 int hot_mlp_judge_reset(dsmc_handle* h) {
   if (!h) return DSMC_ERR_ARG;
-  cudaMemsetAsync(h->mlp.jacc, 0, sizeof(double) * 11 * (size_t)h->ncells, h->stream);
+  cudaMemsetAsync(h->mlp.jacc, 0, sizeof(double) * 16 * (size_t)h->ncells, h->stream);
   return check_cuda(h, "hot_mlp_judge_reset");
 }
 
 int hot_mlp_apply_judged(dsmc_handle* h, const double* dev_fields, const double* dev_hot, const double* dev_kngll,
-                         const uint8_t* dev_mask, const int32_t* dev_group, double z, int min_samples,
+                         const uint8_t* dev_mask, const int32_t* dev_group, double z, int min_samples, double rel,
                          double* dev_hot_out, double* host_judge, int64_t* host_nnet) {
-  if (!h || !dev_fields || !dev_hot || !dev_kngll || !dev_mask || !dev_hot_out || !(z > 0.0) || min_samples < 2)
+  if (!h || !dev_fields || !dev_hot || !dev_kngll || !dev_mask || !dev_hot_out || !(z > 0.0) || min_samples < 2 ||
+      !(rel > 0.0))
     return set_err(h, DSMC_ERR_ARG, "bad arguments");
   mlp_data(h, dev_fields, dev_hot, dev_kngll, dev_mask);
-  mlp_apply(h->mlp, h->ncells, dev_hot, dev_hot_out, h->stream, dev_group, z, min_samples);
+  mlp_apply(h->mlp, h->ncells, dev_hot, dev_hot_out, h->stream, dev_group, z, min_samples, rel);
   double j[3] = {0.0, 0.0, 0.0};
   cudaMemcpyAsync(j, h->mlp.scal + 2, sizeof j, cudaMemcpyDeviceToHost, h->stream);
   const int r = sync_check(h, "hot_mlp_apply_judged");

@@ -174,7 +174,7 @@ struct Mlp {
   float* out;        // ncells x 5 network outputs
   double* scal;      // [0] loss, [2] judge sum, [3] judge count, [4] cells given the network's HoT
   int32_t* count;    // [0] number of cells with w = 1
-  double* jacc;      // ncells x 11 judge statistics per group: sum r (5), sum r^2 (5), count
+  double* jacc;      // ncells x 16 judge statistics per group: sum r (5), sum r^2 (5), count, sum Y (5)
 };
 // inputs, scales, targets (hot may be null) and weights of every cell
 void mlp_prepare(const Mlp& m, const CellParams* cp, const int32_t* cell_case, const int32_t* cell0, int ncells,
@@ -190,6 +190,6 @@ void mlp_to_bf16(const Mlp& m, cudaStream_t st);
 // with z > 0 a cell takes the network's HoT only where its group's running
 // residual statistics pass the judge (see hot_mlp_apply_judged)
 void mlp_apply(const Mlp& m, int ncells, const double* hot, double* hot_out, cudaStream_t st,
-               const int32_t* group = nullptr, double z = 0.0, int min_samples = 0);
+               const int32_t* group = nullptr, double z = 0.0, int min_samples = 0, double rel = 0.0);
 
 }  // namespace dsmc

@@ -428,8 +428,10 @@ __global__ void __launch_bounds__(TC_WARPS * 32) k_mlp_fwd_tc(const uint16_t* __
 }
 
 // The judge's statistics: every cell of the network (w = 1, finite
-// outputs) adds its residual r = network - DSMC (5 normalised outputs) and
-// r^2 to its group's sums, and 1 to its count (FP64).
+// outputs) adds its residual r = network - DSMC (5 normalised outputs), r^2
+// and the DSMC terms Y to its group's sums, and 1 to its count (FP64):
+// JACC doubles per group.
+constexpr int JACC = 16;
 __global__ void k_mlp_judge_acc(int ncells, const float* __restrict__ out, const float* __restrict__ Y,
                                 const float* __restrict__ w, const int32_t* __restrict__ group,
                                 double* __restrict__ jacc) {
@@ -438,25 +440,29 @@ __global__ void k_mlp_judge_acc(int ncells, const float* __restrict__ out, const
     bool fin = true;
     for (int k = 0; k < 5; ++k) fin = fin && isfinite(o[k]);
     if (w[c] == 0.f || !fin) continue;
-    double* a = jacc + (size_t)(group ? group[c] : c) * 11;
+    double* a = jacc + (size_t)(group ? group[c] : c) * JACC;
     for (int k = 0; k < 5; ++k) {
-      const double r = (double)o[k] - (double)Y[(size_t)c * 5 + k];
+      const double y = (double)Y[(size_t)c * 5 + k];
+      const double r = (double)o[k] - y;
       atomicAdd(a + k, r);
       atomicAdd(a + 5 + k, r * r);
+      atomicAdd(a + 11 + k, y);
     }
     atomicAdd(a + 10, 1.0);
   }
 }
 
-// true if the group's residuals are consistent with zero mean: at least
-// min_samples of them, and for every output |mean| <= z standard errors
-__device__ __forceinline__ bool judge_pass(const double* a, double z, int min_samples) {
+// true if the group's residuals show the network's bias to be small: at
+// least min_samples of them and, for every output, |mean r| + z SE(r) <=
+// rel |mean Y| (an equivalence test: the bias is bounded, with z standard
+// errors of confidence, by the fraction rel of the DSMC terms themselves)
+__device__ __forceinline__ bool judge_pass(const double* a, double z, int min_samples, double rel) {
   const double n = a[10];
   if (n < (double)min_samples) return false;
   for (int k = 0; k < 5; ++k) {
     const double m = a[k] / n;
     const double var = fmax(a[5 + k] / n - m * m, 0.0) * n / (n - 1.0);
-    if (fabs(m) > z * sqrt(var / n)) return false;
+    if (fabs(m) + z * sqrt(var / n) > rel * fabs(a[11 + k] / n)) return false;
   }
   return true;
 }
@@ -468,7 +474,7 @@ __device__ __forceinline__ bool judge_pass(const double* a, double z, int min_sa
 __global__ void k_mlp_hot(int ncells, const float* __restrict__ out, const float* __restrict__ Y,
                           const float* __restrict__ S, const float* __restrict__ w, const double* hot,
                           double* hot_out, double* __restrict__ scal, const int32_t* __restrict__ group,
-                          const double* __restrict__ jacc, double z, int min_samples) {
+                          const double* __restrict__ jacc, double z, int min_samples, double rel) {
   double jsum = 0.0, jcnt = 0.0, nnet = 0.0;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
     double h[12];
@@ -477,7 +483,7 @@ __global__ void k_mlp_hot(int ncells, const float* __restrict__ out, const float
     bool fin = true;
     for (int k = 0; k < 5; ++k) fin = fin && isfinite(o[k]);
     const bool judged = z > 0.0 && w[c] != 0.f && fin;
-    const bool pass = !judged || judge_pass(jacc + (size_t)(group ? group[c] : c) * 11, z, min_samples);
+    const bool pass = !judged || judge_pass(jacc + (size_t)(group ? group[c] : c) * JACC, z, min_samples, rel);
     if (w[c] != 0.f && fin) {
       for (int k = 0; k < 5; ++k) {
         const double r = (double)o[k] - (double)Y[(size_t)c * 5 + k];
@@ -549,7 +555,7 @@ void mlp_to_bf16(const Mlp& m, cudaStream_t st) {
 }
 
 void mlp_apply(const Mlp& m, int ncells, const double* hot, double* hot_out, cudaStream_t st,
-               const int32_t* group, double z, int min_samples) {
+               const int32_t* group, double z, int min_samples, double rel) {
   // inference on the tensor cores (bfloat16 weights and activations, FP32 sums)
   const int tiles = blocks_for(ncells, 16);
   const int grid = blocks_for(tiles, TC_WARPS) < MLP_GRID ? blocks_for(tiles, TC_WARPS) : MLP_GRID;
@@ -557,7 +563,8 @@ void mlp_apply(const Mlp& m, int ncells, const double* hot, double* hot_out, cud
   cudaMemsetAsync(m.scal + 2, 0, 3 * sizeof(double), st);
   const int hb = blocks_for(ncells, 256) < 1024 ? blocks_for(ncells, 256) : 1024;
   if (z > 0.0) k_mlp_judge_acc<<<hb, 256, 0, st>>>(ncells, m.out, m.Y, m.w, group, m.jacc);
-  k_mlp_hot<<<hb, 256, 0, st>>>(ncells, m.out, m.Y, m.S, m.w, hot, hot_out, m.scal, group, m.jacc, z, min_samples);
+  k_mlp_hot<<<hb, 256, 0, st>>>(ncells, m.out, m.Y, m.S, m.w, hot, hot_out, m.scal, group, m.jacc, z, min_samples,
+                                rel);
 }
 
 }  // namespace dsmc

@@ -36,15 +36,17 @@ def target_as_fields(target: torch.Tensor) -> torch.Tensor:
 
 def dig_iteration(sim: "dsmc.Dsmc", n_s: int, allow_not_converged: bool = True,
                   hot_model: bool = False, prev_target: torch.Tensor | None = None,
-                  hot_group: torch.Tensor | None = None, judge_z: float = 3.0, judge_min: int = 4) -> dict:
+                  hot_group: torch.Tensor | None = None, judge_z: float = 3.0, judge_min: int = 4,
+                  judge_rel: float = 0.25) -> dict:
     """N_s DSMC steps, sample, HoT, synthetic solve, particle modification.
 
     With hot_model, the higher-order terms where Kn_GLL >= Kn_ref are the
     handle's HoT network evaluated on the previous synthetic solution (a
     smooth state; the sampled fields' gradients are dominated by noise),
     judged against the sampled HoT: a cell takes the network's terms only
-    while the running residuals of its group (hot_group, e.g. the same cell
-    of every replica) stay within judge_z standard errors of zero, and the
+    once the running residuals of its group (hot_group, e.g. the same cell
+    of every replica) bound the network's bias below judge_rel of the
+    sampled terms with judge_z standard errors of confidence, and the
     sampled HoT otherwise; the first iteration, with no previous solution,
     uses the sampled HoT."""
     sim.dsmc_step(n_s, sample=True)
@@ -55,7 +57,7 @@ def dig_iteration(sim: "dsmc.Dsmc", n_s: int, allow_not_converged: bool = True,
         fs = target_as_fields(prev_target)
         _, kn_s, mask_s = sim.dsmc_hot(fs)
         hot, judge, nnet = sim.mlp_apply_judged(fs, hot, kn_s, mask_s, group=hot_group, z=judge_z,
-                                                min_samples=judge_min)
+                                                min_samples=judge_min, rel=judge_rel)
     out, iters, res = sim.synth_solve(f, hot, allow_not_converged=allow_not_converged, allow_fallback=True)
     sim.dig_correct(out)
     # the HoT mask stays on the device (reducing it here would put a host

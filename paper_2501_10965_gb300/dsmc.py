@@ -119,7 +119,7 @@ def load(build_if_missing: bool = True):
         "hot_mlp_grad": ([H, P, P, P, P, P, P], ctypes.c_int),
         "hot_mlp_train": ([H, P, P, P, P, ctypes.c_int, ctypes.c_double, P], ctypes.c_int),
         "hot_mlp_apply": ([H, P, P, P, P, P, P], ctypes.c_int),
-        "hot_mlp_apply_judged": ([H, P, P, P, P, P, D, ctypes.c_int, P, P, P], ctypes.c_int),
+        "hot_mlp_apply_judged": ([H, P, P, P, P, P, D, ctypes.c_int, D, P, P, P], ctypes.c_int),
         "hot_mlp_judge_reset": ([H], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -292,17 +292,19 @@ class Dsmc:
                                          float(lr), ctypes.byref(loss)))
         return loss.value
 
-    def mlp_apply_judged(self, fields, hot, kngll, mask, group=None, z: float = 3.0, min_samples: int = 4):
+    def mlp_apply_judged(self, fields, hot, kngll, mask, group=None, z: float = 3.0, min_samples: int = 4,
+                         rel: float = 0.25):
         """(HoT [ncells x 12], judge, cells given the network's HoT): the
         network where its group's running residuals against the DSMC HoT
-        pass the z-standard-error judge, the DSMC HoT elsewhere."""
+        bound its bias below rel of the DSMC terms (with z standard errors of
+        confidence), the DSMC HoT elsewhere."""
         out = torch.empty_like(hot)
         judge = ctypes.c_double()
         nnet = ctypes.c_int64()
         g = group.to(device=self.device, dtype=torch.int32).contiguous() if group is not None else None
         self._check(load().hot_mlp_apply_judged(self._h, _ptr(fields.contiguous()), _ptr(hot.contiguous()),
                                                 _ptr(kngll.contiguous()), _ptr(mask.contiguous()), _ptr(g),
-                                                float(z), int(min_samples), _ptr(out), ctypes.byref(judge),
+                                                float(z), int(min_samples), float(rel), _ptr(out), ctypes.byref(judge),
                                                 ctypes.byref(nnet)))
         return out, judge.value, nnet.value
 

@@ -268,14 +268,15 @@ def test_hot_kngll_on_annulus_matches_oracle():
     mask exactly, from the oracle's sampled fields of a Mach 2 flow."""
     from oracle.fields import hot_kngll
     cfg = _small(ntheta=24, nr=8, ppc=30, kn=0.1, mach=2.0, t_wall=2.0, dr1=0.1)
-    F = _oracle_annulus_fields(cfg)
+    F = _oracle_annulus_fields(cfg, sample=240)
     _, kn_o, _ = hot_kngll(F, dict(cfg, kn_ref=0.0))
-    cfg = dict(cfg, kn_ref=float(np.median(kn_o)) * 1.0000001)
+    # an empty cell (no particle sampled) has no Kn_GLL on either side
+    cfg = dict(cfg, kn_ref=float(np.nanmedian(kn_o)) * 1.0000001)
     hot_o, kn_o, mask_o = hot_kngll(F, cfg)
     g = _gpu(cfg)
     hot_g, kn_g, mask_g = [t.cpu().numpy() for t in g.dsmc_hot(torch.tensor(F, device="cuda"))]
-    assert 0 < mask_o.sum() < len(mask_o)
-    assert np.allclose(kn_g, kn_o, rtol=1e-12, atol=0.0), np.max(np.abs(kn_g / kn_o - 1))
+    assert 0 < mask_o.sum() < len(mask_o) and np.isfinite(kn_o).sum() > 0.95 * len(kn_o)
+    assert np.allclose(kn_g, kn_o, rtol=1e-12, atol=0.0, equal_nan=True)
     assert np.array_equal(mask_g.astype(bool), mask_o)
     scale = np.maximum(np.abs(hot_o).max(0), 1e-300)
     assert (np.abs(hot_g - hot_o) / scale).max() <= 1e-11
