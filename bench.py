@@ -370,7 +370,7 @@ def run_gpu(args):
     n_end = sim.num_particles()
     n_mean = 0.5 * (n + n_end)
     value = job_throughput(n_mean, args.steps, t, world, dev)
-    cfg_line_shape = sim.launch_config()
+    cfg_line_shape = sim.launch_shape()
 
     # average duration of one fused step kernel: difference of two runs with
     # different step counts on the launching stream (the constant parts --
@@ -466,7 +466,7 @@ def run_gpu(args):
                            "precision": prec + " particles, fp64 compensated moments",
                            "l2": "inputs larger than L2 (particle state %.2f GB)" % (n * 24 / 1e9),
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "fused_warps_per_cta": cfg_line_shape},
+                           "fused_warps_per_cta": cfg_line_shape[0], "fused_tile": cfg_line_shape[1]},
                 "roofline": roofline, "clocks": clocks, "gpu_launches": gpu_launches,
                 "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d / args.steps,
                         "d2h_bytes_per_step": d2h / args.steps},

@@ -323,12 +323,18 @@ int dsmc_get_volumes(dsmc_handle *h, double *host_out);
 int dsmc_get_wall_tally(dsmc_handle *h, double *host_out20);
 
 /* Launch shape of the FP32 fused step (host): warps (= cells) per CTA, 2
- * or 4.  A handle times both shapes on real steps of its first dsmc_step call
- * of at least 10 steps and keeps the faster one (which shape wins depends on
- * the workload: 4 for the 400 x 300 cavity, 2 for the 64-case ensemble);
- * 0 before that call and in the FP64-deterministic mode.  The paper has no
- * counterpart. */
+ * or 4.  A handle times four shapes -- 4 warps with the tile sized from the
+ * particles per cell, 2 warps, and 4 warps with the tile 32 particles
+ * smaller and larger -- on real steps of its first dsmc_step call of at
+ * least 20 steps and keeps the fastest (the first unless another is faster
+ * by more than 1 %); 0 before that call and in the FP64-deterministic mode.
+ * The paper has no counterpart. */
 int dsmc_get_launch_config(dsmc_handle *h, int *host_warps_per_cta);
+
+/* The same launch shape with its tile: particles staged per warp in shared
+ * memory (cells above it take the chunked path); 0, 0 before the tuning
+ * call and in the FP64-deterministic mode. */
+int dsmc_get_launch_shape(dsmc_handle *h, int *host_warps_per_cta, int *host_tile);
 
 /* Derived constants (host, 8 entries): dx, dy, cell volume V, particle weight
  * F, mu_ref, K (nu = K p / mu), C_sigma (sigma g = C_sigma g^(2-2 omega)),

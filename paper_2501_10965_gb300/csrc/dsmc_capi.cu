@@ -1065,6 +1065,13 @@ int dsmc_get_constants(dsmc_handle* h, double* out8) {
   return DSMC_OK;
 }
 
+int dsmc_get_launch_shape(dsmc_handle* h, int* host_warps_per_cta, int* host_tile) {
+  if (!h || !host_warps_per_cta || !host_tile) return set_err(h, DSMC_ERR_ARG, "bad arguments");
+  *host_warps_per_cta = h->det ? 0 : h->sf.fwpb;
+  *host_tile = (h->det || h->sf.fwpb == 0) ? 0 : (h->sf.ftile > 0 ? h->sf.ftile : h->sf.tile);
+  return DSMC_OK;
+}
+
 int dsmc_get_launch_config(dsmc_handle* h, int* host_warps_per_cta) {
   if (!h || !host_warps_per_cta) return set_err(h, DSMC_ERR_ARG, "bad arguments");
   *host_warps_per_cta = h->det ? 0 : h->sf.fwpb;

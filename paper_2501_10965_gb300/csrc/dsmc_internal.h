@@ -83,6 +83,7 @@ struct State {
   bool batch;  // several cases: kernels read their parameters per cell
   bool gen;    // a gas with d_r = 3 or VSS scattering: the fused step's general instantiation
   int fwpb;    // FP32 fused step: warps per CTA (0: not tuned yet)
+  int ftile;   // FP32 fused step: particles staged per warp (0: tile)
   Params<double> pinj;  // annulus: FP64 parameters of the freestream entry
   double* inj_mu;       // annulus: expected entries of every outer face per step
   int inj_max;          // annulus: bound on the entries of one step (sum of floor(mu) + 1)

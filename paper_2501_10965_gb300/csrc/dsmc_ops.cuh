@@ -778,8 +778,8 @@ __device__ __forceinline__ int neighbour_cell_ann(int nx, int cell, int code) {
   return j * nx + k;
 }
 
-// warps per CTA of the fused step: 2 or 4, chosen per handle by timing both
-// on the handle's first long dsmc_step call (fused_tune)
+// warps per CTA of the fused step: 2 or 4, chosen per handle with the tile
+// by timing real steps of the handle's first long dsmc_step call (step_bins)
 constexpr int FWPB_MAX = 4;
 constexpr uint32_t MBAR_POLL_LIMIT = 1u << 22;  // bounded wait for a cell's bulk copies
 
@@ -1709,13 +1709,13 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
     if (nsteps <= 0) return;
     const int ncells = s.ncells;
     const int oblocks = 8;
-    auto launch = [&](int flags, uint32_t sc, uint32_t sm_step, int F) {
+    auto launch = [&](int flags, uint32_t sc, uint32_t sm_step, int F, int ftile) {
       const int other = cur ^ 1;
       const int cblocks = (ncells + F - 1) / F;
-      const size_t smf = fused_smem_bytes(s.tile, F);
+      const size_t smf = fused_smem_bytes(ftile, F);
 #define DSMC_FUSED_ARGS                                                                                         \
   p, s.cases, ncells, s.buf[cur], s.buf[other], s.start[lay], s.count[cur], s.count[other], s.sgmax, s.acc,      \
-      s.comp, s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, s.tile, cblocks, s.tally, s.stats, \
+      s.comp, s.owner, s.ovf[cur], s.ovf[other], s.ovf_cap, sc, sm_step, flags, ftile, cblocks, s.tally, s.stats, \
       s.flags + 8, s.stg, s.stc
 #define DSMC_FUSED_LAUNCH(D, B, W, A) k_fused<D, B, W, A, false><<<cblocks + oblocks, W * 32, smf, st>>>(DSMC_FUSED_ARGS)
 #define DSMC_FUSED_LAUNCH_GEN(D, A) k_fused<D, false, 4, A, true><<<cblocks + oblocks, 128, smf, st>>>(DSMC_FUSED_ARGS)
@@ -1766,7 +1766,8 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
       cur = other;
     };
     // move of step0, then per step: collide (+sample) of step k and move of step k+1
-    launch(4, step0, step0, s.fwpb > 0 ? s.fwpb : FWPB_MAX);
+    const int tile0 = s.ftile > 0 ? s.ftile : s.tile;
+    launch(4, step0, step0, s.fwpb > 0 ? s.fwpb : FWPB_MAX, tile0);
     // sampled sums are staged in FP32 and folded into FP64 every
     // STAGE_STEPS steps and on the last step of the call
     constexpr int STAGE_STEPS = 16;
@@ -1776,35 +1777,45 @@ void Ops<T>::step_bins(const Params<T>& p, State<T>& s, int& cur, int lay, uint3
     };
     int i0 = 0;
     if (s.gen) s.fwpb = 4;  // the general gas has the 4-warp shape only
-    if (s.fwpb == 0 && nsteps >= 10) {
-      // launch shape of the fused step: steps 2-4 timed with 4 warps per
-      // CTA, steps 6-8 with 2 (steps 0-1 and 5 warm each one up); every step
-      // is a real step of the call; 2 is kept only if it is faster by more
-      // than 1 % (the timing's resolution over three steps)
-      cudaEvent_t ev[4];
+    if (s.fwpb == 0 && nsteps >= 20) {
+      // launch shape of the fused step, tuned on real steps of the call:
+      // warps (cells) per CTA and the shared-memory tile (particles staged
+      // per warp; larger cells go through the chunked path).  Each shape
+      // runs one warm-up step and three timed steps; the first shape (4
+      // warps, the tile sized from the particles per cell) is kept unless
+      // another is faster by more than 1 % (the timing's resolution).
+      const int t0 = s.tile;
+      const int tlo = t0 - 32 >= 64 ? t0 - 32 : t0, thi = t0 + 32 <= TILE_MAX_OF<T> ? t0 + 32 : t0;
+      const int shapes[4][2] = {{4, t0}, {2, t0}, {4, tlo}, {4, thi}};
+      cudaEvent_t ev[8];
       for (auto& e : ev) cudaEventCreate(&e);
-      for (int i = 0; i < 9; ++i) {
-        if (i == 2) cudaEventRecord(ev[0], st);
-        if (i == 6) cudaEventRecord(ev[2], st);
-        const uint32_t sc = step0 + (uint32_t)i;
-        launch(fused_flags(i), sc, sc + 1, i < 5 ? 4 : 2);
-        if (i == 4) cudaEventRecord(ev[1], st);
-        if (i == 8) cudaEventRecord(ev[3], st);
+      int i = 0;
+      for (int k = 0; k < 4; ++k) {
+        for (int r = 0; r < 4; ++r, ++i) {
+          if (r == 1) cudaEventRecord(ev[2 * k], st);
+          const uint32_t sc = step0 + (uint32_t)i;
+          launch(fused_flags(i), sc, sc + 1, shapes[k][0], shapes[k][1]);
+        }
+        cudaEventRecord(ev[2 * k + 1], st);
       }
-      float t4 = 0.f, t2 = 0.f;
-      cudaEventSynchronize(ev[3]);
-      cudaEventElapsedTime(&t4, ev[0], ev[1]);
-      cudaEventElapsedTime(&t2, ev[2], ev[3]);
+      cudaEventSynchronize(ev[7]);
+      float tk[4];
+      for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&tk[k], ev[2 * k], ev[2 * k + 1]);
       for (auto& e : ev) cudaEventDestroy(e);
-      s.fwpb = (t2 > 0.f && t2 < 0.99f * t4) ? 2 : 4;
-      i0 = 9;
+      int best = 0;
+      for (int k = 1; k < 4; ++k)
+        if (tk[k] > 0.f && tk[k] < 0.99f * tk[best]) best = k;
+      s.fwpb = shapes[best][0];
+      s.ftile = shapes[best][1];
+      i0 = i;
     }
     const int F = s.fwpb > 0 ? s.fwpb : FWPB_MAX;
+    const int FT = s.ftile > 0 ? s.ftile : s.tile;
     for (int i = i0; i < nsteps; ++i) {
       const bool last = (i == nsteps - 1);
       const uint32_t sc = step0 + (uint32_t)i;
       if (!last) {
-        launch(fused_flags(i), sc, sc + 1, F);
+        launch(fused_flags(i), sc, sc + 1, F, FT);
       } else {
         const int flags = 1 | (do_sample ? 2 : 0);
         if (s.batch)

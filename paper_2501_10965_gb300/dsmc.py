@@ -32,7 +32,7 @@ SYMBOLS = ["dsmc_workspace_size", "dsmc_init", "dsmc_destroy", "dsmc_last_error"
            "dsmc_get_constants", "synth_solve_noalloc", "dsmc_batch_workspace_size", "dsmc_batch_init",
            "hot_mlp_init", "hot_mlp_set_params", "hot_mlp_get_params", "hot_mlp_grad", "hot_mlp_train",
            "hot_mlp_apply", "dsmc_get_launch_config", "dsmc_get_flow", "dsmc_get_volumes",
-           "hot_mlp_apply_judged", "hot_mlp_judge_reset"]
+           "hot_mlp_apply_judged", "hot_mlp_judge_reset", "dsmc_get_launch_shape"]
 MLP_NPARAM = 9477
 
 
@@ -121,6 +121,7 @@ def load(build_if_missing: bool = True):
         "hot_mlp_apply": ([H, P, P, P, P, P, P], ctypes.c_int),
         "hot_mlp_apply_judged": ([H, P, P, P, P, P, D, ctypes.c_int, D, P, P, P], ctypes.c_int),
         "hot_mlp_judge_reset": ([H], ctypes.c_int),
+        "dsmc_get_launch_shape": ([H, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -258,6 +259,12 @@ class Dsmc:
         v = ctypes.c_int()
         self._check(load().dsmc_get_launch_config(self._h, ctypes.byref(v)))
         return v.value
+
+    def launch_shape(self) -> tuple:
+        """(warps per CTA, tile) of the FP32 fused step chosen by the tuner."""
+        w, t = ctypes.c_int(), ctypes.c_int()
+        self._check(load().dsmc_get_launch_shape(self._h, ctypes.byref(w), ctypes.byref(t)))
+        return w.value, t.value
 
     # ---- HoT surrogate network (see the header) ----
     def mlp_init(self, seed: int = 0):

@@ -107,21 +107,27 @@ def test_batch_fp32_ensemble_of_64_uneven_cases():
 
 
 def test_fused_launch_shape_is_tuned_per_handle():
-    """The FP32 fused step times its two launch shapes on the first call of
-    at least 10 steps and keeps one; particles are conserved through the
-    tuning steps; the FP64 mode reports no shape."""
+    """The FP32 fused step times its four launch shapes (warps per CTA and
+    the shared-memory tile) on the first call of at least 20 steps and keeps
+    one; particles are conserved through the tuning steps, and a run tuned
+    on a tile other than the default stays statistically the same gas (the
+    staged and chunked paths are the same algorithm); the FP64 mode reports
+    no shape."""
     from paper_2501_10965_gb300 import dsmc
     g = dsmc.Dsmc(W.ensemble_1d(8))
     n0 = g.num_particles()
-    assert g.launch_config() == 0
+    assert g.launch_config() == 0 and g.launch_shape() == (0, 0)
     g.dsmc_step(5)
     assert g.launch_config() == 0
-    g.dsmc_step(20)
-    assert g.launch_config() in (2, 4)
+    g.dsmc_step(24)
+    w, t = g.launch_shape()
+    assert w in (2, 4) and g.launch_config() == w and t > 0 and t % 16 == 0
+    assert g.num_particles() == n0
+    g.dsmc_step(30)
     assert g.num_particles() == n0
     d = dsmc.Dsmc(W.fourier_1d(nx=20, ppc=30))
-    d.dsmc_step(12)
-    assert d.launch_config() == 0
+    d.dsmc_step(24)
+    assert d.launch_config() == 0 and d.launch_shape() == (0, 0)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
