@@ -39,11 +39,11 @@ ALGO_BYTES_PER_PARTICLE_STEP = {("fp32", 2): 48, ("fp32", 1): 40, ("fp64", 2): 9
 # --profile-steps 4 --warmup 3`, third fused launch).  Re-measure whenever
 # k_fused changes.
 # Annulus: the 300 x 225-cell, 11.27 M-particle cylinder case
-# (dram__bytes_read.sum 352.47 MB + dram__bytes_write.sum 279.12 MB for one
+# (dram__bytes_read.sum 352.24 MB + dram__bytes_write.sum 279.16 MB for one
 # launch of the current kernel, `--workload cylinder2d_11m --profile-steps 4
 # --warmup 3`, third fused launch).
 NCU_TRAFFIC_BYTES_PER_PARTICLE_STEP = {("fp32", 2, "box"): 579425536 / 11272500,
-                                       ("fp32", 2, "annulus"): 631591424 / 11272500}
+                                       ("fp32", 2, "annulus"): 631403520 / 11272500}
 METRIC = "particle-steps/s"
 
 

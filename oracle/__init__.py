@@ -157,7 +157,7 @@ def make_config(cfg: dict) -> OrConfig:
     c.collisions = 1 if cfg.get("collisions", True) else 0
     c.seed = int(cfg.get("seed", 0))
     c.capacity = int(cfg.get("capacity", 0) or 0)
-    c.mesh = 1 if cfg.get("mesh", "box") == "annulus" else 0
+    c.mesh = {"box": 0, "annulus": 1, "refined": 2}[cfg.get("mesh", "box")]
     c.r_in, c.r_out = float(cfg.get("r_in", 0.5)), float(cfg.get("r_out", 5.5))
     c.stretch = float(cfg.get("stretch", 1.0))
     c.fs_rho, c.fs_t = float(cfg.get("fs_rho", 1.0)), float(cfg.get("fs_t", 1.0))

@@ -99,6 +99,7 @@ typedef struct or_state {
   double wall_tally[4][5];
   double *vol;      /* ncells cell volumes (areas per unit depth in 2D) */
   double *rt, *r2t; /* annulus: ny + 1 ring radii and their squares */
+  double *xe, *ye;  /* wall-refined box: nx + 1 and ny + 1 cell edges */
   double *rc, *rs;  /* annulus: nx + 1 rays (cos, sin of 2 pi k / nx) */
   double *fc, *fs;  /* annulus: nx outer-face centre directions */
   int64_t n_inj, n_out;
@@ -219,10 +220,30 @@ static void or_annulus_tables(or_state *S) {
     for (int k = 0; k < nt; ++k) S->vol[j * nt + k] = half * (S->r2t[j + 1] - S->r2t[j]);
 }
 
+/* Wall-refined box (mesh 2, the non-uniform cavity grid of Sec. 4.1): n
+ * cells along an axis of length L whose widths grow geometrically by the
+ * factor q from both walls towards the middle, w_i proportional to
+ * q^min(i, n-1-i), scaled to sum to L; e[0] = 0, e[n] = L. */
+static void or_box_edges(int n, double L, double q, double *e) {
+  double sum = 0.0;
+  for (int i = 0; i < n; ++i) sum += pow(q, (double)(i < n - 1 - i ? i : n - 1 - i));
+  e[0] = 0.0;
+  for (int i = 0; i < n; ++i) e[i + 1] = e[i] + L * pow(q, (double)(i < n - 1 - i ? i : n - 1 - i)) / sum;
+  e[n] = L;
+}
+
 static void or_constants_compute(or_state *S) {
   const or_config *c = &S->c;
   double w = c->omega, a = c->alpha;
-  if (c->mesh == 1) {
+  if (c->mesh == 2) {
+    or_box_edges(c->nx, c->lx, c->stretch, S->xe);
+    or_box_edges(c->ny, c->ly, c->stretch, S->ye);
+    S->dx = c->lx / (double)c->nx;
+    S->dy = c->ly / (double)c->ny;
+    S->vcell = S->dx * S->dy;
+    for (int j = 0; j < c->ny; ++j)
+      for (int i = 0; i < c->nx; ++i) S->vol[j * c->nx + i] = (S->xe[i + 1] - S->xe[i]) * (S->ye[j + 1] - S->ye[j]);
+  } else if (c->mesh == 1) {
     or_annulus_tables(S);
     S->dx = 2.0 * M_PI / (double)c->nx;
     S->dy = (c->r_out - c->r_in) / (double)c->ny;
@@ -286,9 +307,21 @@ static int or_cell_of_annulus(const or_state *S, double x, double y) {
   return lo * nt + k;
 }
 
+/* the largest i with e[i] <= v, clamped to [0, n - 1] */
+static int or_edge_index(const double *e, int n, double v) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) / 2;
+    if (e[mid] <= v) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 static int or_cell_of(const or_state *S, double x, double y) {
   const or_config *c = &S->c;
   if (c->mesh == 1) return or_cell_of_annulus(S, x, y);
+  if (c->mesh == 2) return or_edge_index(S->ye, c->ny, y) * c->nx + or_edge_index(S->xe, c->nx, x);
   int ix = (int)(x * ((double)c->nx / c->lx));
   if (ix < 0) ix = 0;
   if (ix > c->nx - 1) ix = c->nx - 1;
@@ -324,7 +357,10 @@ static int or_alloc(or_state *S, int64_t cap) {
   S->rs = (double *)calloc((size_t)S->c.nx + 1, sizeof(double));
   S->fc = (double *)calloc((size_t)S->c.nx, sizeof(double));
   S->fs = (double *)calloc((size_t)S->c.nx, sizeof(double));
-  if (!S->vol || !S->rt || !S->r2t || !S->rc || !S->rs || !S->fc || !S->fs) return OR_ERR_CAPACITY;
+  S->xe = (double *)calloc((size_t)S->c.nx + 1, sizeof(double));
+  S->ye = (double *)calloc((size_t)S->c.ny + 1, sizeof(double));
+  if (!S->vol || !S->rt || !S->r2t || !S->rc || !S->rs || !S->fc || !S->fs || !S->xe || !S->ye)
+    return OR_ERR_CAPACITY;
   return OR_OK;
 }
 
@@ -346,6 +382,8 @@ void or_destroy(or_state *S) {
   free(S->rs);
   free(S->fc);
   free(S->fs);
+  free(S->xe);
+  free(S->ye);
   free(S);
 }
 
@@ -469,7 +507,8 @@ int or_create(const or_config *cfg, or_state **out) {
   if (cfg->nx <= 0 || (cfg->dim == 2 && cfg->ny <= 0) || cfg->ppc < 0) return OR_ERR_ARG;
   /* d_r = 2 (linear) or 3 (non-linear molecules); VSS exponent 0 < alpha <= 2 */
   if ((cfg->d_r != 2.0 && cfg->d_r != 3.0) || !(cfg->alpha > 0.0 && cfg->alpha <= 2.0)) return OR_ERR_ARG;
-  if (cfg->mesh != 0 && cfg->mesh != 1) return OR_ERR_ARG;
+  if (cfg->mesh != 0 && cfg->mesh != 1 && cfg->mesh != 2) return OR_ERR_ARG;
+  if (cfg->mesh == 2 && (cfg->dim != 2 || !(cfg->stretch > 0.0))) return OR_ERR_ARG;
   if (cfg->mesh == 1 && (cfg->dim != 2 || cfg->nx < 3 || !(cfg->r_in > 0.0) || !(cfg->r_out > cfg->r_in) ||
                          !(cfg->stretch > 0.0) || !(cfg->fs_t > 0.0) || !(cfg->fs_rho >= 0.0)))
     return OR_ERR_ARG;
@@ -500,8 +539,9 @@ int or_create(const or_config *cfg, or_state **out) {
     int ix = cell % c->nx, iy = cell / c->nx;
     S->start[cell] = s;
     int64_t np = c->ppc;
-    if (c->mesh == 1) {
-      /* annulus: the equilibrium density in cells of unequal volume */
+    if (c->mesh != 0) {
+      /* annulus, wall-refined box: the equilibrium density in cells of
+       * unequal volume */
       or_stream sc;
       or_stream_init(&sc, c->seed, OR_TAG_INIT, 0xFFFFFFFFu, (uint32_t)cell, 0u);
       np = or_iround(c->init_rho * S->vol[cell] / S->fnum, or_uni(&sc, 0));
@@ -524,6 +564,9 @@ int or_create(const or_config *cfg, or_state **out) {
         double th = 2.0 * M_PI * ((double)ix + u1) / (double)c->nx;
         S->x[s] = r * cos(th);
         S->y[s] = r * sin(th);
+      } else if (c->mesh == 2) {
+        S->x[s] = S->xe[ix] + u0 * (S->xe[ix + 1] - S->xe[ix]);
+        S->y[s] = S->ye[iy] + u1 * (S->ye[iy + 1] - S->ye[iy]);
       } else {
         S->x[s] = ((double)ix + u0) * S->dx;
         S->y[s] = (c->dim == 2) ? ((double)iy + u1) * S->dy : 0.0;
@@ -1117,6 +1160,9 @@ int or_dig_correct(or_state *S, const double *target) {
           double th = 2.0 * M_PI * ((double)ix + or_uni(&sp, 1)) / (double)c->nx;
           S->tx[d] = r * cos(th);
           S->ty[d] = r * sin(th);
+        } else if (c->mesh == 2) {
+          S->tx[d] = S->xe[ix] + or_uni(&sp, 0) * (S->xe[ix + 1] - S->xe[ix]);
+          S->ty[d] = S->ye[iy] + or_uni(&sp, 1) * (S->ye[iy + 1] - S->ye[iy]);
         } else {
           S->tx[d] = ((double)ix + or_uni(&sp, 0)) * S->dx;
           S->ty[d] = (c->dim == 2) ? ((double)iy + or_uni(&sp, 1)) * S->dy : 0.0;

@@ -127,6 +127,39 @@ def ring_edges(cfg: dict) -> np.ndarray:
     return r
 
 
+def box_edges(n: int, length: float, q: float) -> np.ndarray:
+    """Cell edges of the wall-refined box along one axis: n widths growing
+    geometrically by q from both walls to the middle (w_i proportional to
+    q^min(i, n-1-i)), summing to the length."""
+    i = np.arange(n)
+    w = q ** np.minimum(i, n - 1 - i).astype(np.float64)
+    e = np.concatenate([[0.0], np.cumsum(length * w / w.sum())])
+    e[-1] = length
+    return e
+
+
+def _d_nonuniform(g: np.ndarray, xc: np.ndarray, axis: int):
+    """d/dx along `axis` of cell values g at centres xc: the three-point
+    formula on the unequal spacing (exact for quadratics), one-sided first
+    differences at the two ends."""
+    g = np.moveaxis(g, axis, 0)
+    d = np.zeros_like(g)
+    hm = (xc[1:-1] - xc[:-2])[:, None]
+    hp = (xc[2:] - xc[1:-1])[:, None]
+    d[1:-1] = (hm * hm * g[2:] - hp * hp * g[:-2] + (hp * hp - hm * hm) * g[1:-1]) / (hp * hm * (hp + hm))
+    d[0] = (g[1] - g[0]) / (xc[1] - xc[0])
+    d[-1] = (g[-1] - g[-2]) / (xc[-1] - xc[-2])
+    return np.moveaxis(d, 0, axis)
+
+
+def grad_refined(f: np.ndarray, nx: int, ny: int, xe: np.ndarray, ye: np.ndarray):
+    """Cell-centred gradient on the wall-refined box (cell centres at the
+    middle of their edges)."""
+    g = f.reshape(ny, nx)
+    xc, yc = 0.5 * (xe[:-1] + xe[1:]), 0.5 * (ye[:-1] + ye[1:])
+    return _d_nonuniform(g, xc, 1).reshape(-1), _d_nonuniform(g, yc, 0).reshape(-1)
+
+
 def grad_annulus(f: np.ndarray, nt: int, nr: int, redges: np.ndarray):
     """Cartesian gradient (d/dx, d/dy) of a cell field on the annulus (cell j
     nt + k: ring j, sector k), from its polar derivatives at the cell centre
@@ -155,6 +188,24 @@ def grad_annulus(f: np.ndarray, nt: int, nr: int, redges: np.ndarray):
     return (c * dr - s * dt).reshape(-1), (s * dr + c * dt).reshape(-1)
 
 
+def gradient_of(cfg: dict):
+    """The cell-centred gradient f -> (d/dx, d/dy) of the configuration's
+    mesh: uniform box, annulus or wall-refined box."""
+    dim, nx = int(cfg["dim"]), int(cfg["nx"])
+    ny = int(cfg.get("ny", 1)) if dim == 2 else 1
+    mesh = cfg.get("mesh", "box")
+    if mesh == "annulus":
+        re = ring_edges(cfg)
+        return lambda f: grad_annulus(f, nx, ny, re)
+    if mesh == "refined":
+        q = float(cfg["stretch"])
+        xe, ye = box_edges(nx, float(cfg["lx"]), q), box_edges(ny, float(cfg["ly"]), q)
+        return lambda f: grad_refined(f, nx, ny, xe, ye)
+    dx = float(cfg["lx"]) / nx
+    dy = float(cfg.get("ly", 1.0)) / ny if dim == 2 else 1.0
+    return lambda f: grad_cells(f, nx, ny, dx, dy, dim)
+
+
 def hot_kngll(fields: np.ndarray, cfg: dict):
     """Eq. (ns_constitutive), Eq. (hot_constitutive) and Eq. (Kn_GLL).
 
@@ -168,14 +219,7 @@ def hot_kngll(fields: np.ndarray, cfg: dict):
     ny = int(cfg.get("ny", 1)) if dim == 2 else 1
     dx = float(cfg["lx"]) / nx
     dy = float(cfg.get("ly", 1.0)) / ny if dim == 2 else 1.0
-    if cfg.get("mesh", "box") == "annulus":
-        re = ring_edges(cfg)
-
-        def grad(f):
-            return grad_annulus(f, nx, ny, re)
-    else:
-        def grad(f):
-            return grad_cells(f, nx, ny, dx, dy, dim)
+    grad = gradient_of(cfg)
     d_r, omega = float(cfg["d_r"]), float(cfg["omega"])
     mu_ref = mu_ref_of(float(cfg["kn"]))
     kt_c, kr_c = kappa_coefficients(cfg["a_matrix"], d_r)

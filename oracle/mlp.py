@@ -28,7 +28,7 @@ import math
 
 import numpy as np
 
-from .fields import F_RHO, F_TR, F_TT, F_U, grad_annulus, grad_cells, mu_ref_of, ring_edges
+from .fields import F_RHO, F_TR, F_TT, F_U, gradient_of, mu_ref_of
 
 SIZES = (12, 64, 64, 64, 5)
 NPARAM = sum(SIZES[k] * SIZES[k + 1] + SIZES[k + 1] for k in range(4))
@@ -76,17 +76,9 @@ def _geometry(cfg):
 
 def features(fields: np.ndarray, kngll: np.ndarray, cfg: dict):
     """Returns (X [n x 12], scale [n x 4]) with scale = (p, p sqrt(T), e_x, e_y).
-    Gradients as for the HoT: the box's cell-centred differences, or the
-    annulus's polar ones (fields.grad_annulus)."""
-    dim, nx, ny, dx, dy = _geometry(cfg)
-    if cfg.get("mesh", "box") == "annulus":
-        re = ring_edges(cfg)
-
-        def grad(f):
-            return grad_annulus(f, nx, ny, re)
-    else:
-        def grad(f):
-            return grad_cells(f, nx, ny, dx, dy, dim)
+    Gradients as for the HoT (fields.gradient_of: uniform box, annulus or
+    wall-refined box)."""
+    grad = gradient_of(cfg)
     d_r, omega = float(cfg["d_r"]), float(cfg["omega"])
     mu_ref = mu_ref_of(float(cfg["kn"]))
     rho = fields[:, F_RHO]

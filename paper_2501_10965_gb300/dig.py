@@ -37,7 +37,7 @@ def target_as_fields(target: torch.Tensor) -> torch.Tensor:
 def dig_iteration(sim: "dsmc.Dsmc", n_s: int, allow_not_converged: bool = True,
                   hot_model: bool = False, prev_target: torch.Tensor | None = None,
                   hot_group: torch.Tensor | None = None, judge_z: float = 3.0, judge_min: int = 4,
-                  judge_rel: float = 0.25) -> dict:
+                  judge_rel: float = 0.1) -> dict:
     """N_s DSMC steps, sample, HoT, synthetic solve, particle modification.
 
     With hot_model, the higher-order terms where Kn_GLL >= Kn_ref are the

@@ -300,7 +300,7 @@ class Dsmc:
         return loss.value
 
     def mlp_apply_judged(self, fields, hot, kngll, mask, group=None, z: float = 3.0, min_samples: int = 4,
-                         rel: float = 0.25):
+                         rel: float = 0.1):
         """(HoT [ncells x 12], judge, cells given the network's HoT): the
         network where its group's running residuals against the DSMC HoT
         bound its bias below rel of the DSMC terms (with z standard errors of

@@ -181,7 +181,7 @@ def test_judge_keeps_the_network_only_where_it_agrees_with_dsmc():
     """The statistical judge (the DSMC terms judge the network): with
     unbiased, slightly noisy DSMC terms the network is used once a group
     holds enough residuals to bound its bias below the terms' own size; with
-    a bias of 100 noise units it is rejected at a quarter of the terms; a
+    a bias of 10^4 noise units it is rejected at a quarter of the terms; a
     rejected cell keeps the DSMC HoT and an accepted one the network's."""
     cfg, g, f, hot, kn_g, mask = _data(seed=5)
     m = mask.cpu().numpy().astype(bool)
@@ -190,7 +190,7 @@ def test_judge_keeps_the_network_only_where_it_agrees_with_dsmc():
     rng = np.random.default_rng(0)
     counts, res, ys = [], [], []
     for it in range(8):
-        h = _judge_inputs(g, f, hot, kn_g, mask, rng, 0.0, 0.01)
+        h = _judge_inputs(g, f, hot, kn_g, mask, rng, 0.0, 1e-4)
         out, _, nnet = g.mlp_apply_judged(f, h, kn_g, mask, z=3.0, min_samples=4, rel=1.0)
         counts.append(nnet)
         o, hn, nt = out.cpu().numpy(), h.cpu().numpy(), net.cpu().numpy()
@@ -200,13 +200,13 @@ def test_judge_keeps_the_network_only_where_it_agrees_with_dsmc():
     assert counts[:3] == [0, 0, 0] and counts[-1] >= 0.7 * m.sum(), counts
     g.mlp_judge_reset()
     for it in range(8):
-        h = _judge_inputs(g, f, hot, kn_g, mask, rng, 1.0, 0.01)
+        h = _judge_inputs(g, f, hot, kn_g, mask, rng, 1.0, 1e-4)
         _, _, nnet = g.mlp_apply_judged(f, h, kn_g, mask, z=3.0, min_samples=4, rel=0.25)
     assert nnet <= 0.05 * m.sum(), nnet
     # pooled groups: all cells of one group from the first call on
     g.mlp_judge_reset()
     grp = torch.zeros(g.ncells, dtype=torch.int32)
-    h = _judge_inputs(g, f, hot, kn_g, mask, rng, 0.0, 0.01)
+    h = _judge_inputs(g, f, hot, kn_g, mask, rng, 0.0, 1e-4)
     _, _, nnet = g.mlp_apply_judged(f, h, kn_g, mask, group=grp, z=3.0, min_samples=4, rel=1e6)
     assert nnet >= 0.9 * m.sum(), (nnet, m.sum())
 
@@ -216,7 +216,7 @@ def test_dig_with_judged_network_reaches_steady_no_later_than_dig():
     cell against the DSMC terms, pooled over the replicas of each cell)
     reaches 1 % field error on the 1D Couette flow at Kn 0.1 no later than
     DIG without it (to the 100-step window of the measurement): where the
-    judge cannot bound the network's bias below a quarter of the DSMC terms,
+    judge cannot bound the network's bias below a tenth of the DSMC terms,
     the DSMC terms are used."""
     from paper_2501_10965_gb300 import dig
     cfg = W.couette_1d(kn=0.1, kn_ref=0.01, n_s=50)
