@@ -100,8 +100,15 @@ typedef struct dsmc_config {
    * the one-sided flux of a drifting Maxwellian.  lx, ly are not used; ppc
    * is the mean number of particles per cell, the weight F = init_rho x
    * (annulus area / cells) / ppc, and cell c starts with Iround(init_rho
-   * V_c / F) particles.  Single case only; dsmc_hot, synth_solve,
-   * dig_correct and the HoT network calls return DSMC_ERR_ARG on it. */
+   * V_c / F) particles.  Single case only; synth_solve returns
+   * DSMC_ERR_ARG on it (dsmc_hot, dig_correct and the HoT network work on
+   * its polar gradients and cell volumes).
+   * DSMC_MESH_REFINED is the wall-refined 2D box of Sec. 4.1: the box's
+   * walls, nx x ny cells whose widths grow geometrically by the factor q =
+   * stretch from both walls of each axis to the middle (widths proportional
+   * to q^min(i, n-1-i), summing to lx or ly); ppc is the mean per cell, F
+   * = init_rho lx ly / (nx ny ppc), cell c starts with Iround(init_rho V_c
+   * / F) particles.  Single case only; synth_solve returns DSMC_ERR_ARG. */
   int32_t mesh;
   /* 1: reserve workspace for the 2D synthetic solve of a single box case
    * (synth_solve on dim 2; min(nx, ny) <= 500).  Its banded factorisation
@@ -115,6 +122,7 @@ typedef struct dsmc_config {
 
 #define DSMC_MESH_BOX 0
 #define DSMC_MESH_ANNULUS 1
+#define DSMC_MESH_REFINED 2
 
 typedef struct dsmc_handle dsmc_handle;
 

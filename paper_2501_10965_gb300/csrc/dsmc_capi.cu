@@ -48,6 +48,8 @@ struct dsmc_handle {
   // annulus tables (device): squared ring radii, rays, outer-face
   // directions, cell volumes, in FP64 and FP32
   double *ann_r2t_d = nullptr, *ann_ray_d = nullptr, *ann_fn_d = nullptr, *ann_vol_d = nullptr;
+  double *ref_xe_d = nullptr, *ref_ye_d = nullptr;  // wall-refined box: cell edges (volumes in ann_vol_*)
+  float *ref_xe_f = nullptr, *ref_ye_f = nullptr;
   double* ann_mu_d = nullptr;  // expected freestream entries of every outer face per step
   float *ann_r2t_f = nullptr, *ann_ray_f = nullptr, *ann_fn_f = nullptr, *ann_vol_f = nullptr;
   std::string err;
@@ -99,7 +101,10 @@ int validate(const dsmc_config* c, char* why, size_t n) {
   if (c->dim != 1 && c->dim != 2) return snprintf(why, n, "dim must be 1 or 2"), DSMC_ERR_ARG;
   if (c->nx <= 0 || (c->dim == 2 && c->ny <= 0)) return snprintf(why, n, "cell counts must be positive"), DSMC_ERR_ARG;
   if (c->ppc < 0) return snprintf(why, n, "ppc must be >= 0"), DSMC_ERR_ARG;
-  if (c->mesh != DSMC_MESH_BOX && c->mesh != DSMC_MESH_ANNULUS) return snprintf(why, n, "bad mesh"), DSMC_ERR_ARG;
+  if (c->mesh != DSMC_MESH_BOX && c->mesh != DSMC_MESH_ANNULUS && c->mesh != DSMC_MESH_REFINED)
+    return snprintf(why, n, "bad mesh"), DSMC_ERR_ARG;
+  if (c->mesh == DSMC_MESH_REFINED && (c->dim != 2 || !(c->stretch > 0) || c->synth2d != 0))
+    return snprintf(why, n, "the wall-refined box is 2D with stretch > 0 and no synthetic solve"), DSMC_ERR_ARG;
   const bool ann = c->mesh == DSMC_MESH_ANNULUS;
   if (ann) {
     if (c->dim != 2 || c->nx < 3) return snprintf(why, n, "the annulus is 2D with nx >= 3"), DSMC_ERR_ARG;
@@ -275,9 +280,14 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
   ml.scal = cv.take<double>(8);
   ml.count = cv.take<int32_t>(4);
   ml.jacc = cv.take<double>((size_t)pl.ncells * 16);
-  const bool ann = cs[0].mesh == DSMC_MESH_ANNULUS;
+  const bool ann = cs[0].mesh == DSMC_MESH_ANNULUS, ref = cs[0].mesh == DSMC_MESH_REFINED;
   const size_t nr1 = ann ? (size_t)cs[0].ny + 1 : 1, nray = ann ? 2 * ((size_t)cs[0].nx + 1) : 1;
-  const size_t nfn = ann ? 2 * (size_t)cs[0].nx : 1, nvol = ann ? (size_t)pl.ncells : 1;
+  const size_t nfn = ann ? 2 * (size_t)cs[0].nx : 1, nvol = (ann || ref) ? (size_t)pl.ncells : 1;
+  const size_t nxe = ref ? (size_t)cs[0].nx + 1 : 1, nye = ref ? (size_t)cs[0].ny + 1 : 1;
+  double* r_xed = cv.take<double>(nxe);
+  double* r_yed = cv.take<double>(nye);
+  float* r_xef = cv.take<float>(nxe);
+  float* r_yef = cv.take<float>(nye);
   double* a_r2d = cv.take<double>(nr1);
   double* a_rayd = cv.take<double>(nray);
   double* a_fnd = cv.take<double>(nfn);
@@ -288,6 +298,10 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
   float* a_volf = cv.take<float>(nvol);
   double* a_mu = cv.take<double>(ann ? (size_t)cs[0].nx : 1);
   if (h) {
+    h->ref_xe_d = r_xed;
+    h->ref_ye_d = r_yed;
+    h->ref_xe_f = r_xef;
+    h->ref_ye_f = r_yef;
     h->ann_mu_d = a_mu;
     h->ann_r2t_d = a_r2d;
     h->ann_ray_d = a_rayd;
@@ -353,6 +367,19 @@ AnnTables ann_tables(const dsmc_config* c) {
   return t;
 }
 
+// Wall-refined box: cell edges along an axis of n cells and length L, widths
+// proportional to q^min(i, n-1-i) (growing by q from both walls to the
+// middle), scaled to sum to L; e[0] = 0, e[n] = L
+std::vector<double> refined_edges(int n, double L, double q) {
+  std::vector<double> e(n + 1);
+  double sum = 0.0;
+  for (int i = 0; i < n; ++i) sum += std::pow(q, (double)(i < n - 1 - i ? i : n - 1 - i));
+  e[0] = 0.0;
+  for (int i = 0; i < n; ++i) e[i + 1] = e[i] + L * std::pow(q, (double)(i < n - 1 - i ? i : n - 1 - i)) / sum;
+  e[n] = L;
+  return e;
+}
+
 template <typename T>
 void fill_params(const dsmc_config* c, Params<T>& p, CellParams& cp) {
   const double w = c->omega, a = c->alpha;
@@ -408,8 +435,9 @@ void fill_params(const dsmc_config* c, Params<T>& p, CellParams& cp) {
   p.init_tr = (T)c->init_tr;
   for (int q = 0; q < 3; ++q) p.init_u[q] = (T)c->init_u[q];
   p.init_rho = (T)c->init_rho;
-  p.mesh = ann ? 1 : 0;
-  p.r2t = p.ray = p.fnrm = p.vol = nullptr;  // annulus tables: set_ann_tables
+  p.mesh = ann ? 1 : (c->mesh == DSMC_MESH_REFINED ? 2 : 0);
+  p.r2t = p.ray = p.fnrm = p.vol = nullptr;  // annulus / refined-box tables: set_ann_tables, set_ref_tables
+  p.xe = p.ye = nullptr;
   p.r_in = (T)c->r_in;
   p.r_out = (T)c->r_out;
   p.fs_rho = (T)c->fs_rho;
@@ -441,6 +469,7 @@ void fill_params(const dsmc_config* c, Params<T>& p, CellParams& cp) {
   cp.mesh = p.mesh;
   cp.vol = nullptr;
   cp.r2t = nullptr;
+  cp.xe = cp.ye = nullptr;
 }
 
 // annulus: upload the tables (FP64 and FP32) and point the parameters at them
@@ -474,6 +503,52 @@ int set_ann_tables(dsmc_handle* h) {
   h->cp.vol = h->ann_vol_d;
   h->cp.r2t = h->ann_r2t_d;
   return DSMC_OK;
+}
+
+// wall-refined box: upload the edge and volume tables (FP64 and FP32) and
+// point the parameters at them
+int set_ref_tables(dsmc_handle* h) {
+  const dsmc_config* c = &h->cfg;
+  const std::vector<double> xe = refined_edges(c->nx, c->lx, c->stretch);
+  const std::vector<double> ye = refined_edges(c->ny, c->ly, c->stretch);
+  std::vector<double> vol((size_t)c->nx * c->ny);
+  for (int j = 0; j < c->ny; ++j)
+    for (int i = 0; i < c->nx; ++i) vol[(size_t)j * c->nx + i] = (xe[i + 1] - xe[i]) * (ye[j + 1] - ye[j]);
+  auto f32 = [](const std::vector<double>& v) {
+    std::vector<float> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+    return o;
+  };
+  const std::vector<float> xef = f32(xe), yef = f32(ye), volf = f32(vol);
+  cudaStream_t st = h->stream;
+  cudaMemcpyAsync(h->ref_xe_d, xe.data(), sizeof(double) * xe.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ref_ye_d, ye.data(), sizeof(double) * ye.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ann_vol_d, vol.data(), sizeof(double) * vol.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ref_xe_f, xef.data(), sizeof(float) * xef.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ref_ye_f, yef.data(), sizeof(float) * yef.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ann_vol_f, volf.data(), sizeof(float) * volf.size(), cudaMemcpyHostToDevice, st);
+  const cudaError_t e = cudaStreamSynchronize(st);  // the host vectors die here
+  if (e != cudaSuccess) return set_err(h, DSMC_ERR_CUDA, "refined-box tables: %s", cudaGetErrorString(e));
+  h->pd.xe = h->ref_xe_d;
+  h->pd.ye = h->ref_ye_d;
+  h->pd.vol = h->ann_vol_d;
+  h->pf.xe = h->ref_xe_f;
+  h->pf.ye = h->ref_ye_f;
+  h->pf.vol = h->ann_vol_f;
+  h->cp.vol = h->ann_vol_d;
+  h->cp.xe = h->ref_xe_d;
+  h->cp.ye = h->ref_ye_d;
+  return DSMC_OK;
+}
+
+// cell volumes of the wall-refined box (host)
+std::vector<double> refined_volumes(const dsmc_config* c) {
+  const std::vector<double> xe = refined_edges(c->nx, c->lx, c->stretch);
+  const std::vector<double> ye = refined_edges(c->ny, c->ly, c->stretch);
+  std::vector<double> vol((size_t)c->nx * c->ny);
+  for (int j = 0; j < c->ny; ++j)
+    for (int i = 0; i < c->nx; ++i) vol[(size_t)j * c->nx + i] = (xe[i + 1] - xe[i]) * (ye[j + 1] - ye[j]);
+  return vol;
 }
 
 double sgmax0(const dsmc_config* c, double c_sigma) {
@@ -525,13 +600,14 @@ int init_state(dsmc_handle* h, State<T>& s, Params<T>& p0, Params<T>* d_p) {
   std::vector<int64_t> woff(ncases);
   int64_t total = 0, wacc = 0;
   int32_t slot = 0;
-  // annulus (one case): the initial count of every cell, drawn on the device
-  const bool ann = h->cfg.mesh == DSMC_MESH_ANNULUS;
+  // annulus, wall-refined box (one case): the initial count of every cell,
+  // drawn on the device from its volume
+  const bool ann = h->cfg.mesh != DSMC_MESH_BOX;
   std::vector<int32_t> counts;
   std::vector<double> vol;
   if (ann) {
     counts.resize(nc);
-    vol = ann_tables(&h->cfg).vol;
+    vol = h->cfg.mesh == DSMC_MESH_ANNULUS ? ann_tables(&h->cfg).vol : refined_volumes(&h->cfg);
     Ops<T>::ann_counts(h->pd, nc, s.nt, st);
     cudaMemcpyAsync(counts.data(), s.nt, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, st);
     const cudaError_t e = cudaStreamSynchronize(st);
@@ -567,7 +643,7 @@ int init_state(dsmc_handle* h, State<T>& s, Params<T>& p0, Params<T>* d_p) {
   s.pinj = h->pd;
   s.inj_mu = nullptr;
   s.inj_max = 0;
-  if (ann) {
+  if (h->cfg.mesh == DSMC_MESH_ANNULUS) {
     // expected entries per face and step, and a bound on one step's entries
     std::vector<double> mu(h->cfg.nx);
     Ops<T>::inflow_means(h->pd, h->ann_mu_d, st);
@@ -668,7 +744,7 @@ int init_cases(const dsmc_config* cfgs, int ncases, void* dev_workspace, size_t 
     const int rc = validate(&cfgs[k], why, sizeof why);
     if (rc) return rc;
     if (cfgs[k].dim != cfgs[0].dim || cfgs[k].precision != cfgs[0].precision) return DSMC_ERR_ARG;
-    if (cfgs[k].mesh == DSMC_MESH_ANNULUS && ncases != 1) return DSMC_ERR_ARG;  // the annulus runs alone
+    if (cfgs[k].mesh != DSMC_MESH_BOX && ncases != 1) return DSMC_ERR_ARG;  // the annulus, the refined box run alone
     if (cfgs[k].synth2d && ncases != 1) return DSMC_ERR_ARG;                    // so does the 2D solve
     // the FP32 fused step has its d_r = 3 / VSS instantiation for single cases only
     if (ncases != 1 && cfgs[k].precision == DSMC_PREC_FP32 && (cfgs[k].d_r != 2.0 || cfgs[k].alpha != 1.0))
@@ -701,8 +777,8 @@ int init_cases(const dsmc_config* cfgs, int ncases, void* dev_workspace, size_t 
   fill_params<double>(&h->cfg, h->pd, h->cp);
   fill_params<float>(&h->cfg, h->pf, h->cp);
   int r;
-  if (h->cfg.mesh == DSMC_MESH_ANNULUS) {
-    r = set_ann_tables(h);
+  if (h->cfg.mesh == DSMC_MESH_ANNULUS || h->cfg.mesh == DSMC_MESH_REFINED) {
+    r = h->cfg.mesh == DSMC_MESH_ANNULUS ? set_ann_tables(h) : set_ref_tables(h);
     if (r) {
       delete h;
       return r;
@@ -744,7 +820,7 @@ int dsmc_batch_workspace_size(const dsmc_config* cfgs, int ncases, size_t* bytes
     const int rc = validate(&cfgs[k], why, sizeof why);
     if (rc) return rc;
     if (cfgs[k].dim != cfgs[0].dim || cfgs[k].precision != cfgs[0].precision) return DSMC_ERR_ARG;
-    if (cfgs[k].mesh == DSMC_MESH_ANNULUS && ncases != 1) return DSMC_ERR_ARG;
+    if (cfgs[k].mesh != DSMC_MESH_BOX && ncases != 1) return DSMC_ERR_ARG;
     if (cfgs[k].synth2d && ncases != 1) return DSMC_ERR_ARG;
     if (ncases != 1 && cfgs[k].precision == DSMC_PREC_FP32 && (cfgs[k].d_r != 2.0 || cfgs[k].alpha != 1.0))
       return DSMC_ERR_ARG;
@@ -854,7 +930,8 @@ static int synth_solve_2d(dsmc_handle* h, const double* dev_fields, const double
 int synth_solve(dsmc_handle* h, const double* dev_fields, const double* dev_hot, double* dev_out, int* host_iters,
                 double* host_resid) {
   if (!h || !dev_fields || !dev_hot || !dev_out) return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  if (h->cfg.mesh != DSMC_MESH_BOX) return set_err(h, DSMC_ERR_ARG, "synth_solve: not on the annulus");
+  if (h->cfg.mesh != DSMC_MESH_BOX)
+    return set_err(h, DSMC_ERR_ARG, "synth_solve: only on the uniform box (not the annulus or the refined box)");
   if (h->cfg.dim == 2) return synth_solve_2d(h, dev_fields, dev_hot, dev_out, host_iters, host_resid);
   int n_m = 0;
   double tol = 1.0;
@@ -1029,7 +1106,7 @@ int dsmc_get_flow(dsmc_handle* h, int64_t* out2) {
 
 int dsmc_get_volumes(dsmc_handle* h, double* host_out) {
   if (!h || !host_out) return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  if (h->cfg.mesh == DSMC_MESH_ANNULUS) {
+  if (h->cfg.mesh != DSMC_MESH_BOX) {
     cudaMemcpyAsync(host_out, h->ann_vol_d, sizeof(double) * h->ncells, cudaMemcpyDeviceToHost, h->stream);
     return sync_check(h, "dsmc_get_volumes");
   }

@@ -60,6 +60,9 @@ struct Params {
   const T* ray;   // nx + 1 rays (cos, sin) at 2 pi k / nx; ray nx = ray 0
   const T* fnrm;  // nx outer-face centre directions (cos, sin)
   const T* vol;   // cell volumes (null on the box: vcell)
+  // mesh 2: the wall-refined box, nx + 1 and ny + 1 cell edges
+  const T* xe;
+  const T* ye;
   T r_in, r_out;
   T fs_rho, fs_t, fs_u[3];  // freestream entering through the outer circle
 };
@@ -333,8 +336,21 @@ __device__ __forceinline__ long long iround(T x, T u) {
   return (long long)f + ((u < x - f) ? 1 : 0);
 }
 
+// the largest i with e[i] <= v, clamped to [0, n - 1]
+template <typename T>
+__device__ __forceinline__ int edge_index(const T* e, int n, T v) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (e[mid] <= v) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <typename T, int DIM>
 __device__ __forceinline__ int cell_of(const Params<T>& p, T x, T y) {
+  if (DIM == 2 && p.mesh == 2) return edge_index(p.ye, p.ny, y) * p.nx + edge_index(p.xe, p.nx, x);
   int ix = (int)(x * p.sx);
   ix = ix < 0 ? 0 : (ix > p.nx - 1 ? p.nx - 1 : ix);
   if (DIM == 1) return ix;

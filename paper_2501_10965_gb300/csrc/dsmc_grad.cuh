@@ -39,13 +39,33 @@ __device__ __forceinline__ void grad_ann(const CellParams& cp, int c, int lc, F 
   *gy = st * dr + ct * dt;
 }
 
+// d/dx at cell i of a line with cell edges e (n cells; neighbours at
+// cell-index distance `step`): the three-point formula on the unequal
+// spacing of the cell centres, one-sided first differences at the ends
+template <typename F>
+__device__ __forceinline__ double d_nonuniform(const double* e, int n, int i, int c, int step, F f) {
+  auto xc = [&](int q) { return 0.5 * (e[q] + e[q + 1]); };
+  if (n < 2) return 0.0;
+  if (i == 0) return (f(c + step) - f(c)) / (xc(1) - xc(0));
+  if (i == n - 1) return (f(c) - f(c - step)) / (xc(n - 1) - xc(n - 2));
+  const double hm = xc(i) - xc(i - 1), hp = xc(i + 1) - xc(i);
+  return (hm * hm * f(c + step) - hp * hp * f(c - step) + (hp * hp - hm * hm) * f(c)) / (hp * hm * (hp + hm));
+}
+
 // Cell-centred gradient of field value f(cell): central inside, one-sided
 // first difference in the first/last cell of a line, 0 with a single cell;
-// on the annulus, grad_ann.
+// on the annulus, grad_ann; on the wall-refined box, the three-point
+// formula on the unequal cell widths along each axis.
 template <typename F>
 __device__ __forceinline__ void grad2(const CellParams& cp, int c, int lc, F f, double* gx, double* gy) {
   if (cp.mesh == 1) {
     grad_ann(cp, c, lc, f, gx, gy);
+    return;
+  }
+  if (cp.mesh == 2) {
+    const int ix = lc % cp.nx, iy = lc / cp.nx;
+    *gx = d_nonuniform(cp.xe, cp.nx, ix, c, 1, f);
+    *gy = d_nonuniform(cp.ye, cp.ny, iy, c, cp.nx, f);
     return;
   }
   const int ix = lc % cp.nx, iy = lc / cp.nx;

@@ -36,6 +36,8 @@ struct CellParams {
   int mesh;            // 0 Cartesian box, 1 annulus (single case)
   const double* vol;   // annulus: cell volumes (null on the box: vcell)
   const double* r2t;   // annulus: ny + 1 squared ring radii (nx sectors x ny rings)
+  const double* xe;    // wall-refined box: nx + 1 and ny + 1 cell edges
+  const double* ye;
 };
 
 // Per-case tables of a handle (device memory).  A single simulation is one

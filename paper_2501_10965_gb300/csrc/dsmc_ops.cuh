@@ -142,6 +142,10 @@ __global__ void k_init_cells(Cases<T> cases, int ncells, PBuf<T> b, const int32_
       const T th = T(2.0 * PI_D) * ((T)ix + a1) / (T)p.nx;
       b.x[slot] = r * m_cos(th);
       b.y[slot] = r * m_sin(th);
+    } else if (DIM == 2 && p.mesh == 2) {
+      // wall-refined box: uniform between the cell's edges
+      b.x[slot] = p.xe[ix] + a0 * (p.xe[ix + 1] - p.xe[ix]);
+      b.y[slot] = p.ye[iy] + a1 * (p.ye[iy + 1] - p.ye[iy]);
     } else {
       b.x[slot] = ((T)ix + a0) * p.dx;
       b.y[slot] = (DIM == 2) ? ((T)iy + a1) * p.dy : T(0);
@@ -679,12 +683,18 @@ __device__ __forceinline__ void append_particle(const Params<float>& p, const PB
 // into the 3 x 3 neighbourhood of `cell` (4 = stays), or 9 for a farther cell.
 template <int DIM>
 __device__ __forceinline__ int neighbour_code(const Params<float>& p, int ix, int iy, float x, float y) {
-  int jx = (int)(x * p.sx);
-  jx = jx < 0 ? 0 : (jx > p.nx - 1 ? p.nx - 1 : jx);
-  int jy = 0;
-  if (DIM == 2) {
-    jy = (int)(y * p.sy);
-    jy = jy < 0 ? 0 : (jy > p.ny - 1 ? p.ny - 1 : jy);
+  int jx, jy = 0;
+  if (DIM == 2 && p.mesh == 2) {
+    // wall-refined box: the cell from its edge tables
+    jx = edge_index(p.xe, p.nx, x);
+    jy = edge_index(p.ye, p.ny, y);
+  } else {
+    jx = (int)(x * p.sx);
+    jx = jx < 0 ? 0 : (jx > p.nx - 1 ? p.nx - 1 : jx);
+    if (DIM == 2) {
+      jy = (int)(y * p.sy);
+      jy = jy < 0 ? 0 : (jy > p.ny - 1 ? p.ny - 1 : jy);
+    }
   }
   const int dx = jx - ix, dy = jy - iy;
   if (dx < -1 || dx > 1 || dy < -1 || dy > 1) return 9;
@@ -1470,6 +1480,10 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
         const double th = 2.0 * PI_D * ((double)ix + sp.u(1)) / (double)cp.nx;
         out.x[w] = (T)(r * cos(th));
         out.y[w] = (T)(r * sin(th));
+      } else if (cp.mesh == 2) {
+        // wall-refined box: uniform between the cell's edges
+        out.x[w] = (T)(cp.xe[ix] + sp.u(0) * (cp.xe[ix + 1] - cp.xe[ix]));
+        out.y[w] = (T)(cp.ye[iy] + sp.u(1) * (cp.ye[iy + 1] - cp.ye[iy]));
       } else {
         out.x[w] = (T)(((double)ix + sp.u(0)) * cp.dx);
         out.y[w] = (T)((cp.dim == 2) ? ((double)iy + sp.u(1)) * cp.dy : 0.0);

@@ -22,7 +22,7 @@ ABI_VERSION = 2
 NFIELDS, NHOT, NTARGET, NMOM = 18, 12, 6, 17
 PREC = {"fp64": 0, "fp32": 1}
 WALL = {"diffuse": 0, "specular": 1}
-MESH = {"box": 0, "annulus": 1}
+MESH = {"box": 0, "annulus": 1, "refined": 2}
 
 # every symbol the header declares
 SYMBOLS = ["dsmc_workspace_size", "dsmc_init", "dsmc_destroy", "dsmc_last_error", "dsmc_step", "dsmc_sample",

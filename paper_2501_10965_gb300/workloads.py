@@ -52,7 +52,9 @@ def base_config(**kw) -> dict:
         # mesh "box": the Cartesian box above; "annulus": r_in <= r <= r_out
         # around a cylinder (nx angular x ny radial cells, radial widths
         # growing by `stretch` per ring), wall 0 the cylinder, freestream
-        # (fs_rho, fs_t, fs_u) entering through the outer circle
+        # (fs_rho, fs_t, fs_u) entering through the outer circle;
+        # "refined": the box with cell widths growing by `stretch` from both
+        # walls of each axis to the middle
         "mesh": "box",
         "r_in": 0.5, "r_out": 5.5, "stretch": 1.0,
         "fs_rho": 1.0, "fs_t": 1.0, "fs_u": (0.0, 0.0, 0.0),
@@ -152,6 +154,39 @@ def cylinder_2d(ntheta: int = 400, nr: int = 300, ppc: int = 167, kn: float = 0.
                       lx=2.0 * math.pi, ly=r_out - r_in, r_in=r_in, r_out=r_out, stretch=q,
                       walls=[_wall(T=t_wall), _wall(), _wall(), _wall()],
                       init_u=(u_inf, 0.0, 0.0), fs_rho=1.0, fs_t=1.0, fs_u=(u_inf, 0.0, 0.0),
+                      precision="fp32", dt=dt, kn_ref=0.05, n_s=100)
+    cfg.update(kw)
+    return cfg
+
+
+def refined_stretch(n: int, length: float, d_min: float) -> float:
+    """Growth factor q of the wall-refined box whose first cell at each wall
+    (of n along an axis of this length, widths proportional to
+    q^min(i, n-1-i)) is d_min wide (bisection)."""
+    def first(q):
+        m = [min(i, n - 1 - i) for i in range(n)]
+        return length / sum(q ** k for k in m)
+    lo, hi = 1.0, 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if first(mid) > d_min:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def cavity_2d_refined(nx: int = 100, ny: int = 100, ppc: int = 50, kn: float = 0.01, dx_min: float = 0.001,
+                      lid: float = 50.0 / SPEED_REF, **kw) -> dict:
+    """Lid-driven cavity on the wall-refined grid of Sec. 4.1 (the DIG mesh
+    of its Kn 0.01 case: 100 x 100 cells, first cell 0.001 at every wall),
+    ~ppc particles per cell on average (cell populations follow the cell
+    areas), lid at 50 m/s (0.176), diffuse walls at T0, FP32; dt from the
+    smallest cell."""
+    q = refined_stretch(nx, 1.0, dx_min)
+    dt = min(0.3 * dx_min / (lid + 3.0), 0.5 * kn * math.sqrt(math.pi / 8.0))
+    cfg = base_config(dim=2, nx=nx, ny=ny, ppc=ppc, kn=kn, mesh="refined", stretch=q, lx=1.0, ly=1.0,
+                      walls=[_wall(), _wall(), _wall(), _wall(u=(lid, 0.0, 0.0))],
                       precision="fp32", dt=dt, kn_ref=0.05, n_s=100)
     cfg.update(kw)
     return cfg

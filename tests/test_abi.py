@@ -97,6 +97,11 @@ def test_synth2d_workspace_and_validation():
     assert _ws(W.cavity_2d(nx=2, ny=8, ppc=4, synth2d=True))[0] == -1
     assert _ws(W.cavity_2d(nx=501, ny=501, ppc=1, synth2d=True))[0] == -1
     assert _ws(W.cylinder_2d(ntheta=24, nr=8, ppc=4, synth2d=True))[0] == -1
+    # the wall-refined box: 2D, stretch > 0, no synthetic solve
+    assert _ws(W.cavity_2d_refined(nx=14, ny=12, ppc=4, dx_min=0.02))[0] == 0
+    assert _ws(W.cavity_2d_refined(nx=14, ny=12, ppc=4, dx_min=0.02, synth2d=True))[0] == -1
+    assert _ws(W.cavity_2d_refined(nx=14, ny=12, ppc=4, dx_min=0.02, stretch=0.0))[0] == -1
+    assert _ws(W.cavity_2d_refined(nx=14, ny=12, ppc=4, dx_min=0.02, dim=1))[0] == -1
     L = dsmc.load()
     cs = (dsmc.DsmcConfig * 2)(dsmc.make_config(W.cavity_2d(nx=8, ny=6, ppc=4, synth2d=True)),
                                dsmc.make_config(W.cavity_2d(nx=8, ny=6, ppc=4, synth2d=True)))
