@@ -1191,17 +1191,21 @@ int or_dig_correct(or_state *S, const double *target) {
         ++d;
       }
     }
-    /* step iii: u*, T_t*, T_r* of the current particles, Eq. (DSMC_macroscopic) */
+    /* step iii: u*, T_t*, T_r* of the current particles, Eq. (DSMC_macroscopic).
+       The mean is taken about the first particle's velocity, so that copies
+       of one particle (a cell that held one particle and was refilled) have
+       u* equal to that velocity and T_t* = 0 exactly (then a = 1). */
     int64_t np = d - d0;
     if (np > 0) {
+      const double rx = S->tvx[d0], ry = S->tvy[d0], rz = S->tvz[d0];
       double sx = 0, sy = 0, sz = 0, si = 0;
       for (int64_t q = d0; q < d; ++q) {
-        sx += S->tvx[q];
-        sy += S->tvy[q];
-        sz += S->tvz[q];
+        sx += S->tvx[q] - rx;
+        sy += S->tvy[q] - ry;
+        sz += S->tvz[q] - rz;
         si += S->tir[q];
       }
-      double ux = sx / (double)np, uy = sy / (double)np, uz = sz / (double)np;
+      double ux = rx + sx / (double)np, uy = ry + sy / (double)np, uz = rz + sz / (double)np;
       double c2 = 0;
       for (int64_t q = d0; q < d; ++q) {
         double cx = S->tvx[q] - ux, cy = S->tvy[q] - uy, cz = S->tvz[q] - uz;

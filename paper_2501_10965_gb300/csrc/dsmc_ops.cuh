@@ -1374,24 +1374,6 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
   const int s0 = start_in[cell], n = cnt_in[cell], d0 = start_out[cell], ntg = nt[cell];
   const double* t = target + (size_t)cell * 6;
   const int ix = lcell % cp.nx, iy = lcell / cp.nx;
-  // FP32 particles: the sums of step iii are taken in FP64 while the new
-  // population is written, of w = v - u_target, so that the second moment
-  // about the mean, E[w^2] - E[w]^2, keeps its digits however far the cell's
-  // mean lies from the target; the factors of step iv are FP64 too.  The
-  // FP64 layout sums in a second and third pass below.
-  constexpr bool ONE_PASS = sizeof(T) == 4;
-  const double tux = t[1], tuy = t[2], tuz = t[3];
-  double swx = 0.0, swy = 0.0, swz = 0.0, sir = 0.0, sw2 = 0.0;
-  auto tally = [&](T vx, T vy, T vz, T ir) {
-    if constexpr (ONE_PASS) {
-      const double wx = (double)vx - tux, wy = (double)vy - tuy, wz = (double)vz - tuz;
-      swx += wx;
-      swy += wy;
-      swz += wz;
-      sir += (double)ir;
-      sw2 = fma(wx, wx, fma(wy, wy, fma(wz, wz, sw2)));
-    }
-  };
   int32_t* idx = (n <= tile) ? reinterpret_cast<int32_t*>(smem) + (size_t)warp * tile * 2 : idx_g + s0;
   int32_t* rm = (n <= tile) ? reinterpret_cast<int32_t*>(smem) + (size_t)warp * tile * 2 + tile : nullptr;
   // step ii
@@ -1456,7 +1438,6 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
         out.vy[w] = vy;
         out.vz[w] = vz;
         out.ir[w] = ir;
-        tally(vx, vy, vz, ir);
       }
       kept_before += __popc(m);
     }
@@ -1469,7 +1450,6 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
       out.vy[d0 + q] = vy;
       out.vz[d0 + q] = vz;
       out.ir[d0 + q] = ir;
-      tally(vx, vy, vz, ir);
     }
     for (int q = lane; q < ntg - n; q += 32) {
       Stream<double> sp(TAG_DIG_POS, (uint32_t)q, (uint32_t)lcell, iter, cp.k0, cp.k1);
@@ -1497,7 +1477,6 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
         out.vy[w] = vy;
         out.vz[w] = vz;
         out.ir[w] = ir;
-        tally(vx, vy, vz, ir);
       } else {
         double n1, n2, n3, n4;
         box_muller(sp.u(2), sp.u(3), &n1, &n2);
@@ -1509,48 +1488,24 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
         out.vy[w] = vy;
         out.vz[w] = vz;
         out.ir[w] = ir;
-        tally(vx, vy, vz, ir);
       }
     }
   }
   __syncwarp();
-  // step iii: u*, T_t*, T_r* of the new population
+  // step iii: u*, T_t*, T_r* of the new population, in FP64 in both layouts
+  // (the factors of step iv too; FP32 particles are rounded once).  The mean
+  // is taken about the first particle's velocity: copies of one particle (a
+  // cell that held one particle and was refilled) then give u* equal to that
+  // velocity and T_t* = 0 exactly (a = 1), and the second pass about u*
+  // keeps the digits of the thermal spread.
   const int np = ntg;
-  if constexpr (ONE_PASS) {
-    if (np > 0) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        swx += __shfl_xor_sync(FULL, swx, o);
-        swy += __shfl_xor_sync(FULL, swy, o);
-        swz += __shfl_xor_sync(FULL, swz, o);
-        sir += __shfl_xor_sync(FULL, sir, o);
-        sw2 += __shfl_xor_sync(FULL, sw2, o);
-      }
-      // u* = u_target + m, T_t* = (E[w^2] - m^2) / 3 with m = E[w]
-      const double inv = 1.0 / (double)np;
-      const double mx = swx * inv, my = swy * inv, mz = swz * inv;
-      const double tts = (sw2 * inv - (mx * mx + my * my + mz * mz)) * (1.0 / 3.0);
-      const double trs = 2.0 * sir * inv / cp.d_r;
-      // step iv: v <- a v + b = u_target + a (v - u*), I_r <- c I_r, in FP64
-      // and rounded once to the FP32 particle
-      const double a = (np >= 2 && tts > 0.0) ? sqrt(t[4] / tts) : 1.0;
-      const double bx = tux - (tux + mx) * a, by = tuy - (tuy + my) * a, bz = tuz - (tuz + mz) * a;
-      const double cc = (trs > 0.0) ? t[5] / trs : 1.0;
-      for (int q = lane; q < np; q += 32) {
-        const int w = d0 + q;
-        out.vx[w] = (T)fma(a, (double)out.vx[w], bx);
-        out.vy[w] = (T)fma(a, (double)out.vy[w], by);
-        out.vz[w] = (T)fma(a, (double)out.vz[w], bz);
-        out.ir[w] = (T)(cc * (double)out.ir[w]);
-        if (cellof_out) cellof_out[w] = cell;
-      }
-    }
-  } else if (np > 0) {
+  if (np > 0) {
+    const double rx = (double)out.vx[d0], ry = (double)out.vy[d0], rz = (double)out.vz[d0];
     double sx = 0, sy = 0, sz = 0, si = 0;
     for (int q = lane; q < np; q += 32) {
-      sx += (double)out.vx[d0 + q];
-      sy += (double)out.vy[d0 + q];
-      sz += (double)out.vz[d0 + q];
+      sx += (double)out.vx[d0 + q] - rx;
+      sy += (double)out.vy[d0 + q] - ry;
+      sz += (double)out.vz[d0 + q] - rz;
       si += (double)out.ir[d0 + q];
     }
 #pragma unroll
@@ -1560,7 +1515,7 @@ __global__ void __launch_bounds__(WPB * 32) k_dig_apply(const CellParams* __rest
       sz += __shfl_xor_sync(FULL, sz, o);
       si += __shfl_xor_sync(FULL, si, o);
     }
-    const double ux = sx / (double)np, uy = sy / (double)np, uz = sz / (double)np;
+    const double ux = rx + sx / (double)np, uy = ry + sy / (double)np, uz = rz + sz / (double)np;
     double c2 = 0;
     for (int q = lane; q < np; q += 32) {
       const double cx = (double)out.vx[d0 + q] - ux, cy = (double)out.vy[d0 + q] - uy,

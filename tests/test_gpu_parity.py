@@ -167,6 +167,40 @@ def test_dig_correct_matches_oracle_fp64():
     _compare_states(_np(g.get_particles()), o.particles(), what="after dig")
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dig_correct_refills_one_particle_cells(precision):
+    """Cells holding one particle that the target refills (Sec. 3.2 ii
+    copies that particle): T_t* = 0, so step iv takes a = 1 and every
+    particle ends at the target velocity, I_r at the target T_r.  FP64:
+    particle states equal the oracle's; FP32: velocities at the target to
+    FP32 rounding.  A mean summed as (sum v) / N leaves T_t* at a
+    rounding-sized positive value and a ~ 1e8 instead."""
+    cfg = W.fourier_1d(nx=4, ppc=10, capacity=10000, precision=precision)
+    g = _gpu(cfg)
+    v = np.array([0.1234567891234, -0.7654321987654, 0.333333333333333])
+    p = {"x": (np.arange(4) + 0.5) / 4, "vx": np.full(4, v[0]), "vy": np.full(4, v[1]), "vz": np.full(4, v[2]),
+         "ir": np.full(4, 0.9)}
+    g.set_particles({k: torch.tensor(a) for k, a in p.items()})
+    c = g.constants()
+    t = np.zeros((4, 6))
+    t[:, 0] = 15 * c["fnum"] / c["vcell"]
+    t[:, 1:4] = [0.0125, -0.0404, -0.0566]
+    t[:, 4] = 1.1
+    t[:, 5] = 0.8
+    g.dig_correct(torch.tensor(t, device="cuda"))
+    a = _np(g.get_particles())
+    assert np.all(np.bincount(a["cell"], minlength=4) == 15)
+    if precision == "fp64":
+        o = oracle.OracleSim(cfg)
+        o.set_particles(p)
+        assert o.dig_correct(t) == 0
+        _compare_states(a, o.particles(), what="one-particle refill")
+    tol = 1e-16 if precision == "fp64" else 1e-8
+    for j, k in enumerate(("vx", "vy", "vz")):
+        assert np.allclose(a[k], t[0, 1 + j], rtol=0, atol=tol), (k, a[k])
+    assert np.allclose(a["ir"], 0.8, rtol=1e-7)
+
+
 def test_dig_correct_rejects_bad_target_gpu():
     from paper_2501_10965_gb300.dsmc import DsmcError
     cfg = W.fourier_1d(nx=10, ppc=10)

@@ -144,6 +144,34 @@ def test_dig_correct_fills_empty_cells_from_target_maxwellian():
     assert np.allclose(m[:, 4], 1.5, rtol=1e-13) and np.allclose(m[:, 5], 0.5, rtol=1e-13)
 
 
+def test_dig_correct_copies_of_one_particle_keep_a_equal_to_one():
+    """A cell holding one particle that the target refills: its copies all
+    share one velocity, so T_t* = 0 and step iv takes a = 1 (reading of the
+    degenerate case); every particle then moves to the target velocity
+    u_target exactly up to one rounding, and I_r is scaled to T_r.  A mean
+    taken as (sum v) / N leaves T_t* at a rounding-sized positive value
+    instead, and a = sqrt(T_t / T_t*) ~ 1e8 sends the velocities to
+    garbage: this catches it."""
+    cfg = W.fourier_1d(nx=4, ppc=10, capacity=10000)
+    sim = oracle.OracleSim(cfg)
+    c = sim.constants()
+    # one particle per cell, velocities whose repeated sums round
+    v = np.array([0.1234567891234, -0.7654321987654, 0.333333333333333])
+    sim.set_particles({"x": (np.arange(4) + 0.5) / 4, "vx": np.full(4, v[0]), "vy": np.full(4, v[1]),
+                       "vz": np.full(4, v[2]), "ir": np.full(4, 0.9)})
+    t = np.zeros((4, 6))
+    t[:, 0] = 15 * c["fnum"] / c["vcell"]
+    t[:, 1:4] = [0.0125, -0.0404, -0.0566]
+    t[:, 4] = 1.1
+    t[:, 5] = 0.8
+    assert sim.dig_correct(t) == 0
+    p = sim.particles()
+    assert np.all(np.bincount(p["cell"], minlength=4) == 15)
+    for j, k in enumerate(("vx", "vy", "vz")):
+        assert np.allclose(p[k], t[0, 1 + j], rtol=0, atol=1e-16), (k, p[k])
+    assert np.allclose(p["ir"], 0.8, rtol=1e-15)
+
+
 # ----------------------------------------------------------------------------
 # steady synthetic equations, 1D
 # ----------------------------------------------------------------------------
