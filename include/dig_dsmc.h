@@ -108,7 +108,9 @@ typedef struct dsmc_config {
    * stretch from both walls of each axis to the middle (widths proportional
    * to q^min(i, n-1-i), summing to lx or ly); ppc is the mean per cell, F
    * = init_rho lx ly / (nx ny ppc), cell c starts with Iround(init_rho V_c
-   * / F) particles.  Single case only; synth_solve returns DSMC_ERR_ARG. */
+   * / F) particles.  Single case only; synth_solve works on it with
+   * synth2d = 1 (differences over the distances between cell centres, each
+   * balance divided by its cell's width, the total mass weighted by V_c). */
   int32_t mesh;
   /* 1: reserve workspace for the 2D synthetic solve of a single box case
    * (synth_solve on dim 2; min(nx, ny) <= 500).  Its banded factorisation
@@ -203,11 +205,12 @@ int dsmc_hot(dsmc_handle *h, const double *dev_fields, double *dev_hot, double *
  * T_r (Dirichlet); total mass equals the sampled mass.  Block cyclic
  * reduction of the block-tridiagonal Newton system.
  *
- * 2D box (single case with synth2d = 1; nx, ny >= 3): unknowns rho, u_x,
+ * 2D box, uniform or wall-refined (single case with synth2d = 1; nx, ny >=
+ * 3): unknowns rho, u_x,
  * u_y, T_t, T_r per cell (u_z keeps its sampled value); cells next to a wall
  * keep the sampled u_x, u_y, T_t, T_r and balance their mass; the four
  * corner cells keep their sampled state and exchange no flux; cell (1, 0)'s
- * mass balance is replaced by the total mass; face fluxes carry a
+ * mass balance is replaced by the total mass (sum rho V_c); face fluxes carry a
  * fourth-difference dissipation of the conserved variables (1/32 of the
  * face's |u_n| + sound speed).  Residual and central-difference Jacobian in
  * FP64; each Newton step solves with a blocked banded LU factorisation

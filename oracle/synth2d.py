@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 The steady form of Eq. (macroscopic_equation) on a rectangle of nx x ny
-uniform cells closed by walls, with the constitutive relations of
+cells closed by walls (uniform, or the wall-refined grid of the cavity case
+of Sec. 4.1, whose widths grow geometrically from each wall), with the constitutive relations of
 Eq. (full_constitutive) (sigma = sigma_NSF + HoT, q = q_NSF + HoT; NSF terms
 of Eq. ns_constitutive, kappa from Eq. kappa_A):
 
@@ -21,7 +22,9 @@ overlap:
 * finite volumes; the flux through a face is the mean of the two cells'
   convective fluxes plus the viscous and heat fluxes from compact normal
   differences and tangential differences averaged from the two cells (central
-  within the domain, one-sided in the first and last row); face viscosity
+  within the domain, one-sided in the first and last row); differences are
+  taken over the distances between the cell centres (the middle of each
+  cell's edges) and a cell's balance divides by its own width; face viscosity
   mu(T_f) with T_f from the face means of T_t and T_r; face HoT the mean of
   the two cells' HoT;
 * a fourth-difference dissipation eps4 * lambda_f * (W[i+2] - 3 W[i+1] +
@@ -35,9 +38,12 @@ overlap:
 * a corner cell touches no interior cell, so its mass balance would fix its
   density through its (near-zero) velocity alone: the four corner cells keep
   their whole sampled state and exchange no flux with their neighbours;
-* the mass balances of the remaining cells then sum to zero identically, and
-  the one of cell 1 is replaced by the total mass (equal to the DSMC
-  sample's), which the closed walls leave undetermined otherwise.
+* the mass balances of the remaining cells then sum (weighted by the cell
+  volumes) to zero identically, and the one of cell 1 is replaced by the
+  total mass sum rho V (equal to the DSMC sample's), which the closed walls
+  leave undetermined otherwise; the row is written as
+  sum_c s_c (rho_c - rho_c,sampled) / n with s_c = n V_c / (L_x L_y) (1 on
+  the uniform grid).
 
 Unknowns per cell: rho, u_x, u_y, T_t, T_r.  Newton's method with a Jacobian
 from central finite differences (25-colouring of the 5 x 5 stencil) and a
@@ -49,7 +55,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .fields import F_RHO, F_U, F_TT, F_TR, kappa_coefficients, mu_ref_of
+from .fields import F_RHO, F_U, F_TT, F_TR, box_edges, kappa_coefficients, mu_ref_of
 
 NV = 5  # rho, u_x, u_y, T_t, T_r
 EPS4 = 1.0 / 32.0
@@ -60,12 +66,51 @@ def _geom(cfg):
     return nx, ny, float(cfg["lx"]) / nx, float(cfg["ly"]) / ny
 
 
-def _dy_cells(f, dy):
-    """d f / d y per cell: central inside, one-sided in the first and last row."""
+def _axis_metrics(n, length, mesh, q):
+    """Along one axis: the cell widths, the distances between neighbouring
+    cell centres (one per interior face) and the denominators of the per-cell
+    tangential derivative (centre distance over the two neighbours inside,
+    to the one neighbour in the first and last cell)."""
+    if mesh == "refined":
+        e = box_edges(n, length, q)
+        w = np.diff(e)
+        c = 0.5 * (e[:-1] + e[1:])
+        dn = c[1:] - c[:-1]
+        den = np.empty(n)
+        den[1:-1] = c[2:] - c[:-2]
+        den[0] = c[1] - c[0]
+        den[-1] = c[-1] - c[-2]
+        return w, dn, den
+    h = length / n
+    den = np.full(n, 2.0 * h)
+    den[0] = den[-1] = h
+    return np.full(n, h), np.full(n - 1, h), den
+
+
+def _metrics(cfg):
+    nx, ny = int(cfg["nx"]), int(cfg["ny"])
+    mesh = cfg.get("mesh", "box")
+    q = float(cfg.get("stretch", 1.0))
+    return (_axis_metrics(nx, float(cfg["lx"]), mesh, q), _axis_metrics(ny, float(cfg["ly"]), mesh, q))
+
+
+def _mass_scale(cfg):
+    """s_c = n V_c / (L_x L_y) per cell (rows y, columns x); None on the
+    uniform grid (s_c = 1)."""
+    if cfg.get("mesh", "box") != "refined":
+        return None
+    (wx, _, _), (wy, _, _) = _metrics(cfg)
+    n = len(wx) * len(wy)
+    return n * np.outer(wy, wx) / (float(cfg["lx"]) * float(cfg["ly"]))
+
+
+def _dy_cells(f, den):
+    """d f / d y per cell (rows along axis 0): central inside, one-sided in
+    the first and last row, over the centre distances in den."""
     g = np.empty_like(f)
-    g[1:-1] = (f[2:] - f[:-2]) / (2.0 * dy)
-    g[0] = (f[1] - f[0]) / dy
-    g[-1] = (f[-1] - f[-2]) / dy
+    g[1:-1] = (f[2:] - f[:-2]) / den[1:-1, None]
+    g[0] = (f[1] - f[0]) / den[0]
+    g[-1] = (f[-1] - f[-2]) / den[-1]
     return g
 
 
@@ -73,7 +118,8 @@ def _face_fluxes(q, h, W, axis, d, dt, cfg, consts):
     """Fluxes (5 components) through the faces normal to ``axis`` (1: x
     faces between columns i and i+1; 0: y faces between rows j and j+1),
     written for the x direction on arrays transposed so that the face normal
-    runs along the last axis."""
+    runs along the last axis.  d: centre distances across the faces (along
+    the last axis); dt: the tangential-derivative denominators (rows)."""
     d_r, omega, mu_ref, kt_c, kr_c, gamma = consts
     rho, un, ut, tt, tr = q  # normal and tangential velocity
     # face means
@@ -120,7 +166,8 @@ def _face_fluxes(q, h, W, axis, d, dt, cfg, consts):
 
 
 def residual(x: np.ndarray, dsmc: np.ndarray, hot: np.ndarray, cfg: dict) -> np.ndarray:
-    nx, ny, dx, dy = _geom(cfg)
+    nx, ny, _, _ = _geom(cfg)
+    (wx, dnx, dtx), (wy, dny, dty) = _metrics(cfg)
     n = nx * ny
     d_r, omega, Z = float(cfg["d_r"]), float(cfg["omega"]), float(cfg["z_rot"])
     mu_ref = mu_ref_of(float(cfg["kn"]))
@@ -134,12 +181,12 @@ def residual(x: np.ndarray, dsmc: np.ndarray, hot: np.ndarray, cfg: dict) -> np.
     W = [rho, rho * ux, rho * uy, rho * e, rho * 0.5 * d_r * tr]
     # x faces: normal x, tangential y; HoT (s_xx, s_xy, q_t,x, q_r,x)
     hx = np.stack([H[..., 0], H[..., 3], H[..., 6], H[..., 9]], axis=-1)
-    Fx = _face_fluxes((rho, ux, uy, tt, tr), hx, W, 1, dx, dy, cfg, consts)
+    Fx = _face_fluxes((rho, ux, uy, tt, tr), hx, W, 1, dnx, dty, cfg, consts)
     # y faces: transpose so that y runs along the last axis; normal y,
     # tangential x; HoT (s_yy, s_xy, q_t,y, q_r,y)
     hy = np.stack([H[..., 1], H[..., 3], H[..., 7], H[..., 10]], axis=-1).transpose(1, 0, 2)
     Wy = [W[0].T, W[2].T, W[1].T, W[3].T, W[4].T]  # (rho, rho u_n, rho u_t, ...) with n = y
-    Fy = _face_fluxes((rho.T, uy.T, ux.T, tt.T, tr.T), hy, Wy, 0, dy, dx, cfg, consts)
+    Fy = _face_fluxes((rho.T, uy.T, ux.T, tt.T, tr.T), hy, Wy, 0, dny, dtx, cfg, consts)
     # momentum components of the y faces: (normal, tangential) = (y, x)
     Fy = [Fy[0].T, Fy[2].T, Fy[1].T, Fy[3].T, Fy[4].T]
     # no flux through the faces of the four corner cells
@@ -150,10 +197,10 @@ def residual(x: np.ndarray, dsmc: np.ndarray, hot: np.ndarray, cfg: dict) -> np.
     div = []
     for k in range(NV):
         dk = np.zeros((ny, nx))
-        dk[:, :-1] += Fx[k] / dx
-        dk[:, 1:] -= Fx[k] / dx
-        dk[:-1, :] += Fy[k] / dy
-        dk[1:, :] -= Fy[k] / dy
+        dk[:, :-1] += Fx[k] / wx[None, :-1]
+        dk[:, 1:] -= Fx[k] / wx[None, 1:]
+        dk[:-1, :] += Fy[k] / wy[:-1, None]
+        dk[1:, :] -= Fy[k] / wy[1:, None]
         div.append(dk)
     T = (3.0 * tt + d_r * tr) / (3.0 + d_r)
     mu = mu_ref * T ** omega
@@ -170,7 +217,11 @@ def residual(x: np.ndarray, dsmc: np.ndarray, hot: np.ndarray, cfg: dict) -> np.
         R[0, cj, ci] = rho[cj, ci] - D[cj, ci, F_RHO]
     # the mass balances of the other cells sum to zero identically: the one of
     # cell 1 is replaced by the total mass
-    R[0, 0, 1] = (rho.sum() - D[..., F_RHO].sum()) / n
+    s = _mass_scale(cfg)
+    if s is None:
+        R[0, 0, 1] = (rho.sum() - D[..., F_RHO].sum()) / n
+    else:
+        R[0, 0, 1] = ((s * rho).sum() - (s * D[..., F_RHO]).sum()) / n
     return R.reshape(-1)
 
 
@@ -212,7 +263,8 @@ def _jacobian(x, dsmc, hot, cfg):
     keep = [t for t in range(len(rows)) if rows[t] != 1]
     rows = [rows[t] for t in keep] + [1] * n
     cols = [cols[t] for t in keep] + list(range(n))
-    vals = [vals[t] for t in keep] + [1.0 / n] * n
+    s = _mass_scale(cfg)
+    vals = [vals[t] for t in keep] + (list(s.ravel() / n) if s is not None else [1.0 / n] * n)
     return sp.csr_matrix((vals, (rows, cols)), shape=(NV * n, NV * n))
 
 

@@ -103,8 +103,8 @@ int validate(const dsmc_config* c, char* why, size_t n) {
   if (c->ppc < 0) return snprintf(why, n, "ppc must be >= 0"), DSMC_ERR_ARG;
   if (c->mesh != DSMC_MESH_BOX && c->mesh != DSMC_MESH_ANNULUS && c->mesh != DSMC_MESH_REFINED)
     return snprintf(why, n, "bad mesh"), DSMC_ERR_ARG;
-  if (c->mesh == DSMC_MESH_REFINED && (c->dim != 2 || !(c->stretch > 0) || c->synth2d != 0))
-    return snprintf(why, n, "the wall-refined box is 2D with stretch > 0 and no synthetic solve"), DSMC_ERR_ARG;
+  if (c->mesh == DSMC_MESH_REFINED && (c->dim != 2 || !(c->stretch > 0)))
+    return snprintf(why, n, "the wall-refined box is 2D with stretch > 0"), DSMC_ERR_ARG;
   const bool ann = c->mesh == DSMC_MESH_ANNULUS;
   if (ann) {
     if (c->dim != 2 || c->nx < 3) return snprintf(why, n, "the annulus is 2D with nx >= 3"), DSMC_ERR_ARG;
@@ -930,8 +930,8 @@ static int synth_solve_2d(dsmc_handle* h, const double* dev_fields, const double
 int synth_solve(dsmc_handle* h, const double* dev_fields, const double* dev_hot, double* dev_out, int* host_iters,
                 double* host_resid) {
   if (!h || !dev_fields || !dev_hot || !dev_out) return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  if (h->cfg.mesh != DSMC_MESH_BOX)
-    return set_err(h, DSMC_ERR_ARG, "synth_solve: only on the uniform box (not the annulus or the refined box)");
+  if (h->cfg.mesh == DSMC_MESH_ANNULUS)
+    return set_err(h, DSMC_ERR_ARG, "synth_solve: not on the annulus (boxes only)");
   if (h->cfg.dim == 2) return synth_solve_2d(h, dev_fields, dev_hot, dev_out, host_iters, host_resid);
   int n_m = 0;
   double tol = 1.0;

@@ -33,7 +33,7 @@ struct CellParams {
   double kappa_t, kappa_r;  // kappa / mu from Eq. (kappa_A)
   double kn_ref;
   uint32_t k0, k1;
-  int mesh;            // 0 Cartesian box, 1 annulus (single case)
+  int mesh;            // 0 Cartesian box, 1 annulus, 2 wall-refined box (1, 2: single case)
   const double* vol;   // annulus: cell volumes (null on the box: vcell)
   const double* r2t;   // annulus: ny + 1 squared ring radii (nx sectors x ny rings)
   const double* xe;    // wall-refined box: nx + 1 and ny + 1 cell edges

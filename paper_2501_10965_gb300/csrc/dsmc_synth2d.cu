@@ -8,8 +8,8 @@
 //
 // The total-mass row (cell (1, 0)'s mass balance replaced by the total mass)
 // couples every cell; the factorised matrix B has e_r / n there instead, and
-// the Newton step of J = B + e_r w^T (w = 1/n on the density of every other
-// cell) follows from two solves with B (Sherman-Morrison).
+// the Newton step of J = B + e_r w^T (w = mass_scale / n on the density of
+// every other cell) follows from two solves with B (Sherman-Morrison).
 //
 // Factorisation: per panel of nb columns, one CTA factorises the panel in
 // shared memory, then one launch applies it to the up to kl + ku trailing
@@ -30,8 +30,8 @@ namespace {
 
 // scalar slots of the work area
 enum {
-  S2_SUMD = 0,   // sampled total density (sum over cells)
-  S2_MASS = 1,   // total-mass residual (sum rho - sampled sum) / n
+  S2_SUMD = 0,   // sampled total density (sum over cells, weighted by mass_scale)
+  S2_MASS = 1,   // total-mass residual (weighted sum rho - sampled sum) / n
   S2_DONE = 2,
   S2_IT = 3,
   S2_STATUS = 4, // 0 converged, 1 not (yet) converged, 2 numeric
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(S2_NT) k_s2_init(const s2::Grid g, S2Work w) {
     x[3] = D[4];
     x[4] = D[5];
   }
-  for (int c = threadIdx.x; c < g.n; c += S2_NT) s += g.F[(size_t)c * 18];
+  for (int c = threadIdx.x; c < g.n; c += S2_NT) s += g.F[(size_t)c * 18] * s2::mass_scale(g, c % g.nx, c / g.nx);
   s = s2_block_sum<S2_NT>(s, red);
   if (threadIdx.x == 0) {
     w.sc[S2_SUMD] = s;
@@ -176,7 +176,11 @@ __global__ void __launch_bounds__(S2_NT) k_s2_init(const s2::Grid g, S2Work w) {
 __global__ void __launch_bounds__(S2_NT) k_s2_mass(const s2::Grid g, S2Work w) {
   __shared__ double red[S2_NT];
   double s = 0.0;
-  for (int b = threadIdx.x; b < g.n; b += S2_NT) s += w.x[s2::NV * b];
+  for (int b = threadIdx.x; b < g.n; b += S2_NT) {
+    int i, j;
+    s2::cell_of_band(g, b, i, j);
+    s += w.x[s2::NV * b] * s2::mass_scale(g, i, j);
+  }
   s = s2_block_sum<S2_NT>(s, red);
   if (threadIdx.x == 0) w.sc[S2_MASS] = (s - w.sc[S2_SUMD]) / g.n;
 }
@@ -196,7 +200,7 @@ __global__ void k_s2_jac(const s2::Grid g, S2Work w, int band) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (band && t == 0) {
     const int mr = s2::mass_row(g);
-    w.AB[s2::band_at(g, mr, mr)] = (float)(1.0 / g.n);
+    w.AB[s2::band_at(g, mr, mr)] = (float)(s2::mass_scale(g, 1, 0) / g.n);
   }
   if (t >= g.n * s2::NSTENCIL * s2::NV) return;
   const int b = t / (s2::NSTENCIL * s2::NV);
@@ -506,8 +510,11 @@ __global__ void __launch_bounds__(S2_UPD_NT) k_s2_newton(const s2::Grid g, S2Wor
   double wz = 0.0, wy = 0.0;
   for (int b = tid; b < g.n; b += S2_UPD_NT) {
     if (s2::NV * b == mr) continue;
-    wz += w.v0[s2::NV * b];
-    wy += w.v1[s2::NV * b];
+    int i, j;
+    s2::cell_of_band(g, b, i, j);
+    const double ms = s2::mass_scale(g, i, j);
+    wz += w.v0[s2::NV * b] * ms;
+    wy += w.v1[s2::NV * b] * ms;
   }
   wz = s2_block_sum<S2_UPD_NT>(wz, red) / g.n;
   wy = s2_block_sum<S2_UPD_NT>(wy, red) / g.n;
@@ -615,8 +622,9 @@ size_t synth2d_work_doubles(int nx, int ny) {
 
 int launch_synth2d(const CellParams& cp, const double* fields, const double* hot, double* out, double* work,
                    int n_m, double tol, double* info, int* singular, cudaStream_t st) {
-  const s2::Grid g = s2::make_grid(cp.nx, cp.ny, cp.dx, cp.dy, cp.d_r, cp.omega, cp.mu_ref, cp.z_rot, cp.kappa_t,
-                                   cp.kappa_r, fields, hot);
+  s2::Grid g = s2::make_grid(cp.nx, cp.ny, cp.dx, cp.dy, cp.d_r, cp.omega, cp.mu_ref, cp.z_rot, cp.kappa_t,
+                             cp.kappa_r, fields, hot);
+  if (cp.mesh == 2) s2::set_edges(g, cp.xe, cp.ye, cp.lx * cp.ly);  // the wall-refined grid (device edges)
   const S2Work w = s2_carve(g, work);
   if (w.nb == 0) return (int)cudaErrorInvalidValue;
   const int nb = w.nb;

@@ -1,7 +1,9 @@
 // dsmc_synth2d.cuh -- the steady 2D synthetic equations of the DIG method
 // (Eq. macroscopic_equation with the constitutive relations of
-// Eq. full_constitutive, Sec. 3 step 3) on a rectangle of nx x ny uniform
-// cells closed by walls: per-cell residual, finite-difference Jacobian
+// Eq. full_constitutive, Sec. 3 step 3) on a rectangle of nx x ny cells
+// closed by walls (uniform, or the wall-refined grid of the cavity case of
+// Sec. 4.1: widths growing geometrically from each wall, see set_edges):
+// per-cell residual, finite-difference Jacobian
 // entries, and the steps of a blocked banded LU factorisation with partial
 // pivoting in FP32 and of its substitutions.
 //
@@ -25,7 +27,8 @@
 // the conserved variables W wherever that stencil lies in the domain.
 // Cells next to a wall keep the sampled u_x, u_y, T_t, T_r and balance only
 // their mass; the four corner cells keep their whole sampled state and
-// exchange no flux; cell (1, 0)'s mass balance is replaced by the total mass.
+// exchange no flux; cell (1, 0)'s mass balance is replaced by the total mass
+// (sum rho V against the sampled one).
 //
 // Unknown ordering: cells are numbered along the shorter side first (band
 // cell b = j nx + i when nx <= ny, else i ny + j) and the five unknowns of a
@@ -57,7 +60,10 @@ struct Grid {
   int nx, ny, n;           // cells
   int N, kl, ku, ld;       // unknowns, band widths, leading dimension of the band storage
   int xfast;               // 1: band cell b = j nx + i; 0: b = i ny + j
-  double dx, dy;
+  double dx, dy;           // uniform grid: the cell size
+  const double* xe;        // wall-refined grid: cell edges along x (nx + 1) and y (ny + 1); null: uniform
+  const double* ye;
+  double area;             // L_x L_y (wall-refined grid)
   double d_r, omega, mu_ref, z_rot, kappa_t, kappa_r, gamma;
   const double* F;         // sampled fields, natural order (cell j nx + i) x 18
   const double* hot;       // HoT, natural order x 12
@@ -78,6 +84,9 @@ __host__ __device__ inline Grid make_grid(int nx, int ny, double dx, double dy, 
   g.ld = 2 * g.kl + g.ku + 1;
   g.dx = dx;
   g.dy = dy;
+  g.xe = nullptr;
+  g.ye = nullptr;
+  g.area = 0.0;
   g.d_r = d_r;
   g.omega = omega;
   g.mu_ref = mu_ref;
@@ -88,6 +97,31 @@ __host__ __device__ inline Grid make_grid(int nx, int ny, double dx, double dy, 
   g.F = F;
   g.hot = hot;
   return g;
+}
+
+// The wall-refined grid of the cavity case (Sec. 4.1): cells between the
+// given edges; differences are taken over the distances between cell centres
+// (the middle of each cell's edges) and a balance divides by its cell's width.
+__host__ __device__ inline void set_edges(Grid& g, const double* xe, const double* ye, double area) {
+  g.xe = xe;
+  g.ye = ye;
+  g.area = area;
+}
+
+// width of cell k along axis dir (0: x, 1: y)
+__host__ __device__ inline double width(const Grid& g, int dir, int k) {
+  const double* e = dir == 0 ? g.xe : g.ye;
+  return e ? e[k + 1] - e[k] : (dir == 0 ? g.dx : g.dy);
+}
+
+__host__ __device__ inline double centre(const double* e, int k) { return 0.5 * (e[k] + e[k + 1]); }
+
+// Weight of cell (i, j)'s density in the total-mass row, times n: 1 on the
+// uniform grid, n V_c / (L_x L_y) on the wall-refined one, so that the row
+// holds the mass sum_c rho_c V_c against its sample.
+__host__ __device__ inline double mass_scale(const Grid& g, int i, int j) {
+  if (!g.xe) return 1.0;
+  return (double)g.n * (width(g, 0, i) * width(g, 1, j)) / g.area;
 }
 
 __host__ __device__ inline int band_cell(const Grid& g, int i, int j) { return g.xfast ? j * g.nx + i : i * g.ny + j; }
@@ -135,6 +169,7 @@ __host__ __device__ inline void tangential(const Grid& g, const View& X, int dir
   const int vn = dir == 0 ? 1 : 2, vt = dir == 0 ? 2 : 1;
   const int t = dir == 0 ? j : i, nt = dir == 0 ? g.ny : g.nx;
   const double h = dir == 0 ? g.dy : g.dx;
+  const double* e = dir == 0 ? g.ye : g.xe;  // edges along the tangential axis
   int lo = t - 1, hi = t + 1;
   double den = 2.0 * h;
   if (t == 0) {
@@ -146,6 +181,7 @@ __host__ __device__ inline void tangential(const Grid& g, const View& X, int dir
     hi = nt - 1;
     den = h;
   }
+  if (e) den = centre(e, hi) - centre(e, lo);
   const int il = dir == 0 ? i : lo, jl = dir == 0 ? lo : j;
   const int ih = dir == 0 ? i : hi, jh = dir == 0 ? hi : j;
   gn = (X.at(g, ih, jh, vn) - X.at(g, il, jl, vn)) / den;
@@ -172,7 +208,9 @@ __host__ __device__ inline void face_flux(const Grid& g, const View& X, int dir,
     for (int k = 0; k < NV; ++k) F[k] = 0.0;
     return;
   }
-  const double d = dir == 0 ? g.dx : g.dy;
+  const double* en = dir == 0 ? g.xe : g.ye;  // edges along the normal
+  const int fn = dir == 0 ? i : j;
+  const double d = en ? centre(en, fn + 1) - centre(en, fn) : (dir == 0 ? g.dx : g.dy);
   const double d_r = g.d_r;
   double ql[NV], qr[NV];
   frame_state(g, X, dir, i, j, ql);
@@ -246,7 +284,7 @@ __host__ __device__ inline void face_flux(const Grid& g, const View& X, int dir,
 }
 
 // Residual rows (5) of cell (i, j).  mass_row is the total-mass residual
-// (sum rho - sampled sum) / n, used by cell (1, 0).
+// sum_c mass_scale_c (rho_c - sampled rho_c) / n, used by cell (1, 0).
 __host__ __device__ inline void cell_residual(const Grid& g, const View& X, int i, int j, double mass_row, double* R) {
   const double* D = g.F + (size_t)(j * g.nx + i) * 18;
   if (is_corner(g, i, j)) {
@@ -260,30 +298,31 @@ __host__ __device__ inline void cell_residual(const Grid& g, const View& X, int 
   const bool ring = i == 0 || i == g.nx - 1 || j == 0 || j == g.ny - 1;
   double div[NV] = {0.0, 0.0, 0.0, 0.0, 0.0};
   double Fa[NV];
+  const double wx = width(g, 0, i), wy = width(g, 1, j);
   if (i < g.nx - 1) {
     face_flux(g, X, 0, i, j, Fa);
-    for (int k = 0; k < NV; ++k) div[k] += Fa[k] / g.dx;
+    for (int k = 0; k < NV; ++k) div[k] += Fa[k] / wx;
   }
   if (i > 0) {
     face_flux(g, X, 0, i - 1, j, Fa);
-    for (int k = 0; k < NV; ++k) div[k] -= Fa[k] / g.dx;
+    for (int k = 0; k < NV; ++k) div[k] -= Fa[k] / wx;
   }
   // y faces: frame (normal y, tangential x) -> components 1 and 2 swap
   if (j < g.ny - 1) {
     face_flux(g, X, 1, i, j, Fa);
-    div[0] += Fa[0] / g.dy;
-    div[1] += Fa[2] / g.dy;
-    div[2] += Fa[1] / g.dy;
-    div[3] += Fa[3] / g.dy;
-    div[4] += Fa[4] / g.dy;
+    div[0] += Fa[0] / wy;
+    div[1] += Fa[2] / wy;
+    div[2] += Fa[1] / wy;
+    div[3] += Fa[3] / wy;
+    div[4] += Fa[4] / wy;
   }
   if (j > 0) {
     face_flux(g, X, 1, i, j - 1, Fa);
-    div[0] -= Fa[0] / g.dy;
-    div[1] -= Fa[2] / g.dy;
-    div[2] -= Fa[1] / g.dy;
-    div[3] -= Fa[3] / g.dy;
-    div[4] -= Fa[4] / g.dy;
+    div[0] -= Fa[0] / wy;
+    div[1] -= Fa[2] / wy;
+    div[2] -= Fa[1] / wy;
+    div[3] -= Fa[3] / wy;
+    div[4] -= Fa[4] / wy;
   }
   R[0] = (i == 1 && j == 0) ? mass_row : div[0];
   if (ring) {
@@ -354,9 +393,9 @@ __host__ __device__ inline void jacobian_entries(const Grid& g, const double* x,
 }
 
 // (B v) of unknown u in FP64 from the compact blocks; B's total-mass row is
-// e_r / n
+// e_r u_1 / n (u_1 = mass_scale of cell (1, 0))
 __host__ __device__ inline double bmv_row(const Grid& g, const double* Jc, const double* vec, int u) {
-  if (u == mass_row(g)) return vec[u] / g.n;
+  if (u == mass_row(g)) return mass_scale(g, 1, 0) * vec[u] / g.n;
   const int b = u / NV, r = u - b * NV;
   int i, j;
   cell_of_band(g, b, i, j);

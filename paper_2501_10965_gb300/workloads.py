@@ -166,7 +166,11 @@ def refined_stretch(n: int, length: float, d_min: float) -> float:
     def first(q):
         m = [min(i, n - 1 - i) for i in range(n)]
         return length / sum(q ** k for k in m)
+    if first(1.0) <= d_min:
+        raise ValueError("refined_stretch: a uniform grid's cells are already at most d_min wide")
     lo, hi = 1.0, 2.0
+    while first(hi) > d_min:
+        lo, hi = hi, 2.0 * hi
     for _ in range(200):
         mid = 0.5 * (lo + hi)
         if first(mid) > d_min:

@@ -10,13 +10,24 @@
 #include "dsmc_synth2d.cuh"
 using namespace dsmc::s2;
 
+// the wall-refined grid's edges for the calls that follow (null: uniform)
+static const double* g_xe = nullptr;
+static const double* g_ye = nullptr;
+static double g_area = 0.0;
+extern "C" void h_set_edges(const double* xe, const double* ye, double area) {
+  g_xe = xe;
+  g_ye = ye;
+  g_area = area;
+}
 static Grid G(int nx, int ny, double dx, double dy, const double* c, const double* F, const double* hot) {
-  return make_grid(nx, ny, dx, dy, c[0], c[1], c[2], c[3], c[4], c[5], F, hot);
+  Grid g = make_grid(nx, ny, dx, dy, c[0], c[1], c[2], c[3], c[4], c[5], F, hot);
+  if (g_xe) set_edges(g, g_xe, g_ye, g_area);
+  return g;
 }
 static void residual_all(const Grid& g, const double* xb, double* Rb) {
   double sx = 0, sd = 0;
-  for (int b = 0; b < g.n; ++b) sx += xb[NV * b];
-  for (int c = 0; c < g.n; ++c) sd += g.F[(size_t)c * 18];
+  for (int b = 0; b < g.n; ++b) { int i, j; cell_of_band(g, b, i, j); sx += xb[NV * b] * mass_scale(g, i, j); }
+  for (int c = 0; c < g.n; ++c) sd += g.F[(size_t)c * 18] * mass_scale(g, c % g.nx, c / g.nx);
   const double mrow = (sx - sd) / g.n;
   View X{xb, -1, 0, 0.0};
   for (int b = 0; b < g.n; ++b) { int i, j; cell_of_band(g, b, i, j); cell_residual(g, X, i, j, mrow, Rb + NV * b); }
@@ -121,7 +132,7 @@ extern "C" int h_solve_blk(int nx, int ny, double dx, double dy, const double* c
     for (int b = 0; b < g.n; ++b) for (int s = 0; s < NSTENCIL; ++s) for (int v = 0; v < NV; ++v)
       jacobian_entries(g, x.data(), b, s, v, refac ? f.AB.data() : nullptr, Jc.data());
     if (refac) {
-      f.AB[band_at(g, mr, mr)] = (float)(1.0 / g.n);
+      f.AB[band_at(g, mr, mr)] = (float)(mass_scale(g, 1, 0) / g.n);
       sing |= factor(g, nb, f);
       ++nf;
     }
@@ -134,7 +145,9 @@ extern "C" int h_solve_blk(int nx, int ny, double dx, double dy, const double* c
       for (int u = 0; u < N; ++u) { v0[u] += s0[u]; v1[u] += s1[u]; }
     }
     double wz = 0, wy = 0;
-    for (int b = 0; b < g.n; ++b) if (NV * b != mr) { wz += v0[NV * b]; wy += v1[NV * b]; }
+    for (int b = 0; b < g.n; ++b) if (NV * b != mr) {
+      int i, j; cell_of_band(g, b, i, j); const double ms = mass_scale(g, i, j);
+      wz += v0[NV * b] * ms; wy += v1[NV * b] * ms; }
     wz /= g.n; wy /= g.n;
     const double fct = wz / (1.0 + wy);
     for (int u = 0; u < N; ++u) d[u] = v0[u] - v1[u] * fct;

@@ -97,9 +97,12 @@ def test_synth2d_workspace_and_validation():
     assert _ws(W.cavity_2d(nx=2, ny=8, ppc=4, synth2d=True))[0] == -1
     assert _ws(W.cavity_2d(nx=501, ny=501, ppc=1, synth2d=True))[0] == -1
     assert _ws(W.cylinder_2d(ntheta=24, nr=8, ppc=4, synth2d=True))[0] == -1
-    # the wall-refined box: 2D, stretch > 0, no synthetic solve
+    # the wall-refined box: 2D, stretch > 0; its 2D solve takes the box's workspace
     assert _ws(W.cavity_2d_refined(nx=14, ny=12, ppc=4, dx_min=0.02))[0] == 0
-    assert _ws(W.cavity_2d_refined(nx=14, ny=12, ppc=4, dx_min=0.02, synth2d=True))[0] == -1
+    assert _ws(W.cavity_2d_refined(nx=14, ny=12, ppc=4, dx_min=0.02, synth2d=True)) == \
+        (0, _ws(W.cavity_2d_refined(nx=14, ny=12, ppc=4, dx_min=0.02))[1] + _ws(W.cavity_2d(nx=14, ny=12, ppc=4,
+                                                                                          synth2d=True))[1]
+         - _ws(W.cavity_2d(nx=14, ny=12, ppc=4))[1])
     assert _ws(W.cavity_2d_refined(nx=14, ny=12, ppc=4, dx_min=0.02, stretch=0.0))[0] == -1
     assert _ws(W.cavity_2d_refined(nx=14, ny=12, ppc=4, dx_min=0.02, dim=1))[0] == -1
     L = dsmc.load()

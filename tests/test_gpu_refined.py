@@ -8,7 +8,10 @@ three-point formula on unequal spacing) to relative 1e-11; the particle
 modification over two rounds with steps in between.  FP32 layout: a gas at
 rest stays uniform in cells whose areas differ 25-fold (replicas, 3-SE
 bound), the particle count is conserved, and the modification follows the
-oracle given the GPU's own particles.
+oracle given the GPU's own particles.  The 2D synthetic solve on the refined
+grid: the oracle's converged solution (smooth states, and sampled cavity
+fields with their HoT), one DIG iteration, and the paper's 100 x 100 grid
+with a first cell of 0.001, whose solution zeroes the oracle's residual.
 """
 import numpy as np
 import pytest
@@ -175,3 +178,120 @@ def test_refined_fp32_gas_at_rest_stays_uniform():
     assert abs(np.mean(ratios) - 1.0) < 0.03, ratios
     assert_within_3se(np.array(rels) - 1.0, what="density by cell-area quartile")
     assert_within_3se(np.array(temps) - 1.0, what="temperature")
+
+
+# ---------------------------------------------------------------------------
+# the 2D synthetic solve on the wall-refined grid
+# ---------------------------------------------------------------------------
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _smooth_refined(cfg, seed=0, hot_amp=1e-3):
+    from oracle.fields import F_RHO, F_TR, F_TT, F_U, box_edges
+    nx, ny = int(cfg["nx"]), int(cfg["ny"])
+    ex, ey = box_edges(nx, cfg["lx"], cfg["stretch"]), box_edges(ny, cfg["ly"], cfg["stretch"])
+    X, Y = np.meshgrid(0.5 * (ex[:-1] + ex[1:]), 0.5 * (ey[:-1] + ey[1:]))
+    d = np.zeros((ny, nx, 18))
+    d[..., F_RHO] = 1 + 0.02 * np.cos(np.pi * X)
+    d[..., F_U] = 0.05 * np.sin(np.pi * X) * np.cos(np.pi * Y) * np.sin(np.pi * Y)
+    d[..., F_U + 1] = -0.05 * np.cos(np.pi * X) * np.sin(np.pi * X) * np.sin(np.pi * Y)
+    d[..., F_U + 2] = 0.003
+    d[..., F_TT] = 1 + 0.01 * Y
+    d[..., F_TR] = 1 + 0.012 * Y
+    return d.reshape(nx * ny, 18), hot_amp * np.random.default_rng(seed).standard_normal((nx * ny, 12))
+
+
+def _scfg(nx, ny, **kw):
+    base = dict(nx=nx, ny=ny, ppc=4, kn=0.05, dx_min=0.04, precision="fp64", synth2d=True, synth_tol=1e-12, n_m=50)
+    base.update(kw)
+    return W.cavity_2d_refined(**base)
+
+
+@pytest.mark.parametrize("nx,ny", [(10, 8), (7, 11)])
+def test_synth_solve_on_refined_box_matches_oracle(nx, ny):
+    from oracle import synth2d
+    cfg = _scfg(nx, ny)
+    d, h = _smooth_refined(cfg)
+    g = _gpu(cfg)
+    out_g, it_g, res_g = g.synth_solve(_dev(d), _dev(h))
+    out_o, it_o, res_o = synth2d.synth_solve_2d(d, h, cfg, tol=1e-12, max_iter=50)
+    assert res_g < 1e-11 and res_o < 1e-11, (res_g, res_o)
+    assert abs(it_g - it_o) <= 1, (it_g, it_o)
+    np.testing.assert_allclose(out_g.cpu().numpy(), out_o, rtol=0, atol=1e-10)
+
+
+def test_synth_solve_of_sampled_refined_cavity_matches_oracle():
+    """Fields sampled by the GPU on the refined cavity with their HoT and
+    Kn_GLL mask, solved on both sides; the solution keeps the sampled mass
+    sum rho V and the wall cells' u, T."""
+    from oracle import synth2d
+    from oracle.fields import F_RHO, F_TR, F_TT, F_U
+    nx, ny = 14, 11
+    cfg = _scfg(nx, ny, ppc=60, kn=0.1, lid=0.5)
+    g = _gpu(cfg)
+    g.dsmc_step(150)
+    g.dsmc_step(150, sample=True)
+    f = g.dsmc_sample(reset=False)
+    hot, _, mask = g.dsmc_hot(f)
+    out_g, it_g, res_g = g.synth_solve(f, hot)
+    F, H = f.cpu().numpy(), hot.cpu().numpy()
+    out_o, it_o, res_o = synth2d.synth_solve_2d(F, H, cfg, tol=1e-12, max_iter=50)
+    assert res_g < 1e-10 and res_o < 1e-10, (res_g, res_o)
+    np.testing.assert_allclose(out_g.cpu().numpy(), out_o, rtol=0, atol=1e-9)
+    O, V = out_g.cpu().numpy(), g.volumes()
+    assert abs((O[:, 0] * V).sum() / (F[:, F_RHO] * V).sum() - 1.0) < 1e-12
+    ring = np.zeros((ny, nx), bool)
+    ring[0, :] = ring[-1, :] = ring[:, 0] = ring[:, -1] = True
+    ring = ring.ravel()
+    for k, col in ((1, F_U), (2, F_U + 1), (4, F_TT), (5, F_TR)):
+        np.testing.assert_allclose(O[ring, k], F[ring, col], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dig_iteration_on_refined_cavity(precision):
+    """One DIG iteration on the refined cavity (steps, sample, HoT, the 2D
+    synthetic solve, the modification): the particles number the sum of
+    Iround(rho V_c / F) over cells of their own volumes (within 6 sigma of
+    the stochastic rounding), and the target keeps the sampled mass."""
+    from paper_2501_10965_gb300 import dig
+    cfg = _scfg(12, 10, ppc=50, kn=0.05, synth_tol=1e-8, precision=precision)
+    g = _gpu(cfg)
+    g.dsmc_step(100)
+    r = dig.dig_iteration(g, 100)
+    assert r["synth_status"] == 0 and r["synth_resid"] < 1e-8
+    t = r["target"].cpu().numpy()
+    V, c = g.volumes(), g.constants()
+    m = t[:, 0] * V / c["fnum"]
+    frac = m - np.floor(m)
+    sd = np.sqrt(np.sum(frac * (1.0 - frac)))
+    assert abs(g.num_particles() - m.sum()) <= 6.0 * sd + 1.0, (g.num_particles(), m.sum(), sd)
+    assert abs((t[:, 0] * V).sum() / (r["fields"][:, 0].cpu().numpy() * V).sum() - 1.0) < 1e-8
+
+
+def test_paper_refined_grid_solution_satisfies_the_oracle_equations():
+    """Sec. 4.1's DIG grid: 100 x 100 cells, first cell 0.001 at every wall
+    (50 000 unknowns; the oracle's Newton solver is too slow here): the GPU's
+    converged solution zeroes the oracle's residual at every cell (1e-9),
+    keeps the sampled mass sum rho V and the wall and corner cells."""
+    from oracle import synth2d
+    from oracle.fields import F_RHO, F_TR, F_TT, F_U
+    nx = ny = 100
+    cfg = _scfg(nx, ny, ppc=2, dx_min=0.001, synth_tol=1e-10)
+    d, h = _smooth_refined(cfg, seed=5)
+    g = _gpu(cfg)
+    out, it, res = g.synth_solve(_dev(d), _dev(h))
+    assert res < 1e-9 and it <= 12
+    O, V = out.cpu().numpy(), g.volumes()
+    x = np.concatenate([O[:, 0], O[:, 1], O[:, 2], O[:, 4], O[:, 5]])
+    R = synth2d.residual(x, d, h, cfg)
+    assert np.max(np.abs(R)) < 1e-9, np.max(np.abs(R))
+    assert abs((O[:, 0] * V).sum() / (d[:, F_RHO] * V).sum() - 1.0) < 1e-12
+    ring = np.zeros((ny, nx), bool)
+    ring[0, :] = ring[-1, :] = ring[:, 0] = ring[:, -1] = True
+    ring = ring.ravel()
+    for k, col in ((1, F_U), (2, F_U + 1), (4, F_TT), (5, F_TR)):
+        np.testing.assert_allclose(O[ring, k], d[ring, col], rtol=0, atol=1e-12)
+    corners = [0, nx - 1, nx * (ny - 1), nx * ny - 1]
+    np.testing.assert_allclose(O[corners, 0], d[corners, F_RHO], rtol=0, atol=1e-12)

@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 from oracle import synth1d, synth2d
-from oracle.fields import F_RHO, F_TR, F_TT, F_U, kappa_coefficients, mu_ref_of
+from oracle.fields import F_RHO, F_TR, F_TT, F_U, box_edges, kappa_coefficients, mu_ref_of
 from paper_2501_10965_gb300 import workloads as W
 
 sympy = pytest.importorskip("sympy")
@@ -70,10 +70,18 @@ def _mms_sources(cfg):
     return fields, hot, [f(s) for s in S]
 
 
-def _discrete_error(cfg, fields, hot, S):
+def _centres(cfg):
     nx, ny = int(cfg["nx"]), int(cfg["ny"])
+    if cfg.get("mesh", "box") == "refined":
+        ex, ey = box_edges(nx, cfg["lx"], cfg["stretch"]), box_edges(ny, cfg["ly"], cfg["stretch"])
+        return np.meshgrid(0.5 * (ex[:-1] + ex[1:]), 0.5 * (ey[:-1] + ey[1:]))
     dx, dy = cfg["lx"] / nx, cfg["ly"] / ny
-    X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dy)
+    return np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dy)
+
+
+def _discrete_error(cfg, fields, hot, S, mask=None):
+    nx, ny = int(cfg["nx"]), int(cfg["ny"])
+    X, Y = _centres(cfg)
     q = [np.broadcast_to(fn(X, Y), X.shape).astype(float) for fn in fields]
     x = np.concatenate([a.ravel() for a in q])
     H = np.zeros((ny, nx, 12))
@@ -84,7 +92,8 @@ def _discrete_error(cfg, fields, hot, S):
     errs = []
     for k in range(5):
         ex = np.broadcast_to(S[k](X, Y), X.shape)
-        errs.append(np.max(np.abs(R[k, 1:-1, 1:-1] - ex[1:-1, 1:-1])))
+        e = np.abs(R[k, 1:-1, 1:-1] - ex[1:-1, 1:-1])
+        errs.append(np.max(e if mask is None else e[mask]))
     return np.array(errs)
 
 
@@ -99,6 +108,81 @@ def test_manufactured_solution_second_order():
     assert (order23 > 1.8).all(), (e1, e2, e3, order12, order23)
     # and small in absolute terms on the finest grid
     assert (e3 < 2e-3).all(), e3
+
+
+def test_manufactured_solution_on_the_wall_refined_grid():
+    """The same sources on the wall-refined grid (widths growing by q from
+    each wall, the cavity case of Sec. 4.1), refined as a mapping: q^(12/nx),
+    so that neighbouring widths tend to equal as the grid is refined.  Where
+    the mapping is smooth the residual converges at second order, which a
+    difference over the wrong distance (a uniform dx, a cell width instead of
+    the centre distance) or a balance divided by the wrong width fails.  At
+    the middle lines, where the widths stop growing and shrink again (a kink
+    in the mapping), the error of the two-point face differences is first
+    order: the whole grid converges at first order."""
+    q0 = 1.25
+    base = W.cavity_2d(nx=12, ny=10, ppc=10, kn=0.1, lx=1.2, ly=1.0)
+    fields, hot, S = _mms_sources(base)
+    e_all, e_far = [], []
+    for nx, ny in ((12, 10), (24, 20), (48, 40)):
+        cfg = W.with_overrides(base, nx=nx, ny=ny, mesh="refined", stretch=q0 ** (12.0 / nx))
+        w = np.diff(box_edges(nx, 1.2, cfg["stretch"]))
+        assert w.max() / w.min() > 2.5  # far from uniform on every grid
+        X, Y = _centres(cfg)
+        far = ((np.abs(X - 0.6) > 0.1) & (np.abs(Y - 0.5) > 0.1))[1:-1, 1:-1]
+        e_all.append(_discrete_error(cfg, fields, hot, S))
+        e_far.append(_discrete_error(cfg, fields, hot, S, mask=far))
+    far12, far23 = np.log2(e_far[0] / e_far[1]), np.log2(e_far[1] / e_far[2])
+    all23 = np.log2(e_all[1] / e_all[2])
+    assert (far23 > 1.8).all(), (e_far, far12, far23)
+    assert (all23 > 0.9).all(), (e_all, all23)
+    assert (e_far[2] < 5e-3).all(), e_far[2]
+
+
+def test_refined_grid_with_unit_stretch_is_the_uniform_grid():
+    cfg = W.cavity_2d(nx=9, ny=7, ppc=10, kn=0.05, lx=1.0, ly=0.8)
+    rng = np.random.default_rng(4)
+    n = 63
+    x = np.concatenate([1 + 0.1 * rng.random(n), 0.1 * rng.standard_normal(2 * n), 1 + 0.1 * rng.random(2 * n)])
+    d = np.zeros((n, 18))
+    d[:, F_RHO] = 1.0
+    d[:, F_TT] = d[:, F_TR] = 1.0
+    h = 1e-3 * rng.standard_normal((n, 12))
+    R0 = synth2d.residual(x, d, h, cfg)
+    R1 = synth2d.residual(x, d, h, W.with_overrides(cfg, mesh="refined", stretch=1.0))
+    assert np.allclose(R1, R0, rtol=1e-12, atol=1e-12 * np.abs(R0).max())
+
+
+def test_newton_solution_on_the_wall_refined_grid():
+    """Newton's method on the refined cavity grid: rounding-level residual,
+    the sampled total mass sum rho V (cells of different areas), Dirichlet
+    and corner cells kept."""
+    cfg = W.cavity_2d_refined(nx=12, ny=10, ppc=10, kn=0.05, dx_min=0.03, precision="fp64")
+    nx, ny = 12, 10
+    n = nx * ny
+    X, Y = _centres(cfg)
+    d = np.zeros((ny, nx, 18))
+    d[..., F_RHO] = 1 + 0.02 * np.cos(np.pi * X)
+    d[..., F_U] = 0.05 * np.sin(np.pi * X) * np.cos(np.pi * Y) * np.sin(np.pi * Y)
+    d[..., F_U + 1] = -0.05 * np.cos(np.pi * X) * np.sin(np.pi * X) * np.sin(np.pi * Y)
+    d[..., F_TT] = 1 + 0.01 * Y
+    d[..., F_TR] = 1 + 0.012 * Y
+    d = d.reshape(n, 18)
+    h = 1e-3 * np.random.default_rng(0).standard_normal((n, 12))
+    out, it, res = synth2d.synth_solve_2d(d, h, cfg)
+    assert res < 1e-11 and it < 10
+    V = np.outer(np.diff(box_edges(ny, 1.0, cfg["stretch"])), np.diff(box_edges(nx, 1.0, cfg["stretch"]))).ravel()
+    assert V.max() / V.min() > 4.0
+    assert math.isclose((out[:, 0] * V).sum(), (d[:, F_RHO] * V).sum(), rel_tol=1e-13)
+    assert not math.isclose(out[:, 0].sum(), d[:, F_RHO].sum(), rel_tol=1e-6)
+    ring = np.zeros((ny, nx), bool)
+    ring[0, :] = ring[-1, :] = ring[:, 0] = ring[:, -1] = True
+    ring = ring.ravel()
+    for k, col in ((1, F_U), (2, F_U + 1), (4, F_TT), (5, F_TR)):
+        np.testing.assert_allclose(out[ring, k], d[ring, col], rtol=0, atol=1e-13)
+    corners = [0, nx - 1, n - nx, n - 1]
+    np.testing.assert_allclose(out[corners, 0], d[corners, F_RHO], rtol=0, atol=1e-13)
+    assert (out[:, 0] > 0.9).all() and (out[:, 0] < 1.1).all()
 
 
 def _solve_1d(cfg1):

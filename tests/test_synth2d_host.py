@@ -75,6 +75,33 @@ def test_residual_equals_oracle(lib, nx, ny):
     assert np.max(np.abs(R1 - R0)) <= 1e-12 * max(1.0, np.max(np.abs(R0)))
 
 
+def _refined(lib, cfg):
+    """Hand the wall-refined grid's edges to the harness (kept alive by the
+    returned arrays)."""
+    from oracle.fields import box_edges
+    xe = np.ascontiguousarray(box_edges(cfg["nx"], cfg["lx"], cfg["stretch"]))
+    ye = np.ascontiguousarray(box_edges(cfg["ny"], cfg["ly"], cfg["stretch"]))
+    lib.h_set_edges(_p(xe), _p(ye), ctypes.c_double(cfg["lx"] * cfg["ly"]))
+    return xe, ye
+
+
+@pytest.mark.parametrize("nx,ny", [(9, 6), (6, 9), (12, 12)])
+def test_residual_equals_oracle_on_the_wall_refined_grid(lib, nx, ny):
+    cfg = W.cavity_2d_refined(nx=nx, ny=ny, ppc=4, kn=0.05, dx_min=0.04, precision="fp64")
+    d, h = _smooth(nx, ny, seed=nx)
+    x = synth2d.initial_state(d) * (1.0 + 0.01 * np.random.default_rng(1).standard_normal(5 * nx * ny))
+    R0 = synth2d.residual(x, d, h, cfg)
+    R1 = np.zeros_like(R0)
+    keep = _refined(lib, cfg)
+    try:
+        lib.h_residual(nx, ny, ctypes.c_double(cfg["lx"] / nx), ctypes.c_double(cfg["ly"] / ny), _p(_consts(cfg)),
+                       _p(np.ascontiguousarray(d)), _p(np.ascontiguousarray(h)), _p(x), _p(R1))
+    finally:
+        lib.h_set_edges(None, None, ctypes.c_double(0.0))
+    del keep
+    assert np.max(np.abs(R1 - R0)) <= 1e-12 * max(1.0, np.max(np.abs(R0)))
+
+
 @pytest.mark.parametrize("N,kl,nb", [(40, 5, 4), (200, 30, 16), (333, 37, 32), (400, 54, 32), (300, 100, 8)])
 def test_blocked_band_lu_refines_to_fp64(lib, N, kl, nb):
     rng = np.random.default_rng(N + kl)
@@ -121,4 +148,28 @@ def test_newton_reaches_the_oracle_solution(lib, nx, ny, reuse):
         assert it0 <= it.value <= it0 + 1 and 1 <= nf.value < it.value, (it0, it.value, nf.value)
     else:
         assert it.value == it0 and nf.value == it0
+    np.testing.assert_allclose(out1, out0, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("nx,ny", [(10, 8), (7, 11)])
+def test_newton_reaches_the_oracle_solution_on_the_wall_refined_grid(lib, nx, ny):
+    """The GPU's Newton steps (reuse policy included) on the wall-refined
+    grid, with the volume-weighted total-mass row: the oracle's solution."""
+    cfg = W.cavity_2d_refined(nx=nx, ny=ny, ppc=4, kn=0.05, dx_min=0.04, precision="fp64")
+    d, h = _smooth(nx, ny)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        out0, it0, res0 = synth2d.synth_solve_2d(d, h, cfg, tol=1e-12, max_iter=50)
+    out1 = np.zeros((nx * ny, 6))
+    it, res, st, nf = ctypes.c_int(), ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+    keep = _refined(lib, cfg)
+    try:
+        lib.h_solve_blk(nx, ny, ctypes.c_double(cfg["lx"] / nx), ctypes.c_double(cfg["ly"] / ny), _p(_consts(cfg)),
+                        _p(np.ascontiguousarray(d)), _p(np.ascontiguousarray(h)), 50, ctypes.c_double(1e-12), 32, 1,
+                        1, 3, _p(out1), ctypes.byref(it), ctypes.byref(res), ctypes.byref(st), ctypes.byref(nf))
+    finally:
+        lib.h_set_edges(None, None, ctypes.c_double(0.0))
+    del keep
+    assert st.value == 0 and res.value < 1e-11
+    assert it0 <= it.value <= it0 + 1, (it0, it.value)
     np.testing.assert_allclose(out1, out0, rtol=0, atol=1e-12)
