@@ -13,9 +13,10 @@
 //
 // Factorisation: per panel of nb columns, one CTA factorises the panel in
 // shared memory, then one launch applies it to the up to kl + ku trailing
-// columns, cb columns per CTA.  Substitution: one CTA walks the panels,
-// forward then backward, with the panel's window of the right-hand sides in
-// shared memory.  The launches on one stream order the panels.
+// columns, cb columns per CTA.  Substitution: a cluster of 8 CTAs walks the
+// panels, forward then backward, one cluster barrier per panel
+// (k_s2_subst_cl; one CTA, k_s2_subst, where no cluster fits).  The launches
+// on one stream order the factorisation's panels.
 #include <climits>
 #include <cmath>
 #include <cstdint>
@@ -70,6 +71,7 @@ struct S2Work {
   double *x, *R, *d, *rhs0, *rhs1, *b0, *b1, *y0, *y1, *v0, *v1, *s0, *s1, *sc, *Jc;
   float *AB, *Lp, *ud;
   int32_t* piv;
+  float* q;  // 4 FP32 vectors of N: the clustered substitution's ping-pong right-hand sides
   int nb, cb;
 };
 
@@ -82,7 +84,7 @@ inline size_t s2_doubles(const s2::Grid& g) {
   const size_t N = (size_t)g.N;
   const size_t vec = round32(N);
   const size_t jc = round32((size_t)g.n * s2::NSTENCIL * s2::NV * s2::NV);
-  const size_t f32 = (size_t)g.ld * N + s2_lp_floats(g, bl.nb) + N + N;  // AB, Lp, ud, piv
+  const size_t f32 = (size_t)g.ld * N + s2_lp_floats(g, bl.nb) + N + N + 4 * N;  // AB, Lp, ud, piv, q
   return 13 * vec + 32 + jc + round32((f32 + 1) / 2) + 32;
 }
 
@@ -108,6 +110,8 @@ S2Work s2_carve(const s2::Grid& g, double* w) {
   s.ud = f;
   f += g.N;
   s.piv = reinterpret_cast<int32_t*>(f);
+  f += g.N;
+  s.q = f;
   s.nb = bl.nb;
   s.cb = bl.cb;
   return s;
@@ -472,6 +476,273 @@ __global__ void __launch_bounds__(S2_SUB_NT) k_s2_subst(const s2::Grid g, S2Work
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same substitutions across a cluster of SC_CL CTAs (SC_CL SMs) instead
+// of one CTA.  Per panel, warp 0 of every CTA replays the panel's
+// interchanges and solves the 32 x 32 triangle for itself (the arithmetic of
+// k_s2_subst, in its order), while the other warps update their share of the
+// rows below (above, going backward), one row per lane, with the factor
+// entries of the panel loaded during the previous panel; one cluster barrier
+// per panel.  The right-hand sides live in FP32 ping-pong vectors in global
+// memory (read and written at L2): panel k reads pair k % 2 and writes pair
+// (k + 1) % 2, so no CTA overwrites a value another may still read.  Rows a
+// panel does not write keep their value in both pairs (both start as the
+// input), which is what the next panel needs of them.
+// ---------------------------------------------------------------------------
+constexpr int SC_CL = 8;                 // CTAs: one cluster (the portable maximum)
+constexpr int SC_UW = 8;                 // update warps per CTA
+constexpr int SC_NT = 32 * (1 + SC_UW);  // and the solver warp (warp 0)
+
+__device__ __forceinline__ void sc_cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned sc_cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// The panel's interchanges as a map of window positions: m[r] = the window
+// row whose value ends at position r (identity elsewhere); the entries the
+// previous use touched are put back first.
+__device__ void sc_build_map(const s2::Grid& g, const int32_t* piv, int nb, int k0, int* m, int* touched, int& nt) {
+  for (int q = 0; q < nt; ++q) m[touched[q]] = touched[q];
+  nt = 0;
+  const int wd = s2::panel_width(g, nb, k0);
+  for (int j = 0; j < wd; ++j) {
+    const int p = piv[k0 + j] - k0;
+    if (p != j) {
+      const int t = m[j];
+      m[j] = m[p];
+      m[p] = t;
+      touched[nt++] = j;
+      touched[nt++] = p;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work w, const double* b0,
+                                                       const double* b1, double* o0, double* o1) {
+  __shared__ float ty0[32], ty1[32];
+  __shared__ int touched[2][64];
+  __shared__ int ntouch[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned rank = sc_cluster_rank();
+  const int nb = w.nb, N = g.N, ldp = g.kl + nb, hcap = g.kl + nb;
+  const int nk = (N + nb - 1) / nb;
+  const int nup = SC_CL * SC_UW;                        // update warps in the cluster
+  const int uq = (int)rank * SC_UW + (warp - 1);       // this warp's place among them (warp >= 1)
+  int* const map0 = reinterpret_cast<int*>(s2_smem);  // two maps of hcap entries
+  auto map = [&](int k) { return map0 + (k & 1) * hcap; };
+  // pair p of right-hand-side vectors: rhs 0 at qv(p, 0), rhs 1 at qv(p, 1)
+  auto qv = [&](int p, int c) { return w.q + (size_t)(2 * (p & 1) + c) * N; };
+  // ---- forward: L y = P b ----
+  for (int u = (int)rank * SC_NT + tid; u < N; u += SC_CL * SC_NT) {
+    const float v0 = (float)b0[u], v1 = (float)b1[u];
+    __stcg(qv(0, 0) + u, v0);
+    __stcg(qv(0, 1) + u, v1);
+    __stcg(qv(1, 0) + u, v0);
+    __stcg(qv(1, 1) + u, v1);
+  }
+  for (int r = tid; r < 2 * hcap; r += SC_NT) map0[r] = r < hcap ? r : r - hcap;
+  if (tid < 2) ntouch[tid] = 0;
+  __syncthreads();
+  float fr[32];  // warp 0: row `lane` of the panel's unit lower triangle; update warps: the lane's row of L21
+  auto load_fwd = [&](int k0) {
+    const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
+    const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
+    if (warp == 0) {
+      const int i = lane, ic = i < wd ? i : wd - 1;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const float l = __ldg(Lk + (size_t)(jj < wd ? jj : wd - 1) * ldp + ic);
+        fr[jj] = (jj < i && i < wd) ? l : 0.0f;
+      }
+    } else {
+      const int r = wd + 32 * uq + lane;
+      const int rc = r < H ? r : H - 1;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) fr[jj] = __ldg(Lk + (size_t)(jj < wd ? jj : wd - 1) * ldp + rc);
+    }
+  };
+  if (warp == 0 && lane == 0) sc_build_map(g, w.piv, nb, 0, map(0), touched[0], ntouch[0]);
+  load_fwd(0);
+  sc_cluster_sync();
+  for (int k = 0; k < nk; ++k) {
+    const int k0 = k * nb;
+    const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
+    const float* qa0 = qv(k, 0);
+    const float* qa1 = qv(k, 1);
+    float* qb0 = qv(k + 1, 0);
+    float* qb1 = qv(k + 1, 1);
+    const int* m = map(k);
+    const int r = wd + 32 * uq + lane;
+    float v0 = 0.0f, v1 = 0.0f;
+    if (warp == 0) {
+      const int i = lane;
+      float a0 = i < wd ? __ldcg(qa0 + k0 + m[i]) : 0.0f, a1 = i < wd ? __ldcg(qa1 + k0 + m[i]) : 0.0f;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        if (jj < wd) {
+          const float y0j = __shfl_sync(0xffffffffu, a0, jj);
+          const float y1j = __shfl_sync(0xffffffffu, a1, jj);
+          if (i > jj && i < wd) {
+            a0 -= fr[jj] * y0j;
+            a1 -= fr[jj] * y1j;
+          }
+        }
+      }
+      if (i < wd) {
+        ty0[i] = a0;
+        ty1[i] = a1;
+        if (rank == 0) {
+          w.y0[k0 + i] = a0;
+          w.y1[k0 + i] = a1;
+        }
+      }
+    } else if (r < H) {
+      v0 = __ldcg(qa0 + k0 + m[r]);
+      v1 = __ldcg(qa1 + k0 + m[r]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      if (k + 1 < nk) {
+        load_fwd(k0 + nb);
+        if (lane == 0) sc_build_map(g, w.piv, nb, k0 + nb, map(k + 1), touched[(k + 1) & 1], ntouch[(k + 1) & 1]);
+      }
+    } else {
+      if (r < H) {
+        float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          acc0 += jj < wd ? fr[jj] * ty0[jj] : 0.0f;
+          acc1 += jj < wd ? fr[jj] * ty1[jj] : 0.0f;
+        }
+        __stcg(qb0 + k0 + r, v0 - acc0);
+        __stcg(qb1 + k0 + r, v1 - acc1);
+      }
+      // rows past the cluster's lanes (bands wider than 32 x SC_CL x SC_UW
+      // rows): their entries are loaded here
+      const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
+      for (int rr = r + 32 * nup; rr < H; rr += 32 * nup) {
+        const float x0 = __ldcg(qa0 + k0 + m[rr]), x1 = __ldcg(qa1 + k0 + m[rr]);
+        float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll 8
+        for (int jj = 0; jj < 32; ++jj) {
+          const float l = __ldg(Lk + (size_t)(jj < wd ? jj : wd - 1) * ldp + rr);
+          acc0 += jj < wd ? l * ty0[jj] : 0.0f;
+          acc1 += jj < wd ? l * ty1[jj] : 0.0f;
+        }
+        __stcg(qb0 + k0 + rr, x0 - acc0);
+        __stcg(qb1 + k0 + rr, x1 - acc1);
+      }
+      if (k + 1 < nk) load_fwd(k0 + nb);
+    }
+    sc_cluster_sync();
+  }
+  // ---- backward: U x = y ----
+  for (int u = (int)rank * SC_NT + tid; u < N; u += SC_CL * SC_NT) {
+    const float v0 = (float)__ldcg(w.y0 + u), v1 = (float)__ldcg(w.y1 + u);
+    __stcg(qv(0, 0) + u, v0);
+    __stcg(qv(0, 1) + u, v1);
+    __stcg(qv(1, 0) + u, v0);
+    __stcg(qv(1, 1) + u, v1);
+  }
+  float dg = 1.0f;
+  auto load_bwd = [&](int k0) {
+    const int wd = s2::panel_width(g, nb, k0);
+    if (warp == 0) {
+      const int i = lane, ic = i < wd ? i : wd - 1;
+      dg = i < wd ? __ldg(w.ud + k0 + i) : 1.0f;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const float u = s2::umul(g, w.AB, k0 + ic, k0 + (jj < wd ? jj : wd - 1));
+        fr[jj] = (jj > i && jj < wd) ? u : 0.0f;
+      }
+    } else {
+      const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
+      const int r = lo + 32 * uq + lane;
+      const int rc = r < k0 ? r : (k0 > 0 ? k0 - 1 : 0);
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) fr[jj] = s2::umul(g, w.AB, rc, k0 + (jj < wd ? jj : wd - 1));
+    }
+  };
+  load_bwd((nk - 1) * nb);
+  sc_cluster_sync();
+  for (int k = nk - 1, it = 0; k >= 0; --k, ++it) {
+    const int k0 = k * nb;
+    const int wd = s2::panel_width(g, nb, k0);
+    const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
+    const float* qa0 = qv(it, 0);
+    const float* qa1 = qv(it, 1);
+    float* qb0 = qv(it + 1, 0);
+    float* qb1 = qv(it + 1, 1);
+    const int r = lo + 32 * uq + lane;
+    float v0 = 0.0f, v1 = 0.0f;
+    if (warp == 0) {
+      const int i = lane;
+      float a0 = i < wd ? __ldcg(qa0 + k0 + i) : 0.0f, a1 = i < wd ? __ldcg(qa1 + k0 + i) : 0.0f;
+      float x0i = 0.0f, x1i = 0.0f;
+#pragma unroll
+      for (int jj = 31; jj >= 0; --jj) {
+        if (jj < wd) {
+          const float x0j = __shfl_sync(0xffffffffu, a0 / dg, jj);
+          const float x1j = __shfl_sync(0xffffffffu, a1 / dg, jj);
+          if (i == jj) {
+            x0i = x0j;
+            x1i = x1j;
+          }
+          if (i < jj) {
+            a0 -= fr[jj] * x0j;
+            a1 -= fr[jj] * x1j;
+          }
+        }
+      }
+      if (i < wd) {
+        ty0[i] = x0i;
+        ty1[i] = x1i;
+        if (rank == 0) {
+          o0[k0 + i] = x0i;
+          o1[k0 + i] = x1i;
+        }
+      }
+    } else if (r < k0) {
+      v0 = __ldcg(qa0 + r);
+      v1 = __ldcg(qa1 + r);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      if (k > 0) load_bwd(k0 - nb);
+    } else {
+      if (r < k0) {
+        float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          acc0 += jj < wd ? fr[jj] * ty0[jj] : 0.0f;
+          acc1 += jj < wd ? fr[jj] * ty1[jj] : 0.0f;
+        }
+        __stcg(qb0 + r, v0 - acc0);
+        __stcg(qb1 + r, v1 - acc1);
+      }
+      for (int rr = r + 32 * nup; rr < k0; rr += 32 * nup) {
+        const float x0 = __ldcg(qa0 + rr), x1 = __ldcg(qa1 + rr);
+        float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll 8
+        for (int jj = 0; jj < 32; ++jj) {
+          const float u = s2::umul(g, w.AB, rr, k0 + (jj < wd ? jj : wd - 1));
+          acc0 += jj < wd ? u * ty0[jj] : 0.0f;
+          acc1 += jj < wd ? u * ty1[jj] : 0.0f;
+        }
+        __stcg(qb0 + rr, x0 - acc0);
+        __stcg(qb1 + rr, x1 - acc1);
+      }
+      if (k > 0) load_bwd(k0 - nb);
+    }
+    sc_cluster_sync();
+  }
+}
+
 // right-hand sides of a Newton step: -R and e_r (the total-mass row)
 __global__ void k_s2_prep(const s2::Grid g, S2Work w) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
@@ -615,6 +886,38 @@ void s2_smem_limits(size_t panel, size_t trail, size_t subst) {
 
 }  // namespace
 
+// One substitution (two right-hand sides): on a cluster of SC_CL CTAs where
+// the device can run one, else on one CTA (k_s2_subst).
+cudaError_t s2_subst(const s2::Grid& g, const S2Work& w, double* b0, double* b1, double* o0, double* o1,
+                     size_t sm_subst, cudaStream_t st) {
+  static int cluster_ok = -1;  // per process: 1 when an SC_CL-CTA cluster of k_s2_subst_cl fits
+  const size_t sm_cl = sizeof(int) * 2 * ((size_t)g.kl + w.nb);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = SC_CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(SC_CL);
+  cfg.blockDim = dim3(SC_NT);
+  cfg.dynamicSmemBytes = sm_cl;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cluster_ok < 0) {
+    int n = 0;
+    cluster_ok = (sm_cl <= 48 * 1024 && cudaOccupancyMaxActiveClusters(&n, k_s2_subst_cl, &cfg) == cudaSuccess &&
+                  n >= 1)
+                     ? 1
+                     : 0;
+    cudaGetLastError();  // a refused query leaves no error behind
+  }
+  if (cluster_ok && sm_cl <= 48 * 1024)
+    return cudaLaunchKernelEx(&cfg, k_s2_subst_cl, g, w, (const double*)b0, (const double*)b1, o0, o1);
+  k_s2_subst<<<1, S2_SUB_NT, sm_subst, st>>>(g, w, b0, b1, o0, o1);
+  return cudaGetLastError();
+}
+
 size_t synth2d_work_doubles(int nx, int ny) {
   const s2::Grid g = s2::make_grid(nx, ny, 1.0, 1.0, 2.0, 0.75, 1.0, 1.0, 1.0, 1.0, nullptr, nullptr);
   return s2_doubles(g);
@@ -662,12 +965,13 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
     }
     const int nsweep = refactor ? S2_NREF : S2_NREF_REUSE;
     k_s2_prep<<<vec_grid, nt, 0, st>>>(g, w);
-    k_s2_subst<<<1, S2_SUB_NT, sm_subst, st>>>(g, w, w.b0, w.b1, w.v0, w.v1);
-    for (int r = 0; r < nsweep; ++r) {
+    cudaError_t le = s2_subst(g, w, w.b0, w.b1, w.v0, w.v1, sm_subst, st);
+    for (int r = 0; r < nsweep && le == cudaSuccess; ++r) {
       k_s2_bmv<<<vec_grid, nt, 0, st>>>(g, w);
-      k_s2_subst<<<1, S2_SUB_NT, sm_subst, st>>>(g, w, w.b0, w.b1, w.s0, w.s1);
+      le = s2_subst(g, w, w.b0, w.b1, w.s0, w.s1, sm_subst, st);
       k_s2_add<<<vec_grid, nt, 0, st>>>(g, w);
     }
+    if (le != cudaSuccess) return (int)le;
     k_s2_newton<<<1, S2_UPD_NT, 0, st>>>(g, w, n_m, tol);
     cudaMemcpyAsync(sc, w.sc, sizeof(double) * (S2_LAM + 1), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);

@@ -206,3 +206,18 @@ extern "C" int h_residual(int nx, int ny, double dx, double dy, const double* c,
       for (int v = 0; v < NV; ++v) R_nat[(size_t)v * g.n + j * g.nx + i] = Rb[NV * band_cell(g, i, j) + v];
   return 0;
 }
+
+// the FP32 factors of a band matrix given densely, for checks of the
+// substitution's data flow: AB (N x ld), Lp, ud, piv
+extern "C" int h_band_factor(int N, int kl, int nb, const double* A, float* AB, float* Lp, float* ud, int32_t* piv) {
+  Grid g{};
+  g.N = N; g.kl = kl; g.ku = kl; g.ld = 2 * kl + kl + 1;
+  F32 f; f.AB.assign((size_t)N * g.ld, 0.f); f.Lm.assign(lp_size(g, nb), 0.f); f.ud.assign(N, 0.f); f.piv.assign(N, 0);
+  for (int r = 0; r < N; ++r) for (int c = 0; c < N; ++c) if (std::abs(r - c) <= kl) f.AB[band_at(g, r, c)] = (float)A[(size_t)r * N + c];
+  factor(g, nb, f);
+  std::copy(f.AB.begin(), f.AB.end(), AB);
+  std::copy(f.Lm.begin(), f.Lm.end(), Lp);
+  std::copy(f.ud.begin(), f.ud.end(), ud);
+  std::copy(f.piv.begin(), f.piv.end(), piv);
+  return 0;
+}
