@@ -13,7 +13,7 @@
 //
 // Factorisation: per panel of nb columns, one CTA factorises the panel in
 // shared memory, then one launch applies it to the up to kl + ku trailing
-// columns, cb columns per CTA.  Substitution: a cluster of 8 CTAs walks the
+// columns, up to 16 columns per CTA.  Substitution: a cluster of 8 CTAs walks the
 // panels, forward then backward, one cluster barrier per panel
 // (k_s2_subst_cl; one CTA, k_s2_subst, where no cluster fits).  The launches
 // on one stream order the factorisation's panels.
@@ -212,23 +212,16 @@ __global__ void k_s2_jac(const s2::Grid g, S2Work w, int band) {
   s2::jacobian_entries(g, w.x, b, rem / s2::NV, rem % s2::NV, band ? w.AB : nullptr, w.Jc);
 }
 
-// First row of largest |P(r, j)|, r = j .. panel_rmax, as s2::panel_pivot_seq
-// (magnitudes that are not numbers never win; such a column pivots on its
-// diagonal); *best gets the pivot's magnitude.
-__device__ int s2_panel_argmax(const s2::Grid& g, const float* P, int H, int j, float* sv, int* si, float& best_out) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// Block-wide first row of largest magnitude from each thread's candidate
+// (best, bi): warps reduce by shuffles and write one candidate each into
+// buffer buf; after one barrier every warp reduces those candidates itself
+// (the same order, so the same answer everywhere).  Magnitudes that are not
+// numbers never win; no candidate gives row `fallback` with magnitude -1.
+__device__ __forceinline__ int s2_block_argmax(float best, int bi, float (*cbest)[S2_PNL_NT / 32],
+                                               int (*cidx)[S2_PNL_NT / 32], int buf, int fallback,
+                                               float& best_out) {
   constexpr int NW = S2_PNL_NT / 32;
-  const float* col = P + (size_t)j * H;
-  const int rmax = s2::panel_rmax(g, H, j);
-  float best = -1.0f;
-  int bi = INT_MAX;
-  for (int r = j + tid; r <= rmax; r += S2_PNL_NT) {
-    const float a = fabsf(col[r]);
-    if (a > best) {
-      best = a;
-      bi = r;
-    }
-  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     const float ob = __shfl_down_sync(0xffffffffu, best, off);
@@ -239,93 +232,182 @@ __device__ int s2_panel_argmax(const s2::Grid& g, const float* P, int H, int j, 
     }
   }
   if (lane == 0) {
-    sv[warp] = best;
-    si[warp] = bi;
+    cbest[buf][warp] = best;
+    cidx[buf][warp] = bi;
   }
   __syncthreads();
-  if (warp == 0) {
-    best = lane < NW ? sv[lane] : -1.0f;
-    bi = lane < NW ? si[lane] : INT_MAX;
+  best = lane < NW ? cbest[buf][lane] : -1.0f;
+  bi = lane < NW ? cidx[buf][lane] : INT_MAX;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float ob = __shfl_down_sync(0xffffffffu, best, off);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      sv[NW] = best;
-      si[NW] = bi;
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
     }
   }
-  __syncthreads();
-  const int p = si[NW];
-  best_out = sv[NW];
-  __syncthreads();
-  return p == INT_MAX ? j : p;
+  best_out = best;
+  return bi == INT_MAX ? fallback : bi;
 }
 
-// factorisation of the panel at column k0 (one CTA; panel in shared memory)
+// Factorisation of the panel at column k0 (one CTA; panel in shared memory,
+// column-major).  Thread t owns the panel rows r = t (mod S2_PNL_NT): in
+// step j it scales its rows' multipliers of column j, updates its rows of
+// columns j+1 .. w-1 (the arithmetic of s2::panel_scale and panel_rank1)
+// and scans its rows of column j+1 for the next pivot, so that a step needs
+// two barriers: one in the pivot search, one after the interchange.
 __global__ void __launch_bounds__(S2_PNL_NT) k_s2_panel(const s2::Grid g, S2Work w, int k0) {
-  __shared__ float sv[S2_PNL_NT / 32 + 1];
-  __shared__ int si[S2_PNL_NT / 32 + 1];
+  __shared__ float cbest[2][S2_PNL_NT / 32];
+  __shared__ int cidx[2][S2_PNL_NT / 32];
   float* P = reinterpret_cast<float*>(s2_smem);
   const int tid = threadIdx.x;
   const int wd = s2::panel_width(g, w.nb, k0), H = s2::panel_height(g, wd, k0);
   s2::panel_load(g, w.AB, k0, wd, H, P, tid, S2_PNL_NT);
   __syncthreads();
+  float best = -1.0f, pbest = -1.0f;
+  int bi = INT_MAX;
+  for (int r = tid; r <= s2::panel_rmax(g, H, 0); r += S2_PNL_NT) {
+    const float a = fabsf(P[r]);
+    if (a > best) {
+      best = a;
+      bi = r;
+    }
+  }
+  int p = s2_block_argmax(best, bi, cbest, cidx, 0, 0, pbest);
   for (int j = 0; j < wd; ++j) {
-    float best;
-    const int p = s2_panel_argmax(g, P, H, j, sv, si, best);
     if (tid == 0) {
       w.piv[k0 + j] = k0 + p;
-      if (!(best > 0.0f)) w.sc[S2_SING] = 1.0;
+      if (!(pbest > 0.0f)) w.sc[S2_SING] = 1.0;
     }
-    s2::panel_swap(P, H, wd, j, p, tid, S2_PNL_NT);
+    if (p != j && tid < wd) {
+      float* col = P + (size_t)tid * H;
+      const float t = col[j];
+      col[j] = col[p];
+      col[p] = t;
+    }
     __syncthreads();
-    s2::panel_scale(g, P, H, j, tid, S2_PNL_NT);
-    __syncthreads();
-    s2::panel_rank1(g, P, H, wd, j, tid, S2_PNL_NT, 4);
-    __syncthreads();
+    const float* lj0 = P + (size_t)j * H;
+    const float piv = lj0[j];
+    const int rm = s2::panel_rmax(g, H, j);
+    const int rm1 = j + 1 < wd ? s2::panel_rmax(g, H, j + 1) : -1;
+    const int rend = rm > rm1 ? rm : rm1;
+    best = -1.0f;
+    bi = INT_MAX;
+    int r = tid;
+    if (r <= j) r += ((j - tid) / S2_PNL_NT + 1) * S2_PNL_NT;
+    for (; r <= rend; r += S2_PNL_NT) {
+      if (r <= rm) {
+        float* lj = P + (size_t)j * H;
+        const float l = piv != 0.0f ? lj[r] / piv : 0.0f;
+        lj[r] = l;
+        for (int c = j + 1; c < wd; ++c) {
+          float* col = P + (size_t)c * H;
+          col[r] -= l * col[j];
+        }
+      }
+      if (r <= rm1) {
+        const float a = fabsf(P[(size_t)(j + 1) * H + r]);
+        if (a > best) {
+          best = a;
+          bi = r;
+        }
+      }
+    }
+    if (j + 1 < wd) p = s2_block_argmax(best, bi, cbest, cidx, (j + 1) & 1, j + 1, pbest);
   }
+  __syncthreads();
   s2::panel_store(g, w.nb, w.AB, w.Lp, w.ud, k0, wd, H, P, tid, S2_PNL_NT);
 }
 
-// the panel's interchanges and eliminations on cb trailing columns per CTA
-__global__ void __launch_bounds__(S2_NT) k_s2_trail(const s2::Grid g, S2Work w, int k0) {
-  const int tid = threadIdx.x;
-  const int wd = s2::panel_width(g, w.nb, k0), H = s2::panel_height(g, wd, k0);
-  const int cfirst = k0 + wd + blockIdx.x * w.cb;
+__device__ __forceinline__ void s2_cp_async4(float* sdst, const float* gsrc, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void s2_cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// The panel's interchanges and eliminations on up to cbt trailing columns per
+// CTA (the arithmetic of s2::trail_swaps, trail_l11_step and trail_l21, in
+// their order): the column segments arrive by asynchronous copies (zero
+// outside the band), a thread per column applies the interchanges, a warp
+// per column the unit-lower solve with L11 (lane i holding L11's row i), and
+// a thread per row of L21 (its multipliers in registers) updates that row of
+// every column of the CTA.  No copy of the multipliers in shared memory, so
+// the CTAs stay small and many.
+__global__ void __launch_bounds__(S2_NT) k_s2_trail(const s2::Grid g, S2Work w, int k0, int cbt) {
+  __shared__ int spv[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = w.nb, ldp = g.kl + nb;
+  const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
+  const int cfirst = k0 + wd + blockIdx.x * cbt;
   const int clast = s2::trail_last(g, k0, wd);
-  const int ncols = clast - cfirst + 1 < w.cb ? clast - cfirst + 1 : w.cb;
+  const int ncols = clast - cfirst + 1 < cbt ? clast - cfirst + 1 : cbt;
   if (ncols <= 0) return;
-  float* Ls = reinterpret_cast<float*>(s2_smem);
-  float* Cs = Ls + (size_t)wd * H;
-  s2::trail_load_l(g, w.nb, w.Lp, k0, wd, H, Ls, tid, S2_NT);
-  s2::trail_load_cols(g, w.AB, k0, H, cfirst, ncols, Cs, tid, S2_NT);
+  float* Cs = reinterpret_cast<float*>(s2_smem);
+  const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
+  for (int e = tid; e < ncols * H; e += S2_NT) {
+    const int cc = e / H, r = e - cc * H, c = cfirst + cc;
+    const bool in = s2::in_band(g, k0 + r, c);
+    s2_cp_async4(Cs + e, w.AB + (in ? s2::band_at(g, k0 + r, c) : 0), in ? 4 : 0);
+  }
+  if (tid < wd) spv[tid] = w.piv[k0 + tid] - k0;
+  s2_cp_async_wait_all();
   __syncthreads();
-  s2::trail_swaps(w.piv, k0, wd, H, ncols, Cs, tid, S2_NT);
+  for (int cc = tid; cc < ncols; cc += S2_NT) {
+    float* a = Cs + (size_t)cc * H;
+    for (int j = 0; j < wd; ++j) {
+      const int p = spv[j];
+      if (p != j) {
+        const float t = a[j];
+        a[j] = a[p];
+        a[p] = t;
+      }
+    }
+  }
   __syncthreads();
-  // unit-lower solve with the panel's top block: one warp per column, lane i
-  // holding row i (the same eliminations as s2::trail_l11_step, in order)
   {
-    const int lane = tid & 31, warp = tid >> 5;
+    const int i = lane, ic = i < wd ? i : wd - 1;
+    float lr[32];
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const float l = Lk[(size_t)(jj < wd ? jj : wd - 1) * ldp + ic];
+      lr[jj] = (jj < i && i < wd) ? l : 0.0f;
+    }
     for (int cc = warp; cc < ncols; cc += S2_NT / 32) {
       float* a = Cs + (size_t)cc * H;
       float ai = lane < wd ? a[lane] : 0.0f;
-      for (int j = 0; j < wd; ++j) {
-        const float aj = __shfl_sync(0xffffffffu, ai, j);
-        if (lane > j && lane < wd) ai -= Ls[(size_t)j * H + lane] * aj;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (j < wd) {
+          const float aj = __shfl_sync(0xffffffffu, ai, j);
+          if (lane > j && lane < wd) ai -= lr[j] * aj;
+        }
       }
       if (lane < wd) a[lane] = ai;
     }
   }
   __syncthreads();
-  s2::trail_l21(Ls, wd, H, ncols, Cs, tid, S2_NT);
+  for (int r = wd + tid; r < H; r += S2_NT) {
+    float l[32];
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) l[jj] = Lk[(size_t)(jj < wd ? jj : wd - 1) * ldp + r];
+    for (int cc = 0; cc < ncols; ++cc) {
+      const float* a = Cs + (size_t)cc * H;
+      float acc = 0.0f;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj)
+        if (jj < wd) acc += l[jj] * a[jj];
+      Cs[(size_t)cc * H + r] -= acc;
+    }
+  }
   __syncthreads();
-  s2::trail_store(g, w.AB, k0, H, cfirst, ncols, Cs, tid, S2_NT);
+  for (int e = tid; e < ncols * H; e += S2_NT) {
+    const int cc = e / H, r = e - cc * H, c = cfirst + cc;
+    if (s2::in_band(g, k0 + r, c)) w.AB[s2::band_at(g, k0 + r, c)] = Cs[e];
+  }
 }
 
 // Forward and backward substitution with the FP32 factors for two
@@ -942,7 +1024,12 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
   const int nb = w.nb;
   const size_t hmax = (size_t)g.kl + nb;
   const size_t sm_panel = sizeof(float) * nb * hmax;
-  const size_t sm_trail = sizeof(float) * (nb + w.cb) * hmax;
+  // trailing columns per CTA of the trailing update: up to 16, as shared
+  // memory allows (column segments of hmax rows)
+  int cbt = (int)(S2_SMEM_CAP / (sizeof(float) * hmax));
+  if (cbt > 16) cbt = 16;
+  if (cbt < 1) cbt = 1;
+  const size_t sm_trail = sizeof(float) * (size_t)cbt * hmax;
   const size_t sm_subst = sizeof(float) * 2 * ((size_t)g.kl + g.ku + nb);
   s2_smem_limits(sm_panel, sm_trail, sm_subst);
   const int nt = 256;
@@ -969,7 +1056,7 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
         k_s2_panel<<<1, S2_PNL_NT, sizeof(float) * (size_t)wd * H, st>>>(g, w, k0);
         const int ntrail = s2::trail_last(g, k0, wd) - (k0 + wd) + 1;
         if (ntrail > 0)
-          k_s2_trail<<<(ntrail + w.cb - 1) / w.cb, S2_NT, sizeof(float) * (size_t)(wd + w.cb) * H, st>>>(g, w, k0);
+          k_s2_trail<<<(ntrail + cbt - 1) / cbt, S2_NT, sizeof(float) * (size_t)cbt * H, st>>>(g, w, k0, cbt);
       }
     }
     const int nsweep = refactor ? S2_NREF : S2_NREF_REUSE;
