@@ -560,14 +560,13 @@ __global__ void __launch_bounds__(S2_SUB_NT) k_s2_subst(const s2::Grid g, S2Work
 
 // ---------------------------------------------------------------------------
 // The same substitutions across a cluster of SC_CL CTAs (SC_CL SMs) instead
-// of one CTA.  Per panel, warp 0 of every CTA applies the panel's
+// of one CTA.  Per panel, warp 0 of every CTA replays the panel's
 // interchanges and solves the 32 x 32 triangle for itself (the arithmetic of
 // k_s2_subst, in its order), while the other warps update their share of the
-// rows below (above, going backward), one row per lane; one cluster barrier
-// per panel.  Each thread asks L2 for the factor lines of the next panel
-// before the barrier, so that the panel's loads after it meet L2, not
-// DRAM.  The right-hand sides live in FP32 ping-pong vectors in global memory
-// (read and written at L2): panel k reads pair k % 2 and writes pair
+// rows below (above, going backward), one row per lane, with the factor
+// entries of the panel loaded during the previous panel; one cluster barrier
+// per panel.  The right-hand sides live in FP32 ping-pong vectors in global
+// memory (read and written at L2): panel k reads pair k % 2 and writes pair
 // (k + 1) % 2, so no CTA overwrites a value another may still read.  Rows a
 // panel does not write keep their value in both pairs (both start as the
 // input), which is what the next panel needs of them.
@@ -586,25 +585,16 @@ __device__ __forceinline__ unsigned sc_cluster_rank() {
   return r;
 }
 
-__device__ __forceinline__ void sc_prefetch_l2(const void* ptr) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
-}
-
-// Warp 0: the interchanges of the panel at k0 as a map of window positions,
-// m[r] = the window row whose value ends at position r (identity elsewhere);
-// the entries the previous use touched are put back first.  Lane j reads
-// pivot j; lane 0 applies them in order.
-__device__ void sc_build_map(const s2::Grid& g, const int32_t* piv, int nb, int k0, int* m, int* touched, int& nt,
-                             int lane) {
+// The panel's interchanges as a map of window positions: m[r] = the window
+// row whose value ends at position r (identity elsewhere); the entries the
+// previous use touched are put back first.
+__device__ void sc_build_map(const s2::Grid& g, const int32_t* piv, int nb, int k0, int* m, int* touched, int& nt) {
+  for (int q = 0; q < nt; ++q) m[touched[q]] = touched[q];
+  nt = 0;
   const int wd = s2::panel_width(g, nb, k0);
-  const int pl = lane < wd ? piv[k0 + lane] - k0 : 0;
-  if (lane == 0) {
-    for (int q = 0; q < nt; ++q) m[touched[q]] = touched[q];
-    nt = 0;
-  }
   for (int j = 0; j < wd; ++j) {
-    const int p = __shfl_sync(0xffffffffu, pl, j);
-    if (lane == 0 && p != j) {
+    const int p = piv[k0 + j] - k0;
+    if (p != j) {
       const int t = m[j];
       m[j] = m[p];
       m[p] = t;
@@ -623,43 +613,47 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
   const unsigned rank = sc_cluster_rank();
   const int nb = w.nb, N = g.N, ldp = g.kl + nb, hcap = g.kl + nb;
   const int nk = (N + nb - 1) / nb;
-  const int nup = SC_CL * SC_UW;                   // update warps in the cluster
-  const int uq = (int)rank * SC_UW + (warp - 1);  // this warp's place among them (warp >= 1)
+  const int nup = SC_CL * SC_UW;                        // update warps in the cluster
+  const int uq = (int)rank * SC_UW + (warp - 1);       // this warp's place among them (warp >= 1)
   int* const map0 = reinterpret_cast<int*>(s2_smem);  // two maps of hcap entries
   auto map = [&](int k) { return map0 + (k & 1) * hcap; };
   // pair p of right-hand-side vectors: rhs 0 at qv(p, 0), rhs 1 at qv(p, 1)
   auto qv = [&](int p, int c) { return w.q + (size_t)(2 * (p & 1) + c) * N; };
-  auto fill = [&](const double* v0s, const double* v1s) {
-    for (int u = (int)rank * SC_NT + tid; u < N; u += SC_CL * SC_NT) {
-      const float v0 = (float)__ldcg(v0s + u), v1 = (float)__ldcg(v1s + u);
-      __stcg(qv(0, 0) + u, v0);
-      __stcg(qv(0, 1) + u, v1);
-      __stcg(qv(1, 0) + u, v0);
-      __stcg(qv(1, 1) + u, v1);
-    }
-  };
-  // the factor lines a thread reads in the forward panel at k0 (one line per
-  // column: lane jj asks for column jj's)
-  auto prefetch_fwd = [&](int k0) {
-    const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
-    const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
-    const int jc = lane < wd ? lane : wd - 1;
-    const int r0 = warp == 0 ? 0 : wd + 32 * uq;
-    if (r0 < H) sc_prefetch_l2(Lk + (size_t)jc * ldp + r0);
-  };
   // ---- forward: L y = P b ----
-  fill(b0, b1);
+  for (int u = (int)rank * SC_NT + tid; u < N; u += SC_CL * SC_NT) {
+    const float v0 = (float)b0[u], v1 = (float)b1[u];
+    __stcg(qv(0, 0) + u, v0);
+    __stcg(qv(0, 1) + u, v1);
+    __stcg(qv(1, 0) + u, v0);
+    __stcg(qv(1, 1) + u, v1);
+  }
   for (int r = tid; r < 2 * hcap; r += SC_NT) map0[r] = r < hcap ? r : r - hcap;
   if (tid < 2) ntouch[tid] = 0;
   __syncthreads();
-  if (warp == 0) sc_build_map(g, w.piv, nb, 0, map(0), touched[0], ntouch[0], lane);
-  prefetch_fwd(0);
+  float fr[32];  // warp 0: row `lane` of the panel's unit lower triangle; update warps: the lane's row of L21
+  auto load_fwd = [&](int k0) {
+    const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
+    const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
+    if (warp == 0) {
+      const int i = lane, ic = i < wd ? i : wd - 1;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const float l = __ldg(Lk + (size_t)(jj < wd ? jj : wd - 1) * ldp + ic);
+        fr[jj] = (jj < i && i < wd) ? l : 0.0f;
+      }
+    } else {
+      const int r = wd + 32 * uq + lane;
+      const int rc = r < H ? r : H - 1;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) fr[jj] = __ldg(Lk + (size_t)(jj < wd ? jj : wd - 1) * ldp + rc);
+    }
+  };
+  if (warp == 0 && lane == 0) sc_build_map(g, w.piv, nb, 0, map(0), touched[0], ntouch[0]);
+  load_fwd(0);
   sc_cluster_sync();
-  float fr[32];
   for (int k = 0; k < nk; ++k) {
     const int k0 = k * nb;
     const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
-    const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
     const float* qa0 = qv(k, 0);
     const float* qa1 = qv(k, 1);
     float* qb0 = qv(k + 1, 0);
@@ -668,13 +662,8 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
     const int r = wd + 32 * uq + lane;
     float v0 = 0.0f, v1 = 0.0f;
     if (warp == 0) {
-      const int i = lane, ic = i < wd ? i : wd - 1;
+      const int i = lane;
       float a0 = i < wd ? __ldcg(qa0 + k0 + m[i]) : 0.0f, a1 = i < wd ? __ldcg(qa1 + k0 + m[i]) : 0.0f;
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) {
-        const float l = __ldg(Lk + (size_t)(jj < wd ? jj : wd - 1) * ldp + ic);
-        fr[jj] = (jj < i && i < wd) ? l : 0.0f;
-      }
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         if (jj < wd) {
@@ -694,19 +683,16 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
           w.y1[k0 + i] = a1;
         }
       }
-    } else {
-      const int rc = r < H ? r : H - 1;
-      if (r < H) {
-        v0 = __ldcg(qa0 + k0 + m[r]);
-        v1 = __ldcg(qa1 + k0 + m[r]);
-      }
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) fr[jj] = __ldg(Lk + (size_t)(jj < wd ? jj : wd - 1) * ldp + rc);
+    } else if (r < H) {
+      v0 = __ldcg(qa0 + k0 + m[r]);
+      v1 = __ldcg(qa1 + k0 + m[r]);
     }
     __syncthreads();
     if (warp == 0) {
-      if (k + 1 < nk)
-        sc_build_map(g, w.piv, nb, k0 + nb, map(k + 1), touched[(k + 1) & 1], ntouch[(k + 1) & 1], lane);
+      if (k + 1 < nk) {
+        load_fwd(k0 + nb);
+        if (lane == 0) sc_build_map(g, w.piv, nb, k0 + nb, map(k + 1), touched[(k + 1) & 1], ntouch[(k + 1) & 1]);
+      }
     } else {
       if (r < H) {
         float acc0 = 0.0f, acc1 = 0.0f;
@@ -718,7 +704,9 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
         __stcg(qb0 + k0 + r, v0 - acc0);
         __stcg(qb1 + k0 + r, v1 - acc1);
       }
-      // rows past the cluster's lanes (bands wider than 32 x SC_CL x SC_UW rows)
+      // rows past the cluster's lanes (bands wider than 32 x SC_CL x SC_UW
+      // rows): their entries are loaded here
+      const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
       for (int rr = r + 32 * nup; rr < H; rr += 32 * nup) {
         const float x0 = __ldcg(qa0 + k0 + m[rr]), x1 = __ldcg(qa1 + k0 + m[rr]);
         float acc0 = 0.0f, acc1 = 0.0f;
@@ -731,26 +719,38 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
         __stcg(qb0 + k0 + rr, x0 - acc0);
         __stcg(qb1 + k0 + rr, x1 - acc1);
       }
+      if (k + 1 < nk) load_fwd(k0 + nb);
     }
-    if (k + 1 < nk) prefetch_fwd(k0 + nb);
     sc_cluster_sync();
   }
   // ---- backward: U x = y ----
-  auto prefetch_bwd = [&](int k0) {
-    const int wd = s2::panel_width(g, nb, k0);
-    const int c = k0 + (lane < wd ? lane : wd - 1);
-    int r0 = k0, r1 = k0 + 1;  // rows [r0, r1) of column c this warp reads
-    if (warp != 0) {
-      const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
-      r0 = lo + 32 * uq;
-      r1 = r0 + 32 < k0 ? r0 + 32 : k0;
-      if (r0 < c - g.kl - g.ku) r0 = c - g.kl - g.ku;
-    }
-    if (r0 < r1) sc_prefetch_l2(w.AB + s2::band_at(g, r0, c));
-  };
-  fill(w.y0, w.y1);
+  for (int u = (int)rank * SC_NT + tid; u < N; u += SC_CL * SC_NT) {
+    const float v0 = (float)__ldcg(w.y0 + u), v1 = (float)__ldcg(w.y1 + u);
+    __stcg(qv(0, 0) + u, v0);
+    __stcg(qv(0, 1) + u, v1);
+    __stcg(qv(1, 0) + u, v0);
+    __stcg(qv(1, 1) + u, v1);
+  }
   float dg = 1.0f;
-  prefetch_bwd((nk - 1) * nb);
+  auto load_bwd = [&](int k0) {
+    const int wd = s2::panel_width(g, nb, k0);
+    if (warp == 0) {
+      const int i = lane, ic = i < wd ? i : wd - 1;
+      dg = i < wd ? __ldg(w.ud + k0 + i) : 1.0f;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const float u = s2::umul(g, w.AB, k0 + ic, k0 + (jj < wd ? jj : wd - 1));
+        fr[jj] = (jj > i && jj < wd) ? u : 0.0f;
+      }
+    } else {
+      const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
+      const int r = lo + 32 * uq + lane;
+      const int rc = r < k0 ? r : (k0 > 0 ? k0 - 1 : 0);
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) fr[jj] = s2::umul(g, w.AB, rc, k0 + (jj < wd ? jj : wd - 1));
+    }
+  };
+  load_bwd((nk - 1) * nb);
   sc_cluster_sync();
   for (int k = nk - 1, it = 0; k >= 0; --k, ++it) {
     const int k0 = k * nb;
@@ -763,14 +763,8 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
     const int r = lo + 32 * uq + lane;
     float v0 = 0.0f, v1 = 0.0f;
     if (warp == 0) {
-      const int i = lane, ic = i < wd ? i : wd - 1;
+      const int i = lane;
       float a0 = i < wd ? __ldcg(qa0 + k0 + i) : 0.0f, a1 = i < wd ? __ldcg(qa1 + k0 + i) : 0.0f;
-      dg = i < wd ? __ldg(w.ud + k0 + i) : 1.0f;
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) {
-        const float u = s2::umul(g, w.AB, k0 + ic, k0 + (jj < wd ? jj : wd - 1));
-        fr[jj] = (jj > i && jj < wd) ? u : 0.0f;
-      }
       float x0i = 0.0f, x1i = 0.0f;
 #pragma unroll
       for (int jj = 31; jj >= 0; --jj) {
@@ -795,17 +789,14 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
           o1[k0 + i] = x1i;
         }
       }
-    } else {
-      const int rc = r < k0 ? r : (k0 > 0 ? k0 - 1 : 0);
-      if (r < k0) {
-        v0 = __ldcg(qa0 + r);
-        v1 = __ldcg(qa1 + r);
-      }
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) fr[jj] = s2::umul(g, w.AB, rc, k0 + (jj < wd ? jj : wd - 1));
+    } else if (r < k0) {
+      v0 = __ldcg(qa0 + r);
+      v1 = __ldcg(qa1 + r);
     }
     __syncthreads();
-    if (warp != 0) {
+    if (warp == 0) {
+      if (k > 0) load_bwd(k0 - nb);
+    } else {
       if (r < k0) {
         float acc0 = 0.0f, acc1 = 0.0f;
 #pragma unroll
@@ -828,8 +819,8 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
         __stcg(qb0 + rr, x0 - acc0);
         __stcg(qb1 + rr, x1 - acc1);
       }
+      if (k > 0) load_bwd(k0 - nb);
     }
-    if (k > 0) prefetch_bwd(k0 - nb);
     sc_cluster_sync();
   }
 }
