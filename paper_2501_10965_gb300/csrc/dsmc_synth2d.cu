@@ -212,6 +212,15 @@ __global__ void k_s2_jac(const s2::Grid g, S2Work w, int band) {
   s2::jacobian_entries(g, w.x, b, rem / s2::NV, rem % s2::NV, band ? w.AB : nullptr, w.Jc);
 }
 
+__device__ __forceinline__ void s2_cp_async4(float* sdst, const float* gsrc, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void s2_cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Block-wide first row of largest magnitude from each thread's candidate
 // (best, bi): warps reduce by shuffles and write one candidate each into
 // buffer buf; after one barrier every warp reduces those candidates itself
@@ -263,7 +272,14 @@ __global__ void __launch_bounds__(S2_PNL_NT) k_s2_panel(const s2::Grid g, S2Work
   float* P = reinterpret_cast<float*>(s2_smem);
   const int tid = threadIdx.x;
   const int wd = s2::panel_width(g, w.nb, k0), H = s2::panel_height(g, wd, k0);
-  s2::panel_load(g, w.AB, k0, wd, H, P, tid, S2_PNL_NT);
+  // the panel arrives by asynchronous copies, all in flight at once (zero
+  // outside the band: the values of s2::panel_load)
+  for (int e = tid; e < wd * H; e += S2_PNL_NT) {
+    const int c = e / H, r = e - c * H;
+    const bool in = s2::in_band(g, k0 + r, k0 + c);
+    s2_cp_async4(P + e, w.AB + (in ? s2::band_at(g, k0 + r, k0 + c) : 0), in ? 4 : 0);
+  }
+  s2_cp_async_wait_all();
   __syncthreads();
   float best = -1.0f, pbest = -1.0f;
   int bi = INT_MAX;
@@ -318,15 +334,6 @@ __global__ void __launch_bounds__(S2_PNL_NT) k_s2_panel(const s2::Grid g, S2Work
   }
   __syncthreads();
   s2::panel_store(g, w.nb, w.AB, w.Lp, w.ud, k0, wd, H, P, tid, S2_PNL_NT);
-}
-
-__device__ __forceinline__ void s2_cp_async4(float* sdst, const float* gsrc, int src_bytes) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gsrc), "r"(src_bytes) : "memory");
-}
-
-__device__ __forceinline__ void s2_cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 // The panel's interchanges and eliminations on up to cbt trailing columns per
@@ -564,8 +571,8 @@ __global__ void __launch_bounds__(S2_SUB_NT) k_s2_subst(const s2::Grid g, S2Work
 // interchanges and solves the 32 x 32 triangle for itself (the arithmetic of
 // k_s2_subst, in its order), while the other warps update their share of the
 // rows below (above, going backward), one row per lane, with the factor
-// entries of the panel loaded during the previous panel; one cluster barrier
-// per panel.  The right-hand sides live in FP32 ping-pong vectors in global
+// entries of the panel loaded during the previous panel, between a thread's
+// arrival at the panel's cluster barrier and its wait there.  The right-hand sides live in FP32 ping-pong vectors in global
 // memory (read and written at L2): panel k reads pair k % 2 and writes pair
 // (k + 1) % 2, so no CTA overwrites a value another may still read.  Rows a
 // panel does not write keep their value in both pairs (both start as the
@@ -577,6 +584,16 @@ constexpr int SC_NT = 32 * (1 + SC_UW);  // and the solver warp (warp 0)
 
 __device__ __forceinline__ void sc_cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// the two halves of the barrier: a thread arrives once its stores of the
+// panel are issued, asks for the next panel's factor entries, and waits
+__device__ __forceinline__ void sc_cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void sc_cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ unsigned sc_cluster_rank() {
@@ -689,10 +706,11 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
     }
     __syncthreads();
     if (warp == 0) {
-      if (k + 1 < nk) {
-        load_fwd(k0 + nb);
-        if (lane == 0) sc_build_map(g, w.piv, nb, k0 + nb, map(k + 1), touched[(k + 1) & 1], ntouch[(k + 1) & 1]);
-      }
+      if (k + 1 < nk && lane == 0)
+        sc_build_map(g, w.piv, nb, k0 + nb, map(k + 1), touched[(k + 1) & 1], ntouch[(k + 1) & 1]);
+      __syncwarp();
+      sc_cluster_arrive();
+      if (k + 1 < nk) load_fwd(k0 + nb);
     } else {
       if (r < H) {
         float acc0 = 0.0f, acc1 = 0.0f;
@@ -719,9 +737,10 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
         __stcg(qb0 + k0 + rr, x0 - acc0);
         __stcg(qb1 + k0 + rr, x1 - acc1);
       }
+      sc_cluster_arrive();
       if (k + 1 < nk) load_fwd(k0 + nb);
     }
-    sc_cluster_sync();
+    sc_cluster_wait();
   }
   // ---- backward: U x = y ----
   for (int u = (int)rank * SC_NT + tid; u < N; u += SC_CL * SC_NT) {
@@ -795,6 +814,7 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
     }
     __syncthreads();
     if (warp == 0) {
+      sc_cluster_arrive();
       if (k > 0) load_bwd(k0 - nb);
     } else {
       if (r < k0) {
@@ -819,9 +839,10 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
         __stcg(qb0 + rr, x0 - acc0);
         __stcg(qb1 + rr, x1 - acc1);
       }
+      sc_cluster_arrive();
       if (k > 0) load_bwd(k0 - nb);
     }
-    sc_cluster_sync();
+    sc_cluster_wait();
   }
 }
 
