@@ -330,6 +330,58 @@ def run_adaptive_region(args):
     print(json.dumps({"adaptive_region": out, "kn_ref": 0.01}), flush=True)
 
 
+def run_synth2d(args):
+    """The 2D synthetic solve (Sec. 3 step 3) on its own: a smooth
+    recirculating cavity state with seeded HoT (workloads.smooth_cavity_state)
+    solved to a relative update of 1e-10 on nx x ny cells (uniform, or the
+    wall-refined grid of Sec. 4.1 with a first cell of 0.001), timed on the
+    host around the call (it synchronises), best of --synth2d-reps."""
+    import numpy as np
+    import torch
+
+    from paper_2501_10965_gb300 import dsmc, workloads as W
+    nx, ny = (int(v) for v in args.synth2d.lower().split("x"))
+    refined = args.synth2d_refined
+    if refined:
+        cfg = W.cavity_2d_refined(nx=nx, ny=ny, ppc=2, kn=0.05, dx_min=0.001, precision="fp64", synth2d=True,
+                                  synth_tol=1e-10, n_m=50)
+        q = float(cfg["stretch"])
+
+        def centres(n):
+            w = q ** np.minimum(np.arange(n), n - 1 - np.arange(n)).astype(np.float64)
+            e = np.concatenate([[0.0], np.cumsum(w / w.sum())])
+            return 0.5 * (e[:-1] + e[1:])
+        d, h = W.smooth_cavity_state(nx, ny, seed=5, xc=centres(nx), yc=centres(ny))
+    else:
+        cfg = W.cavity_2d(nx=nx, ny=ny, ppc=2, kn=0.05, precision="fp64", synth2d=True, synth_tol=1e-10, n_m=50)
+        d, h = W.smooth_cavity_state(nx, ny, seed=5)
+    sim = dsmc.Dsmc(cfg)
+    D = torch.tensor(d, dtype=torch.float64, device="cuda")
+    H = torch.tensor(h, dtype=torch.float64, device="cuda")
+    ts, it, res = [], 0, 0.0
+    for _ in range(max(1, args.synth2d_reps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, it, res = sim.synth_solve(D, H)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    print(json.dumps({"synth2d": f"{nx} x {ny}", "refined": refined, "unknowns": 5 * nx * ny,
+                      "ms_per_solve": 1e3 * min(ts), "all_ms": [1e3 * t for t in ts], "newton_steps": it,
+                      "max_residual": res}), flush=True)
+
+
+def run_tts2d(args):
+    """DIG against plain DSMC on a 2D lid-driven cavity, steps and GPU wall
+    time to steady state (dig.time_to_steady_2d): 50 x 50 cells of 0.02 (the
+    mean free path at Kn 0.02), 1000 particles per cell (2.5 M), lid 100 m/s,
+    N_s = 100, FP32 particles."""
+    from paper_2501_10965_gb300 import dig, workloads as W
+    cfg = W.cavity_2d(nx=50, ny=50, ppc=1000, kn=0.02, lid_mps=100.0, synth2d=True, synth_tol=1e-8, n_m=50)
+    out = dig.time_to_steady_2d(cfg)
+    print(json.dumps({"time_to_steady_2d": out, "kn": 0.02, "lid_mps": 100.0, "n_s": int(cfg["n_s"]),
+                      "kn_ref": float(cfg["kn_ref"])}), flush=True)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -496,8 +548,18 @@ def main():
                     help="only run warm-up + this many steps (for profiler captures)")
     ap.add_argument("--adaptive-region", action="store_true",
                     help="only measure the equilibrium area fraction of the cylinder cases")
+    ap.add_argument("--synth2d", default="",
+                    help="only time the 2D synthetic solve on NXxNY cells (e.g. 100x100)")
+    ap.add_argument("--synth2d-refined", action="store_true", help="on the wall-refined grid")
+    ap.add_argument("--synth2d-reps", type=int, default=3)
+    ap.add_argument("--tts2d", action="store_true",
+                    help="only measure DIG against plain DSMC to steady state on a 2D cavity")
     args = ap.parse_args()
-    if args.adaptive_region:
+    if args.tts2d:
+        run_tts2d(args)
+    elif args.synth2d:
+        run_synth2d(args)
+    elif args.adaptive_region:
         run_adaptive_region(args)
     elif args.profile_steps > 0:
         run_profile(args)

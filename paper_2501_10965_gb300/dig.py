@@ -326,3 +326,86 @@ def train_hot_model(cfgs: list, replicas: int = 32, snapshots=(100, 300, 700, 15
     info = {"cases": len(cases), "cells": g.ncells, "snapshots": len(data), "loss": loss}
     del g
     return params, info
+
+
+def binned2d(a: np.ndarray, nx: int, ny: int, bx: int, by: int) -> np.ndarray:
+    """Means over blocks of bx x by cells of a cell field (cell j nx + i)."""
+    g = a.reshape(ny, nx)[: (ny // by) * by, : (nx // bx) * bx]
+    return g.reshape(ny // by, by, nx // bx, bx).mean(axis=(1, 3))
+
+
+def time_to_steady_2d(cfg: dict, window: int = 200, bx: int = 5, by: int = 5, transient: int = 15000,
+                      average: int = 10000, threshold: float = 0.01, max_dig: int = 4000,
+                      max_plain: int = 20000) -> dict:
+    """Time to steady state of a 2D case, DIG against plain DSMC, from the
+    same uniform initial state.  The 2D synthetic solve takes one case per
+    handle, so each method runs one handle (many particles per cell instead
+    of an ensemble).  err(t) = the relative L2 errors of the flow velocity
+    (both components) and the total temperature, averaged over a window of
+    steps and over blocks of bx x by cells, against the long-run plain-DSMC
+    average of an independent handle (seed + 1000); the noise floor is the
+    median window error of that handle's averaging phase, and a run is
+    steady from the first window after which the larger error stays at or
+    below max(threshold, 1.5 x floor) for three windows."""
+    nx, ny = int(cfg["nx"]), int(cfg["ny"])
+
+    def reduce(f):
+        u = np.stack([binned2d(f[:, 1], nx, ny, bx, by), binned2d(f[:, 2], nx, ny, bx, by)])
+        return u, binned2d(total_temperature(f), nx, ny, bx, by)
+
+    def err(f, ref_u, ref_t):
+        u, t = reduce(f)
+        return (float(np.linalg.norm(u - ref_u) / np.linalg.norm(ref_u)),
+                float(np.linalg.norm(t - ref_t) / np.linalg.norm(ref_t)))
+
+    t0 = time.perf_counter()
+    ref = dsmc.Dsmc(dict(cfg, seed=int(cfg.get("seed", 0)) + 1000))
+    ref.dsmc_step(transient, sample=False)
+    wins = []
+    for _ in range(max(1, average // window)):
+        ref.dsmc_step(window, sample=True)
+        wins.append(ref.dsmc_sample(reset=True).cpu().numpy())
+    mean = np.mean(wins, axis=0)
+    ref_u, ref_t = reduce(mean)
+    floor = float(np.median([max(err(w, ref_u, ref_t)) for w in wins]))
+    del ref
+    thr = max(threshold, 1.5 * floor)
+    out = {"cells": f"{nx} x {ny}", "particles": nx * ny * int(cfg["ppc"]), "window": window,
+           "bins": f"{bx} x {by} cells", "noise_floor": floor, "threshold": thr, "reference_wall_s": time.perf_counter() - t0}
+    n_s = int(cfg["n_s"])
+    for method, cap in (("dig", max_dig), ("plain", max_plain)):
+        sim = dsmc.Dsmc(cfg)
+        hist, steps, walls, wall, nsteps = [], [], [], 0.0, 0
+        steady = None
+        while nsteps < cap:
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            if method == "dig":
+                fs = []
+                for _ in range(max(1, window // n_s)):
+                    r = dig_iteration(sim, n_s)
+                    fs.append(r["fields"].cpu().numpy())
+                f = np.mean(fs, axis=0)
+                nsteps += n_s * len(fs)
+            else:
+                sim.dsmc_step(window, sample=True)
+                f = sim.dsmc_sample(reset=True).cpu().numpy()
+                nsteps += window
+            torch.cuda.synchronize()
+            wall += time.perf_counter() - ta
+            hist.append(max(err(f, ref_u, ref_t)))
+            steps.append(nsteps)
+            walls.append(wall)
+            i = time_to_steady(hist, thr)
+            if i is not None:
+                steady = i
+                break
+        out[method] = {"steady_step": steps[steady] if steady is not None else None,
+                       "steady_wall_s": walls[steady] if steady is not None else None,
+                       "errors": [round(e, 4) for e in hist], "final_error": hist[-1] if hist else None}
+        del sim
+    d, p = out["dig"], out["plain"]
+    if d["steady_step"] and p["steady_step"]:
+        out["speedup_steps"] = p["steady_step"] / d["steady_step"]
+        out["speedup_wall"] = p["steady_wall_s"] / d["steady_wall_s"]
+    return out

@@ -243,3 +243,26 @@ def ensemble_1d(ncases: int = 64, seed: int = 0, **kw) -> list:
 def replicas(cfg: dict, n: int, seed0: int = 0) -> list:
     """`n` copies of one workload with Philox seeds seed0, seed0 + 1, ..."""
     return [dict(copy.deepcopy(cfg), seed=seed0 + r) for r in range(n)]
+
+def smooth_cavity_state(nx: int, ny: int, seed: int = 0, hot_amp: float = 1e-3, xc=None, yc=None):
+    """A smooth recirculating cavity-like state as sampled fields (ncells x
+    18: rho 1 + 0.02 cos(pi x), a single vortex of amplitude 0.05 in (u_x,
+    u_y), u_z 0.003, T_t 1 + 0.01 y, T_r 1 + 0.012 y) and seeded normal HoT
+    of amplitude hot_amp (ncells x 12), at the cell centres xc (nx), yc (ny)
+    (default: the uniform grid's), for timing and checking the synthetic
+    solve."""
+    import numpy as np
+    if xc is None:
+        xc = (np.arange(nx) + 0.5) / nx
+    if yc is None:
+        yc = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(np.asarray(xc), np.asarray(yc))
+    d = np.zeros((ny, nx, 18))
+    d[..., 0] = 1 + 0.02 * np.cos(np.pi * X)
+    d[..., 1] = 0.05 * np.sin(np.pi * X) * np.cos(np.pi * Y) * np.sin(np.pi * Y)
+    d[..., 2] = -0.05 * np.cos(np.pi * X) * np.sin(np.pi * X) * np.sin(np.pi * Y)
+    d[..., 3] = 0.003
+    d[..., 4] = 1 + 0.01 * Y
+    d[..., 5] = 1 + 0.012 * Y
+    h = hot_amp * np.random.default_rng(seed).standard_normal((nx * ny, 12))
+    return d.reshape(nx * ny, 18), h
