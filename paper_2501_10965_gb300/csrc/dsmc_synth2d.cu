@@ -567,33 +567,39 @@ __global__ void __launch_bounds__(S2_SUB_NT) k_s2_subst(const s2::Grid g, S2Work
 
 // ---------------------------------------------------------------------------
 // The same substitutions across a cluster of SC_CL CTAs (SC_CL SMs) instead
-// of one CTA.  Per panel, warp 0 of every CTA replays the panel's
-// interchanges and solves the 32 x 32 triangle for itself (the arithmetic of
-// k_s2_subst, in its order), while the other warps update their share of the
-// rows below (above, going backward), one row per lane, with the factor
-// entries of the panel loaded during the previous panel, between a thread's
-// arrival at the panel's cluster barrier and its wait there.  The right-hand sides live in FP32 ping-pong vectors in global
-// memory (read and written at L2): panel k reads pair k % 2 and writes pair
-// (k + 1) % 2, so no CTA overwrites a value another may still read.  Rows a
-// panel does not write keep their value in both pairs (both start as the
-// input), which is what the next panel needs of them.
+// of one CTA.  Per panel, warp 0 of every CTA applies the panel's
+// interchanges and multiplies the panel's head by the inverse of its 32 x 32
+// triangle (a product of 32 independent terms instead of a chain of 32
+// dependent eliminations); warp 1 computes those inverses two panels ahead;
+// the other warps update their share of the rows below (above, going
+// backward), one row per lane, with the factor entries of the panel loaded
+// between a thread's arrival at the previous panel's cluster barrier and its
+// wait there.  One cluster barrier per panel.  The right-hand sides live in
+// FP32 ping-pong vectors in global memory (read and written at L2): panel k
+// reads pair k % 2 and writes pair (k + 1) % 2, so no CTA overwrites a value
+// another may still read.  Rows a panel does not write keep their value in
+// both pairs (both start as the input), which is what the next panel needs.
 // ---------------------------------------------------------------------------
 constexpr int SC_CL = 8;                 // CTAs: one cluster (the portable maximum)
-constexpr int SC_UW = 8;                 // update warps per CTA
-constexpr int SC_NT = 32 * (1 + SC_UW);  // and the solver warp (warp 0)
+constexpr int SC_UW = 8;                 // update warps per CTA (warps 2 .. SC_UW + 1)
+constexpr int SC_NT = 32 * (2 + SC_UW);  // warp 0 solves, warp 1 inverts ahead
 
 __device__ __forceinline__ void sc_cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// the two halves of the barrier: a thread arrives once its stores of the
-// panel are issued, asks for the next panel's factor entries, and waits
 __device__ __forceinline__ void sc_cluster_arrive() {
   asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void sc_cluster_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// barrier 1 of the CTA for the solver and update warps only (warp 1 keeps
+// to its own pace between cluster barriers)
+__device__ __forceinline__ void sc_bar_solve_update() {
+  asm volatile("bar.sync 1, %0;" ::"r"(32 * (1 + SC_UW)) : "memory");
 }
 
 __device__ __forceinline__ unsigned sc_cluster_rank() {
@@ -621,52 +627,108 @@ __device__ void sc_build_map(const s2::Grid& g, const int32_t* piv, int nb, int 
   }
 }
 
+// Row `lane` of the panel at k0's 32 x 32 triangle (identity rows past the
+// panel's width): the unit lower L11 (forward, below the diagonal only) or
+// the upper U11 with its diagonal (backward).
+__device__ __forceinline__ void sc_tri_row(const s2::Grid& g, const S2Work& w, bool lower, int k0, int lane,
+                                           float* row) {
+  const int nb = w.nb, ldp = g.kl + nb;
+  const int wd = s2::panel_width(g, nb, k0);
+  const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    float v = j == lane ? 1.0f : 0.0f;
+    if (lane < wd && j < wd) {
+      if (lower)
+        v = j < lane ? __ldg(Lk + (size_t)j * ldp + lane) : (j == lane ? 1.0f : 0.0f);
+      else
+        v = j >= lane ? s2::umul(g, w.AB, k0 + lane, k0 + j) : 0.0f;
+    }
+    row[j] = v;
+  }
+}
+
+// The inverse of a triangle given by rows (row[j] of lane i = T[i][j]) into
+// inv[i][j]: lane c solves T x = e_c, forward (lower, unit diagonal) or
+// backward (upper), with the triangle staged in sc.
+__device__ __forceinline__ void sc_tri_inverse(bool lower, const float* row, float (*sc)[33], float (*inv)[33],
+                                               int lane) {
+#pragma unroll
+  for (int j = 0; j < 32; ++j) sc[lane][j] = row[j];
+  __syncwarp();
+  float x[32];
+  if (lower) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int j = 0; j < i; ++j) acc += sc[i][j] * x[j];
+      x[i] = i == lane ? 1.0f : (i > lane ? -acc : 0.0f);
+    }
+  } else {
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int j = i + 1; j < 32; ++j) acc += sc[i][j] * x[j];
+      const float rd = 1.0f / sc[i][i];
+      x[i] = i == lane ? rd : (i < lane ? -acc * rd : 0.0f);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 32; ++i) inv[i][lane] = x[i];
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work w, const double* b0,
                                                        const double* b1, double* o0, double* o1) {
   __shared__ float ty0[32], ty1[32];
   __shared__ int touched[2][64];
   __shared__ int ntouch[2];
+  __shared__ float invs[3][32][33];  // triangle inverses: panels k, k + 1, k + 2
+  __shared__ float scr[32][33];      // warp 1's staging of a triangle
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned rank = sc_cluster_rank();
   const int nb = w.nb, N = g.N, ldp = g.kl + nb, hcap = g.kl + nb;
   const int nk = (N + nb - 1) / nb;
-  const int nup = SC_CL * SC_UW;                        // update warps in the cluster
-  const int uq = (int)rank * SC_UW + (warp - 1);       // this warp's place among them (warp >= 1)
+  const int nup = SC_CL * SC_UW;                  // update warps in the cluster
+  const int uq = (int)rank * SC_UW + (warp - 2);  // this warp's place among them (warp >= 2)
   int* const map0 = reinterpret_cast<int*>(s2_smem);  // two maps of hcap entries
   auto map = [&](int k) { return map0 + (k & 1) * hcap; };
   // pair p of right-hand-side vectors: rhs 0 at qv(p, 0), rhs 1 at qv(p, 1)
   auto qv = [&](int p, int c) { return w.q + (size_t)(2 * (p & 1) + c) * N; };
+  auto fill = [&](const double* v0s, const double* v1s) {
+    for (int u = (int)rank * SC_NT + tid; u < N; u += SC_CL * SC_NT) {
+      const float v0 = (float)__ldcg(v0s + u), v1 = (float)__ldcg(v1s + u);
+      __stcg(qv(0, 0) + u, v0);
+      __stcg(qv(0, 1) + u, v1);
+      __stcg(qv(1, 0) + u, v0);
+      __stcg(qv(1, 1) + u, v1);
+    }
+  };
+  float fr[32];  // warp 1: a triangle's row `lane`, fetched ahead; update warps: the lane's row of L21 or U12
   // ---- forward: L y = P b ----
-  for (int u = (int)rank * SC_NT + tid; u < N; u += SC_CL * SC_NT) {
-    const float v0 = (float)b0[u], v1 = (float)b1[u];
-    __stcg(qv(0, 0) + u, v0);
-    __stcg(qv(0, 1) + u, v1);
-    __stcg(qv(1, 0) + u, v0);
-    __stcg(qv(1, 1) + u, v1);
-  }
+  auto load_l21 = [&](int k0) {
+    const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
+    const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
+    const int r = wd + 32 * uq + lane;
+    const int rc = r < H ? r : H - 1;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) fr[jj] = __ldg(Lk + (size_t)(jj < wd ? jj : wd - 1) * ldp + rc);
+  };
+  fill(b0, b1);
   for (int r = tid; r < 2 * hcap; r += SC_NT) map0[r] = r < hcap ? r : r - hcap;
   if (tid < 2) ntouch[tid] = 0;
   __syncthreads();
-  float fr[32];  // warp 0: row `lane` of the panel's unit lower triangle; update warps: the lane's row of L21
-  auto load_fwd = [&](int k0) {
-    const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
-    const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
-    if (warp == 0) {
-      const int i = lane, ic = i < wd ? i : wd - 1;
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) {
-        const float l = __ldg(Lk + (size_t)(jj < wd ? jj : wd - 1) * ldp + ic);
-        fr[jj] = (jj < i && i < wd) ? l : 0.0f;
-      }
-    } else {
-      const int r = wd + 32 * uq + lane;
-      const int rc = r < H ? r : H - 1;
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) fr[jj] = __ldg(Lk + (size_t)(jj < wd ? jj : wd - 1) * ldp + rc);
-    }
-  };
   if (warp == 0 && lane == 0) sc_build_map(g, w.piv, nb, 0, map(0), touched[0], ntouch[0]);
-  load_fwd(0);
+  if (warp == 1) {
+    for (int q = 0; q < 2 && q < nk; ++q) {
+      sc_tri_row(g, w, true, q * nb, lane, fr);
+      sc_tri_inverse(true, fr, scr, invs[q], lane);
+    }
+    if (nk > 2) sc_tri_row(g, w, true, 2 * nb, lane, fr);
+  }
+  if (warp >= 2) load_l21(0);
   sc_cluster_sync();
   for (int k = 0; k < nk; ++k) {
     const int k0 = k * nb;
@@ -680,37 +742,38 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
     float v0 = 0.0f, v1 = 0.0f;
     if (warp == 0) {
       const int i = lane;
-      float a0 = i < wd ? __ldcg(qa0 + k0 + m[i]) : 0.0f, a1 = i < wd ? __ldcg(qa1 + k0 + m[i]) : 0.0f;
+      const float a0 = i < wd ? __ldcg(qa0 + k0 + m[i]) : 0.0f, a1 = i < wd ? __ldcg(qa1 + k0 + m[i]) : 0.0f;
+      float (*inv)[33] = invs[k % 3];
+      float y0 = 0.0f, y1 = 0.0f;
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
-        if (jj < wd) {
-          const float y0j = __shfl_sync(0xffffffffu, a0, jj);
-          const float y1j = __shfl_sync(0xffffffffu, a1, jj);
-          if (i > jj && i < wd) {
-            a0 -= fr[jj] * y0j;
-            a1 -= fr[jj] * y1j;
-          }
-        }
+        const float b0j = __shfl_sync(0xffffffffu, a0, jj), b1j = __shfl_sync(0xffffffffu, a1, jj);
+        const float t = inv[i][jj];
+        y0 += t * b0j;
+        y1 += t * b1j;
       }
       if (i < wd) {
-        ty0[i] = a0;
-        ty1[i] = a1;
+        ty0[i] = y0;
+        ty1[i] = y1;
         if (rank == 0) {
-          w.y0[k0 + i] = a0;
-          w.y1[k0 + i] = a1;
+          w.y0[k0 + i] = y0;
+          w.y1[k0 + i] = y1;
         }
       }
-    } else if (r < H) {
+    } else if (warp >= 2 && r < H) {
       v0 = __ldcg(qa0 + k0 + m[r]);
       v1 = __ldcg(qa1 + k0 + m[r]);
     }
-    __syncthreads();
+    if (warp != 1) sc_bar_solve_update();
     if (warp == 0) {
       if (k + 1 < nk && lane == 0)
         sc_build_map(g, w.piv, nb, k0 + nb, map(k + 1), touched[(k + 1) & 1], ntouch[(k + 1) & 1]);
       __syncwarp();
       sc_cluster_arrive();
-      if (k + 1 < nk) load_fwd(k0 + nb);
+    } else if (warp == 1) {
+      if (k + 2 < nk) sc_tri_inverse(true, fr, scr, invs[(k + 2) % 3], lane);
+      sc_cluster_arrive();
+      if (k + 3 < nk) sc_tri_row(g, w, true, k0 + 3 * nb, lane, fr);
     } else {
       if (r < H) {
         float acc0 = 0.0f, acc1 = 0.0f;
@@ -722,8 +785,7 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
         __stcg(qb0 + k0 + r, v0 - acc0);
         __stcg(qb1 + k0 + r, v1 - acc1);
       }
-      // rows past the cluster's lanes (bands wider than 32 x SC_CL x SC_UW
-      // rows): their entries are loaded here
+      // rows past the cluster's lanes (bands wider than 32 x SC_CL x SC_UW rows)
       const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
       for (int rr = r + 32 * nup; rr < H; rr += 32 * nup) {
         const float x0 = __ldcg(qa0 + k0 + m[rr]), x1 = __ldcg(qa1 + k0 + m[rr]);
@@ -738,38 +800,29 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
         __stcg(qb1 + k0 + rr, x1 - acc1);
       }
       sc_cluster_arrive();
-      if (k + 1 < nk) load_fwd(k0 + nb);
+      if (k + 1 < nk) load_l21(k0 + nb);
     }
     sc_cluster_wait();
   }
   // ---- backward: U x = y ----
-  for (int u = (int)rank * SC_NT + tid; u < N; u += SC_CL * SC_NT) {
-    const float v0 = (float)__ldcg(w.y0 + u), v1 = (float)__ldcg(w.y1 + u);
-    __stcg(qv(0, 0) + u, v0);
-    __stcg(qv(0, 1) + u, v1);
-    __stcg(qv(1, 0) + u, v0);
-    __stcg(qv(1, 1) + u, v1);
-  }
-  float dg = 1.0f;
-  auto load_bwd = [&](int k0) {
+  auto load_u12 = [&](int k0) {
     const int wd = s2::panel_width(g, nb, k0);
-    if (warp == 0) {
-      const int i = lane, ic = i < wd ? i : wd - 1;
-      dg = i < wd ? __ldg(w.ud + k0 + i) : 1.0f;
+    const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
+    const int r = lo + 32 * uq + lane;
+    const int rc = r < k0 ? r : (k0 > 0 ? k0 - 1 : 0);
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) {
-        const float u = s2::umul(g, w.AB, k0 + ic, k0 + (jj < wd ? jj : wd - 1));
-        fr[jj] = (jj > i && jj < wd) ? u : 0.0f;
-      }
-    } else {
-      const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
-      const int r = lo + 32 * uq + lane;
-      const int rc = r < k0 ? r : (k0 > 0 ? k0 - 1 : 0);
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) fr[jj] = s2::umul(g, w.AB, rc, k0 + (jj < wd ? jj : wd - 1));
-    }
+    for (int jj = 0; jj < 32; ++jj) fr[jj] = s2::umul(g, w.AB, rc, k0 + (jj < wd ? jj : wd - 1));
   };
-  load_bwd((nk - 1) * nb);
+  fill(w.y0, w.y1);
+  const int klast = (nk - 1) * nb;
+  if (warp == 1) {
+    for (int q = 0; q < 2 && q < nk; ++q) {
+      sc_tri_row(g, w, false, klast - q * nb, lane, fr);
+      sc_tri_inverse(false, fr, scr, invs[q], lane);
+    }
+    if (nk > 2) sc_tri_row(g, w, false, klast - 2 * nb, lane, fr);
+  }
+  if (warp >= 2) load_u12(klast);
   sc_cluster_sync();
   for (int k = nk - 1, it = 0; k >= 0; --k, ++it) {
     const int k0 = k * nb;
@@ -783,39 +836,35 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
     float v0 = 0.0f, v1 = 0.0f;
     if (warp == 0) {
       const int i = lane;
-      float a0 = i < wd ? __ldcg(qa0 + k0 + i) : 0.0f, a1 = i < wd ? __ldcg(qa1 + k0 + i) : 0.0f;
-      float x0i = 0.0f, x1i = 0.0f;
+      const float a0 = i < wd ? __ldcg(qa0 + k0 + i) : 0.0f, a1 = i < wd ? __ldcg(qa1 + k0 + i) : 0.0f;
+      float (*inv)[33] = invs[it % 3];
+      float x0 = 0.0f, x1 = 0.0f;
 #pragma unroll
-      for (int jj = 31; jj >= 0; --jj) {
-        if (jj < wd) {
-          const float x0j = __shfl_sync(0xffffffffu, a0 / dg, jj);
-          const float x1j = __shfl_sync(0xffffffffu, a1 / dg, jj);
-          if (i == jj) {
-            x0i = x0j;
-            x1i = x1j;
-          }
-          if (i < jj) {
-            a0 -= fr[jj] * x0j;
-            a1 -= fr[jj] * x1j;
-          }
-        }
+      for (int jj = 0; jj < 32; ++jj) {
+        const float y0j = __shfl_sync(0xffffffffu, a0, jj), y1j = __shfl_sync(0xffffffffu, a1, jj);
+        const float t = inv[i][jj];
+        x0 += t * y0j;
+        x1 += t * y1j;
       }
       if (i < wd) {
-        ty0[i] = x0i;
-        ty1[i] = x1i;
+        ty0[i] = x0;
+        ty1[i] = x1;
         if (rank == 0) {
-          o0[k0 + i] = x0i;
-          o1[k0 + i] = x1i;
+          o0[k0 + i] = x0;
+          o1[k0 + i] = x1;
         }
       }
-    } else if (r < k0) {
+    } else if (warp >= 2 && r < k0) {
       v0 = __ldcg(qa0 + r);
       v1 = __ldcg(qa1 + r);
     }
-    __syncthreads();
+    if (warp != 1) sc_bar_solve_update();
     if (warp == 0) {
       sc_cluster_arrive();
-      if (k > 0) load_bwd(k0 - nb);
+    } else if (warp == 1) {
+      if (it + 2 < nk) sc_tri_inverse(false, fr, scr, invs[(it + 2) % 3], lane);
+      sc_cluster_arrive();
+      if (it + 3 < nk) sc_tri_row(g, w, false, k0 - 3 * nb, lane, fr);
     } else {
       if (r < k0) {
         float acc0 = 0.0f, acc1 = 0.0f;
@@ -840,7 +889,7 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
         __stcg(qb1 + rr, x1 - acc1);
       }
       sc_cluster_arrive();
-      if (k > 0) load_bwd(k0 - nb);
+      if (k > 0) load_u12(k0 - nb);
     }
     sc_cluster_wait();
   }
