@@ -371,15 +371,24 @@ def run_synth2d(args):
 
 
 def run_tts2d(args):
-    """DIG against plain DSMC on a 2D lid-driven cavity, steps and GPU wall
-    time to steady state (dig.time_to_steady_2d): 50 x 50 cells of 0.02 (the
-    mean free path at Kn 0.02), 1000 particles per cell (2.5 M), lid 100 m/s,
-    N_s = 100, FP32 particles."""
+    """DIG against plain DSMC on 2D lid-driven cavities, steps and GPU wall
+    time to steady state (dig.time_to_steady_2d), from the same uniform
+    state, lid 100 m/s, N_s = 100, FP32 particles, cells of the mean free
+    path: Kn 0.02 on 50 x 50 cells (1000 per cell, 2.5 M particles; windows
+    of 200 steps, bins of 5 x 5 cells) and Kn 0.01 on 100 x 100 (500 per
+    cell, 5 M; windows of 500 steps, bins of 10 x 10 cells), where viscous
+    diffusion takes four times longer."""
     from paper_2501_10965_gb300 import dig, workloads as W
-    cfg = W.cavity_2d(nx=50, ny=50, ppc=1000, kn=0.02, lid_mps=100.0, synth2d=True, synth_tol=1e-8, n_m=50)
-    out = dig.time_to_steady_2d(cfg)
-    print(json.dumps({"time_to_steady_2d": out, "kn": 0.02, "lid_mps": 100.0, "n_s": int(cfg["n_s"]),
-                      "kn_ref": float(cfg["kn_ref"])}), flush=True)
+    out = []
+    for kn, n, ppc, window, b, transient, average, max_plain in ((0.02, 50, 1000, 200, 5, 15000, 10000, 20000),
+                                                                 (0.01, 100, 500, 500, 10, 40000, 20000, 40000)):
+        if args.tts2d_case and args.tts2d_case != str(kn):
+            continue
+        cfg = W.cavity_2d(nx=n, ny=n, ppc=ppc, kn=kn, lid_mps=100.0, synth2d=True, synth_tol=1e-8, n_m=50)
+        r = dig.time_to_steady_2d(cfg, window=window, bx=b, by=b, transient=transient, average=average,
+                                  max_dig=4000, max_plain=max_plain)
+        out.append(dict(r, kn=kn, lid_mps=100.0, n_s=int(cfg["n_s"]), kn_ref=float(cfg["kn_ref"])))
+        print(json.dumps({"time_to_steady_2d": out[-1]}), flush=True)
 
 
 def run_gpu(args):
@@ -553,7 +562,8 @@ def main():
     ap.add_argument("--synth2d-refined", action="store_true", help="on the wall-refined grid")
     ap.add_argument("--synth2d-reps", type=int, default=3)
     ap.add_argument("--tts2d", action="store_true",
-                    help="only measure DIG against plain DSMC to steady state on a 2D cavity")
+                    help="only measure DIG against plain DSMC to steady state on 2D cavities")
+    ap.add_argument("--tts2d-case", default="", help="only the case of this Kn (0.02 or 0.01)")
     args = ap.parse_args()
     if args.tts2d:
         run_tts2d(args)
