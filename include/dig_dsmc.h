@@ -100,9 +100,9 @@ typedef struct dsmc_config {
    * the one-sided flux of a drifting Maxwellian.  lx, ly are not used; ppc
    * is the mean number of particles per cell, the weight F = init_rho x
    * (annulus area / cells) / ppc, and cell c starts with Iround(init_rho
-   * V_c / F) particles.  Single case only; synth_solve returns
-   * DSMC_ERR_ARG on it (dsmc_hot, dig_correct and the HoT network work on
-   * its polar gradients and cell volumes).
+   * V_c / F) particles.  Single case only; dsmc_hot, dig_correct and the
+   * HoT network work on its polar gradients and cell volumes, synth_solve
+   * with synth2d = 1 (nx >= 5 sectors, ny >= 3 rings).
    * DSMC_MESH_REFINED is the wall-refined 2D box of Sec. 4.1: the box's
    * walls, nx x ny cells whose widths grow geometrically by the factor q =
    * stretch from both walls of each axis to the middle (widths proportional
@@ -206,13 +206,21 @@ int dsmc_hot(dsmc_handle *h, const double *dev_fields, double *dev_hot, double *
  * reduction of the block-tridiagonal Newton system.
  *
  * 2D box, uniform or wall-refined (single case with synth2d = 1; nx, ny >=
- * 3): unknowns rho, u_x,
- * u_y, T_t, T_r per cell (u_z keeps its sampled value); cells next to a wall
- * keep the sampled u_x, u_y, T_t, T_r and balance their mass; the four
- * corner cells keep their sampled state and exchange no flux; cell (1, 0)'s
- * mass balance is replaced by the total mass (sum rho V_c); face fluxes carry a
- * fourth-difference dissipation of the conserved variables (1/32 of the
- * face's |u_n| + sound speed).  Residual and central-difference Jacobian in
+ * 3): unknowns rho, u_x, u_y, T_t, T_r per cell (u_z keeps its sampled
+ * value); cells next to a wall keep the sampled u_x, u_y, T_t, T_r and
+ * balance their mass; the four corner cells keep their sampled state and
+ * exchange no flux; cell (1, 0)'s mass balance is replaced by the total mass
+ * (sum rho V_c); face fluxes carry a fourth-difference dissipation of the
+ * conserved variables (1/32 of the face's |u_n| + sound speed).
+ *
+ * Annulus around a cylinder (single case with synth2d = 1; nx >= 5 sectors,
+ * ny >= 3 rings): the same equations by finite volumes on the sector cells
+ * (face vectors the integrals of the faces' normals, so a uniform state is
+ * exact; velocities Cartesian, each face's flux in its own normal frame);
+ * the ring next to the cylinder keeps the sampled u, T and balances its
+ * mass, the outer ring keeps its whole sampled state; no total-mass row.
+ *
+ * Residual and central-difference Jacobian in
  * FP64; each Newton step solves with a blocked banded LU factorisation
  * (partial pivoting) of the Jacobian in FP32 and iterative refinement with
  * FP64 residuals; later Newton steps reuse the factorisation while the
@@ -220,7 +228,7 @@ int dsmc_hot(dsmc_handle *h, const double *dev_fields, double *dev_hot, double *
  *
  * dev_out is ncells x DSMC_NTARGET.  host_iters / host_resid (may be NULL)
  * receive the iteration count and the final max |residual|.  Returns
- * DSMC_ERR_ARG on the annulus and on a 2D handle without synth2d;
+ * DSMC_ERR_ARG on a 2D handle without synth2d;
  * DSMC_ERR_NOT_CONVERGED (outputs written) when the iteration limit is
  * reached; DSMC_ERR_NUMERIC when no Newton update keeps rho > 0 and T > 0
  * (noisy HoT can make rho = (P - HoT_xx) / T_t negative in 1D, and a

@@ -48,6 +48,7 @@ struct dsmc_handle {
   // annulus tables (device): squared ring radii, rays, outer-face
   // directions, cell volumes, in FP64 and FP32
   double *ann_r2t_d = nullptr, *ann_ray_d = nullptr, *ann_fn_d = nullptr, *ann_vol_d = nullptr;
+  double* ann_rt_d = nullptr;  // ring radii (the annulus's synthetic solve)
   double *ref_xe_d = nullptr, *ref_ye_d = nullptr;  // wall-refined box: cell edges (volumes in ann_vol_*)
   float *ref_xe_f = nullptr, *ref_ye_f = nullptr;
   double* ann_mu_d = nullptr;  // expected freestream entries of every outer face per step
@@ -139,10 +140,12 @@ int validate(const dsmc_config* c, char* why, size_t n) {
   if (ncells > (1LL << 26)) return snprintf(why, n, "too many cells"), DSMC_ERR_ARG;
   if (c->synth2d != 0 && c->synth2d != 1) return snprintf(why, n, "synth2d must be 0 or 1"), DSMC_ERR_ARG;
   if (c->synth2d) {
-    if (c->dim != 2 || ann || c->nx < 3 || c->ny < 3)
-      return snprintf(why, n, "synth2d needs a 2D box of at least 3 x 3 cells"), DSMC_ERR_ARG;
-    if (std::min(c->nx, c->ny) > 500)
-      return snprintf(why, n, "synth2d: the shorter side must have at most 500 cells"), DSMC_ERR_ARG;
+    if (c->dim != 2 || (ann ? (c->nx < 5 || c->ny < 3) : (c->nx < 3 || c->ny < 3)))
+      return snprintf(why, n, "synth2d needs a 2D box of at least 3 x 3 cells or an annulus of at least 5 x 3"),
+             DSMC_ERR_ARG;
+    if ((ann ? c->nx : std::min(c->nx, c->ny)) > 500)
+      return snprintf(why, n, "synth2d: at most 500 cells on the band's side (the sectors of an annulus)"),
+             DSMC_ERR_ARG;
     // the band storage must stay addressable with 64-bit offsets and the
     // unknowns with int
     if (ncells * 5 > (1LL << 28)) return snprintf(why, n, "synth2d: too many cells"), DSMC_ERR_ARG;
@@ -238,7 +241,7 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
     int t = pl.det ? 2 * c->ppc : (5 * c->ppc) / 4 + 32;
     if (t > tile) tile = t;
     if (c->dim == 1) synth += synth1d_work_doubles(nc);
-    if (c->dim == 2 && c->synth2d) synth += synth2d_work_doubles(c->nx, c->ny);
+    if (c->dim == 2 && c->synth2d) synth += synth2d_work_doubles(c->nx, c->ny, c->mesh == DSMC_MESH_ANNULUS);
   }
   pl.capacity = capacity;
   tile = pl.det ? (tile + 31) & ~31 : (tile + 15) & ~15;  // FP32: 16-float multiple for bulk copies
@@ -289,6 +292,7 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
   float* r_xef = cv.take<float>(nxe);
   float* r_yef = cv.take<float>(nye);
   double* a_r2d = cv.take<double>(nr1);
+  double* a_rtd = cv.take<double>(nr1);
   double* a_rayd = cv.take<double>(nray);
   double* a_fnd = cv.take<double>(nfn);
   double* a_vold = cv.take<double>(nvol);
@@ -304,6 +308,7 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
     h->ref_ye_f = r_yef;
     h->ann_mu_d = a_mu;
     h->ann_r2t_d = a_r2d;
+    h->ann_rt_d = a_rtd;
     h->ann_ray_d = a_rayd;
     h->ann_fn_d = a_fnd;
     h->ann_vol_d = a_vold;
@@ -330,7 +335,7 @@ Plan make_plan(const dsmc_config* cs, int ncases, char* base, dsmc_handle* h) {
 // 2 pi k / nx (ray nx = ray 0), outer-face centre directions at 2 pi (k +
 // 1/2) / nx, cell volumes (pi / nx) (R_{j+1}^2 - R_j^2).
 struct AnnTables {
-  std::vector<double> r2t, ray, fn, vol;
+  std::vector<double> rt, r2t, ray, fn, vol;
   double area = 0.0;
 };
 
@@ -345,6 +350,7 @@ AnnTables ann_tables(const dsmc_config* c) {
   }
   rt[0] = c->r_in;
   rt[nr] = c->r_out;
+  t.rt = rt;
   t.r2t.resize(nr + 1);
   for (int j = 0; j <= nr; ++j) t.r2t[j] = rt[j] * rt[j];
   t.ray.resize(2 * (nt + 1));
@@ -469,6 +475,7 @@ void fill_params(const dsmc_config* c, Params<T>& p, CellParams& cp) {
   cp.mesh = p.mesh;
   cp.vol = nullptr;
   cp.r2t = nullptr;
+  cp.rt = nullptr;
   cp.xe = cp.ye = nullptr;
 }
 
@@ -483,6 +490,7 @@ int set_ann_tables(dsmc_handle* h) {
   const std::vector<float> r2f = f32(t.r2t), rayf = f32(t.ray), fnf = f32(t.fn), volf = f32(t.vol);
   cudaStream_t st = h->stream;
   cudaMemcpyAsync(h->ann_r2t_d, t.r2t.data(), sizeof(double) * t.r2t.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ann_rt_d, t.rt.data(), sizeof(double) * t.rt.size(), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(h->ann_ray_d, t.ray.data(), sizeof(double) * t.ray.size(), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(h->ann_fn_d, t.fn.data(), sizeof(double) * t.fn.size(), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(h->ann_vol_d, t.vol.data(), sizeof(double) * t.vol.size(), cudaMemcpyHostToDevice, st);
@@ -502,6 +510,7 @@ int set_ann_tables(dsmc_handle* h) {
   h->pf.vol = h->ann_vol_f;
   h->cp.vol = h->ann_vol_d;
   h->cp.r2t = h->ann_r2t_d;
+  h->cp.rt = h->ann_rt_d;
   return DSMC_OK;
 }
 
@@ -930,8 +939,6 @@ static int synth_solve_2d(dsmc_handle* h, const double* dev_fields, const double
 int synth_solve(dsmc_handle* h, const double* dev_fields, const double* dev_hot, double* dev_out, int* host_iters,
                 double* host_resid) {
   if (!h || !dev_fields || !dev_hot || !dev_out) return set_err(h, DSMC_ERR_ARG, "bad arguments");
-  if (h->cfg.mesh == DSMC_MESH_ANNULUS)
-    return set_err(h, DSMC_ERR_ARG, "synth_solve: not on the annulus (boxes only)");
   if (h->cfg.dim == 2) return synth_solve_2d(h, dev_fields, dev_hot, dev_out, host_iters, host_resid);
   int n_m = 0;
   double tol = 1.0;

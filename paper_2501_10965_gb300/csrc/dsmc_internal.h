@@ -36,6 +36,7 @@ struct CellParams {
   int mesh;            // 0 Cartesian box, 1 annulus, 2 wall-refined box (1, 2: single case)
   const double* vol;   // annulus: cell volumes (null on the box: vcell)
   const double* r2t;   // annulus: ny + 1 squared ring radii (nx sectors x ny rings)
+  const double* rt;    // annulus: the ny + 1 ring radii themselves
   const double* xe;    // wall-refined box: nx + 1 and ny + 1 cell edges
   const double* ye;
 };
@@ -154,7 +155,7 @@ size_t synth1d_work_doubles(int ncells);
 // 2D synthetic equations of one box case (dsmc_synth2d.cu): doubles of work,
 // and the solve (info = iterations, max residual, status; *singular set when
 // a zero pivot was met); returns a cudaError_t value
-size_t synth2d_work_doubles(int nx, int ny);
+size_t synth2d_work_doubles(int nx, int ny, int annulus);
 int launch_synth2d(const CellParams& cp, const double* fields, const double* hot, double* out, double* work,
                    int n_m, double tol, double* info, int* singular, cudaStream_t st);
 

@@ -203,8 +203,8 @@ __global__ void k_s2_res(const s2::Grid g, S2Work w) {
 __global__ void k_s2_jac(const s2::Grid g, S2Work w, int band) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (band && t == 0) {
-    const int mr = s2::mass_row(g);
-    w.AB[s2::band_at(g, mr, mr)] = (float)(s2::mass_scale(g, 1, 0) / g.n);
+    const int mr = s2::mass_row(g);  // none on the annulus
+    if (mr >= 0) w.AB[s2::band_at(g, mr, mr)] = (float)(s2::mass_scale(g, 1, 0) / g.n);
   }
   if (t >= g.n * s2::NSTENCIL * s2::NV) return;
   const int b = t / (s2::NSTENCIL * s2::NV);
@@ -1070,8 +1070,9 @@ cudaError_t s2_subst(const s2::Grid& g, const S2Work& w, double* b0, double* b1,
   return cudaGetLastError();
 }
 
-size_t synth2d_work_doubles(int nx, int ny) {
-  const s2::Grid g = s2::make_grid(nx, ny, 1.0, 1.0, 2.0, 0.75, 1.0, 1.0, 1.0, 1.0, nullptr, nullptr);
+size_t synth2d_work_doubles(int nx, int ny, int annulus) {
+  s2::Grid g = s2::make_grid(nx, ny, 1.0, 1.0, 2.0, 0.75, 1.0, 1.0, 1.0, 1.0, nullptr, nullptr);
+  if (annulus) s2::set_annulus(g, nullptr);  // the band of the annulus's ordering
   return s2_doubles(g);
 }
 
@@ -1080,6 +1081,7 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
   s2::Grid g = s2::make_grid(cp.nx, cp.ny, cp.dx, cp.dy, cp.d_r, cp.omega, cp.mu_ref, cp.z_rot, cp.kappa_t,
                              cp.kappa_r, fields, hot);
   if (cp.mesh == 2) s2::set_edges(g, cp.xe, cp.ye, cp.lx * cp.ly);  // the wall-refined grid (device edges)
+  if (cp.mesh == 1) s2::set_annulus(g, cp.rt);  // the annulus (device ring radii)
   const S2Work w = s2_carve(g, work);
   if (w.nb == 0) return (int)cudaErrorInvalidValue;
   const int nb = w.nb;

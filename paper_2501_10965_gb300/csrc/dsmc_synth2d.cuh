@@ -64,6 +64,9 @@ struct Grid {
   const double* xe;        // wall-refined grid: cell edges along x (nx + 1) and y (ny + 1); null: uniform
   const double* ye;
   double area;             // L_x L_y (wall-refined grid)
+  int ann;                 // 1: the annulus around a cylinder (nx sectors, periodic; ny rings)
+  const double* R;         // annulus: ring edges R_0 .. R_ny
+  double dth, s2, sdth;    // annulus: sector angle, sin(dth / 2), sin(dth)
   double d_r, omega, mu_ref, z_rot, kappa_t, kappa_r, gamma;
   const double* F;         // sampled fields, natural order (cell j nx + i) x 18
   const double* hot;       // HoT, natural order x 12
@@ -87,6 +90,9 @@ __host__ __device__ inline Grid make_grid(int nx, int ny, double dx, double dy, 
   g.xe = nullptr;
   g.ye = nullptr;
   g.area = 0.0;
+  g.ann = 0;
+  g.R = nullptr;
+  g.dth = g.s2 = g.sdth = 0.0;
   g.d_r = d_r;
   g.omega = omega;
   g.mu_ref = mu_ref;
@@ -116,10 +122,29 @@ __host__ __device__ inline double width(const Grid& g, int dir, int k) {
 
 __host__ __device__ inline double centre(const double* e, int k) { return 0.5 * (e[k] + e[k + 1]); }
 
+// The annulus around a cylinder (Sec. 4.2): cell (i, j) in sector i (angles
+// dth i .. dth (i + 1)) and ring j (radii R_j .. R_{j+1}), cells numbered
+// ring by ring (band cell j nx + i, periodic in i), so the band holds the
+// wrap-around neighbours too: kl = ku = 10 nx + 4.  Needs nx >= 5 (the
+// stencil's five sectors distinct) and ny >= 3.
+__host__ __device__ inline void set_annulus(Grid& g, const double* R) {
+  g.ann = 1;
+  g.R = R;
+  g.dth = 2.0 * 3.14159265358979323846 / g.nx;
+  g.s2 = sin(0.5 * g.dth);
+  g.sdth = sin(g.dth);
+  g.xfast = 1;
+  g.kl = 10 * g.nx + 4;
+  g.ku = g.kl;
+  g.ld = 2 * g.kl + g.ku + 1;
+}
+
 // Weight of cell (i, j)'s density in the total-mass row, times n: 1 on the
 // uniform grid, n V_c / (L_x L_y) on the wall-refined one, so that the row
-// holds the mass sum_c rho_c V_c against its sample.
+// holds the mass sum_c rho_c V_c against its sample; the annulus has no
+// total-mass row (its outer ring keeps its sampled density).
 __host__ __device__ inline double mass_scale(const Grid& g, int i, int j) {
+  if (g.ann) return 0.0;
   if (!g.xe) return 1.0;
   return (double)g.n * (width(g, 0, i) * width(g, 1, j)) / g.area;
 }
@@ -135,7 +160,20 @@ __host__ __device__ inline void cell_of_band(const Grid& g, int b, int& i, int& 
   }
 }
 __host__ __device__ inline bool is_corner(const Grid& g, int i, int j) {
-  return (i == 0 || i == g.nx - 1) && (j == 0 || j == g.ny - 1);
+  return !g.ann && (i == 0 || i == g.nx - 1) && (j == 0 || j == g.ny - 1);
+}
+
+// the cell at stencil offset (di, dj) of cell (i, j); false outside the grid
+// (the annulus wraps around in i)
+__host__ __device__ inline bool stencil_cell(const Grid& g, int i, int j, int di, int dj, int& ik, int& jk) {
+  ik = i + di;
+  jk = j + dj;
+  if (jk < 0 || jk >= g.ny) return false;
+  if (g.ann) {
+    ik = ik < 0 ? ik + g.nx : (ik >= g.nx ? ik - g.nx : ik);
+    return true;
+  }
+  return ik >= 0 && ik < g.nx;
 }
 
 // The state x (band order) with one unknown (band cell pb, variable pv)
@@ -283,9 +321,198 @@ __host__ __device__ inline void face_flux(const Grid& g, const View& X, int dir,
   }
 }
 
+// ---------------------------------------------------------------------------
+// The annulus (set_annulus): finite volumes with the exact face vectors (an
+// arc at radius R in sector i: 2 R sin(dth / 2) e_r(theta_i), theta_i =
+// dth (i + 1/2); a ray at angle phi in ring j: (R_{j+1} - R_j) e_theta(phi)),
+// sector areas as volumes, the box's face flux in each face's frame (n, t =
+// n turned by +90 degrees) with the tangential derivatives averaged from the
+// two cells' Cartesian gradients; the first ring keeps u, T and balances its
+// mass (no flux through the cylinder), the outer ring keeps its whole state.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline double ann_rc(const Grid& g, int j) { return 0.5 * (g.R[j] + g.R[j + 1]); }
+
+// Cartesian gradient (du_x/dx, du_x/dy, du_y/dx, du_y/dy) of cell (i, j):
+// d/dr by the three-point formula on the ring centres (one-sided in the
+// first and last ring), (1/r) d/dtheta = (f_{i+1} - f_{i-1}) / (2 r_c
+// sin(dth)), turned to Cartesian at theta_i.
+__host__ __device__ inline void ann_grad(const Grid& g, const View& X, int i, int j, double* gr) {
+  const int nt = g.nx, nr = g.ny;
+  const int ip = i + 1 < nt ? i + 1 : 0, im = i > 0 ? i - 1 : nt - 1;
+  const double rc = ann_rc(g, j);
+  const double th = g.dth * (i + 0.5);
+  const double c = cos(th), s = sin(th);
+  for (int q = 0; q < 2; ++q) {
+    const int v = 1 + q;
+    double dr;
+    if (j == 0) {
+      dr = (X.at(g, i, 1, v) - X.at(g, i, 0, v)) / (ann_rc(g, 1) - ann_rc(g, 0));
+    } else if (j == nr - 1) {
+      dr = (X.at(g, i, nr - 1, v) - X.at(g, i, nr - 2, v)) / (ann_rc(g, nr - 1) - ann_rc(g, nr - 2));
+    } else {
+      const double hm = rc - ann_rc(g, j - 1), hp = ann_rc(g, j + 1) - rc;
+      dr = (hm * hm * X.at(g, i, j + 1, v) - hp * hp * X.at(g, i, j - 1, v) + (hp * hp - hm * hm) * X.at(g, i, j, v)) /
+           (hp * hm * (hp + hm));
+    }
+    const double dt = (X.at(g, ip, j, v) - X.at(g, im, j, v)) / (2.0 * rc * g.sdth);
+    gr[2 * q] = c * dr - s * dt;
+    gr[2 * q + 1] = s * dr + c * dt;
+  }
+}
+
+// Flux per unit area (mass, x-momentum, y-momentum, energy, rotational
+// energy) through the ray between sectors i and i + 1 of ring j (dir 0) or
+// the arc between rings j and j + 1 of sector i (dir 1).
+__host__ __device__ inline void ann_face_flux(const Grid& g, const View& X, int dir, int i, int j, double* F) {
+  const int nt = g.nx;
+  const int i2 = dir == 0 ? (i + 1 < nt ? i + 1 : 0) : i, j2 = dir == 0 ? j : j + 1;
+  const double ang = dir == 0 ? g.dth * (i + 1.0) : g.dth * (i + 0.5);
+  const double nx = dir == 0 ? -sin(ang) : cos(ang), ny = dir == 0 ? cos(ang) : sin(ang);
+  const double tx = -ny, ty = nx;
+  const double d = dir == 0 ? 2.0 * ann_rc(g, j) * g.s2 : ann_rc(g, j + 1) - ann_rc(g, j);
+  const double d_r = g.d_r;
+  double q[2][NV];
+  for (int side = 0; side < 2; ++side) {
+    const int ci = side ? i2 : i, cj = side ? j2 : j;
+    const double ux = X.at(g, ci, cj, 1), uy = X.at(g, ci, cj, 2);
+    q[side][0] = X.at(g, ci, cj, 0);
+    q[side][1] = ux * nx + uy * ny;
+    q[side][2] = -ux * ny + uy * nx;
+    q[side][3] = X.at(g, ci, cj, 3);
+    q[side][4] = X.at(g, ci, cj, 4);
+  }
+  const double* ql = q[0];
+  const double* qr = q[1];
+  const double unf = 0.5 * (ql[1] + qr[1]), utf = 0.5 * (ql[2] + qr[2]);
+  const double ttf = 0.5 * (ql[3] + qr[3]), trf = 0.5 * (ql[4] + qr[4]);
+  const double Tf = (3.0 * ttf + d_r * trf) / (3.0 + d_r);
+  const double muf = g.mu_ref * pow(Tf, g.omega);
+  const double dun_n = (qr[1] - ql[1]) / d, dut_n = (qr[2] - ql[2]) / d;
+  const double dtt_n = (qr[3] - ql[3]) / d, dtr_n = (qr[4] - ql[4]) / d;
+  double gl[4], grr[4];
+  ann_grad(g, X, i, j, gl);
+  ann_grad(g, X, i2, j2, grr);
+  double gn[2], gt[2];
+  for (int side = 0; side < 2; ++side) {
+    const double* gg = side ? grr : gl;
+    const double tgx = tx * gg[0] + ty * gg[1], tgy = tx * gg[2] + ty * gg[3];
+    gn[side] = nx * tgx + ny * tgy;
+    gt[side] = tx * tgx + ty * tgy;
+  }
+  const double dun_t = 0.5 * (gn[0] + gn[1]), dut_t = 0.5 * (gt[0] + gt[1]);
+  double hs[2][4];
+  for (int side = 0; side < 2; ++side) {
+    const double* h = g.hot + (size_t)((side ? j2 : j) * g.nx + (side ? i2 : i)) * 12;
+    hs[side][0] = h[0] * nx * nx + 2.0 * h[3] * nx * ny + h[1] * ny * ny;
+    hs[side][1] = h[0] * nx * tx + h[3] * (nx * ty + ny * tx) + h[1] * ny * ty;
+    hs[side][2] = h[6] * nx + h[7] * ny;
+    hs[side][3] = h[9] * nx + h[10] * ny;
+  }
+  const double s_nn = -muf * ((4.0 / 3.0) * dun_n - (2.0 / 3.0) * dut_t) + 0.5 * (hs[0][0] + hs[1][0]);
+  const double s_nt = -muf * (dut_n + dun_t) + 0.5 * (hs[0][1] + hs[1][1]);
+  const double qt = -g.kappa_t * muf * dtt_n + 0.5 * (hs[0][2] + hs[1][2]);
+  const double qrr = -g.kappa_r * muf * dtr_n + 0.5 * (hs[0][3] + hs[1][3]);
+  double Fn[NV];
+  {
+    double cl[NV], cr[NV];
+    for (int side = 0; side < 2; ++side) {
+      const double* qq = q[side];
+      double* cc = side ? cr : cl;
+      const double e = 0.5 * (3.0 * qq[3] + d_r * qq[4]) + 0.5 * (qq[1] * qq[1] + qq[2] * qq[2]);
+      cc[0] = qq[0] * qq[1];
+      cc[1] = qq[0] * qq[1] * qq[1] + qq[0] * qq[3];
+      cc[2] = qq[0] * qq[1] * qq[2];
+      cc[3] = qq[0] * qq[1] * (e + qq[3]);
+      cc[4] = qq[0] * qq[1] * (0.5 * d_r * qq[4]);
+    }
+    for (int k = 0; k < NV; ++k) Fn[k] = 0.5 * (cl[k] + cr[k]);
+  }
+  Fn[1] += s_nn;
+  Fn[2] += s_nt;
+  Fn[3] += s_nn * unf + s_nt * utf + qt + qrr;
+  Fn[4] += qrr;
+  // fourth-difference dissipation: along the sectors (rays, periodic) or the
+  // rings (arcs, where rings j-1 .. j+2 exist)
+  const bool diss = dir == 0 || (g.ny - 1 >= 3 && j >= 1 && j <= g.ny - 3);
+  if (diss) {
+    const int im = dir == 0 ? (i > 0 ? i - 1 : nt - 1) : i, jm = dir == 0 ? j : j - 1;
+    const int ip = dir == 0 ? (i + 2 < nt ? i + 2 : i + 2 - nt) : i, jp = dir == 0 ? j : j + 2;
+    double qm[NV], qp[NV], wm[NV], w0[NV], w1[NV], wp[NV];
+    const int cis[2] = {im, ip}, cjs[2] = {jm, jp};
+    for (int side = 0; side < 2; ++side) {
+      double* qq = side ? qp : qm;
+      const double ux = X.at(g, cis[side], cjs[side], 1), uy = X.at(g, cis[side], cjs[side], 2);
+      qq[0] = X.at(g, cis[side], cjs[side], 0);
+      qq[1] = ux * nx + uy * ny;
+      qq[2] = -ux * ny + uy * nx;
+      qq[3] = X.at(g, cis[side], cjs[side], 3);
+      qq[4] = X.at(g, cis[side], cjs[side], 4);
+    }
+    conserved(g, qm, wm);
+    conserved(g, ql, w0);
+    conserved(g, qr, w1);
+    conserved(g, qp, wp);
+    const double lam = fabs(unf) + sqrt(g.gamma * Tf);
+    for (int k = 0; k < NV; ++k) Fn[k] += EPS4 * lam * (wp[k] - 3.0 * w1[k] + 3.0 * w0[k] - wm[k]);
+  }
+  F[0] = Fn[0];
+  F[1] = Fn[1] * nx + Fn[2] * tx;
+  F[2] = Fn[1] * ny + Fn[2] * ty;
+  F[3] = Fn[3];
+  F[4] = Fn[4];
+}
+
+__host__ __device__ inline void ann_cell_residual(const Grid& g, const View& X, int i, int j, double* R) {
+  const double* D = g.F + (size_t)(j * g.nx + i) * 18;
+  if (j == g.ny - 1) {  // the outer ring: its sampled state
+    R[0] = X.at(g, i, j, 0) - D[0];
+    R[1] = X.at(g, i, j, 1) - D[1];
+    R[2] = X.at(g, i, j, 2) - D[2];
+    R[3] = X.at(g, i, j, 3) - D[4];
+    R[4] = X.at(g, i, j, 4) - D[5];
+    return;
+  }
+  double div[NV] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double Fa[NV];
+  const double sa = 2.0 * g.R[j + 1] * g.s2, sr = g.R[j + 1] - g.R[j];
+  ann_face_flux(g, X, 1, i, j, Fa);  // the outer arc
+  for (int k = 0; k < NV; ++k) div[k] += Fa[k] * sa;
+  if (j > 0) {  // the inner arc (none at the cylinder)
+    ann_face_flux(g, X, 1, i, j - 1, Fa);
+    const double sb = 2.0 * g.R[j] * g.s2;
+    for (int k = 0; k < NV; ++k) div[k] -= Fa[k] * sb;
+  }
+  ann_face_flux(g, X, 0, i, j, Fa);  // the ray at the sector's upper angle
+  for (int k = 0; k < NV; ++k) div[k] += Fa[k] * sr;
+  ann_face_flux(g, X, 0, i > 0 ? i - 1 : g.nx - 1, j, Fa);  // and at its lower angle
+  for (int k = 0; k < NV; ++k) div[k] -= Fa[k] * sr;
+  const double V = 0.5 * g.dth * (g.R[j + 1] * g.R[j + 1] - g.R[j] * g.R[j]);
+  for (int k = 0; k < NV; ++k) div[k] /= V;
+  R[0] = div[0];
+  if (j == 0) {  // next to the cylinder: the sampled u, T
+    R[1] = X.at(g, i, j, 1) - D[1];
+    R[2] = X.at(g, i, j, 2) - D[2];
+    R[3] = X.at(g, i, j, 3) - D[4];
+    R[4] = X.at(g, i, j, 4) - D[5];
+    return;
+  }
+  const double rho = X.at(g, i, j, 0), tt = X.at(g, i, j, 3), tr = X.at(g, i, j, 4);
+  const double T = (3.0 * tt + g.d_r * tr) / (3.0 + g.d_r);
+  const double mu = g.mu_ref * pow(T, g.omega);
+  const double src = 0.5 * g.d_r * rho * (rho * T) * (T - tr) / (g.z_rot * mu);
+  R[1] = div[1];
+  R[2] = div[2];
+  R[3] = div[3];
+  R[4] = div[4] - src;
+}
+
 // Residual rows (5) of cell (i, j).  mass_row is the total-mass residual
 // sum_c mass_scale_c (rho_c - sampled rho_c) / n, used by cell (1, 0).
 __host__ __device__ inline void cell_residual(const Grid& g, const View& X, int i, int j, double mass_row, double* R) {
+  if (g.ann) {
+    ann_cell_residual(g, X, i, j, R);
+    return;
+  }
   const double* D = g.F + (size_t)(j * g.nx + i) * 18;
   if (is_corner(g, i, j)) {
     R[0] = X.at(g, i, j, 0) - D[0];
@@ -343,7 +570,7 @@ __host__ __device__ inline void cell_residual(const Grid& g, const View& X, int 
 }
 
 // row of the total-mass equation: unknown rho of cell (1, 0)
-__host__ __device__ inline int mass_row(const Grid& g) { return NV * band_cell(g, 1, 0); }
+__host__ __device__ inline int mass_row(const Grid& g) { return g.ann ? -1 : NV * band_cell(g, 1, 0); }
 
 // Band storage (column-major, leading dimension ld): entry (r, c) of the
 // matrix at AB[c * ld + r - c + kl + ku], rows c - kl - ku .. c + kl of column
@@ -370,8 +597,8 @@ __host__ __device__ inline void jacobian_entries(const Grid& g, const double* x,
   int i, j, di, dj;
   cell_of_band(g, b, i, j);
   stencil_offset(s, di, dj);
-  const int ik = i + di, jk = j + dj;
-  if (ik < 0 || ik >= g.nx || jk < 0 || jk >= g.ny) {
+  int ik, jk;
+  if (!stencil_cell(g, i, j, di, dj, ik, jk)) {
     for (int r = 0; r < NV; ++r) Jc[jc_at(b, s, r, v)] = 0.0;
     return;
   }
@@ -403,8 +630,8 @@ __host__ __device__ inline double bmv_row(const Grid& g, const double* Jc, const
   for (int s = 0; s < NSTENCIL; ++s) {
     int di, dj;
     stencil_offset(s, di, dj);
-    const int ik = i + di, jk = j + dj;
-    if (ik < 0 || ik >= g.nx || jk < 0 || jk >= g.ny) continue;
+    int ik, jk;
+    if (!stencil_cell(g, i, j, di, dj, ik, jk)) continue;
     const double* blk = Jc + jc_at(b, s, r, 0);
     const double* xv = vec + NV * band_cell(g, ik, jk);
     for (int v = 0; v < NV; ++v) acc += blk[v] * xv[v];

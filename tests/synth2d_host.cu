@@ -19,9 +19,13 @@ extern "C" void h_set_edges(const double* xe, const double* ye, double area) {
   g_ye = ye;
   g_area = area;
 }
+// the annulus's ring edges for the calls that follow (null: a box)
+static const double* g_R = nullptr;
+extern "C" void h_set_annulus(const double* R) { g_R = R; }
 static Grid G(int nx, int ny, double dx, double dy, const double* c, const double* F, const double* hot) {
   Grid g = make_grid(nx, ny, dx, dy, c[0], c[1], c[2], c[3], c[4], c[5], F, hot);
   if (g_xe) set_edges(g, g_xe, g_ye, g_area);
+  if (g_R) set_annulus(g, g_R);
   return g;
 }
 static void residual_all(const Grid& g, const double* xb, double* Rb) {
@@ -132,7 +136,7 @@ extern "C" int h_solve_blk(int nx, int ny, double dx, double dy, const double* c
     for (int b = 0; b < g.n; ++b) for (int s = 0; s < NSTENCIL; ++s) for (int v = 0; v < NV; ++v)
       jacobian_entries(g, x.data(), b, s, v, refac ? f.AB.data() : nullptr, Jc.data());
     if (refac) {
-      f.AB[band_at(g, mr, mr)] = (float)(mass_scale(g, 1, 0) / g.n);
+      if (mr >= 0) f.AB[band_at(g, mr, mr)] = (float)(mass_scale(g, 1, 0) / g.n);
       sing |= factor(g, nb, f);
       ++nf;
     }

@@ -96,7 +96,13 @@ def test_synth2d_workspace_and_validation():
     assert _ws(W.fourier_1d(synth2d=True))[0] == -1
     assert _ws(W.cavity_2d(nx=2, ny=8, ppc=4, synth2d=True))[0] == -1
     assert _ws(W.cavity_2d(nx=501, ny=501, ppc=1, synth2d=True))[0] == -1
-    assert _ws(W.cylinder_2d(ntheta=24, nr=8, ppc=4, synth2d=True))[0] == -1
+    # the annulus: at least 5 sectors and 3 rings, at most 500 sectors (its band follows the sectors)
+    rc0, nc0 = _ws(W.cylinder_2d(ntheta=24, nr=8, ppc=4))
+    rc1, nc1 = _ws(W.cylinder_2d(ntheta=24, nr=8, ppc=4, synth2d=True))
+    assert rc0 == 0 and rc1 == 0 and nc1 > nc0
+    assert _ws(W.cylinder_2d(ntheta=4, nr=8, ppc=4, synth2d=True))[0] == -1
+    assert _ws(W.cylinder_2d(ntheta=24, nr=2, ppc=4, synth2d=True))[0] == -1
+    assert _ws(W.cylinder_2d(ntheta=501, nr=8, ppc=1, synth2d=True))[0] == -1
     # the wall-refined box: 2D, stretch > 0; its 2D solve takes the box's workspace
     assert _ws(W.cavity_2d_refined(nx=14, ny=12, ppc=4, dx_min=0.02))[0] == 0
     assert _ws(W.cavity_2d_refined(nx=14, ny=12, ppc=4, dx_min=0.02, synth2d=True)) == \

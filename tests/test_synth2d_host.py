@@ -173,3 +173,70 @@ def test_newton_reaches_the_oracle_solution_on_the_wall_refined_grid(lib, nx, ny
     assert st.value == 0 and res.value < 1e-11
     assert it0 <= it.value <= it0 + 1, (it0, it.value)
     np.testing.assert_allclose(out1, out0, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# the annulus around a cylinder
+# ---------------------------------------------------------------------------
+
+def _ann_cfg(nt, nr, **kw):
+    base = dict(ntheta=nt, nr=nr, ppc=4, kn=0.1, mach=0.5, r_in=0.5, r_out=1.5, dr1=0.1, precision="fp64")
+    base.update(kw)
+    return W.cylinder_2d(**base)
+
+
+def _ann_state(cfg, seed=0, hot_amp=1e-3):
+    from oracle import synth_annulus as SA
+    nt, nr, R, rc, dth, thc = SA.geometry(cfg)
+    r, th = np.meshgrid(rc, thc, indexing="ij")
+    x, y, r = (r * np.cos(th)).ravel(), (r * np.sin(th)).ravel(), r.ravel()
+    n = nt * nr
+    d = np.zeros((n, 18))
+    d[:, F_RHO] = 1.0 + 0.05 * np.cos(x)
+    d[:, F_U] = 0.2 * (1.0 - 0.5 / r) * np.sin(y)
+    d[:, F_U + 1] = -0.1 * x * y
+    d[:, F_U + 2] = 0.01
+    d[:, F_TT] = 1.0 + 0.1 * np.exp(-r)
+    d[:, F_TR] = 1.0 + 0.08 * np.exp(-r)
+    return d, hot_amp * np.random.default_rng(seed).standard_normal((n, 12)), R
+
+
+@pytest.mark.parametrize("nt,nr", [(10, 6), (7, 5), (16, 4)])
+def test_annulus_residual_equals_oracle(lib, nt, nr):
+    from oracle import synth_annulus as SA
+    cfg = _ann_cfg(nt, nr)
+    d, h, R = _ann_state(cfg, seed=nt)
+    x = SA.initial_state(d) * (1.0 + 0.01 * np.random.default_rng(2).standard_normal(5 * nt * nr))
+    R0 = SA.residual(x, d, h, cfg)
+    R1 = np.zeros_like(R0)
+    Rk = np.ascontiguousarray(R)
+    lib.h_set_annulus(_p(Rk))
+    try:
+        lib.h_residual(nt, nr, ctypes.c_double(1.0), ctypes.c_double(1.0), _p(_consts(cfg)),
+                       _p(np.ascontiguousarray(d)), _p(np.ascontiguousarray(h)), _p(x), _p(R1))
+    finally:
+        lib.h_set_annulus(None)
+    assert np.max(np.abs(R1 - R0)) <= 1e-12 * max(1.0, np.max(np.abs(R0)))
+
+
+@pytest.mark.parametrize("nt,nr", [(10, 6), (12, 5)])
+def test_annulus_newton_reaches_the_oracle_solution(lib, nt, nr):
+    """The GPU's Newton steps on the annulus (no total-mass row; the reuse
+    policy): the oracle's solution."""
+    from oracle import synth_annulus as SA
+    cfg = _ann_cfg(nt, nr)
+    d, h, R = _ann_state(cfg)
+    out0, it0, res0 = SA.synth_solve_annulus(d, h, cfg, tol=1e-12, max_iter=50)
+    out1 = np.zeros((nt * nr, 6))
+    it, res, st, nf = ctypes.c_int(), ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+    Rk = np.ascontiguousarray(R)
+    lib.h_set_annulus(_p(Rk))
+    try:
+        lib.h_solve_blk(nt, nr, ctypes.c_double(1.0), ctypes.c_double(1.0), _p(_consts(cfg)),
+                        _p(np.ascontiguousarray(d)), _p(np.ascontiguousarray(h)), 50, ctypes.c_double(1e-12), 32, 1,
+                        1, 3, _p(out1), ctypes.byref(it), ctypes.byref(res), ctypes.byref(st), ctypes.byref(nf))
+    finally:
+        lib.h_set_annulus(None)
+    assert st.value == 0 and res.value < 1e-11 and res0 < 1e-11
+    assert it0 <= it.value <= it0 + 1, (it0, it.value)
+    np.testing.assert_allclose(out1, out0, rtol=0, atol=1e-12)
