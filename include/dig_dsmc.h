@@ -232,7 +232,9 @@ int dsmc_hot(dsmc_handle *h, const double *dev_fields, double *dev_hot, double *
  * DSMC_ERR_NOT_CONVERGED (outputs written) when the iteration limit is
  * reached; DSMC_ERR_NUMERIC when no Newton update keeps rho > 0 and T > 0
  * (noisy HoT can make rho = (P - HoT_xx) / T_t negative in 1D, and a
- * singular 2D system admits no update), in which case the output is the
+ * singular 2D system admits no update) or, in 2D, when positivity cuts a
+ * Newton step below 1/1024 of itself (no solution near the state, e.g. a
+ * shock the central differences cannot carry), in which case the output is the
  * sampled fields, so that it can still serve as a dig_correct target.  In a
  * batch the worst status of the slabs is returned. */
 int synth_solve(dsmc_handle *h, const double *dev_fields, const double *dev_hot, double *dev_out,

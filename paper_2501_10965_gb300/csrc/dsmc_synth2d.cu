@@ -923,8 +923,8 @@ __global__ void k_s2_add(const s2::Grid g, S2Work w) {
 
 // The rank-one correction for the total-mass row (z = v0, y = v1), the damped
 // update that keeps rho, T_t, T_r positive and finite (step halved up to 60
-// times), and the convergence test on the largest relative update
-// (|lam dx| / max(|x|, 1e-3) < tol).
+// times), and the convergence test on the largest relative update of a full
+// step (|dx| / max(|x|, 1e-3) < tol); a step cut below 1/1024 is a stall.
 __global__ void __launch_bounds__(S2_UPD_NT) k_s2_newton(const s2::Grid g, S2Work w, int n_m, double tol) {
   __shared__ double red[S2_UPD_NT];
   const int tid = threadIdx.x;
@@ -976,8 +976,15 @@ __global__ void __launch_bounds__(S2_UPD_NT) k_s2_newton(const s2::Grid g, S2Wor
     w.sc[S2_IT] = it;
     w.sc[S2_DMAX] = dm;
     w.sc[S2_LAM] = lam;
-    if (dm < tol) {
+    if (dm < tol && lam == 1.0) {
+      // converged: a full Newton step below the tolerance
       w.sc[S2_STATUS] = 0.0;
+      w.sc[S2_DONE] = 1.0;
+    } else if (lam < 1.0 / 1024.0) {
+      // stalled: positivity holds the step to a sliver, so the equations
+      // have no solution near this state (e.g. a shock the central
+      // differences cannot carry); the sampled fields are the output
+      w.sc[S2_STATUS] = 2.0;
       w.sc[S2_DONE] = 1.0;
     } else if (it >= n_m) {
       w.sc[S2_DONE] = 1.0;
