@@ -39,7 +39,6 @@ enum {
   S2_DMAX = 5,
   S2_SING = 6,   // a zero pivot was met
   S2_LAM = 7,    // length of the last Newton update (1 = full step)
-  S2_REF = 8,    // the last refinement sweep's correction relative to the solution
   S2_NSC = 16
 };
 
@@ -48,8 +47,7 @@ constexpr int S2_UPD_NT = 512;    // the Newton update
 constexpr int S2_SUB_NT = 512;    // the substitutions
 constexpr int S2_PNL_NT = 512;    // the panel factorisation
 constexpr int S2_NREF = 1;        // refinement sweeps after a fresh factorisation
-constexpr int S2_NREF_REUSE = 3;  // refinement sweeps (at most) when an earlier factorisation is reused
-constexpr double S2_REF_TOL = 1e-4;  // a sweep whose correction is below this (relative) ends the sweeps
+constexpr int S2_NREF_REUSE = 3;  // refinement sweeps when an earlier factorisation is reused
 constexpr int S2_SMEM_CAP = 200 * 1024;
 
 // Panel width nb and trailing columns per CTA cb (4: enough CTAs to fill the
@@ -923,24 +921,6 @@ __global__ void k_s2_add(const s2::Grid g, S2Work w) {
   w.v1[u] += w.s1[u];
 }
 
-// the last sweep's correction against the refined solution, the larger of
-// max|s| / max|v| over the two right-hand sides
-__global__ void __launch_bounds__(S2_UPD_NT) k_s2_refmeas(const s2::Grid g, S2Work w) {
-  __shared__ double red[S2_UPD_NT];
-  double s0 = 0.0, v0 = 0.0, s1 = 0.0, v1 = 0.0;
-  for (int u = threadIdx.x; u < g.N; u += S2_UPD_NT) {
-    s0 = fmax(s0, fabs(w.s0[u]));
-    v0 = fmax(v0, fabs(w.v0[u]));
-    s1 = fmax(s1, fabs(w.s1[u]));
-    v1 = fmax(v1, fabs(w.v1[u]));
-  }
-  s0 = s2_block_max<S2_UPD_NT>(s0, red);
-  v0 = s2_block_max<S2_UPD_NT>(v0, red);
-  s1 = s2_block_max<S2_UPD_NT>(s1, red);
-  v1 = s2_block_max<S2_UPD_NT>(v1, red);
-  if (threadIdx.x == 0) w.sc[S2_REF] = fmax(s0 / fmax(v0, 1e-300), v1 > 0.0 ? s1 / v1 : 0.0);
-}
-
 // The rank-one correction for the total-mass row (z = v0, y = v1), the damped
 // update that keeps rho, T_t, T_r positive and finite (step halved up to 60
 // times), and the convergence test on the largest relative update of a full
@@ -1149,9 +1129,6 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
           k_s2_trail<<<(ntrail + cbt - 1) / cbt, S2_NT, sizeof(float) * (size_t)cbt * H, st>>>(g, w, k0, cbt);
       }
     }
-    // refinement: one sweep after a fresh factorisation; with a reused one,
-    // sweeps until a correction falls below S2_REF_TOL of the solution (at
-    // most S2_NREF_REUSE)
     const int nsweep = refactor ? S2_NREF : S2_NREF_REUSE;
     k_s2_prep<<<vec_grid, nt, 0, st>>>(g, w);
     cudaError_t le = s2_subst(g, w, w.b0, w.b1, w.v0, w.v1, sm_subst, st);
@@ -1159,13 +1136,6 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
       k_s2_bmv<<<vec_grid, nt, 0, st>>>(g, w);
       le = s2_subst(g, w, w.b0, w.b1, w.s0, w.s1, sm_subst, st);
       k_s2_add<<<vec_grid, nt, 0, st>>>(g, w);
-      if (r + 1 < nsweep && le == cudaSuccess) {
-        k_s2_refmeas<<<1, S2_UPD_NT, 0, st>>>(g, w);
-        double ref = 0.0;
-        cudaMemcpyAsync(&ref, w.sc + S2_REF, sizeof(double), cudaMemcpyDeviceToHost, st);
-        le = cudaStreamSynchronize(st);
-        if (le == cudaSuccess && ref <= S2_REF_TOL) break;
-      }
     }
     if (le != cudaSuccess) return (int)le;
     k_s2_newton<<<1, S2_UPD_NT, 0, st>>>(g, w, n_m, tol);
