@@ -217,8 +217,8 @@ int dsmc_hot(dsmc_handle *h, const double *dev_fields, double *dev_hot, double *
  * ny >= 3 rings): the same equations by finite volumes on the sector cells
  * (face vectors the integrals of the faces' normals, so a uniform state is
  * exact; velocities Cartesian, each face's flux in its own normal frame);
- * the ring next to the cylinder keeps the sampled u, T and balances its
- * mass, the outer ring keeps its whole sampled state; no total-mass row.
+ * both boundary rings (next to the cylinder and on the freestream side)
+ * keep their whole sampled state; no total-mass row.
  *
  * Residual and central-difference Jacobian in
  * FP64; each Newton step solves with a blocked banded LU factorisation

@@ -274,28 +274,42 @@ def initial_state(dsmc: np.ndarray) -> np.ndarray:
 
 def synth_solve_2d(dsmc: np.ndarray, hot: np.ndarray, cfg: dict, tol: float = 1e-12, max_iter: int = 50):
     """Newton iterations from the DSMC fields until the largest relative
-    update is below ``tol``.  Returns (out [ncells x 6] = rho, u_x, u_y, u_z
-    (the sampled one), T_t, T_r; iterations; final max |residual|)."""
+    update of a full step is below ``tol``.  Returns (out [ncells x 6] = rho,
+    u_x, u_y, u_z (the sampled one), T_t, T_r; iterations; final max
+    |residual|); when positivity cuts a step below 1/1024 (a stall: no
+    solution near the state) out is the sampled fields."""
     nx, ny, _, _ = _geom(cfg)
     if nx < 3 or ny < 3:
         raise ValueError("synth_solve_2d needs at least 3 x 3 cells")
     n = nx * ny
     x = initial_state(dsmc)
     it = 0
+    stalled = False
     for it in range(1, max_iter + 1):
         R = residual(x, dsmc, hot, cfg)
         J = _jacobian(x, dsmc, hot, cfg)
         dxv = spla.spsolve(J.tocsc(), -R)
+        # halve the step (at most 60 times) until rho, T_t, T_r stay
+        # positive and finite; a step cut below 1/1024 is a stall (no
+        # solution near this state): the sampled fields are the answer
         lam = 1.0
         xn = x + dxv
-        while np.any(xn[0:n] <= 0) or np.any(xn[3 * n:] <= 0):
+        for _ in range(60):
+            if np.all(np.isfinite(xn)) and not (np.any(xn[0:n] <= 0) or np.any(xn[3 * n:] <= 0)):
+                break
             lam *= 0.5
             xn = x + lam * dxv
+        if lam < 1.0 / 1024.0 or not np.all(np.isfinite(xn)):
+            stalled = True
+            break
         scale = np.maximum(np.abs(x), 1e-3)
         x = xn
-        if np.max(np.abs(lam * dxv) / scale) < tol:
+        if lam == 1.0 and np.max(np.abs(dxv) / scale) < tol:
             break
     R = residual(x, dsmc, hot, cfg)
     X = x.reshape(NV, n)
     out = np.stack([X[0], X[1], X[2], dsmc[:, F_U + 2], X[3], X[4]], axis=1)
+    if stalled:
+        out = np.stack([dsmc[:, F_RHO], dsmc[:, F_U], dsmc[:, F_U + 1], dsmc[:, F_U + 2], dsmc[:, F_TT],
+                        dsmc[:, F_TR]], axis=1)
     return out, it, float(np.max(np.abs(R)))

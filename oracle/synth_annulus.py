@@ -30,11 +30,13 @@ j (radii R_j .. R_{j+1}, ``fields.ring_edges``) and sector k (angles
   the frame; the fourth-difference dissipation of the box on the conserved
   variables in the face's frame, along the ring index (arcs, where rings
   f-1 .. f+2 exist) or the sector index (rays, periodic);
-* the ring next to the cylinder keeps the sampled u_x, u_y, T_t, T_r and
-  balances its mass (no flux through the cylinder); the outer ring, on the
-  freestream side, keeps its whole sampled state; every other cell balances
-  all five.  The outer ring's density fixes the mass, so there is no
-  total-mass row.
+* both boundary rings keep their whole sampled state: the one next to the
+  cylinder (the wall's Knudsen layer, as the box's wall cells keep u, T)
+  and the outer one, on the freestream side; every other cell balances all
+  five.  The rings' densities fix the mass, so there is no total-mass row.
+  (A first ring that balanced its mass with its velocity held, as the box's
+  wall cells do, has no solution behind a hypersonic cylinder: its density
+  collapses in the wake.)
 
 Newton's method from the sampled fields, the Jacobian by central
 differences (cells of one colour perturbed together), a dense solve (the
@@ -204,9 +206,8 @@ def residual(x: np.ndarray, dsmc: np.ndarray, hot: np.ndarray, cfg: dict) -> np.
     Rm = np.stack([div[0], div[1], div[2], div[3], div[4] - src])
     D = dsmc.reshape(nr, nt, -1)
     cols = (F_RHO, F_U, F_U + 1, F_TT, F_TR)
-    for v in range(1, NV):  # the ring next to the cylinder: Dirichlet u, T
+    for v in range(NV):  # the boundary rings: their whole sampled state
         Rm[v, 0] = X[v, 0] - D[0, :, cols[v]]
-    for v in range(NV):  # the outer ring: the whole sampled state
         Rm[v, -1] = X[v, -1] - D[-1, :, cols[v]]
     return Rm.reshape(-1)
 
@@ -258,27 +259,41 @@ def jacobian(x: np.ndarray, dsmc: np.ndarray, hot: np.ndarray, cfg: dict) -> np.
 
 def synth_solve_annulus(dsmc: np.ndarray, hot: np.ndarray, cfg: dict, tol: float = 1e-12, max_iter: int = 50):
     """Newton iterations from the sampled fields until the largest relative
-    update is below tol.  Returns (out [ncells x 6] = rho, u_x, u_y, u_z (the
-    sampled one), T_t, T_r; iterations; final max |residual|)."""
+    update of a full step is below tol.  Returns (out [ncells x 6] = rho,
+    u_x, u_y, u_z (the sampled one), T_t, T_r; iterations; final max
+    |residual|); when positivity cuts a step below 1/1024 (a stall: no
+    solution near the state) out is the sampled fields."""
     nt, nr = int(cfg["nx"]), int(cfg["ny"])
     if nt < 4 or nr < 3:
         raise ValueError("synth_solve_annulus needs at least 4 sectors and 3 rings")
     n = nt * nr
     x = initial_state(dsmc)
     it = 0
+    stalled = False
     for it in range(1, max_iter + 1):
         Rv = residual(x, dsmc, hot, cfg)
         dxv = np.linalg.solve(jacobian(x, dsmc, hot, cfg), -Rv)
+        # halve the step (at most 60 times) until rho, T_t, T_r stay
+        # positive and finite; a step cut below 1/1024 is a stall (no
+        # solution near this state): the sampled fields are the answer
         lam = 1.0
         xn = x + dxv
-        while np.any(xn[0:n] <= 0) or np.any(xn[3 * n:] <= 0):
+        for _ in range(60):
+            if np.all(np.isfinite(xn)) and not (np.any(xn[0:n] <= 0) or np.any(xn[3 * n:] <= 0)):
+                break
             lam *= 0.5
             xn = x + lam * dxv
+        if lam < 1.0 / 1024.0 or not np.all(np.isfinite(xn)):
+            stalled = True
+            break
         scale = np.maximum(np.abs(x), 1e-3)
         x = xn
-        if np.max(np.abs(lam * dxv) / scale) < tol:
+        if lam == 1.0 and np.max(np.abs(dxv) / scale) < tol:
             break
     Rv = residual(x, dsmc, hot, cfg)
     X = x.reshape(NV, n)
     out = np.stack([X[0], X[1], X[2], dsmc[:, F_U + 2], X[3], X[4]], axis=1)
+    if stalled:
+        out = np.stack([dsmc[:, F_RHO], dsmc[:, F_U], dsmc[:, F_U + 1], dsmc[:, F_U + 2], dsmc[:, F_TT],
+                        dsmc[:, F_TR]], axis=1)
     return out, it, float(np.max(np.abs(Rv)))

@@ -327,8 +327,8 @@ __host__ __device__ inline void face_flux(const Grid& g, const View& X, int dir,
 // dth (i + 1/2); a ray at angle phi in ring j: (R_{j+1} - R_j) e_theta(phi)),
 // sector areas as volumes, the box's face flux in each face's frame (n, t =
 // n turned by +90 degrees) with the tangential derivatives averaged from the
-// two cells' Cartesian gradients; the first ring keeps u, T and balances its
-// mass (no flux through the cylinder), the outer ring keeps its whole state.
+// two cells' Cartesian gradients; the ring next to the cylinder and the outer
+// ring keep their whole sampled state.
 // ---------------------------------------------------------------------------
 __host__ __device__ inline double ann_rc(const Grid& g, int j) { return 0.5 * (g.R[j] + g.R[j + 1]); }
 
@@ -464,7 +464,7 @@ __host__ __device__ inline void ann_face_flux(const Grid& g, const View& X, int 
 
 __host__ __device__ inline void ann_cell_residual(const Grid& g, const View& X, int i, int j, double* R) {
   const double* D = g.F + (size_t)(j * g.nx + i) * 18;
-  if (j == g.ny - 1) {  // the outer ring: its sampled state
+  if (j == 0 || j == g.ny - 1) {  // the boundary rings: their sampled state
     R[0] = X.at(g, i, j, 0) - D[0];
     R[1] = X.at(g, i, j, 1) - D[1];
     R[2] = X.at(g, i, j, 2) - D[2];
@@ -477,11 +477,9 @@ __host__ __device__ inline void ann_cell_residual(const Grid& g, const View& X, 
   const double sa = 2.0 * g.R[j + 1] * g.s2, sr = g.R[j + 1] - g.R[j];
   ann_face_flux(g, X, 1, i, j, Fa);  // the outer arc
   for (int k = 0; k < NV; ++k) div[k] += Fa[k] * sa;
-  if (j > 0) {  // the inner arc (none at the cylinder)
-    ann_face_flux(g, X, 1, i, j - 1, Fa);
-    const double sb = 2.0 * g.R[j] * g.s2;
-    for (int k = 0; k < NV; ++k) div[k] -= Fa[k] * sb;
-  }
+  ann_face_flux(g, X, 1, i, j - 1, Fa);  // the inner arc
+  const double sb = 2.0 * g.R[j] * g.s2;
+  for (int k = 0; k < NV; ++k) div[k] -= Fa[k] * sb;
   ann_face_flux(g, X, 0, i, j, Fa);  // the ray at the sector's upper angle
   for (int k = 0; k < NV; ++k) div[k] += Fa[k] * sr;
   ann_face_flux(g, X, 0, i > 0 ? i - 1 : g.nx - 1, j, Fa);  // and at its lower angle
@@ -489,13 +487,6 @@ __host__ __device__ inline void ann_cell_residual(const Grid& g, const View& X, 
   const double V = 0.5 * g.dth * (g.R[j + 1] * g.R[j + 1] - g.R[j] * g.R[j]);
   for (int k = 0; k < NV; ++k) div[k] /= V;
   R[0] = div[0];
-  if (j == 0) {  // next to the cylinder: the sampled u, T
-    R[1] = X.at(g, i, j, 1) - D[1];
-    R[2] = X.at(g, i, j, 2) - D[2];
-    R[3] = X.at(g, i, j, 3) - D[4];
-    R[4] = X.at(g, i, j, 4) - D[5];
-    return;
-  }
   const double rho = X.at(g, i, j, 0), tt = X.at(g, i, j, 3), tr = X.at(g, i, j, 4);
   const double T = (3.0 * tt + g.d_r * tr) / (3.0 + g.d_r);
   const double mu = g.mu_ref * pow(T, g.omega);
