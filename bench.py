@@ -377,8 +377,8 @@ def run_tts2d(args):
     path: Kn 0.02 on 50 x 50 cells (1000 per cell, 2.5 M particles; windows
     of 200 steps, bins of 5 x 5 cells) and Kn 0.01 on 100 x 100 (500 per
     cell, 5 M; windows of 500 steps, bins of 10 x 10 cells), where viscous
-    diffusion takes four times longer; and a subsonic flow past the cylinder
-    at Kn 0.1 on the paper's 100 x 64 annulus."""
+    diffusion takes four times longer; and the flow past the cylinder at Kn
+    0.1 on the paper's 100 x 64 annulus, at Mach 5 and Mach 0.5."""
     from paper_2501_10965_gb300 import dig, workloads as W
     out = []
     for kn, n, ppc, window, b, transient, average, max_plain in ((0.02, 50, 1000, 200, 5, 15000, 10000, 20000),
@@ -390,18 +390,21 @@ def run_tts2d(args):
                                   max_dig=4000, max_plain=max_plain)
         out.append(dict(r, case="cavity", kn=kn, lid_mps=100.0, n_s=int(cfg["n_s"]), kn_ref=float(cfg["kn_ref"])))
         print(json.dumps({"time_to_steady_2d": out[-1]}), flush=True)
-    if not args.tts2d_case or args.tts2d_case == "cylinder":
-        # the flow past the cylinder at Kn 0.1 on the paper's 100 x 64 mesh,
-        # subsonic (Mach 0.5: the synthetic equations' central differences
-        # have no shock), 100 particles per cell (0.64 M), the wall at the
-        # freestream temperature, Kn_ref 0.01 as in Sec. 4.2; windows of 1000
-        # steps (a transit of the domain takes ~11 100), bins of 10 sectors x
-        # 8 rings
-        cfg = W.cylinder_2d(ntheta=100, nr=64, ppc=100, kn=0.1, mach=0.5, t_wall=1.0, kn_ref=0.01, synth2d=True,
+    # the flow past the cylinder at Kn 0.1 on the paper's 100 x 64 mesh
+    # (Sec. 4.2), 100 particles per cell (0.64 M), the wall at the freestream
+    # temperature, Kn_ref 0.01 as in the paper: Mach 5 (the paper's case;
+    # windows of 500 steps, a transit of the domain takes ~2 760) and Mach
+    # 0.5 (windows of 1 000 steps, a transit ~11 100); bins of 10 sectors x
+    # 8 rings
+    for mach, window, transient, average, max_plain in ((5.0, 500, 15000, 15000, 25000),
+                                                        (0.5, 1000, 60000, 30000, 80000)):
+        if args.tts2d_case and args.tts2d_case != f"cylinder{mach:g}":
+            continue
+        cfg = W.cylinder_2d(ntheta=100, nr=64, ppc=100, kn=0.1, mach=mach, t_wall=1.0, kn_ref=0.01, synth2d=True,
                             synth_tol=1e-8, n_m=50)
-        r = dig.time_to_steady_2d(cfg, window=1000, bx=10, by=8, transient=60000, average=30000, max_dig=6000,
-                                  max_plain=80000)
-        out.append(dict(r, case="cylinder", kn=0.1, mach=0.5, n_s=int(cfg["n_s"]), kn_ref=0.01))
+        r = dig.time_to_steady_2d(cfg, window=window, bx=10, by=8, transient=transient, average=average,
+                                  max_dig=6000, max_plain=max_plain)
+        out.append(dict(r, case="cylinder", kn=0.1, mach=mach, n_s=int(cfg["n_s"]), kn_ref=0.01))
         print(json.dumps({"time_to_steady_2d": out[-1]}), flush=True)
 
 
@@ -577,7 +580,8 @@ def main():
     ap.add_argument("--synth2d-reps", type=int, default=3)
     ap.add_argument("--tts2d", action="store_true",
                     help="only measure DIG against plain DSMC to steady state on 2D cavities")
-    ap.add_argument("--tts2d-case", default="", help="only one case: 0.02, 0.01 (cavities) or cylinder")
+    ap.add_argument("--tts2d-case", default="",
+                    help="only one case: 0.02, 0.01 (cavities), cylinder5 or cylinder0.5")
     args = ap.parse_args()
     if args.tts2d:
         run_tts2d(args)

@@ -377,6 +377,7 @@ def time_to_steady_2d(cfg: dict, window: int = 200, bx: int = 5, by: int = 5, tr
         sim = dsmc.Dsmc(cfg)
         hist, steps, walls, wall, nsteps = [], [], [], 0.0, 0
         steady = None
+        solves = []  # (status, Newton iterations) of the DIG iterations' synthetic solves
         while nsteps < cap:
             torch.cuda.synchronize()
             ta = time.perf_counter()
@@ -385,6 +386,7 @@ def time_to_steady_2d(cfg: dict, window: int = 200, bx: int = 5, by: int = 5, tr
                 for _ in range(max(1, window // n_s)):
                     r = dig_iteration(sim, n_s)
                     fs.append(r["fields"].cpu().numpy())
+                    solves.append((int(r["synth_status"]), int(r["synth_iters"])))
                 f = np.mean(fs, axis=0)
                 nsteps += n_s * len(fs)
             else:
@@ -403,6 +405,10 @@ def time_to_steady_2d(cfg: dict, window: int = 200, bx: int = 5, by: int = 5, tr
         out[method] = {"steady_step": steps[steady] if steady is not None else None,
                        "steady_wall_s": walls[steady] if steady is not None else None,
                        "errors": [round(e, 4) for e in hist], "final_error": hist[-1] if hist else None}
+        if solves:
+            out[method]["synth_solves"] = len(solves)
+            out[method]["synth_not_converged"] = sum(1 for st, _ in solves if st != 0)
+            out[method]["synth_mean_newton_steps"] = float(np.mean([it for _, it in solves]))
         del sim
     d, p = out["dig"], out["plain"]
     if d["steady_step"] and p["steady_step"]:
