@@ -246,9 +246,10 @@ int synth_solve(dsmc_handle *h, const double *dev_fields, const double *dev_hot,
  * placed uniformly in the cell (an empty cell draws from the target
  * Maxwellian); (iii) sample u*, T_t*, T_r* of the result; (iv) v <- a v + b,
  * I_r <- c I_r with a = sqrt(T_t/T_t*), b = u - a u*, c = T_r/T_r*.
- * DSMC_ERR_NUMERIC (nothing changed) if a target is non-finite, rho < 0 or a
- * temperature <= 0; DSMC_ERR_CAPACITY (nothing changed) if the new total does
- * not fit. */
+ * DSMC_ERR_NUMERIC (nothing changed) if a target is non-finite, rho < 0 or,
+ * where rho > 0, a temperature <= 0 (a cell with rho = 0, such as an
+ * unsampled cell's fields, empties and its temperatures are not used);
+ * DSMC_ERR_CAPACITY (nothing changed) if the new total does not fit. */
 int dig_correct(dsmc_handle *h, const double *dev_target);
 
 /* Largest slab synth_solve_noalloc accepts. */

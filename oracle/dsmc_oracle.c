@@ -1089,7 +1089,8 @@ int or_dig_correct(or_state *S, const double *target) {
     const double *t = target + (size_t)cell * 6;
     for (int q = 0; q < 6; ++q)
       if (!isfinite(t[q])) return OR_ERR_NUMERIC;
-    if (!(t[0] >= 0.0) || !(t[4] > 0.0) || !(t[5] > 0.0)) return OR_ERR_NUMERIC;
+    /* an empty target cell (rho 0) has no particles whose T would matter */
+    if (!(t[0] >= 0.0) || (t[0] > 0.0 && (!(t[4] > 0.0) || !(t[5] > 0.0)))) return OR_ERR_NUMERIC;
   }
   /* step i: target counts */
   int64_t *nt = (int64_t *)malloc(sizeof(int64_t) * (size_t)nc);

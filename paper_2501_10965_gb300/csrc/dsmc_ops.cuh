@@ -1302,7 +1302,9 @@ static __global__ void k_dig_counts(const CellParams* __restrict__ cps, const in
       bool bad = false;
       for (int q = 0; q < 6; ++q)
         if (!isfinite(t[q])) bad = true;
-      if (!(t[0] >= 0.0) || !(t[4] > 0.0) || !(t[5] > 0.0)) bad = true;
+      // an empty target cell (rho 0, as an unsampled cell's fields read)
+      // has no particles whose temperatures would matter
+      if (!(t[0] >= 0.0) || (t[0] > 0.0 && (!(t[4] > 0.0) || !(t[5] > 0.0)))) bad = true;
       if (bad) {
         atomicOr(flags, 1);
         nt[c] = 0;

@@ -201,6 +201,30 @@ def test_dig_correct_refills_one_particle_cells(precision):
     assert np.allclose(a["ir"], 0.8, rtol=1e-7)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dig_correct_accepts_an_unsampled_cells_zero_row(precision):
+    """A target row of zeros (an unsampled cell's fields) empties the cell;
+    the other cells follow their targets (FP64: the oracle's particles)."""
+    cfg = W.fourier_1d(nx=8, ppc=30, precision=precision)
+    g = _gpu(cfg)
+    g.dsmc_step(3)
+    rng = np.random.default_rng(9)
+    t = np.zeros((8, 6))
+    t[:, 0] = 0.8 + 0.4 * rng.random(8)
+    t[:, 4] = 0.9 + 0.2 * rng.random(8)
+    t[:, 5] = 0.9 + 0.2 * rng.random(8)
+    t[3] = 0.0
+    if precision == "fp64":
+        o = oracle.OracleSim(cfg)
+        o.step(3)
+    g.dig_correct(torch.tensor(t, device="cuda"))
+    cnt = np.bincount(_np(g.get_particles())["cell"], minlength=8)
+    assert cnt[3] == 0 and np.all(np.delete(cnt, 3) > 0)
+    if precision == "fp64":
+        assert o.dig_correct(t) == 0
+        _compare_states(_np(g.get_particles()), o.particles(), what="zero row")
+
+
 def test_dig_correct_rejects_bad_target_gpu():
     from paper_2501_10965_gb300.dsmc import DsmcError
     cfg = W.fourier_1d(nx=10, ppc=10)

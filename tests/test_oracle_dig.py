@@ -246,3 +246,22 @@ def test_synth_residual_zero_at_solution_and_hot_enters_as_flux():
     assert r2 < 1e-10 and np.max(np.abs(out2[:, 4] - out0[:, 4])) > 1e-3
     x = np.concatenate([out2[:, 0], out2[:, 2], out2[:, 3], out2[:, 4], out2[:, 5]])
     assert np.max(np.abs(residual(x, f, hot, cfg))) < 1e-10
+
+
+def test_dig_correct_empties_a_cell_whose_target_density_is_zero():
+    """A target row of zeros (an unsampled cell's fields) empties the cell
+    and is accepted although its temperatures are zero; with rho > 0 a zero
+    temperature is still rejected."""
+    cfg = W.fourier_1d(nx=6, ppc=20)
+    sim = oracle.OracleSim(cfg)
+    t = _cell_moments(sim.particles(), 6)
+    c = sim.constants()
+    t[:, 0] = t[:, 0] * c["fnum"] / c["vcell"]
+    t[2] = 0.0
+    assert sim.dig_correct(t) == 0
+    cnt = np.bincount(sim.particles()["cell"], minlength=6)
+    assert cnt[2] == 0 and np.all(cnt[[0, 1, 3, 4, 5]] > 0)
+    t[3, 4] = 0.0
+    p0 = sim.particles()
+    assert sim.dig_correct(t) == -3
+    assert np.array_equal(sim.particles()["x"], p0["x"])
