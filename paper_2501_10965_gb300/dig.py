@@ -59,11 +59,21 @@ def dig_iteration(sim: "dsmc.Dsmc", n_s: int, allow_not_converged: bool = True,
         hot, judge, nnet = sim.mlp_apply_judged(fs, hot, kn_s, mask_s, group=hot_group, z=judge_z,
                                                 min_samples=judge_min, rel=judge_rel)
     out, iters, res = sim.synth_solve(f, hot, allow_not_converged=allow_not_converged, allow_fallback=True)
-    sim.dig_correct(out)
+    # a target the modification refuses (a sampled cell with particles but a
+    # zero temperature, as a nearly empty cell of an early wake has) leaves
+    # the particles as they are: the iteration is plain DSMC
+    modified = True
+    try:
+        sim.dig_correct(out)
+    except dsmc.DsmcError as e:
+        if e.code != -3:
+            raise
+        modified = False
     # the HoT mask stays on the device (reducing it here would put a host
     # round trip, and the first use of a framework kernel, into the loop)
     return {"fields": f, "target": out, "synth_iters": iters, "synth_resid": res,
-            "synth_status": sim.last_synth_status, "mask": mask, "judge": judge, "network_cells": nnet}
+            "synth_status": sim.last_synth_status, "mask": mask, "judge": judge, "network_cells": nnet,
+            "modified": modified}
 
 
 def total_temperature(f: np.ndarray, d_r: float = 2.0) -> np.ndarray:
@@ -386,7 +396,7 @@ def time_to_steady_2d(cfg: dict, window: int = 200, bx: int = 5, by: int = 5, tr
                 for _ in range(max(1, window // n_s)):
                     r = dig_iteration(sim, n_s)
                     fs.append(r["fields"].cpu().numpy())
-                    solves.append((int(r["synth_status"]), int(r["synth_iters"])))
+                    solves.append((int(r["synth_status"]), int(r["synth_iters"]), bool(r["modified"])))
                 f = np.mean(fs, axis=0)
                 nsteps += n_s * len(fs)
             else:
@@ -407,8 +417,9 @@ def time_to_steady_2d(cfg: dict, window: int = 200, bx: int = 5, by: int = 5, tr
                        "errors": [round(e, 4) for e in hist], "final_error": hist[-1] if hist else None}
         if solves:
             out[method]["synth_solves"] = len(solves)
-            out[method]["synth_not_converged"] = sum(1 for st, _ in solves if st != 0)
-            out[method]["synth_mean_newton_steps"] = float(np.mean([it for _, it in solves]))
+            out[method]["synth_not_converged"] = sum(1 for st, _, _ in solves if st != 0)
+            out[method]["synth_mean_newton_steps"] = float(np.mean([it for _, it, _ in solves]))
+            out[method]["modifications_skipped"] = sum(1 for _, _, mod in solves if not mod)
         del sim
     d, p = out["dig"], out["plain"]
     if d["steady_step"] and p["steady_step"]:
