@@ -921,6 +921,7 @@ static int synth_solve_2d(dsmc_handle* h, const double* dev_fields, const double
   int singular = 0;
   const int e = launch_synth2d(h->cp, dev_fields, dev_hot, dev_out, h->synth_work, n_m, tol, h->synth_info,
                                &singular, h->stream);
+  if (e == S2_TIMEOUT_RC) return set_err(h, DSMC_ERR_TIMEOUT, "synth_solve: a wait of the substitution gave up");
   if (e) return set_err(h, DSMC_ERR_CUDA, "synth_solve: %s", cudaGetErrorString((cudaError_t)e));
   double info[3];
   cudaMemcpyAsync(info, h->synth_info, sizeof info, cudaMemcpyDeviceToHost, h->stream);

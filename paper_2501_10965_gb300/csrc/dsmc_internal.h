@@ -154,7 +154,9 @@ cudaError_t launch_synth1d_single(const CellParams& cp, const double* fields, co
 size_t synth1d_work_doubles(int ncells);
 // 2D synthetic equations of one box case (dsmc_synth2d.cu): doubles of work,
 // and the solve (info = iterations, max residual, status; *singular set when
-// a zero pivot was met); returns a cudaError_t value
+// a zero pivot was met); returns a cudaError_t value, or S2_TIMEOUT_RC when a
+// bounded wait of the substitution gave up
+constexpr int S2_TIMEOUT_RC = -2;
 size_t synth2d_work_doubles(int nx, int ny, int annulus);
 int launch_synth2d(const CellParams& cp, const double* fields, const double* hot, double* out, double* work,
                    int n_m, double tol, double* info, int* singular, cudaStream_t st);

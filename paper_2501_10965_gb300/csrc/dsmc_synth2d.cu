@@ -21,6 +21,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <type_traits>
+#include <utility>
 
 #include "dsmc_internal.h"
 #include "dsmc_synth2d.cuh"
@@ -39,6 +41,7 @@ enum {
   S2_DMAX = 5,
   S2_SING = 6,   // a zero pivot was met
   S2_LAM = 7,    // length of the last Newton update (1 = full step)
+  S2_TOUT = 8,   // a wait of the substitution gave up
   S2_NSC = 16
 };
 
@@ -49,6 +52,7 @@ constexpr int S2_PNL_NT = 512;    // the panel factorisation
 constexpr int S2_NREF = 1;        // refinement sweeps after a fresh factorisation
 constexpr int S2_NREF_REUSE = 3;  // refinement sweeps when an earlier factorisation is reused
 constexpr int S2_SMEM_CAP = 200 * 1024;
+constexpr size_t S2_DF_SMEM_CAP = 200 * 1024;  // rows of the data-flow substitution per CTA (4 copies of 32 floats a block)
 
 // Panel width nb and trailing columns per CTA cb (4: enough CTAs to fill the
 // GPU for the kl + ku trailing columns): the largest nb of 32, 16, 8 whose
@@ -72,6 +76,8 @@ struct S2Work {
   float *AB, *Lp, *ud;
   int32_t* piv;
   float* q;  // 4 FP32 vectors of N: the clustered substitution's ping-pong right-hand sides
+  float* inv;     // per panel: the inverses of its L11 and U11 triangles (2 x 32 x 32)
+  int32_t* smap;  // per panel: its interchanges as a map of rows (128 entries, k_s2_sprep)
   int nb, cb;
 };
 
@@ -84,7 +90,9 @@ inline size_t s2_doubles(const s2::Grid& g) {
   const size_t N = (size_t)g.N;
   const size_t vec = round32(N);
   const size_t jc = round32((size_t)g.n * s2::NSTENCIL * s2::NV * s2::NV);
-  const size_t f32 = (size_t)g.ld * N + s2_lp_floats(g, bl.nb) + N + N + 4 * N;  // AB, Lp, ud, piv, q
+  const size_t nk = (N + bl.nb - 1) / bl.nb;
+  // AB, Lp, ud, piv, q, inv, smap
+  const size_t f32 = (size_t)g.ld * N + s2_lp_floats(g, bl.nb) + N + N + 4 * N + 2048 * nk + 128 * nk;
   return 13 * vec + 32 + jc + round32((f32 + 1) / 2) + 32;
 }
 
@@ -112,6 +120,10 @@ S2Work s2_carve(const s2::Grid& g, double* w) {
   s.piv = reinterpret_cast<int32_t*>(f);
   f += g.N;
   s.q = f;
+  f += 4 * (size_t)g.N;
+  s.inv = f;
+  f += 2048 * (size_t)((g.N + bl.nb - 1) / bl.nb);
+  s.smap = reinterpret_cast<int32_t*>(f);
   s.nb = bl.nb;
   s.cb = bl.cb;
   return s;
@@ -173,6 +185,7 @@ __global__ void __launch_bounds__(S2_NT) k_s2_init(const s2::Grid g, S2Work w) {
     w.sc[S2_DMAX] = 0.0;
     w.sc[S2_SING] = 0.0;
     w.sc[S2_LAM] = 0.0;
+    w.sc[S2_TOUT] = 0.0;
   }
 }
 
@@ -334,6 +347,153 @@ __global__ void __launch_bounds__(S2_PNL_NT) k_s2_panel(const s2::Grid g, S2Work
   }
   __syncthreads();
   s2::panel_store(g, w.nb, w.AB, w.Lp, w.ud, k0, wd, H, P, tid, S2_PNL_NT);
+}
+
+// f(integral_constant<int, J>) for J = 0, 1, ... in order
+template <typename F, int... J>
+__device__ __forceinline__ void s2_static_for(F& f, std::integer_sequence<int, J...>) {
+  (f(std::integral_constant<int, J>{}), ...);
+}
+
+// The same factorisation with the panel in registers: thread t holds rows
+// r = t + s S2_PNL_NT (s < RPT) of all 32 columns.  Per step the pivot row
+// passes through shared memory once (and the displaced row j, when the
+// interchange moves it), instead of every rank-one update reading and
+// writing the panel there.  The operations on each entry, their order and
+// the choice of pivots are those of k_s2_panel, so the factors are the same.
+template <int RPT>
+__global__ void __launch_bounds__(S2_PNL_NT, 1) k_s2_panel_rg(const s2::Grid g, S2Work w, int k0) {
+  __shared__ float cbest[2][S2_PNL_NT / 32];
+  __shared__ int cidx[2][S2_PNL_NT / 32];
+  __shared__ float prow[32], jrow[32];
+  const int tid = threadIdx.x;
+  const int wd = s2::panel_width(g, w.nb, k0), H = s2::panel_height(g, wd, k0);
+  float a[RPT][32];
+#pragma unroll
+  for (int s = 0; s < RPT; ++s) {
+    const int r = tid + s * S2_PNL_NT;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const bool in = r < H && c < wd && s2::in_band(g, k0 + r, k0 + c);
+      a[s][c] = in ? w.AB[s2::band_at(g, k0 + r, k0 + c)] : 0.0f;
+    }
+  }
+  float best = -1.0f, pbest = -1.0f;
+  int bi = INT_MAX;
+  {
+    const int rm0 = s2::panel_rmax(g, H, 0);
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) {
+      const int r = tid + s * S2_PNL_NT;
+      const float v = fabsf(a[s][0]);
+      if (r <= rm0 && v > best) {
+        best = v;
+        bi = r;
+      }
+    }
+  }
+  int p = s2_block_argmax(best, bi, cbest, cidx, 0, 0, pbest);
+  // step j of the elimination, j a compile-time constant so that the rows
+  // stay in registers
+  auto step = [&](auto jt) {
+    constexpr int j = decltype(jt)::value;
+    if (j < wd) {
+      if (tid == 0) {
+        w.piv[k0 + j] = k0 + p;
+        if (!(pbest > 0.0f)) w.sc[S2_SING] = 1.0;
+      }
+      const int pt = p % S2_PNL_NT, ps = p / S2_PNL_NT;
+      // the pivot row to prow (and row j to jrow when they trade places)
+      if (tid == pt) {
+#pragma unroll
+        for (int s = 0; s < RPT; ++s)
+          if (s == ps) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) prow[c] = a[s][c];
+          }
+      }
+      if (p != j && tid == j) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) jrow[c] = a[0][c];
+      }
+      __syncthreads();
+      if (p != j) {
+        if (tid == pt) {
+#pragma unroll
+          for (int s = 0; s < RPT; ++s)
+            if (s == ps) {
+#pragma unroll
+              for (int c = 0; c < 32; ++c) a[s][c] = jrow[c];
+            }
+        }
+        if (tid == j) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) a[0][c] = prow[c];
+        }
+      }
+      const float piv = prow[j];
+      const int rm = s2::panel_rmax(g, H, j);
+      float l[RPT];
+      bool upd[RPT];
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        const int r = tid + s * S2_PNL_NT;
+        upd[s] = r > j && r <= rm;
+        l[s] = piv != 0.0f ? a[s][j] / piv : 0.0f;
+        if (upd[s]) a[s][j] = l[s];
+      }
+#pragma unroll
+      for (int c = j + 1; c < 32; ++c) {
+        if (c < wd) {
+          const float pc = prow[c];
+#pragma unroll
+          for (int s = 0; s < RPT; ++s)
+            if (upd[s]) a[s][c] -= l[s] * pc;
+        }
+      }
+      if (j + 1 < wd) {
+        const int rm1 = s2::panel_rmax(g, H, j + 1);
+        best = -1.0f;
+        bi = INT_MAX;
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) {
+          const int r = tid + s * S2_PNL_NT;
+          const float v = fabsf(a[s][(j + 1) & 31]);
+          if (r > j && r <= rm1 && v > best) {
+            best = v;
+            bi = r;
+          }
+        }
+        p = s2_block_argmax(best, bi, cbest, cidx, (j + 1) & 1, j + 1, pbest);
+      }
+    }
+  };
+  s2_static_for(step, std::make_integer_sequence<int, 32>{});
+  // U (rows above and on the diagonal), its diagonal and the multipliers: the
+  // stores of s2::panel_store
+  const size_t base = s2::lp_base(g, w.nb, k0);
+  const int ldp = g.kl + w.nb;
+#pragma unroll
+  for (int s = 0; s < RPT; ++s) {
+    const int r = tid + s * S2_PNL_NT;
+    if (r < H) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < wd) {
+          const int k = k0 + c;
+          const float v = a[s][c];
+          if (r < c) {
+            w.AB[s2::band_at(g, k0 + r, k)] = v;
+          } else if (r == c) {
+            w.ud[k] = v;
+            w.AB[s2::band_at(g, k, k)] = v;
+          } else {
+            w.Lp[base + (size_t)c * ldp + r] = v;
+          }
+        }
+      }
+    }
+  }
 }
 
 // The panel's interchanges and eliminations on up to cbt trailing columns per
@@ -895,6 +1055,532 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Substitution tables of one factorisation, a warp per panel k (used by
+// k_s2_subst_df): the inverses of the panel's unit-lower L11 and upper U11
+// triangles (sc_tri_row / sc_tri_inverse, row-major 32 x 32 at inv + 2048 k
+// and inv + 2048 k + 1024), and the panel's interchanges as a map of rows:
+// smap[128 k + i], i < 32, the row whose value ends at head position k0 + i
+// (k0 + i itself past the panel's width); smap[128 k + 32 + q] and
+// smap[128 k + 64 + q], q < smap[128 k + 96], the rows past the head whose
+// value changes (ascending) and the head position each takes it from.
+// ---------------------------------------------------------------------------
+constexpr int SP_WPB = 4;  // warps (panels) per CTA of k_s2_sprep
+
+__global__ void __launch_bounds__(SP_WPB * 32) k_s2_sprep(const s2::Grid g, S2Work w) {
+  __shared__ float scr[SP_WPB][32][33];
+  __shared__ float inv[SP_WPB][32][33];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int nb = w.nb, N = g.N, nk = (N + nb - 1) / nb;
+  const int k = blockIdx.x * SP_WPB + wp;
+  if (k >= nk) return;
+  const int k0 = k * nb, wd = s2::panel_width(g, nb, k0);
+  float fr[32];
+  for (int t = 0; t < 2; ++t) {
+    sc_tri_row(g, w, t == 0, k0, lane, fr);
+    sc_tri_inverse(t == 0, fr, scr[wp], inv[wp], lane);
+    float* dst = w.inv + (size_t)k * 2048 + t * 1024;
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) dst[i * 32 + lane] = inv[wp][i][lane];
+    __syncwarp();
+  }
+  if (lane == 0) {
+    // the interchanges applied in order to a sparse map (touched rows only)
+    int pos[64], val[64], nt = 0;
+    auto find = [&](int r) {
+      for (int q = 0; q < nt; ++q)
+        if (pos[q] == r) return q;
+      pos[nt] = r;
+      val[nt] = r;
+      return nt++;
+    };
+    for (int j = 0; j < wd; ++j) {
+      const int p = w.piv[k0 + j];
+      if (p != k0 + j) {
+        const int a = find(k0 + j), b = find(p);
+        const int t = val[a];
+        val[a] = val[b];
+        val[b] = t;
+      }
+    }
+    int32_t* sm = w.smap + (size_t)k * 128;
+    for (int i = 0; i < 32; ++i) sm[i] = k0 + i;
+    int ntail = 0;
+    for (int q = 0; q < nt; ++q) {
+      if (pos[q] < k0 + wd) {
+        sm[pos[q] - k0] = val[q];
+      } else if (val[q] != pos[q]) {
+        // insertion in ascending order of the row
+        int z = ntail++;
+        while (z > 0 && sm[32 + z - 1] > pos[q]) {
+          sm[32 + z] = sm[32 + z - 1];
+          sm[64 + z] = sm[64 + z - 1];
+          --z;
+        }
+        sm[32 + z] = pos[q];
+        sm[64 + z] = val[q];
+      }
+    }
+    sm[96] = ntail;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The substitutions as a data flow across a cluster of DF_C CTAs, with no
+// cluster-wide barrier per panel.  Rows are owned by 32-row block: block b
+// (rows 32 b .. 32 b + 31) by CTA b % DF_C, its values in that CTA's shared
+// memory in two copies (parities): step s reads copy s % 2 and writes copy
+// (s + 1) % 2, so that values read remotely are never overwritten while
+// still needed (rows outside a step's window keep their value in both).
+//
+// Warp 0 of the owner of panel k's head block computes the head's values
+// itself, from the other copy and the previous step's result (the previous
+// panel's multipliers for the head's source rows), applies the inverse of
+// the panel's triangle and sends the 32 results (two right-hand sides) into
+// a ring of DF_S slots in every CTA, each slot completed on an mbarrier.
+// Warps 1 .. DF_UW of every CTA take each step's result from the ring and
+// update their CTA's rows of the step's window, then publish the number of
+// steps done (release); a reader of another CTA's rows first waits (acquire)
+// until that count covers the step the values come from.  Each wait gives
+// up after DF_WAIT_NS (the kernel then records the timeout in the work area
+// and every CTA leaves at the next cluster barrier).
+//
+// The arithmetic of each row and head value, and its order, are those of
+// k_s2_subst_cl; forward, then (after one cluster barrier) backward.
+// ---------------------------------------------------------------------------
+constexpr int DF_C = 8;                  // CTAs of the cluster
+constexpr int DF_UW = 8;                 // update warps per CTA
+constexpr int DF_NT = 32 * (1 + DF_UW);  // warp 0 solves the heads
+constexpr int DF_S = 32;                 // ring slots (steps in flight)
+constexpr unsigned long long DF_WAIT_NS = 500000000ull;  // 0.5 s
+
+__device__ __forceinline__ unsigned long long df_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned df_smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// shared::cluster address of the same shared variable in CTA `cta`
+__device__ __forceinline__ unsigned df_mapa(const void* p, unsigned cta) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(df_smem_addr(p)), "r"(cta));
+  return r;
+}
+
+__device__ __forceinline__ float df_ld_remote(unsigned addr) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned df_ld_acquire(unsigned addr) {
+  unsigned v;
+  asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void df_st_release(unsigned addr, unsigned v) {
+  asm volatile("st.release.cluster.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void df_st_remote4(unsigned addr, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
+
+__device__ __forceinline__ void df_arrive_remote(unsigned addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+__device__ __forceinline__ bool df_try_wait(const uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(df_smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// until the ring slot's phase `parity` completes; false after DF_WAIT_NS
+__device__ __forceinline__ bool df_wait_slot(const uint64_t* bar, unsigned parity) {
+  if (df_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = df_clock_ns();
+  for (;;) {
+    for (int q = 0; q < 64; ++q)
+      if (df_try_wait(bar, parity)) return true;
+    if (df_clock_ns() - t0 > DF_WAIT_NS) return false;
+  }
+}
+
+// until the step count at `addr` (any CTA of the cluster) reaches `need`;
+// false after DF_WAIT_NS
+__device__ __forceinline__ bool df_wait_count(unsigned addr, unsigned need) {
+  if (df_ld_acquire(addr) >= need) return true;
+  const unsigned long long t0 = df_clock_ns();
+  for (;;) {
+    for (int q = 0; q < 64; ++q)
+      if (df_ld_acquire(addr) >= need) return true;
+    if (df_clock_ns() - t0 > DF_WAIT_NS) return false;
+  }
+}
+
+// barrier 1 for the update warps, returning whether any of them has `bad` set
+__device__ __forceinline__ bool df_update_bar_any(bool bad) {
+  unsigned r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "barrier.cta.red.or.pred q, 1, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((unsigned)bad), "r"(32 * DF_UW)
+      : "memory");
+  return r != 0;
+}
+
+// acc0 += l . y[0:32], acc1 += l . y[32:64] (the order of k_s2_subst_cl)
+__device__ __forceinline__ void df_dot2(const float (&l)[32], const float* y, float& acc0, float& acc1) {
+#pragma unroll
+  for (int jj = 0; jj < 32; ++jj) {
+    acc0 += l[jj] * y[jj];
+    acc1 += l[jj] * y[32 + jj];
+  }
+}
+
+__global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Work w, const double* b0,
+                                                         const double* b1, double* o0, double* o1) {
+  __shared__ __align__(16) float ring[DF_S][64];  // step results: rhs 0 in [0, 32), rhs 1 in [32, 64)
+  __shared__ __align__(16) float stage[64];       // warp 0's result before it is sent
+  __shared__ __align__(8) uint64_t full[DF_S];
+  __shared__ unsigned done;       // steps this CTA's update warps have finished
+  __shared__ unsigned abort_all;  // set in every CTA once a wait gave up
+  float* const As = reinterpret_cast<float*>(s2_smem);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned rank = sc_cluster_rank();
+  constexpr int nb = 32;
+  const int N = g.N, nk = (N + nb - 1) / nb, nbl = (nk + DF_C - 1) / DF_C, ldp = g.kl + nb;
+  // copy `par` of right-hand side `rhs` at row R, in the shared memory of R's owner
+  auto aloc = [&](int par, int rhs, int R) -> float* {
+    return As + ((size_t)(2 * par + rhs) * nbl + (size_t)((R >> 5) / DF_C)) * 32 + (R & 31);
+  };
+  auto owner = [](int R) -> unsigned { return (unsigned)((R >> 5) % DF_C); };
+  auto fail = [&]() {
+    for (unsigned c = 0; c < DF_C; ++c)
+      asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(df_mapa(&abort_all, c)), "r"(1u) : "memory");
+    w.sc[S2_TOUT] = 1.0;
+  };
+  // both copies of this CTA's rows from v0s, v1s (FP64 or FP32)
+  auto fill = [&](auto v0s, auto v1s) {
+    for (int e = tid; e < nbl * 32; e += DF_NT) {
+      const int R = ((e >> 5) * DF_C + (int)rank) * 32 + (e & 31);
+      const float v0 = R < N ? (float)__ldcg(v0s + R) : 0.0f, v1 = R < N ? (float)__ldcg(v1s + R) : 0.0f;
+#pragma unroll
+      for (int par = 0; par < 2; ++par) {
+        As[(size_t)(2 * par) * nbl * 32 + e] = v0;
+        As[(size_t)(2 * par + 1) * nbl * 32 + e] = v1;
+      }
+    }
+  };
+  if (tid == 0) {
+    done = 0;
+    abort_all = 0;
+  }
+  if (tid < DF_S) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(df_smem_addr(&full[tid])) : "memory");
+  fill(b0, b1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  sc_cluster_sync();
+  unsigned known = 0;  // warp 0, lane c < DF_C: steps CTA c is known to have finished
+  // warp 0: send this step's 32 results (stage) to every CTA's ring slot t % DF_S, once the
+  // CTA has finished step t - DF_S (the slot's previous use)
+  auto send = [&](int t) -> bool {
+    __syncwarp();
+    bool ok = true;
+    if (lane < DF_C) {
+      const unsigned need = t >= DF_S ? (unsigned)(t - DF_S + 1) : 0u;
+      if (known < need) {
+        ok = df_wait_count(df_mapa(&done, lane), need);
+        if (ok) known = need;
+      }
+      if (ok) {
+        const unsigned dst = df_mapa(&ring[t % DF_S][0], lane);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) df_st_remote4(dst + 16 * q, reinterpret_cast<const float4*>(stage)[q]);
+        df_arrive_remote(df_mapa(&full[t % DF_S], lane));
+      }
+    }
+    return __all_sync(0xffffffffu, ok);
+  };
+  // ---- forward: L y = P b ----
+  if (warp == 0) {
+    for (int k = (int)rank; k < nk; k += DF_C) {
+      const int k0 = k * nb, wd = s2::panel_width(g, nb, k0);
+      const int32_t* sm = w.smap + (size_t)k * 128;
+      const int hs = sm[lane];  // the row whose value ends at head position k0 + lane
+      float invr[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) invr[jj] = __ldg(w.inv + (size_t)k * 2048 + lane * 32 + jj);
+      // hs after step k - 1: its source under panel k - 1's interchanges, less
+      // that panel's multipliers (row hs - (k0 - 32) of its window) times y_{k-1}
+      int src = hs;
+      bool inwin = false;
+      float lr[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) lr[jj] = 0.0f;
+      if (k > 0) {
+        const int p0 = k0 - nb, Hp = s2::panel_height(g, nb, p0);
+        const int r = hs - p0;
+        inwin = lane < wd && r < Hp;
+        const float* Lk = w.Lp + s2::lp_base(g, nb, p0);
+        if (inwin) {
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) lr[jj] = __ldg(Lk + (size_t)jj * ldp + r);
+        }
+        const int32_t* smp = sm - 128;
+        const int ntp = smp[96];
+        const int td = lane < ntp ? smp[32 + lane] : -1, ts = lane < ntp ? smp[64 + lane] : 0;
+        for (int q = 0; q < ntp; ++q) {
+          const int d = __shfl_sync(0xffffffffu, td, q), sv = __shfl_sync(0xffffffffu, ts, q);
+          if (d == hs) src = sv;
+        }
+      }
+      // the value after step k - 2 (copy (k - 1) % 2) once src's owner has finished it
+      bool ok = true;
+      if (k >= 2 && lane < wd) ok = df_wait_count(df_mapa(&done, owner(src)), (unsigned)(k - 1));
+      float a0 = 0.0f, a1 = 0.0f;
+      if (ok && lane < wd) {
+        const int par = (k + 1) & 1;
+        a0 = df_ld_remote(df_mapa(aloc(par, 0, src), owner(src)));
+        a1 = df_ld_remote(df_mapa(aloc(par, 1, src), owner(src)));
+      }
+      if (k > 0 && ok) {
+        const int t = k - 1;
+        ok = df_wait_slot(&full[t % DF_S], (unsigned)(t / DF_S) & 1u);
+        if (ok && inwin) {
+          float acc0 = 0.0f, acc1 = 0.0f;
+          df_dot2(lr, ring[t % DF_S], acc0, acc1);
+          a0 -= acc0;
+          a1 -= acc1;
+        }
+      }
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) fail();
+        break;
+      }
+      float y0 = 0.0f, y1 = 0.0f;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const float b0j = __shfl_sync(0xffffffffu, a0, jj), b1j = __shfl_sync(0xffffffffu, a1, jj);
+        y0 += invr[jj] * b0j;
+        y1 += invr[jj] * b1j;
+      }
+      if (lane >= wd) y0 = y1 = 0.0f;
+      stage[lane] = y0;
+      stage[32 + lane] = y1;
+      if (lane < wd) {
+        w.q[k0 + lane] = y0;  // the forward result, right-hand side of the backward pass
+        w.q[(size_t)N + k0 + lane] = y1;
+      }
+      if (!send(k)) {
+        if (lane == 0) fail();
+        break;
+      }
+    }
+  } else {
+    // update warps: warp u takes the u-th, (u + DF_UW)-th, ... of this CTA's blocks
+    // in each step's window, lane = row in the block
+    const int u = warp - 1;
+    float lr[32];
+    int td = -1, ts = 0, ntl = 0;
+    // this warp's first block of forward step s (rows 32 (s + 1) .. k0 + H - 1), or -1
+    auto first_block = [&](int s) -> int {
+      const int k0 = s * nb, H = s2::panel_height(g, s2::panel_width(g, nb, k0), k0);
+      const int bf = s + 1, bl = (k0 + H - 1) >> 5;
+      const int b = bf + (((int)rank - bf) % DF_C + DF_C) % DF_C + u * DF_C;
+      return b <= bl ? b : -1;
+    };
+    // multipliers of step s for this lane's row of block b (zero outside the window
+    // and past the panel's width), and the step's interchanges past the head
+    auto load_fwd = [&](int s, int b) {
+      const int k0 = s * nb, wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
+      const int r = 32 * b + lane - k0;
+      const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) lr[jj] = (b >= 0 && r < H && jj < wd) ? __ldg(Lk + (size_t)jj * ldp + r) : 0.0f;
+    };
+    auto load_tail = [&](int s) {
+      const int32_t* sm = w.smap + (size_t)s * 128;
+      ntl = sm[96];
+      td = lane < ntl ? sm[32 + lane] : -1;
+      ts = lane < ntl ? sm[64 + lane] : 0;
+    };
+    int bcur = first_block(0);
+    load_fwd(0, bcur);
+    load_tail(0);
+    for (int s = 0; s < nk; ++s) {
+      const int k0 = s * nb, wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
+      const int bl = (k0 + H - 1) >> 5;
+      const float* y = ring[s % DF_S];
+      bool bad = !df_wait_slot(&full[s % DF_S], (unsigned)(s / DF_S) & 1u);
+      for (int b = bcur; !bad && b >= 0 && b <= bl; b += DF_UW * DF_C) {
+        if (b != bcur) load_fwd(s, b);  // a window wider than DF_UW x DF_C blocks
+        const int R = 32 * b + lane;
+        // the source of row R under the step's interchanges (a head position, or R)
+        int src = R;
+        for (unsigned m = __ballot_sync(0xffffffffu, lane < ntl && (td >> 5) == b); m; m &= m - 1) {
+          const int q = __ffs(m) - 1;
+          const int d = __shfl_sync(0xffffffffu, td, q), sv = __shfl_sync(0xffffffffu, ts, q);
+          if (d == R) src = sv;
+        }
+        if (R - k0 < H) {
+          float v0, v1;
+          const int par = s & 1;
+          if (src == R) {
+            v0 = *aloc(par, 0, R);
+            v1 = *aloc(par, 1, R);
+          } else {
+            // a head value: its owner has written it in step s - 1
+            if (s >= 1 && !df_wait_count(df_mapa(&done, owner(src)), (unsigned)s)) bad = true;
+            v0 = df_ld_remote(df_mapa(aloc(par, 0, src), owner(src)));
+            v1 = df_ld_remote(df_mapa(aloc(par, 1, src), owner(src)));
+          }
+          float acc0 = 0.0f, acc1 = 0.0f;
+          df_dot2(lr, y, acc0, acc1);
+          *aloc(par ^ 1, 0, R) = v0 - acc0;
+          *aloc(par ^ 1, 1, R) = v1 - acc1;
+        }
+      }
+      if (df_update_bar_any(bad)) {
+        if (tid == 32) fail();
+        break;
+      }
+      if (tid == 32) df_st_release(df_mapa(&done, rank), (unsigned)(s + 1));
+      if (s + 1 < nk) {
+        bcur = first_block(s + 1);
+        load_fwd(s + 1, bcur);
+        load_tail(s + 1);
+      }
+    }
+  }
+  // ---- backward: U x = y, steps t = nk + it for panel k = nk - 1 - it ----
+  sc_cluster_sync();
+  if (abort_all) {
+    sc_cluster_sync();
+    return;
+  }
+  fill(w.q, w.q + N);
+  __syncthreads();
+  if (warp == 0) {
+    const int klast = nk - 1;
+    for (int k = klast - ((klast - (int)rank) % DF_C + DF_C) % DF_C; k >= 0; k -= DF_C) {
+      const int it = klast - k, t = nk + it;
+      const int k0 = k * nb, wd = s2::panel_width(g, nb, k0);
+      const int R = k0 + lane;
+      float invr[32], ur[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) invr[jj] = __ldg(w.inv + (size_t)k * 2048 + 1024 + lane * 32 + jj);
+      // row R after step it - 1: less U(R, columns of panel k + 1) times x_{k+1}
+      const int kn0 = k0 + nb, wdn = k + 1 < nk ? s2::panel_width(g, nb, kn0) : 0;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) ur[jj] = (lane < wd && jj < wdn) ? s2::umul(g, w.AB, R, kn0 + jj) : 0.0f;
+      bool ok = true;
+      if (it >= 2) ok = df_wait_count(df_mapa(&done, rank), (unsigned)(t - 1));
+      float a0 = 0.0f, a1 = 0.0f;
+      if (lane < wd) {
+        a0 = *aloc((it + 1) & 1, 0, R);
+        a1 = *aloc((it + 1) & 1, 1, R);
+      }
+      if (it > 0 && ok) {
+        ok = df_wait_slot(&full[(t - 1) % DF_S], (unsigned)((t - 1) / DF_S) & 1u);
+        if (ok && lane < wd) {
+          float acc0 = 0.0f, acc1 = 0.0f;
+          df_dot2(ur, ring[(t - 1) % DF_S], acc0, acc1);
+          a0 -= acc0;
+          a1 -= acc1;
+        }
+      }
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) fail();
+        break;
+      }
+      float x0 = 0.0f, x1 = 0.0f;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const float y0j = __shfl_sync(0xffffffffu, a0, jj), y1j = __shfl_sync(0xffffffffu, a1, jj);
+        x0 += invr[jj] * y0j;
+        x1 += invr[jj] * y1j;
+      }
+      if (lane >= wd) x0 = x1 = 0.0f;
+      stage[lane] = x0;
+      stage[32 + lane] = x1;
+      if (lane < wd) {
+        o0[R] = x0;
+        o1[R] = x1;
+      }
+      if (!send(t)) {
+        if (lane == 0) fail();
+        break;
+      }
+    }
+  } else {
+    const int u = warp - 1;
+    float ur[32];
+    // rows lo .. k0 - 1 of backward step it (panel k = nk - 1 - it): this warp's first block, or -1
+    auto first_block = [&](int it) -> int {
+      const int k = nk - 1 - it, k0 = k * nb;
+      const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
+      const int bf = lo >> 5, bl = k - 1;
+      const int b = bf + (((int)rank - bf) % DF_C + DF_C) % DF_C + u * DF_C;
+      return b <= bl ? b : -1;
+    };
+    auto load_bwd = [&](int it, int b) {
+      const int k = nk - 1 - it, k0 = k * nb, wd = s2::panel_width(g, nb, k0);
+      const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
+      const int R = 32 * b + lane;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) ur[jj] = (b >= 0 && R >= lo && jj < wd) ? s2::umul(g, w.AB, R, k0 + jj) : 0.0f;
+    };
+    int bcur = first_block(0);
+    load_bwd(0, bcur);
+    for (int it = 0; it < nk; ++it) {
+      const int t = nk + it, k = nk - 1 - it, k0 = k * nb;
+      const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
+      const float* x = ring[t % DF_S];
+      bool bad = !df_wait_slot(&full[t % DF_S], (unsigned)(t / DF_S) & 1u);
+      for (int b = bcur; !bad && b >= 0 && b <= k - 1; b += DF_UW * DF_C) {
+        if (b != bcur) load_bwd(it, b);
+        const int R = 32 * b + lane;
+        if (R >= lo) {
+          const int par = it & 1;
+          float acc0 = 0.0f, acc1 = 0.0f;
+          df_dot2(ur, x, acc0, acc1);
+          const float v0 = *aloc(par, 0, R), v1 = *aloc(par, 1, R);
+          *aloc(par ^ 1, 0, R) = v0 - acc0;
+          *aloc(par ^ 1, 1, R) = v1 - acc1;
+        }
+      }
+      if (df_update_bar_any(bad)) {
+        if (tid == 32) fail();
+        break;
+      }
+      if (tid == 32) df_st_release(df_mapa(&done, rank), (unsigned)(t + 1));
+      if (it + 1 < nk) {
+        bcur = first_block(it + 1);
+        load_bwd(it + 1, bcur);
+      }
+    }
+  }
+  sc_cluster_sync();
+}
+
+
 // right-hand sides of a Newton step: -R and e_r (the total-mass row)
 __global__ void k_s2_prep(const s2::Grid g, S2Work w) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1049,6 +1735,43 @@ void s2_smem_limits(size_t panel, size_t trail, size_t subst) {
 // the device can run one, else on one CTA (k_s2_subst).
 cudaError_t s2_subst(const s2::Grid& g, const S2Work& w, double* b0, double* b1, double* o0, double* o1,
                      size_t sm_subst, cudaStream_t st) {
+  // the data-flow form where its rows fit the cluster's shared memory
+  static int df_ok = -1;  // per process: 1 when a DF_C-CTA cluster of k_s2_subst_df fits
+  static size_t df_set = 0;
+  const size_t nk = (size_t)(g.N + 31) / 32;
+  const size_t sm_df = sizeof(float) * 4 * 32 * ((nk + DF_C - 1) / DF_C);
+  if (w.nb == 32 && sm_df <= S2_DF_SMEM_CAP) {
+    if (df_set < sm_df) {
+      if (cudaFuncSetAttribute(k_s2_subst_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S2_DF_SMEM_CAP) ==
+          cudaSuccess)
+        df_set = S2_DF_SMEM_CAP;
+      cudaGetLastError();
+    }
+    cudaLaunchConfig_t dc = {};
+    cudaLaunchAttribute da[1];
+    da[0].id = cudaLaunchAttributeClusterDimension;
+    da[0].val.clusterDim.x = DF_C;
+    da[0].val.clusterDim.y = 1;
+    da[0].val.clusterDim.z = 1;
+    dc.gridDim = dim3(DF_C);
+    dc.blockDim = dim3(DF_NT);
+    dc.dynamicSmemBytes = S2_DF_SMEM_CAP;
+    dc.stream = st;
+    dc.attrs = da;
+    dc.numAttrs = 1;
+    if (df_ok < 0) {
+      int n = 0;
+      df_ok = (df_set >= S2_DF_SMEM_CAP && cudaOccupancyMaxActiveClusters(&n, k_s2_subst_df, &dc) == cudaSuccess &&
+               n >= 1)
+                  ? 1
+                  : 0;
+      cudaGetLastError();
+    }
+    if (df_ok) {
+      dc.dynamicSmemBytes = sm_df;
+      return cudaLaunchKernelEx(&dc, k_s2_subst_df, g, w, (const double*)b0, (const double*)b1, o0, o1);
+    }
+  }
   static int cluster_ok = -1;  // per process: 1 when an SC_CL-CTA cluster of k_s2_subst_cl fits
   const size_t sm_cl = sizeof(int) * 2 * ((size_t)g.kl + w.nb);
   cudaLaunchConfig_t cfg = {};
@@ -1123,11 +1846,20 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
     if (refactor) {
       for (int k0 = 0; k0 < g.N; k0 += nb) {
         const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
-        k_s2_panel<<<1, S2_PNL_NT, sizeof(float) * (size_t)wd * H, st>>>(g, w, k0);
+        if (nb == 32 && H <= S2_PNL_NT)
+          k_s2_panel_rg<1><<<1, S2_PNL_NT, 0, st>>>(g, w, k0);
+        else if (nb == 32 && H <= 2 * S2_PNL_NT)
+          k_s2_panel_rg<2><<<1, S2_PNL_NT, 0, st>>>(g, w, k0);
+        else if (nb == 32 && H <= 3 * S2_PNL_NT)
+          k_s2_panel_rg<3><<<1, S2_PNL_NT, 0, st>>>(g, w, k0);
+        else
+          k_s2_panel<<<1, S2_PNL_NT, sizeof(float) * (size_t)wd * H, st>>>(g, w, k0);
         const int ntrail = s2::trail_last(g, k0, wd) - (k0 + wd) + 1;
         if (ntrail > 0)
           k_s2_trail<<<(ntrail + cbt - 1) / cbt, S2_NT, sizeof(float) * (size_t)cbt * H, st>>>(g, w, k0, cbt);
       }
+      const int nk = (g.N + nb - 1) / nb;
+      k_s2_sprep<<<(nk + SP_WPB - 1) / SP_WPB, SP_WPB * 32, 0, st>>>(g, w);
     }
     const int nsweep = refactor ? S2_NREF : S2_NREF_REUSE;
     k_s2_prep<<<vec_grid, nt, 0, st>>>(g, w);
@@ -1139,10 +1871,11 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
     }
     if (le != cudaSuccess) return (int)le;
     k_s2_newton<<<1, S2_UPD_NT, 0, st>>>(g, w, n_m, tol);
-    cudaMemcpyAsync(sc, w.sc, sizeof(double) * (S2_LAM + 1), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(sc, w.sc, sizeof(double) * (S2_TOUT + 1), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
+    if (sc[S2_TOUT] != 0.0) return S2_TIMEOUT_RC;
     if (sc[S2_DONE] != 0.0) break;
     refactor = it > 0 && !(sc[S2_DMAX] <= 0.5 * dm_prev);
     dm_prev = sc[S2_DMAX];
@@ -1150,7 +1883,7 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
   k_s2_mass<<<1, S2_NT, 0, st>>>(g, w);
   k_s2_res<<<cell_grid, nt, 0, st>>>(g, w);
   k_s2_final<<<1, S2_NT, 0, st>>>(g, w, out, info);
-  cudaMemcpyAsync(sc, w.sc, sizeof(double) * (S2_LAM + 1), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(sc, w.sc, sizeof(double) * (S2_TOUT + 1), cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
