@@ -22,7 +22,6 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <type_traits>
-#include <utility>
 
 #include "dsmc_internal.h"
 #include "dsmc_synth2d.cuh"
@@ -349,149 +348,195 @@ __global__ void __launch_bounds__(S2_PNL_NT) k_s2_panel(const s2::Grid g, S2Work
   s2::panel_store(g, w.nb, w.AB, w.Lp, w.ud, k0, wd, H, P, tid, S2_PNL_NT);
 }
 
-// f(integral_constant<int, J>) for J = 0, 1, ... in order
-template <typename F, int... J>
-__device__ __forceinline__ void s2_static_for(F& f, std::integer_sequence<int, J...>) {
-  (f(std::integral_constant<int, J>{}), ...);
+// (largest candidate, its position) over the CTA's nw warps: a candidate's
+// key is 1 + the bits of its magnitude (0: no candidate; magnitudes that are
+// not numbers never win), ties go to the lowest position; no candidate gives
+// `fallback` with magnitude -1 (the choice of s2_block_argmax)
+__device__ __forceinline__ int s2_argmax_key(unsigned key, int pos, unsigned (*ck)[32], int (*cp)[32], int buf,
+                                             int fallback, float& best_out, int nw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned kw = __reduce_max_sync(0xffffffffu, key);
+  const int pw = __reduce_min_sync(0xffffffffu, key == kw ? pos : INT_MAX);
+  if (lane == 0) {
+    ck[buf][warp] = kw;
+    cp[buf][warp] = pw;
+  }
+  __syncthreads();
+  const unsigned k2 = lane < nw ? ck[buf][lane] : 0u;
+  const int p2 = lane < nw ? cp[buf][lane] : INT_MAX;
+  const unsigned km = __reduce_max_sync(0xffffffffu, k2);
+  const int pm = __reduce_min_sync(0xffffffffu, k2 == km ? p2 : INT_MAX);
+  best_out = km == 0u ? -1.0f : __uint_as_float(km - 1u);
+  return km == 0u ? fallback : pm;
 }
 
-// The same factorisation with the panel in registers: thread t holds rows
-// r = t + s S2_PNL_NT (s < RPT) of all 32 columns.  Per step the pivot row
-// passes through shared memory once (and the displaced row j, when the
-// interchange moves it), instead of every rank-one update reading and
-// writing the panel there.  The operations on each entry, their order and
-// the choice of pivots are those of k_s2_panel, so the factors are the same.
+__device__ __forceinline__ unsigned s2_cand_key(float v, bool cand) {
+  const float a = fabsf(v);
+  return (cand && a == a) ? __float_as_uint(a) + 1u : 0u;
+}
+
+// The panel factorisation with the rows in registers.  Thread t holds the
+// rows loaded from positions t + s T (s < RPT, T threads), each as 32
+// columns of a frame that starts at column 4 g in steps 4 g .. 4 g + 3 (the
+// frame shifts by four columns every four steps, so one loop body of four
+// unrolled steps serves the panel; columns past the panel's width are
+// skipped eight at a time).  Interchanges move no row: each row carries its
+// current position, and pos_owner maps a position to the row (by load index)
+// that holds it; the pivot row goes to shared memory for the rank-one
+// update, its U entries to global memory, and each row's multipliers to
+// shared memory (Ls, by load index) until the end, when they are stored at
+// the rows' final positions.  The operations on each entry, their order and
+// the choice of pivots are those of k_s2_panel.
 template <int RPT>
-__global__ void __launch_bounds__(S2_PNL_NT, 1) k_s2_panel_rg(const s2::Grid g, S2Work w, int k0) {
-  __shared__ float cbest[2][S2_PNL_NT / 32];
-  __shared__ int cidx[2][S2_PNL_NT / 32];
-  __shared__ float prow[32], jrow[32];
+__global__ void __launch_bounds__(512) k_s2_panel_rot(const s2::Grid g, S2Work w, int k0) {
+  __shared__ unsigned ckey[2][32];
+  __shared__ int cpos[2][32];
+  __shared__ float prow[32];
+  const int T = blockDim.x, NS = T * RPT, nw = T >> 5;
   const int tid = threadIdx.x;
   const int wd = s2::panel_width(g, w.nb, k0), H = s2::panel_height(g, wd, k0);
+  float* Ls = reinterpret_cast<float*>(s2_smem);                  // [32][NS]
+  int* pos_owner = reinterpret_cast<int*>(Ls + (size_t)32 * NS);  // [H]
   float a[RPT][32];
+  int pos[RPT];
+  bool act[RPT];
 #pragma unroll
   for (int s = 0; s < RPT; ++s) {
-    const int r = tid + s * S2_PNL_NT;
+    const int r = tid + s * T;
+    pos[s] = r;
+    act[s] = r < H;
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
       const bool in = r < H && c < wd && s2::in_band(g, k0 + r, k0 + c);
       a[s][c] = in ? w.AB[s2::band_at(g, k0 + r, k0 + c)] : 0.0f;
     }
   }
-  float best = -1.0f, pbest = -1.0f;
-  int bi = INT_MAX;
-  {
-    const int rm0 = s2::panel_rmax(g, H, 0);
+  for (int r = tid; r < H; r += T) pos_owner[r] = r;
+  // this thread's best candidate of frame column fc for positions lo .. hi
+  auto cand = [&](auto fct, int lo, int hi, unsigned& key, int& bp) {
+    constexpr int fc = decltype(fct)::value;
+    key = 0u;
+    bp = INT_MAX;
 #pragma unroll
     for (int s = 0; s < RPT; ++s) {
-      const int r = tid + s * S2_PNL_NT;
-      const float v = fabsf(a[s][0]);
-      if (r <= rm0 && v > best) {
-        best = v;
-        bi = r;
+      const unsigned kq = s2_cand_key(a[s][fc], act[s] && pos[s] >= lo && pos[s] <= hi);
+      if (kq > key || (kq == key && kq != 0u && pos[s] < bp)) {
+        key = kq;
+        bp = pos[s];
       }
     }
+  };
+  float pbest = -1.0f;
+  int p;
+  {
+    unsigned key;
+    int bp;
+    cand(std::integral_constant<int, 0>{}, 0, s2::panel_rmax(g, H, 0), key, bp);
+    p = s2_argmax_key(key, bp, ckey, cpos, 0, 0, pbest, nw);
   }
-  int p = s2_block_argmax(best, bi, cbest, cidx, 0, 0, pbest);
-  // step j of the elimination, j a compile-time constant so that the rows
-  // stay in registers
-  auto step = [&](auto jt) {
-    constexpr int j = decltype(jt)::value;
-    if (j < wd) {
+  const int ld = g.ld;
+#pragma unroll 1
+  for (int jb = 0; jb < wd; jb += 4) {
+    const int live = wd - jb;  // frame columns inside the panel
+    // step j = jb + jj, its pivot column at frame column jj
+    auto step = [&](auto jjt) {
+      constexpr int jj = decltype(jjt)::value;
+      const int j = jb + jj;
+      if (j >= wd) return;
+      const int idp = pos_owner[p], idj = pos_owner[j];
       if (tid == 0) {
         w.piv[k0 + j] = k0 + p;
         if (!(pbest > 0.0f)) w.sc[S2_SING] = 1.0;
       }
-      const int pt = p % S2_PNL_NT, ps = p / S2_PNL_NT;
-      // the pivot row to prow (and row j to jrow when they trade places)
-      if (tid == pt) {
+      if (tid == idp % T) {
+        const int sp = idp / T;
+#pragma unroll
+        for (int c = jj; c < 32; ++c) {
+          float v = a[0][c];
+#pragma unroll
+          for (int s = 1; s < RPT; ++s)
+            if (s == sp) v = a[s][c];
+          prow[c] = v;
+        }
 #pragma unroll
         for (int s = 0; s < RPT; ++s)
-          if (s == ps) {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) prow[c] = a[s][c];
+          if (s == sp) {
+            act[s] = false;
+            pos[s] = j;
           }
       }
-      if (p != j && tid == j) {
+      if (p != j && tid == idj % T) {
+        const int sj = idj / T;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) jrow[c] = a[0][c];
+        for (int s = 0; s < RPT; ++s)
+          if (s == sj) pos[s] = p;
       }
       __syncthreads();
-      if (p != j) {
-        if (tid == pt) {
-#pragma unroll
-          for (int s = 0; s < RPT; ++s)
-            if (s == ps) {
-#pragma unroll
-              for (int c = 0; c < 32; ++c) a[s][c] = jrow[c];
-            }
-        }
-        if (tid == j) {
-#pragma unroll
-          for (int c = 0; c < 32; ++c) a[0][c] = prow[c];
-        }
+      if (tid == 0 && p != j) {
+        pos_owner[j] = idp;
+        pos_owner[p] = idj;
       }
-      const float piv = prow[j];
+      // U(j, j + c) of the pivot row
+      if (tid < wd - j) {
+        const float v = prow[jj + tid];
+        w.AB[(size_t)(k0 + j + tid) * ld + (size_t)(g.kl + g.ku - tid)] = v;
+        if (tid == 0) w.ud[k0 + j] = v;
+      }
+      const float piv = prow[jj];
       const int rm = s2::panel_rmax(g, H, j);
       float l[RPT];
       bool upd[RPT];
 #pragma unroll
       for (int s = 0; s < RPT; ++s) {
-        const int r = tid + s * S2_PNL_NT;
-        upd[s] = r > j && r <= rm;
-        l[s] = piv != 0.0f ? a[s][j] / piv : 0.0f;
-        if (upd[s]) a[s][j] = l[s];
+        upd[s] = act[s] && pos[s] <= rm;
+        l[s] = piv != 0.0f ? a[s][jj] / piv : 0.0f;
+        if (act[s]) Ls[(size_t)j * NS + tid + s * T] = upd[s] ? l[s] : a[s][jj];
       }
 #pragma unroll
-      for (int c = j + 1; c < 32; ++c) {
-        if (c < wd) {
-          const float pc = prow[c];
+      for (int q = 0; q < 4; ++q) {
+        if (8 * q + 7 > jj && 8 * q < live) {
 #pragma unroll
-          for (int s = 0; s < RPT; ++s)
-            if (upd[s]) a[s][c] -= l[s] * pc;
+          for (int c = (8 * q > jj ? 8 * q : jj + 1); c < 8 * q + 8; ++c) {
+            const float pc = prow[c];
+#pragma unroll
+            for (int s = 0; s < RPT; ++s)
+              if (upd[s]) a[s][c] -= l[s] * pc;
+          }
         }
       }
       if (j + 1 < wd) {
-        const int rm1 = s2::panel_rmax(g, H, j + 1);
-        best = -1.0f;
-        bi = INT_MAX;
+        unsigned key;
+        int bp;
+        cand(std::integral_constant<int, jj + 1>{}, j + 1, s2::panel_rmax(g, H, j + 1), key, bp);
+        p = s2_argmax_key(key, bp, ckey, cpos, (j + 1) & 1, j + 1, pbest, nw);
+      }
+    };
+    step(std::integral_constant<int, 0>{});
+    step(std::integral_constant<int, 1>{});
+    step(std::integral_constant<int, 2>{});
+    step(std::integral_constant<int, 3>{});
+    // the next frame: columns jb + 4 .. (those inside the panel)
 #pragma unroll
-        for (int s = 0; s < RPT; ++s) {
-          const int r = tid + s * S2_PNL_NT;
-          const float v = fabsf(a[s][(j + 1) & 31]);
-          if (r > j && r <= rm1 && v > best) {
-            best = v;
-            bi = r;
-          }
+    for (int q = 0; q < 4; ++q) {
+      if (8 * q + 4 < live) {
+#pragma unroll
+        for (int c = 8 * q; c < 8 * q + 8 && c + 4 < 32; ++c) {
+#pragma unroll
+          for (int s = 0; s < RPT; ++s) a[s][c] = a[s][c + 4];
         }
-        p = s2_block_argmax(best, bi, cbest, cidx, (j + 1) & 1, j + 1, pbest);
       }
     }
-  };
-  s2_static_for(step, std::make_integer_sequence<int, 32>{});
-  // U (rows above and on the diagonal), its diagonal and the multipliers: the
-  // stores of s2::panel_store
+  }
+  __syncthreads();
+  // multipliers at the rows' final positions (zero rows past the band included)
   const size_t base = s2::lp_base(g, w.nb, k0);
   const int ldp = g.kl + w.nb;
 #pragma unroll
   for (int s = 0; s < RPT; ++s) {
-    const int r = tid + s * S2_PNL_NT;
-    if (r < H) {
-#pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        if (c < wd) {
-          const int k = k0 + c;
-          const float v = a[s][c];
-          if (r < c) {
-            w.AB[s2::band_at(g, k0 + r, k)] = v;
-          } else if (r == c) {
-            w.ud[k] = v;
-            w.AB[s2::band_at(g, k, k)] = v;
-          } else {
-            w.Lp[base + (size_t)c * ldp + r] = v;
-          }
-        }
-      }
+    const int id = tid + s * T;
+    if (id < H) {
+      const int ps = pos[s], cend = ps < wd ? ps : wd;
+      for (int c = 0; c < cend; ++c) w.Lp[base + (size_t)c * ldp + ps] = Ls[(size_t)c * NS + id];
     }
   }
 }
@@ -1137,11 +1182,13 @@ __global__ void __launch_bounds__(SP_WPB * 32) k_s2_sprep(const s2::Grid g, S2Wo
 // itself, from the other copy and the previous step's result (the previous
 // panel's multipliers for the head's source rows), applies the inverse of
 // the panel's triangle and sends the 32 results (two right-hand sides) into
-// a ring of DF_S slots in every CTA, each slot completed on an mbarrier.
-// Warps 1 .. DF_UW of every CTA take each step's result from the ring and
-// update their CTA's rows of the step's window, then publish the number of
-// steps done (release); a reader of another CTA's rows first waits (acquire)
-// until that count covers the step the values come from.  Each wait gives
+// a ring of DF_S slots in every CTA, each slot completed on an mbarrier;
+// with them go the head values that the panel's interchanges move to rows
+// below the head, computed the same way.  Warps 1 .. DF_UW of every CTA take
+// each step's result from the ring and update their CTA's rows of the step's
+// window, then publish the number of steps done (release).  Warp 0 reads
+// other CTAs' rows only after waiting (acquire) until that count covers the
+// step the values come from, one step ahead of their use.  Each wait gives
 // up after DF_WAIT_NS (the kernel then records the timeout in the work area
 // and every CTA leaves at the next cluster barrier).
 //
@@ -1150,8 +1197,9 @@ __global__ void __launch_bounds__(SP_WPB * 32) k_s2_sprep(const s2::Grid g, S2Wo
 // ---------------------------------------------------------------------------
 constexpr int DF_C = 8;                  // CTAs of the cluster
 constexpr int DF_UW = 8;                 // update warps per CTA
-constexpr int DF_NT = 32 * (1 + DF_UW);  // warp 0 solves the heads
+constexpr int DF_NT = 32 * (2 + DF_UW);  // warp 0 solves the heads, warp DF_UW + 1 publishes
 constexpr int DF_S = 32;                 // ring slots (steps in flight)
+constexpr int DF_SEND_LANES = 32 / DF_C;  // lanes of warp 0 that write one CTA's ring slot
 constexpr unsigned long long DF_WAIT_NS = 500000000ull;  // 0.5 s
 
 __device__ __forceinline__ unsigned long long df_clock_ns() {
@@ -1222,17 +1270,22 @@ __device__ __forceinline__ bool df_wait_slot(const uint64_t* bar, unsigned parit
 
 // until the step count at `addr` (any CTA of the cluster) reaches `need`;
 // false after DF_WAIT_NS
-__device__ __forceinline__ bool df_wait_count(unsigned addr, unsigned need) {
-  if (df_ld_acquire(addr) >= need) return true;
-  const unsigned long long t0 = df_clock_ns();
-  for (;;) {
-    for (int q = 0; q < 64; ++q)
-      if (df_ld_acquire(addr) >= need) return true;
-    if (df_clock_ns() - t0 > DF_WAIT_NS) return false;
+__device__ __forceinline__ bool df_wait_count(unsigned addr, unsigned need, unsigned* seen = nullptr) {
+  unsigned v = df_ld_acquire(addr);
+  if (v < need) {
+    const unsigned long long t0 = df_clock_ns();
+    for (;;) {
+      for (int q = 0; q < 64 && v < need; ++q) v = df_ld_acquire(addr);
+      if (v >= need) break;
+      if (df_clock_ns() - t0 > DF_WAIT_NS) return false;
+    }
   }
+  if (seen) *seen = v;
+  return true;
 }
 
-// barrier 1 for the update warps, returning whether any of them has `bad` set
+// barrier 1 for the update warps and the publishing warp, returning whether
+// any of them has `bad` set
 __device__ __forceinline__ bool df_update_bar_any(bool bad) {
   unsigned r;
   asm volatile(
@@ -1241,24 +1294,35 @@ __device__ __forceinline__ bool df_update_bar_any(bool bad) {
       "barrier.cta.red.or.pred q, 1, %2, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
-      : "r"((unsigned)bad), "r"(32 * DF_UW)
+      : "r"((unsigned)bad), "r"(32 * (DF_UW + 1))
       : "memory");
   return r != 0;
 }
 
 // acc0 += l . y[0:32], acc1 += l . y[32:64] (the order of k_s2_subst_cl)
 __device__ __forceinline__ void df_dot2(const float (&l)[32], const float* y, float& acc0, float& acc1) {
+  const float4* y4 = reinterpret_cast<const float4*>(y);  // a 256-byte ring slot
 #pragma unroll
-  for (int jj = 0; jj < 32; ++jj) {
-    acc0 += l[jj] * y[jj];
-    acc1 += l[jj] * y[32 + jj];
+  for (int q = 0; q < 8; ++q) {
+    const float4 a = y4[q], b = y4[8 + q];
+    acc0 += l[4 * q] * a.x;
+    acc1 += l[4 * q] * b.x;
+    acc0 += l[4 * q + 1] * a.y;
+    acc1 += l[4 * q + 1] * b.y;
+    acc0 += l[4 * q + 2] * a.z;
+    acc1 += l[4 * q + 2] * b.z;
+    acc0 += l[4 * q + 3] * a.w;
+    acc1 += l[4 * q + 3] * b.w;
   }
 }
 
 __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Work w, const double* b0,
                                                          const double* b1, double* o0, double* o1) {
-  __shared__ __align__(16) float ring[DF_S][64];  // step results: rhs 0 in [0, 32), rhs 1 in [32, 64)
-  __shared__ __align__(16) float stage[64];       // warp 0's result before it is sent
+  // step results: rhs 0 in [0, 32), rhs 1 in [32, 64); forward steps also the
+  // values the step's interchanges move below the head (list entry q: rhs 0 at
+  // 64 + q, rhs 1 at 96 + q)
+  __shared__ __align__(16) float ring[DF_S][128];
+  __shared__ __align__(16) float stage[128];  // warp 0's result before it is sent
   __shared__ __align__(8) uint64_t full[DF_S];
   __shared__ unsigned done;       // steps this CTA's update warps have finished
   __shared__ unsigned abort_all;  // set in every CTA once a wait gave up
@@ -1293,28 +1357,29 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     done = 0;
     abort_all = 0;
   }
-  if (tid < DF_S) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(df_smem_addr(&full[tid])) : "memory");
+  if (tid < DF_S)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(df_smem_addr(&full[tid])), "r"(DF_SEND_LANES)
+                 : "memory");
   fill(b0, b1);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   sc_cluster_sync();
-  unsigned known = 0;  // warp 0, lane c < DF_C: steps CTA c is known to have finished
-  // warp 0: send this step's 32 results (stage) to every CTA's ring slot t % DF_S, once the
-  // CTA has finished step t - DF_S (the slot's previous use)
-  auto send = [&](int t) -> bool {
+  unsigned known = 0;  // warp 0: steps CTA lane % DF_C is known to have finished
+  // warp 0: send the first nf floats of this step's result (stage) to every
+  // CTA's ring slot t % DF_S, once the CTA has finished step t - DF_S (the
+  // slot's previous use).  Lane l writes part l / DF_C of the floats to CTA
+  // l % DF_C and arrives on its slot's mbarrier (DF_SEND_LANES arrivals).
+  auto send = [&](int t, int nf) -> bool {
     __syncwarp();
+    const unsigned c = (unsigned)(lane % DF_C);
+    const unsigned need = t >= DF_S ? (unsigned)(t - DF_S + 1) : 0u;
     bool ok = true;
-    if (lane < DF_C) {
-      const unsigned need = t >= DF_S ? (unsigned)(t - DF_S + 1) : 0u;
-      if (known < need) {
-        ok = df_wait_count(df_mapa(&done, lane), need);
-        if (ok) known = need;
-      }
-      if (ok) {
-        const unsigned dst = df_mapa(&ring[t % DF_S][0], lane);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) df_st_remote4(dst + 16 * q, reinterpret_cast<const float4*>(stage)[q]);
-        df_arrive_remote(df_mapa(&full[t % DF_S], lane));
-      }
+    if (known < need) ok = df_wait_count(df_mapa(&done, c), need, &known);
+    if (ok) {
+      const int part = lane / DF_C, n4 = nf / (4 * DF_SEND_LANES);
+      const unsigned dst = df_mapa(&ring[t % DF_S][0], c) + 16u * (unsigned)(part * n4);
+      const float4* src = reinterpret_cast<const float4*>(stage) + part * n4;
+      for (int q = 0; q < n4; ++q) df_st_remote4(dst + 16 * q, src[q]);
+      df_arrive_remote(df_mapa(&full[t % DF_S], c));
     }
     return __all_sync(0xffffffffu, ok);
   };
@@ -1323,51 +1388,78 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     for (int k = (int)rank; k < nk; k += DF_C) {
       const int k0 = k * nb, wd = s2::panel_width(g, nb, k0);
       const int32_t* sm = w.smap + (size_t)k * 128;
-      const int hs = sm[lane];  // the row whose value ends at head position k0 + lane
+      // lane i follows two rows to their values after step k - 1: hs, whose
+      // value ends at head position k0 + i, and (i < ntail) tp, the head
+      // position whose value the interchanges move to the i-th row of the
+      // list past the head
+      const int hs = sm[lane];
+      const int ntail = sm[96];
+      const int tp = lane < ntail ? sm[64 + lane] : -1;
       float invr[32];
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) invr[jj] = __ldg(w.inv + (size_t)k * 2048 + lane * 32 + jj);
-      // hs after step k - 1: its source under panel k - 1's interchanges, less
-      // that panel's multipliers (row hs - (k0 - 32) of its window) times y_{k-1}
-      int src = hs;
-      bool inwin = false;
-      float lr[32];
+      // a row's value after step k - 1: its source under panel k - 1's
+      // interchanges, less that panel's multipliers (the row's place in its
+      // window) times y_{k-1}
+      int hsrc = hs, tsrc = tp;
+      bool hin = false, tin = false;
+      float lh[32], lt[32];
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) lr[jj] = 0.0f;
+      for (int jj = 0; jj < 32; ++jj) lh[jj] = lt[jj] = 0.0f;
       if (k > 0) {
         const int p0 = k0 - nb, Hp = s2::panel_height(g, nb, p0);
-        const int r = hs - p0;
-        inwin = lane < wd && r < Hp;
         const float* Lk = w.Lp + s2::lp_base(g, nb, p0);
-        if (inwin) {
+        hin = lane < wd && hs - p0 < Hp;
+        tin = tp >= 0;  // a head position of panel k: inside panel k - 1's window
+        if (hin) {
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) lr[jj] = __ldg(Lk + (size_t)jj * ldp + r);
+          for (int jj = 0; jj < 32; ++jj) lh[jj] = __ldg(Lk + (size_t)jj * ldp + (hs - p0));
+        }
+        if (tin) {
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) lt[jj] = __ldg(Lk + (size_t)jj * ldp + (tp - p0));
         }
         const int32_t* smp = sm - 128;
         const int ntp = smp[96];
         const int td = lane < ntp ? smp[32 + lane] : -1, ts = lane < ntp ? smp[64 + lane] : 0;
         for (int q = 0; q < ntp; ++q) {
           const int d = __shfl_sync(0xffffffffu, td, q), sv = __shfl_sync(0xffffffffu, ts, q);
-          if (d == hs) src = sv;
+          if (d == hs) hsrc = sv;
+          if (d == tp) tsrc = sv;
         }
       }
-      // the value after step k - 2 (copy (k - 1) % 2) once src's owner has finished it
+      // the values after step k - 2 (copy (k - 1) % 2) once their owners have finished it
       bool ok = true;
-      if (k >= 2 && lane < wd) ok = df_wait_count(df_mapa(&done, owner(src)), (unsigned)(k - 1));
-      float a0 = 0.0f, a1 = 0.0f;
+      const unsigned need = k >= 2 ? (unsigned)(k - 1) : 0u;
+      if (lane < wd && need) ok = df_wait_count(df_mapa(&done, owner(hsrc)), need);
+      if (ok && tp >= 0 && need) ok = df_wait_count(df_mapa(&done, owner(tsrc)), need);
+      const int par = (k + 1) & 1;
+      float a0 = 0.0f, a1 = 0.0f, c0 = 0.0f, c1 = 0.0f;
       if (ok && lane < wd) {
-        const int par = (k + 1) & 1;
-        a0 = df_ld_remote(df_mapa(aloc(par, 0, src), owner(src)));
-        a1 = df_ld_remote(df_mapa(aloc(par, 1, src), owner(src)));
+        a0 = df_ld_remote(df_mapa(aloc(par, 0, hsrc), owner(hsrc)));
+        a1 = df_ld_remote(df_mapa(aloc(par, 1, hsrc), owner(hsrc)));
+      }
+      if (ok && tp >= 0) {
+        c0 = df_ld_remote(df_mapa(aloc(par, 0, tsrc), owner(tsrc)));
+        c1 = df_ld_remote(df_mapa(aloc(par, 1, tsrc), owner(tsrc)));
       }
       if (k > 0 && ok) {
         const int t = k - 1;
         ok = df_wait_slot(&full[t % DF_S], (unsigned)(t / DF_S) & 1u);
-        if (ok && inwin) {
-          float acc0 = 0.0f, acc1 = 0.0f;
-          df_dot2(lr, ring[t % DF_S], acc0, acc1);
-          a0 -= acc0;
-          a1 -= acc1;
+        if (ok) {
+          const float* yp = ring[t % DF_S];
+          if (hin) {
+            float acc0 = 0.0f, acc1 = 0.0f;
+            df_dot2(lh, yp, acc0, acc1);
+            a0 -= acc0;
+            a1 -= acc1;
+          }
+          if (tin) {
+            float acc0 = 0.0f, acc1 = 0.0f;
+            df_dot2(lt, yp, acc0, acc1);
+            c0 -= acc0;
+            c1 -= acc1;
+          }
         }
       }
       if (!__all_sync(0xffffffffu, ok)) {
@@ -1384,21 +1476,31 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       if (lane >= wd) y0 = y1 = 0.0f;
       stage[lane] = y0;
       stage[32 + lane] = y1;
-      if (lane < wd) {
-        w.q[k0 + lane] = y0;  // the forward result, right-hand side of the backward pass
-        w.q[(size_t)N + k0 + lane] = y1;
-      }
-      if (!send(k)) {
+      stage[64 + lane] = c0;
+      stage[96 + lane] = c1;
+      if (!send(k, 128)) {
         if (lane == 0) fail();
         break;
       }
+      // the forward result, right-hand side of the backward pass (stored
+      // after the send, whose release would otherwise wait for these stores)
+      if (lane < wd) {
+        w.q[k0 + lane] = y0;
+        w.q[(size_t)N + k0 + lane] = y1;
+      }
+    }
+  } else if (warp == DF_UW + 1) {
+    // publisher: after each step's barrier, the count of steps done (its
+    // release waits for no loads of its own, unlike the update warps')
+    for (int s = 0; s < nk; ++s) {
+      if (df_update_bar_any(false)) break;
+      if (lane == 0) df_st_release(df_mapa(&done, rank), (unsigned)(s + 1));
     }
   } else {
     // update warps: warp u takes the u-th, (u + DF_UW)-th, ... of this CTA's blocks
-    // in each step's window, lane = row in the block
+    // in each step's window, lane = row in the block; the multipliers and the
+    // interchanges of a step are loaded two steps ahead (two register sets)
     const int u = warp - 1;
-    float lr[32];
-    int td = -1, ts = 0, ntl = 0;
     // this warp's first block of forward step s (rows 32 (s + 1) .. k0 + H - 1), or -1
     auto first_block = [&](int s) -> int {
       const int k0 = s * nb, H = s2::panel_height(g, s2::panel_width(g, nb, k0), k0);
@@ -1406,50 +1508,51 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       const int b = bf + (((int)rank - bf) % DF_C + DF_C) % DF_C + u * DF_C;
       return b <= bl ? b : -1;
     };
-    // multipliers of step s for this lane's row of block b (zero outside the window
-    // and past the panel's width), and the step's interchanges past the head
-    auto load_fwd = [&](int s, int b) {
+    // multipliers of step s for this lane's row of block b (zero outside the
+    // window and past the panel's width)
+    auto load_l = [&](float (&lr)[32], int s, int b) {
       const int k0 = s * nb, wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
       const int r = 32 * b + lane - k0;
       const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) lr[jj] = (b >= 0 && r < H && jj < wd) ? __ldg(Lk + (size_t)jj * ldp + r) : 0.0f;
     };
-    auto load_tail = [&](int s) {
-      const int32_t* sm = w.smap + (size_t)s * 128;
-      ntl = sm[96];
-      td = lane < ntl ? sm[32 + lane] : -1;
-      ts = lane < ntl ? sm[64 + lane] : 0;
+    // the step's interchanges past the head: entry `lane` of its list
+    struct Tail {
+      int n, d;
     };
-    int bcur = first_block(0);
-    load_fwd(0, bcur);
-    load_tail(0);
-    for (int s = 0; s < nk; ++s) {
+    auto load_tail = [&](int s) -> Tail {
+      const int32_t* sm = w.smap + (size_t)s * 128;
+      Tail t;
+      t.n = __ldg(sm + 96);
+      t.d = lane < t.n ? __ldg(sm + 32 + lane) : -1;
+      return t;
+    };
+    // step s with this warp's first block b and its multipliers lr; false once a wait gave up
+    auto step = [&](int s, int bfirst, float (&lr)[32], const Tail& tl) -> bool {
       const int k0 = s * nb, wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
       const int bl = (k0 + H - 1) >> 5;
       const float* y = ring[s % DF_S];
       bool bad = !df_wait_slot(&full[s % DF_S], (unsigned)(s / DF_S) & 1u);
-      for (int b = bcur; !bad && b >= 0 && b <= bl; b += DF_UW * DF_C) {
-        if (b != bcur) load_fwd(s, b);  // a window wider than DF_UW x DF_C blocks
+      for (int b = bfirst; !bad && b >= 0 && b <= bl; b += DF_UW * DF_C) {
+        if (b != bfirst) load_l(lr, s, b);  // a window wider than DF_UW x DF_C blocks
         const int R = 32 * b + lane;
-        // the source of row R under the step's interchanges (a head position, or R)
-        int src = R;
-        for (unsigned m = __ballot_sync(0xffffffffu, lane < ntl && (td >> 5) == b); m; m &= m - 1) {
+        // row R's entry in the step's list of rows past the head that take a
+        // head value (-1: none; the value came with the step's result)
+        int qi = -1;
+        for (unsigned m = __ballot_sync(0xffffffffu, lane < tl.n && (tl.d >> 5) == b); m; m &= m - 1) {
           const int q = __ffs(m) - 1;
-          const int d = __shfl_sync(0xffffffffu, td, q), sv = __shfl_sync(0xffffffffu, ts, q);
-          if (d == R) src = sv;
+          if (__shfl_sync(0xffffffffu, tl.d, q) == R) qi = q;
         }
         if (R - k0 < H) {
           float v0, v1;
           const int par = s & 1;
-          if (src == R) {
+          if (qi < 0) {
             v0 = *aloc(par, 0, R);
             v1 = *aloc(par, 1, R);
           } else {
-            // a head value: its owner has written it in step s - 1
-            if (s >= 1 && !df_wait_count(df_mapa(&done, owner(src)), (unsigned)s)) bad = true;
-            v0 = df_ld_remote(df_mapa(aloc(par, 0, src), owner(src)));
-            v1 = df_ld_remote(df_mapa(aloc(par, 1, src), owner(src)));
+            v0 = y[64 + qi];
+            v1 = y[96 + qi];
           }
           float acc0 = 0.0f, acc1 = 0.0f;
           df_dot2(lr, y, acc0, acc1);
@@ -1459,13 +1562,28 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       }
       if (df_update_bar_any(bad)) {
         if (tid == 32) fail();
-        break;
+        return false;
       }
-      if (tid == 32) df_st_release(df_mapa(&done, rank), (unsigned)(s + 1));
-      if (s + 1 < nk) {
-        bcur = first_block(s + 1);
-        load_fwd(s + 1, bcur);
-        load_tail(s + 1);
+      return true;
+    };
+    float lrA[32], lrB[32];
+    int bA = first_block(0), bB = nk > 1 ? first_block(1) : -1;
+    Tail tA = load_tail(0), tB = nk > 1 ? load_tail(1) : Tail{0, -1};
+    load_l(lrA, 0, bA);
+    load_l(lrB, 1, bB);
+    for (int s = 0; s < nk; s += 2) {
+      if (!step(s, bA, lrA, tA)) break;
+      if (s + 2 < nk) {
+        bA = first_block(s + 2);
+        tA = load_tail(s + 2);
+        load_l(lrA, s + 2, bA);
+      }
+      if (s + 1 >= nk) break;
+      if (!step(s + 1, bB, lrB, tB)) break;
+      if (s + 3 < nk) {
+        bB = first_block(s + 3);
+        tB = load_tail(s + 3);
+        load_l(lrB, s + 3, bB);
       }
     }
   }
@@ -1520,18 +1638,22 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       if (lane >= wd) x0 = x1 = 0.0f;
       stage[lane] = x0;
       stage[32 + lane] = x1;
+      if (!send(t, 64)) {
+        if (lane == 0) fail();
+        break;
+      }
       if (lane < wd) {
         o0[R] = x0;
         o1[R] = x1;
       }
-      if (!send(t)) {
-        if (lane == 0) fail();
-        break;
-      }
+    }
+  } else if (warp == DF_UW + 1) {
+    for (int it = 0; it < nk; ++it) {
+      if (df_update_bar_any(false)) break;
+      if (lane == 0) df_st_release(df_mapa(&done, rank), (unsigned)(nk + it + 1));
     }
   } else {
     const int u = warp - 1;
-    float ur[32];
     // rows lo .. k0 - 1 of backward step it (panel k = nk - 1 - it): this warp's first block, or -1
     auto first_block = [&](int it) -> int {
       const int k = nk - 1 - it, k0 = k * nb;
@@ -1540,22 +1662,20 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       const int b = bf + (((int)rank - bf) % DF_C + DF_C) % DF_C + u * DF_C;
       return b <= bl ? b : -1;
     };
-    auto load_bwd = [&](int it, int b) {
+    auto load_u = [&](float (&ur)[32], int it, int b) {
       const int k = nk - 1 - it, k0 = k * nb, wd = s2::panel_width(g, nb, k0);
       const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
       const int R = 32 * b + lane;
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) ur[jj] = (b >= 0 && R >= lo && jj < wd) ? s2::umul(g, w.AB, R, k0 + jj) : 0.0f;
     };
-    int bcur = first_block(0);
-    load_bwd(0, bcur);
-    for (int it = 0; it < nk; ++it) {
+    auto step = [&](int it, int bfirst, float (&ur)[32]) -> bool {
       const int t = nk + it, k = nk - 1 - it, k0 = k * nb;
       const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
       const float* x = ring[t % DF_S];
       bool bad = !df_wait_slot(&full[t % DF_S], (unsigned)(t / DF_S) & 1u);
-      for (int b = bcur; !bad && b >= 0 && b <= k - 1; b += DF_UW * DF_C) {
-        if (b != bcur) load_bwd(it, b);
+      for (int b = bfirst; !bad && b >= 0 && b <= k - 1; b += DF_UW * DF_C) {
+        if (b != bfirst) load_u(ur, it, b);
         const int R = 32 * b + lane;
         if (R >= lo) {
           const int par = it & 1;
@@ -1568,18 +1688,30 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       }
       if (df_update_bar_any(bad)) {
         if (tid == 32) fail();
-        break;
+        return false;
       }
-      if (tid == 32) df_st_release(df_mapa(&done, rank), (unsigned)(t + 1));
-      if (it + 1 < nk) {
-        bcur = first_block(it + 1);
-        load_bwd(it + 1, bcur);
+      return true;
+    };
+    float urA[32], urB[32];
+    int bA = first_block(0), bB = nk > 1 ? first_block(1) : -1;
+    load_u(urA, 0, bA);
+    load_u(urB, 1, bB);
+    for (int it = 0; it < nk; it += 2) {
+      if (!step(it, bA, urA)) break;
+      if (it + 2 < nk) {
+        bA = first_block(it + 2);
+        load_u(urA, it + 2, bA);
+      }
+      if (it + 1 >= nk) break;
+      if (!step(it + 1, bB, urB)) break;
+      if (it + 3 < nk) {
+        bB = first_block(it + 3);
+        load_u(urB, it + 3, bB);
       }
     }
   }
   sc_cluster_sync();
 }
-
 
 // right-hand sides of a Newton step: -R and e_r (the total-mass row)
 __global__ void k_s2_prep(const s2::Grid g, S2Work w) {
@@ -1727,6 +1859,15 @@ void s2_smem_limits(size_t panel, size_t trail, size_t subst) {
       set[k] = need[k];
     }
   }
+  // the register-row panels: multipliers of up to 3 x 512 rows and the position map
+  static bool rot_set = false;
+  if (!rot_set) {
+    const int cap = (int)(sizeof(float) * 32 * 3 * S2_PNL_NT + sizeof(int) * 3 * S2_PNL_NT);
+    cudaFuncSetAttribute(k_s2_panel_rot<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    cudaFuncSetAttribute(k_s2_panel_rot<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    cudaFuncSetAttribute(k_s2_panel_rot<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    rot_set = true;
+  }
 }
 
 }  // namespace
@@ -1846,12 +1987,16 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
     if (refactor) {
       for (int k0 = 0; k0 < g.N; k0 += nb) {
         const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
-        if (nb == 32 && H <= S2_PNL_NT)
-          k_s2_panel_rg<1><<<1, S2_PNL_NT, 0, st>>>(g, w, k0);
-        else if (nb == 32 && H <= 2 * S2_PNL_NT)
-          k_s2_panel_rg<2><<<1, S2_PNL_NT, 0, st>>>(g, w, k0);
-        else if (nb == 32 && H <= 3 * S2_PNL_NT)
-          k_s2_panel_rg<3><<<1, S2_PNL_NT, 0, st>>>(g, w, k0);
+        // rows in registers (up to 3 a thread, 512 threads) where they fit
+        const int rpt = (H + S2_PNL_NT - 1) / S2_PNL_NT;
+        const int tpb = rpt <= 3 ? (H + 32 * rpt - 1) / (32 * rpt) * 32 : 0;
+        const size_t smr = tpb ? sizeof(float) * 32 * (size_t)tpb * rpt + sizeof(int) * (size_t)H : 0;
+        if (nb == 32 && rpt == 1)
+          k_s2_panel_rot<1><<<1, tpb, smr, st>>>(g, w, k0);
+        else if (nb == 32 && rpt == 2)
+          k_s2_panel_rot<2><<<1, tpb, smr, st>>>(g, w, k0);
+        else if (nb == 32 && rpt == 3)
+          k_s2_panel_rot<3><<<1, tpb, smr, st>>>(g, w, k0);
         else
           k_s2_panel<<<1, S2_PNL_NT, sizeof(float) * (size_t)wd * H, st>>>(g, w, k0);
         const int ntrail = s2::trail_last(g, k0, wd) - (k0 + wd) + 1;
