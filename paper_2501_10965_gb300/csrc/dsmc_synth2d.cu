@@ -348,28 +348,8 @@ __global__ void __launch_bounds__(S2_PNL_NT) k_s2_panel(const s2::Grid g, S2Work
   s2::panel_store(g, w.nb, w.AB, w.Lp, w.ud, k0, wd, H, P, tid, S2_PNL_NT);
 }
 
-// (largest candidate, its position) over the CTA's nw warps: a candidate's
-// key is 1 + the bits of its magnitude (0: no candidate; magnitudes that are
-// not numbers never win), ties go to the lowest position; no candidate gives
-// `fallback` with magnitude -1 (the choice of s2_block_argmax)
-__device__ __forceinline__ int s2_argmax_key(unsigned key, int pos, unsigned (*ck)[32], int (*cp)[32], int buf,
-                                             int fallback, float& best_out, int nw) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned kw = __reduce_max_sync(0xffffffffu, key);
-  const int pw = __reduce_min_sync(0xffffffffu, key == kw ? pos : INT_MAX);
-  if (lane == 0) {
-    ck[buf][warp] = kw;
-    cp[buf][warp] = pw;
-  }
-  __syncthreads();
-  const unsigned k2 = lane < nw ? ck[buf][lane] : 0u;
-  const int p2 = lane < nw ? cp[buf][lane] : INT_MAX;
-  const unsigned km = __reduce_max_sync(0xffffffffu, k2);
-  const int pm = __reduce_min_sync(0xffffffffu, k2 == km ? p2 : INT_MAX);
-  best_out = km == 0u ? -1.0f : __uint_as_float(km - 1u);
-  return km == 0u ? fallback : pm;
-}
-
+// a pivot candidate's key: 1 + the bits of its magnitude (0: not a
+// candidate; magnitudes that are not numbers never win)
 __device__ __forceinline__ unsigned s2_cand_key(float v, bool cand) {
   const float a = fabsf(v);
   return (cand && a == a) ? __float_as_uint(a) + 1u : 0u;
@@ -381,22 +361,23 @@ __device__ __forceinline__ unsigned s2_cand_key(float v, bool cand) {
 // frame shifts by four columns every four steps, so one loop body of four
 // unrolled steps serves the panel; columns past the panel's width are
 // skipped eight at a time).  Interchanges move no row: each row carries its
-// current position, and pos_owner maps a position to the row (by load index)
-// that holds it; the pivot row goes to shared memory for the rank-one
-// update, its U entries to global memory, and each row's multipliers to
-// shared memory (Ls, by load index) until the end, when they are stored at
-// the rows' final positions.  The operations on each entry, their order and
-// the choice of pivots are those of k_s2_panel.
+// current position.  One barrier per step: in the pivot search each warp
+// writes its best candidate row (from the pivot column on) to shared memory
+// with its key, so the row the block chooses is already there for the
+// rank-one update of the next step.  The pivot row's U entries go to global
+// memory at once, each row's multipliers to shared memory (Ls, by load
+// index) until the end, when they are stored at the rows' final positions.
+// The pivots are chosen as in k_s2_panel (largest magnitude, lowest position
+// among equals), and each entry takes the same operations in the same order.
 template <int RPT>
 __global__ void __launch_bounds__(512) k_s2_panel_rot(const s2::Grid g, S2Work w, int k0) {
   __shared__ unsigned ckey[2][32];
   __shared__ int cpos[2][32];
-  __shared__ float prow[32];
+  __shared__ __align__(16) float crow[2][32][32];  // per warp: its candidate row (frame of the next step)
   const int T = blockDim.x, NS = T * RPT, nw = T >> 5;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wd = s2::panel_width(g, w.nb, k0), H = s2::panel_height(g, wd, k0);
-  float* Ls = reinterpret_cast<float*>(s2_smem);                  // [32][NS]
-  int* pos_owner = reinterpret_cast<int*>(Ls + (size_t)32 * NS);  // [H]
+  float* Ls = reinterpret_cast<float*>(s2_smem);  // [32][NS]
   float a[RPT][32];
   int pos[RPT];
   bool act[RPT];
@@ -411,29 +392,50 @@ __global__ void __launch_bounds__(512) k_s2_panel_rot(const s2::Grid g, S2Work w
       a[s][c] = in ? w.AB[s2::band_at(g, k0 + r, k0 + c)] : 0.0f;
     }
   }
-  for (int r = tid; r < H; r += T) pos_owner[r] = r;
-  // this thread's best candidate of frame column fc for positions lo .. hi
-  auto cand = [&](auto fct, int lo, int hi, unsigned& key, int& bp) {
-    constexpr int fc = decltype(fct)::value;
-    key = 0u;
-    bp = INT_MAX;
+  float pbest = -1.0f;
+  int p = 0, pwin = 0;
+  // pivot search on frame column fc among positions lo .. hi; the winning
+  // rows go to crow[buf] in the frame shifted by sh columns
+  auto search = [&](auto fct, auto sht, int lo, int hi, int buf, int fallback) {
+    constexpr int fc = decltype(fct)::value, sh = decltype(sht)::value;
+    unsigned key = 0u;
+    int bp = INT_MAX, bs = 0;
 #pragma unroll
     for (int s = 0; s < RPT; ++s) {
       const unsigned kq = s2_cand_key(a[s][fc], act[s] && pos[s] >= lo && pos[s] <= hi);
       if (kq > key || (kq == key && kq != 0u && pos[s] < bp)) {
         key = kq;
         bp = pos[s];
+        bs = s;
       }
     }
+    const unsigned kw = __reduce_max_sync(0xffffffffu, key);
+    const int pw = __reduce_min_sync(0xffffffffu, key == kw ? bp : INT_MAX);
+    if (kw != 0u && key == kw && bp == pw) {
+#pragma unroll
+      for (int c = fc - sh; c + sh < 32; ++c) {
+        float v = a[0][c + sh];
+#pragma unroll
+        for (int s = 1; s < RPT; ++s)
+          if (s == bs) v = a[s][c + sh];
+        crow[buf][warp][c] = v;
+      }
+    }
+    if (lane == 0) {
+      ckey[buf][warp] = kw;
+      cpos[buf][warp] = pw;
+    }
+    __syncthreads();
+    const unsigned k2 = lane < nw ? ckey[buf][lane] : 0u;
+    const int p2 = lane < nw ? cpos[buf][lane] : INT_MAX;
+    const unsigned km = __reduce_max_sync(0xffffffffu, k2);
+    const int pm = __reduce_min_sync(0xffffffffu, k2 == km ? p2 : INT_MAX);
+    const unsigned won = __ballot_sync(0xffffffffu, lane < nw && k2 == km && p2 == pm);
+    pbest = km == 0u ? -1.0f : __uint_as_float(km - 1u);
+    p = km == 0u ? fallback : pm;
+    pwin = km == 0u ? 0 : __ffs(won) - 1;
   };
-  float pbest = -1.0f;
-  int p;
-  {
-    unsigned key;
-    int bp;
-    cand(std::integral_constant<int, 0>{}, 0, s2::panel_rmax(g, H, 0), key, bp);
-    p = s2_argmax_key(key, bp, ckey, cpos, 0, 0, pbest, nw);
-  }
+  search(std::integral_constant<int, 0>{}, std::integral_constant<int, 0>{}, 0, s2::panel_rmax(g, H, 0), 0, 0);
   const int ld = g.ld;
 #pragma unroll 1
   for (int jb = 0; jb < wd; jb += 4) {
@@ -443,38 +445,20 @@ __global__ void __launch_bounds__(512) k_s2_panel_rot(const s2::Grid g, S2Work w
       constexpr int jj = decltype(jjt)::value;
       const int j = jb + jj;
       if (j >= wd) return;
-      const int idp = pos_owner[p], idj = pos_owner[j];
+      const float* prow = crow[j & 1][pwin];
+      // the interchange: the pivot row takes position j, the row there takes p
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        if (act[s] && pos[s] == p) {
+          act[s] = false;
+          pos[s] = j;
+        } else if (act[s] && pos[s] == j) {
+          pos[s] = p;
+        }
+      }
       if (tid == 0) {
         w.piv[k0 + j] = k0 + p;
         if (!(pbest > 0.0f)) w.sc[S2_SING] = 1.0;
-      }
-      if (tid == idp % T) {
-        const int sp = idp / T;
-#pragma unroll
-        for (int c = jj; c < 32; ++c) {
-          float v = a[0][c];
-#pragma unroll
-          for (int s = 1; s < RPT; ++s)
-            if (s == sp) v = a[s][c];
-          prow[c] = v;
-        }
-#pragma unroll
-        for (int s = 0; s < RPT; ++s)
-          if (s == sp) {
-            act[s] = false;
-            pos[s] = j;
-          }
-      }
-      if (p != j && tid == idj % T) {
-        const int sj = idj / T;
-#pragma unroll
-        for (int s = 0; s < RPT; ++s)
-          if (s == sj) pos[s] = p;
-      }
-      __syncthreads();
-      if (tid == 0 && p != j) {
-        pos_owner[j] = idp;
-        pos_owner[p] = idj;
       }
       // U(j, j + c) of the pivot row
       if (tid < wd - j) {
@@ -505,10 +489,12 @@ __global__ void __launch_bounds__(512) k_s2_panel_rot(const s2::Grid g, S2Work w
         }
       }
       if (j + 1 < wd) {
-        unsigned key;
-        int bp;
-        cand(std::integral_constant<int, jj + 1>{}, j + 1, s2::panel_rmax(g, H, j + 1), key, bp);
-        p = s2_argmax_key(key, bp, ckey, cpos, (j + 1) & 1, j + 1, pbest, nw);
+        const int rm1 = s2::panel_rmax(g, H, j + 1);
+        if constexpr (jj < 3)
+          search(std::integral_constant<int, jj + 1>{}, std::integral_constant<int, 0>{}, j + 1, rm1, (j + 1) & 1,
+                 j + 1);
+        else
+          search(std::integral_constant<int, 4>{}, std::integral_constant<int, 4>{}, j + 1, rm1, (j + 1) & 1, j + 1);
       }
     };
     step(std::integral_constant<int, 0>{});
@@ -1182,15 +1168,18 @@ __global__ void __launch_bounds__(SP_WPB * 32) k_s2_sprep(const s2::Grid g, S2Wo
 // itself, from the other copy and the previous step's result (the previous
 // panel's multipliers for the head's source rows), applies the inverse of
 // the panel's triangle and sends the 32 results (two right-hand sides) into
-// a ring of DF_S slots in every CTA, each slot completed on an mbarrier;
-// with them go the head values that the panel's interchanges move to rows
-// below the head, computed the same way.  Warps 1 .. DF_UW of every CTA take
-// each step's result from the ring and update their CTA's rows of the step's
-// window, then publish the number of steps done (release).  Warp 0 reads
-// other CTAs' rows only after waiting (acquire) until that count covers the
-// step the values come from, one step ahead of their use.  Each wait gives
-// up after DF_WAIT_NS (the kernel then records the timeout in the work area
-// and every CTA leaves at the next cluster barrier).
+// a ring of DF_S slots in every CTA by asynchronous stores, which complete
+// the slot's mbarrier phase there; with them go the head values that the
+// panel's interchanges move to rows below the head, computed the same way.
+// Warps 1 .. DF_UW of every CTA take each step's result from the ring and
+// update their CTA's rows of the step's window; warp DF_UW + 1 arms each
+// slot's next phase and, after the update warps' barrier, publishes the
+// number of steps done (release).  Warp 0 reads other CTAs' rows only after
+// waiting (acquire) until that count covers the step the values come from,
+// one step ahead of their use, and writes a slot only when every CTA has
+// finished the slot's previous step.  Each wait gives up after DF_WAIT_NS
+// (the kernel then records the timeout in the work area, drains the slots
+// still armed and every CTA leaves at the next cluster barrier).
 //
 // The arithmetic of each row and head value, and its order, are those of
 // k_s2_subst_cl; forward, then (after one cluster barrier) backward.
@@ -1201,6 +1190,8 @@ constexpr int DF_NT = 32 * (2 + DF_UW);  // warp 0 solves the heads, warp DF_UW 
 constexpr int DF_S = 32;                 // ring slots (steps in flight)
 constexpr int DF_SEND_LANES = 32 / DF_C;  // lanes of warp 0 that write one CTA's ring slot
 constexpr unsigned long long DF_WAIT_NS = 500000000ull;  // 0.5 s
+constexpr unsigned long long DF_DRAIN_NS = 1000000ull;   // 1 ms
+constexpr unsigned DF_SUSPEND_NS = 4000;                  // longest suspension of one wait test
 
 __device__ __forceinline__ unsigned long long df_clock_ns() {
   unsigned long long t;
@@ -1241,18 +1232,31 @@ __device__ __forceinline__ void df_st_remote4(unsigned addr, float4 v) {
                : "memory");
 }
 
-__device__ __forceinline__ void df_arrive_remote(unsigned addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+// asynchronous store of 16 bytes into another CTA's shared memory, counted
+// on that CTA's mbarrier at `mbar` (complete_tx) once it has landed
+__device__ __forceinline__ void df_st_async4(unsigned addr, float4 v, unsigned mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+               "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(mbar)
+               : "memory");
 }
 
+// this CTA's arrival on its mbarrier, expecting `bytes` of asynchronous stores in the phase
+__device__ __forceinline__ void df_arm(const uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(df_smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// test for the completion of the phase of parity `parity`; the thread may be
+// suspended until then, for at most DF_SUSPEND_NS, instead of spinning (a
+// spinning warp takes issue slots from the warps that compute)
 __device__ __forceinline__ bool df_try_wait(const uint64_t* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(df_smem_addr(bar)), "r"(parity)
+      : "r"(df_smem_addr(bar)), "r"(parity), "r"(DF_SUSPEND_NS)
       : "memory");
   return ok != 0;
 }
@@ -1262,7 +1266,7 @@ __device__ __forceinline__ bool df_wait_slot(const uint64_t* bar, unsigned parit
   if (df_try_wait(bar, parity)) return true;
   const unsigned long long t0 = df_clock_ns();
   for (;;) {
-    for (int q = 0; q < 64; ++q)
+    for (int q = 0; q < 8; ++q)
       if (df_try_wait(bar, parity)) return true;
     if (df_clock_ns() - t0 > DF_WAIT_NS) return false;
   }
@@ -1299,21 +1303,25 @@ __device__ __forceinline__ bool df_update_bar_any(bool bad) {
   return r != 0;
 }
 
-// acc0 += l . y[0:32], acc1 += l . y[32:64] (the order of k_s2_subst_cl)
+// acc0 = l . y[0:32], acc1 = l . y[32:64] (y 16-byte aligned; four partial
+// sums each, for a short dependency chain)
 __device__ __forceinline__ void df_dot2(const float (&l)[32], const float* y, float& acc0, float& acc1) {
-  const float4* y4 = reinterpret_cast<const float4*>(y);  // a 256-byte ring slot
+  const float4* y4 = reinterpret_cast<const float4*>(y);
+  float p0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, p1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const float4 a = y4[q], b = y4[8 + q];
-    acc0 += l[4 * q] * a.x;
-    acc1 += l[4 * q] * b.x;
-    acc0 += l[4 * q + 1] * a.y;
-    acc1 += l[4 * q + 1] * b.y;
-    acc0 += l[4 * q + 2] * a.z;
-    acc1 += l[4 * q + 2] * b.z;
-    acc0 += l[4 * q + 3] * a.w;
-    acc1 += l[4 * q + 3] * b.w;
+    p0[0] += l[4 * q] * a.x;
+    p1[0] += l[4 * q] * b.x;
+    p0[1] += l[4 * q + 1] * a.y;
+    p1[1] += l[4 * q + 1] * b.y;
+    p0[2] += l[4 * q + 2] * a.z;
+    p1[2] += l[4 * q + 2] * b.z;
+    p0[3] += l[4 * q + 3] * a.w;
+    p1[3] += l[4 * q + 3] * b.w;
   }
+  acc0 = (p0[0] + p0[1]) + (p0[2] + p0[3]);
+  acc1 = (p1[0] + p1[1]) + (p1[2] + p1[3]);
 }
 
 __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Work w, const double* b0,
@@ -1323,6 +1331,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   // 64 + q, rhs 1 at 96 + q)
   __shared__ __align__(16) float ring[DF_S][128];
   __shared__ __align__(16) float stage[128];  // warp 0's result before it is sent
+  __shared__ __align__(16) float hsol[64];    // warp 0: the head's values before the triangle solve
   __shared__ __align__(8) uint64_t full[DF_S];
   __shared__ unsigned done;       // steps this CTA's update warps have finished
   __shared__ unsigned abort_all;  // set in every CTA once a wait gave up
@@ -1357,9 +1366,12 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     done = 0;
     abort_all = 0;
   }
-  if (tid < DF_S)
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(df_smem_addr(&full[tid])), "r"(DF_SEND_LANES)
-                 : "memory");
+  // bytes a step's result brings into each CTA's ring slot
+  auto step_bytes = [&](int t) -> unsigned { return t < nk ? 512u : 256u; };
+  if (tid < DF_S) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(df_smem_addr(&full[tid])) : "memory");
+    if (tid < 2 * nk) df_arm(&full[tid], step_bytes(tid));
+  }
   fill(b0, b1);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   sc_cluster_sync();
@@ -1367,7 +1379,8 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   // warp 0: send the first nf floats of this step's result (stage) to every
   // CTA's ring slot t % DF_S, once the CTA has finished step t - DF_S (the
   // slot's previous use).  Lane l writes part l / DF_C of the floats to CTA
-  // l % DF_C and arrives on its slot's mbarrier (DF_SEND_LANES arrivals).
+  // l % DF_C by asynchronous stores, which complete the slot's phase there
+  // (its publishing warp armed the phase for the step's bytes).
   auto send = [&](int t, int nf) -> bool {
     __syncwarp();
     const unsigned c = (unsigned)(lane % DF_C);
@@ -1377,11 +1390,26 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     if (ok) {
       const int part = lane / DF_C, n4 = nf / (4 * DF_SEND_LANES);
       const unsigned dst = df_mapa(&ring[t % DF_S][0], c) + 16u * (unsigned)(part * n4);
+      const unsigned mb = df_mapa(&full[t % DF_S], c);
       const float4* src = reinterpret_cast<const float4*>(stage) + part * n4;
-      for (int q = 0; q < n4; ++q) df_st_remote4(dst + 16 * q, src[q]);
-      df_arrive_remote(df_mapa(&full[t % DF_S], c));
+      for (int q = 0; q < n4; ++q) df_st_async4(dst + 16 * q, src[q], mb);
     }
     return __all_sync(0xffffffffu, ok);
+  };
+  // the publishing warp's lane 0: the first step whose slot it has not consumed
+  int tnext = 0;
+  // after a cluster barrier that ends the sends: wait (briefly) for the slots
+  // armed but not consumed, so that no asynchronous store is still on its way
+  // into this CTA when it exits (only after a wait gave up)
+  auto drain = [&]() {
+    if (warp == DF_UW + 1 && lane == 0) {
+      const int tend = tnext + DF_S < 2 * nk ? tnext + DF_S : 2 * nk;
+      for (int t = tnext; t < tend; ++t) {
+        const unsigned long long t0 = df_clock_ns();
+        while (!df_try_wait(&full[t % DF_S], (unsigned)(t / DF_S) & 1u))
+          if (df_clock_ns() - t0 > DF_DRAIN_NS) break;
+      }
+    }
   };
   // ---- forward: L y = P b ----
   if (warp == 0) {
@@ -1466,13 +1494,12 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         if (lane == 0) fail();
         break;
       }
-      float y0 = 0.0f, y1 = 0.0f;
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) {
-        const float b0j = __shfl_sync(0xffffffffu, a0, jj), b1j = __shfl_sync(0xffffffffu, a1, jj);
-        y0 += invr[jj] * b0j;
-        y1 += invr[jj] * b1j;
-      }
+      // y = (inverse of L11) times the head's values
+      hsol[lane] = a0;
+      hsol[32 + lane] = a1;
+      __syncwarp();
+      float y0, y1;
+      df_dot2(invr, hsol, y0, y1);
       if (lane >= wd) y0 = y1 = 0.0f;
       stage[lane] = y0;
       stage[32 + lane] = y1;
@@ -1490,10 +1517,19 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       }
     }
   } else if (warp == DF_UW + 1) {
-    // publisher: after each step's barrier, the count of steps done (its
-    // release waits for no loads of its own, unlike the update warps')
+    // publisher: waits for each step's slot and arms its next use, then after
+    // the step's barrier publishes the count of steps done (its release waits
+    // for no loads of its own, unlike the update warps')
     for (int s = 0; s < nk; ++s) {
-      if (df_update_bar_any(false)) break;
+      bool bad = false;
+      if (lane == 0) {
+        bad = !df_wait_slot(&full[s % DF_S], (unsigned)(s / DF_S) & 1u);
+        if (!bad) {
+          tnext = s + 1;
+          if (s + DF_S < 2 * nk) df_arm(&full[s % DF_S], step_bytes(s + DF_S));
+        }
+      }
+      if (df_update_bar_any(bad)) break;
       if (lane == 0) df_st_release(df_mapa(&done, rank), (unsigned)(s + 1));
     }
   } else {
@@ -1590,6 +1626,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   // ---- backward: U x = y, steps t = nk + it for panel k = nk - 1 - it ----
   sc_cluster_sync();
   if (abort_all) {
+    drain();
     sc_cluster_sync();
     return;
   }
@@ -1628,13 +1665,12 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         if (lane == 0) fail();
         break;
       }
-      float x0 = 0.0f, x1 = 0.0f;
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) {
-        const float y0j = __shfl_sync(0xffffffffu, a0, jj), y1j = __shfl_sync(0xffffffffu, a1, jj);
-        x0 += invr[jj] * y0j;
-        x1 += invr[jj] * y1j;
-      }
+      // x = (inverse of U11) times the head's values
+      hsol[lane] = a0;
+      hsol[32 + lane] = a1;
+      __syncwarp();
+      float x0, x1;
+      df_dot2(invr, hsol, x0, x1);
       if (lane >= wd) x0 = x1 = 0.0f;
       stage[lane] = x0;
       stage[32 + lane] = x1;
@@ -1649,8 +1685,17 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     }
   } else if (warp == DF_UW + 1) {
     for (int it = 0; it < nk; ++it) {
-      if (df_update_bar_any(false)) break;
-      if (lane == 0) df_st_release(df_mapa(&done, rank), (unsigned)(nk + it + 1));
+      const int t = nk + it;
+      bool bad = false;
+      if (lane == 0) {
+        bad = !df_wait_slot(&full[t % DF_S], (unsigned)(t / DF_S) & 1u);
+        if (!bad) {
+          tnext = t + 1;
+          if (t + DF_S < 2 * nk) df_arm(&full[t % DF_S], step_bytes(t + DF_S));
+        }
+      }
+      if (df_update_bar_any(bad)) break;
+      if (lane == 0) df_st_release(df_mapa(&done, rank), (unsigned)(t + 1));
     }
   } else {
     const int u = warp - 1;
@@ -1710,6 +1755,8 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       }
     }
   }
+  sc_cluster_sync();
+  drain();
   sc_cluster_sync();
 }
 
@@ -1859,10 +1906,10 @@ void s2_smem_limits(size_t panel, size_t trail, size_t subst) {
       set[k] = need[k];
     }
   }
-  // the register-row panels: multipliers of up to 3 x 512 rows and the position map
+  // the register-row panels: multipliers of up to 3 x 512 rows
   static bool rot_set = false;
   if (!rot_set) {
-    const int cap = (int)(sizeof(float) * 32 * 3 * S2_PNL_NT + sizeof(int) * 3 * S2_PNL_NT);
+    const int cap = (int)(sizeof(float) * 32 * 3 * S2_PNL_NT);
     cudaFuncSetAttribute(k_s2_panel_rot<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
     cudaFuncSetAttribute(k_s2_panel_rot<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
     cudaFuncSetAttribute(k_s2_panel_rot<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
@@ -1948,7 +1995,7 @@ size_t synth2d_work_doubles(int nx, int ny, int annulus) {
 }
 
 int launch_synth2d(const CellParams& cp, const double* fields, const double* hot, double* out, double* work,
-                   int n_m, double tol, double* info, int* singular, cudaStream_t st) {
+                   int n_m, double tol, double* info, int* singular, int reuse, cudaStream_t st) {
   s2::Grid g = s2::make_grid(cp.nx, cp.ny, cp.dx, cp.dy, cp.d_r, cp.omega, cp.mu_ref, cp.z_rot, cp.kappa_t,
                              cp.kappa_r, fields, hot);
   if (cp.mesh == 2) s2::set_edges(g, cp.xe, cp.ye, cp.lx * cp.ly);  // the wall-refined grid (device edges)
@@ -1973,11 +2020,12 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
   const int jac_grid = (int)((jac_threads + nt - 1) / nt);
   double sc[S2_NSC];
   k_s2_init<<<1, S2_NT, 0, st>>>(g, w);
-  // The factorisation of the first Newton step is reused while the updates
+  // The factorisation of the first Newton step (with `reuse`, the one the
+  // work area holds from the previous solve) is reused while the updates
   // keep shrinking (by half or more per step), with more refinement sweeps
   // against each step's fresh FP64 Jacobian; otherwise the next step
   // refactorises.
-  bool refactor = true;
+  bool refactor = !reuse;
   double dm_prev = 0.0;
   for (int it = 0; it < n_m; ++it) {
     k_s2_mass<<<1, S2_NT, 0, st>>>(g, w);
@@ -1990,7 +2038,7 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
         // rows in registers (up to 3 a thread, 512 threads) where they fit
         const int rpt = (H + S2_PNL_NT - 1) / S2_PNL_NT;
         const int tpb = rpt <= 3 ? (H + 32 * rpt - 1) / (32 * rpt) * 32 : 0;
-        const size_t smr = tpb ? sizeof(float) * 32 * (size_t)tpb * rpt + sizeof(int) * (size_t)H : 0;
+        const size_t smr = tpb ? sizeof(float) * 32 * (size_t)tpb * rpt : 0;
         if (nb == 32 && rpt == 1)
           k_s2_panel_rot<1><<<1, tpb, smr, st>>>(g, w, k0);
         else if (nb == 32 && rpt == 2)
@@ -2032,6 +2080,10 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
   cudaError_t e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
+  // a solve that started from an earlier factorisation and did not
+  // converge is repeated from a fresh one
+  if (reuse && sc[S2_STATUS] != 0.0)
+    return launch_synth2d(cp, fields, hot, out, work, n_m, tol, info, singular, 0, st);
   if (singular) *singular = sc[S2_SING] != 0.0;
   return 0;
 }

@@ -26,7 +26,7 @@ MESH = {"box": 0, "annulus": 1, "refined": 2}
 
 # every symbol the header declares
 SYMBOLS = ["dsmc_workspace_size", "dsmc_init", "dsmc_destroy", "dsmc_last_error", "dsmc_step", "dsmc_sample",
-           "dsmc_hot", "synth_solve", "dig_correct", "dsmc_num_particles", "dsmc_get_particles",
+           "dsmc_hot", "synth_solve", "dsmc_synth_reuse", "dig_correct", "dsmc_num_particles", "dsmc_get_particles",
            "dsmc_set_particles", "dsmc_get_accumulators", "dsmc_get_sgmax", "dsmc_set_sgmax",
            "dsmc_get_counters", "dsmc_set_counters", "dsmc_get_stats", "dsmc_get_wall_tally",
            "dsmc_get_constants", "synth_solve_noalloc", "dsmc_batch_workspace_size", "dsmc_batch_init",
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True):
         "dsmc_sample": ([H, P, ctypes.c_int], ctypes.c_int),
         "dsmc_hot": ([H, P, P, P, P], ctypes.c_int),
         "synth_solve": ([H, P, P, P, P, P], ctypes.c_int),
+        "dsmc_synth_reuse": ([H, ctypes.c_int], ctypes.c_int),
         "dig_correct": ([H, P], ctypes.c_int),
         "dsmc_num_particles": ([H, P], ctypes.c_int),
         "dsmc_get_particles": ([H, P, P, P, P, P, P, P, I64, P], ctypes.c_int),
@@ -253,6 +254,10 @@ class Dsmc:
         self._check(rc, allow=allow)
         self.last_synth_status = rc
         return out, it.value, res.value
+
+    def synth_reuse(self, on: bool = True):
+        """2D: let each synth_solve start from the previous call's factorisation."""
+        self._check(load().dsmc_synth_reuse(self._h, 1 if on else 0))
 
     def launch_config(self) -> int:
         """Warps (cells) per CTA of the FP32 fused step chosen by the tuner."""

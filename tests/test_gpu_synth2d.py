@@ -166,3 +166,22 @@ def test_full_size_cavity_solution_satisfies_the_oracle_equations(nx, ny):
         np.testing.assert_allclose(O[ring, k], d[ring, col], rtol=0, atol=1e-12)
     corners = [0, nx - 1, nx * (ny - 1), nx * ny - 1]
     np.testing.assert_allclose(O[corners, 0], d[corners, F_RHO], rtol=0, atol=1e-12)
+
+
+def test_factorisation_reused_across_solves_gives_the_same_solution():
+    """dsmc_synth_reuse: a solve of another state that starts from the
+    previous solve's factorisation converges to the solution a fresh solve
+    finds (to the tolerance); a handle without the 2D solve refuses it."""
+    nx, ny = 24, 20
+    cfg = _cfg(nx, ny, synth_tol=1e-10)
+    d1, h1 = _smooth(nx, ny, seed=1)
+    d2, h2 = _smooth(nx, ny, seed=2, hot_amp=2e-3)
+    g = _gpu(cfg)
+    g.synth_reuse(True)
+    g.synth_solve(_dev(d1), _dev(h1))
+    out_r, it_r, res_r = g.synth_solve(_dev(d2), _dev(h2))
+    out_f, it_f, res_f = _gpu(cfg).synth_solve(_dev(d2), _dev(h2))
+    assert res_r < 1e-9 and res_f < 1e-9
+    np.testing.assert_allclose(out_r.cpu().numpy(), out_f.cpu().numpy(), rtol=0, atol=1e-8)
+    with pytest.raises(RuntimeError):
+        _gpu(W.fourier_1d(precision="fp64")).synth_reuse(True)
