@@ -114,8 +114,8 @@ typedef struct dsmc_config {
   int32_t mesh;
   /* 1: reserve workspace for the 2D synthetic solve of a single box case
    * (synth_solve on dim 2; min(nx, ny) <= 500).  Its banded factorisation
-   * takes about 8 N (20 m + 140) bytes, N = 5 nx ny unknowns,
-   * m = min(nx, ny) (14 MB at 24 x 24, 0.86 GB at 100 x 100); 0 leaves it
+   * takes about 8 N (20 m + 158) bytes, N = 5 nx ny unknowns,
+   * m = min(nx, ny) (15 MB at 24 x 24, 0.86 GB at 100 x 100); 0 leaves it
    * out (synth_solve on a 2D handle then returns DSMC_ERR_ARG). */
   int32_t synth2d;
   double r_in, r_out, stretch;

@@ -51,6 +51,7 @@ constexpr int S2_PNL_NT = 512;    // the panel factorisation
 constexpr int S2_NREF = 1;        // refinement sweeps after a fresh factorisation
 constexpr int S2_NREF_REUSE = 3;  // refinement sweeps when an earlier factorisation is reused
 constexpr int S2_SMEM_CAP = 200 * 1024;
+constexpr int S2_SMAP = 256;  // ints of a panel's row maps (k_s2_sprep, k_s2_spush)
 constexpr size_t S2_DF_SMEM_CAP = 200 * 1024;  // rows of the data-flow substitution per CTA (4 copies of 32 floats a block)
 
 // Panel width nb and trailing columns per CTA cb (4: enough CTAs to fill the
@@ -76,7 +77,8 @@ struct S2Work {
   int32_t* piv;
   float* q;  // 4 FP32 vectors of N: the clustered substitution's ping-pong right-hand sides
   float* inv;     // per panel: the inverses of its L11 and U11 triangles (2 x 32 x 32)
-  int32_t* smap;  // per panel: its interchanges as a map of rows (128 entries, k_s2_sprep)
+  float* mh;      // per panel k: inv(L11_k) times panel k - 1's multipliers of its head rows (32 x 32)
+  int32_t* smap;  // per panel: its interchanges as maps of rows (S2_SMAP entries, k_s2_sprep, k_s2_spush)
   int nb, cb;
 };
 
@@ -91,7 +93,7 @@ inline size_t s2_doubles(const s2::Grid& g) {
   const size_t jc = round32((size_t)g.n * s2::NSTENCIL * s2::NV * s2::NV);
   const size_t nk = (N + bl.nb - 1) / bl.nb;
   // AB, Lp, ud, piv, q, inv, smap
-  const size_t f32 = (size_t)g.ld * N + s2_lp_floats(g, bl.nb) + N + N + 4 * N + 2048 * nk + 128 * nk;
+  const size_t f32 = (size_t)g.ld * N + s2_lp_floats(g, bl.nb) + N + N + 4 * N + 3072 * nk + S2_SMAP * nk;
   return 13 * vec + 32 + jc + round32((f32 + 1) / 2) + 32;
 }
 
@@ -122,6 +124,8 @@ S2Work s2_carve(const s2::Grid& g, double* w) {
   f += 4 * (size_t)g.N;
   s.inv = f;
   f += 2048 * (size_t)((g.N + bl.nb - 1) / bl.nb);
+  s.mh = f;
+  f += 1024 * (size_t)((g.N + bl.nb - 1) / bl.nb);
   s.smap = reinterpret_cast<int32_t*>(f);
   s.nb = bl.nb;
   s.cb = bl.cb;
@@ -1091,9 +1095,9 @@ __global__ void __launch_bounds__(SC_NT) k_s2_subst_cl(const s2::Grid g, S2Work 
 // k_s2_subst_df): the inverses of the panel's unit-lower L11 and upper U11
 // triangles (sc_tri_row / sc_tri_inverse, row-major 32 x 32 at inv + 2048 k
 // and inv + 2048 k + 1024), and the panel's interchanges as a map of rows:
-// smap[128 k + i], i < 32, the row whose value ends at head position k0 + i
-// (k0 + i itself past the panel's width); smap[128 k + 32 + q] and
-// smap[128 k + 64 + q], q < smap[128 k + 96], the rows past the head whose
+// smap[S k + i], i < 32 (S = S2_SMAP), the row whose value ends at head
+// position k0 + i (k0 + i itself past the panel's width); smap[S k + 32 + q]
+// and smap[S k + 64 + q], q < smap[S k + 96], the rows past the head whose
 // value changes (ascending) and the head position each takes it from.
 // ---------------------------------------------------------------------------
 constexpr int SP_WPB = 4;  // warps (panels) per CTA of k_s2_sprep
@@ -1134,7 +1138,7 @@ __global__ void __launch_bounds__(SP_WPB * 32) k_s2_sprep(const s2::Grid g, S2Wo
         val[b] = t;
       }
     }
-    int32_t* sm = w.smap + (size_t)k * 128;
+    int32_t* sm = w.smap + (size_t)k * S2_SMAP;
     for (int i = 0; i < 32; ++i) sm[i] = k0 + i;
     int ntail = 0;
     for (int q = 0; q < nt; ++q) {
@@ -1156,6 +1160,74 @@ __global__ void __launch_bounds__(SP_WPB * 32) k_s2_sprep(const s2::Grid g, S2Wo
   }
 }
 
+// The rows each head of the data-flow substitution needs, a warp per panel
+// k (after k_s2_sprep): the head position i < wd takes the value, after
+// step k - 1, of row h_i = smap[S k + i], and the tail entry q that of head
+// position t_q = smap[S k + 64 + q]; both follow from the value after step
+// k - 2 of the row that panel k - 1's interchanges move there,
+// smap[S k + 128 + d] (d = i, or 32 + q; -1 where there is none).  Those of
+// them that step k - 2 updates (rows of its window) are sent to the head by
+// their owners (bit d of smap[S k + 192 + d / 32]; smap[S k + 194] of them);
+// the others still hold their input.
+__global__ void __launch_bounds__(SP_WPB * 32) k_s2_spush(const s2::Grid g, S2Work w) {
+  __shared__ float lb[SP_WPB][32][33];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int nb = w.nb, N = g.N, nk = (N + nb - 1) / nb, ldp = g.kl + nb;
+  const int k = blockIdx.x * SP_WPB + wp;
+  if (k >= nk) return;
+  const int k0 = k * nb, wd = s2::panel_width(g, nb, k0);
+  int32_t* sm = w.smap + (size_t)k * S2_SMAP;
+  const int ntail = sm[96];
+  int rh = lane < wd ? sm[lane] : -1, rt = lane < ntail ? sm[64 + lane] : -1;
+  // mh = inv(L11_k) times panel k - 1's multipliers of the head's rows (row
+  // l: those of row h_l, zero where h_l is past that panel's window): the
+  // head's result is then inv(L11_k) a - mh y_{k-1}
+  {
+    const int p0 = k0 - nb;
+    const bool hin = k > 0 && rh >= 0 && rh - p0 < s2::panel_height(g, nb, p0 > 0 ? p0 : 0);
+    const float* Lk = w.Lp + s2::lp_base(g, nb, p0 > 0 ? p0 : 0);
+#pragma unroll 8
+    for (int jj = 0; jj < 32; ++jj) lb[wp][lane][jj] = hin ? Lk[(size_t)jj * ldp + (rh - p0)] : 0.0f;
+    __syncwarp();
+    float ir[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) ir[l] = w.inv[(size_t)k * 2048 + lane * 32 + l];
+    for (int j = 0; j < 32; ++j) {
+      float m = 0.0f;
+#pragma unroll
+      for (int l = 0; l < 32; ++l) m += ir[l] * lb[wp][l][j];
+      w.mh[(size_t)k * 1024 + lane * 32 + j] = m;
+    }
+  }
+  if (k > 0) {
+    const int32_t* smp = sm - S2_SMAP;
+    const int ntp = smp[96];
+    const int td = lane < ntp ? smp[32 + lane] : -1, ts = lane < ntp ? smp[64 + lane] : 0;
+    int sh = rh, st = rt;
+    for (int q = 0; q < ntp; ++q) {
+      const int d = __shfl_sync(0xffffffffu, td, q), sv = __shfl_sync(0xffffffffu, ts, q);
+      if (rh >= 0 && d == rh) sh = sv;
+      if (rt >= 0 && d == rt) st = sv;
+    }
+    rh = sh;
+    rt = st;
+  }
+  bool ph = false, pt = false;
+  if (k >= 2) {
+    const int p0 = k0 - 2 * nb, lo = p0 + nb, hi = p0 + s2::panel_height(g, nb, p0);
+    ph = rh >= lo && rh < hi;
+    pt = rt >= lo && rt < hi;
+  }
+  sm[128 + lane] = rh;
+  sm[160 + lane] = rt;
+  const unsigned mh = __ballot_sync(0xffffffffu, ph), mt = __ballot_sync(0xffffffffu, pt);
+  if (lane == 0) {
+    sm[192] = (int)mh;
+    sm[193] = (int)mt;
+    sm[194] = __popc(mh) + __popc(mt);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // The substitutions as a data flow across a cluster of DF_C CTAs, with no
 // cluster-wide barrier per panel.  Rows are owned by 32-row block: block b
@@ -1165,24 +1237,27 @@ __global__ void __launch_bounds__(SP_WPB * 32) k_s2_sprep(const s2::Grid g, S2Wo
 // still needed (rows outside a step's window keep their value in both).
 //
 // Warp 0 of the owner of panel k's head block computes the head's values
-// itself, from the other copy and the previous step's result (the previous
-// panel's multipliers for the head's source rows), applies the inverse of
+// itself: each source row's value after step k - 2 (sent into a buffer of
+// the head's CTA by the row's owner, by an asynchronous store that completes
+// the buffer's mbarrier phase, as soon as step k - 2 has updated it; rows
+// that step did not reach still hold their input) less the previous panel's
+// multipliers times the previous step's result.  It applies the inverse of
 // the panel's triangle and sends the 32 results (two right-hand sides) into
 // a ring of DF_S slots in every CTA by asynchronous stores, which complete
 // the slot's mbarrier phase there; with them go the head values that the
 // panel's interchanges move to rows below the head, computed the same way.
-// Warps 1 .. DF_UW of every CTA take each step's result from the ring and
-// update their CTA's rows of the step's window; warp DF_UW + 1 arms each
-// slot's next phase and, after the update warps' barrier, publishes the
-// number of steps done (release).  Warp 0 reads other CTAs' rows only after
-// waiting (acquire) until that count covers the step the values come from,
-// one step ahead of their use, and writes a slot only when every CTA has
-// finished the slot's previous step.  Each wait gives up after DF_WAIT_NS
-// (the kernel then records the timeout in the work area, drains the slots
-// still armed and every CTA leaves at the next cluster barrier).
+// Warps 1 .. DF_UW of every CTA take each step's result from the ring,
+// update their CTA's rows of the step's window and send the new values a
+// later head needs; warp DF_UW + 1 arms each slot's next phase and, after the
+// update warps' barrier, publishes the number of steps done (release).  Warp
+// 0 writes a ring slot only once every CTA has finished the slot's previous
+// step, and (backward) reads its own rows once this CTA's count covers them.
+// Each wait gives up after DF_WAIT_NS (the kernel then records the timeout in
+// the work area, drains the buffers still armed and every CTA leaves at the
+// next cluster barrier).
 //
-// The arithmetic of each row and head value, and its order, are those of
-// k_s2_subst_cl; forward, then (after one cluster barrier) backward.
+// Each row takes the operations of k_s2_subst_cl (the dot products in four
+// partial sums); forward, then (after one cluster barrier) backward.
 // ---------------------------------------------------------------------------
 constexpr int DF_C = 8;                  // CTAs of the cluster
 constexpr int DF_UW = 8;                 // update warps per CTA
@@ -1238,6 +1313,23 @@ __device__ __forceinline__ void df_st_async4(unsigned addr, float4 v, unsigned m
   asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
                "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(mbar)
                : "memory");
+}
+
+__device__ __forceinline__ void df_st_async2(unsigned addr, float a, float b, unsigned mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+               "f"(a), "f"(b), "r"(mbar)
+               : "memory");
+}
+
+// a count in this CTA's shared memory, published and read at CTA scope
+__device__ __forceinline__ void df_st_release_cta(const unsigned* p, unsigned v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(df_smem_addr(p)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned df_ld_acquire_cta(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(df_smem_addr(p)) : "memory");
+  return v;
 }
 
 // this CTA's arrival on its mbarrier, expecting `bytes` of asynchronous stores in the phase
@@ -1303,6 +1395,28 @@ __device__ __forceinline__ bool df_update_bar_any(bool bad) {
   return r != 0;
 }
 
+// *p where pred holds, else 0, as one predicated load: nothing waits for the
+// value until it is used (a select after the load would stall the warp for
+// the memory round trip at once)
+__device__ __forceinline__ float df_ldg_or0(const float* p, bool pred) {
+  float v;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t"
+      "setp.ne.u32 q, %2, 0;\n\t"
+      "mov.f32 %0, 0f00000000;\n\t"
+      "@q ld.global.nc.f32 %0, [%1];\n\t}"
+      : "=f"(v)
+      : "l"(p), "r"((unsigned)pred));
+  return v;
+}
+
+// *p issued here (an asm load the compiler does not move down to its use)
+__device__ __forceinline__ int df_ldg_s32(const int32_t* p) {
+  int v;
+  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
 // acc0 = l . y[0:32], acc1 = l . y[32:64] (y 16-byte aligned; four partial
 // sums each, for a short dependency chain)
 __device__ __forceinline__ void df_dot2(const float (&l)[32], const float* y, float& acc0, float& acc1) {
@@ -1333,7 +1447,13 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   __shared__ __align__(16) float stage[128];  // warp 0's result before it is sent
   __shared__ __align__(16) float hsol[64];    // warp 0: the head's values before the triangle solve
   __shared__ __align__(8) uint64_t full[DF_S];
+  // this CTA's forward heads k = rank + DF_C u: the values of the rows they
+  // need after step k - 2, sent by the rows' owners (entry d: rhs 0, rhs 1 at
+  // 2 d, 2 d + 1), in buffer u % 2, completed on hbar[u % 2]
+  __shared__ __align__(16) float hbuf[2][128];
+  __shared__ __align__(8) uint64_t hbar[2];
   __shared__ unsigned done;       // steps this CTA's update warps have finished
+  __shared__ unsigned done_l;     // the same, published at CTA scope
   __shared__ unsigned abort_all;  // set in every CTA once a wait gave up
   float* const As = reinterpret_cast<float*>(s2_smem);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1364,6 +1484,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   };
   if (tid == 0) {
     done = 0;
+    done_l = 0;
     abort_all = 0;
   }
   // bytes a step's result brings into each CTA's ring slot
@@ -1371,6 +1492,11 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   if (tid < DF_S) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(df_smem_addr(&full[tid])) : "memory");
     if (tid < 2 * nk) df_arm(&full[tid], step_bytes(tid));
+  }
+  if (tid < 2) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(df_smem_addr(&hbar[tid])) : "memory");
+    const int k = (int)rank + DF_C * tid;
+    if (k < nk) df_arm(&hbar[tid], 8u * (unsigned)w.smap[(size_t)k * S2_SMAP + 194]);
   }
   fill(b0, b1);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1398,10 +1524,19 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   };
   // the publishing warp's lane 0: the first step whose slot it has not consumed
   int tnext = 0;
+  // warp 0: how many of this CTA's head buffers it has consumed
+  int hcons = 0;
   // after a cluster barrier that ends the sends: wait (briefly) for the slots
   // armed but not consumed, so that no asynchronous store is still on its way
   // into this CTA when it exits (only after a wait gave up)
   auto drain = [&]() {
+    if (warp == 0 && lane == 0) {
+      for (int u = hcons; u < hcons + 2 && (int)rank + DF_C * u < nk; ++u) {
+        const unsigned long long t0 = df_clock_ns();
+        while (!df_try_wait(&hbar[u & 1], (unsigned)(u >> 1) & 1u))
+          if (df_clock_ns() - t0 > DF_DRAIN_NS) break;
+      }
+    }
     if (warp == DF_UW + 1 && lane == 0) {
       const int tend = tnext + DF_S < 2 * nk ? tnext + DF_S : 2 * nk;
       for (int t = tnext; t < tend; ++t) {
@@ -1413,77 +1548,88 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   };
   // ---- forward: L y = P b ----
   if (warp == 0) {
-    for (int k = (int)rank; k < nk; k += DF_C) {
+    for (int k = (int)rank, u = 0; k < nk; k += DF_C, ++u) {
       const int k0 = k * nb, wd = s2::panel_width(g, nb, k0);
-      const int32_t* sm = w.smap + (size_t)k * 128;
+      const int32_t* sm = w.smap + (size_t)k * S2_SMAP;
       // lane i follows two rows to their values after step k - 1: hs, whose
       // value ends at head position k0 + i, and (i < ntail) tp, the head
       // position whose value the interchanges move to the i-th row of the
-      // list past the head
+      // list past the head; each from the value after step k - 2 of the row
+      // panel k - 1's interchanges move there (sent by its owner if step
+      // k - 2 updated it, else its input)
       const int hs = sm[lane];
-      const int ntail = sm[96];
-      const int tp = lane < ntail ? sm[64 + lane] : -1;
+      const int ntail = sm[96], tpl = sm[64 + lane];
+      const int tp = lane < ntail ? tpl : -1;
+      const int rh = sm[128 + lane], rt = sm[160 + lane];
+      // the byte count of this buffer's next use (loaded now: the arm after the
+      // wait must not wait for memory)
+      const unsigned nnext = k + 2 * DF_C < nk ? 8u * (unsigned)w.smap[(size_t)(k + 2 * DF_C) * S2_SMAP + 194] : 0u;
+      const bool sh = (((unsigned)sm[192] >> lane) & 1u) != 0, st = (((unsigned)sm[193] >> lane) & 1u) != 0;
+      float a0 = 0.0f, a1 = 0.0f, c0 = 0.0f, c1 = 0.0f;
+      if (lane < wd && !sh) {
+        a0 = (float)__ldcg(b0 + rh);
+        a1 = (float)__ldcg(b1 + rh);
+      }
+      if (tp >= 0 && !st) {
+        c0 = (float)__ldcg(b0 + rt);
+        c1 = (float)__ldcg(b1 + rt);
+      }
       float invr[32];
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) invr[jj] = __ldg(w.inv + (size_t)k * 2048 + lane * 32 + jj);
-      // a row's value after step k - 1: its source under panel k - 1's
-      // interchanges, less that panel's multipliers (the row's place in its
-      // window) times y_{k-1}
-      int hsrc = hs, tsrc = tp;
-      bool hin = false, tin = false;
-      float lh[32], lt[32];
+      // row `lane` of mh (the previous panel's multipliers of the head's rows,
+      // through the triangle's inverse), and that panel's multipliers of tp
+      // (a head position of panel k: inside panel k - 1's window)
+      bool tin = false;
+      float mrow[32], lt[32];
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) lh[jj] = lt[jj] = 0.0f;
+      for (int jj = 0; jj < 32; ++jj) {
+        mrow[jj] = __ldg(w.mh + (size_t)k * 1024 + lane * 32 + jj);
+        lt[jj] = 0.0f;
+      }
       if (k > 0) {
-        const int p0 = k0 - nb, Hp = s2::panel_height(g, nb, p0);
+        const int p0 = k0 - nb;
         const float* Lk = w.Lp + s2::lp_base(g, nb, p0);
-        hin = lane < wd && hs - p0 < Hp;
-        tin = tp >= 0;  // a head position of panel k: inside panel k - 1's window
-        if (hin) {
-#pragma unroll
-          for (int jj = 0; jj < 32; ++jj) lh[jj] = __ldg(Lk + (size_t)jj * ldp + (hs - p0));
-        }
+        tin = tp >= 0;
         if (tin) {
 #pragma unroll
           for (int jj = 0; jj < 32; ++jj) lt[jj] = __ldg(Lk + (size_t)jj * ldp + (tp - p0));
         }
-        const int32_t* smp = sm - 128;
-        const int ntp = smp[96];
-        const int td = lane < ntp ? smp[32 + lane] : -1, ts = lane < ntp ? smp[64 + lane] : 0;
-        for (int q = 0; q < ntp; ++q) {
-          const int d = __shfl_sync(0xffffffffu, td, q), sv = __shfl_sync(0xffffffffu, ts, q);
-          if (d == hs) hsrc = sv;
-          if (d == tp) tsrc = sv;
+      }
+      // the values sent by their owners (slot u % 2 of this CTA's head buffers)
+      bool ok = df_wait_slot(&hbar[u & 1], (unsigned)(u >> 1) & 1u);
+      if (ok) {
+        if (lane < wd && sh) {
+          a0 = hbuf[u & 1][2 * lane];
+          a1 = hbuf[u & 1][2 * lane + 1];
+        }
+        if (tp >= 0 && st) {
+          c0 = hbuf[u & 1][64 + 2 * lane];
+          c1 = hbuf[u & 1][64 + 2 * lane + 1];
         }
       }
-      // the values after step k - 2 (copy (k - 1) % 2) once their owners have finished it
-      bool ok = true;
-      const unsigned need = k >= 2 ? (unsigned)(k - 1) : 0u;
-      if (lane < wd && need) ok = df_wait_count(df_mapa(&done, owner(hsrc)), need);
-      if (ok && tp >= 0 && need) ok = df_wait_count(df_mapa(&done, owner(tsrc)), need);
-      const int par = (k + 1) & 1;
-      float a0 = 0.0f, a1 = 0.0f, c0 = 0.0f, c1 = 0.0f;
-      if (ok && lane < wd) {
-        a0 = df_ld_remote(df_mapa(aloc(par, 0, hsrc), owner(hsrc)));
-        a1 = df_ld_remote(df_mapa(aloc(par, 1, hsrc), owner(hsrc)));
+      __syncwarp();
+      if (lane == 0 && ok) {
+        hcons = u + 1;
+        if (k + 2 * DF_C < nk) df_arm(&hbar[u & 1], nnext);
       }
-      if (ok && tp >= 0) {
-        c0 = df_ld_remote(df_mapa(aloc(par, 0, tsrc), owner(tsrc)));
-        c1 = df_ld_remote(df_mapa(aloc(par, 1, tsrc), owner(tsrc)));
-      }
+      // inv(L11) times the head's values after step k - 2, before the
+      // previous step's result is there
+      hsol[lane] = a0;
+      hsol[32 + lane] = a1;
+      __syncwarp();
+      float y0, y1;
+      df_dot2(invr, hsol, y0, y1);
       if (k > 0 && ok) {
         const int t = k - 1;
         ok = df_wait_slot(&full[t % DF_S], (unsigned)(t / DF_S) & 1u);
         if (ok) {
           const float* yp = ring[t % DF_S];
-          if (hin) {
-            float acc0 = 0.0f, acc1 = 0.0f;
-            df_dot2(lh, yp, acc0, acc1);
-            a0 -= acc0;
-            a1 -= acc1;
-          }
+          float acc0, acc1;
+          df_dot2(mrow, yp, acc0, acc1);
+          y0 -= acc0;
+          y1 -= acc1;
           if (tin) {
-            float acc0 = 0.0f, acc1 = 0.0f;
             df_dot2(lt, yp, acc0, acc1);
             c0 -= acc0;
             c1 -= acc1;
@@ -1494,12 +1640,6 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         if (lane == 0) fail();
         break;
       }
-      // y = (inverse of L11) times the head's values
-      hsol[lane] = a0;
-      hsol[32 + lane] = a1;
-      __syncwarp();
-      float y0, y1;
-      df_dot2(invr, hsol, y0, y1);
       if (lane >= wd) y0 = y1 = 0.0f;
       stage[lane] = y0;
       stage[32 + lane] = y1;
@@ -1530,7 +1670,10 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         }
       }
       if (df_update_bar_any(bad)) break;
-      if (lane == 0) df_st_release(df_mapa(&done, rank), (unsigned)(s + 1));
+      if (lane == 0) {
+        df_st_release_cta(&done_l, (unsigned)(s + 1));
+        df_st_release(df_mapa(&done, rank), (unsigned)(s + 1));
+      }
     }
   } else {
     // update warps: warp u takes the u-th, (u + DF_UW)-th, ... of this CTA's blocks
@@ -1551,17 +1694,32 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       const int r = 32 * b + lane - k0;
       const float* Lk = w.Lp + s2::lp_base(g, nb, k0);
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) lr[jj] = (b >= 0 && r < H && jj < wd) ? __ldg(Lk + (size_t)jj * ldp + r) : 0.0f;
+      for (int jj = 0; jj < 32; ++jj) lr[jj] = df_ldg_or0(Lk + (size_t)jj * ldp + r, b >= 0 && r < H && jj < wd);
     };
     // the step's interchanges past the head: entry `lane` of its list
+    // step s's rows past the head that take a head value (entry `lane`), and
+    // the rows whose values after step s the head of step s + 2 needs
+    // (entries lane and 32 + lane, with their bits of the send masks)
     struct Tail {
-      int n, d;
+      int n, d, r0, r1;
+      unsigned m0, m1;
     };
     auto load_tail = [&](int s) -> Tail {
-      const int32_t* sm = w.smap + (size_t)s * 128;
+      const int32_t* sm = w.smap + (size_t)s * S2_SMAP;
       Tail t;
-      t.n = __ldg(sm + 96);
-      t.d = lane < t.n ? __ldg(sm + 32 + lane) : -1;
+      // loaded as they are (entries past the count are masked where used: a
+      // select here would stall the warp for the memory round trip)
+      t.n = df_ldg_s32(sm + 96);
+      t.d = df_ldg_s32(sm + 32 + lane);
+      t.r0 = t.r1 = -1;
+      t.m0 = t.m1 = 0u;
+      if (s + 2 < nk) {
+        const int32_t* sp = sm + 2 * S2_SMAP;
+        t.r0 = df_ldg_s32(sp + 128 + lane);
+        t.r1 = df_ldg_s32(sp + 160 + lane);
+        t.m0 = (unsigned)df_ldg_s32(sp + 192);
+        t.m1 = (unsigned)df_ldg_s32(sp + 193);
+      }
       return t;
     };
     // step s with this warp's first block b and its multipliers lr; false once a wait gave up
@@ -1569,19 +1727,36 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       const int k0 = s * nb, wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
       const int bl = (k0 + H - 1) >> 5;
       const float* y = ring[s % DF_S];
-      bool bad = !df_wait_slot(&full[s % DF_S], (unsigned)(s / DF_S) & 1u);
-      for (int b = bfirst; !bad && b >= 0 && b <= bl; b += DF_UW * DF_C) {
-        if (b != bfirst) load_l(lr, s, b);  // a window wider than DF_UW x DF_C blocks
+      // where the new values go: the head of step s + 2 (its owner's buffer u % 2)
+      const unsigned ho = (unsigned)((s + 2) % DF_C);
+      const int hslot = ((s + 2) / DF_C) & 1;
+      // row R's entry in the step's list of rows past the head that take a
+      // head value (-1: none; the value came with the step's result), and the
+      // entries of the head's list that row R's new value serves (masks over
+      // d and 32 + d); found before the wait, for the first block
+      auto lists = [&](int b, int& qi, unsigned& pm0, unsigned& pm1) {
         const int R = 32 * b + lane;
-        // row R's entry in the step's list of rows past the head that take a
-        // head value (-1: none; the value came with the step's result)
-        int qi = -1;
+        qi = -1;
         for (unsigned m = __ballot_sync(0xffffffffu, lane < tl.n && (tl.d >> 5) == b); m; m &= m - 1) {
           const int q = __ffs(m) - 1;
           if (__shfl_sync(0xffffffffu, tl.d, q) == R) qi = q;
         }
-        if (R - k0 < H) {
-          float v0, v1;
+        pm0 = __ballot_sync(0xffffffffu, ((tl.m0 >> lane) & 1u) && (tl.r0 >> 5) == b);
+        pm1 = __ballot_sync(0xffffffffu, ((tl.m1 >> lane) & 1u) && (tl.r1 >> 5) == b);
+      };
+      int qi = -1;
+      unsigned pm0 = 0u, pm1 = 0u;
+      if (bfirst >= 0 && bfirst <= bl) lists(bfirst, qi, pm0, pm1);
+      bool bad = !df_wait_slot(&full[s % DF_S], (unsigned)(s / DF_S) & 1u);
+      for (int b = bfirst; !bad && b >= 0 && b <= bl; b += DF_UW * DF_C) {
+        if (b != bfirst) {  // a window wider than DF_UW x DF_C blocks
+          load_l(lr, s, b);
+          lists(b, qi, pm0, pm1);
+        }
+        const int R = 32 * b + lane;
+        const bool in = R - k0 < H;
+        float v0 = 0.0f, v1 = 0.0f;
+        if (in) {
           const int par = s & 1;
           if (qi < 0) {
             v0 = *aloc(par, 0, R);
@@ -1592,8 +1767,21 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
           }
           float acc0 = 0.0f, acc1 = 0.0f;
           df_dot2(lr, y, acc0, acc1);
-          *aloc(par ^ 1, 0, R) = v0 - acc0;
-          *aloc(par ^ 1, 1, R) = v1 - acc1;
+          v0 -= acc0;
+          v1 -= acc1;
+          *aloc(par ^ 1, 0, R) = v0;
+          *aloc(par ^ 1, 1, R) = v1;
+        }
+        // send the new values that the head of step s + 2 takes from this block
+        for (unsigned m = pm0; m; m &= m - 1) {
+          const int q = __ffs(m) - 1;
+          if (__shfl_sync(0xffffffffu, tl.r0, q) == R && in)
+            df_st_async2(df_mapa(&hbuf[hslot][2 * q], ho), v0, v1, df_mapa(&hbar[hslot], ho));
+        }
+        for (unsigned m = pm1; m; m &= m - 1) {
+          const int q = __ffs(m) - 1;
+          if (__shfl_sync(0xffffffffu, tl.r1, q) == R && in)
+            df_st_async2(df_mapa(&hbuf[hslot][64 + 2 * q], ho), v0, v1, df_mapa(&hbar[hslot], ho));
         }
       }
       if (df_update_bar_any(bad)) {
@@ -1646,7 +1834,15 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) ur[jj] = (lane < wd && jj < wdn) ? s2::umul(g, w.AB, R, kn0 + jj) : 0.0f;
       bool ok = true;
-      if (it >= 2) ok = df_wait_count(df_mapa(&done, rank), (unsigned)(t - 1));
+      if (it >= 2 && df_ld_acquire_cta(&done_l) < (unsigned)(t - 1)) {
+        // this CTA's update warps finish step t - 2 (a count at CTA scope)
+        const unsigned long long t0 = df_clock_ns();
+        while (df_ld_acquire_cta(&done_l) < (unsigned)(t - 1))
+          if (df_clock_ns() - t0 > DF_WAIT_NS) {
+            ok = false;
+            break;
+          }
+      }
       float a0 = 0.0f, a1 = 0.0f;
       if (lane < wd) {
         a0 = *aloc((it + 1) & 1, 0, R);
@@ -1695,7 +1891,10 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         }
       }
       if (df_update_bar_any(bad)) break;
-      if (lane == 0) df_st_release(df_mapa(&done, rank), (unsigned)(t + 1));
+      if (lane == 0) {
+        df_st_release_cta(&done_l, (unsigned)(t + 1));
+        df_st_release(df_mapa(&done, rank), (unsigned)(t + 1));
+      }
     }
   } else {
     const int u = warp - 1;
@@ -1712,7 +1911,9 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
       const int R = 32 * b + lane;
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) ur[jj] = (b >= 0 && R >= lo && jj < wd) ? s2::umul(g, w.AB, R, k0 + jj) : 0.0f;
+      for (int jj = 0; jj < 32; ++jj)
+        ur[jj] = df_ldg_or0(w.AB + s2::band_at(g, R, k0 + jj),
+                            b >= 0 && R >= lo && jj < wd && s2::in_band(g, R, k0 + jj));  // U(R, k0 + jj)
     };
     auto step = [&](int it, int bfirst, float (&ur)[32]) -> bool {
       const int t = nk + it, k = nk - 1 - it, k0 = k * nb;
@@ -2053,6 +2254,7 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
       }
       const int nk = (g.N + nb - 1) / nb;
       k_s2_sprep<<<(nk + SP_WPB - 1) / SP_WPB, SP_WPB * 32, 0, st>>>(g, w);
+      k_s2_spush<<<(nk + SP_WPB - 1) / SP_WPB, SP_WPB * 32, 0, st>>>(g, w);
     }
     const int nsweep = refactor ? S2_NREF : S2_NREF_REUSE;
     k_s2_prep<<<vec_grid, nt, 0, st>>>(g, w);
