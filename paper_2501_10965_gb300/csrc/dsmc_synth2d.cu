@@ -1246,10 +1246,12 @@ __global__ void __launch_bounds__(SP_WPB * 32) k_s2_spush(const s2::Grid g, S2Wo
 // a ring of DF_S slots in every CTA by asynchronous stores, which complete
 // the slot's mbarrier phase there; with them go the head values that the
 // panel's interchanges move to rows below the head, computed the same way.
-// Warps 1 .. DF_UW of every CTA take each step's result from the ring,
-// update their CTA's rows of the step's window and send the new values a
-// later head needs; warp DF_UW + 1 arms each slot's next phase and, after the
-// update warps' barrier, publishes the number of steps done (release).  Warp
+// Warps 1 .. DF_UW of every CTA, in two groups that take alternate steps
+// (a group waits, on a CTA-local mbarrier, for the other group's previous
+// step), take each step's result from the ring, update their CTA's rows of
+// the step's window and send the new values a later head needs; warp
+// DF_UW + 1 arms each slot's next phase and, once the step's group has
+// finished, publishes the number of steps done (release).  Warp
 // 0 writes a ring slot only once every CTA has finished the slot's previous
 // step, and (backward) reads its own rows once this CTA's count covers them.
 // Each wait gives up after DF_WAIT_NS (the kernel then records the timeout in
@@ -1260,13 +1262,14 @@ __global__ void __launch_bounds__(SP_WPB * 32) k_s2_spush(const s2::Grid g, S2Wo
 // partial sums); forward, then (after one cluster barrier) backward.
 // ---------------------------------------------------------------------------
 constexpr int DF_C = 8;                  // CTAs of the cluster
-constexpr int DF_UW = 8;                 // update warps per CTA
+constexpr int DF_UWG = 5;                // update warps per group
+constexpr int DF_UW = 2 * DF_UWG;        // update warps per CTA: group 0 takes the even steps, group 1 the odd
 constexpr int DF_NT = 32 * (2 + DF_UW);  // warp 0 solves the heads, warp DF_UW + 1 publishes
 constexpr int DF_S = 32;                 // ring slots (steps in flight)
 constexpr int DF_SEND_LANES = 32 / DF_C;  // lanes of warp 0 that write one CTA's ring slot
 constexpr unsigned long long DF_WAIT_NS = 500000000ull;  // 0.5 s
 constexpr unsigned long long DF_DRAIN_NS = 1000000ull;   // 1 ms
-constexpr unsigned DF_SUSPEND_NS = 4000;                  // longest suspension of one wait test
+constexpr unsigned DF_SUSPEND_NS = 2000;                  // longest suspension of one wait test
 
 __device__ __forceinline__ unsigned long long df_clock_ns() {
   unsigned long long t;
@@ -1380,21 +1383,6 @@ __device__ __forceinline__ bool df_wait_count(unsigned addr, unsigned need, unsi
   return true;
 }
 
-// barrier 1 for the update warps and the publishing warp, returning whether
-// any of them has `bad` set
-__device__ __forceinline__ bool df_update_bar_any(bool bad) {
-  unsigned r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "barrier.cta.red.or.pred q, 1, %2, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"((unsigned)bad), "r"(32 * (DF_UW + 1))
-      : "memory");
-  return r != 0;
-}
-
 // *p where pred holds, else 0, as one predicated load: nothing waits for the
 // value until it is used (a select after the load would stall the warp for
 // the memory round trip at once)
@@ -1452,6 +1440,9 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   // 2 d, 2 d + 1), in buffer u % 2, completed on hbar[u % 2]
   __shared__ __align__(16) float hbuf[2][128];
   __shared__ __align__(8) uint64_t hbar[2];
+  // gdone[t % 4]: the update warps of step t's group have finished it (a
+  // phase per use, DF_UWG arrivals)
+  __shared__ __align__(8) uint64_t gdone[4];
   __shared__ unsigned done;       // steps this CTA's update warps have finished
   __shared__ unsigned done_l;     // the same, published at CTA scope
   __shared__ unsigned abort_all;  // set in every CTA once a wait gave up
@@ -1493,6 +1484,8 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(df_smem_addr(&full[tid])) : "memory");
     if (tid < 2 * nk) df_arm(&full[tid], step_bytes(tid));
   }
+  if (tid < 4)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(df_smem_addr(&gdone[tid])), "r"(DF_UWG) : "memory");
   if (tid < 2) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(df_smem_addr(&hbar[tid])) : "memory");
     const int k = (int)rank + DF_C * tid;
@@ -1657,9 +1650,9 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       }
     }
   } else if (warp == DF_UW + 1) {
-    // publisher: waits for each step's slot and arms its next use, then after
-    // the step's barrier publishes the count of steps done (its release waits
-    // for no loads of its own, unlike the update warps')
+    // publisher: waits for each step's slot and arms its next use, then, once
+    // the step's group has finished it, publishes the count of steps done
+    // (its release waits for no loads of its own, unlike the update warps')
     for (int s = 0; s < nk; ++s) {
       bool bad = false;
       if (lane == 0) {
@@ -1667,25 +1660,33 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         if (!bad) {
           tnext = s + 1;
           if (s + DF_S < 2 * nk) df_arm(&full[s % DF_S], step_bytes(s + DF_S));
+          bad = !df_wait_slot(&gdone[s & 3], (unsigned)(s >> 2) & 1u);
+        }
+        if (!bad) {
+          df_st_release_cta(&done_l, (unsigned)(s + 1));
+          df_st_release(df_mapa(&done, rank), (unsigned)(s + 1));
         }
       }
-      if (df_update_bar_any(bad)) break;
-      if (lane == 0) {
-        df_st_release_cta(&done_l, (unsigned)(s + 1));
-        df_st_release(df_mapa(&done, rank), (unsigned)(s + 1));
-      }
+      if (__shfl_sync(0xffffffffu, (int)bad, 0)) break;
     }
   } else {
-    // update warps: warp u takes the u-th, (u + DF_UW)-th, ... of this CTA's blocks
-    // in each step's window, lane = row in the block; the multipliers and the
-    // interchanges of a step are loaded two steps ahead (two register sets)
-    const int u = warp - 1;
+    // update warps: group grp takes the steps of its parity; its warp u the
+    // u-th, (u + DF_UWG)-th, ... of this CTA's blocks in a step's window,
+    // lane = row in the block; a step's multipliers and interchanges are
+    // loaded when the group's previous step is done (two steps ahead)
+    const int grp = (warp - 1) / DF_UWG, u = (warp - 1) % DF_UWG;
     // this warp's first block of forward step s (rows 32 (s + 1) .. k0 + H - 1), or -1
     auto first_block = [&](int s) -> int {
       const int k0 = s * nb, H = s2::panel_height(g, s2::panel_width(g, nb, k0), k0);
       const int bf = s + 1, bl = (k0 + H - 1) >> 5;
       const int b = bf + (((int)rank - bf) % DF_C + DF_C) % DF_C + u * DF_C;
       return b <= bl ? b : -1;
+    };
+    // this group's arrival once its warps have finished step t (after this
+    // lane's stores)
+    auto finished = [&](int t) {
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(df_smem_addr(&gdone[t & 3])) : "memory");
     };
     // multipliers of step s for this lane's row of block b (zero outside the
     // window and past the panel's width)
@@ -1747,9 +1748,15 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       int qi = -1;
       unsigned pm0 = 0u, pm1 = 0u;
       if (bfirst >= 0 && bfirst <= bl) lists(bfirst, qi, pm0, pm1);
-      bool bad = !df_wait_slot(&full[s % DF_S], (unsigned)(s / DF_S) & 1u);
-      for (int b = bfirst; !bad && b >= 0 && b <= bl; b += DF_UW * DF_C) {
-        if (b != bfirst) {  // a window wider than DF_UW x DF_C blocks
+      bool ok = df_wait_slot(&full[s % DF_S], (unsigned)(s / DF_S) & 1u);
+      // the rows' values after step s - 1: the other group's step
+      if (ok && s >= 1) ok = df_wait_slot(&gdone[(s - 1) & 3], (unsigned)((s - 1) >> 2) & 1u);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) fail();
+        return false;
+      }
+      for (int b = bfirst; b >= 0 && b <= bl; b += DF_UWG * DF_C) {
+        if (b != bfirst) {  // a window wider than DF_UWG x DF_C blocks
           load_l(lr, s, b);
           lists(b, qi, pm0, pm1);
         }
@@ -1784,30 +1791,23 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
             df_st_async2(df_mapa(&hbuf[hslot][64 + 2 * q], ho), v0, v1, df_mapa(&hbar[hslot], ho));
         }
       }
-      if (df_update_bar_any(bad)) {
-        if (tid == 32) fail();
-        return false;
-      }
+      finished(s);
       return true;
     };
-    float lrA[32], lrB[32];
-    int bA = first_block(0), bB = nk > 1 ? first_block(1) : -1;
-    Tail tA = load_tail(0), tB = nk > 1 ? load_tail(1) : Tail{0, -1};
-    load_l(lrA, 0, bA);
-    load_l(lrB, 1, bB);
-    for (int s = 0; s < nk; s += 2) {
-      if (!step(s, bA, lrA, tA)) break;
+    float lr[32];
+    int bc = -1;
+    Tail tc{0, -1, -1, -1, 0u, 0u};
+    if (grp < nk) {
+      bc = first_block(grp);
+      tc = load_tail(grp);
+      load_l(lr, grp, bc);
+    }
+    for (int s = grp; s < nk; s += 2) {
+      if (!step(s, bc, lr, tc)) break;
       if (s + 2 < nk) {
-        bA = first_block(s + 2);
-        tA = load_tail(s + 2);
-        load_l(lrA, s + 2, bA);
-      }
-      if (s + 1 >= nk) break;
-      if (!step(s + 1, bB, lrB, tB)) break;
-      if (s + 3 < nk) {
-        bB = first_block(s + 3);
-        tB = load_tail(s + 3);
-        load_l(lrB, s + 3, bB);
+        bc = first_block(s + 2);
+        tc = load_tail(s + 2);
+        load_l(lr, s + 2, bc);
       }
     }
   }
@@ -1888,16 +1888,18 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         if (!bad) {
           tnext = t + 1;
           if (t + DF_S < 2 * nk) df_arm(&full[t % DF_S], step_bytes(t + DF_S));
+          bad = !df_wait_slot(&gdone[t & 3], (unsigned)(t >> 2) & 1u);
+        }
+        if (!bad) {
+          df_st_release_cta(&done_l, (unsigned)(t + 1));
+          df_st_release(df_mapa(&done, rank), (unsigned)(t + 1));
         }
       }
-      if (df_update_bar_any(bad)) break;
-      if (lane == 0) {
-        df_st_release_cta(&done_l, (unsigned)(t + 1));
-        df_st_release(df_mapa(&done, rank), (unsigned)(t + 1));
-      }
+      if (__shfl_sync(0xffffffffu, (int)bad, 0)) break;
     }
   } else {
-    const int u = warp - 1;
+    // the groups take the backward steps t = nk + it of their parity
+    const int grp = (warp - 1) / DF_UWG, u = (warp - 1) % DF_UWG;
     // rows lo .. k0 - 1 of backward step it (panel k = nk - 1 - it): this warp's first block, or -1
     auto first_block = [&](int it) -> int {
       const int k = nk - 1 - it, k0 = k * nb;
@@ -1905,6 +1907,10 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       const int bf = lo >> 5, bl = k - 1;
       const int b = bf + (((int)rank - bf) % DF_C + DF_C) % DF_C + u * DF_C;
       return b <= bl ? b : -1;
+    };
+    auto finished = [&](int t) {
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(df_smem_addr(&gdone[t & 3])) : "memory");
     };
     auto load_u = [&](float (&ur)[32], int it, int b) {
       const int k = nk - 1 - it, k0 = k * nb, wd = s2::panel_width(g, nb, k0);
@@ -1919,8 +1925,13 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       const int t = nk + it, k = nk - 1 - it, k0 = k * nb;
       const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
       const float* x = ring[t % DF_S];
-      bool bad = !df_wait_slot(&full[t % DF_S], (unsigned)(t / DF_S) & 1u);
-      for (int b = bfirst; !bad && b >= 0 && b <= k - 1; b += DF_UW * DF_C) {
+      bool ok = df_wait_slot(&full[t % DF_S], (unsigned)(t / DF_S) & 1u);
+      if (ok) ok = df_wait_slot(&gdone[(t - 1) & 3], (unsigned)((t - 1) >> 2) & 1u);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) fail();
+        return false;
+      }
+      for (int b = bfirst; b >= 0 && b <= k - 1; b += DF_UWG * DF_C) {
         if (b != bfirst) load_u(ur, it, b);
         const int R = 32 * b + lane;
         if (R >= lo) {
@@ -1932,27 +1943,21 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
           *aloc(par ^ 1, 1, R) = v1 - acc1;
         }
       }
-      if (df_update_bar_any(bad)) {
-        if (tid == 32) fail();
-        return false;
-      }
+      finished(t);
       return true;
     };
-    float urA[32], urB[32];
-    int bA = first_block(0), bB = nk > 1 ? first_block(1) : -1;
-    load_u(urA, 0, bA);
-    load_u(urB, 1, bB);
-    for (int it = 0; it < nk; it += 2) {
-      if (!step(it, bA, urA)) break;
+    float ur[32];
+    const int it0 = (nk + grp) & 1;  // first backward step of this group's parity (t = nk + it)
+    int bc = -1;
+    if (it0 < nk) {
+      bc = first_block(it0);
+      load_u(ur, it0, bc);
+    }
+    for (int it = it0; it < nk; it += 2) {
+      if (!step(it, bc, ur)) break;
       if (it + 2 < nk) {
-        bA = first_block(it + 2);
-        load_u(urA, it + 2, bA);
-      }
-      if (it + 1 >= nk) break;
-      if (!step(it + 1, bB, urB)) break;
-      if (it + 3 < nk) {
-        bB = first_block(it + 3);
-        load_u(urB, it + 3, bB);
+        bc = first_block(it + 2);
+        load_u(ur, it + 2, bc);
       }
     }
   }
