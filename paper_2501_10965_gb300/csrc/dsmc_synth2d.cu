@@ -1443,6 +1443,8 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   // gdone[t % 4]: the update warps of step t's group have finished it (a
   // phase per use, DF_UWG arrivals)
   __shared__ __align__(8) uint64_t gdone[4];
+  // per update warp: lane -> list entry maps for the scatter of its lookups (-1: none)
+  __shared__ int lsc[DF_UW][3][32];
   __shared__ unsigned done;       // steps this CTA's update warps have finished
   __shared__ unsigned done_l;     // the same, published at CTA scope
   __shared__ unsigned abort_all;  // set in every CTA once a wait gave up
@@ -1486,6 +1488,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   }
   if (tid < 4)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(df_smem_addr(&gdone[tid])), "r"(DF_UWG) : "memory");
+  for (int i = tid; i < DF_UW * 3 * 32; i += DF_NT) (&lsc[0][0][0])[i] = -1;
   if (tid < 2) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(df_smem_addr(&hbar[tid])) : "memory");
     const int k = (int)rank + DF_C * tid;
@@ -1735,13 +1738,15 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       // head value (-1: none; the value came with the step's result), and the
       // entries of the head's list that row R's new value serves (masks over
       // d and 32 + d); found before the wait, for the first block
+      int* const sc = lsc[warp - 1][0];
       auto lists = [&](int b, int& qi, unsigned& pm0, unsigned& pm1) {
-        const int R = 32 * b + lane;
-        qi = -1;
-        for (unsigned m = __ballot_sync(0xffffffffu, lane < tl.n && (tl.d >> 5) == b); m; m &= m - 1) {
-          const int q = __ffs(m) - 1;
-          if (__shfl_sync(0xffffffffu, tl.d, q) == R) qi = q;
-        }
+        // each entry lane writes its index at its row's lane (rows in a list are distinct)
+        const bool et = lane < tl.n && (tl.d >> 5) == b;
+        if (et) sc[tl.d & 31] = lane;
+        __syncwarp();
+        qi = sc[lane];
+        __syncwarp();
+        if (et) sc[tl.d & 31] = -1;
         pm0 = __ballot_sync(0xffffffffu, ((tl.m0 >> lane) & 1u) && (tl.r0 >> 5) == b);
         pm1 = __ballot_sync(0xffffffffu, ((tl.m1 >> lane) & 1u) && (tl.r1 >> 5) == b);
       };
@@ -1779,17 +1784,31 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
           *aloc(par ^ 1, 0, R) = v0;
           *aloc(par ^ 1, 1, R) = v1;
         }
-        // send the new values that the head of step s + 2 takes from this block
-        for (unsigned m = pm0; m; m &= m - 1) {
-          const int q = __ffs(m) - 1;
-          if (__shfl_sync(0xffffffffu, tl.r0, q) == R && in)
-            df_st_async2(df_mapa(&hbuf[hslot][2 * q], ho), v0, v1, df_mapa(&hbar[hslot], ho));
-        }
-        for (unsigned m = pm1; m; m &= m - 1) {
-          const int q = __ffs(m) - 1;
-          if (__shfl_sync(0xffffffffu, tl.r1, q) == R && in)
-            df_st_async2(df_mapa(&hbuf[hslot][64 + 2 * q], ho), v0, v1, df_mapa(&hbar[hslot], ho));
-        }
+        // send the new values that the head of step s + 2 takes from this
+        // block: the entry lanes (bits of pm) name their rows, scattered to the
+        // rows' lanes, so each lane sends its own (one entry at a time where
+        // two entries share a row)
+        auto send_part = [&](unsigned pm, int rs, int base, int* scp) {
+          if (pm == 0u) return;
+          const bool e = ((pm >> lane) & 1u) != 0u;
+          const unsigned same = __match_any_sync(0xffffffffu, e ? rs : -1 - lane);
+          if (__any_sync(0xffffffffu, e && __popc(same) > 1)) {
+            for (unsigned m = pm; m; m &= m - 1) {
+              const int q = __ffs(m) - 1;
+              if (__shfl_sync(0xffffffffu, rs, q) == R && in)
+                df_st_async2(df_mapa(&hbuf[hslot][2 * (base + q)], ho), v0, v1, df_mapa(&hbar[hslot], ho));
+            }
+            return;
+          }
+          if (e) scp[rs & 31] = lane;
+          __syncwarp();
+          const int q = scp[lane];
+          if (q >= 0 && in) df_st_async2(df_mapa(&hbuf[hslot][2 * (base + q)], ho), v0, v1, df_mapa(&hbar[hslot], ho));
+          __syncwarp();
+          if (e) scp[rs & 31] = -1;
+        };
+        send_part(pm0, tl.r0, 0, sc + 32);
+        send_part(pm1, tl.r1, 32, sc + 64);
       }
       finished(s);
       return true;
