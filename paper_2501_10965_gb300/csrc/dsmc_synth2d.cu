@@ -1266,7 +1266,6 @@ constexpr int DF_UWG = 5;                // update warps per group
 constexpr int DF_UW = 2 * DF_UWG;        // update warps per CTA: group 0 takes the even steps, group 1 the odd
 constexpr int DF_NT = 32 * (2 + DF_UW);  // warp 0 solves the heads, warp DF_UW + 1 publishes
 constexpr int DF_S = 32;                 // ring slots (steps in flight)
-constexpr int DF_SEND_LANES = 32 / DF_C;  // lanes of warp 0 that write one CTA's ring slot
 constexpr unsigned long long DF_WAIT_NS = 500000000ull;  // 0.5 s
 constexpr unsigned long long DF_DRAIN_NS = 1000000ull;   // 1 ms
 constexpr unsigned DF_SUSPEND_NS = 2000;                  // longest suspension of one wait test
@@ -1398,6 +1397,26 @@ __device__ __forceinline__ float df_ldg_or0(const float* p, bool pred) {
   return v;
 }
 
+// acc0 = l . y.x, acc1 = l . y.y over a ring slot of 32 float4 (four
+// partial sums each)
+__device__ __forceinline__ void df_dot2i(const float (&l)[32], const float4* y4, float& acc0, float& acc1) {
+  float p0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, p1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float4 v = y4[j];
+    p0[j & 3] += l[j] * v.x;
+    p1[j & 3] += l[j] * v.y;
+  }
+  acc0 = (p0[0] + p0[1]) + (p0[2] + p0[3]);
+  acc1 = (p1[0] + p1[1]) + (p1[2] + p1[3]);
+}
+
+__device__ __forceinline__ unsigned df_mapa_u32(unsigned addr, unsigned cta) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(cta));
+  return r;
+}
+
 // *p issued here (an asm load the compiler does not move down to its use)
 __device__ __forceinline__ int df_ldg_s32(const int32_t* p) {
   int v;
@@ -1428,11 +1447,10 @@ __device__ __forceinline__ void df_dot2(const float (&l)[32], const float* y, fl
 
 __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Work w, const double* b0,
                                                          const double* b1, double* o0, double* o1) {
-  // step results: rhs 0 in [0, 32), rhs 1 in [32, 64); forward steps also the
-  // values the step's interchanges move below the head (list entry q: rhs 0 at
-  // 64 + q, rhs 1 at 96 + q)
-  __shared__ __align__(16) float ring[DF_S][128];
-  __shared__ __align__(16) float stage[128];  // warp 0's result before it is sent
+  // step results, entry j = (rhs 0, rhs 1) of head position j and, forward,
+  // the values the step's interchanges move below the head (list entry j:
+  // rhs 0, rhs 1)
+  __shared__ __align__(16) float4 ring[DF_S][32];
   __shared__ __align__(16) float hsol[64];    // warp 0: the head's values before the triangle solve
   __shared__ __align__(8) uint64_t full[DF_S];
   // this CTA's forward heads k = rank + DF_C u: the values of the rows they
@@ -1481,7 +1499,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     abort_all = 0;
   }
   // bytes a step's result brings into each CTA's ring slot
-  auto step_bytes = [&](int t) -> unsigned { return t < nk ? 512u : 256u; };
+  auto step_bytes = [&](int t) -> unsigned { return t < 2 * nk ? 512u : 0u; };
   if (tid < DF_S) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(df_smem_addr(&full[tid])) : "memory");
     if (tid < 2 * nk) df_arm(&full[tid], step_bytes(tid));
@@ -1497,26 +1515,20 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   fill(b0, b1);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   sc_cluster_sync();
-  unsigned known = 0;  // warp 0: steps CTA lane % DF_C is known to have finished
-  // warp 0: send the first nf floats of this step's result (stage) to every
-  // CTA's ring slot t % DF_S, once the CTA has finished step t - DF_S (the
-  // slot's previous use).  Lane l writes part l / DF_C of the floats to CTA
-  // l % DF_C by asynchronous stores, which complete the slot's phase there
-  // (its publishing warp armed the phase for the step's bytes).
-  auto send = [&](int t, int nf) -> bool {
-    __syncwarp();
-    const unsigned c = (unsigned)(lane % DF_C);
+  unsigned known = 0;  // warp 0, lane c < DF_C: steps CTA c is known to have finished
+  // warp 0: send this lane's entry v of the step's result into every CTA's
+  // ring slot t % DF_S by asynchronous stores, which complete the slot's
+  // phase there (its publishing warp armed it for 32 entries), once every CTA
+  // has finished step t - DF_S (the slot's previous use)
+  auto send = [&](int t, float4 v) -> bool {
     const unsigned need = t >= DF_S ? (unsigned)(t - DF_S + 1) : 0u;
     bool ok = true;
-    if (known < need) ok = df_wait_count(df_mapa(&done, c), need, &known);
-    if (ok) {
-      const int part = lane / DF_C, n4 = nf / (4 * DF_SEND_LANES);
-      const unsigned dst = df_mapa(&ring[t % DF_S][0], c) + 16u * (unsigned)(part * n4);
-      const unsigned mb = df_mapa(&full[t % DF_S], c);
-      const float4* src = reinterpret_cast<const float4*>(stage) + part * n4;
-      for (int q = 0; q < n4; ++q) df_st_async4(dst + 16 * q, src[q], mb);
-    }
-    return __all_sync(0xffffffffu, ok);
+    if (lane < DF_C && known < need) ok = df_wait_count(df_mapa(&done, lane), need, &known);
+    if (!__all_sync(0xffffffffu, ok)) return false;
+    const unsigned d = df_smem_addr(&ring[t % DF_S][lane]), mb = df_smem_addr(&full[t % DF_S]);
+#pragma unroll
+    for (unsigned c = 0; c < DF_C; ++c) df_st_async4(df_mapa_u32(d, c), v, df_mapa_u32(mb, c));
+    return true;
   };
   // the publishing warp's lane 0: the first step whose slot it has not consumed
   int tnext = 0;
@@ -1620,13 +1632,13 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         const int t = k - 1;
         ok = df_wait_slot(&full[t % DF_S], (unsigned)(t / DF_S) & 1u);
         if (ok) {
-          const float* yp = ring[t % DF_S];
+          const float4* yp = ring[t % DF_S];
           float acc0, acc1;
-          df_dot2(mrow, yp, acc0, acc1);
+          df_dot2i(mrow, yp, acc0, acc1);
           y0 -= acc0;
           y1 -= acc1;
           if (tin) {
-            df_dot2(lt, yp, acc0, acc1);
+            df_dot2i(lt, yp, acc0, acc1);
             c0 -= acc0;
             c1 -= acc1;
           }
@@ -1637,11 +1649,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         break;
       }
       if (lane >= wd) y0 = y1 = 0.0f;
-      stage[lane] = y0;
-      stage[32 + lane] = y1;
-      stage[64 + lane] = c0;
-      stage[96 + lane] = c1;
-      if (!send(k, 128)) {
+      if (!send(k, make_float4(y0, y1, c0, c1))) {
         if (lane == 0) fail();
         break;
       }
@@ -1730,7 +1738,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     auto step = [&](int s, int bfirst, float (&lr)[32], const Tail& tl) -> bool {
       const int k0 = s * nb, wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
       const int bl = (k0 + H - 1) >> 5;
-      const float* y = ring[s % DF_S];
+      const float4* y = ring[s % DF_S];
       // where the new values go: the head of step s + 2 (its owner's buffer u % 2)
       const unsigned ho = (unsigned)((s + 2) % DF_C);
       const int hslot = ((s + 2) / DF_C) & 1;
@@ -1774,11 +1782,11 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
             v0 = *aloc(par, 0, R);
             v1 = *aloc(par, 1, R);
           } else {
-            v0 = y[64 + qi];
-            v1 = y[96 + qi];
+            v0 = y[qi].z;
+            v1 = y[qi].w;
           }
           float acc0 = 0.0f, acc1 = 0.0f;
-          df_dot2(lr, y, acc0, acc1);
+          df_dot2i(lr, y, acc0, acc1);
           v0 -= acc0;
           v1 -= acc1;
           *aloc(par ^ 1, 0, R) = v0;
@@ -1871,7 +1879,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         ok = df_wait_slot(&full[(t - 1) % DF_S], (unsigned)((t - 1) / DF_S) & 1u);
         if (ok && lane < wd) {
           float acc0 = 0.0f, acc1 = 0.0f;
-          df_dot2(ur, ring[(t - 1) % DF_S], acc0, acc1);
+          df_dot2i(ur, ring[(t - 1) % DF_S], acc0, acc1);
           a0 -= acc0;
           a1 -= acc1;
         }
@@ -1887,9 +1895,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       float x0, x1;
       df_dot2(invr, hsol, x0, x1);
       if (lane >= wd) x0 = x1 = 0.0f;
-      stage[lane] = x0;
-      stage[32 + lane] = x1;
-      if (!send(t, 64)) {
+      if (!send(t, make_float4(x0, x1, 0.0f, 0.0f))) {
         if (lane == 0) fail();
         break;
       }
@@ -1943,7 +1949,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     auto step = [&](int it, int bfirst, float (&ur)[32]) -> bool {
       const int t = nk + it, k = nk - 1 - it, k0 = k * nb;
       const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
-      const float* x = ring[t % DF_S];
+      const float4* x = ring[t % DF_S];
       bool ok = df_wait_slot(&full[t % DF_S], (unsigned)(t / DF_S) & 1u);
       if (ok) ok = df_wait_slot(&gdone[(t - 1) & 3], (unsigned)((t - 1) >> 2) & 1u);
       if (!__all_sync(0xffffffffu, ok)) {
@@ -1956,7 +1962,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         if (R >= lo) {
           const int par = it & 1;
           float acc0 = 0.0f, acc1 = 0.0f;
-          df_dot2(ur, x, acc0, acc1);
+          df_dot2i(ur, x, acc0, acc1);
           const float v0 = *aloc(par, 0, R), v1 = *aloc(par, 1, R);
           *aloc(par ^ 1, 0, R) = v0 - acc0;
           *aloc(par ^ 1, 1, R) = v1 - acc1;
