@@ -1411,6 +1411,25 @@ __device__ __forceinline__ void df_dot2i(const float (&l)[32], const float4* y4,
   acc1 = (p1[0] + p1[1]) + (p1[2] + p1[3]);
 }
 
+// the two dot products of df_dot2i for the rows l and m at once (each ring
+// entry read once)
+__device__ __forceinline__ void df_dot4i(const float (&l)[32], const float (&m)[32], const float4* y4, float& a0,
+                                         float& a1, float& b0, float& b1) {
+  float p0[2] = {0.0f, 0.0f}, p1[2] = {0.0f, 0.0f}, q0[2] = {0.0f, 0.0f}, q1[2] = {0.0f, 0.0f};
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float4 v = y4[j];
+    p0[j & 1] += l[j] * v.x;
+    p1[j & 1] += l[j] * v.y;
+    q0[j & 1] += m[j] * v.x;
+    q1[j & 1] += m[j] * v.y;
+  }
+  a0 = p0[0] + p0[1];
+  a1 = p1[0] + p1[1];
+  b0 = q0[0] + q0[1];
+  b1 = q1[0] + q1[1];
+}
+
 __device__ __forceinline__ unsigned df_mapa_u32(unsigned addr, unsigned cta) {
   unsigned r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(cta));
@@ -1520,14 +1539,22 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   // ring slot t % DF_S by asynchronous stores, which complete the slot's
   // phase there (its publishing warp armed it for 32 entries), once every CTA
   // has finished step t - DF_S (the slot's previous use)
+  // this lane's ring entry of slot 0 and slot 0's mbarrier, in each CTA
+  unsigned rbase[DF_C], fbase[DF_C];
+#pragma unroll
+  for (unsigned c = 0; c < DF_C; ++c) {
+    rbase[c] = df_mapa(&ring[0][lane], c);
+    fbase[c] = df_mapa(&full[0], c);
+  }
   auto send = [&](int t, float4 v) -> bool {
     const unsigned need = t >= DF_S ? (unsigned)(t - DF_S + 1) : 0u;
     bool ok = true;
     if (lane < DF_C && known < need) ok = df_wait_count(df_mapa(&done, lane), need, &known);
     if (!__all_sync(0xffffffffu, ok)) return false;
-    const unsigned d = df_smem_addr(&ring[t % DF_S][lane]), mb = df_smem_addr(&full[t % DF_S]);
+    const unsigned slot = (unsigned)(t % DF_S);
 #pragma unroll
-    for (unsigned c = 0; c < DF_C; ++c) df_st_async4(df_mapa_u32(d, c), v, df_mapa_u32(mb, c));
+    for (unsigned c = 0; c < DF_C; ++c)
+      df_st_async4(rbase[c] + slot * (unsigned)sizeof(ring[0]), v, fbase[c] + slot * (unsigned)sizeof(full[0]));
     return true;
   };
   // the publishing warp's lane 0: the first step whose slot it has not consumed
@@ -1633,15 +1660,12 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         ok = df_wait_slot(&full[t % DF_S], (unsigned)(t / DF_S) & 1u);
         if (ok) {
           const float4* yp = ring[t % DF_S];
-          float acc0, acc1;
-          df_dot2i(mrow, yp, acc0, acc1);
+          float acc0, acc1, bcc0, bcc1;
+          df_dot4i(mrow, lt, yp, acc0, acc1, bcc0, bcc1);  // lt is zero where tin is false
           y0 -= acc0;
           y1 -= acc1;
-          if (tin) {
-            df_dot2i(lt, yp, acc0, acc1);
-            c0 -= acc0;
-            c1 -= acc1;
-          }
+          c0 -= bcc0;
+          c1 -= bcc1;
         }
       }
       if (!__all_sync(0xffffffffu, ok)) {
