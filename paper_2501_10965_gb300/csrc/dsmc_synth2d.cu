@@ -11,11 +11,13 @@
 // the Newton step of J = B + e_r w^T (w = mass_scale / n on the density of
 // every other cell) follows from two solves with B (Sherman-Morrison).
 //
-// Factorisation: per panel of nb columns, one CTA factorises the panel in
-// shared memory, then one launch applies it to the up to kl + ku trailing
-// columns, up to 16 columns per CTA.  Substitution: a cluster of 8 CTAs walks the
-// panels, forward then backward, one cluster barrier per panel
-// (k_s2_subst_cl; one CTA, k_s2_subst, where no cluster fits).  The launches
+// Factorisation: per panel of nb columns, one CTA factorises the panel (its
+// rows in registers, k_s2_panel_rot, or in shared memory for taller panels),
+// then one launch applies it to the up to kl + ku trailing columns, up to 8
+// columns per CTA.  Substitution: a cluster of 8 CTAs walks the panels,
+// forward then backward, as a data flow (k_s2_subst_df; with one cluster
+// barrier per panel, k_s2_subst_cl, where its rows do not fit the cluster's
+// shared memory; one CTA, k_s2_subst, where no cluster fits).  The launches
 // on one stream order the factorisation's panels.
 #include <climits>
 #include <cmath>
@@ -2260,10 +2262,11 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
   const int nb = w.nb;
   const size_t hmax = (size_t)g.kl + nb;
   const size_t sm_panel = sizeof(float) * nb * hmax;
-  // trailing columns per CTA of the trailing update: up to 16, as shared
-  // memory allows (column segments of hmax rows)
+  // trailing columns per CTA of the trailing update: up to 8, as shared
+  // memory allows (column segments of hmax rows; 8 beat 16 by 5 % at 100 x
+  // 100: twice the CTAs, each with half the serial work)
   int cbt = (int)(S2_SMEM_CAP / (sizeof(float) * hmax));
-  if (cbt > 16) cbt = 16;
+  if (cbt > 8) cbt = 8;
   if (cbt < 1) cbt = 1;
   const size_t sm_trail = sizeof(float) * (size_t)cbt * hmax;
   const size_t sm_subst = sizeof(float) * 2 * ((size_t)g.kl + g.ku + nb);
