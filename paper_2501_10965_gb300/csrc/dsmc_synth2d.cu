@@ -51,7 +51,7 @@ constexpr int S2_UPD_NT = 512;    // the Newton update
 constexpr int S2_SUB_NT = 512;    // the substitutions
 constexpr int S2_PNL_NT = 512;    // the panel factorisation
 constexpr int S2_NREF = 1;        // refinement sweeps after a fresh factorisation
-constexpr int S2_NREF_REUSE = 3;  // refinement sweeps when an earlier factorisation is reused
+constexpr int S2_NREF_REUSE = 2;  // refinement sweeps when an earlier factorisation is reused
 constexpr int S2_SMEM_CAP = 200 * 1024;
 constexpr int S2_SMAP = 256;  // ints of a panel's row maps (k_s2_sprep, k_s2_spush)
 constexpr size_t S2_DF_SMEM_CAP = 200 * 1024;  // rows of the data-flow substitution per CTA (4 copies of 32 floats a block)
