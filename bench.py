@@ -386,6 +386,17 @@ def run_synth2d(args):
             torch.cuda.synchronize()
             tr.append(time.perf_counter() - t0)
         line.update(ms_per_solve_reused=1e3 * min(tr), newton_steps_reused=it2)
+        # and Newton from the previous solution too
+        sim.synth_reuse(True, warm=True)
+        tw = []
+        for rep in range(max(1, args.synth2d_reps)):
+            sim.synth_solve(D if rep % 2 else D2, H if rep % 2 else H2)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, it3, _ = sim.synth_solve(D2 if rep % 2 else D, H2 if rep % 2 else H)
+            torch.cuda.synchronize()
+            tw.append(time.perf_counter() - t0)
+        line.update(ms_per_solve_warm=1e3 * min(tw), newton_steps_warm=it3)
     print(json.dumps(line), flush=True)
 
 

@@ -242,14 +242,17 @@ int synth_solve(dsmc_handle *h, const double *dev_fields, const double *dev_hot,
 
 /* 2D synthetic solve across calls (Sec. 3: each DIG iteration solves the
  * same grid's equations again, for fields that change little from one
- * iteration to the next).  on = 1: each synth_solve starts from the
+ * iteration to the next).  Bit 0 of `on`: each synth_solve starts from the
  * factorisation of the Jacobian that the handle's previous synth_solve left
  * in the workspace (none before the first call), and refactorises only when
- * the Newton updates stop halving; a solve that does not converge from the
- * old factorisation is repeated from a fresh one, so the converged solution
- * is the same as with on = 0 up to the tolerance.  on = 0 (the default)
- * factorises in every call.  DSMC_ERR_ARG unless the handle is a single 2D
- * case with synth2d = 1. */
+ * the Newton updates stop halving.  Bit 1: Newton starts from the previous
+ * call's solution (when that call converged) instead of the sampled fields
+ * (the boundary rows' equations pin their cells to the new sampled values
+ * in the first step).  A solve that does not converge this way is repeated
+ * from a fresh factorisation and the sampled fields, so the converged
+ * solution is the same as with on = 0 up to the tolerance.  on = 0 (the
+ * default) factorises in every call and starts from the sampled fields.
+ * DSMC_ERR_ARG unless the handle is a single 2D case with synth2d = 1. */
 int dsmc_synth_reuse(dsmc_handle *h, int on);
 
 /* Particle modification of Sec. 3.2 to the target dev_target (ncells x

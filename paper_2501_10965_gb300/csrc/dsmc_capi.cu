@@ -45,6 +45,8 @@ struct dsmc_handle {
   double* synth_info = nullptr;
   int synth_reuse = 0;       // 2D: start synth_solve from the previous call's factorisation
   int synth_fact_valid = 0;  // 2D: the workspace holds a factorisation of this grid's Jacobian
+  int synth_warm = 0;        // 2D: start Newton from the previous call's solution
+  int synth_last_ok = 0;     // 2D: the previous call converged (its solution is in the workspace)
   Mlp mlp{};       // HoT surrogate network
   int mlp_t = 0;   // Adam steps taken since the parameters were set
   // annulus tables (device): squared ring radii, rays, outer-face
@@ -922,8 +924,10 @@ static int synth_solve_2d(dsmc_handle* h, const double* dev_fields, const double
   const double tol = c.synth_tol > 0 ? c.synth_tol : 1e-5;
   int singular = 0;
   const int e = launch_synth2d(h->cp, dev_fields, dev_hot, dev_out, h->synth_work, n_m, tol, h->synth_info,
-                               &singular, h->synth_reuse && h->synth_fact_valid, h->stream);
+                               &singular, h->synth_reuse && h->synth_fact_valid,
+                               h->synth_warm && h->synth_last_ok, h->stream);
   h->synth_fact_valid = e == 0;
+  h->synth_last_ok = 0;
   if (e == S2_TIMEOUT_RC) return set_err(h, DSMC_ERR_TIMEOUT, "synth_solve: a wait of the substitution gave up");
   if (e) return set_err(h, DSMC_ERR_CUDA, "synth_solve: %s", cudaGetErrorString((cudaError_t)e));
   double info[3];
@@ -937,13 +941,15 @@ static int synth_solve_2d(dsmc_handle* h, const double* dev_fields, const double
     return set_err(h, DSMC_ERR_NUMERIC, "synth_solve: no update keeps rho, T positive%s",
                    singular ? " (singular Jacobian)" : "");
   if (status == 1) return set_err(h, DSMC_ERR_NOT_CONVERGED, "synth_solve: %d iterations without convergence", n_m);
+  h->synth_last_ok = 1;
   return DSMC_OK;
 }
 
 int dsmc_synth_reuse(dsmc_handle* h, int on) {
   if (!h || h->cfg.dim != 2 || !h->cfg.synth2d || h->ncases != 1)
     return set_err(h, DSMC_ERR_ARG, "dsmc_synth_reuse: needs a single 2D case with synth2d = 1");
-  h->synth_reuse = on != 0;
+  h->synth_reuse = (on & 1) != 0;
+  h->synth_warm = (on & 2) != 0;
   return DSMC_OK;
 }
 

@@ -159,7 +159,7 @@ size_t synth1d_work_doubles(int ncells);
 constexpr int S2_TIMEOUT_RC = -2;
 size_t synth2d_work_doubles(int nx, int ny, int annulus);
 int launch_synth2d(const CellParams& cp, const double* fields, const double* hot, double* out, double* work,
-                   int n_m, double tol, double* info, int* singular, int reuse, cudaStream_t st);
+                   int n_m, double tol, double* info, int* singular, int reuse, int warm, cudaStream_t st);
 
 // HoT surrogate network (dsmc_mlp.cu): 12 -> 64 -> 64 -> 64 -> 5, tanh
 // hidden layers; parameters per layer: W (n_out x n_in, row major), then b.

@@ -51,7 +51,7 @@ constexpr int S2_UPD_NT = 512;    // the Newton update
 constexpr int S2_SUB_NT = 512;    // the substitutions
 constexpr int S2_PNL_NT = 512;    // the panel factorisation
 constexpr int S2_NREF = 1;        // refinement sweeps after a fresh factorisation
-constexpr int S2_NREF_REUSE = 2;  // refinement sweeps when an earlier factorisation is reused
+constexpr int S2_NREF_REUSE = 3;  // refinement sweeps when an earlier factorisation is reused
 constexpr int S2_SMEM_CAP = 200 * 1024;
 constexpr int S2_SMAP = 256;  // ints of a panel's row maps (k_s2_sprep, k_s2_spush)
 constexpr size_t S2_DF_SMEM_CAP = 200 * 1024;  // rows of the data-flow substitution per CTA (4 copies of 32 floats a block)
@@ -166,10 +166,13 @@ __device__ double s2_block_max(double v, double* red) {
 
 extern __shared__ __align__(16) unsigned char s2_smem[];
 
-__global__ void __launch_bounds__(S2_NT) k_s2_init(const s2::Grid g, S2Work w) {
+// the sampled fields as Newton's first state (warm: keep the state the work
+// area holds, the previous solve's solution), the sampled total mass, and the
+// scalar slots
+__global__ void __launch_bounds__(S2_NT) k_s2_init(const s2::Grid g, S2Work w, int warm) {
   __shared__ double red[S2_NT];
   double s = 0.0;
-  for (int b = threadIdx.x; b < g.n; b += S2_NT) {
+  for (int b = threadIdx.x; b < g.n && !warm; b += S2_NT) {
     int i, j;
     s2::cell_of_band(g, b, i, j);
     const double* D = g.F + (size_t)(j * g.nx + i) * 18;
@@ -2252,7 +2255,7 @@ size_t synth2d_work_doubles(int nx, int ny, int annulus) {
 }
 
 int launch_synth2d(const CellParams& cp, const double* fields, const double* hot, double* out, double* work,
-                   int n_m, double tol, double* info, int* singular, int reuse, cudaStream_t st) {
+                   int n_m, double tol, double* info, int* singular, int reuse, int warm, cudaStream_t st) {
   s2::Grid g = s2::make_grid(cp.nx, cp.ny, cp.dx, cp.dy, cp.d_r, cp.omega, cp.mu_ref, cp.z_rot, cp.kappa_t,
                              cp.kappa_r, fields, hot);
   if (cp.mesh == 2) s2::set_edges(g, cp.xe, cp.ye, cp.lx * cp.ly);  // the wall-refined grid (device edges)
@@ -2277,7 +2280,7 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
   const long long jac_threads = (long long)g.n * s2::NSTENCIL * s2::NV;
   const int jac_grid = (int)((jac_threads + nt - 1) / nt);
   double sc[S2_NSC];
-  k_s2_init<<<1, S2_NT, 0, st>>>(g, w);
+  k_s2_init<<<1, S2_NT, 0, st>>>(g, w, warm);
   // The factorisation of the first Newton step (with `reuse`, the one the
   // work area holds from the previous solve) is reused while the updates
   // keep shrinking (by half or more per step), with more refinement sweeps
@@ -2341,8 +2344,8 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
   if (e != cudaSuccess) return (int)e;
   // a solve that started from an earlier factorisation and did not
   // converge is repeated from a fresh one
-  if (reuse && sc[S2_STATUS] != 0.0)
-    return launch_synth2d(cp, fields, hot, out, work, n_m, tol, info, singular, 0, st);
+  if ((reuse || warm) && sc[S2_STATUS] != 0.0)
+    return launch_synth2d(cp, fields, hot, out, work, n_m, tol, info, singular, 0, 0, st);
   if (singular) *singular = sc[S2_SING] != 0.0;
   return 0;
 }

@@ -346,7 +346,7 @@ def binned2d(a: np.ndarray, nx: int, ny: int, bx: int, by: int) -> np.ndarray:
 
 def time_to_steady_2d(cfg: dict, window: int = 200, bx: int = 5, by: int = 5, transient: int = 15000,
                       average: int = 10000, threshold: float = 0.01, max_dig: int = 4000,
-                      max_plain: int = 20000, reuse_factorisation: bool = True) -> dict:
+                      max_plain: int = 20000, reuse_factorisation: bool = True, warm_start: bool = True) -> dict:
     """Time to steady state of a 2D case, DIG against plain DSMC, from the
     same uniform initial state.  The 2D synthetic solve takes one case per
     handle, so each method runs one handle (many particles per cell instead
@@ -358,7 +358,8 @@ def time_to_steady_2d(cfg: dict, window: int = 200, bx: int = 5, by: int = 5, tr
     steady from the first window after which the larger error stays at or
     below max(threshold, 1.5 x floor) for three windows.  With
     reuse_factorisation each DIG synthetic solve starts from the previous
-    solve's factorisation (dsmc_synth_reuse)."""
+    solve's factorisation, with warm_start Newton from its solution
+    (dsmc_synth_reuse)."""
     nx, ny = int(cfg["nx"]), int(cfg["ny"])
 
     def reduce(f):
@@ -387,8 +388,8 @@ def time_to_steady_2d(cfg: dict, window: int = 200, bx: int = 5, by: int = 5, tr
     n_s = int(cfg["n_s"])
     for method, cap in (("dig", max_dig), ("plain", max_plain)):
         sim = dsmc.Dsmc(cfg)
-        if method == "dig" and reuse_factorisation:
-            sim.synth_reuse(True)
+        if method == "dig" and (reuse_factorisation or warm_start):
+            sim.synth_reuse(reuse_factorisation, warm=warm_start)
         hist, steps, walls, wall, nsteps = [], [], [], 0.0, 0
         steady = None
         solves = []  # (status, Newton iterations) of the DIG iterations' synthetic solves

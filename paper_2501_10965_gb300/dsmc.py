@@ -255,9 +255,10 @@ class Dsmc:
         self.last_synth_status = rc
         return out, it.value, res.value
 
-    def synth_reuse(self, on: bool = True):
-        """2D: let each synth_solve start from the previous call's factorisation."""
-        self._check(load().dsmc_synth_reuse(self._h, 1 if on else 0))
+    def synth_reuse(self, on: bool = True, warm: bool = False):
+        """2D: let each synth_solve start from the previous call's
+        factorisation (and with warm, Newton from its solution)."""
+        self._check(load().dsmc_synth_reuse(self._h, (1 if on else 0) | (2 if warm else 0)))
 
     def launch_config(self) -> int:
         """Warps (cells) per CTA of the FP32 fused step chosen by the tuner."""

@@ -183,5 +183,12 @@ def test_factorisation_reused_across_solves_gives_the_same_solution():
     out_f, it_f, res_f = _gpu(cfg).synth_solve(_dev(d2), _dev(h2))
     assert res_r < 1e-9 and res_f < 1e-9
     np.testing.assert_allclose(out_r.cpu().numpy(), out_f.cpu().numpy(), rtol=0, atol=1e-8)
+    # and Newton from the previous solution as well (bit 1)
+    gw = _gpu(cfg)
+    gw.synth_reuse(True, warm=True)
+    gw.synth_solve(_dev(d1), _dev(h1))
+    out_w, it_w, res_w = gw.synth_solve(_dev(d2), _dev(h2))
+    assert res_w < 1e-9
+    np.testing.assert_allclose(out_w.cpu().numpy(), out_f.cpu().numpy(), rtol=0, atol=1e-8)
     with pytest.raises(RuntimeError):
         _gpu(W.fourier_1d(precision="fp64")).synth_reuse(True)
