@@ -140,7 +140,7 @@ def test_dig_iteration_on_a_cavity():
     assert abs(t[:, 0].sum() / r["fields"][:, 0].sum().item() - 1.0) < 1e-8
 
 
-@pytest.mark.parametrize("nx,ny", [(100, 100), (60, 50)])
+@pytest.mark.parametrize("nx,ny", [(100, 100), (60, 50), (130, 128)])
 def test_full_size_cavity_solution_satisfies_the_oracle_equations(nx, ny):
     """The paper's cavity grid, 100 x 100 cells (50 000 unknowns), where the
     oracle's Newton solver is too slow to run: the GPU's converged solution
@@ -148,7 +148,9 @@ def test_full_size_cavity_solution_satisfies_the_oracle_equations(nx, ny):
     cell (to 1e-9, against O(100) terms), keeps the sampled total mass, and
     keeps the wall cells' u, T and the corner cells' whole state.  (60 x 50:
     panels of 536 rows, two rows of each thread in the panel factorisation's
-    registers; 100 x 100: 1 036 rows, three.)"""
+    registers; 100 x 100: 1 036 rows, three; 130 x 128: windows of 41
+    blocks of 32 rows, more than one pass of a substitution group's warps
+    over a CTA's blocks.)"""
     cfg = _cfg(nx, ny, ppc=2, synth_tol=1e-10)
     d, h = _smooth(nx, ny, seed=5)
     g = _gpu(cfg)
