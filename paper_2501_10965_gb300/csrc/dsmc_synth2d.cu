@@ -43,6 +43,8 @@ enum {
   S2_SING = 6,   // a zero pivot was met
   S2_LAM = 7,    // length of the last Newton update (1 = full step)
   S2_TOUT = 8,   // a wait of the substitution gave up
+  S2_EPS0 = 9,   // step of the directional differences along v0, v1
+  S2_EPS1 = 10,
   S2_NSC = 16
 };
 
@@ -2039,6 +2041,65 @@ __global__ void k_s2_bmv(const s2::Grid g, S2Work w) {
   w.b1[u] = w.rhs1[u] - s2::bmv_row(g, w.Jc, w.v1, u);
 }
 
+// The same refinement residuals without the stored Jacobian (on Newton steps
+// that keep an earlier factorisation): B v from central differences of the
+// FP64 residual along v, (R(x + e v) - R(x - e v)) / (2 e), e = S2_JV_H
+// max(1, |x|) / |v| (maxima over the unknowns), and the total-mass row as in
+// bmv_row.  The differences use y0, y1 (the states) and s0, s1 (their
+// residuals), which the sweep overwrites later.
+constexpr double S2_JV_H = 1e-6;
+// from this many cells on (measured: slower below ~3 000 cells, where the
+// Jacobian is cheaper than the extra launches; 100 x 100 gains 5 %, a solve
+// from an earlier factorisation 12 %)
+constexpr int S2_JV_MIN_CELLS = 4096;
+
+__global__ void __launch_bounds__(S2_UPD_NT) k_s2_jveps(const s2::Grid g, S2Work w) {
+  __shared__ double red[S2_UPD_NT];
+  double mx = 0.0, m0 = 0.0, m1 = 0.0;
+  for (int u = threadIdx.x; u < g.N; u += S2_UPD_NT) {
+    mx = fmax(mx, fabs(w.x[u]));
+    m0 = fmax(m0, fabs(w.v0[u]));
+    m1 = fmax(m1, fabs(w.v1[u]));
+  }
+  mx = s2_block_max<S2_UPD_NT>(mx, red);
+  m0 = s2_block_max<S2_UPD_NT>(m0, red);
+  m1 = s2_block_max<S2_UPD_NT>(m1, red);
+  if (threadIdx.x == 0) {
+    const double h = S2_JV_H * fmax(1.0, mx);
+    w.sc[S2_EPS0] = m0 > 0.0 ? h / m0 : 1.0;
+    w.sc[S2_EPS1] = m1 > 0.0 ? h / m1 : 1.0;
+  }
+}
+
+// y0 = x + e v_c, y1 = x - e v_c
+__global__ void k_s2_jvx(const s2::Grid g, S2Work w, int c) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= g.N) return;
+  const double e = w.sc[c ? S2_EPS1 : S2_EPS0], v = (c ? w.v1 : w.v0)[u];
+  w.y0[u] = w.x[u] + e * v;
+  w.y1[u] = w.x[u] - e * v;
+}
+
+// s0 = R(y0), s1 = R(y1) (the total-mass row is replaced below)
+__global__ void k_s2_jvres(const s2::Grid g, S2Work w) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= g.n) return;
+  int i, j;
+  s2::cell_of_band(g, b, i, j);
+  s2::cell_residual(g, s2::View{w.y0, -1, 0, 0.0}, i, j, 0.0, w.s0 + s2::NV * b);
+  s2::cell_residual(g, s2::View{w.y1, -1, 0, 0.0}, i, j, 0.0, w.s1 + s2::NV * b);
+}
+
+// b_c = rhs_c - B v_c
+__global__ void k_s2_jvb(const s2::Grid g, S2Work w, int c) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= g.N) return;
+  const double e = w.sc[c ? S2_EPS1 : S2_EPS0];
+  const double* v = c ? w.v1 : w.v0;
+  const double bv = u == s2::mass_row(g) ? s2::mass_scale(g, 1, 0) * v[u] / g.n : (w.s0[u] - w.s1[u]) / (2.0 * e);
+  (c ? w.b1 : w.b0)[u] = (c ? w.rhs1 : w.rhs0)[u] - bv;
+}
+
 __global__ void k_s2_add(const s2::Grid g, S2Work w) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= g.N) return;
@@ -2291,8 +2352,11 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
   for (int it = 0; it < n_m; ++it) {
     k_s2_mass<<<1, S2_NT, 0, st>>>(g, w);
     k_s2_res<<<cell_grid, nt, 0, st>>>(g, w);
+    // on large grids the Jacobian only where it is factorised: a step that
+    // keeps an earlier factorisation refines with directional differences
+    const bool jv = !refactor && g.n >= S2_JV_MIN_CELLS;
     if (refactor) cudaMemsetAsync(w.AB, 0, sizeof(float) * (size_t)g.ld * g.N, st);
-    k_s2_jac<<<jac_grid, nt, 0, st>>>(g, w, refactor ? 1 : 0);
+    if (!jv) k_s2_jac<<<jac_grid, nt, 0, st>>>(g, w, refactor ? 1 : 0);
     if (refactor) {
       for (int k0 = 0; k0 < g.N; k0 += nb) {
         const int wd = s2::panel_width(g, nb, k0), H = s2::panel_height(g, wd, k0);
@@ -2320,7 +2384,16 @@ int launch_synth2d(const CellParams& cp, const double* fields, const double* hot
     k_s2_prep<<<vec_grid, nt, 0, st>>>(g, w);
     cudaError_t le = s2_subst(g, w, w.b0, w.b1, w.v0, w.v1, sm_subst, st);
     for (int r = 0; r < nsweep && le == cudaSuccess; ++r) {
-      k_s2_bmv<<<vec_grid, nt, 0, st>>>(g, w);
+      if (!jv) {
+        k_s2_bmv<<<vec_grid, nt, 0, st>>>(g, w);
+      } else {
+        k_s2_jveps<<<1, S2_UPD_NT, 0, st>>>(g, w);
+        for (int c = 0; c < 2; ++c) {
+          k_s2_jvx<<<vec_grid, nt, 0, st>>>(g, w, c);
+          k_s2_jvres<<<cell_grid, nt, 0, st>>>(g, w);
+          k_s2_jvb<<<vec_grid, nt, 0, st>>>(g, w, c);
+        }
+      }
       le = s2_subst(g, w, w.b0, w.b1, w.s0, w.s1, sm_subst, st);
       k_s2_add<<<vec_grid, nt, 0, st>>>(g, w);
     }
