@@ -1294,12 +1294,6 @@ __device__ __forceinline__ unsigned df_mapa(const void* p, unsigned cta) {
   return r;
 }
 
-__device__ __forceinline__ float df_ld_remote(unsigned addr) {
-  float v;
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ unsigned df_ld_acquire(unsigned addr) {
   unsigned v;
   asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
@@ -1308,12 +1302,6 @@ __device__ __forceinline__ unsigned df_ld_acquire(unsigned addr) {
 
 __device__ __forceinline__ void df_st_release(unsigned addr, unsigned v) {
   asm volatile("st.release.cluster.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ void df_st_remote4(unsigned addr, float4 v) {
-  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
-               "f"(v.w)
-               : "memory");
 }
 
 // asynchronous store of 16 bytes into another CTA's shared memory, counted
@@ -1437,12 +1425,6 @@ __device__ __forceinline__ void df_dot4i(const float (&l)[32], const float (&m)[
   b1 = q1[0] + q1[1];
 }
 
-__device__ __forceinline__ unsigned df_mapa_u32(unsigned addr, unsigned cta) {
-  unsigned r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(cta));
-  return r;
-}
-
 // *p issued here (an asm load the compiler does not move down to its use)
 __device__ __forceinline__ int df_ldg_s32(const int32_t* p) {
   int v;
@@ -1501,7 +1483,6 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   auto aloc = [&](int par, int rhs, int R) -> float* {
     return As + ((size_t)(2 * par + rhs) * nbl + (size_t)((R >> 5) / DF_C)) * 32 + (R & 31);
   };
-  auto owner = [](int R) -> unsigned { return (unsigned)((R >> 5) % DF_C); };
   auto fail = [&]() {
     for (unsigned c = 0; c < DF_C; ++c)
       asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(df_mapa(&abort_all, c)), "r"(1u) : "memory");
@@ -1593,13 +1574,12 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     for (int k = (int)rank, u = 0; k < nk; k += DF_C, ++u) {
       const int k0 = k * nb, wd = s2::panel_width(g, nb, k0);
       const int32_t* sm = w.smap + (size_t)k * S2_SMAP;
-      // lane i follows two rows to their values after step k - 1: hs, whose
-      // value ends at head position k0 + i, and (i < ntail) tp, the head
-      // position whose value the interchanges move to the i-th row of the
-      // list past the head; each from the value after step k - 2 of the row
-      // panel k - 1's interchanges move there (sent by its owner if step
-      // k - 2 updated it, else its input)
-      const int hs = sm[lane];
+      // lane i follows two rows to their values after step k - 1: the row
+      // whose value ends at head position k0 + i, and (i < ntail) tp, the
+      // head position whose value the interchanges move to the i-th row of
+      // the list past the head; each from the value after step k - 2 of the
+      // row panel k - 1's interchanges move there (rh, rt: sent by its owner
+      // if step k - 2 updated it, else its input)
       const int ntail = sm[96], tpl = sm[64 + lane];
       const int tp = lane < ntail ? tpl : -1;
       const int rh = sm[128 + lane], rt = sm[160 + lane];
