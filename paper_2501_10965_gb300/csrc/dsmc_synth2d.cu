@@ -1275,6 +1275,10 @@ constexpr int DF_NT = 32 * (2 + DF_UW);  // warp 0 solves the heads, warp DF_UW 
 constexpr int DF_S = 32;                 // ring slots (steps in flight)
 constexpr unsigned long long DF_WAIT_NS = 500000000ull;  // 0.5 s
 constexpr unsigned long long DF_DRAIN_NS = 1000000ull;   // 1 ms
+// step barriers of the update-warp groups: more than the DF_S steps the
+// groups can run ahead of the publishing warp (the ring's back-pressure), so
+// a phase is never overtaken by the next use of its slot
+constexpr int DF_GD = 64;
 constexpr unsigned DF_SUSPEND_NS = 2000;                  // longest suspension of one wait test
 
 __device__ __forceinline__ unsigned long long df_clock_ns() {
@@ -1466,9 +1470,9 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
   // 2 d, 2 d + 1), in buffer u % 2, completed on hbar[u % 2]
   __shared__ __align__(16) float hbuf[2][128];
   __shared__ __align__(8) uint64_t hbar[2];
-  // gdone[t % 4]: the update warps of step t's group have finished it (a
+  // gdone[t % DF_GD]: the update warps of step t's group have finished it (a
   // phase per use, DF_UWG arrivals)
-  __shared__ __align__(8) uint64_t gdone[4];
+  __shared__ __align__(8) uint64_t gdone[DF_GD];
   // per update warp: lane -> list entry maps for the scatter of its lookups (-1: none)
   __shared__ int lsc[DF_UW][3][32];
   __shared__ unsigned done;       // steps this CTA's update warps have finished
@@ -1511,7 +1515,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(df_smem_addr(&full[tid])) : "memory");
     if (tid < 2 * nk) df_arm(&full[tid], step_bytes(tid));
   }
-  if (tid < 4)
+  if (tid < DF_GD)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(df_smem_addr(&gdone[tid])), "r"(DF_UWG) : "memory");
   for (int i = tid; i < DF_UW * 3 * 32; i += DF_NT) (&lsc[0][0][0])[i] = -1;
   if (tid < 2) {
@@ -1682,7 +1686,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         if (!bad) {
           tnext = s + 1;
           if (s + DF_S < 2 * nk) df_arm(&full[s % DF_S], step_bytes(s + DF_S));
-          bad = !df_wait_slot(&gdone[s & 3], (unsigned)(s >> 2) & 1u);
+          bad = !df_wait_slot(&gdone[s % DF_GD], (unsigned)(s / DF_GD) & 1u);
         }
         if (!bad) {
           df_st_release_cta(&done_l, (unsigned)(s + 1));
@@ -1708,7 +1712,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     // lane's stores)
     auto finished = [&](int t) {
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(df_smem_addr(&gdone[t & 3])) : "memory");
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(df_smem_addr(&gdone[t % DF_GD])) : "memory");
     };
     // multipliers of step s for this lane's row of block b (zero outside the
     // window and past the panel's width)
@@ -1774,7 +1778,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       if (bfirst >= 0 && bfirst <= bl) lists(bfirst, qi, pm0, pm1);
       bool ok = df_wait_slot(&full[s % DF_S], (unsigned)(s / DF_S) & 1u);
       // the rows' values after step s - 1: the other group's step
-      if (ok && s >= 1) ok = df_wait_slot(&gdone[(s - 1) & 3], (unsigned)((s - 1) >> 2) & 1u);
+      if (ok && s >= 1) ok = df_wait_slot(&gdone[(s - 1) % DF_GD], (unsigned)((s - 1) / DF_GD) & 1u);
       if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) fail();
         return false;
@@ -1924,7 +1928,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
         if (!bad) {
           tnext = t + 1;
           if (t + DF_S < 2 * nk) df_arm(&full[t % DF_S], step_bytes(t + DF_S));
-          bad = !df_wait_slot(&gdone[t & 3], (unsigned)(t >> 2) & 1u);
+          bad = !df_wait_slot(&gdone[t % DF_GD], (unsigned)(t / DF_GD) & 1u);
         }
         if (!bad) {
           df_st_release_cta(&done_l, (unsigned)(t + 1));
@@ -1946,7 +1950,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
     };
     auto finished = [&](int t) {
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(df_smem_addr(&gdone[t & 3])) : "memory");
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(df_smem_addr(&gdone[t % DF_GD])) : "memory");
     };
     auto load_u = [&](float (&ur)[32], int it, int b) {
       const int k = nk - 1 - it, k0 = k * nb, wd = s2::panel_width(g, nb, k0);
@@ -1962,7 +1966,7 @@ __global__ void __launch_bounds__(DF_NT, 1) k_s2_subst_df(const s2::Grid g, S2Wo
       const int lo = k0 - g.kl - g.ku > 0 ? k0 - g.kl - g.ku : 0;
       const float4* x = ring[t % DF_S];
       bool ok = df_wait_slot(&full[t % DF_S], (unsigned)(t / DF_S) & 1u);
-      if (ok) ok = df_wait_slot(&gdone[(t - 1) & 3], (unsigned)((t - 1) >> 2) & 1u);
+      if (ok) ok = df_wait_slot(&gdone[(t - 1) % DF_GD], (unsigned)((t - 1) / DF_GD) & 1u);
       if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) fail();
         return false;
