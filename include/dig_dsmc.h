@@ -235,8 +235,10 @@ int dsmc_hot(dsmc_handle *h, const double *dev_fields, double *dev_hot, double *
  * singular 2D system admits no update) or, in 2D, when positivity cuts a
  * Newton step below 1/1024 of itself (no solution near the state, e.g. a
  * shock the central differences cannot carry), in which case the output is the
- * sampled fields, so that it can still serve as a dig_correct target.  In a
- * batch the worst status of the slabs is returned. */
+ * sampled fields, so that it can still serve as a dig_correct target;
+ * DSMC_ERR_TIMEOUT when a bounded wait of the 2D substitution gave up (its
+ * CTAs wait on one another; no result is written then).  In a batch the
+ * worst status of the slabs is returned. */
 int synth_solve(dsmc_handle *h, const double *dev_fields, const double *dev_hot, double *dev_out,
                 int *host_iters, double *host_resid);
 
