@@ -407,7 +407,9 @@ __global__ void __launch_bounds__(512) k_s2_panel_rot(const s2::Grid g, S2Work w
   int p = 0, pwin = 0;
   // pivot search on frame column fc among positions lo .. hi; the winning
   // rows go to crow[buf] in the frame shifted by sh columns
-  auto search = [&](auto fct, auto sht, int lo, int hi, int buf, int fallback) {
+  // (lim: the frame columns inside the panel before the shift; the columns
+  // past it are written eight at a time only where a chunk reaches inside)
+  auto search = [&](auto fct, auto sht, int lo, int hi, int buf, int fallback, int lim) {
     constexpr int fc = decltype(fct)::value, sh = decltype(sht)::value;
     unsigned key = 0u;
     int bp = INT_MAX, bs = 0;
@@ -424,12 +426,17 @@ __global__ void __launch_bounds__(512) k_s2_panel_rot(const s2::Grid g, S2Work w
     const int pw = __reduce_min_sync(0xffffffffu, key == kw ? bp : INT_MAX);
     if (kw != 0u && key == kw && bp == pw) {
 #pragma unroll
-      for (int c = fc - sh; c + sh < 32; ++c) {
-        float v = a[0][c + sh];
+      for (int q = 0; q < 4; ++q) {
+        if (8 * q + 7 >= fc && 8 * q < lim) {  // chunk q of the frame before the shift
 #pragma unroll
-        for (int s = 1; s < RPT; ++s)
-          if (s == bs) v = a[s][c + sh];
-        crow[buf][warp][c] = v;
+          for (int c = (8 * q > fc ? 8 * q : fc); c < 8 * q + 8; ++c) {
+            float v = a[0][c];
+#pragma unroll
+            for (int s = 1; s < RPT; ++s)
+              if (s == bs) v = a[s][c];
+            crow[buf][warp][c - sh] = v;
+          }
+        }
       }
     }
     if (lane == 0) {
@@ -446,7 +453,7 @@ __global__ void __launch_bounds__(512) k_s2_panel_rot(const s2::Grid g, S2Work w
     p = km == 0u ? fallback : pm;
     pwin = km == 0u ? 0 : __ffs(won) - 1;
   };
-  search(std::integral_constant<int, 0>{}, std::integral_constant<int, 0>{}, 0, s2::panel_rmax(g, H, 0), 0, 0);
+  search(std::integral_constant<int, 0>{}, std::integral_constant<int, 0>{}, 0, s2::panel_rmax(g, H, 0), 0, 0, wd);
   const int ld = g.ld;
 #pragma unroll 1
   for (int jb = 0; jb < wd; jb += 4) {
@@ -503,9 +510,10 @@ __global__ void __launch_bounds__(512) k_s2_panel_rot(const s2::Grid g, S2Work w
         const int rm1 = s2::panel_rmax(g, H, j + 1);
         if constexpr (jj < 3)
           search(std::integral_constant<int, jj + 1>{}, std::integral_constant<int, 0>{}, j + 1, rm1, (j + 1) & 1,
-                 j + 1);
+                 j + 1, live);
         else
-          search(std::integral_constant<int, 4>{}, std::integral_constant<int, 4>{}, j + 1, rm1, (j + 1) & 1, j + 1);
+          search(std::integral_constant<int, 4>{}, std::integral_constant<int, 4>{}, j + 1, rm1, (j + 1) & 1, j + 1,
+                 live);
       }
     };
     step(std::integral_constant<int, 0>{});
