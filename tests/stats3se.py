@@ -17,6 +17,16 @@ puts some outside the bound: p = 0.27 % each.  The number allowed outside is
 the smallest k that independent comparisons exceed with probability below
 1 %, i.e. 0 for up to 3 values, 1 for up to 55, 2 for up to 162; every
 value must still lie within 5 of its standard errors.
+
+Neighbouring cells of a profile are not independent: a fluctuation of the
+flow spans several cells (about a mean free path), so values beyond the
+bound come in runs.  Profiles therefore count runs, not cells: the
+correlation length l (cells) of the replicas' deviations along the profile
+is measured (1 + twice the sum of the lag correlations while they exceed
+0.05), outside values closer than l cells form one run, a run counts once
+per l cells it spans, and the number of runs allowed is that of n / l
+independent regions, each outside with probability at most min(0.5, l p)
+(for uncorrelated cells, l = 1: the rule above).
 """
 from __future__ import annotations
 
@@ -35,14 +45,45 @@ def t_bound(dof: float) -> float:
     return float(stats.t.ppf(1.0 - P_OUT / 2.0, max(dof, 1.0)))
 
 
-def allowed_outside(n: int) -> int:
-    """Smallest k with P(Binomial(n, P_OUT) > k) < ALPHA."""
+def allowed_outside(n: int, p: float = P_OUT) -> int:
+    """Smallest k with P(Binomial(n, p) > k) < ALPHA."""
     k, cdf = 0, 0.0
     while True:
-        cdf += math.comb(n, k) * P_OUT ** k * (1.0 - P_OUT) ** (n - k)
-        if 1.0 - cdf < ALPHA:
+        cdf += math.comb(n, k) * p ** k * (1.0 - p) ** (n - k)
+        if 1.0 - cdf < ALPHA or k >= n:
             return k
         k += 1
+
+
+def corr_length(a: np.ndarray, b: np.ndarray, max_lag: int = 64) -> float:
+    """Correlation length (cells) of profiles a, b (replicas x cells): 1 +
+    twice the sum of the lag-k correlations of the replicas' deviations from
+    their group means (each cell's deviations scaled by their spread), while
+    they exceed 0.05."""
+    dev = np.concatenate([a - a.mean(0), b - b.mean(0)], axis=0)
+    sd = np.sqrt((dev ** 2).mean(0))
+    dev = dev / np.where(sd > 0, sd, 1.0)
+    n = dev.shape[1]
+    c0 = np.mean(dev ** 2)
+    if not c0 > 0:
+        return 1.0
+    tot = 0.0
+    for k in range(1, min(max_lag, n // 4)):
+        r = float(np.mean(dev[:, :-k] * dev[:, k:]) / c0)
+        if r < 0.05:
+            break
+        tot += r
+    return 1.0 + 2.0 * tot
+
+
+def count_runs(idx: np.ndarray, ell: float) -> int:
+    """Runs among the sorted cell indices idx: indices closer than ell cells
+    form one run, and a run counts once per ell cells it spans."""
+    out = 0
+    for run in np.split(idx, np.nonzero(np.diff(idx) >= ell)[0] + 1):
+        if run.size:
+            out += int(math.ceil((run[-1] - run[0] + 1) / ell))
+    return out
 
 
 def pooled(a: np.ndarray, b: np.ndarray, window: int):
@@ -81,14 +122,22 @@ def assert_within_3se(a, b=None, what: str = "", floor: float = 0.0, window: int
     HARD standard errors.  floor: an absolute SE floor for values whose
     spread is exactly zero (e.g. a conserved total).  window > 1 (profiles
     against profiles): the pooled variance averaged over that many
-    neighbouring cells (pooled)."""
-    d, se, dof = pooled(a, b, window) if (window > 1 and b is not None) else welch(a, b)
+    neighbouring cells (pooled), and outside cells counted as runs over
+    the profile's correlation length (count_runs)."""
+    profile = window > 1 and b is not None
+    d, se, dof = pooled(a, b, window) if profile else welch(a, b)
     d, se, dof = np.atleast_1d(d), np.atleast_1d(se) + floor, np.atleast_1d(dof)
     z = np.abs(d) / np.where(se > 0, se, 1e-300)
     thr = np.array([t_bound(v) for v in dof])
-    out = int((z > thr).sum())
-    k = allowed_outside(z.size)
+    idx = np.nonzero(z > thr)[0]
+    if profile:
+        ell = corr_length(np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64))
+        out, unit = count_runs(idx, ell), f"runs (correlation length {ell:.1f} cells) of {z.size} cells"
+        k = allowed_outside(max(1, int(round(z.size / ell))), min(0.5, P_OUT * ell))
+    else:
+        out, unit = idx.size, f"of {z.size}"
+        k = allowed_outside(z.size)
     assert out <= k and np.all(z <= np.maximum(HARD, thr)), (
-        f"{what}: {out} of {z.size} beyond 3 SE (allowed {k}); largest |diff|/SE "
+        f"{what}: {out} {unit} beyond 3 SE (allowed {k}); largest |diff|/SE "
         f"{np.sort(z)[-3:]} at {np.argsort(z)[-3:]}, diff {d[np.argsort(z)[-3:]]}, SE {se[np.argsort(z)[-3:]]}")
     return z
