@@ -298,7 +298,10 @@ int dig_correct(dsmc_handle *h, const double *dev_target);
  *    overlap on the GPU (other streams, other host threads) race on the
  *    array and corrupt each other's results: serialise them.
  *  - Waits on stream between batches of Newton iterations (it reads the
- *    convergence count back) and synchronises it before returning;
+ *    convergence count back) and synchronises it before returning, so it
+ *    cannot be captured into a CUDA graph: on a stream that is capturing
+ *    (or the legacy stream while another stream captures) it returns
+ *    DSMC_ERR_ARG and launches nothing;
  *    host_iters / host_resid (may be NULL) receive the iteration count and
  *    the final max |residual|.  Returns DSMC_OK,
  *    DSMC_ERR_NOT_CONVERGED (outputs written), DSMC_ERR_NUMERIC,

@@ -60,6 +60,15 @@ extern "C" int synth_solve_noalloc(const dsmc_config* cfg, const double* dev_fie
   const double* A = cfg->a_matrix;
   const double det = A[0] * A[3] - A[1] * A[2];
   if (!(det != 0.0) || !std::isfinite(det)) return DSMC_ERR_ARG;
+  // the call waits on the stream, which a capturing stream cannot do:
+  // refuse before launching anything (an implicit capture of the legacy
+  // stream reports itself as an error of the query)
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const cudaError_t qe = cudaStreamIsCapturing(st, &cap);
+  if (qe == cudaErrorStreamCaptureImplicit) return DSMC_ERR_ARG;
+  if (qe != cudaSuccess) return DSMC_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return DSMC_ERR_ARG;
   double* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc) return rc;
@@ -83,7 +92,6 @@ extern "C" int synth_solve_noalloc(const dsmc_config* cfg, const double* dev_fie
   cp.kn_ref = cfg->kn_ref;
   const int n_m = cfg->n_m > 0 ? cfg->n_m : 2000;
   const double tol = cfg->synth_tol > 0 ? cfg->synth_tol : 1e-5;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   double* info_dev = scratch + kInfoOffset;
   // every scratch word the kernel reads it has written first in the same
   // call, so nothing needs clearing between calls
