@@ -15,8 +15,12 @@ freedom of a single cell.
 Where many values are compared at once (cells, rings, regions), chance alone
 puts some outside the bound: p = 0.27 % each.  The number allowed outside is
 the smallest k that independent comparisons exceed with probability below
-1 %, i.e. 0 for up to 3 values, 1 for up to 55, 2 for up to 162; every
-value must still lie within 5 of its standard errors.
+1 %, i.e. 0 for up to 3 values, 1 for up to 55, 2 for up to 162.  No
+value may lie beyond 5 of its standard errors, or, where few replicas give
+the t variable a heavier tail than that, beyond the t point that any of the
+n values exceeds with probability below 1 % (ALPHA / n each, Bonferroni,
+valid however the values are correlated): 6.8 SE for 200 cells at 10
+degrees of freedom, 5 SE at 31 degrees of freedom and more.
 
 Neighbouring cells of a profile are not independent: a fluctuation of the
 flow spans several cells (about a mean free path), so values beyond the
@@ -37,6 +41,13 @@ import numpy as np
 P_OUT = 0.0027      # two-sided tail beyond 3 standard errors of a normal variable
 ALPHA = 0.01        # false-alarm probability of a whole comparison
 HARD = 5.0          # no value beyond this many standard errors
+
+
+def hard_bound(dof, n: int):
+    """The bound no value may exceed: HARD, or the two-sided t point at
+    level ALPHA / n where the t variable's tail is heavier."""
+    from scipy import stats
+    return np.maximum(HARD, stats.t.ppf(1.0 - ALPHA / (2.0 * n), np.maximum(dof, 1.0)))
 
 
 def t_bound(dof: float) -> float:
@@ -119,7 +130,7 @@ def welch(a: np.ndarray, b: np.ndarray | None = None):
 def assert_within_3se(a, b=None, what: str = "", floor: float = 0.0, window: int = 0):
     """Replicas a against replicas b (or against 0): every compared value
     within the 3-SE bound, up to allowed_outside(n) of them, and none beyond
-    HARD standard errors.  floor: an absolute SE floor for values whose
+    hard_bound standard errors.  floor: an absolute SE floor for values whose
     spread is exactly zero (e.g. a conserved total).  window > 1 (profiles
     against profiles): the pooled variance averaged over that many
     neighbouring cells (pooled), and outside cells counted as runs over
@@ -137,7 +148,7 @@ def assert_within_3se(a, b=None, what: str = "", floor: float = 0.0, window: int
     else:
         out, unit = idx.size, f"of {z.size}"
         k = allowed_outside(z.size)
-    assert out <= k and np.all(z <= np.maximum(HARD, thr)), (
+    assert out <= k and np.all(z <= np.maximum(hard_bound(dof, z.size), thr)), (
         f"{what}: {out} {unit} beyond 3 SE (allowed {k}); largest |diff|/SE "
         f"{np.sort(z)[-3:]} at {np.argsort(z)[-3:]}, diff {d[np.argsort(z)[-3:]]}, SE {se[np.argsort(z)[-3:]]}")
     return z

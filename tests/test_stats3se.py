@@ -5,7 +5,7 @@ of five may lie outside 3 standard errors, none beyond 5)."""
 import numpy as np
 import pytest
 
-from stats3se import allowed_outside, assert_within_3se, corr_length, count_runs, t_bound
+from stats3se import allowed_outside, assert_within_3se, corr_length, count_runs, hard_bound, t_bound
 
 
 def test_bounds():
@@ -96,3 +96,13 @@ def test_correlated_profile_false_alarm_rate_and_power():
         a[:, lo:hi] += shift * se[lo:hi]
         with pytest.raises(AssertionError):
             assert_within_3se(a, b, what="shifted", window=9)
+
+
+def test_hard_bound():
+    """5 SE wherever the t variable's tail is no heavier; with 10 degrees of
+    freedom over 200 cells the point that any cell passes with probability
+    1 % (Bonferroni)."""
+    assert hard_bound(1e7, 200) == 5.0 and hard_bound(31, 5) == 5.0
+    assert 6.7 < hard_bound(10, 200) < 6.8
+    from scipy import stats
+    assert abs(200 * 2 * stats.t.sf(hard_bound(10, 200), 10) - 0.01) < 1e-9
