@@ -72,8 +72,8 @@ def test_correlation_length_and_runs():
 
 
 def test_correlated_profile_false_alarm_rate_and_power():
-    """Profiles whose cells are correlated over ~20 cells (as sampled DSMC
-    fields are, over about a mean free path): outside cells come in runs,
+    """Profiles whose cells are correlated over ~20 cells (sampled DSMC
+    profiles are, over 10 to 85 cells): outside cells come in runs,
     and the run count keeps the false-alarm rate near 1 %, where counting
     cells raised it to ~3.5 %.  A shift of 4.5 standard errors over 60
     cells still fails, and so does one of 8 over 3 cells."""
